@@ -14,8 +14,13 @@ diagonal of scales.
 Readings (the paper is silent on these):
   - quaternion order (w, x, y, z), normalised before use;
   - scales are exp(log_scale), so S S^T = diag(exp(2 log_scale));
-  - J is the Jacobian of the map above with rho = sqrt(x'^2 + z'^2) replaced
-    by max(rho, 1e-3 |x'|) to keep it finite at the zenith;
+  - J is the Jacobian of the map above, except that in the azimuth row the
+    factor 1/rho (rho = sqrt(x'^2 + z'^2)) is capped at 1/max(rho, 1e-3 |x'|)
+    while the row keeps its direction (z'/rho, 0, -x'/rho); exactly at the
+    zenith that direction is taken as (1, 0, 0).  The elevation row is exact.
+    Near the zenith the azimuth of a direction changes faster than any
+    footprint the linearisation can describe, and this keeps the footprint
+    wide in azimuth (every column) instead of collapsing it;
   - 0.3 px^2 is added to the diagonal of Sigma' (3D Gaussian Splatting
     practice, on which the paper builds);
   - a Gaussian closer than r_near to the receiver is culled;
@@ -63,17 +68,21 @@ def equirect_map(xp: torch.Tensor, H: int, W: int):
 
 
 def map_jacobian(xp: torch.Tensor, H: int, W: int) -> torch.Tensor:
-    """d(p_x, p_y)/d(x', y', z'), a [.., 2, 3] matrix, with the zenith floor on rho."""
+    """d(p_x, p_y)/d(x', y', z'), a [.., 2, 3] matrix, with the zenith cap on 1/rho."""
     x, y, z = xp.unbind(-1)
     r2 = (xp * xp).sum(-1)
     r = torch.sqrt(r2)
     rho = torch.sqrt(x * x + z * z)
-    rho = torch.maximum(rho, RHO_FLOOR * r)
+    pos = rho > 0
+    safe = torch.where(pos, rho, torch.ones_like(rho))
+    cx = torch.where(pos, x / safe, torch.zeros_like(x))     # sin(azimuth)
+    cz = torch.where(pos, z / safe, torch.ones_like(z))      # cos(azimuth)
+    rho_cap = torch.maximum(rho, RHO_FLOOR * r)
     sx = W / (2.0 * math.pi)
     sy = 2.0 * H / math.pi
     zero = torch.zeros_like(x)
-    row0 = torch.stack([sx * z / (rho * rho), zero, -sx * x / (rho * rho)], -1)
-    row1 = torch.stack([-sy * x * y / (r2 * rho), sy * rho / r2, -sy * z * y / (r2 * rho)], -1)
+    row0 = torch.stack([sx * cz / rho_cap, zero, -sx * cx / rho_cap], -1)
+    row1 = torch.stack([-sy * y * cx / r2, sy * rho / r2, -sy * y * cz / r2], -1)
     return torch.stack([row0, row1], -2)
 
 

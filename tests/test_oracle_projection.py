@@ -155,3 +155,34 @@ def test_cull_and_extents():
     # at the bounding box's x extent the kernel equals 1/255 along the principal axis
     qv = out["ext_x"][1] ** 2 * out["cxx"][1]
     np.testing.assert_allclose(math.exp(-0.5 * qv.item()), 1 / 255.0, rtol=1e-12)
+
+
+def test_zenith_footprint_closed_form():
+    """Exactly at the zenith (x' = z' = 0) the azimuth row of J is (s_x / (1e-3 r), 0, 0)
+    and the elevation row (0, 0, -s_y / r), so for an isotropic Gaussian
+    Sigma' = diag(s^2 s_x^2 / (1e-3 r)^2, s^2 s_y^2 / r^2) + 0.3 I: the footprint spans
+    every azimuth column."""
+    r, s = 3.0, 0.2
+    out = P.project(torch.tensor([[0.0, r, 0.0]], dtype=torch.float64),
+                    torch.full((1, 3), math.log(s), dtype=torch.float64),
+                    torch.tensor([[1.0, 0, 0, 0]], dtype=torch.float64), _view())
+    sx = sy = 180.0 / math.pi
+    np.testing.assert_allclose(out["sxx"].item(), s * s * sx * sx / (1e-3 * r) ** 2 + 0.3, rtol=1e-12)
+    np.testing.assert_allclose(out["syy"].item(), s * s * sy * sy / r ** 2 + 0.3, rtol=1e-12)
+    assert abs(out["sxy"].item()) < 1e-9
+    assert out["ext_x"].item() > 180.0
+    np.testing.assert_allclose(out["py"].item(), 90.0, rtol=1e-14)
+
+
+def test_jacobian_cap_continuous_at_threshold():
+    """Just outside the cap the azimuth row is the exact 1/rho; inside it is capped
+    at 1/(1e-3 r) with the same direction: the row's norm is continuous at rho = 1e-3 r."""
+    r = 2.0
+    rhos = np.array([0.5e-3, 0.999e-3, 1.0e-3, 1.001e-3, 2e-3]) * r
+    ang = 0.7
+    xp = np.stack([rhos * math.sin(ang), np.sqrt(r * r - rhos ** 2), rhos * math.cos(ang)], 1)
+    J = P.map_jacobian(torch.tensor(xp), 90, 360).numpy()
+    sx = 180.0 / math.pi
+    expect = sx / np.maximum(rhos, 1e-3 * r)
+    np.testing.assert_allclose(np.linalg.norm(J[:, 0, :], axis=1), expect, rtol=1e-12)
+    np.testing.assert_allclose(J[:, 0, 0] / np.linalg.norm(J[:, 0, :], axis=1), math.cos(ang), rtol=1e-12)
