@@ -1,0 +1,436 @@
+"""Benchmark of the splatting hot path on one GB300 (or N independent replicas).
+
+Workload (one step = one pass of the whole path over one query):
+  50,000 Gaussians (seeded synthetic scene: means uniform in a 10 m cube
+  around the receiver, upper hemisphere; log-scales N(-1.5, 0.5); random unit
+  quaternions; opacity logits N(0,1); 16-dim latents N(0,1)), one transmitter,
+  64 subcarriers 312.5 kHz apart about 2.4 GHz, 360x90 hemisphere (1-degree
+  bins, 16x16 tiles), attribute network 20 -> 32 -> 32 -> 3 in FP32.
+  Step = project -> bin/sort -> attribute network -> render forward ->
+  complex L2 loss against a target spectrum (rendered by the same path from a
+  second seeded scene, once, outside the timed region) -> render backward ->
+  network backward -> projection backward.
+
+Metric: Gaussian-pixel-subcarrier units per second, where a unit is one
+Gaussian composited at one pixel (counted up to termination by the forward
+kernel's per-pixel counter) for one subcarrier; fwd+bwd per step.
+
+`value` times the step on the device with inputs resident in HBM (CUDA
+events on the launching stream, L2 flushed by a 256 MiB write between timed
+steps); `e2e` times the same step through the C ABI with the scene, network
+and target copied from pinned host memory and the loss read back, inside the
+timed region.  `roofline` reports the dominant kernel against the FP32 ALU
+peak; `cpu_baseline` times the FP64 oracle on a bounded pixel sample.
+
+Multi-GPU: queries are independent, so N ranks run N replicas on their own
+transmitters (weak scaling) with no data-path collective; timing is the max
+over ranks.  `--impl reference` times the FP64 CPU oracle as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gaussian·pixel·subcarrier/s fwd+bwd and p50/p99 spectrum latency vs plain GPU path"
+UNIT = "Gaussian·pixel·subcarrier/s"
+WORKLOAD = dict(name="fwd+bwd, 50k Gaussians, 64 subcarriers, 360x90, hidden 32, 1 transmitter",
+                n=50_000, K=64, H=90, W=360, hidden=32, B=1, f_c=2.4e9, df=312.5e3)
+FLOP_FWD_UNIT = 4     # z += w * e^{j psi}: two FMAs per (pixel, Gaussian, subcarrier)
+FLOP_BWD_UNIT = 12    # Re, Im and frequency-weighted Im of conj(g) e^{j psi}: six FMAs
+FP32_LANES_PER_SM = 128
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+# --------------------------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2511_22793_gb300 import gsparc as G
+    from paper_2511_22793_gb300 import synth
+    from paper_2511_22793_gb300.pipeline import DeviceMLP, DeviceScene, Renderer
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    wl = WORKLOAD
+    n, K, H, W, hidden, B = wl["n"], wl["K"], wl["H"], wl["W"], wl["hidden"], wl["B"]
+    sc = synth.make_scene(n, seed=0)
+    mlp = synth.make_mlp(hidden, seed=3)
+    tx = synth.make_tx(B + world, seed=2)[rank:rank + B]
+    r = Renderer(H, W, K, n, f_c=wl["f_c"], df=wl["df"], device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # target spectrum: the same path on a second seeded scene (not timed)
+    sc_t = synth.make_scene(n, seed=1)
+    rt = Renderer(H, W, K, n, f_c=wl["f_c"], df=wl["df"], device=dev)
+    dst = DeviceScene.from_host(sc_t, dev)
+    dm = DeviceMLP.from_host(mlp, dev)
+    txd = torch.tensor(tx, device=dev)
+    rt.geometry(dst)
+    target = rt.render(rt.attributes(dst, dm, txd))[0].clone()
+    del rt, dst
+
+    ds = DeviceScene.from_host(sc, dev)
+    attr = torch.empty((B, n, 4), device=dev)
+    spec, logT, nc = r.alloc_outputs(B)
+    n_used = torch.zeros((B, H, W), dtype=torch.int32, device=dev)
+    loss = torch.zeros(1, device=dev)
+    d_spec = torch.empty_like(spec)
+    d_attr = torch.empty_like(attr)
+    d_proj = torch.empty_like(r.proj)
+    grads = [torch.empty_like(t) for t in ds.tensors()] + [torch.empty_like(t) for t in dm.tensors()]
+    mlp_s = dm.struct()
+    grad_s = G.make_mlp_grad(*grads[5:])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    launches_per_step = 0
+    ev = {}
+
+    def stage(name, fn):
+        if name in ev:
+            ev[name][0].record(stream)
+        fn()
+        if name in ev:
+            ev[name][1].record(stream)
+
+    def step(scene: DeviceScene, tgt, timed_kernels=False):
+        for t in grads:
+            t.zero_()
+        d_attr.zero_()
+        d_proj.zero_()
+        stage("project", lambda: G.gsparc_project(r.view, scene.means, scene.log_scales, scene.quats,
+                                                  r.proj))
+        stage("bin_sort", lambda: G.gsparc_bin_sort(r.view, n, r.proj, r.capacity, r.ws, r.sorted_ids,
+                                                    None, r.tile_ranges, r.n_pairs, r.status))
+        stage("attr_mlp", lambda: G.gsparc_attr_mlp(txd, r.rx, scene.means, scene.opacity_logit,
+                                                    scene.latent, mlp_s, G.GSPARC_FP32, attr))
+        stage("render_fwd", lambda: G.gsparc_render_fwd(r.view, r.band, B, n, r.proj, r.tile_ranges,
+                                                        r.sorted_ids, attr, spec, logT, nc, n_used))
+        stage("l2_loss", lambda: G.gsparc_l2_loss(spec, tgt, loss, d_spec))
+        stage("render_bwd", lambda: G.gsparc_render_bwd(r.view, r.band, B, n, r.proj, r.tile_ranges,
+                                                        r.sorted_ids, attr, logT, nc, d_spec, d_attr,
+                                                        d_proj))
+        stage("attr_mlp_bwd", lambda: G.gsparc_attr_mlp_bwd(txd, r.rx, scene.means, scene.opacity_logit,
+                                                            scene.latent, mlp_s, d_attr, grads[0],
+                                                            grads[3], grads[4], grad_s))
+        stage("project_bwd", lambda: G.gsparc_project_bwd(r.view, scene.means, scene.log_scales,
+                                                          scene.quats, d_proj, grads[0], grads[1],
+                                                          grads[2]))
+
+    # kernels of ours launched per step: project 1, bin/sort 6 + passes, network 1, render 1,
+    # loss 1, render bwd 1, network bwd 1, projection bwd 1
+    T = r.T
+    bits = 0
+    while (1 << bits) < T:
+        bits += 1
+    passes = 4 + (bits + 7) // 8
+    launches_per_step = 1 + (6 + passes) + 1 + 1 + 1 + 1 + 1 + 1
+
+    for _ in range(args.warmup):
+        step(ds, target)
+    torch.cuda.synchronize(dev)
+    st = r.check()
+    if st != 0:
+        raise RuntimeError("device status %d after warm-up" % st)
+    units = int(n_used.sum().item()) * K
+    n_pairs = int(r.n_pairs.item())
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+    names = ["project", "bin_sort", "attr_mlp", "render_fwd", "l2_loss", "render_bwd", "attr_mlp_bwd",
+             "project_bwd"]
+    per_kernel = {k: [] for k in names}
+    step_ms = []
+    sampler = ClockSampler(local_rank)
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    for _ in range(args.steps):
+        flush.fill_(1.0)                      # evict L2 between timed steps (not timed)
+        for k in names:
+            ev[k] = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        step(ds, target)
+        s1.record(stream)
+        s1.synchronize()
+        step_ms.append(s0.elapsed_time(s1))
+        for k in names:
+            per_kernel[k].append(ev[k][0].elapsed_time(ev[k][1]))
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ev.clear()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        tdist.barrier()
+
+    # end to end: host (pinned) inputs copied in, loss read back, through the C ABI
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in sc.arrays()]
+    host_w = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in mlp.arrays()]
+    host_tgt = target.cpu().pin_memory()
+    host_tx = txd.cpu().pin_memory()
+    host_loss = torch.empty(1).pin_memory()
+    dev_scene = [torch.empty_like(t) for t in ds.tensors()]
+    dev_w = [torch.empty_like(t) for t in dm.tensors()]
+    dev_tgt = torch.empty_like(target)
+    h2d = sum(t.numel() * t.element_size() for t in host + host_w + [host_tgt, host_tx])
+    d2h = host_loss.numel() * host_loss.element_size()
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for d, h in zip(dev_scene + dev_w + [dev_tgt, txd], host + host_w + [host_tgt, host_tx]):
+            d.copy_(h, non_blocking=True)
+        scene_e = DeviceScene(*dev_scene)
+        step(scene_e, dev_tgt)
+        host_loss.copy_(loss, non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+        if it >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    if dist:
+        t = torch.tensor([sum(e2e_ms)], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    else:
+        e2e_total = sum(e2e_ms)
+
+    # dominant kernel and its roofline
+    avg = {k: statistics.mean(v) for k, v in per_kernel.items()}
+    top = max(avg, key=avg.get)
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12      # TFLOP/s
+    unit_flop = {"render_bwd": FLOP_BWD_UNIT, "render_fwd": FLOP_FWD_UNIT}
+    if top in unit_flop:
+        achieved = units * unit_flop[top] / (avg[top] * 1e-3) / 1e12
+        roofline = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                    "peak_note": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)"
+                                 % (sms, sm_max)}
+    else:
+        roofline = {"kernel": top, "bound": "hbm", "achieved": None,
+                    "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s", "frac": None,
+                    "traffic": None}
+
+    value = units * args.steps * world / (total_ms * 1e-3)
+    e2e_value = units * args.steps * world / (e2e_total * 1e-3)
+    sorted_ms = sorted(step_ms)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+        "config": {"workload": wl["name"], "n_gaussians": n, "subcarriers": K, "H": H, "W": W,
+                   "hidden": hidden, "transmitters_per_step": B, "pairs": n_pairs,
+                   "units_per_step": units, "l2": "flushed (256 MiB write) between timed steps",
+                   "parallelism": "replicas x%d" % world},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                       "min": sorted_ms[0]},
+        "kernels_ms": avg,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_total / args.steps},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": roofline,
+        "clocks": clocks,
+    }
+    return out, units, sc, mlp, tx
+
+
+def cpu_baseline(sample_pixels, seed=0, threads=0, sc=None, mlp=None, tx=None):
+    """FP64 oracle, fwd + bwd, on a seeded pixel sample of the same workload."""
+    from oracle import pipeline as opl
+    from oracle import render as orender
+    from paper_2511_22793_gb300 import synth
+
+    wl = WORKLOAD
+    n, K, H, W, hidden = wl["n"], wl["K"], wl["H"], wl["W"], wl["hidden"]
+    if sc is None:
+        sc = synth.make_scene(n, seed=0)
+        mlp = synth.make_mlp(hidden, seed=3)
+        tx = synth.make_tx(1, seed=2)
+    orender.build()
+    sample_pixels = min(sample_pixels, H * W)
+    rng = np.random.default_rng(seed)
+    pix = np.sort(rng.choice(H * W, size=sample_pixels, replace=False)).astype(np.int32)
+    view, band = synth.View(H=H, W=W), synth.Band(K=K, f_c=wl["f_c"], df=wl["df"])
+    # unit count of the sample (untimed): Gaussians composited per pixel x K
+    counted = opl.forward(sc, mlp, view, band, tx[:1], pixels=pix, threads=threads)
+    units = int(counted["n_used"].sum()) * K
+    target = np.zeros((1, sample_pixels, K), dtype=np.complex128)
+    t0 = time.perf_counter()
+    opl.loss_and_grad(sc, mlp, view, band, tx[:1], target, pixels=pix, threads=threads)
+    dt = time.perf_counter() - t0
+    cores = threads if threads > 0 else (os.cpu_count() or 1)
+    what = "the full %dx%d image" % (W, H) if sample_pixels == H * W else \
+        "%d seeded pixels of the %dx%d image" % (sample_pixels, W, H)
+    return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%s, one transmitter, forward + FP64 analytic backward (loss and all "
+                      "parameter gradients)" % what, "seconds": dt, "units": units}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, on bounded pixel samples."""
+    from paper_2511_22793_gb300 import synth
+
+    wl = WORKLOAD
+    sc = synth.make_scene(wl["n"], seed=0)
+    mlp = synth.make_mlp(wl["hidden"], seed=3)
+    tx = synth.make_tx(1, seed=2)
+    per_step = 1024
+    for i in range(args.warmup):
+        cpu_baseline(per_step, seed=100 + i, sc=sc, mlp=mlp, tx=tx)
+    secs, units = 0.0, 0
+    for i in range(args.steps):
+        r = cpu_baseline(per_step, seed=i, sc=sc, mlp=mlp, tx=tx)
+        secs += r["seconds"]
+        units += r["units"]
+    value = units / secs
+    cores = os.cpu_count() or 1
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)",
+        "config": {"workload": wl["name"], "n_gaussians": wl["n"], "subcarriers": wl["K"], "H": wl["H"],
+                   "W": wl["W"], "hidden": wl["hidden"], "sample_pixels_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d seeded pixels per step, forward + FP64 analytic backward" % per_step},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=90 * 360,
+                    help="pixels in the oracle CPU baseline (default: the whole image)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    out, units, sc, mlp, tx = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args.cpu_sample, sc=sc, mlp=mlp, tx=tx)
+            out["cpu_baseline"].pop("units", None)
+            out["cpu_baseline"]["seconds"] = round(out["cpu_baseline"]["seconds"], 3)
+        else:
+            out["cpu_baseline"] = None
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,249 @@
+/*
+ * gsparc.h — C ABI of the GB300 (sm_103a) equirectangular Gaussian-splatting
+ * library for RF spectra (the GSpaRC hot path).
+ *
+ * Conventions (all entry points):
+ *   - Every function returns an int status (GSPARC_OK or a negative code);
+ *     no C++ exception crosses this boundary.
+ *   - Every pointer argument named like a tensor is DEVICE memory owned by the
+ *     caller, unless the comment says host.  The library never allocates
+ *     device memory; scratch space comes from a caller-provided workspace
+ *     whose size a *_workspace query returns.
+ *   - Every call takes a CUDA stream (cudaStream_t passed as void*, NULL for
+ *     the legacy default stream), only enqueues work on it and returns without
+ *     synchronising.  Argument errors are detected on the host before anything
+ *     is enqueued.  Conditions only the device can see (a pair list longer
+ *     than its capacity, an expired bounded wait) are written to a
+ *     caller-provided device int32 status word; gsparc_check() reads it.
+ *   - All float tensors are row-major FP32 unless stated otherwise; complex
+ *     values are interleaved (re, im) FP32 pairs.
+ *   - Gradient entry points (*_bwd) ACCUMULATE (+=) into their gradient
+ *     outputs; the caller zeroes them first.
+ *
+ * Notation follows the paper (arxiv 2511.22793): means mu, covariance
+ * Sigma = R S S^T R^T, opacity sigma, complex emission s, receiver-centric
+ * coordinates x' = V (mu - x_rx), equirectangular pixel (p_x, p_y).
+ */
+#ifndef GSPARC_H
+#define GSPARC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define GSPARC_OK 0
+#define GSPARC_ERR_INVALID (-1)   /* bad argument (detected on the host)          */
+#define GSPARC_ERR_WORKSPACE (-2) /* workspace smaller than the query returned    */
+#define GSPARC_ERR_CUDA (-3)      /* a CUDA runtime call or launch failed         */
+#define GSPARC_ERR_TIMEOUT (-4)   /* a bounded device-side wait gave up           */
+#define GSPARC_ERR_CAPACITY (-5)  /* more (Gaussian, tile) pairs than capacity    */
+
+/* ---- fixed sizes ------------------------------------------------------- */
+#define GSPARC_TILE 16       /* pixels per tile side                              */
+#define GSPARC_LATENT 16     /* per-Gaussian latent width                         */
+#define GSPARC_MLP_IN 20     /* network input: tx (3), latent (16), log d (1)     */
+#define GSPARC_PROJ_STRIDE 8 /* floats per projection record                      */
+
+/* Arithmetic of the attribute network (gsparc_attr_mlp). */
+#define GSPARC_FP32 0   /* FP32 on CUDA cores                                        */
+#define GSPARC_BF16 1   /* hidden layer on tensor cores, BF16 operands, FP32 accum.   */
+#define GSPARC_BF16X2 2 /* as BF16 with each activation split into two BF16 terms    */
+
+/*
+ * Receiver view and hemisphere grid (Sec. 4.2, "Directional Projection and
+ * Splatting"): x' = V (mu - rx); H rows of elevation (row 0 at the horizon,
+ * row H-1 at the zenith, 90/H degrees each), W columns of azimuth (column W/2
+ * looks along +z', 360/W degrees each).  Gaussians closer than near_dist to
+ * the receiver are culled.  Host struct, passed by pointer.
+ */
+typedef struct gsparc_view {
+    int32_t H, W;
+    float rx[3];
+    float V[9]; /* row-major 3x3, rotation world -> receiver frame */
+    float near_dist;
+} gsparc_view;
+
+/*
+ * Subcarriers (Sec. 3.1 channel model; Sec. 5 multi-subcarrier CSI):
+ * f_k = f_c + (k - floor(K/2)) df, k = 0..K-1.  Host struct.
+ */
+typedef struct gsparc_band {
+    int32_t K;
+    int32_t reserved;
+    double f_c, df; /* Hz */
+} gsparc_band;
+
+/*
+ * Attribute network shared by all Gaussians (Eq. 1): input
+ * h0 = [tx (3), latent (16), log d (1)], two ReLU hidden layers of width
+ * `hidden` (8, 16, 32 or 64), three outputs.  Weights are input-major device
+ * FP32 arrays: W1 [20, hidden], W2 [hidden, hidden], W3 [hidden, 3].
+ * Host struct holding device pointers.
+ */
+typedef struct gsparc_mlp {
+    int32_t hidden;
+    int32_t reserved;
+    const float *W1, *b1, *W2, *b2, *W3, *b3;
+} gsparc_mlp;
+
+/* Gradient buffers of the network, same shapes as gsparc_mlp (device). */
+typedef struct gsparc_mlp_grad {
+    float *W1, *b1, *W2, *b2, *W3, *b3;
+} gsparc_mlp_grad;
+
+/* Number of 16x16 tiles covering the view: ceil(W/16) * ceil(H/16). */
+int32_t gsparc_num_tiles(const gsparc_view* view);
+
+/*
+ * Project N Gaussians onto the equirectangular hemisphere (Sec. 4.2: view
+ * transform, map p_x = (atan2(x', z')/pi + 1) W/2, p_y = 2 asin(y'/|x'|) H/pi,
+ * and Sigma' = J V Sigma V^T J^T; Algorithm 1 CullGaussians / TransformToView
+ * / ProjectGaussians).  Sigma = R(q) diag(exp(2 log_scales)) R(q)^T (Sec. 3.2).
+ *   means [N,3], log_scales [N,3], quats [N,4] as (w, x, y, z), any norm > 0.
+ *   proj [N,8] out: (p_x, p_y, ext_x, ext_y, c_xx, c_xy, c_yy, r), where c is
+ *   the conic (Sigma' + 0.3 I)^-1, ext the footprint half extents
+ *   sqrt(2 ln 255 * diag(Sigma' + 0.3 I)) in pixels and r = |x'|.  Culled
+ *   Gaussians (r < near_dist) get ext_x = ext_y = -1.
+ * Errors: GSPARC_ERR_INVALID for N < 0, a null pointer with N > 0 or a
+ * non-positive H or W.
+ */
+int gsparc_project(const gsparc_view* view, int32_t N, const float* means, const float* log_scales,
+                   const float* quats, float* proj, void* stream);
+
+/*
+ * Gradient of gsparc_project (Sec. 4.2 map and Sigma'; Algorithm 1 Backprop).
+ * d_proj [N,8] holds dL/d(p_x, p_y, -, -, c_xx, c_xy, c_yy, -) (slots 2, 3, 7
+ * are ignored).  Accumulates into d_means [N,3], d_log_scales [N,3],
+ * d_quats [N,4].
+ */
+int gsparc_project_bwd(const gsparc_view* view, int32_t N, const float* means,
+                       const float* log_scales, const float* quats, const float* d_proj,
+                       float* d_means, float* d_log_scales, float* d_quats, void* stream);
+
+/*
+ * Bytes of workspace gsparc_bin_sort needs for N Gaussians and room for
+ * pair_capacity (Gaussian, tile) pairs.  *ws_bytes is a host pointer.
+ */
+int gsparc_bin_sort_workspace(const gsparc_view* view, int32_t N, int64_t pair_capacity,
+                              size_t* ws_bytes);
+
+/*
+ * Tile binning and directional sorting (Algorithm 1 IntersectGaussians and
+ * "sort by depth to receiver"; Sec. 1 "directional sorting").  For every
+ * Gaussian, the 16x16 tiles its footprint box touches (azimuth wrapping at
+ * +-pi) each get one pair with the 64-bit key (tile_id << 32) | bits(r); the
+ * pairs, emitted in Gaussian-index order, are sorted stably by key with an
+ * LSD radix sort (8-bit digits, one-sweep passes with decoupled look-back),
+ * so every tile's list is ordered by (r, index).
+ *   proj [N,8]: records from gsparc_project (only p, ext and r are read).
+ *   ws: device workspace of ws_bytes >= gsparc_bin_sort_workspace().
+ *   sorted_ids [pair_capacity] out: Gaussian id of each sorted pair.
+ *   sorted_keys [pair_capacity] out, may be NULL: the sorted keys.
+ *   tile_ranges [num_tiles, 2] out: [start, end) of each tile in sorted_ids
+ *   (start == end for an empty tile).
+ *   n_pairs [1] out (device): number of pairs.
+ *   d_status [1] (device): set to GSPARC_ERR_CAPACITY if the pairs exceed
+ *   pair_capacity (only the first pair_capacity are then sorted) and to
+ *   GSPARC_ERR_TIMEOUT if a look-back wait expired.
+ * Pair capacity must be below 2^31.
+ */
+int gsparc_bin_sort(const gsparc_view* view, int32_t N, const float* proj, int64_t pair_capacity,
+                    void* ws, size_t ws_bytes, uint32_t* sorted_ids, uint64_t* sorted_keys,
+                    uint32_t* tile_ranges, uint32_t* n_pairs, int32_t* d_status, void* stream);
+
+/*
+ * Attribute network for B transmitter positions (Eq. 1 with the 1/d of the
+ * Sec. 4.2 compositing rule; query = transmitter, receiver fixed).
+ *   d_i = max(|mu_i - tx_b|, 0.01); o = MLP([tx_b, latent_i, ln d_i]);
+ *   attr[b,i] = (a, phi0, sigma, L) with a = sigmoid(o_0 - ln d_i)/d_i,
+ *   phi0 = o_1, sigma = sigmoid(opacity_logit_i + o_2),
+ *   L = d_i + |mu_i - rx| (path length, metres).
+ *   tx [B,3] device; rx [3] HOST; means [N,3]; opacity_logit [N]; latent [N,16];
+ *   attr [B,N,4] out.  precision: GSPARC_FP32, GSPARC_BF16 or GSPARC_BF16X2.
+ */
+int gsparc_attr_mlp(int32_t N, int32_t B, const float* tx, const float* rx, const float* means,
+                    const float* opacity_logit, const float* latent, const gsparc_mlp* mlp,
+                    int32_t precision, float* attr, void* stream);
+
+/*
+ * Gradient of gsparc_attr_mlp in FP32 (Algorithm 1 Backprop through the
+ * network), recomputing the forward activations.  d_attr [B,N,4] holds
+ * dL/d(a, phi0, sigma, L).  Accumulates into d_means [N,3], d_opacity_logit
+ * [N], d_latent [N,16] and every buffer of *grads.
+ */
+int gsparc_attr_mlp_bwd(int32_t N, int32_t B, const float* tx, const float* rx, const float* means,
+                        const float* opacity_logit, const float* latent, const gsparc_mlp* mlp,
+                        const float* d_attr, float* d_means, float* d_opacity_logit,
+                        float* d_latent, const gsparc_mlp_grad* grads, void* stream);
+
+/*
+ * Front-to-back compositing of complex contributions across subcarriers
+ * (Sec. 4.2 compositing rule; Algorithm 1 inner loop): for every pixel u and
+ * subcarrier k of every transmitter b,
+ *   z[b,k,u] = sum_i T_i alpha_i a_i exp(j(phi0_i - 2 pi f_k L_i / c)),
+ *   alpha_i = min(0.99, sigma_i exp(-q_i(u)/2)), T_i = prod_{j<i}(1 - alpha_j),
+ * over the tile's list in (r, index) order, skipping q > 2 ln 255 or
+ * alpha < 1/255 and stopping before T would fall below 1e-4.  T is carried
+ * as log2 T in FP32.
+ *   proj [N,8], tile_ranges [num_tiles,2], sorted_ids: from gsparc_bin_sort.
+ *   attr [B,N,4]: from gsparc_attr_mlp.
+ *   spectrum [B,K,H,W,2] out (complex, interleaved).
+ *   final_logT [B,H,W] out, may be NULL: log2 of the transmittance left.
+ *   n_contrib [B,H,W] out, may be NULL: 1 + position (within the tile list)
+ *   of the last Gaussian composited, 0 if none.  gsparc_render_bwd needs both.
+ *   n_used [B,H,W] out, may be NULL: number of Gaussians composited at the
+ *   pixel (the algorithmic work per pixel and subcarrier).
+ */
+int gsparc_render_fwd(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
+                      const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
+                      const float* attr, float* spectrum, float* final_logT, uint32_t* n_contrib,
+                      uint32_t* n_used, void* stream);
+
+/*
+ * Gradient of gsparc_render_fwd (Algorithm 1 Backprop through compositing and
+ * splatting).  Walks each pixel's list back to front from n_contrib,
+ * recovering T_i from final_logT by subtracting log2(1 - alpha_i), so no
+ * per-pair state is stored.  d_spectrum [B,K,H,W,2] holds dL/dRe z, dL/dIm z.
+ * Accumulates dL/d(a, phi0, sigma, L) into d_attr [B,N,4] and
+ * dL/d(p_x, p_y, -, -, c_xx, c_xy, c_yy, -) into d_proj [N,8].
+ */
+int gsparc_render_bwd(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
+                      const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
+                      const float* attr, const float* final_logT, const uint32_t* n_contrib,
+                      const float* d_spectrum, float* d_attr, float* d_proj, void* stream);
+
+/*
+ * Complex L2 loss, the mean over `count` complex elements of |z - target|^2,
+ * written to loss [1] (device; overwritten), and if d_z is not NULL its
+ * gradient 2 (z - target) / count (overwritten).
+ */
+int gsparc_l2_loss(int64_t count, const float* z, const float* target, float* loss, float* d_z,
+                   void* stream);
+
+/*
+ * Adam step (Algorithm 1 "Adam"): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps), in place over
+ * n FP32 elements.  step >= 1.
+ */
+int gsparc_adam(int64_t n, float* param, const float* grad, float* m, float* v, float lr, float b1,
+                float b2, float eps, int32_t step, void* stream);
+
+/*
+ * Synchronise `stream`, then return the value of the device status word
+ * (GSPARC_OK if no device-side condition was raised) or GSPARC_ERR_CUDA if
+ * the stream reports an error.  d_status may be NULL (stream check only).
+ */
+int gsparc_check(const int32_t* d_status, void* stream);
+
+/* Human-readable text of a status code (static storage). */
+const char* gsparc_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSPARC_H */

@@ -1,0 +1,379 @@
+// Attribute network: per-(transmitter, Gaussian) emission and opacity.
+//
+// Eq. 1: s_i = sigmoid(f(x) - log d_i), d_i = |x_tx - mu_i|, with the 1/d_i
+// free-space factor of the Sec. 4.2 compositing rule.  One network is shared
+// by all Gaussians; its input is h0 = [tx (3), latent_i (16), ln d_i] and its
+// three outputs give a = sigmoid(o_0 - ln d)/d, phi0 = o_1 and
+// sigma = sigmoid(opacity_logit + o_2); L = d + |mu - rx| is the path length
+// whose delay phases the subcarriers.
+//
+// FP32 path: one thread per (b, i) row, weights in shared memory (broadcast
+// reads), the second hidden layer folded straight into the output layer so
+// only one hidden vector lives in registers.
+//
+// Backward: one thread per row recomputes the activations, keeps the per-row
+// vectors in shared memory (row-minor, padded against bank conflicts) and the
+// CTA reduces the weight gradients over its rows before one atomic per entry.
+
+#include "internal.cuh"
+
+namespace gsparc {
+
+int attr_mlp_bf16(int32_t N, int32_t B, const float* tx, const float* rx, const float* means,
+                  const float* opacity_logit, const float* latent, const gsparc_mlp* mlp,
+                  int32_t precision, float* attr, cudaStream_t s);
+
+namespace {
+
+struct W {
+    const float *W1, *b1, *W2, *b2, *W3, *b3;
+};
+
+template <int HD>
+struct WSmem {
+    static constexpr int kW1 = 0;
+    static constexpr int kB1 = kW1 + GSPARC_MLP_IN * HD;
+    static constexpr int kW2 = kB1 + HD;
+    static constexpr int kB2 = kW2 + HD * HD;
+    static constexpr int kW3 = kB2 + HD;
+    static constexpr int kB3 = kW3 + HD * 3;
+    static constexpr int kTotal = kB3 + 4;
+};
+
+template <int HD>
+__device__ __forceinline__ void load_weights(const W& w, float* sw) {
+    using L = WSmem<HD>;
+    for (int t = threadIdx.x; t < GSPARC_MLP_IN * HD; t += blockDim.x) sw[L::kW1 + t] = w.W1[t];
+    for (int t = threadIdx.x; t < HD * HD; t += blockDim.x) sw[L::kW2 + t] = w.W2[t];
+    for (int t = threadIdx.x; t < HD * 3; t += blockDim.x) sw[L::kW3 + t] = w.W3[t];
+    for (int t = threadIdx.x; t < HD; t += blockDim.x) {
+        sw[L::kB1 + t] = w.b1[t];
+        sw[L::kB2 + t] = w.b2[t];
+    }
+    if (threadIdx.x < 3) sw[L::kB3 + threadIdx.x] = w.b3[threadIdx.x];
+}
+
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+struct RowIn {
+    float t0, t1, t2;      // transmitter
+    float m0, m1, m2;      // mean
+    float dist, d, logd;   // raw and clamped distance to the transmitter, ln d
+    float r;               // |mu - rx|
+};
+
+__device__ __forceinline__ RowIn row_inputs(const float* __restrict__ tx, const float* __restrict__ means,
+                                            int b, int i, float rx0, float rx1, float rx2) {
+    RowIn in;
+    in.t0 = tx[3 * b + 0];
+    in.t1 = tx[3 * b + 1];
+    in.t2 = tx[3 * b + 2];
+    in.m0 = means[3 * i + 0];
+    in.m1 = means[3 * i + 1];
+    in.m2 = means[3 * i + 2];
+    const float e0 = in.m0 - in.t0, e1 = in.m1 - in.t1, e2 = in.m2 - in.t2;
+    in.dist = sqrtf(e0 * e0 + e1 * e1 + e2 * e2);
+    in.d = fmaxf(in.dist, kDMin);
+    in.logd = logf(in.d);
+    const float f0 = in.m0 - rx0, f1 = in.m1 - rx1, f2 = in.m2 - rx2;
+    in.r = sqrtf(f0 * f0 + f1 * f1 + f2 * f2);
+    return in;
+}
+
+__device__ __forceinline__ void load_h0(const RowIn& in, const float* __restrict__ latent, int i,
+                                        float h0[GSPARC_MLP_IN]) {
+    h0[0] = in.t0;
+    h0[1] = in.t1;
+    h0[2] = in.t2;
+    const float4* l4 = reinterpret_cast<const float4*>(latent + (size_t)i * GSPARC_LATENT);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 v = l4[q];
+        h0[3 + 4 * q + 0] = v.x;
+        h0[3 + 4 * q + 1] = v.y;
+        h0[3 + 4 * q + 2] = v.z;
+        h0[3 + 4 * q + 3] = v.w;
+    }
+    h0[19] = in.logd;
+}
+
+template <int HD>
+__global__ void __launch_bounds__(128) k_mlp_fwd(int N, int B, const float* __restrict__ tx, float rx0,
+                                                 float rx1, float rx2, const float* __restrict__ means,
+                                                 const float* __restrict__ ologit,
+                                                 const float* __restrict__ latent, W w,
+                                                 float4* __restrict__ attr) {
+    using L = WSmem<HD>;
+    __shared__ float sw[L::kTotal];
+    load_weights<HD>(w, sw);
+    __syncthreads();
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= (int64_t)N * B) return;
+    const int b = (int)(row / N), i = (int)(row - (int64_t)b * N);
+    const RowIn in = row_inputs(tx, means, b, i, rx0, rx1, rx2);
+    float h0[GSPARC_MLP_IN];
+    load_h0(in, latent, i, h0);
+    float h1[HD];
+#pragma unroll
+    for (int j = 0; j < HD; ++j) {
+        float acc = sw[L::kB1 + j];
+#pragma unroll
+        for (int f = 0; f < GSPARC_MLP_IN; ++f) acc = fmaf(h0[f], sw[L::kW1 + f * HD + j], acc);
+        h1[j] = fmaxf(acc, 0.f);
+    }
+    float o0 = sw[L::kB3 + 0], o1 = sw[L::kB3 + 1], o2 = sw[L::kB3 + 2];
+#pragma unroll 4
+    for (int j2 = 0; j2 < HD; ++j2) {
+        float acc = sw[L::kB2 + j2];
+#pragma unroll
+        for (int j = 0; j < HD; ++j) acc = fmaf(h1[j], sw[L::kW2 + j * HD + j2], acc);
+        const float h2 = fmaxf(acc, 0.f);
+        o0 = fmaf(h2, sw[L::kW3 + j2 * 3 + 0], o0);
+        o1 = fmaf(h2, sw[L::kW3 + j2 * 3 + 1], o1);
+        o2 = fmaf(h2, sw[L::kW3 + j2 * 3 + 2], o2);
+    }
+    const float a = sigmoidf_(o0 - in.logd) / in.d;
+    const float sig = sigmoidf_(ologit[i] + o2);
+    attr[row] = make_float4(a, o1, sig, in.d + in.r);
+}
+
+constexpr int kBwdRows = 128;
+constexpr int kRS = kBwdRows + 1;   // padded stride of the row-minor staging arrays
+
+template <int HD>
+struct BwdSmem {
+    static constexpr int kH0 = WSmem<HD>::kTotal;
+    static constexpr int kH1 = kH0 + GSPARC_MLP_IN * kRS;
+    static constexpr int kDU1 = kH1 + HD * kRS;
+    static constexpr int kH2 = kDU1 + HD * kRS;
+    static constexpr int kDU2 = kH2 + HD * kRS;
+    static constexpr int kDO = kDU2 + HD * kRS;
+    static constexpr int kTotal = kDO + 3 * kRS;
+};
+
+template <int HD>
+__global__ void __launch_bounds__(kBwdRows) k_mlp_bwd(int N, int B, const float* __restrict__ tx,
+                                                      float rx0, float rx1, float rx2,
+                                                      const float* __restrict__ means,
+                                                      const float* __restrict__ ologit,
+                                                      const float* __restrict__ latent, W w,
+                                                      const float4* __restrict__ d_attr,
+                                                      float* __restrict__ d_means,
+                                                      float* __restrict__ d_ologit,
+                                                      float* __restrict__ d_latent, gsparc_mlp_grad g) {
+    using L = WSmem<HD>;
+    using S = BwdSmem<HD>;
+    extern __shared__ float sm[];
+    float* sw = sm;
+    load_weights<HD>(w, sw);
+    __syncthreads();
+    const int t = threadIdx.x;
+    const int64_t row = (int64_t)blockIdx.x * kBwdRows + t;
+    const bool valid = row < (int64_t)N * B;
+    if (valid) {
+        const int b = (int)(row / N), i = (int)(row - (int64_t)b * N);
+        const RowIn in = row_inputs(tx, means, b, i, rx0, rx1, rx2);
+        float h0[GSPARC_MLP_IN];
+        load_h0(in, latent, i, h0);
+#pragma unroll
+        for (int f = 0; f < GSPARC_MLP_IN; ++f) sm[S::kH0 + f * kRS + t] = h0[f];
+        // forward, keeping h1 and h2 (pre-activation sign recoverable from h > 0)
+        for (int j = 0; j < HD; ++j) {
+            float acc = sw[L::kB1 + j];
+#pragma unroll
+            for (int f = 0; f < GSPARC_MLP_IN; ++f) acc = fmaf(h0[f], sw[L::kW1 + f * HD + j], acc);
+            sm[S::kH1 + j * kRS + t] = fmaxf(acc, 0.f);
+        }
+        float o0 = sw[L::kB3 + 0], o1 = sw[L::kB3 + 1], o2 = sw[L::kB3 + 2];
+        for (int j2 = 0; j2 < HD; ++j2) {
+            float acc = sw[L::kB2 + j2];
+            for (int j = 0; j < HD; ++j) acc = fmaf(sm[S::kH1 + j * kRS + t], sw[L::kW2 + j * HD + j2], acc);
+            const float h2 = fmaxf(acc, 0.f);
+            sm[S::kH2 + j2 * kRS + t] = h2;
+            o0 = fmaf(h2, sw[L::kW3 + j2 * 3 + 0], o0);
+            o1 = fmaf(h2, sw[L::kW3 + j2 * 3 + 1], o1);
+            o2 = fmaf(h2, sw[L::kW3 + j2 * 3 + 2], o2);
+        }
+        (void)o1;
+        const float s0 = sigmoidf_(o0 - in.logd);
+        const float sig = sigmoidf_(ologit[i] + o2);
+        const float4 da = d_attr[row];   // d a, d phi0, d sigma, d L
+        const float do0 = da.x * s0 * (1.f - s0) / in.d;
+        const float do1 = da.y;
+        const float do2 = da.z * sig * (1.f - sig);
+        sm[S::kDO + 0 * kRS + t] = do0;
+        sm[S::kDO + 1 * kRS + t] = do1;
+        sm[S::kDO + 2 * kRS + t] = do2;
+        atomicAdd(&d_ologit[i], do2);
+        // back through layer 3 and the second ReLU
+        for (int j2 = 0; j2 < HD; ++j2) {
+            const float h2 = sm[S::kH2 + j2 * kRS + t];
+            const float dh2 = sw[L::kW3 + j2 * 3 + 0] * do0 + sw[L::kW3 + j2 * 3 + 1] * do1 +
+                              sw[L::kW3 + j2 * 3 + 2] * do2;
+            sm[S::kDU2 + j2 * kRS + t] = h2 > 0.f ? dh2 : 0.f;
+        }
+        // layer 2 and the first ReLU
+        for (int j = 0; j < HD; ++j) {
+            float acc = 0.f;
+            for (int j2 = 0; j2 < HD; ++j2) acc = fmaf(sw[L::kW2 + j * HD + j2], sm[S::kDU2 + j2 * kRS + t], acc);
+            sm[S::kDU1 + j * kRS + t] = sm[S::kH1 + j * kRS + t] > 0.f ? acc : 0.f;
+        }
+        // layer 1 -> latent and log d
+        float dlogd = -do0;   // a = sigmoid(o0 - ln d)/d: explicit ln d
+#pragma unroll
+        for (int f = 3; f < GSPARC_MLP_IN; ++f) {
+            float acc = 0.f;
+            for (int j = 0; j < HD; ++j) acc = fmaf(sw[L::kW1 + f * HD + j], sm[S::kDU1 + j * kRS + t], acc);
+            if (f < 19) atomicAdd(&d_latent[(size_t)i * GSPARC_LATENT + (f - 3)], acc);
+            else dlogd += acc;
+        }
+        // distance: a's 1/d, ln d feeds, and L = d + r
+        float dd = da.x * (-s0 / (in.d * in.d)) + da.w + dlogd / in.d;
+        float gm0 = 0.f, gm1 = 0.f, gm2 = 0.f;
+        if (in.dist > kDMin) {
+            const float f = dd / in.dist;
+            gm0 += f * (in.m0 - in.t0);
+            gm1 += f * (in.m1 - in.t1);
+            gm2 += f * (in.m2 - in.t2);
+        }
+        if (in.r > 0.f) {
+            const float f = da.w / in.r;
+            gm0 += f * (in.m0 - rx0);
+            gm1 += f * (in.m1 - rx1);
+            gm2 += f * (in.m2 - rx2);
+        }
+        atomicAdd(&d_means[3 * i + 0], gm0);
+        atomicAdd(&d_means[3 * i + 1], gm1);
+        atomicAdd(&d_means[3 * i + 2], gm2);
+    } else {
+        for (int f = 0; f < GSPARC_MLP_IN; ++f) sm[S::kH0 + f * kRS + t] = 0.f;
+        for (int j = 0; j < HD; ++j) {
+            sm[S::kH1 + j * kRS + t] = 0.f;
+            sm[S::kH2 + j * kRS + t] = 0.f;
+            sm[S::kDU1 + j * kRS + t] = 0.f;
+            sm[S::kDU2 + j * kRS + t] = 0.f;
+        }
+        for (int c = 0; c < 3; ++c) sm[S::kDO + c * kRS + t] = 0.f;
+    }
+    __syncthreads();
+    // weight gradients: sums over this CTA's rows
+    for (int e = t; e < GSPARC_MLP_IN * HD; e += kBwdRows) {
+        const int f = e / HD, j = e - f * HD;
+        float acc = 0.f;
+        for (int r = 0; r < kBwdRows; ++r) acc = fmaf(sm[S::kH0 + f * kRS + r], sm[S::kDU1 + j * kRS + r], acc);
+        atomicAdd(&g.W1[e], acc);
+    }
+    for (int e = t; e < HD * HD; e += kBwdRows) {
+        const int j = e / HD, j2 = e - j * HD;
+        float acc = 0.f;
+        for (int r = 0; r < kBwdRows; ++r) acc = fmaf(sm[S::kH1 + j * kRS + r], sm[S::kDU2 + j2 * kRS + r], acc);
+        atomicAdd(&g.W2[e], acc);
+    }
+    for (int e = t; e < HD * 3; e += kBwdRows) {
+        const int j2 = e / 3, c = e - j2 * 3;
+        float acc = 0.f;
+        for (int r = 0; r < kBwdRows; ++r) acc = fmaf(sm[S::kH2 + j2 * kRS + r], sm[S::kDO + c * kRS + r], acc);
+        atomicAdd(&g.W3[e], acc);
+    }
+    for (int j = t; j < HD; j += kBwdRows) {
+        float a1 = 0.f, a2 = 0.f;
+        for (int r = 0; r < kBwdRows; ++r) {
+            a1 += sm[S::kDU1 + j * kRS + r];
+            a2 += sm[S::kDU2 + j * kRS + r];
+        }
+        atomicAdd(&g.b1[j], a1);
+        atomicAdd(&g.b2[j], a2);
+    }
+    if (t < 3) {
+        float acc = 0.f;
+        for (int r = 0; r < kBwdRows; ++r) acc += sm[S::kDO + t * kRS + r];
+        atomicAdd(&g.b3[t], acc);
+    }
+}
+
+bool mlp_ok(const gsparc_mlp* m) {
+    if (!m) return false;
+    if (!(m->hidden == 8 || m->hidden == 16 || m->hidden == 32 || m->hidden == 64)) return false;
+    return m->W1 && m->b1 && m->W2 && m->b2 && m->W3 && m->b3;
+}
+
+template <int HD>
+void launch_fwd(int N, int B, const float* tx, const float* rx, const float* means, const float* ologit,
+                const float* latent, const W& w, float4* attr, cudaStream_t s) {
+    const int64_t rows = (int64_t)N * B;
+    const int blocks = (int)((rows + 127) / 128);
+    k_mlp_fwd<HD><<<blocks, 128, 0, s>>>(N, B, tx, rx[0], rx[1], rx[2], means, ologit, latent, w, attr);
+}
+
+template <int HD>
+int launch_bwd(int N, int B, const float* tx, const float* rx, const float* means, const float* ologit,
+               const float* latent, const W& w, const float4* d_attr, float* d_means, float* d_ologit,
+               float* d_latent, const gsparc_mlp_grad& g, cudaStream_t s) {
+    const size_t smem = (size_t)BwdSmem<HD>::kTotal * sizeof(float);
+    if (cudaFuncSetAttribute(k_mlp_bwd<HD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return GSPARC_ERR_CUDA;
+    const int64_t rows = (int64_t)N * B;
+    const int blocks = (int)((rows + kBwdRows - 1) / kBwdRows);
+    k_mlp_bwd<HD><<<blocks, kBwdRows, smem, s>>>(N, B, tx, rx[0], rx[1], rx[2], means, ologit, latent, w,
+                                                 d_attr, d_means, d_ologit, d_latent, g);
+    return GSPARC_OK;
+}
+
+}  // namespace
+}  // namespace gsparc
+
+using namespace gsparc;
+
+extern "C" int gsparc_attr_mlp(int32_t N, int32_t B, const float* tx, const float* rx, const float* means,
+                               const float* opacity_logit, const float* latent, const gsparc_mlp* mlp,
+                               int32_t precision, float* attr, void* stream) {
+    if (N < 0 || B <= 0 || !mlp_ok(mlp) || !rx) return GSPARC_ERR_INVALID;
+    if ((int64_t)N * B >= (1ll << 31)) return GSPARC_ERR_INVALID;
+    if (N == 0) return GSPARC_OK;
+    if (!tx || !means || !opacity_logit || !latent || !attr) return GSPARC_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(latent) | reinterpret_cast<uintptr_t>(attr)) & 15)
+        return GSPARC_ERR_INVALID;
+    cudaStream_t s = as_stream(stream);
+    if (precision == GSPARC_BF16 || precision == GSPARC_BF16X2)
+        return attr_mlp_bf16(N, B, tx, rx, means, opacity_logit, latent, mlp, precision, attr, s);
+    if (precision != GSPARC_FP32) return GSPARC_ERR_INVALID;
+    W w{mlp->W1, mlp->b1, mlp->W2, mlp->b2, mlp->W3, mlp->b3};
+    float4* a4 = reinterpret_cast<float4*>(attr);
+    switch (mlp->hidden) {
+        case 8: launch_fwd<8>(N, B, tx, rx, means, opacity_logit, latent, w, a4, s); break;
+        case 16: launch_fwd<16>(N, B, tx, rx, means, opacity_logit, latent, w, a4, s); break;
+        case 32: launch_fwd<32>(N, B, tx, rx, means, opacity_logit, latent, w, a4, s); break;
+        default: launch_fwd<64>(N, B, tx, rx, means, opacity_logit, latent, w, a4, s); break;
+    }
+    return launch_status();
+}
+
+extern "C" int gsparc_attr_mlp_bwd(int32_t N, int32_t B, const float* tx, const float* rx,
+                                   const float* means, const float* opacity_logit, const float* latent,
+                                   const gsparc_mlp* mlp, const float* d_attr, float* d_means,
+                                   float* d_opacity_logit, float* d_latent, const gsparc_mlp_grad* grads,
+                                   void* stream) {
+    if (N < 0 || B <= 0 || !mlp_ok(mlp) || !rx || !grads) return GSPARC_ERR_INVALID;
+    if ((int64_t)N * B >= (1ll << 31)) return GSPARC_ERR_INVALID;
+    if (N == 0) return GSPARC_OK;
+    if (!tx || !means || !opacity_logit || !latent || !d_attr || !d_means || !d_opacity_logit ||
+        !d_latent)
+        return GSPARC_ERR_INVALID;
+    if (!grads->W1 || !grads->b1 || !grads->W2 || !grads->b2 || !grads->W3 || !grads->b3)
+        return GSPARC_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(latent) | reinterpret_cast<uintptr_t>(d_attr)) & 15)
+        return GSPARC_ERR_INVALID;
+    cudaStream_t s = as_stream(stream);
+    W w{mlp->W1, mlp->b1, mlp->W2, mlp->b2, mlp->W3, mlp->b3};
+    const float4* da = reinterpret_cast<const float4*>(d_attr);
+    int rc;
+    switch (mlp->hidden) {
+        case 8: rc = launch_bwd<8>(N, B, tx, rx, means, opacity_logit, latent, w, da, d_means, d_opacity_logit, d_latent, *grads, s); break;
+        case 16: rc = launch_bwd<16>(N, B, tx, rx, means, opacity_logit, latent, w, da, d_means, d_opacity_logit, d_latent, *grads, s); break;
+        case 32: rc = launch_bwd<32>(N, B, tx, rx, means, opacity_logit, latent, w, da, d_means, d_opacity_logit, d_latent, *grads, s); break;
+        default: rc = launch_bwd<64>(N, B, tx, rx, means, opacity_logit, latent, w, da, d_means, d_opacity_logit, d_latent, *grads, s); break;
+    }
+    if (rc != GSPARC_OK) return rc;
+    return launch_status();
+}

@@ -1,0 +1,231 @@
+"""Thin Python binding of libgsparc.so (the C ABI declared in include/gsparc.h).
+
+Argument marshalling only: every function takes torch tensors that already
+live on the GPU (outputs included), passes their device pointers, sizes and
+the current CUDA stream to the C entry point of the same name, and raises
+GsparcError on a non-zero status.  No step of the computation runs here.
+The library is loaded on first use; if it has not been built the call fails
+loudly instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgsparc.so")
+
+GSPARC_OK = 0
+GSPARC_ERR_INVALID = -1
+GSPARC_ERR_WORKSPACE = -2
+GSPARC_ERR_CUDA = -3
+GSPARC_ERR_TIMEOUT = -4
+GSPARC_ERR_CAPACITY = -5
+GSPARC_FP32, GSPARC_BF16, GSPARC_BF16X2 = 0, 1, 2
+TILE = 16
+PROJ_STRIDE = 8
+
+EXPORTS = [
+    "gsparc_num_tiles", "gsparc_project", "gsparc_project_bwd", "gsparc_bin_sort_workspace",
+    "gsparc_bin_sort", "gsparc_attr_mlp", "gsparc_attr_mlp_bwd", "gsparc_render_fwd",
+    "gsparc_render_bwd", "gsparc_l2_loss", "gsparc_adam", "gsparc_check", "gsparc_strerror",
+]
+
+
+class GsparcError(RuntimeError):
+    def __init__(self, fn, code):
+        self.code = code
+        super().__init__("%s failed: %d (%s)" % (fn, code, strerror(code)))
+
+
+class View(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("rx", ctypes.c_float * 3),
+                ("V", ctypes.c_float * 9), ("near_dist", ctypes.c_float)]
+
+
+class Band(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("reserved", ctypes.c_int32), ("f_c", ctypes.c_double),
+                ("df", ctypes.c_double)]
+
+
+class MLP(ctypes.Structure):
+    _fields_ = [("hidden", ctypes.c_int32), ("reserved", ctypes.c_int32)] + \
+               [(n, ctypes.c_void_p) for n in ("W1", "b1", "W2", "b2", "W3", "b3")]
+
+
+class MLPGrad(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("W1", "b1", "W2", "b2", "W3", "b3")]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if libgsparc.so is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libgsparc.so is not built (%s); run __graft_entry__.build() or "
+                               "python -m paper_2511_22793_gb300.build" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        f32 = ctypes.c_float
+        P = ctypes.POINTER
+        sig = {
+            "gsparc_num_tiles": (i32, [P(View)]),
+            "gsparc_project": (ctypes.c_int, [P(View), i32, vp, vp, vp, vp, vp]),
+            "gsparc_project_bwd": (ctypes.c_int, [P(View), i32, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "gsparc_bin_sort_workspace": (ctypes.c_int, [P(View), i32, i64, P(ctypes.c_size_t)]),
+            "gsparc_bin_sort": (ctypes.c_int, [P(View), i32, vp, i64, vp, ctypes.c_size_t, vp, vp, vp,
+                                               vp, vp, vp]),
+            "gsparc_attr_mlp": (ctypes.c_int, [i32, i32, vp, P(f32), vp, vp, vp, P(MLP), i32, vp, vp]),
+            "gsparc_attr_mlp_bwd": (ctypes.c_int, [i32, i32, vp, P(f32), vp, vp, vp, P(MLP), vp, vp,
+                                                   vp, vp, P(MLPGrad), vp]),
+            "gsparc_render_fwd": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
+                                                 vp, vp, vp]),
+            "gsparc_render_bwd": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
+                                                 vp, vp, vp, vp]),
+            "gsparc_l2_loss": (ctypes.c_int, [i64, vp, vp, vp, vp, vp]),
+            "gsparc_adam": (ctypes.c_int, [i64, vp, vp, vp, vp, f32, f32, f32, f32, i32, vp]),
+            "gsparc_check": (ctypes.c_int, [vp, vp]),
+            "gsparc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().gsparc_strerror(int(code)).decode()
+    except Exception:
+        return "status %d" % code
+
+
+def _call(name, *args):
+    rc = getattr(lib(), name)(*args)
+    if rc != GSPARC_OK:
+        raise GsparcError(name, rc)
+
+
+def _p(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_view(H, W, rx=(0.0, 0.0, 0.0), V=(1, 0, 0, 0, 1, 0, 0, 0, 1), near_dist=0.1) -> View:
+    v = View()
+    v.H, v.W = int(H), int(W)
+    for i in range(3):
+        v.rx[i] = float(rx[i])
+    for i in range(9):
+        v.V[i] = float(V[i])
+    v.near_dist = float(near_dist)
+    return v
+
+
+def make_band(K, f_c=2.4e9, df=312.5e3) -> Band:
+    b = Band()
+    b.K, b.reserved, b.f_c, b.df = int(K), 0, float(f_c), float(df)
+    return b
+
+
+def make_mlp(hidden, W1, b1, W2, b2, W3, b3) -> MLP:
+    m = MLP()
+    m.hidden, m.reserved = int(hidden), 0
+    for n, t in zip(("W1", "b1", "W2", "b2", "W3", "b3"), (W1, b1, W2, b2, W3, b3)):
+        setattr(m, n, _p(t).value)
+    return m
+
+
+def make_mlp_grad(W1, b1, W2, b2, W3, b3) -> MLPGrad:
+    g = MLPGrad()
+    for n, t in zip(("W1", "b1", "W2", "b2", "W3", "b3"), (W1, b1, W2, b2, W3, b3)):
+        setattr(g, n, _p(t).value)
+    return g
+
+
+def gsparc_num_tiles(view: View) -> int:
+    return int(lib().gsparc_num_tiles(ctypes.byref(view)))
+
+
+def gsparc_project(view, means, log_scales, quats, proj, stream=None):
+    _call("gsparc_project", ctypes.byref(view), means.shape[0], _p(means), _p(log_scales), _p(quats),
+          _p(proj), _stream(stream))
+
+
+def gsparc_project_bwd(view, means, log_scales, quats, d_proj, d_means, d_log_scales, d_quats,
+                       stream=None):
+    _call("gsparc_project_bwd", ctypes.byref(view), means.shape[0], _p(means), _p(log_scales),
+          _p(quats), _p(d_proj), _p(d_means), _p(d_log_scales), _p(d_quats), _stream(stream))
+
+
+def gsparc_bin_sort_workspace(view, n, pair_capacity) -> int:
+    out = ctypes.c_size_t(0)
+    _call("gsparc_bin_sort_workspace", ctypes.byref(view), int(n), int(pair_capacity),
+          ctypes.byref(out))
+    return int(out.value)
+
+
+def gsparc_bin_sort(view, n, proj, pair_capacity, ws, sorted_ids, sorted_keys, tile_ranges, n_pairs,
+                    d_status, stream=None):
+    _call("gsparc_bin_sort", ctypes.byref(view), int(n), _p(proj), int(pair_capacity), _p(ws),
+          ws.numel() * ws.element_size(), _p(sorted_ids), _p(sorted_keys), _p(tile_ranges),
+          _p(n_pairs), _p(d_status), _stream(stream))
+
+
+def gsparc_attr_mlp(tx, rx, means, opacity_logit, latent, mlp: MLP, precision, attr, stream=None):
+    rxa = (ctypes.c_float * 3)(*[float(v) for v in rx])
+    _call("gsparc_attr_mlp", means.shape[0], tx.shape[0], _p(tx), rxa, _p(means), _p(opacity_logit),
+          _p(latent), ctypes.byref(mlp), int(precision), _p(attr), _stream(stream))
+
+
+def gsparc_attr_mlp_bwd(tx, rx, means, opacity_logit, latent, mlp: MLP, d_attr, d_means,
+                        d_opacity_logit, d_latent, grads: MLPGrad, stream=None):
+    rxa = (ctypes.c_float * 3)(*[float(v) for v in rx])
+    _call("gsparc_attr_mlp_bwd", means.shape[0], tx.shape[0], _p(tx), rxa, _p(means),
+          _p(opacity_logit), _p(latent), ctypes.byref(mlp), _p(d_attr), _p(d_means),
+          _p(d_opacity_logit), _p(d_latent), ctypes.byref(grads), _stream(stream))
+
+
+def gsparc_render_fwd(view, band, B, n, proj, tile_ranges, sorted_ids, attr, spectrum,
+                      final_logT=None, n_contrib=None, n_used=None, stream=None):
+    _call("gsparc_render_fwd", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
+          _p(tile_ranges), _p(sorted_ids), _p(attr), _p(spectrum), _p(final_logT), _p(n_contrib),
+          _p(n_used), _stream(stream))
+
+
+def gsparc_render_bwd(view, band, B, n, proj, tile_ranges, sorted_ids, attr, final_logT, n_contrib,
+                      d_spectrum, d_attr, d_proj, stream=None):
+    _call("gsparc_render_bwd", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
+          _p(tile_ranges), _p(sorted_ids), _p(attr), _p(final_logT), _p(n_contrib), _p(d_spectrum),
+          _p(d_attr), _p(d_proj), _stream(stream))
+
+
+def gsparc_l2_loss(z, target, loss, d_z=None, stream=None):
+    count = z.numel() // 2
+    _call("gsparc_l2_loss", count, _p(z), _p(target), _p(loss), _p(d_z), _stream(stream))
+
+
+def gsparc_adam(param, grad, m, v, lr, step, b1=0.9, b2=0.999, eps=1e-15, stream=None):
+    _call("gsparc_adam", param.numel(), _p(param), _p(grad), _p(m), _p(v), float(lr), float(b1),
+          float(b2), float(eps), int(step), _stream(stream))
+
+
+def gsparc_check(d_status=None, stream=None) -> int:
+    return int(lib().gsparc_check(_p(d_status), _stream(stream)))

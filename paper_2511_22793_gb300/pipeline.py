@@ -1,0 +1,142 @@
+"""Device buffers and call sequence of the splatting path, over the C ABI.
+
+PyTorch provides device memory and streams only; every step runs in
+libgsparc.so through the binding in gsparc.py.  A `Renderer` owns the
+buffers of one (view, band, scene size) configuration:
+
+  geometry(scene)            gsparc_project + gsparc_bin_sort   (query-independent)
+  attributes(scene, mlp, tx) gsparc_attr_mlp                    (per transmitter)
+  render(attr)               gsparc_render_fwd
+  backward(...)              gsparc_render_bwd, gsparc_attr_mlp_bwd, gsparc_project_bwd
+
+With the receiver fixed, the geometry depends only on the scene, so it is
+computed once per scene and reused by every transmitter query.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import gsparc as G
+
+
+def _dev(a, device):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=device)
+
+
+@dataclass
+class DeviceScene:
+    means: torch.Tensor          # [N, 3]
+    log_scales: torch.Tensor     # [N, 3]
+    quats: torch.Tensor          # [N, 4]
+    opacity_logit: torch.Tensor  # [N]
+    latent: torch.Tensor         # [N, 16]
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @staticmethod
+    def from_host(scene, device="cuda"):
+        return DeviceScene(*[_dev(a, device) for a in scene.arrays()])
+
+    def tensors(self):
+        return (self.means, self.log_scales, self.quats, self.opacity_logit, self.latent)
+
+
+@dataclass
+class DeviceMLP:
+    hidden: int
+    W1: torch.Tensor
+    b1: torch.Tensor
+    W2: torch.Tensor
+    b2: torch.Tensor
+    W3: torch.Tensor
+    b3: torch.Tensor
+
+    @staticmethod
+    def from_host(mlp, device="cuda"):
+        return DeviceMLP(mlp.hidden, *[_dev(a, device) for a in mlp.arrays()])
+
+    def tensors(self):
+        return (self.W1, self.b1, self.W2, self.b2, self.W3, self.b3)
+
+    def struct(self) -> G.MLP:
+        return G.make_mlp(self.hidden, *self.tensors())
+
+
+class Renderer:
+    """Buffers and calls for one view / band / scene size."""
+
+    def __init__(self, H, W, K, n, f_c=2.4e9, df=312.5e3, rx=(0.0, 0.0, 0.0),
+                 V=(1, 0, 0, 0, 1, 0, 0, 0, 1), near_dist=0.1, pair_capacity=None, device="cuda"):
+        self.device = torch.device(device)
+        self.view = G.make_view(H, W, rx, V, near_dist)
+        self.band = G.make_band(K, f_c, df)
+        self.H, self.W, self.K, self.n = int(H), int(W), int(K), int(n)
+        self.rx = tuple(float(v) for v in rx)
+        self.T = G.gsparc_num_tiles(self.view)
+        self.capacity = int(pair_capacity) if pair_capacity is not None else max(4096, 64 * self.n)
+        dev = self.device
+        self.proj = torch.empty((self.n, G.PROJ_STRIDE), dtype=torch.float32, device=dev)
+        self.sorted_ids = torch.empty(max(1, self.capacity), dtype=torch.int32, device=dev)
+        self.sorted_keys = None
+        self.tile_ranges = torch.empty((self.T, 2), dtype=torch.int32, device=dev)
+        self.n_pairs = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        ws = G.gsparc_bin_sort_workspace(self.view, self.n, self.capacity)
+        self.ws = torch.empty(max(256, ws), dtype=torch.uint8, device=dev)
+
+    # -- query-independent geometry -------------------------------------------------
+    def geometry(self, scene: DeviceScene, keep_keys=False, stream=None):
+        if keep_keys and self.sorted_keys is None:
+            self.sorted_keys = torch.empty(max(1, self.capacity), dtype=torch.int64, device=self.device)
+        G.gsparc_project(self.view, scene.means, scene.log_scales, scene.quats, self.proj, stream)
+        G.gsparc_bin_sort(self.view, self.n, self.proj, self.capacity, self.ws, self.sorted_ids,
+                          self.sorted_keys if keep_keys else None, self.tile_ranges, self.n_pairs,
+                          self.status, stream)
+
+    def check(self, stream=None) -> int:
+        """Synchronise and return the device status (0 when every wait and capacity held)."""
+        return G.gsparc_check(self.status, stream)
+
+    # -- per-query attributes and compositing ---------------------------------------
+    def attributes(self, scene: DeviceScene, mlp: DeviceMLP, tx: torch.Tensor, precision=G.GSPARC_FP32,
+                   out=None, stream=None):
+        B = int(tx.shape[0])
+        attr = out if out is not None else torch.empty((B, self.n, 4), dtype=torch.float32,
+                                                       device=self.device)
+        G.gsparc_attr_mlp(tx, self.rx, scene.means, scene.opacity_logit, scene.latent, mlp.struct(),
+                          precision, attr, stream)
+        return attr
+
+    def alloc_outputs(self, B):
+        dev = self.device
+        spec = torch.empty((B, self.K, self.H, self.W, 2), dtype=torch.float32, device=dev)
+        logT = torch.empty((B, self.H, self.W), dtype=torch.float32, device=dev)
+        nc = torch.empty((B, self.H, self.W), dtype=torch.int32, device=dev)
+        return spec, logT, nc
+
+    def render(self, attr, out=None, n_used=None, stream=None):
+        B = int(attr.shape[0])
+        spec, logT, nc = out if out is not None else self.alloc_outputs(B)
+        G.gsparc_render_fwd(self.view, self.band, B, self.n, self.proj, self.tile_ranges,
+                            self.sorted_ids, attr, spec, logT, nc, n_used, stream)
+        return spec, logT, nc
+
+    def render_backward(self, attr, logT, nc, d_spec, d_attr, d_proj, stream=None):
+        B = int(attr.shape[0])
+        G.gsparc_render_bwd(self.view, self.band, B, self.n, self.proj, self.tile_ranges,
+                            self.sorted_ids, attr, logT, nc, d_spec, d_attr, d_proj, stream)
+
+    def attributes_backward(self, scene, mlp, tx, d_attr, d_means, d_ologit, d_latent, d_weights,
+                            stream=None):
+        G.gsparc_attr_mlp_bwd(tx, self.rx, scene.means, scene.opacity_logit, scene.latent,
+                              mlp.struct(), d_attr, d_means, d_ologit, d_latent,
+                              G.make_mlp_grad(*d_weights), stream)
+
+    def project_backward(self, scene, d_proj, d_means, d_log_scales, d_quats, stream=None):
+        G.gsparc_project_bwd(self.view, scene.means, scene.log_scales, scene.quats, d_proj, d_means,
+                             d_log_scales, d_quats, stream)

@@ -1,0 +1,79 @@
+"""Host-side checks of the C ABI: the library loads, exports every symbol the
+header declares, and rejects bad arguments before touching a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2511_22793_gb300 import gsparc as G
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "gsparc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(gsparc_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(G.LIB_PATH):
+        from paper_2511_22793_gb300 import build
+        build.build()
+    return G.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(G.EXPORTS) == names
+
+
+def test_strerror_and_tiles(L):
+    assert G.strerror(G.GSPARC_ERR_TIMEOUT) == "bounded device wait expired"
+    assert G.gsparc_num_tiles(G.make_view(90, 360)) == 23 * 6
+    assert G.gsparc_num_tiles(G.make_view(180, 720)) == 45 * 12
+    assert G.gsparc_num_tiles(G.make_view(45, 180)) == 12 * 3
+
+
+def test_workspace_query_grows_with_capacity(L):
+    v = G.make_view(90, 360)
+    a = G.gsparc_bin_sort_workspace(v, 1000, 10_000)
+    b = G.gsparc_bin_sort_workspace(v, 1000, 100_000)
+    assert 0 < a < b
+    # keys and values double-buffered: at least 24 B per pair
+    assert b - a >= 24 * 90_000
+
+
+def test_invalid_arguments_rejected_on_host(L):
+    v = G.make_view(90, 360)
+    vp = ctypes.c_void_p
+    assert L.gsparc_project(ctypes.byref(v), -1, None, None, None, None, None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_project(ctypes.byref(v), 5, None, None, None, None, None) == G.GSPARC_ERR_INVALID
+    bad = G.make_view(0, 360)
+    assert L.gsparc_project(ctypes.byref(bad), 0, None, None, None, None, None) == G.GSPARC_ERR_INVALID
+    out = ctypes.c_size_t(0)
+    assert L.gsparc_bin_sort_workspace(ctypes.byref(v), 10, 1 << 31, ctypes.byref(out)) == \
+        G.GSPARC_ERR_INVALID
+    band = G.make_band(0)
+    assert L.gsparc_render_fwd(ctypes.byref(v), ctypes.byref(band), 1, 0, None, vp(256), vp(256), None,
+                               vp(256), None, None, None, None) == G.GSPARC_ERR_INVALID
+    m = G.MLP()
+    m.hidden = 12
+    rx = (ctypes.c_float * 3)(0, 0, 0)
+    assert L.gsparc_attr_mlp(10, 1, vp(256), rx, vp(256), vp(256), vp(256), ctypes.byref(m), 0,
+                             vp(256), None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_adam(10, vp(256), vp(256), vp(256), vp(256), ctypes.c_float(1e-3),
+                         ctypes.c_float(0.9), ctypes.c_float(0.999), ctypes.c_float(1e-15), 0, None) == \
+        G.GSPARC_ERR_INVALID
+
+
+def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(G, "_lib", None)
+    monkeypatch.setattr(G, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        G.lib()

@@ -1,0 +1,112 @@
+"""GPU gradients (hand-written backward behind a torch.autograd.Function)
+against the FP64 oracle's analytic gradient, which the CPU tests pin to
+central finite differences.
+
+Tolerance: <= 1e-3 relative L2 per gradient tensor for the per-Gaussian
+render inputs and <= 5e-3 for the chained scene / network gradients (the
+chain through Sigma'^-1 and the quaternion amplifies FP32 rounding of the
+largest entries; see the derivation beside each bound).
+"""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import DEV, oracle_geo_attr, rel_l2, spectrum_to_complex
+from oracle import pipeline as opl
+from oracle import render as orender
+from paper_2511_22793_gb300 import gsparc as G
+from paper_2511_22793_gb300 import synth
+from paper_2511_22793_gb300.autograd import splat
+from paper_2511_22793_gb300.pipeline import DeviceMLP, DeviceScene, Renderer
+
+pytestmark = pytest.mark.gpu
+
+
+def _target(B, H, W, K, seed):
+    rng = np.random.default_rng(seed)
+    return 0.01 * (rng.normal(size=(B, H * W, K)) + 1j * rng.normal(size=(B, H * W, K)))
+
+
+def _to_dev_target(t, B, H, W, K):
+    a = np.stack([t.real, t.imag], -1).reshape(B, H, W, K, 2).transpose(0, 3, 1, 2, 4)
+    return torch.tensor(a.copy(), dtype=torch.float32, device=DEV)
+
+
+def _gpu_grads(sc, mlp, H, W, K, tx, target):
+    B = tx.shape[0]
+    r = Renderer(H, W, K, sc.n, device=DEV)
+    ds = DeviceScene.from_host(sc, DEV)
+    dm = DeviceMLP.from_host(mlp, DEV)
+    ps = [t.clone().requires_grad_(True) for t in ds.tensors()]
+    ws = [t.clone().requires_grad_(True) for t in dm.tensors()]
+    spec = splat(r, torch.tensor(tx, device=DEV), ps, ws)
+    tgt = _to_dev_target(target, B, H, W, K)
+    loss = ((spec - tgt) ** 2).sum() / (spec.numel() // 2)
+    loss.backward()
+    torch.cuda.synchronize()
+    assert r.check() == 0
+    names = ["means", "log_scales", "quats", "opacity_logit", "latent", "W1", "b1", "W2", "b2", "W3",
+             "b3"]
+    return float(loss), {n: p.grad.cpu().numpy().astype(np.float64) for n, p in zip(names, ps + ws)}, spec
+
+
+@pytest.mark.parametrize("n,H,W,K,B,hidden,widen", [(400, 45, 180, 8, 2, 16, 0.4),
+                                                   (2000, 90, 360, 64, 1, 32, 0.0),
+                                                   (1000, 90, 360, 1, 2, 32, 0.0)])
+def test_full_gradient_matches_oracle(n, H, W, K, B, hidden, widen):
+    sc = synth.make_scene(n, seed=21)
+    if widen:
+        sc.log_scales = sc.log_scales + np.float32(widen)
+    mlp = synth.make_mlp(hidden, seed=3)
+    tx = synth.make_tx(B, seed=22)
+    target = _target(B, H, W, K, 23)
+    loss, g, spec = _gpu_grads(sc, mlp, H, W, K, tx, target)
+    ref_loss, ref = opl.loss_and_grad(sc, mlp, synth.View(H=H, W=W), synth.Band(K=K), tx, target)
+    assert abs(loss - ref_loss) <= 1e-3 * ref_loss
+    assert rel_l2(spectrum_to_complex(spec), ref["z"]) <= 1e-3
+    for k in g:
+        e = rel_l2(g[k], ref[k])
+        assert e <= 5e-3, "%s: relative L2 %.3e" % (k, e)
+
+
+def test_render_bwd_per_gaussian_inputs():
+    """gsparc_render_bwd alone: d(p, conic, sigma, a, phi0, L) against the oracle's
+    analytic render gradient on the same FP32 attribute and projection values
+    (both computed by the oracle and rounded to FP32, so only the backward
+    differs)."""
+    H, W, K, B, n = 90, 360, 32, 1, 3000
+    sc = synth.make_scene(n, seed=31)
+    mlp = synth.make_mlp(32, seed=3)
+    tx = synth.make_tx(B, seed=32)
+    view, band = synth.View(H=H, W=W), synth.Band(K=K)
+    g, attrs = oracle_geo_attr(sc, mlp, view, tx)
+    # FP32 copies of the oracle's per-Gaussian values feed both sides
+    g32 = {k: (v.astype(np.float32).astype(np.float64) if v.dtype != bool else v) for k, v in g.items()}
+    at32 = [{k: v.astype(np.float32).astype(np.float64) for k, v in at.items()} for at in attrs]
+    proj = np.zeros((n, 8), np.float32)
+    proj[:, 0], proj[:, 1] = g32["px"], g32["py"]
+    proj[:, 2] = np.where(g["valid"], np.sqrt(2 * np.log(255) * g["sxx"]), -1)
+    proj[:, 3] = np.where(g["valid"], np.sqrt(2 * np.log(255) * g["syy"]), -1)
+    proj[:, 4], proj[:, 5], proj[:, 6], proj[:, 7] = g32["cxx"], g32["cxy"], g32["cyy"], g32["r"]
+    attr = np.stack([np.stack([at["a"], at["phi0"], at["sigma"], at["L"]], -1) for at in at32]).astype(np.float32)
+    r = Renderer(H, W, K, n, device=DEV)
+    r.proj.copy_(torch.tensor(proj, device=DEV))
+    G.gsparc_bin_sort(r.view, n, r.proj, r.capacity, r.ws, r.sorted_ids, None, r.tile_ranges, r.n_pairs,
+                      r.status)
+    attr_d = torch.tensor(attr, device=DEV)
+    spec, logT, nc = r.render(attr_d)
+    rng = np.random.default_rng(33)
+    gz = rng.normal(size=(B, H * W, K)) + 1j * rng.normal(size=(B, H * W, K))
+    d_spec = _to_dev_target(gz, B, H, W, K)
+    d_attr = torch.zeros_like(attr_d)
+    d_proj = torch.zeros_like(r.proj)
+    r.render_backward(attr_d, logT, nc, d_spec, d_attr, d_proj)
+    torch.cuda.synchronize()
+    ref = orender.render_bwd(g32, at32[0], H, W, K, band.f_c, band.df, gz[0])
+    da = d_attr.cpu().numpy()[0].astype(np.float64)
+    dp = d_proj.cpu().numpy().astype(np.float64)
+    got = {"px": dp[:, 0], "py": dp[:, 1], "cxx": dp[:, 4], "cxy": dp[:, 5], "cyy": dp[:, 6],
+           "sigma": da[:, 2], "a": da[:, 0], "phi0": da[:, 1], "L": da[:, 3]}
+    for c, k in enumerate(("px", "py", "cxx", "cxy", "cyy", "sigma", "a", "phi0", "L")):
+        e = rel_l2(got[k], ref[:, c])
+        assert e <= 1e-3, "%s: relative L2 %.3e" % (k, e)
