@@ -41,6 +41,7 @@ extern "C" {
 #define GSPARC_ERR_CUDA (-3)      /* a CUDA runtime call or launch failed         */
 #define GSPARC_ERR_TIMEOUT (-4)   /* a bounded device-side wait gave up           */
 #define GSPARC_ERR_CAPACITY (-5)  /* more (Gaussian, tile) pairs than capacity    */
+#define GSPARC_ERR_TOO_LARGE (-6) /* sizes above a fixed-scratch entry point's cap */
 
 /* ---- fixed sizes ------------------------------------------------------- */
 #define GSPARC_TILE 16       /* pixels per tile side                              */
@@ -154,6 +155,35 @@ int gsparc_bin_sort_workspace(const gsparc_view* view, int32_t N, int64_t pair_c
 int gsparc_bin_sort(const gsparc_view* view, int32_t N, const float* proj, int64_t pair_capacity,
                     void* ws, size_t ws_bytes, uint32_t* sorted_ids, uint64_t* sorted_keys,
                     uint32_t* tile_ranges, uint32_t* n_pairs, int32_t* d_status, void* stream);
+
+/*
+ * gsparc_bin_sort without a workspace: the same binning and sort, bit for bit,
+ * for callers that cannot allocate device memory.  (The paper has no
+ * counterpart; this is a deployment variant of the call above.)  Some callers
+ * may not call cudaMalloc at all: a real-time loop that must not take the
+ * implicit device-wide synchronisation and unbounded latency of an allocation
+ * after start-up, or a plugin whose host hands it buffers but no allocator.
+ * They still pass every input and output; the scratch space (counts, the
+ * ping-pong key/value buffers, histograms, look-back flags) is a fixed
+ * 14 MiB array in the library's own device memory, which every GPU that
+ * loads the library holds until the process exits.
+ *   Limits: N <= GSPARC_NOALLOC_MAX_N and pair_capacity <=
+ *   GSPARC_NOALLOC_MAX_PAIRS; larger sizes return GSPARC_ERR_TOO_LARGE before
+ *   anything is enqueued.  Other arguments and errors as gsparc_bin_sort.
+ *   The first call on each device looks up that device's address of the
+ *   array (with the device current); make that first call before any stream
+ *   capture.  The call allocates nothing.
+ *   Every call on a device shares the one array and it keeps what the last
+ *   call left there: the call clears what must start at zero itself, but two
+ *   calls whose work overlaps on the GPU (different streams, no ordering
+ *   between them) race on the array and both results are undefined.
+ */
+#define GSPARC_NOALLOC_MAX_N 65536
+#define GSPARC_NOALLOC_MAX_PAIRS 524288
+int gsparc_bin_sort_noalloc(const gsparc_view* view, int32_t N, const float* proj,
+                            int64_t pair_capacity, uint32_t* sorted_ids, uint64_t* sorted_keys,
+                            uint32_t* tile_ranges, uint32_t* n_pairs, int32_t* d_status,
+                            void* stream);
 
 /*
  * Attribute network for B transmitter positions (Eq. 1 with the 1/d of the

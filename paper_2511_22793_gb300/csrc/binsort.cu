@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -460,6 +461,96 @@ extern "C" int gsparc_bin_sort(const gsparc_view* view, int32_t N, const float* 
     const int sms = num_sms();
     const int hist_blocks = sms * 2;
     k_hist<<<hist_blocks, 256, 0, s>>>(kb[0], misc, L.passes, hist, look, L.look_tiles);
+    k_hist_scan<<<1, 256, 0, s>>>(L.passes, hist);
+    const int os_blocks = (int)std::min<int64_t>(L.look_tiles, (int64_t)sms * 2);
+    uint64_t* kfinal = nullptr;
+    for (int p = 0; p < L.passes; ++p) {
+        const int src = p & 1, dst = src ^ 1;
+        const bool last = p == L.passes - 1;
+        uint64_t* kd = last ? (sorted_keys ? sorted_keys : kb[dst]) : kb[dst];
+        uint32_t* vd = last ? sorted_ids : vb[dst];
+        k_onesweep<<<os_blocks, kOsThreads, 0, s>>>(p, kb[src], vb[src], kd, vd, misc, ctr + p,
+                                                    look + (size_t)p * L.look_tiles * 256,
+                                                    hist + p * 256, d_status);
+        if (last) kfinal = kd;
+    }
+    k_ranges<<<sms * 4, 256, 0, s>>>(kfinal, misc, (uint32_t)T, reinterpret_cast<uint2*>(tile_ranges));
+    return launch_status();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Scratch-free variant for callers that cannot allocate device memory (a real-time loop that
+// must not pay cudaMalloc's device-wide synchronisation after start-up, a plugin given buffers
+// but no allocator).  Same kernels and launch sequence as gsparc_bin_sort; the scratch lives in
+// one file-scope device array instead of a caller workspace.
+// ---------------------------------------------------------------------------------------------
+
+namespace gsparc {
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(14) << 20;   // covers layout(65536, 524288, 7 passes)
+constexpr int kMaxDevices = 64;
+
+// Host code must not use this symbol as an address: it only names the array.  The device
+// address comes from cudaGetSymbolAddress, once per device, with that device current.
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::once_flag g_noalloc_once[kMaxDevices];
+void* g_noalloc_ptr[kMaxDevices];
+cudaError_t g_noalloc_err[kMaxDevices];
+
+}  // namespace
+}  // namespace gsparc
+
+extern "C" int gsparc_bin_sort_noalloc(const gsparc_view* view, int32_t N, const float* proj,
+                                       int64_t pair_capacity, uint32_t* sorted_ids,
+                                       uint64_t* sorted_keys, uint32_t* tile_ranges, uint32_t* n_pairs,
+                                       int32_t* d_status, void* stream) {
+    if (!view_ok(view) || N < 0 || pair_capacity < 0) return GSPARC_ERR_INVALID;
+    if (N > GSPARC_NOALLOC_MAX_N || pair_capacity > GSPARC_NOALLOC_MAX_PAIRS) return GSPARC_ERR_TOO_LARGE;
+    if (!tile_ranges || !n_pairs || (N > 0 && !proj) || (pair_capacity > 0 && !sorted_ids))
+        return GSPARC_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(proj) & 15) return GSPARC_ERR_INVALID;
+    const int TW = tiles_x(*view), TH = tiles_y(*view), T = TW * TH;
+    const Layout L = layout(N, pair_capacity, T);
+    if (L.total > kNoAllocBytes) return GSPARC_ERR_TOO_LARGE;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GSPARC_ERR_CUDA;
+    std::call_once(g_noalloc_once[dev], [dev]() {
+        g_noalloc_err[dev] = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_scratch);
+    });
+    if (g_noalloc_err[dev] != cudaSuccess || !g_noalloc_ptr[dev]) return GSPARC_ERR_CUDA;
+
+    cudaStream_t s = as_stream(stream);
+    char* w = static_cast<char*>(g_noalloc_ptr[dev]);
+    uint32_t* local = reinterpret_cast<uint32_t*>(w + L.local);
+    uint32_t* blk = reinterpret_cast<uint32_t*>(w + L.blk);
+    uint64_t* kb[2] = {reinterpret_cast<uint64_t*>(w + L.k0), reinterpret_cast<uint64_t*>(w + L.k1)};
+    uint32_t* vb[2] = {reinterpret_cast<uint32_t*>(w + L.v0), reinterpret_cast<uint32_t*>(w + L.v1)};
+    uint32_t* hist = reinterpret_cast<uint32_t*>(w + L.hist);
+    uint32_t* ctr = reinterpret_cast<uint32_t*>(w + L.ctr);
+    uint32_t* misc = reinterpret_cast<uint32_t*>(w + L.misc);
+    uint32_t* look = reinterpret_cast<uint32_t*>(w + L.look);
+    const uint32_t cap = (uint32_t)pair_capacity;
+
+    // the array keeps the previous call's contents: clear the counters, histograms and
+    // pass counters here (the look-back flags are cleared by k_hist)
+    if (cudaMemsetAsync(tile_ranges, 0, (size_t)T * 2 * sizeof(uint32_t), s) != cudaSuccess)
+        return GSPARC_ERR_CUDA;
+    if (cudaMemsetAsync(w + L.hist, 0, L.look - L.hist, s) != cudaSuccess) return GSPARC_ERR_CUDA;
+    if (N == 0) {
+        if (cudaMemsetAsync(n_pairs, 0, sizeof(uint32_t), s) != cudaSuccess) return GSPARC_ERR_CUDA;
+        return GSPARC_OK;
+    }
+    const float4* p4 = reinterpret_cast<const float4*>(proj);
+    k_count<<<L.nblk, kScanThreads, 0, s>>>(N, view->H, view->W, TW, p4, local, blk);
+    k_scan_blocks<<<1, 1024, 0, s>>>(L.nblk, blk, n_pairs, misc, cap, d_status);
+    k_emit<<<L.nblk, kScanThreads, 0, s>>>(N, view->H, view->W, TW, p4, local, blk, cap, kb[0], vb[0]);
+    if (cudaGetLastError() != cudaSuccess) return GSPARC_ERR_CUDA;
+    if (cap == 0) return GSPARC_OK;
+    const int sms = num_sms();
+    k_hist<<<sms * 2, 256, 0, s>>>(kb[0], misc, L.passes, hist, look, L.look_tiles);
     k_hist_scan<<<1, 256, 0, s>>>(L.passes, hist);
     const int os_blocks = (int)std::min<int64_t>(L.look_tiles, (int64_t)sms * 2);
     uint64_t* kfinal = nullptr;

@@ -23,13 +23,16 @@ GSPARC_ERR_WORKSPACE = -2
 GSPARC_ERR_CUDA = -3
 GSPARC_ERR_TIMEOUT = -4
 GSPARC_ERR_CAPACITY = -5
+GSPARC_ERR_TOO_LARGE = -6
+GSPARC_NOALLOC_MAX_N = 65536
+GSPARC_NOALLOC_MAX_PAIRS = 524288
 GSPARC_FP32, GSPARC_BF16, GSPARC_BF16X2 = 0, 1, 2
 TILE = 16
 PROJ_STRIDE = 8
 
 EXPORTS = [
     "gsparc_num_tiles", "gsparc_project", "gsparc_project_bwd", "gsparc_bin_sort_workspace",
-    "gsparc_bin_sort", "gsparc_attr_mlp", "gsparc_attr_mlp_bwd", "gsparc_render_fwd",
+    "gsparc_bin_sort", "gsparc_bin_sort_noalloc", "gsparc_attr_mlp", "gsparc_attr_mlp_bwd", "gsparc_render_fwd",
     "gsparc_render_bwd", "gsparc_l2_loss", "gsparc_adam", "gsparc_check", "gsparc_strerror",
 ]
 
@@ -80,6 +83,7 @@ def lib():
             "gsparc_bin_sort_workspace": (ctypes.c_int, [P(View), i32, i64, P(ctypes.c_size_t)]),
             "gsparc_bin_sort": (ctypes.c_int, [P(View), i32, vp, i64, vp, ctypes.c_size_t, vp, vp, vp,
                                                vp, vp, vp]),
+            "gsparc_bin_sort_noalloc": (ctypes.c_int, [P(View), i32, vp, i64, vp, vp, vp, vp, vp, vp]),
             "gsparc_attr_mlp": (ctypes.c_int, [i32, i32, vp, P(f32), vp, vp, vp, P(MLP), i32, vp, vp]),
             "gsparc_attr_mlp_bwd": (ctypes.c_int, [i32, i32, vp, P(f32), vp, vp, vp, P(MLP), vp, vp,
                                                    vp, vp, P(MLPGrad), vp]),
@@ -187,6 +191,14 @@ def gsparc_bin_sort(view, n, proj, pair_capacity, ws, sorted_ids, sorted_keys, t
     _call("gsparc_bin_sort", ctypes.byref(view), int(n), _p(proj), int(pair_capacity), _p(ws),
           ws.numel() * ws.element_size(), _p(sorted_ids), _p(sorted_keys), _p(tile_ranges),
           _p(n_pairs), _p(d_status), _stream(stream))
+
+
+def gsparc_bin_sort_noalloc(view, n, proj, pair_capacity, sorted_ids, sorted_keys, tile_ranges,
+                            n_pairs, d_status, stream=None):
+    """gsparc_bin_sort with its scratch in the library's fixed device array (no workspace)."""
+    _call("gsparc_bin_sort_noalloc", ctypes.byref(view), int(n), _p(proj), int(pair_capacity),
+          _p(sorted_ids), _p(sorted_keys), _p(tile_ranges), _p(n_pairs), _p(d_status),
+          _stream(stream))
 
 
 def gsparc_attr_mlp(tx, rx, means, opacity_logit, latent, mlp: MLP, precision, attr, stream=None):
