@@ -160,9 +160,13 @@ def run_ours(args, rank, world, local_rank):
     n_used = torch.zeros((B, H, W), dtype=torch.int32, device=dev)
     loss = torch.zeros(1, device=dev)
     d_spec = torch.empty_like(spec)
-    d_attr = torch.empty_like(attr)
-    d_proj = torch.empty_like(r.proj)
-    grads = [torch.empty_like(t) for t in ds.tensors()] + [torch.empty_like(t) for t in dm.tensors()]
+    # every gradient buffer is a view of one flat allocation, zeroed by one memset per step
+    shapes = [attr.shape, r.proj.shape] + [t.shape for t in ds.tensors()] + [t.shape for t in dm.tensors()]
+    sizes = [int(np.prod(sh)) for sh in shapes]
+    offs = np.cumsum([0] + [(z + 63) // 64 * 64 for z in sizes])
+    gbuf = torch.zeros(int(offs[-1]), device=dev)
+    views = [gbuf[int(o):int(o) + z].view(sh) for o, z, sh in zip(offs[:-1], sizes, shapes)]
+    d_attr, d_proj, grads = views[0], views[1], views[2:]
     mlp_s = dm.struct()
     grad_s = G.make_mlp_grad(*grads[5:])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -176,11 +180,8 @@ def run_ours(args, rank, world, local_rank):
         if name in ev:
             ev[name][1].record(stream)
 
-    def step(scene: DeviceScene, tgt, timed_kernels=False):
-        for t in grads:
-            t.zero_()
-        d_attr.zero_()
-        d_proj.zero_()
+    def step(scene: DeviceScene, tgt):
+        gbuf.zero_()
         stage("project", lambda: G.gsparc_project(r.view, scene.means, scene.log_scales, scene.quats,
                                                   r.proj))
         stage("bin_sort", lambda: G.gsparc_bin_sort(r.view, n, r.proj, r.capacity, r.ws, r.sorted_ids,
@@ -394,7 +395,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=90 * 360,

@@ -165,7 +165,7 @@ int gsparc_bin_sort(const gsparc_view* view, int32_t N, const float* proj, int64
  * after start-up, or a plugin whose host hands it buffers but no allocator.
  * They still pass every input and output; the scratch space (counts, the
  * ping-pong key/value buffers, histograms, look-back flags) is a fixed
- * 14 MiB array in the library's own device memory, which every GPU that
+ * 15 MiB array in the library's own device memory, which every GPU that
  * loads the library holds until the process exits.
  *   Limits: N <= GSPARC_NOALLOC_MAX_N and pair_capacity <=
  *   GSPARC_NOALLOC_MAX_PAIRS; larger sizes return GSPARC_ERR_TOO_LARGE before

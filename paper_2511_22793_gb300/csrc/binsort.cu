@@ -31,8 +31,8 @@ namespace {
 constexpr int kScanThreads = 256;
 constexpr int kOsThreads = 256;
 constexpr int kOsWarps = kOsThreads / 32;
-constexpr int kOsKpt = 16;                          // keys per thread
-constexpr int kOsTile = kOsThreads * kOsKpt;        // 4096 keys per sort tile
+constexpr int kOsKpt = 8;                           // keys per thread
+constexpr int kOsTile = kOsThreads * kOsKpt;        // 2048 keys per sort tile
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
@@ -488,7 +488,8 @@ extern "C" int gsparc_bin_sort(const gsparc_view* view, int32_t N, const float* 
 namespace gsparc {
 namespace {
 
-constexpr size_t kNoAllocBytes = size_t(14) << 20;   // covers layout(65536, 524288, 7 passes)
+constexpr size_t kNoAllocBytes = size_t(15) << 20;   // covers layout(65536, 524288, 7 passes)
+static_assert(kOsTile == 2048, "the no-alloc budget assumes 2048-key sort tiles");
 constexpr int kMaxDevices = 64;
 
 // Host code must not use this symbol as an address: it only names the array.  The device

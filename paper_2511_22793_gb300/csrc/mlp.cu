@@ -11,9 +11,13 @@
 // reads), the second hidden layer folded straight into the output layer so
 // only one hidden vector lives in registers.
 //
-// Backward: one thread per row recomputes the activations, keeps the per-row
-// vectors in shared memory (row-minor, padded against bank conflicts) and the
-// CTA reduces the weight gradients over its rows before one atomic per entry.
+// Backward: persistent CTAs; one thread per row recomputes the activations in
+// registers, the per-row vectors the weight gradients need are staged in
+// shared memory (row-minor, padded against bank conflicts), and every CTA keeps
+// its weight-gradient partials in registers until one atomic per entry at the
+// end.
+
+#include <algorithm>
 
 #include "internal.cuh"
 
@@ -151,6 +155,17 @@ struct BwdSmem {
     static constexpr int kTotal = kDO + 3 * kRS;
 };
 
+// Weight-gradient entries owned by one thread: entry e = t + kBwdRows * m.
+template <int COUNT>
+struct Owned {
+    static constexpr int kPer = (COUNT + kBwdRows - 1) / kBwdRows;
+};
+
+// Persistent CTAs of 128 threads; each pass takes 128 rows (one per thread).  A thread
+// recomputes its row's activations in registers (independent accumulators, fully
+// unrolled), stages the per-row vectors needed by the weight gradients in shared memory,
+// and after a barrier adds the CTA's 128 rows into weight-gradient partials it keeps in
+// registers across passes.  One atomic per weight entry per CTA at the end.
 template <int HD>
 __global__ void __launch_bounds__(kBwdRows) k_mlp_bwd(int N, int B, const float* __restrict__ tx,
                                                       float rx0, float rx1, float rx2,
@@ -163,132 +178,193 @@ __global__ void __launch_bounds__(kBwdRows) k_mlp_bwd(int N, int B, const float*
                                                       float* __restrict__ d_latent, gsparc_mlp_grad g) {
     using L = WSmem<HD>;
     using S = BwdSmem<HD>;
+    constexpr int kP1 = Owned<GSPARC_MLP_IN * HD>::kPer;
+    constexpr int kP2 = Owned<HD * HD>::kPer;
+    constexpr int kP3 = Owned<HD * 3>::kPer;
     extern __shared__ float sm[];
     float* sw = sm;
     load_weights<HD>(w, sw);
-    __syncthreads();
     const int t = threadIdx.x;
-    const int64_t row = (int64_t)blockIdx.x * kBwdRows + t;
-    const bool valid = row < (int64_t)N * B;
-    if (valid) {
-        const int b = (int)(row / N), i = (int)(row - (int64_t)b * N);
-        const RowIn in = row_inputs(tx, means, b, i, rx0, rx1, rx2);
-        float h0[GSPARC_MLP_IN];
-        load_h0(in, latent, i, h0);
+    float aW1[kP1], aW2[kP2], aW3[kP3], ab1 = 0.f, ab2 = 0.f, ab3 = 0.f;
 #pragma unroll
-        for (int f = 0; f < GSPARC_MLP_IN; ++f) sm[S::kH0 + f * kRS + t] = h0[f];
-        // forward, keeping h1 and h2 (pre-activation sign recoverable from h > 0)
-        for (int j = 0; j < HD; ++j) {
-            float acc = sw[L::kB1 + j];
+    for (int m = 0; m < kP1; ++m) aW1[m] = 0.f;
 #pragma unroll
-            for (int f = 0; f < GSPARC_MLP_IN; ++f) acc = fmaf(h0[f], sw[L::kW1 + f * HD + j], acc);
-            sm[S::kH1 + j * kRS + t] = fmaxf(acc, 0.f);
-        }
-        float o0 = sw[L::kB3 + 0], o1 = sw[L::kB3 + 1], o2 = sw[L::kB3 + 2];
-        for (int j2 = 0; j2 < HD; ++j2) {
-            float acc = sw[L::kB2 + j2];
-            for (int j = 0; j < HD; ++j) acc = fmaf(sm[S::kH1 + j * kRS + t], sw[L::kW2 + j * HD + j2], acc);
-            const float h2 = fmaxf(acc, 0.f);
-            sm[S::kH2 + j2 * kRS + t] = h2;
-            o0 = fmaf(h2, sw[L::kW3 + j2 * 3 + 0], o0);
-            o1 = fmaf(h2, sw[L::kW3 + j2 * 3 + 1], o1);
-            o2 = fmaf(h2, sw[L::kW3 + j2 * 3 + 2], o2);
-        }
-        (void)o1;
-        const float s0 = sigmoidf_(o0 - in.logd);
-        const float sig = sigmoidf_(ologit[i] + o2);
-        const float4 da = d_attr[row];   // d a, d phi0, d sigma, d L
-        const float do0 = da.x * s0 * (1.f - s0) / in.d;
-        const float do1 = da.y;
-        const float do2 = da.z * sig * (1.f - sig);
-        sm[S::kDO + 0 * kRS + t] = do0;
-        sm[S::kDO + 1 * kRS + t] = do1;
-        sm[S::kDO + 2 * kRS + t] = do2;
-        atomicAdd(&d_ologit[i], do2);
-        // back through layer 3 and the second ReLU
-        for (int j2 = 0; j2 < HD; ++j2) {
-            const float h2 = sm[S::kH2 + j2 * kRS + t];
-            const float dh2 = sw[L::kW3 + j2 * 3 + 0] * do0 + sw[L::kW3 + j2 * 3 + 1] * do1 +
-                              sw[L::kW3 + j2 * 3 + 2] * do2;
-            sm[S::kDU2 + j2 * kRS + t] = h2 > 0.f ? dh2 : 0.f;
-        }
-        // layer 2 and the first ReLU
-        for (int j = 0; j < HD; ++j) {
-            float acc = 0.f;
-            for (int j2 = 0; j2 < HD; ++j2) acc = fmaf(sw[L::kW2 + j * HD + j2], sm[S::kDU2 + j2 * kRS + t], acc);
-            sm[S::kDU1 + j * kRS + t] = sm[S::kH1 + j * kRS + t] > 0.f ? acc : 0.f;
-        }
-        // layer 1 -> latent and log d
-        float dlogd = -do0;   // a = sigmoid(o0 - ln d)/d: explicit ln d
+    for (int m = 0; m < kP2; ++m) aW2[m] = 0.f;
 #pragma unroll
-        for (int f = 3; f < GSPARC_MLP_IN; ++f) {
-            float acc = 0.f;
-            for (int j = 0; j < HD; ++j) acc = fmaf(sw[L::kW1 + f * HD + j], sm[S::kDU1 + j * kRS + t], acc);
-            if (f < 19) atomicAdd(&d_latent[(size_t)i * GSPARC_LATENT + (f - 3)], acc);
-            else dlogd += acc;
-        }
-        // distance: a's 1/d, ln d feeds, and L = d + r
-        float dd = da.x * (-s0 / (in.d * in.d)) + da.w + dlogd / in.d;
-        float gm0 = 0.f, gm1 = 0.f, gm2 = 0.f;
-        if (in.dist > kDMin) {
-            const float f = dd / in.dist;
-            gm0 += f * (in.m0 - in.t0);
-            gm1 += f * (in.m1 - in.t1);
-            gm2 += f * (in.m2 - in.t2);
-        }
-        if (in.r > 0.f) {
-            const float f = da.w / in.r;
-            gm0 += f * (in.m0 - rx0);
-            gm1 += f * (in.m1 - rx1);
-            gm2 += f * (in.m2 - rx2);
-        }
-        atomicAdd(&d_means[3 * i + 0], gm0);
-        atomicAdd(&d_means[3 * i + 1], gm1);
-        atomicAdd(&d_means[3 * i + 2], gm2);
-    } else {
-        for (int f = 0; f < GSPARC_MLP_IN; ++f) sm[S::kH0 + f * kRS + t] = 0.f;
-        for (int j = 0; j < HD; ++j) {
-            sm[S::kH1 + j * kRS + t] = 0.f;
-            sm[S::kH2 + j * kRS + t] = 0.f;
-            sm[S::kDU1 + j * kRS + t] = 0.f;
-            sm[S::kDU2 + j * kRS + t] = 0.f;
-        }
-        for (int c = 0; c < 3; ++c) sm[S::kDO + c * kRS + t] = 0.f;
-    }
+    for (int m = 0; m < kP3; ++m) aW3[m] = 0.f;
+    const int64_t rows = (int64_t)N * B;
+    const int64_t tiles = (rows + kBwdRows - 1) / kBwdRows;
     __syncthreads();
-    // weight gradients: sums over this CTA's rows
-    for (int e = t; e < GSPARC_MLP_IN * HD; e += kBwdRows) {
-        const int f = e / HD, j = e - f * HD;
-        float acc = 0.f;
-        for (int r = 0; r < kBwdRows; ++r) acc = fmaf(sm[S::kH0 + f * kRS + r], sm[S::kDU1 + j * kRS + r], acc);
-        atomicAdd(&g.W1[e], acc);
-    }
-    for (int e = t; e < HD * HD; e += kBwdRows) {
-        const int j = e / HD, j2 = e - j * HD;
-        float acc = 0.f;
-        for (int r = 0; r < kBwdRows; ++r) acc = fmaf(sm[S::kH1 + j * kRS + r], sm[S::kDU2 + j2 * kRS + r], acc);
-        atomicAdd(&g.W2[e], acc);
-    }
-    for (int e = t; e < HD * 3; e += kBwdRows) {
-        const int j2 = e / 3, c = e - j2 * 3;
-        float acc = 0.f;
-        for (int r = 0; r < kBwdRows; ++r) acc = fmaf(sm[S::kH2 + j2 * kRS + r], sm[S::kDO + c * kRS + r], acc);
-        atomicAdd(&g.W3[e], acc);
-    }
-    for (int j = t; j < HD; j += kBwdRows) {
-        float a1 = 0.f, a2 = 0.f;
-        for (int r = 0; r < kBwdRows; ++r) {
-            a1 += sm[S::kDU1 + j * kRS + r];
-            a2 += sm[S::kDU2 + j * kRS + r];
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t row = tile * kBwdRows + t;
+        if (row < rows) {
+            const int b = (int)(row / N), i = (int)(row - (int64_t)b * N);
+            const RowIn in = row_inputs(tx, means, b, i, rx0, rx1, rx2);
+            float h0[GSPARC_MLP_IN];
+            load_h0(in, latent, i, h0);
+#pragma unroll
+            for (int f = 0; f < GSPARC_MLP_IN; ++f) sm[S::kH0 + f * kRS + t] = h0[f];
+            float h1[HD];
+#pragma unroll
+            for (int j = 0; j < HD; ++j) {
+                float acc = sw[L::kB1 + j];
+#pragma unroll
+                for (int f = 0; f < GSPARC_MLP_IN; ++f) acc = fmaf(h0[f], sw[L::kW1 + f * HD + j], acc);
+                h1[j] = fmaxf(acc, 0.f);
+                sm[S::kH1 + j * kRS + t] = h1[j];
+            }
+            float v[HD];   // h2, then du2
+#pragma unroll
+            for (int j2 = 0; j2 < HD; ++j2) v[j2] = sw[L::kB2 + j2];
+#pragma unroll
+            for (int j = 0; j < HD; ++j) {
+#pragma unroll
+                for (int j2 = 0; j2 < HD; ++j2) v[j2] = fmaf(h1[j], sw[L::kW2 + j * HD + j2], v[j2]);
+            }
+            float o0 = sw[L::kB3 + 0], o2 = sw[L::kB3 + 2];
+#pragma unroll
+            for (int j2 = 0; j2 < HD; ++j2) {
+                v[j2] = fmaxf(v[j2], 0.f);
+                sm[S::kH2 + j2 * kRS + t] = v[j2];
+                o0 = fmaf(v[j2], sw[L::kW3 + j2 * 3 + 0], o0);
+                o2 = fmaf(v[j2], sw[L::kW3 + j2 * 3 + 2], o2);
+            }
+            const float s0 = sigmoidf_(o0 - in.logd);
+            const float sig = sigmoidf_(ologit[i] + o2);
+            const float4 da = d_attr[row];   // d a, d phi0, d sigma, d L
+            const float do0 = da.x * s0 * (1.f - s0) / in.d;
+            const float do1 = da.y;
+            const float do2 = da.z * sig * (1.f - sig);
+            sm[S::kDO + 0 * kRS + t] = do0;
+            sm[S::kDO + 1 * kRS + t] = do1;
+            sm[S::kDO + 2 * kRS + t] = do2;
+            atomicAdd(&d_ologit[i], do2);
+#pragma unroll
+            for (int j2 = 0; j2 < HD; ++j2) {
+                const float dh2 = sw[L::kW3 + j2 * 3 + 0] * do0 + sw[L::kW3 + j2 * 3 + 1] * do1 +
+                                  sw[L::kW3 + j2 * 3 + 2] * do2;
+                v[j2] = v[j2] > 0.f ? dh2 : 0.f;
+                sm[S::kDU2 + j2 * kRS + t] = v[j2];
+            }
+            float dh1[HD];
+#pragma unroll
+            for (int j = 0; j < HD; ++j) dh1[j] = 0.f;
+#pragma unroll
+            for (int j2 = 0; j2 < HD; ++j2) {
+#pragma unroll
+                for (int j = 0; j < HD; ++j) dh1[j] = fmaf(sw[L::kW2 + j * HD + j2], v[j2], dh1[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < HD; ++j) {
+                dh1[j] = h1[j] > 0.f ? dh1[j] : 0.f;
+                sm[S::kDU1 + j * kRS + t] = dh1[j];
+            }
+            float dh0[GSPARC_MLP_IN - 3];
+#pragma unroll
+            for (int f = 0; f < GSPARC_MLP_IN - 3; ++f) dh0[f] = 0.f;
+#pragma unroll
+            for (int j = 0; j < HD; ++j) {
+#pragma unroll
+                for (int f = 0; f < GSPARC_MLP_IN - 3; ++f)
+                    dh0[f] = fmaf(sw[L::kW1 + (f + 3) * HD + j], dh1[j], dh0[f]);
+            }
+#pragma unroll
+            for (int f = 0; f < GSPARC_LATENT; ++f) atomicAdd(&d_latent[(size_t)i * GSPARC_LATENT + f], dh0[f]);
+            // a = sigmoid(o0 - ln d)/d: explicit ln d (-do0), network input ln d, L = d + r
+            const float dlogd = -do0 + dh0[GSPARC_MLP_IN - 4];
+            const float dd = da.x * (-s0 / (in.d * in.d)) + da.w + dlogd / in.d;
+            float gm0 = 0.f, gm1 = 0.f, gm2 = 0.f;
+            if (in.dist > kDMin) {
+                const float f = dd / in.dist;
+                gm0 += f * (in.m0 - in.t0);
+                gm1 += f * (in.m1 - in.t1);
+                gm2 += f * (in.m2 - in.t2);
+            }
+            if (in.r > 0.f) {
+                const float f = da.w / in.r;
+                gm0 += f * (in.m0 - rx0);
+                gm1 += f * (in.m1 - rx1);
+                gm2 += f * (in.m2 - rx2);
+            }
+            atomicAdd(&d_means[3 * i + 0], gm0);
+            atomicAdd(&d_means[3 * i + 1], gm1);
+            atomicAdd(&d_means[3 * i + 2], gm2);
+        } else {
+#pragma unroll
+            for (int f = 0; f < GSPARC_MLP_IN; ++f) sm[S::kH0 + f * kRS + t] = 0.f;
+#pragma unroll
+            for (int j = 0; j < HD; ++j) {
+                sm[S::kH1 + j * kRS + t] = 0.f;
+                sm[S::kH2 + j * kRS + t] = 0.f;
+                sm[S::kDU1 + j * kRS + t] = 0.f;
+                sm[S::kDU2 + j * kRS + t] = 0.f;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sm[S::kDO + c * kRS + t] = 0.f;
         }
-        atomicAdd(&g.b1[j], a1);
-        atomicAdd(&g.b2[j], a2);
+        __syncthreads();
+        // this pass's 128 rows into the register partials
+#pragma unroll
+        for (int m = 0; m < kP1; ++m) {
+            const int e = t + kBwdRows * m;
+            if (e < GSPARC_MLP_IN * HD) {
+                const int f = e / HD, j = e - f * HD;
+                float acc = aW1[m];
+                for (int r = 0; r < kBwdRows; ++r) acc = fmaf(sm[S::kH0 + f * kRS + r], sm[S::kDU1 + j * kRS + r], acc);
+                aW1[m] = acc;
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < kP2; ++m) {
+            const int e = t + kBwdRows * m;
+            if (e < HD * HD) {
+                const int j = e / HD, j2 = e - j * HD;
+                float acc = aW2[m];
+                for (int r = 0; r < kBwdRows; ++r) acc = fmaf(sm[S::kH1 + j * kRS + r], sm[S::kDU2 + j2 * kRS + r], acc);
+                aW2[m] = acc;
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < kP3; ++m) {
+            const int e = t + kBwdRows * m;
+            if (e < HD * 3) {
+                const int j2 = e / 3, c = e - j2 * 3;
+                float acc = aW3[m];
+                for (int r = 0; r < kBwdRows; ++r) acc = fmaf(sm[S::kH2 + j2 * kRS + r], sm[S::kDO + c * kRS + r], acc);
+                aW3[m] = acc;
+            }
+        }
+        if (t < HD) {
+            for (int r = 0; r < kBwdRows; ++r) {
+                ab1 += sm[S::kDU1 + t * kRS + r];
+                ab2 += sm[S::kDU2 + t * kRS + r];
+            }
+        }
+        if (t < 3) {
+            for (int r = 0; r < kBwdRows; ++r) ab3 += sm[S::kDO + t * kRS + r];
+        }
+        __syncthreads();
     }
-    if (t < 3) {
-        float acc = 0.f;
-        for (int r = 0; r < kBwdRows; ++r) acc += sm[S::kDO + t * kRS + r];
-        atomicAdd(&g.b3[t], acc);
+#pragma unroll
+    for (int m = 0; m < kP1; ++m) {
+        const int e = t + kBwdRows * m;
+        if (e < GSPARC_MLP_IN * HD) atomicAdd(&g.W1[e], aW1[m]);
     }
+#pragma unroll
+    for (int m = 0; m < kP2; ++m) {
+        const int e = t + kBwdRows * m;
+        if (e < HD * HD) atomicAdd(&g.W2[e], aW2[m]);
+    }
+#pragma unroll
+    for (int m = 0; m < kP3; ++m) {
+        const int e = t + kBwdRows * m;
+        if (e < HD * 3) atomicAdd(&g.W3[e], aW3[m]);
+    }
+    if (t < HD) {
+        atomicAdd(&g.b1[t], ab1);
+        atomicAdd(&g.b2[t], ab2);
+    }
+    if (t < 3) atomicAdd(&g.b3[t], ab3);
 }
 
 bool mlp_ok(const gsparc_mlp* m) {
@@ -314,7 +390,8 @@ int launch_bwd(int N, int B, const float* tx, const float* rx, const float* mean
         cudaSuccess)
         return GSPARC_ERR_CUDA;
     const int64_t rows = (int64_t)N * B;
-    const int blocks = (int)((rows + kBwdRows - 1) / kBwdRows);
+    const int64_t tiles = (rows + kBwdRows - 1) / kBwdRows;
+    const int blocks = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * 2);
     k_mlp_bwd<HD><<<blocks, kBwdRows, smem, s>>>(N, B, tx, rx[0], rx[1], rx[2], means, ologit, latent, w,
                                                  d_attr, d_means, d_ologit, d_latent, g);
     return GSPARC_OK;

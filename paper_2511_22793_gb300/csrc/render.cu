@@ -85,8 +85,8 @@ __device__ __forceinline__ bool eval_alpha(float ux, float uy, int W, const floa
 // unit phasors of the strip's subcarriers.
 template <int S>
 __device__ __forceinline__ void stage_batch(const RenderArgs& a, int b, uint32_t list_pos, int nb,
-                                            int k0, float4* s_geo, float2* s_geo2, float* s_amp,
-                                            float2 (*s_tab)[S], uint32_t* s_gid) {
+                                            int k0, float4* s_geo, float2* s_geo2, float2* s_ext,
+                                            float* s_amp, float2 (*s_tab)[S], uint32_t* s_gid) {
     const int tid = threadIdx.x;
     __shared__ float s_L[kBatch], s_phi[kBatch];
     if (tid < nb) {
@@ -97,6 +97,7 @@ __device__ __forceinline__ void stage_batch(const RenderArgs& a, int b, uint32_t
             const float4 at = a.attr[(size_t)b * a.N + gid];
             s_geo[tid] = make_float4(p0.x, p0.y, p1.x, p1.y);
             s_geo2[tid] = make_float2(p1.z, at.z);
+            s_ext[tid] = make_float2(p0.z, p0.w);
             s_amp[tid] = at.x;
             s_phi[tid] = at.y;
             s_L[tid] = at.w;
@@ -105,6 +106,7 @@ __device__ __forceinline__ void stage_batch(const RenderArgs& a, int b, uint32_t
             // every pixel skip it, and it receives no gradient
             s_geo[tid] = make_float4(0.f, 0.f, __int_as_float(0x7fc00000), 0.f);
             s_geo2[tid] = make_float2(0.f, 0.f);
+            s_ext[tid] = make_float2(-1.f, -1.f);
             s_amp[tid] = 0.f;
             s_phi[tid] = 0.f;
             s_L[tid] = 0.f;
@@ -135,10 +137,40 @@ __device__ __forceinline__ void stage_batch(const RenderArgs& a, int b, uint32_t
     __syncthreads();
 }
 
+// Bit j set when staged entry j's footprint box reaches the warp's 16x2 block of
+// pixel centres (centre (wcx, wcy), half sizes 7.5 x 0.5).  The box is the
+// bounding box of q <= q_max, so a cleared bit means q > q_max at every pixel
+// of the warp; the 0.01 px margin covers rounding at the box edge.
+__device__ __forceinline__ uint64_t warp_entry_mask(const float4* s_geo, const float2* s_ext, int nb,
+                                                    float wcx, float wcy, int W) {
+    const int lane = threadIdx.x & 31;
+    const float hw = 0.5f * (float)W;
+    bool h0 = false, h1 = false;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int j = lane + 32 * half;
+        bool hit = false;
+        if (j < nb) {
+            const float2 e = s_ext[j];
+            float dx = wcx - s_geo[j].x;
+            if (dx >= hw) dx -= (float)W;
+            else if (dx < -hw) dx += (float)W;
+            const float dy = wcy - s_geo[j].y;
+            hit = e.x >= 0.f && fabsf(dx) <= e.x + 7.51f && fabsf(dy) <= e.y + 0.51f;
+        }
+        if (half == 0) h0 = hit;
+        else h1 = hit;
+    }
+    const uint32_t lo = __ballot_sync(0xffffffffu, h0);
+    const uint32_t hi = __ballot_sync(0xffffffffu, h1);
+    return ((uint64_t)hi << 32) | lo;
+}
+
 template <int S>
 __global__ void __launch_bounds__(kThreads, 2) k_render_fwd(RenderArgs a) {
     __shared__ float4 s_geo[kBatch];
     __shared__ float2 s_geo2[kBatch];
+    __shared__ float2 s_ext[kBatch];
     __shared__ float s_amp[kBatch];
     __shared__ uint32_t s_gid[kBatch];
     __shared__ __align__(16) float2 s_tab[kBatch][S];
@@ -146,10 +178,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_fwd(RenderArgs a) {
     const int strip = blockIdx.x, tile = blockIdx.y, b = blockIdx.z;
     const int k0 = strip * S;
     const int tid = threadIdx.x;
-    const int x = (tile % a.TW) * kTile + (tid & 15);
-    const int y = (tile / a.TW) * kTile + (tid >> 4);
+    const int tx0 = (tile % a.TW) * kTile, ty0 = (tile / a.TW) * kTile;
+    const int x = tx0 + (tid & 15);
+    const int y = ty0 + (tid >> 4);
     const bool inside = x < a.W && y < a.H;
     const float ux = (float)x + 0.5f, uy = (float)y + 0.5f;
+    const float wcx = (float)tx0 + 8.0f, wcy = (float)(ty0 + 2 * (tid >> 5)) + 1.0f;
     const uint2 range = a.ranges[tile];
 
     float2 acc[S];
@@ -162,9 +196,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_fwd(RenderArgs a) {
     for (uint32_t bs = range.x; bs < range.y; bs += kBatch) {
         if (__syncthreads_or(!done) == 0) break;
         const int nb = (int)min((uint32_t)kBatch, range.y - bs);
-        stage_batch<S>(a, b, bs, nb, k0, s_geo, s_geo2, s_amp, s_tab, s_gid);
+        stage_batch<S>(a, b, bs, nb, k0, s_geo, s_geo2, s_ext, s_amp, s_tab, s_gid);
+        uint64_t mask = warp_entry_mask(s_geo, s_ext, nb, wcx, wcy, a.W);
         if (!done) {
-            for (int j = 0; j < nb; ++j) {
+            while (mask) {
+                const int j = __ffsll((long long)mask) - 1;
+                mask &= mask - 1;
                 float dx, dy, G, alpha;
                 bool clamped;
                 if (!eval_alpha(ux, uy, a.W, s_geo[j], s_geo2[j], dx, dy, G, alpha, clamped)) continue;
@@ -205,19 +242,23 @@ template <int S>
 __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
     __shared__ float4 s_geo[kBatch];
     __shared__ float2 s_geo2[kBatch];
+    __shared__ float2 s_ext[kBatch];
     __shared__ float s_amp[kBatch];
     __shared__ uint32_t s_gid[kBatch];
     __shared__ __align__(16) float2 s_tab[kBatch][S];
     __shared__ float s_red[kThreads / 32][kBatch][9];
+    __shared__ uint64_t s_wmask[kThreads / 32];
     __shared__ uint32_t s_maxlast;
 
     const int strip = blockIdx.x, tile = blockIdx.y, b = blockIdx.z;
     const int k0 = strip * S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int x = (tile % a.TW) * kTile + (tid & 15);
-    const int y = (tile / a.TW) * kTile + (tid >> 4);
+    const int tx0 = (tile % a.TW) * kTile, ty0 = (tile / a.TW) * kTile;
+    const int x = tx0 + (tid & 15);
+    const int y = ty0 + (tid >> 4);
     const bool inside = x < a.W && y < a.H;
     const float ux = (float)x + 0.5f, uy = (float)y + 0.5f;
+    const float wcx = (float)tx0 + 8.0f, wcy = (float)(ty0 + 2 * warp) + 1.0f;
     const uint2 range = a.ranges[tile];
     const size_t plane = (size_t)a.H * a.W;
     const size_t pix = (size_t)y * a.W + x;
@@ -245,8 +286,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
         const uint32_t bstart = bend > (uint32_t)kBatch ? bend - kBatch : 0u;
         const int nb = (int)(bend - bstart);
         __syncthreads();
-        stage_batch<S>(a, b, range.x + bstart, nb, k0, s_geo, s_geo2, s_amp, s_tab, s_gid);
-        for (int j = nb - 1; j >= 0; --j) {
+        stage_batch<S>(a, b, range.x + bstart, nb, k0, s_geo, s_geo2, s_ext, s_amp, s_tab, s_gid);
+        uint64_t mask = warp_entry_mask(s_geo, s_ext, nb, wcx, wcy, a.W);
+        if (lane == 0) s_wmask[warp] = mask;
+        while (mask) {
+            const int j = 63 - __clzll((long long)mask);
+            mask ^= 1ull << j;
             float gr[9];
 #pragma unroll
             for (int c = 0; c < 9; ++c) gr[c] = 0.f;
@@ -312,7 +357,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
             const int j = e / 9, c = e - j * 9;
             float v = 0.f;
 #pragma unroll
-            for (int w2 = 0; w2 < kThreads / 32; ++w2) v += s_red[w2][j][c];
+            for (int w2 = 0; w2 < kThreads / 32; ++w2)
+                if ((s_wmask[w2] >> j) & 1ull) v += s_red[w2][j][c];
             if (v != 0.f) {
                 const uint32_t gid = s_gid[j];
                 if (c >= 5) {
@@ -330,13 +376,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
     }
 }
 
-int pick_strip(int K) {
-    if (K <= 1) return 1;
-    if (K <= 2) return 2;
-    if (K <= 4) return 4;
-    if (K <= 8) return 8;
-    if (K <= 16) return 16;
-    return 32;
+// Subcarriers per thread: the smallest power of two covering K, at most 32, then
+// halved (down to 8) while the launch would have fewer than three CTAs per SM, so
+// small views still fill the GPU (each extra strip re-evaluates alpha and T).
+int pick_strip(int K, int64_t tiles_times_B) {
+    int S = 1;
+    while (S < K && S < 32) S <<= 1;
+    const int64_t want = 3 * (int64_t)num_sms();
+    while (S > 8 && tiles_times_B * ((K + S - 1) / S) < want) S >>= 1;
+    return S;
 }
 
 bool fill_args(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
@@ -407,7 +455,7 @@ extern "C" int gsparc_render_fwd(const gsparc_view* view, const gsparc_band* ban
     a.n_used = n_used;
     const int T = tiles_x(*view) * tiles_y(*view);
     cudaStream_t s = as_stream(stream);
-    switch (pick_strip(band->K)) {
+    switch (pick_strip(band->K, (int64_t)T * B)) {
         case 1: launch_fwd<1>(a, T, s); break;
         case 2: launch_fwd<2>(a, T, s); break;
         case 4: launch_fwd<4>(a, T, s); break;
@@ -437,7 +485,7 @@ extern "C" int gsparc_render_bwd(const gsparc_view* view, const gsparc_band* ban
     a.d_proj = d_proj;
     const int T = tiles_x(*view) * tiles_y(*view);
     cudaStream_t s = as_stream(stream);
-    switch (pick_strip(band->K)) {
+    switch (pick_strip(band->K, (int64_t)T * B)) {
         case 1: launch_bwd<1>(a, T, s); break;
         case 2: launch_bwd<2>(a, T, s); break;
         case 4: launch_bwd<4>(a, T, s); break;
