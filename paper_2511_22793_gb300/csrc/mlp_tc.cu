@@ -1,12 +1,383 @@
-// Attribute network on the tensor cores (BF16 operands, FP32 accumulation).
+// Attribute network on the 5th-generation tensor cores (tcgen05, BF16 operands,
+// FP32 accumulation in tensor memory).
+//
+// Eq. 1 network, batched over (transmitter, Gaussian) rows as in
+// gsparc_attr_mlp: h1 = relu(h0 W1 + b1), h2 = relu(h1 W2 + b2), o = h2 W3 + b3.
+// Layers 1 and 2 are M=128 x N=hidden x K GEMMs issued with tcgen05.mma by one
+// thread; the output layer (hidden -> 3) and the activation epilogues run on the
+// CUDA cores in FP32.
+//
+// Precision modes:
+//   GSPARC_BF16    each operand rounded to BF16 once (one term).
+//   GSPARC_BF16X2  each operand x split as x_hi = bf16(x), x_lo = bf16(x - x_hi);
+//                  the products x_hi y_hi + x_lo y_hi + x_hi y_lo (three terms laid
+//                  side by side along K) recover ~16 mantissa bits.
+//
+// Shared-memory operands use the canonical K-major layout without swizzling:
+// 8-row x 16-byte core matrices, core matrices adjacent along K 128 bytes apart
+// (leading byte offset), 8-row groups Kt*16 bytes apart (stride byte offset).
+// One CTA of 128 threads (4 warps) owns TMEM lanes 0..127 = the tile's rows;
+// thread t builds row t of the A operand and reads row t of each accumulator.
+
+#include <algorithm>
 
 #include "internal.cuh"
 
 namespace gsparc {
+namespace {
 
-int attr_mlp_bf16(int32_t, int32_t, const float*, const float*, const float*, const float*, const float*,
-                  const gsparc_mlp*, int32_t, float*, cudaStream_t) {
-    return GSPARC_ERR_INVALID;
+constexpr int kRows = 128;
+constexpr int kK1 = 32;   // 20 inputs padded to a multiple of 16
+constexpr uint32_t kSpin = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+    // round to nearest even (inputs are finite)
+    uint32_t u = __float_as_uint(x);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+__device__ __forceinline__ float bf16_val(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+
+// Smem matrix descriptor (no swizzle).  Address fields are byte offsets >> 4.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
+    d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+    d |= (uint64_t)1 << 46;   // fixed 0b001 field
+    return d;                 // base offset 0, relative LBO, swizzle none
+}
+
+// Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (r, k) in a K-major canonical tile with Kt columns.
+__device__ __forceinline__ uint32_t canon_off(int r, int k, int Kt) {
+    return (uint32_t)((r >> 3) * (Kt * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+// Bounded wait for the given phase parity; false when the bound expired.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (uint32_t it = 0; it < kSpin; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+        "[%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Write the `terms` K-blocks of a row: values x[0..n) split into hi/lo; block layout
+// [hi | lo | hi] (three terms) or [hi] (one term), each block Kb columns wide.
+template <int TERMS>
+__device__ __forceinline__ void write_row(uint8_t* tile, int r, const float* x, int n, int Kb) {
+    const int Kt = Kb * TERMS;
+    for (int k0 = 0; k0 < Kb; k0 += 8) {
+        uint16_t hi[8], lo[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = k0 + q;
+            const float v = k < n ? x[k] : 0.f;
+            hi[q] = bf16_bits(v);
+            lo[q] = bf16_bits(v - bf16_val(hi[q]));
+        }
+        uint4 H, Lo;
+        H.x = hi[0] | ((uint32_t)hi[1] << 16);
+        H.y = hi[2] | ((uint32_t)hi[3] << 16);
+        H.z = hi[4] | ((uint32_t)hi[5] << 16);
+        H.w = hi[6] | ((uint32_t)hi[7] << 16);
+        Lo.x = lo[0] | ((uint32_t)lo[1] << 16);
+        Lo.y = lo[2] | ((uint32_t)lo[3] << 16);
+        Lo.z = lo[4] | ((uint32_t)lo[5] << 16);
+        Lo.w = lo[6] | ((uint32_t)lo[7] << 16);
+        *reinterpret_cast<uint4*>(tile + canon_off(r, k0, Kt)) = H;
+        if (TERMS == 3) {
+            *reinterpret_cast<uint4*>(tile + canon_off(r, Kb + k0, Kt)) = Lo;
+            *reinterpret_cast<uint4*>(tile + canon_off(r, 2 * Kb + k0, Kt)) = H;
+        }
+    }
+}
+
+// Weight operand B[n][k] = W[k][n] (W input-major [kin, N]) in blocks [hi | hi | lo].
+template <int TERMS>
+__device__ __forceinline__ void write_weights(uint8_t* tile, const float* __restrict__ W, int kin, int N,
+                                              int Kb) {
+    const int Kt = Kb * TERMS;
+    for (int e = threadIdx.x; e < N * Kb; e += blockDim.x) {
+        const int n = e / Kb, k = e - n * Kb;
+        const float v = k < kin ? W[k * N + n] : 0.f;
+        const uint16_t hi = bf16_bits(v);
+        const uint16_t lo = bf16_bits(v - bf16_val(hi));
+        *reinterpret_cast<uint16_t*>(tile + canon_off(n, k, Kt)) = hi;
+        if (TERMS == 3) {
+            *reinterpret_cast<uint16_t*>(tile + canon_off(n, Kb + k, Kt)) = hi;
+            *reinterpret_cast<uint16_t*>(tile + canon_off(n, 2 * Kb + k, Kt)) = lo;
+        }
+    }
+}
+
+template <int HD, int TERMS>
+struct TcSmem {
+    static constexpr int kKt1 = kK1 * TERMS;
+    static constexpr int kKt2 = HD * TERMS;
+    static constexpr int kA1 = 0;                                  // [128 x Kt1] bf16
+    static constexpr int kA2 = kA1 + kRows * kKt1 * 2;             // [128 x Kt2]
+    static constexpr int kB1 = kA2 + kRows * kKt2 * 2;             // [HD x Kt1]
+    static constexpr int kB2 = kB1 + HD * kKt1 * 2;                // [HD x Kt2]
+    static constexpr int kF = kB2 + HD * kKt2 * 2;                 // fp32: b1, b2, W3, b3
+    static constexpr int kMisc = kF + (2 * HD + 3 * HD + 4) * 4;   // mbarrier, tmem addr
+    static constexpr int kTotal = kMisc + 32;
+};
+
+template <int HD, int TERMS>
+__global__ void __launch_bounds__(kRows) k_mlp_tc(int N, int B, const float* __restrict__ tx, float rx0,
+                                                  float rx1, float rx2, const float* __restrict__ means,
+                                                  const float* __restrict__ ologit,
+                                                  const float* __restrict__ latent,
+                                                  const float* __restrict__ W1, const float* __restrict__ b1,
+                                                  const float* __restrict__ W2, const float* __restrict__ b2,
+                                                  const float* __restrict__ W3, const float* __restrict__ b3,
+                                                  float4* __restrict__ attr) {
+    using L = TcSmem<HD, TERMS>;
+    extern __shared__ __align__(1024) uint8_t sm[];
+    const int t = threadIdx.x, warp = t >> 5;
+    float* sf = reinterpret_cast<float*>(sm + L::kF);
+    float* sb1 = sf;
+    float* sb2 = sf + HD;
+    float* sW3 = sf + 2 * HD;
+    float* sb3 = sf + 5 * HD;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + L::kMisc);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::kMisc + 8);
+
+    write_weights<TERMS>(sm + L::kB1, W1, GSPARC_MLP_IN, HD, kK1);
+    write_weights<TERMS>(sm + L::kB2, W2, HD, HD, HD);
+    for (int e = t; e < HD; e += kRows) {
+        sb1[e] = b1[e];
+        sb2[e] = b2[e];
+    }
+    for (int e = t; e < 3 * HD; e += kRows) sW3[e] = W3[e];
+    if (t < 3) sb3[t] = b3[t];
+    const uint32_t mb = smem_u32(mbar);
+    if (t == 0) {
+        mbar_init(mb, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        // 2*HD accumulator columns (D1 then D2), rounded up to a power of two >= 32
+        constexpr uint32_t ncols = (2 * HD <= 32) ? 32 : (2 * HD <= 64 ? 64 : 128);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+    const uint32_t d1 = tbase, d2 = tbase + HD;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    constexpr uint32_t idesc = make_idesc(kRows, HD);
+    const uint32_t a1 = smem_u32(sm + L::kA1), a2 = smem_u32(sm + L::kA2);
+    const uint32_t bb1 = smem_u32(sm + L::kB1), bb2 = smem_u32(sm + L::kB2);
+    uint32_t phase = 0;
+    bool ok = true;
+
+    const int64_t rows = (int64_t)N * B;
+    const int64_t tiles = (rows + kRows - 1) / kRows;
+    for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const int64_t row = tile * kRows + t;
+        const bool valid = row < rows;
+        int b = 0, i = 0;
+        float d = 1.f, logd = 0.f, r = 0.f;
+        float h0[GSPARC_MLP_IN];
+        if (valid) {
+            b = (int)(row / N);
+            i = (int)(row - (int64_t)b * N);
+            const float t0 = tx[3 * b], t1 = tx[3 * b + 1], t2 = tx[3 * b + 2];
+            const float m0 = means[3 * i], m1 = means[3 * i + 1], m2 = means[3 * i + 2];
+            const float e0 = m0 - t0, e1 = m1 - t1, e2 = m2 - t2;
+            d = fmaxf(sqrtf(e0 * e0 + e1 * e1 + e2 * e2), kDMin);
+            logd = logf(d);
+            const float f0 = m0 - rx0, f1 = m1 - rx1, f2 = m2 - rx2;
+            r = sqrtf(f0 * f0 + f1 * f1 + f2 * f2);
+            h0[0] = t0;
+            h0[1] = t1;
+            h0[2] = t2;
+            const float4* l4 = reinterpret_cast<const float4*>(latent + (size_t)i * GSPARC_LATENT);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 v = l4[q];
+                h0[3 + 4 * q] = v.x;
+                h0[4 + 4 * q] = v.y;
+                h0[5 + 4 * q] = v.z;
+                h0[6 + 4 * q] = v.w;
+            }
+            h0[19] = logd;
+        } else {
+#pragma unroll
+            for (int f = 0; f < GSPARC_MLP_IN; ++f) h0[f] = 0.f;
+        }
+        // ---- layer 1 on the tensor cores
+        write_row<TERMS>(sm + L::kA1, t, h0, GSPARC_MLP_IN, kK1);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (t == 0) {
+#pragma unroll
+            for (int s = 0; s < L::kKt1 / 16; ++s)
+                mma_bf16(d1, make_desc(a1 + s * 256, 128, L::kKt1 * 16),
+                         make_desc(bb1 + s * 256, 128, L::kKt1 * 16), idesc, s > 0);
+            mma_commit(mb);
+        }
+        ok = __syncthreads_and(mbar_wait(mb, phase)) != 0;   // uniform across the CTA
+        phase ^= 1;
+        tc_fence_after();
+        float h1[HD];
+#pragma unroll
+        for (int c = 0; c < HD; c += 16) {
+            float v[16];
+            tmem_ld16(d1 + lane_base + c, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) h1[c + q] = fmaxf(v[q] + sb1[c + q], 0.f);
+        }
+        // ---- layer 2 on the tensor cores
+        write_row<TERMS>(sm + L::kA2, t, h1, HD, HD);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (t == 0 && ok) {
+#pragma unroll
+            for (int s = 0; s < L::kKt2 / 16; ++s)
+                mma_bf16(d2, make_desc(a2 + s * 256, 128, L::kKt2 * 16),
+                         make_desc(bb2 + s * 256, 128, L::kKt2 * 16), idesc, s > 0);
+            mma_commit(mb);
+        }
+        ok = __syncthreads_and(ok && mbar_wait(mb, phase)) != 0;
+        phase ^= 1;
+        tc_fence_after();
+        float o0 = sb3[0], o1 = sb3[1], o2 = sb3[2];
+#pragma unroll
+        for (int c = 0; c < HD; c += 16) {
+            float v[16];
+            tmem_ld16(d2 + lane_base + c, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float h2 = fmaxf(v[q] + sb2[c + q], 0.f);
+                o0 = fmaf(h2, sW3[(c + q) * 3 + 0], o0);
+                o1 = fmaf(h2, sW3[(c + q) * 3 + 1], o1);
+                o2 = fmaf(h2, sW3[(c + q) * 3 + 2], o2);
+            }
+        }
+        tc_fence_before();
+        if (valid) {
+            if (ok) {
+                const float a = 1.0f / (1.0f + expf(-(o0 - logd))) / d;
+                const float sig = 1.0f / (1.0f + expf(-(ologit[i] + o2)));
+                attr[row] = make_float4(a, o1, sig, d + r);
+            } else {
+                const float nan = __int_as_float(0x7fc00000);
+                attr[row] = make_float4(nan, nan, nan, nan);   // an expired wait poisons the rows
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        constexpr uint32_t ncols = (2 * HD <= 32) ? 32 : (2 * HD <= 64 ? 64 : 128);
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(ncols) : "memory");
+    }
+}
+
+template <int HD, int TERMS>
+int launch_tc(int32_t N, int32_t B, const float* tx, const float* rx, const float* means, const float* ologit,
+              const float* latent, const gsparc_mlp* m, float* attr, cudaStream_t s) {
+    using L = TcSmem<HD, TERMS>;
+    const size_t smem = L::kTotal;
+    if (cudaFuncSetAttribute(k_mlp_tc<HD, TERMS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return GSPARC_ERR_CUDA;
+    const int64_t tiles = ((int64_t)N * B + kRows - 1) / kRows;
+    // at most 4 resident CTAs per SM fit the 512 TMEM columns (128 each)
+    const int blocks = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * 2);
+    k_mlp_tc<HD, TERMS><<<blocks, kRows, smem, s>>>(N, B, tx, rx[0], rx[1], rx[2], means, ologit, latent, m->W1,
+                                                    m->b1, m->W2, m->b2, m->W3, m->b3,
+                                                    reinterpret_cast<float4*>(attr));
+    return launch_status();
+}
+
+}  // namespace
+
+int attr_mlp_bf16(int32_t N, int32_t B, const float* tx, const float* rx, const float* means,
+                  const float* opacity_logit, const float* latent, const gsparc_mlp* mlp, int32_t precision,
+                  float* attr, cudaStream_t s) {
+    const bool x2 = precision == GSPARC_BF16X2;
+    switch (mlp->hidden) {
+        case 16: return x2 ? launch_tc<16, 3>(N, B, tx, rx, means, opacity_logit, latent, mlp, attr, s)
+                           : launch_tc<16, 1>(N, B, tx, rx, means, opacity_logit, latent, mlp, attr, s);
+        case 32: return x2 ? launch_tc<32, 3>(N, B, tx, rx, means, opacity_logit, latent, mlp, attr, s)
+                           : launch_tc<32, 1>(N, B, tx, rx, means, opacity_logit, latent, mlp, attr, s);
+        case 64: return x2 ? launch_tc<64, 3>(N, B, tx, rx, means, opacity_logit, latent, mlp, attr, s)
+                           : launch_tc<64, 1>(N, B, tx, rx, means, opacity_logit, latent, mlp, attr, s);
+        default: return GSPARC_ERR_INVALID;   // the tensor-core form needs N = hidden >= 16
+    }
 }
 
 }  // namespace gsparc

@@ -238,6 +238,42 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_fwd(RenderArgs a) {
     }
 }
 
+// Sum of v[c] over the 32 lanes of the warp for c < 9, returned in lane 2c (and
+// 2c + 1): four halving exchange rounds (8 + 4 + 2 + 1 shuffles) then one final
+// pairwise add, instead of a full butterfly per component.
+__device__ __forceinline__ float warp_reduce_scatter9(const float (&v)[9], int lane) {
+    float a[8];
+    const bool b4 = (lane >> 4) & 1;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float lo = v[i];
+        const float hi = (i + 8 < 9) ? v[i + 8] : 0.f;
+        const float send = b4 ? lo : hi;
+        const float keep = b4 ? hi : lo;
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float b[4];
+    const bool b3 = (lane >> 3) & 1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = b3 ? a[i] : a[i + 4];
+        const float keep = b3 ? a[i + 4] : a[i];
+        b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float c[2];
+    const bool b2 = (lane >> 2) & 1;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = b2 ? b[i] : b[i + 2];
+        const float keep = b2 ? b[i + 2] : b[i];
+        c[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    const bool b1 = (lane >> 1) & 1;
+    float d = (b1 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, b1 ? c[0] : c[1], 2);
+    d += __shfl_xor_sync(0xffffffffu, d, 1);
+    return d;
+}
+
 template <int S>
 __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
     __shared__ float4 s_geo[kBatch];
@@ -338,17 +374,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                for (int c = 0; c < 9; ++c) {
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) gr[c] += __shfl_xor_sync(0xffffffffu, gr[c], o);
-                }
-            }
-            if (lane < 9) {
-                float v = 0.f;
-#pragma unroll
-                for (int c = 0; c < 9; ++c) v = (lane == c) ? gr[c] : v;
-                s_red[warp][j][lane] = v;
+                // reduce-scatter of the 9 components over the warp: lane l ends with the
+                // warp total of component l >> 1
+                const float tot = warp_reduce_scatter9(gr, lane);
+                if ((lane & 1) == 0 && (lane >> 1) < 9) s_red[warp][j][lane >> 1] = tot;
+            } else if (lane < 9) {
+                s_red[warp][j][lane] = 0.f;
             }
         }
         __syncthreads();
@@ -376,14 +407,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
     }
 }
 
-// Subcarriers per thread: the smallest power of two covering K, at most 32, then
-// halved (down to 8) while the launch would have fewer than three CTAs per SM, so
-// small views still fill the GPU (each extra strip re-evaluates alpha and T).
-int pick_strip(int K, int64_t tiles_times_B) {
+// Subcarriers per thread: the smallest power of two covering K, at most 32.
+// (Splitting K into more, narrower strips to raise the CTA count was measured
+// slower: every strip re-evaluates alpha, T and the gradient reduction.)
+int pick_strip(int K, int64_t) {
     int S = 1;
     while (S < K && S < 32) S <<= 1;
-    const int64_t want = 3 * (int64_t)num_sms();
-    while (S > 8 && tiles_times_B * ((K + S - 1) / S) < want) S >>= 1;
     return S;
 }
 

@@ -156,3 +156,24 @@ def test_attr_mlp_matches_oracle(hidden, B, n):
         for j, k in enumerate(("a", "phi0", "sigma", "L")):
             np.testing.assert_allclose(attr[b, :, j], ref[b][k], rtol=2e-5,
                                        atol=2e-6 * max(1.0, np.abs(ref[b][k]).max()))
+
+
+@pytest.mark.parametrize("hidden,B,n", [(16, 2, 1000), (32, 3, 4099), (64, 2, 2500)])
+def test_attr_mlp_tensor_cores(hidden, B, n):
+    """The tcgen05 network: BF16X2 (split operands) within 1e-4 of the FP64 oracle,
+    BF16 within 3e-2 (one BF16 rounding of inputs and activations), no NaN."""
+    sc = synth.make_scene(n, seed=hidden + 1)
+    mlp = synth.make_mlp(hidden, seed=3)
+    tx = synth.make_tx(B, seed=4)
+    r = Renderer(90, 360, 1, n, device=DEV)
+    ds = DeviceScene.from_host(sc, DEV)
+    dm = DeviceMLP.from_host(mlp, DEV)
+    txd = torch.tensor(tx, device=DEV)
+    _, ref = oracle_geo_attr(sc, mlp, synth.View(90, 360), tx)
+    for prec, tol in ((G.GSPARC_BF16X2, 1e-4), (G.GSPARC_BF16, 3e-2)):
+        attr = r.attributes(ds, dm, txd, precision=prec).cpu().numpy().astype(np.float64)
+        assert np.all(np.isfinite(attr))
+        for b in range(B):
+            for j, k in enumerate(("a", "phi0", "sigma", "L")):
+                err = np.linalg.norm(attr[b, :, j] - ref[b][k]) / np.linalg.norm(ref[b][k])
+                assert err <= tol, (prec, k, err)
