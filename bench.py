@@ -308,6 +308,7 @@ def run_ours(args, rank, world, local_rank):
     value = units * args.steps * world / (total_ms * 1e-3)
     e2e_value = units * args.steps * world / (e2e_total * 1e-3)
     sorted_ms = sorted(step_ms)
+    latency = query_latency(dev, queries=max(50, min(args.steps, 400)))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -322,10 +323,125 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_total / args.steps},
         "gpu_launches": launches_per_step * args.steps,
+        "query_latency": latency,
         "roofline": roofline,
         "clocks": clocks,
     }
     return out, units, sc, mlp, tx
+
+
+def query_latency(dev, queries=200):
+    """Single-query forward latency (1,024 Gaussians, 1 subcarrier, 360x90, hidden 32, FP32):
+    the plain one-query path (projection, bin/sort, network, render) and the query part alone
+    when the receiver is fixed and the geometry is cached (network + render), each timed per
+    query with CUDA events, L2 not flushed (a serving loop keeps the scene hot)."""
+    import torch
+
+    from paper_2511_22793_gb300 import synth
+    from paper_2511_22793_gb300.pipeline import DeviceMLP, DeviceScene, Renderer
+
+    n, K, H, W = 1024, 1, 90, 360
+    sc = synth.make_scene(n, seed=0)
+    mlp = synth.make_mlp(32, seed=3)
+    txs = torch.tensor(synth.make_tx(queries, seed=2), device=dev)
+    r = Renderer(H, W, K, n, device=dev)
+    ds = DeviceScene.from_host(sc, dev)
+    dm = DeviceMLP.from_host(mlp, dev)
+    attr = torch.empty((1, n, 4), device=dev)
+    outs = r.alloc_outputs(1)
+    stream = torch.cuda.current_stream(dev)
+
+    def full(q):
+        r.geometry(ds)
+        r.attributes(ds, dm, txs[q:q + 1], out=attr)
+        r.render(attr, out=outs)
+
+    def cached(q):
+        r.attributes(ds, dm, txs[q:q + 1], out=attr)
+        r.render(attr, out=outs)
+
+    res = {}
+    for name, fn in (("full_path", full), ("cached_geometry", cached)):
+        for q in range(5):
+            fn(q)
+        torch.cuda.synchronize(dev)
+        ms = []
+        for q in range(queries):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(q)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        res[name] = {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99))}
+    res["workload"] = "1,024 Gaussians, 1 subcarrier, 360x90, hidden 32, FP32, one query at a time"
+    res["queries"] = queries
+    return res
+
+
+def run_batched(args):
+    """Batched inference: 200,000 Gaussians, 64 transmitters in one launch, 256 subcarriers,
+    720x180, hidden 64; BF16X2 tensor-core network + FP32 compositing, against the plain path
+    (FP32 network, one transmitter per launch) on the same queries."""
+    import torch
+
+    from paper_2511_22793_gb300 import gsparc as G
+    from paper_2511_22793_gb300 import synth
+    from paper_2511_22793_gb300.pipeline import DeviceMLP, DeviceScene, Renderer
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n, B, K, H, W, hd = 200_000, 64, 256, 180, 720, 64
+    sc = synth.make_scene(n, seed=0, bf16_latent=True)
+    mlp = synth.make_mlp(hd, seed=3, bf16_weights=True)
+    tx = torch.tensor(synth.make_tx(B, seed=2), device=dev)
+    r = Renderer(H, W, K, n, device=dev)
+    ds = DeviceScene.from_host(sc, dev)
+    dm = DeviceMLP.from_host(mlp, dev)
+    r.geometry(ds)
+    assert r.check() == 0
+    attr = torch.empty((B, n, 4), device=dev)
+    spec, logT, nc = r.alloc_outputs(B)
+    n_used = torch.empty((B, H, W), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def batched():
+        r.attributes(ds, dm, tx, G.GSPARC_BF16X2, out=attr)
+        r.render(attr, out=(spec, logT, nc), n_used=n_used)
+
+    attr1 = torch.empty((1, n, 4), device=dev)
+    out1 = r.alloc_outputs(1)
+
+    def plain():
+        for b in range(B):
+            r.attributes(ds, dm, tx[b:b + 1], G.GSPARC_FP32, out=attr1)
+            r.render(attr1, out=out1)
+
+    batched()
+    torch.cuda.synchronize(dev)
+    units = int(n_used.sum().item()) * K
+    res = {}
+    for name, fn, reps in (("batched_bf16x2", batched, args.steps), ("plain_fp32_one_query", plain, 1)):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms_per_64_queries": ms, "units_per_s": units / (ms * 1e-3)}
+    out = {"metric": "Gaussian·pixel·subcarrier/s forward, batched", "value": res["batched_bf16x2"]["units_per_s"],
+           "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "bf16x2 network, f32 compositing",
+           "data": "synthetic (seeded)",
+           "config": {"workload": "batched inference, 200k Gaussians, 64 transmitters per launch, 256 subcarriers, "
+                                  "720x180, hidden 64", "units_per_launch": units, "pairs": int(r.n_pairs.item())},
+           "forms": res,
+           "speedup_vs_plain": res["plain_fp32_one_query"]["ms_per_64_queries"] / res["batched_bf16x2"]["ms_per_64_queries"]}
+    print(json.dumps(out))
 
 
 def cpu_baseline(sample_pixels, seed=0, threads=0, sc=None, mlp=None, tx=None):
@@ -401,6 +517,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=90 * 360,
                     help="pixels in the oracle CPU baseline (default: the whole image)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="fwdbwd", choices=["fwdbwd", "batched"],
+                    help="fwdbwd: the default step; batched: 64-transmitter inference with the "
+                         "tensor-core network against the plain one-query path")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -411,6 +530,10 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             run_reference(args)
+        return
+    if args.workload == "batched":
+        if rank == 0:
+            run_batched(args)
         return
 
     if world > 1:

@@ -69,6 +69,29 @@ def test_render_full_size_sampled_pixels():
     _check(50_000, 90, 360, 64, 1, 32, seed=0, pixels=pix)
 
 
+@pytest.mark.parametrize("precision,tol", [(G.GSPARC_BF16X2, TOL), (G.GSPARC_BF16, 1e-2)])
+def test_render_batched_tensor_core_network_full_size_sampled(precision, tol):
+    """The batched inference form at full size: 200,000 Gaussians, 256 subcarriers,
+    720x180, hidden 64, BF16-representable weights and latents, the network on the
+    tensor cores and FP32 compositing; 4 transmitters in one launch, 256 seeded
+    pixels per spectrum evaluated by the oracle.  BF16X2 must meet the 1e-3 bound;
+    the single-term BF16 network is reported against a looser 1e-2 bound."""
+    n, H, W, K, B = 200_000, 180, 720, 256, 4
+    sc = synth.make_scene(n, seed=0, bf16_latent=True)
+    mlp = synth.make_mlp(64, seed=3, bf16_weights=True)
+    tx = synth.make_tx(B, seed=2)
+    _, _, _, _, _, spec, _, _ = gpu_forward(sc, mlp, H, W, K, tx, precision=precision)
+    rng = np.random.default_rng(5)
+    pix = np.sort(rng.choice(H * W, size=256, replace=False)).astype(np.int32)
+    view, band = synth.View(H=H, W=W), synth.Band(K=K)
+    g, attrs = oracle_geo_attr(sc, mlp, view, tx)
+    zref, _, _ = oracle_render(g, attrs, view, band, pixels=pix)
+    z = spectrum_to_complex(spec)[:, pix]
+    errs = [rel_l2(z[b], zref[b]) for b in range(B)]
+    print("per-spectrum relative L2 (precision %d):" % precision, ["%.2e" % e for e in errs])
+    assert max(errs) <= tol
+
+
 def test_render_empty_and_all_culled():
     sc = synth.make_scene(64, seed=5)
     sc.means[:] = 0.0                          # every Gaussian inside the near distance
