@@ -172,6 +172,7 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     launches_per_step = 0
     ev = {}
+    render_fwd = G.gsparc_render_fwd_tc if args.render == "tc" else G.gsparc_render_fwd
 
     def stage(name, fn):
         if name in ev:
@@ -188,8 +189,8 @@ def run_ours(args, rank, world, local_rank):
                                                     None, r.tile_ranges, r.n_pairs, r.status))
         stage("attr_mlp", lambda: G.gsparc_attr_mlp(txd, r.rx, scene.means, scene.opacity_logit,
                                                     scene.latent, mlp_s, G.GSPARC_FP32, attr))
-        stage("render_fwd", lambda: G.gsparc_render_fwd(r.view, r.band, B, n, r.proj, r.tile_ranges,
-                                                        r.sorted_ids, attr, spec, logT, nc, n_used))
+        stage("render_fwd", lambda: render_fwd(r.view, r.band, B, n, r.proj, r.tile_ranges,
+                                               r.sorted_ids, attr, spec, logT, nc, n_used))
         stage("l2_loss", lambda: G.gsparc_l2_loss(spec, tgt, loss, d_spec))
         stage("render_bwd", lambda: G.gsparc_render_bwd(r.view, r.band, B, n, r.proj, r.tile_ranges,
                                                         r.sorted_ids, attr, logT, nc, d_spec, d_attr,
@@ -316,6 +317,8 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": wl["name"], "n_gaussians": n, "subcarriers": K, "H": H, "W": W,
                    "hidden": hidden, "transmitters_per_step": B, "pairs": n_pairs,
                    "units_per_step": units, "l2": "flushed (256 MiB write) between timed steps",
+                   "compositing_fwd": "tensor cores (split-BF16 products, FP32 accumulation)"
+                                      if args.render == "tc" else "FP32 CUDA cores",
                    "parallelism": "replicas x%d" % world},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "min": sorted_ms[0]},
@@ -517,6 +520,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=90 * 360,
                     help="pixels in the oracle CPU baseline (default: the whole image)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--render", default="tc", choices=["tc", "fp32"],
+                    help="forward compositing: tcgen05 (default) or FP32 CUDA cores")
     ap.add_argument("--workload", default="fwdbwd", choices=["fwdbwd", "batched"],
                     help="fwdbwd: the default step; batched: 64-transmitter inference with the "
                          "tensor-core network against the plain one-query path")

@@ -234,6 +234,22 @@ int gsparc_render_fwd(const gsparc_view* view, const gsparc_band* band, int32_t 
                       uint32_t* n_used, void* stream);
 
 /*
+ * gsparc_render_fwd with the subcarrier sum on the tensor cores (same
+ * arguments, same outputs).  The per-pixel weights w_i = T_i alpha_i are taken
+ * exactly as in gsparc_render_fwd (identical alpha, log2 T, cut-off and
+ * termination decisions, hence identical final_logT, n_contrib and n_used);
+ * the sum over the tile list of w_i s_ik (Sec. 4.2 compositing rule) runs as
+ * tcgen05 matrix products over batches of 32 list entries, with w and s each
+ * split into two BF16 terms (three products, ~16-bit operands) and FP32
+ * accumulation in tensor memory.  Spectra agree with gsparc_render_fwd to
+ * ~1e-5 relative.
+ */
+int gsparc_render_fwd_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
+                         const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
+                         const float* attr, float* spectrum, float* final_logT,
+                         uint32_t* n_contrib, uint32_t* n_used, void* stream);
+
+/*
  * Gradient of gsparc_render_fwd (Algorithm 1 Backprop through compositing and
  * splatting).  Walks each pixel's list back to front from n_contrib,
  * recovering T_i from final_logT by subtracting log2(1 - alpha_i), so no

@@ -37,6 +37,7 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 constexpr int kSpinLimit = 1 << 20;
+constexpr int kLookWin = 8;                         // predecessors read per look-back round trip
 constexpr int kMaxPasses = 7;
 
 __device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
@@ -321,22 +322,34 @@ __global__ void __launch_bounds__(kOsThreads, 2) k_onesweep(
                 st_relaxed(my, kFlagInc | sum);
             } else {
                 st_relaxed(my, kFlagAgg | sum);
+                // look back over windows of kLookWin predecessors: the window's flags are
+                // loaded together (one L2 round trip per window, not per tile), then summed
+                // from the nearest tile down to the first inclusive prefix
                 int j = (int)tile - 1;
                 int spins = 0;
-                for (;;) {
-                    const uint32_t s = ld_relaxed(look + (size_t)j * 256 + d);
-                    const uint32_t flag = s & ~kValMask;
-                    if (flag == 0) {
-                        if (++spins > kSpinLimit) {
-                            set_status(status, GSPARC_ERR_TIMEOUT);
-                            break;
+                bool fin = false;
+                while (!fin) {
+                    uint32_t v[kLookWin];
+#pragma unroll
+                    for (int q = 0; q < kLookWin; ++q)
+                        v[q] = (j - q >= 0) ? ld_relaxed(look + (size_t)(j - q) * 256 + d) : kFlagInc;
+#pragma unroll
+                    for (int q = 0; q < kLookWin; ++q) {
+                        if (fin) break;
+                        uint32_t s = v[q];
+                        while ((s & ~kValMask) == 0) {   // that tile has not published yet
+                            if (++spins > kSpinLimit) {
+                                set_status(status, GSPARC_ERR_TIMEOUT);
+                                s = kFlagInc;
+                                break;
+                            }
+                            __nanosleep(32);
+                            s = ld_relaxed(look + (size_t)(j - q) * 256 + d);
                         }
-                        __nanosleep(32);
-                        continue;
+                        prefix += s & kValMask;
+                        if ((s & ~kValMask) == kFlagInc) fin = true;
                     }
-                    prefix += s & kValMask;
-                    if (flag == kFlagInc || j == 0) break;
-                    --j;
+                    j -= kLookWin;
                 }
                 st_relaxed(my, kFlagInc | ((prefix + sum) & kValMask));
             }

@@ -524,3 +524,320 @@ extern "C" int gsparc_render_bwd(const gsparc_view* view, const gsparc_band* ban
     }
     return launch_status();
 }
+
+// =============================================================================================
+// Tensor-core forward: the subcarrier contraction on tcgen05.
+//
+// For one (transmitter, tile, strip of S subcarriers) and a batch of E list entries, every
+// pixel's compositing weights w_pj = T_pj alpha_pj are computed on the CUDA cores exactly as in
+// k_render_fwd (same alpha, same log2 T recursion, same termination), and the strip of the
+// spectrum accumulates
+//     Z[p][2kk + {re, im}] += sum_j w_pj * Re/Im(a_j e^{j psi_jk})
+// as a [128 pixels x E] x [E x 2S] product per half tile on the tensor cores, accumulating in
+// TMEM (FP32).  Both operands are split into BF16 hi/lo terms laid side by side along K
+// ([w_hi | w_lo | w_hi] . [s_hi | s_hi | s_lo]), so every product carries ~16 mantissa bits
+// and the sum is accumulated in FP32.  A and B are double-buffered: the CUDA cores build
+// batch i+1 while the tensor cores consume batch i; tcgen05.commit on a per-stage mbarrier
+// frees a stage.  Every mbarrier wait is bounded; an expired wait poisons the strip with NaN.
+// =============================================================================================
+
+#include "tc.cuh"
+
+namespace gsparc {
+namespace {
+
+constexpr int kTcE = 32;            // list entries per batch
+constexpr int kTcKt = 3 * kTcE;     // three split-BF16 terms along K
+
+template <int S>
+struct RTcSmem {
+    static constexpr int kN = 2 * S;
+    static constexpr int kAHalf = 128 * kTcKt * 2;
+    static constexpr int kA = 0;                              // [stage][half] 128 x Kt bf16
+    static constexpr int kBStage = kN * kTcKt * 2;
+    static constexpr int kB = kA + 4 * kAHalf;                // [stage] 2S x Kt bf16
+    static constexpr int kGeo = kB + 2 * kBStage;             // float4[E]
+    static constexpr int kGeo2 = kGeo + kTcE * 16;            // float2[E]
+    static constexpr int kExt = kGeo2 + kTcE * 8;             // float2[E]
+    static constexpr int kAmp = kExt + kTcE * 8;              // float[E]
+    static constexpr int kPhi = kAmp + kTcE * 4;
+    static constexpr int kLen = kPhi + kTcE * 4;
+    static constexpr int kBar = kLen + kTcE * 4;              // 2 mbarriers + TMEM slot
+    static constexpr int kTotal = kBar + 32;
+    static constexpr uint32_t kCols = (4 * S <= 32) ? 32 : (4 * S <= 64 ? 64 : (4 * S <= 128 ? 128 : 256));
+};
+
+__device__ __forceinline__ uint4 pack8(const uint16_t (&h)[8]) {
+    uint4 u;
+    u.x = h[0] | ((uint32_t)h[1] << 16);
+    u.y = h[2] | ((uint32_t)h[3] << 16);
+    u.z = h[4] | ((uint32_t)h[5] << 16);
+    u.w = h[6] | ((uint32_t)h[7] << 16);
+    return u;
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
+    using L = RTcSmem<S>;
+    extern __shared__ __align__(1024) uint8_t sm[];
+    float4* s_geo = reinterpret_cast<float4*>(sm + L::kGeo);
+    float2* s_geo2 = reinterpret_cast<float2*>(sm + L::kGeo2);
+    float2* s_ext = reinterpret_cast<float2*>(sm + L::kExt);
+    float* s_amp = reinterpret_cast<float*>(sm + L::kAmp);
+    float* s_phi = reinterpret_cast<float*>(sm + L::kPhi);
+    float* s_len = reinterpret_cast<float*>(sm + L::kLen);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::kBar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::kBar + 16);
+
+    const int strip = blockIdx.x, tile = blockIdx.y, b = blockIdx.z;
+    const int k0 = strip * S;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int half = tid >> 7, m = tid & 127;
+    const int tx0 = (tile % a.TW) * kTile, ty0 = (tile / a.TW) * kTile;
+    const int x = tx0 + (tid & 15), y = ty0 + (tid >> 4);
+    const bool inside = x < a.W && y < a.H;
+    const float ux = (float)x + 0.5f, uy = (float)y + 0.5f;
+    const float wcx = (float)tx0 + 8.0f, wcy = (float)(ty0 + 2 * warp) + 1.0f;
+    const uint2 range = a.ranges[tile];
+
+    const uint32_t bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
+    if (tid == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(L::kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    constexpr uint32_t idesc = make_idesc(128, 2 * S);
+    const uint32_t a_base = smem_u32(sm + L::kA), b_base = smem_u32(sm + L::kB);
+
+    float logT = 0.f;
+    uint32_t last = 0, used = 0;
+    bool done = !inside;
+    uint32_t ph0 = 0, ph1 = 0;
+    bool pend0 = false, pend1 = false, any_mma = false, ok = true;
+    int it = 0;
+    for (uint32_t bs = range.x; bs < range.y; bs += kTcE, ++it) {
+        if (__syncthreads_or(!done) == 0) break;
+        const int st = it & 1;
+        // the stage's buffers are free once the MMAs issued two batches ago completed
+        bool wok = true;
+        if (st == 0 && pend0) { wok = mbar_wait(bar0, ph0); ph0 ^= 1; pend0 = false; }
+        if (st == 1 && pend1) { wok = mbar_wait(bar1, ph1); ph1 ^= 1; pend1 = false; }
+        ok = __syncthreads_and(wok && ok) != 0;
+        if (!ok) break;
+        tc_fence_after();
+        const int nb = (int)min((uint32_t)kTcE, range.y - bs);
+        if (tid < kTcE) {
+            uint32_t gid = tid < nb ? a.ids[bs + tid] : 0xffffffffu;
+            if (gid < (uint32_t)a.N) {
+                const float4 p0 = a.proj[2 * gid];
+                const float4 p1 = a.proj[2 * gid + 1];
+                const float4 at = a.attr[(size_t)b * a.N + gid];
+                s_geo[tid] = make_float4(p0.x, p0.y, p1.x, p1.y);
+                s_geo2[tid] = make_float2(p1.z, at.z);
+                s_ext[tid] = make_float2(p0.z, p0.w);
+                s_amp[tid] = at.x;
+                s_phi[tid] = at.y;
+                s_len[tid] = at.w;
+            } else {
+                s_geo[tid] = make_float4(0.f, 0.f, __int_as_float(0x7fc00000), 0.f);
+                s_geo2[tid] = make_float2(0.f, 0.f);
+                s_ext[tid] = make_float2(-1.f, -1.f);
+                s_amp[tid] = 0.f;
+                s_phi[tid] = 0.f;
+                s_len[tid] = 0.f;
+            }
+        }
+        __syncthreads();
+        // ---- B: amplitude-scaled phasors of the strip, [hi | hi | lo] along K
+        uint8_t* Bst = sm + L::kB + st * L::kBStage;
+        for (int e = tid; e < S * (kTcE / 8); e += kThreads) {
+            const int kk = e % S, j0 = (e / S) * 8;
+            const int k = k0 + kk;
+            uint16_t rh[8], rl[8], ih[8], il[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int j = j0 + q;
+                float re = 0.f, im = 0.f;
+                if (j < nb && k < a.K) {
+                    const float Lj = s_len[j];
+                    const float p = Lj * a.lam0_hi;
+                    const float e0 = fmaf(Lj, a.lam0_hi, -p);
+                    float c = (p - rintf(p)) + (e0 + Lj * a.lam0_lo);
+                    c += Lj * ((float)k * a.dlam);
+                    c -= s_phi[j] * 0.15915494309189535f;
+                    c -= rintf(c);
+                    float sn, cs;
+                    sincospif(2.0f * c, &sn, &cs);
+                    re = s_amp[j] * cs;
+                    im = -s_amp[j] * sn;
+                }
+                rh[q] = bf16_bits(re);
+                rl[q] = bf16_bits(re - bf16_val(rh[q]));
+                ih[q] = bf16_bits(im);
+                il[q] = bf16_bits(im - bf16_val(ih[q]));
+            }
+            const uint4 RH = pack8(rh), RL = pack8(rl), IH = pack8(ih), IL = pack8(il);
+            const int nre = 2 * kk, nim = 2 * kk + 1;
+            *reinterpret_cast<uint4*>(Bst + canon_off(nre, j0, kTcKt)) = RH;
+            *reinterpret_cast<uint4*>(Bst + canon_off(nre, kTcE + j0, kTcKt)) = RH;
+            *reinterpret_cast<uint4*>(Bst + canon_off(nre, 2 * kTcE + j0, kTcKt)) = RL;
+            *reinterpret_cast<uint4*>(Bst + canon_off(nim, j0, kTcKt)) = IH;
+            *reinterpret_cast<uint4*>(Bst + canon_off(nim, kTcE + j0, kTcKt)) = IH;
+            *reinterpret_cast<uint4*>(Bst + canon_off(nim, 2 * kTcE + j0, kTcKt)) = IL;
+        }
+        // ---- A: this pixel's weights for the batch
+        float wv[kTcE];
+#pragma unroll
+        for (int j = 0; j < kTcE; ++j) wv[j] = 0.f;
+        const uint64_t mask = warp_entry_mask(s_geo, s_ext, nb, wcx, wcy, a.W);
+        if (!done) {
+            // phase 1: alpha and log2(1 - alpha) of every entry, independent of each other
+            float al[kTcE], nlv[kTcE];
+#pragma unroll
+            for (int j = 0; j < kTcE; ++j) {
+                al[j] = -1.f;
+                nlv[j] = 0.f;
+                if ((mask >> j) & 1ull) {   // warp-uniform
+                    float dx, dy, G, alpha;
+                    bool clamped;
+                    if (eval_alpha(ux, uy, a.W, s_geo[j], s_geo2[j], dx, dy, G, alpha, clamped)) {
+                        al[j] = alpha;
+                        nlv[j] = lg2(__fsub_rn(1.0f, alpha));
+                    }
+                }
+            }
+            // phase 2: the transmittance recursion, one FADD per entry on the serial chain
+#pragma unroll
+            for (int j = 0; j < kTcE; ++j) {
+                if (al[j] < 0.f) continue;
+                const float alpha = al[j], nl = nlv[j];
+                if (__fadd_rn(logT, nl) < kLog2TMin) {
+                    done = true;
+                    break;
+                }
+                wv[j] = ex2(logT) * alpha;
+                logT = __fadd_rn(logT, nl);
+                last = bs - range.x + (uint32_t)j + 1u;
+                ++used;
+            }
+        }
+        uint8_t* Ast = sm + L::kA + (st * 2 + half) * L::kAHalf;
+#pragma unroll
+        for (int j0 = 0; j0 < kTcE; j0 += 8) {
+            uint16_t hi[8], lo[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                hi[q] = bf16_bits(wv[j0 + q]);
+                lo[q] = bf16_bits(wv[j0 + q] - bf16_val(hi[q]));
+            }
+            const uint4 H = pack8(hi), Lo = pack8(lo);
+            *reinterpret_cast<uint4*>(Ast + canon_off(m, j0, kTcKt)) = H;
+            *reinterpret_cast<uint4*>(Ast + canon_off(m, kTcE + j0, kTcKt)) = Lo;
+            *reinterpret_cast<uint4*>(Ast + canon_off(m, 2 * kTcE + j0, kTcKt)) = H;
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            const uint32_t bst = b_base + st * L::kBStage;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t ast = a_base + (st * 2 + h) * L::kAHalf;
+#pragma unroll
+                for (int q = 0; q < kTcKt / 16; ++q)
+                    mma_bf16(tbase + h * 2 * S, make_desc(ast + q * 256, 128, kTcKt * 16),
+                             make_desc(bst + q * 256, 128, kTcKt * 16), idesc, (any_mma || q > 0) ? 1u : 0u);
+            }
+            mma_commit(st == 0 ? bar0 : bar1);
+        }
+        any_mma = true;
+        if (st == 0) pend0 = true;
+        else pend1 = true;
+    }
+    bool wok = true;
+    if (pend0) wok = mbar_wait(bar0, ph0) && wok;
+    if (pend1) wok = mbar_wait(bar1, ph1) && wok;
+    ok = __syncthreads_and(wok && ok) != 0;
+    tc_fence_after();
+    const size_t plane = (size_t)a.H * a.W;
+    const size_t pix = (size_t)y * a.W + x;
+#pragma unroll
+    for (int c = 0; c < 2 * S; c += 16) {
+        float v[16];
+        if (any_mma) {
+            tmem_ld16(tbase + half * 2 * S + lane_base + c, v);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = 0.f;
+        }
+        if (inside) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = k0 + c / 2 + q;
+                if (k < a.K) {
+                    const float nan = __int_as_float(0x7fc00000);
+                    a.spectrum[((size_t)b * a.K + k) * plane + pix] =
+                        ok ? make_float2(v[2 * q], v[2 * q + 1]) : make_float2(nan, nan);
+                }
+            }
+        }
+    }
+    if (inside && strip == 0) {
+        if (a.final_logT) a.final_logT[(size_t)b * plane + pix] = logT;
+        if (a.n_contrib) a.n_contrib[(size_t)b * plane + pix] = last;
+        if (a.n_used) a.n_used[(size_t)b * plane + pix] = used;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(L::kCols) : "memory");
+    }
+}
+
+template <int S>
+int launch_fwd_tc(const RenderArgs& a, int T, cudaStream_t s) {
+    using L = RTcSmem<S>;
+    if (cudaFuncSetAttribute(k_render_fwd_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal) !=
+        cudaSuccess)
+        return GSPARC_ERR_CUDA;
+    dim3 grid((a.K + S - 1) / S, T, a.B);
+    k_render_fwd_tc<S><<<grid, kThreads, L::kTotal, s>>>(a);
+    return launch_status();
+}
+
+}  // namespace
+}  // namespace gsparc
+
+extern "C" int gsparc_render_fwd_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
+                                    const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
+                                    const float* attr, float* spectrum, float* final_logT, uint32_t* n_contrib,
+                                    uint32_t* n_used, void* stream) {
+    using namespace gsparc;
+    if (!common_ok(view, band, B, N, proj, tile_ranges, sorted_ids, attr) || !spectrum) return GSPARC_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(spectrum) & 7) return GSPARC_ERR_INVALID;
+    RenderArgs a{};
+    fill_args(view, band, B, N, proj, tile_ranges, sorted_ids, attr, a);
+    a.spectrum = reinterpret_cast<float2*>(spectrum);
+    a.final_logT = final_logT;
+    a.n_contrib = n_contrib;
+    a.n_used = n_used;
+    const int T = tiles_x(*view) * tiles_y(*view);
+    cudaStream_t s = as_stream(stream);
+    if (band->K <= 8) return launch_fwd_tc<8>(a, T, s);
+    if (band->K <= 16) return launch_fwd_tc<16>(a, T, s);
+    if (band->K <= 32) return launch_fwd_tc<32>(a, T, s);
+    return launch_fwd_tc<64>(a, T, s);
+}

@@ -33,7 +33,7 @@ PROJ_STRIDE = 8
 EXPORTS = [
     "gsparc_num_tiles", "gsparc_project", "gsparc_project_bwd", "gsparc_bin_sort_workspace",
     "gsparc_bin_sort", "gsparc_bin_sort_noalloc", "gsparc_attr_mlp", "gsparc_attr_mlp_bwd", "gsparc_render_fwd",
-    "gsparc_render_bwd", "gsparc_l2_loss", "gsparc_adam", "gsparc_check", "gsparc_strerror",
+    "gsparc_render_fwd_tc", "gsparc_render_bwd", "gsparc_l2_loss", "gsparc_adam", "gsparc_check", "gsparc_strerror",
 ]
 
 
@@ -89,6 +89,8 @@ def lib():
                                                    vp, vp, P(MLPGrad), vp]),
             "gsparc_render_fwd": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
                                                  vp, vp, vp]),
+            "gsparc_render_fwd_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
+                                                    vp, vp, vp]),
             "gsparc_render_bwd": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
                                                  vp, vp, vp, vp]),
             "gsparc_l2_loss": (ctypes.c_int, [i64, vp, vp, vp, vp, vp]),
@@ -218,6 +220,13 @@ def gsparc_attr_mlp_bwd(tx, rx, means, opacity_logit, latent, mlp: MLP, d_attr, 
 def gsparc_render_fwd(view, band, B, n, proj, tile_ranges, sorted_ids, attr, spectrum,
                       final_logT=None, n_contrib=None, n_used=None, stream=None):
     _call("gsparc_render_fwd", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
+          _p(tile_ranges), _p(sorted_ids), _p(attr), _p(spectrum), _p(final_logT), _p(n_contrib),
+          _p(n_used), _stream(stream))
+
+
+def gsparc_render_fwd_tc(view, band, B, n, proj, tile_ranges, sorted_ids, attr, spectrum,
+                         final_logT=None, n_contrib=None, n_used=None, stream=None):
+    _call("gsparc_render_fwd_tc", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
           _p(tile_ranges), _p(sorted_ids), _p(attr), _p(spectrum), _p(final_logT), _p(n_contrib),
           _p(n_used), _stream(stream))
 

@@ -119,11 +119,13 @@ class Renderer:
         nc = torch.empty((B, self.H, self.W), dtype=torch.int32, device=dev)
         return spec, logT, nc
 
-    def render(self, attr, out=None, n_used=None, stream=None):
+    def render(self, attr, out=None, n_used=None, tensor_cores=False, stream=None):
+        """Forward compositing; tensor_cores selects gsparc_render_fwd_tc (same outputs)."""
         B = int(attr.shape[0])
         spec, logT, nc = out if out is not None else self.alloc_outputs(B)
-        G.gsparc_render_fwd(self.view, self.band, B, self.n, self.proj, self.tile_ranges,
-                            self.sorted_ids, attr, spec, logT, nc, n_used, stream)
+        fn = G.gsparc_render_fwd_tc if tensor_cores else G.gsparc_render_fwd
+        fn(self.view, self.band, B, self.n, self.proj, self.tile_ranges, self.sorted_ids, attr, spec,
+           logT, nc, n_used, stream)
         return spec, logT, nc
 
     def render_backward(self, attr, logT, nc, d_spec, d_attr, d_proj, stream=None):
