@@ -41,6 +41,21 @@ inline int num_sms() {
     return n > 0 ? n : 1;
 }
 
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (kernel, device): the attribute
+// persists, and skipping the repeat keeps launches cheap and capture-friendly.
+template <typename Kernel>
+inline bool ensure_smem_attr(Kernel k, int bytes) {
+    static uint64_t done_mask = 0;   // bit d: set on device d (first 64 devices)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+    if (bit && (done_mask & bit)) return true;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+        return false;
+    done_mask |= bit;
+    return true;
+}
+
 // Device-side view constants passed by value to kernels.
 struct ViewDev {
     int H, W;

@@ -386,9 +386,7 @@ int launch_bwd(int N, int B, const float* tx, const float* rx, const float* mean
                const float* latent, const W& w, const float4* d_attr, float* d_means, float* d_ologit,
                float* d_latent, const gsparc_mlp_grad& g, cudaStream_t s) {
     const size_t smem = (size_t)BwdSmem<HD>::kTotal * sizeof(float);
-    if (cudaFuncSetAttribute(k_mlp_bwd<HD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return GSPARC_ERR_CUDA;
+    if (!ensure_smem_attr(k_mlp_bwd<HD>, (int)smem)) return GSPARC_ERR_CUDA;
     const int64_t rows = (int64_t)N * B;
     const int64_t tiles = (rows + kBwdRows - 1) / kBwdRows;
     const int blocks = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * 2);

@@ -260,9 +260,7 @@ int launch_tc(int32_t N, int32_t B, const float* tx, const float* rx, const floa
               const float* latent, const gsparc_mlp* m, float* attr, cudaStream_t s) {
     using L = TcSmem<HD, TERMS>;
     const size_t smem = L::kTotal;
-    if (cudaFuncSetAttribute(k_mlp_tc<HD, TERMS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return GSPARC_ERR_CUDA;
+    if (!ensure_smem_attr(k_mlp_tc<HD, TERMS>, (int)smem)) return GSPARC_ERR_CUDA;
     const int64_t tiles = ((int64_t)N * B + kRows - 1) / kRows;
     // at most 4 resident CTAs per SM fit the 512 TMEM columns (128 each)
     const int blocks = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * 2);

@@ -810,9 +810,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
 template <int S>
 int launch_fwd_tc(const RenderArgs& a, int T, cudaStream_t s) {
     using L = RTcSmem<S>;
-    if (cudaFuncSetAttribute(k_render_fwd_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal) !=
-        cudaSuccess)
-        return GSPARC_ERR_CUDA;
+    if (!ensure_smem_attr(k_render_fwd_tc<S>, L::kTotal)) return GSPARC_ERR_CUDA;
     dim3 grid((a.K + S - 1) / S, T, a.B);
     k_render_fwd_tc<S><<<grid, kThreads, L::kTotal, s>>>(a);
     return launch_status();
