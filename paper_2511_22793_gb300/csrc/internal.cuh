@@ -4,6 +4,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "gsparc.h"
 
 namespace gsparc {
@@ -43,16 +47,20 @@ inline int num_sms() {
 
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (kernel, device): the attribute
 // persists, and skipping the repeat keeps launches cheap and capture-friendly.
+// Keyed by the kernel's address (kernels of one signature share a type).
 template <typename Kernel>
 inline bool ensure_smem_attr(Kernel k, int bytes) {
-    static uint64_t done_mask = 0;   // bit d: set on device d (first 64 devices)
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> done;   // (kernel, device) -> bytes set
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
-    const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
-    if (bit && (done_mask & bit)) return true;
+    const auto key = std::make_pair(reinterpret_cast<const void*>(k), dev);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = done.find(key);
+    if (it != done.end() && it->second >= bytes) return true;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
         return false;
-    done_mask |= bit;
+    done[key] = bytes;
     return true;
 }
 
