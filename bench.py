@@ -549,7 +549,7 @@ def run_serve(args):
     sat = st["spectra_per_s"]
     out_rows = []
     srv = Server(ds, dm, res, mem_budget_bytes=24 << 30, max_batch=8, n_streams=4, device=dev)
-    for frac in (0.25, 0.5, 0.75, 0.9):
+    for frac in (0.25, 0.5, 0.75, 0.9, 1.25, 2.0):
         lam = frac * sat
         reqs = make(n_req)
         arr = np.cumsum(rng.exponential(1.0 / lam, size=n_req))
@@ -565,6 +565,18 @@ def run_serve(args):
             q.spectrum = None
         b = latency_stats(plain)
         out_rows.append({"load": frac, "rate_per_s": lam, "batched": a, "plain": b})
+    # saturated: every request queued at once
+    burst = make(n_req)
+    srv.done = []
+    srv.run(burst, np.zeros(n_req))
+    torch.cuda.synchronize(dev)
+    for q in burst:
+        q.spectrum = None
+    burst_plain = [Request(q.rid, q.tx, q.res, q.K) for q in burst]
+    serve_plain(ds, dm, burst_plain, np.zeros(n_req), res, device=dev)
+    for q in burst_plain:
+        q.spectrum = None
+    out_rows.append({"load": "burst", "batched": latency_stats(burst), "plain": latency_stats(burst_plain)})
     out = {"metric": "query latency p50/p99 and spectra/s under Poisson load", "unit": "ms",
            "n_gpus": 1, "requests_per_load": n_req, "plain_saturated_spectra_per_s": sat,
            "config": {"workload": "serving: 500k-Gaussian resident scene, resolutions {180x45, 360x90, "

@@ -52,13 +52,20 @@ def init_scene(n, seed=10, init_scale=0.2, init_opacity=0.1):
 
 class Trainer:
     def __init__(self, n, gt_scene, gt_mlp, train_tx, H=90, W=360, K=128, hidden=32, batch=4,
-                 total_steps=1000, device="cuda", seed=10, tensor_cores=True):
+                 total_steps=1000, device="cuda", seed=10, tensor_cores=True, init=None):
+        """init: optional (Scene, MLPWeights) to start from instead of the paper's
+        geometry-agnostic initialisation."""
         self.dev = torch.device(device)
         self.H, self.W, self.K, self.n, self.batch = H, W, K, n, batch
         self.total_steps = total_steps
         self.tensor_cores = tensor_cores
-        sc = init_scene(n, seed=seed)
-        mlp = synth.make_mlp(hidden, seed=seed + 1)
+        if init is None:
+            sc = init_scene(n, seed=seed)
+            mlp = synth.make_mlp(hidden, seed=seed + 1)
+        else:
+            sc, mlp = init
+            n = sc.n
+            self.n = n
         self.scene = DeviceScene.from_host(sc, self.dev)
         self.mlp = DeviceMLP.from_host(mlp, self.dev)
         self.params = dict(zip(SCENE_KEYS, self.scene.tensors()))
