@@ -173,6 +173,7 @@ def run_ours(args, rank, world, local_rank):
     launches_per_step = 0
     ev = {}
     render_fwd = G.gsparc_render_fwd_tc if args.render == "tc" else G.gsparc_render_fwd
+    render_bwd = G.gsparc_render_bwd_tc if args.render == "tc" else G.gsparc_render_bwd
 
     def stage(name, fn):
         if name in ev:
@@ -192,9 +193,8 @@ def run_ours(args, rank, world, local_rank):
         stage("render_fwd", lambda: render_fwd(r.view, r.band, B, n, r.proj, r.tile_ranges,
                                                r.sorted_ids, attr, spec, logT, nc, n_used))
         stage("l2_loss", lambda: G.gsparc_l2_loss(spec, tgt, loss, d_spec))
-        stage("render_bwd", lambda: G.gsparc_render_bwd(r.view, r.band, B, n, r.proj, r.tile_ranges,
-                                                        r.sorted_ids, attr, logT, nc, d_spec, d_attr,
-                                                        d_proj))
+        stage("render_bwd", lambda: render_bwd(r.view, r.band, B, n, r.proj, r.tile_ranges,
+                                               r.sorted_ids, attr, logT, nc, d_spec, d_attr, d_proj))
         stage("attr_mlp_bwd", lambda: G.gsparc_attr_mlp_bwd(txd, r.rx, scene.means, scene.opacity_logit,
                                                             scene.latent, mlp_s, d_attr, grads[0],
                                                             grads[3], grads[4], grad_s))
@@ -331,8 +331,9 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": wl["name"], "n_gaussians": n, "subcarriers": K, "H": H, "W": W,
                    "hidden": hidden, "transmitters_per_step": B, "pairs": n_pairs,
                    "units_per_step": units, "l2": "flushed (256 MiB write) between timed steps",
-                   "compositing_fwd": "tensor cores (split-BF16 products, FP32 accumulation)"
-                                      if args.render == "tc" else "FP32 CUDA cores",
+                   "compositing": "subcarrier sums on tensor cores (split-BF16 products, FP32 "
+                                  "accumulation), transmittance and gradients FP32"
+                                  if args.render == "tc" else "FP32 CUDA cores",
                    "parallelism": "replicas x%d" % world},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "min": sorted_ms[0]},

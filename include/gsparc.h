@@ -263,6 +263,21 @@ int gsparc_render_bwd(const gsparc_view* view, const gsparc_band* band, int32_t 
                       const float* d_spectrum, float* d_attr, float* d_proj, void* stream);
 
 /*
+ * gsparc_render_bwd with its three per-(pixel, Gaussian) subcarrier sums on the
+ * tensor cores (same arguments, same outputs): Re and Im of
+ * sum_k conj(dL/dz_k) e^{j psi_k} and the subcarrier-weighted Im sum that gives
+ * dL/dL.  The upstream gradient of the strip is one operand, the Gaussians'
+ * unit phasors the other, both split into two BF16 terms with FP32
+ * accumulation in tensor memory; the back-to-front recursion (recovered T,
+ * suffix sums, alpha and conic derivatives) runs on the CUDA cores exactly as
+ * in gsparc_render_bwd.  Gradients agree with gsparc_render_bwd to ~1e-5.
+ */
+int gsparc_render_bwd_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
+                         const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
+                         const float* attr, const float* final_logT, const uint32_t* n_contrib,
+                         const float* d_spectrum, float* d_attr, float* d_proj, void* stream);
+
+/*
  * Complex L2 loss, the mean over `count` complex elements of |z - target|^2,
  * written to loss [1] (device; overwritten), and if d_z is not NULL its
  * gradient 2 (z - target) / count (overwritten).

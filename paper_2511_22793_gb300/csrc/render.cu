@@ -81,6 +81,22 @@ __device__ __forceinline__ bool eval_alpha(float ux, float uy, int W, const floa
     return alpha >= kAlphaMin;
 }
 
+// Unit phasor e^{j psi_k} of a Gaussian with path length L and phase offset phi0 at
+// subcarrier k: psi = phi0 - 2 pi f_k L / c.  The cycle count L f_k / c (~10^2) is formed
+// with an error-free product of the split f_0 / c, reduced to [-1/2, 1/2], and the angle
+// 2 pi c (in [-pi, pi]) goes to the SFU sine/cosine.
+__device__ __forceinline__ float2 unit_phasor(const RenderArgs& a, float L, float phi0, int k) {
+    const float p = L * a.lam0_hi;
+    const float e0 = fmaf(L, a.lam0_hi, -p);
+    float c = (p - rintf(p)) + (e0 + L * a.lam0_lo);
+    c += L * ((float)k * a.dlam);
+    c -= phi0 * 0.15915494309189535f;
+    c -= rintf(c);
+    float sn, cs;
+    __sincosf(6.283185307179586f * c, &sn, &cs);
+    return make_float2(cs, -sn);   // e^{j psi} = e^{-j 2 pi c}
+}
+
 // Stage batch entries [list_pos, list_pos + nb) of the tile list, and the
 // unit phasors of the strip's subcarriers.
 template <int S>
@@ -119,19 +135,7 @@ __device__ __forceinline__ void stage_batch(const RenderArgs& a, int b, uint32_t
         const int j = e / S, kk = e - j * S;
         const int k = k0 + kk;
         float2 ph = make_float2(0.f, 0.f);
-        if (k < a.K) {
-            const float L = s_L[j];
-            // cycles = L (lam0 + k dlam) - phi0 / (2 pi), reduced to [-1/2, 1/2]
-            const float p = L * a.lam0_hi;
-            const float e0 = fmaf(L, a.lam0_hi, -p);
-            float c = (p - rintf(p)) + (e0 + L * a.lam0_lo);
-            c += L * ((float)k * a.dlam);
-            c -= s_phi[j] * 0.15915494309189535f;
-            c -= rintf(c);
-            float sn, cs;
-            sincospif(2.0f * c, &sn, &cs);
-            ph = make_float2(cs, -sn);   // e^{j psi} = e^{-j 2 pi c}
-        }
+        if (k < a.K) ph = unit_phasor(a, s_L[j], s_phi[j], k);
         s_tab[j][kk] = ph;
     }
     __syncthreads();
@@ -670,17 +674,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
                 const int j = j0 + q;
                 float re = 0.f, im = 0.f;
                 if (j < nb && k < a.K) {
-                    const float Lj = s_len[j];
-                    const float p = Lj * a.lam0_hi;
-                    const float e0 = fmaf(Lj, a.lam0_hi, -p);
-                    float c = (p - rintf(p)) + (e0 + Lj * a.lam0_lo);
-                    c += Lj * ((float)k * a.dlam);
-                    c -= s_phi[j] * 0.15915494309189535f;
-                    c -= rintf(c);
-                    float sn, cs;
-                    sincospif(2.0f * c, &sn, &cs);
-                    re = s_amp[j] * cs;
-                    im = -s_amp[j] * sn;
+                    const float2 ph = unit_phasor(a, s_len[j], s_phi[j], k);
+                    re = s_amp[j] * ph.x;
+                    im = s_amp[j] * ph.y;
                 }
                 rh[q] = bf16_bits(re);
                 rl[q] = bf16_bits(re - bf16_val(rh[q]));
@@ -838,4 +834,365 @@ extern "C" int gsparc_render_fwd_tc(const gsparc_view* view, const gsparc_band* 
     if (band->K <= 16) return launch_fwd_tc<16>(a, T, s);
     if (band->K <= 32) return launch_fwd_tc<32>(a, T, s);
     return launch_fwd_tc<64>(a, T, s);
+}
+
+namespace gsparc {
+namespace {
+
+// =============================================================================================
+// Tensor-core backward.
+//
+// For one (transmitter, tile, strip of S subcarriers) the pixel's upstream gradient
+// g = dL/dz over the strip is the A operand (constant over the walk), and each batch of E list
+// entries contributes three B rows per entry j built from its unit phasors u_jk = e^{j psi_jk}:
+//     row 3j   : (Re u, Im u)      ->  D = sum_k Re(conj(g_k) u_jk)         (ReG)
+//     row 3j+1 : (Im u, -Re u)     ->  D = sum_k Im(conj(g_k) u_jk)         (ImG)
+//     row 3j+2 : kk (Im u, -Re u)  ->  D = sum_k kk Im(conj(g_k) u_jk)      (ImF)
+// (K index 2kk + {re, im} matches A = (Re g_k, Im g_k)).  Both operands are split into BF16
+// hi/lo terms and the products g_hi u_hi + g_lo u_hi + g_hi u_lo are accumulated in FP32 in
+// TMEM.  The CUDA cores then run the same back-to-front recursion as k_render_bwd on the three
+// contractions.  B and D are double-buffered: the tensor cores work on batch i while the CUDA
+// cores consume batch i-1.
+// =============================================================================================
+
+constexpr int kTbE = 16;   // entries per backward batch
+
+template <int S>
+struct RTbSmem {
+    static constexpr int kKa = 2 * S;                          // K of one term
+    static constexpr int kATile = 128 * kKa * 2;               // bytes of one (half, term) tile
+    static constexpr int kA = 0;                               // [half][hi, lo]
+    static constexpr int kBTile = 3 * kTbE * kKa * 2;          // bytes of one (stage, term) tile
+    static constexpr int kB = kA + 4 * kATile;                 // [stage][hi, lo]
+    static constexpr int kMeta = kB + 4 * kBTile;
+    // per stage: geo float4, geo2 float2, ext float2, amp, phi, len, gid (E each)
+    static constexpr int kMetaStage = kTbE * (16 + 8 + 8 + 4 + 4 + 4 + 4);
+    static constexpr int kRed = kMeta + 2 * kMetaStage;        // float [8 warps][E][9]
+    static constexpr int kMask = kRed + 8 * kTbE * 9 * 4;      // uint64 [8]
+    static constexpr int kBar = kMask + 8 * 8;                 // 2 mbarriers + TMEM slot + maxlast
+    static constexpr int kTotal = kBar + 32;
+    static constexpr uint32_t kCols = 256;                     // 2 stages x 2 halves x 3E columns
+};
+
+struct TbMeta {
+    float4* geo;
+    float2* geo2;
+    float2* ext;
+    float* amp;
+    float* phi;
+    float* len;
+    uint32_t* gid;
+};
+
+__device__ __forceinline__ TbMeta tb_meta(uint8_t* base) {
+    TbMeta m;
+    m.geo = reinterpret_cast<float4*>(base);
+    m.geo2 = reinterpret_cast<float2*>(base + kTbE * 16);
+    m.ext = reinterpret_cast<float2*>(base + kTbE * 24);
+    m.amp = reinterpret_cast<float*>(base + kTbE * 32);
+    m.phi = reinterpret_cast<float*>(base + kTbE * 36);
+    m.len = reinterpret_cast<float*>(base + kTbE * 40);
+    m.gid = reinterpret_cast<uint32_t*>(base + kTbE * 44);
+    return m;
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1) k_render_bwd_tc(RenderArgs a) {
+    using L = RTbSmem<S>;
+    extern __shared__ __align__(1024) uint8_t sm[];
+    float (*s_red)[kTbE][9] = reinterpret_cast<float (*)[kTbE][9]>(sm + L::kRed);
+    uint64_t* s_wmask = reinterpret_cast<uint64_t*>(sm + L::kMask);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::kBar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::kBar + 16);
+    uint32_t* s_maxlast = reinterpret_cast<uint32_t*>(sm + L::kBar + 20);
+
+    const int strip = blockIdx.x, tile = blockIdx.y, b = blockIdx.z;
+    const int k0 = strip * S;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int half = tid >> 7, m = tid & 127;
+    const int tx0 = (tile % a.TW) * kTile, ty0 = (tile / a.TW) * kTile;
+    const int x = tx0 + (tid & 15), y = ty0 + (tid >> 4);
+    const bool inside = x < a.W && y < a.H;
+    const float ux = (float)x + 0.5f, uy = (float)y + 0.5f;
+    const float wcx = (float)tx0 + 8.0f, wcy = (float)(ty0 + 2 * warp) + 1.0f;
+    const uint2 range = a.ranges[tile];
+    const size_t plane = (size_t)a.H * a.W;
+    const size_t pix = (size_t)y * a.W + x;
+
+    const uint32_t bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
+    if (tid == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *s_maxlast = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(L::kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // A operand: this pixel's upstream gradient over the strip, split hi / lo
+    {
+        uint8_t* Ahi = sm + L::kA + (half * 2 + 0) * L::kATile;
+        uint8_t* Alo = sm + L::kA + (half * 2 + 1) * L::kATile;
+#pragma unroll 1
+        for (int c0 = 0; c0 < 2 * S; c0 += 8) {
+            uint16_t hi[8], lo[8];
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+                const int k = k0 + (c0 + q) / 2;
+                float2 g = make_float2(0.f, 0.f);
+                if (inside && k < a.K) g = a.d_spectrum[((size_t)b * a.K + k) * plane + pix];
+                hi[q] = bf16_bits(g.x);
+                lo[q] = bf16_bits(g.x - bf16_val(hi[q]));
+                hi[q + 1] = bf16_bits(g.y);
+                lo[q + 1] = bf16_bits(g.y - bf16_val(hi[q + 1]));
+            }
+            *reinterpret_cast<uint4*>(Ahi + canon_off(m, c0, L::kKa)) = pack8(hi);
+            *reinterpret_cast<uint4*>(Alo + canon_off(m, c0, L::kKa)) = pack8(lo);
+        }
+    }
+    float logT = inside ? a.final_logT[(size_t)b * plane + pix] : 0.f;
+    const uint32_t last = inside ? a.n_contrib[(size_t)b * plane + pix] : 0u;
+    __syncthreads();
+    if (last) atomicMax(s_maxlast, last);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t maxlast = min(*s_maxlast, range.y - range.x);
+    const uint32_t tbase = *tslot;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    constexpr uint32_t idesc = make_idesc(128, 3 * kTbE);
+    const uint32_t a_base = smem_u32(sm + L::kA), b_base = smem_u32(sm + L::kB);
+    const float c_f0 = (float)(a.two_pi_over_c * (a.f0 + (double)k0 * a.df));
+    const float c_df = (float)(a.two_pi_over_c * a.df);
+    float suffix = 0.f;
+    const int nbatch = (int)((maxlast + kTbE - 1) / kTbE);
+    uint32_t ph0 = 0, ph1 = 0;
+    bool ok = true;
+
+    for (int i = 0; i <= nbatch && ok; ++i) {
+        if (i < nbatch) {
+            // ---- stage batch i (entries [lo, hi) of the list, walking back from maxlast)
+            const int st = i & 1;
+            const uint32_t hi_pos = maxlast - (uint32_t)i * kTbE;
+            const uint32_t lo_pos = hi_pos > (uint32_t)kTbE ? hi_pos - kTbE : 0u;
+            const int nb = (int)(hi_pos - lo_pos);
+            TbMeta md = tb_meta(sm + L::kMeta + st * L::kMetaStage);
+            if (tid < kTbE) {
+                uint32_t gid = tid < nb ? a.ids[range.x + lo_pos + tid] : 0xffffffffu;
+                if (gid < (uint32_t)a.N) {
+                    const float4 p0 = a.proj[2 * gid];
+                    const float4 p1 = a.proj[2 * gid + 1];
+                    const float4 at = a.attr[(size_t)b * a.N + gid];
+                    md.geo[tid] = make_float4(p0.x, p0.y, p1.x, p1.y);
+                    md.geo2[tid] = make_float2(p1.z, at.z);
+                    md.ext[tid] = make_float2(p0.z, p0.w);
+                    md.amp[tid] = at.x;
+                    md.phi[tid] = at.y;
+                    md.len[tid] = at.w;
+                    md.gid[tid] = gid;
+                } else {
+                    md.geo[tid] = make_float4(0.f, 0.f, __int_as_float(0x7fc00000), 0.f);
+                    md.geo2[tid] = make_float2(0.f, 0.f);
+                    md.ext[tid] = make_float2(-1.f, -1.f);
+                    md.amp[tid] = 0.f;
+                    md.phi[tid] = 0.f;
+                    md.len[tid] = 0.f;
+                    md.gid[tid] = 0;
+                }
+            }
+            __syncthreads();
+            // ---- B rows of the batch: thread (j, 8 consecutive K columns) computes 4 phasors
+            uint8_t* Bhi = sm + L::kB + (st * 2 + 0) * L::kBTile;
+            uint8_t* Blo = sm + L::kB + (st * 2 + 1) * L::kBTile;
+            for (int e = tid; e < kTbE * (L::kKa / 8); e += kThreads) {
+                const int j = e / (L::kKa / 8), c0 = (e % (L::kKa / 8)) * 8;
+                float r0[8], r1[8], r2[8];
+#pragma unroll
+                for (int q = 0; q < 8; q += 2) {
+                    const int kk = (c0 + q) / 2, k = k0 + kk;
+                    float2 u = make_float2(0.f, 0.f);
+                    if (j < nb && k < a.K) u = unit_phasor(a, md.len[j], md.phi[j], k);
+                    r0[q] = u.x;
+                    r0[q + 1] = u.y;
+                    r1[q] = u.y;
+                    r1[q + 1] = -u.x;
+                    r2[q] = (float)kk * u.y;
+                    r2[q + 1] = -(float)kk * u.x;
+                }
+                const float* rows[3] = {r0, r1, r2};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    uint16_t hi[8], lo[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        hi[q] = bf16_bits(rows[c][q]);
+                        lo[q] = bf16_bits(rows[c][q] - bf16_val(hi[q]));
+                    }
+                    *reinterpret_cast<uint4*>(Bhi + canon_off(3 * j + c, c0, L::kKa)) = pack8(hi);
+                    *reinterpret_cast<uint4*>(Blo + canon_off(3 * j + c, c0, L::kKa)) = pack8(lo);
+                }
+            }
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (tid == 0) {
+                const uint32_t bhi = b_base + (st * 2 + 0) * L::kBTile, blo = b_base + (st * 2 + 1) * L::kBTile;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t ahi = a_base + (h * 2 + 0) * L::kATile, alo = a_base + (h * 2 + 1) * L::kATile;
+                    const uint32_t d = tbase + (uint32_t)((st * 2 + h) * 3 * kTbE);
+                    // g_hi u_hi + g_lo u_hi + g_hi u_lo
+                    const uint32_t as_[3] = {ahi, alo, ahi};
+                    const uint32_t bs_[3] = {bhi, bhi, blo};
+#pragma unroll
+                    for (int t = 0; t < 3; ++t)
+#pragma unroll
+                        for (int q = 0; q < L::kKa / 16; ++q)
+                            mma_bf16(d, make_desc(as_[t] + q * 256, 128, L::kKa * 16),
+                                     make_desc(bs_[t] + q * 256, 128, L::kKa * 16), idesc,
+                                     (t > 0 || q > 0) ? 1u : 0u);
+                }
+                mma_commit(st == 0 ? bar0 : bar1);
+            }
+        }
+        if (i >= 1) {
+            // ---- consume batch i-1 on the CUDA cores
+            const int pi = i - 1, st = pi & 1;
+            const bool wok = st == 0 ? mbar_wait(bar0, ph0) : mbar_wait(bar1, ph1);
+            if (st == 0) ph0 ^= 1;
+            else ph1 ^= 1;
+            ok = __syncthreads_and(wok) != 0;
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t hi_pos = maxlast - (uint32_t)pi * kTbE;
+            const uint32_t lo_pos = hi_pos > (uint32_t)kTbE ? hi_pos - kTbE : 0u;
+            const int nb = (int)(hi_pos - lo_pos);
+            TbMeta md = tb_meta(sm + L::kMeta + st * L::kMetaStage);
+            float v[3 * kTbE];
+#pragma unroll
+            for (int c = 0; c < 3 * kTbE; c += 16) {
+                float t16[16];
+                tmem_ld16(tbase + (uint32_t)((st * 2 + half) * 3 * kTbE + c) + lane_base, t16);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) v[c + q] = t16[q];
+            }
+            const uint64_t mask = warp_entry_mask(md.geo, md.ext, nb, wcx, wcy, a.W);
+            if (lane == 0) s_wmask[warp] = mask;
+#pragma unroll
+            for (int j = kTbE - 1; j >= 0; --j) {
+                if (!((mask >> j) & 1ull)) continue;   // warp-uniform
+                float gr[9];
+#pragma unroll
+                for (int c = 0; c < 9; ++c) gr[c] = 0.f;
+                bool contrib = false;
+                const uint32_t pos = lo_pos + (uint32_t)j;
+                if (pos < last) {
+                    const float4 gg = md.geo[j];
+                    const float2 g2 = md.geo2[j];
+                    float dx, dy, G, alpha;
+                    bool clamped;
+                    if (eval_alpha(ux, uy, a.W, gg, g2, dx, dy, G, alpha, clamped)) {
+                        contrib = true;
+                        const float nl = lg2(__fsub_rn(1.0f, alpha));
+                        const float logT_before = __fsub_rn(logT, nl);
+                        const float T = ex2(logT_before);
+                        const float w = T * alpha;
+                        const float reG = v[3 * j], imG = v[3 * j + 1], imF = v[3 * j + 2];
+                        const float amp = md.amp[j];
+                        const float reGa = amp * reG;
+                        const float dalpha = T * reGa - suffix / (1.0f - alpha);
+                        suffix = fmaf(w, reGa, suffix);
+                        gr[6] = w * reG;
+                        gr[7] = -w * amp * imG;
+                        gr[8] = w * amp * (c_f0 * imG + c_df * imF);
+                        if (!clamped) {
+                            const float sig = g2.y;
+                            gr[5] = dalpha * G;
+                            const float dq = -0.5f * dalpha * sig * G;
+                            gr[0] = dq * (-2.0f * (gg.z * dx + gg.w * dy));
+                            gr[1] = dq * (-2.0f * (gg.w * dx + g2.x * dy));
+                            gr[2] = dq * dx * dx;
+                            gr[3] = dq * 2.0f * dx * dy;
+                            gr[4] = dq * dy * dy;
+                        }
+                        logT = logT_before;
+                    }
+                }
+                if (__any_sync(0xffffffffu, contrib)) {
+                    const float tot = warp_reduce_scatter9(gr, lane);
+                    if ((lane & 1) == 0 && (lane >> 1) < 9) s_red[warp][j][lane >> 1] = tot;
+                } else if (lane < 9) {
+                    s_red[warp][j][lane] = 0.f;
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+            for (int e = tid; e < nb * 9; e += kThreads) {
+                const int j = e / 9, c = e - j * 9;
+                float acc = 0.f;
+#pragma unroll
+                for (int w2 = 0; w2 < kThreads / 32; ++w2)
+                    if ((s_wmask[w2] >> j) & 1ull) acc += s_red[w2][j][c];
+                if (acc != 0.f) {
+                    const uint32_t gid = md.gid[j];
+                    if (c >= 5) {
+                        float* dst = reinterpret_cast<float*>(&a.d_attr[(size_t)b * a.N + gid]);
+                        const int slot = c == 5 ? 2 : (c == 6 ? 0 : (c == 7 ? 1 : 3));
+                        atomicAdd(dst + slot, acc);
+                    } else {
+                        const int slot = c < 2 ? c : c + 2;
+                        atomicAdd(a.d_proj + (size_t)gid * 8 + slot, acc);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // drain a batch whose MMAs were issued but not consumed (only after an expired wait)
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(L::kCols) : "memory");
+    }
+}
+
+template <int S>
+int launch_bwd_tc(const RenderArgs& a, int T, cudaStream_t s) {
+    using L = RTbSmem<S>;
+    if (!ensure_smem_attr(k_render_bwd_tc<S>, L::kTotal)) return GSPARC_ERR_CUDA;
+    dim3 grid((a.K + S - 1) / S, T, a.B);
+    k_render_bwd_tc<S><<<grid, kThreads, L::kTotal, s>>>(a);
+    return launch_status();
+}
+
+}  // namespace
+}  // namespace gsparc
+
+extern "C" int gsparc_render_bwd_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
+                                    const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
+                                    const float* attr, const float* final_logT, const uint32_t* n_contrib,
+                                    const float* d_spectrum, float* d_attr, float* d_proj, void* stream) {
+    using namespace gsparc;
+    if (!common_ok(view, band, B, N, proj, tile_ranges, sorted_ids, attr)) return GSPARC_ERR_INVALID;
+    if (!final_logT || !n_contrib || !d_spectrum || !d_attr || !d_proj) return GSPARC_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(d_spectrum) & 7) || (reinterpret_cast<uintptr_t>(d_attr) & 15))
+        return GSPARC_ERR_INVALID;
+    RenderArgs a{};
+    fill_args(view, band, B, N, proj, tile_ranges, sorted_ids, attr, a);
+    a.final_logT = const_cast<float*>(final_logT);
+    a.n_contrib = const_cast<uint32_t*>(n_contrib);
+    a.d_spectrum = reinterpret_cast<const float2*>(d_spectrum);
+    a.d_attr = reinterpret_cast<float4*>(d_attr);
+    a.d_proj = d_proj;
+    const int T = tiles_x(*view) * tiles_y(*view);
+    cudaStream_t s = as_stream(stream);
+    if (band->K <= 8) return launch_bwd_tc<8>(a, T, s);
+    if (band->K <= 16) return launch_bwd_tc<16>(a, T, s);
+    if (band->K <= 32) return launch_bwd_tc<32>(a, T, s);
+    return launch_bwd_tc<64>(a, T, s);
 }

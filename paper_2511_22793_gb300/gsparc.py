@@ -33,7 +33,7 @@ PROJ_STRIDE = 8
 EXPORTS = [
     "gsparc_num_tiles", "gsparc_project", "gsparc_project_bwd", "gsparc_bin_sort_workspace",
     "gsparc_bin_sort", "gsparc_bin_sort_noalloc", "gsparc_attr_mlp", "gsparc_attr_mlp_bwd", "gsparc_render_fwd",
-    "gsparc_render_fwd_tc", "gsparc_render_bwd", "gsparc_l2_loss", "gsparc_adam", "gsparc_check", "gsparc_strerror",
+    "gsparc_render_fwd_tc", "gsparc_render_bwd", "gsparc_render_bwd_tc", "gsparc_l2_loss", "gsparc_adam", "gsparc_check", "gsparc_strerror",
 ]
 
 
@@ -93,6 +93,8 @@ def lib():
                                                     vp, vp, vp]),
             "gsparc_render_bwd": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
                                                  vp, vp, vp, vp]),
+            "gsparc_render_bwd_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
+                                                    vp, vp, vp, vp]),
             "gsparc_l2_loss": (ctypes.c_int, [i64, vp, vp, vp, vp, vp]),
             "gsparc_adam": (ctypes.c_int, [i64, vp, vp, vp, vp, f32, f32, f32, f32, i32, vp]),
             "gsparc_check": (ctypes.c_int, [vp, vp]),
@@ -234,6 +236,13 @@ def gsparc_render_fwd_tc(view, band, B, n, proj, tile_ranges, sorted_ids, attr, 
 def gsparc_render_bwd(view, band, B, n, proj, tile_ranges, sorted_ids, attr, final_logT, n_contrib,
                       d_spectrum, d_attr, d_proj, stream=None):
     _call("gsparc_render_bwd", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
+          _p(tile_ranges), _p(sorted_ids), _p(attr), _p(final_logT), _p(n_contrib), _p(d_spectrum),
+          _p(d_attr), _p(d_proj), _stream(stream))
+
+
+def gsparc_render_bwd_tc(view, band, B, n, proj, tile_ranges, sorted_ids, attr, final_logT, n_contrib,
+                         d_spectrum, d_attr, d_proj, stream=None):
+    _call("gsparc_render_bwd_tc", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
           _p(tile_ranges), _p(sorted_ids), _p(attr), _p(final_logT), _p(n_contrib), _p(d_spectrum),
           _p(d_attr), _p(d_proj), _stream(stream))
 

@@ -128,10 +128,12 @@ class Renderer:
            logT, nc, n_used, stream)
         return spec, logT, nc
 
-    def render_backward(self, attr, logT, nc, d_spec, d_attr, d_proj, stream=None):
+    def render_backward(self, attr, logT, nc, d_spec, d_attr, d_proj, tensor_cores=False, stream=None):
+        """Compositing gradient; tensor_cores selects gsparc_render_bwd_tc (same outputs)."""
         B = int(attr.shape[0])
-        G.gsparc_render_bwd(self.view, self.band, B, self.n, self.proj, self.tile_ranges,
-                            self.sorted_ids, attr, logT, nc, d_spec, d_attr, d_proj, stream)
+        fn = G.gsparc_render_bwd_tc if tensor_cores else G.gsparc_render_bwd
+        fn(self.view, self.band, B, self.n, self.proj, self.tile_ranges, self.sorted_ids, attr, logT, nc,
+           d_spec, d_attr, d_proj, stream)
 
     def attributes_backward(self, scene, mlp, tx, d_attr, d_means, d_ologit, d_latent, d_weights,
                             stream=None):

@@ -127,7 +127,8 @@ class Trainer:
         self.d_proj.zero_()
         (spec, logT, nc), attr = self.forward(self.tx)
         G.gsparc_l2_loss(spec, target, self.loss, self.d_spec)
-        self.r.render_backward(attr, logT, nc, self.d_spec, self.d_attr, self.d_proj)
+        self.r.render_backward(attr, logT, nc, self.d_spec, self.d_attr, self.d_proj,
+                               tensor_cores=self.tensor_cores)
         g = self.grads
         self.r.attributes_backward(self.scene, self.mlp, self.tx, self.d_attr, g["means"],
                                    g["opacity_logit"], g["latent"], [g[k] for k in MLP_KEYS])

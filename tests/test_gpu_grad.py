@@ -110,3 +110,50 @@ def test_render_bwd_per_gaussian_inputs():
     for c, k in enumerate(("px", "py", "cxx", "cxy", "cyy", "sigma", "a", "phi0", "L")):
         e = rel_l2(got[k], ref[:, c])
         assert e <= 1e-3, "%s: relative L2 %.3e" % (k, e)
+
+
+@pytest.mark.parametrize("n,H,W,K,B,seed", [(3000, 90, 360, 64, 1, 31), (2000, 90, 360, 37, 2, 32),
+                                             (1500, 45, 180, 8, 2, 33), (3000, 180, 720, 100, 1, 34)])
+def test_render_bwd_tensor_cores_matches_fp32_kernel_and_oracle(n, H, W, K, B, seed):
+    """gsparc_render_bwd_tc against gsparc_render_bwd (same inputs, relative L2 <= 1e-4 per
+    component) and the oracle's analytic gradient of transmitter 0 (<= 1e-3)."""
+    sc = synth.make_scene(n, seed=seed)
+    mlp = synth.make_mlp(32, seed=3)
+    tx = synth.make_tx(B, seed=seed + 1)
+    view, band = synth.View(H=H, W=W), synth.Band(K=K)
+    g, attrs = oracle_geo_attr(sc, mlp, view, tx)
+    g32 = {k: (v.astype(np.float32).astype(np.float64) if v.dtype != bool else v) for k, v in g.items()}
+    at32 = [{k: v.astype(np.float32).astype(np.float64) for k, v in at.items()} for at in attrs]
+    proj = np.zeros((n, 8), np.float32)
+    proj[:, 0], proj[:, 1] = g32["px"], g32["py"]
+    proj[:, 2] = np.where(g["valid"], np.sqrt(2 * np.log(255) * g["sxx"]), -1)
+    proj[:, 3] = np.where(g["valid"], np.sqrt(2 * np.log(255) * g["syy"]), -1)
+    proj[:, 4], proj[:, 5], proj[:, 6], proj[:, 7] = g32["cxx"], g32["cxy"], g32["cyy"], g32["r"]
+    attr = np.stack([np.stack([at["a"], at["phi0"], at["sigma"], at["L"]], -1) for at in at32]).astype(np.float32)
+    r = Renderer(H, W, K, n, device=DEV)
+    r.proj.copy_(torch.tensor(proj, device=DEV))
+    G.gsparc_bin_sort(r.view, n, r.proj, r.capacity, r.ws, r.sorted_ids, None, r.tile_ranges, r.n_pairs,
+                      r.status)
+    attr_d = torch.tensor(attr, device=DEV)
+    spec, logT, nc = r.render(attr_d)
+    rng = np.random.default_rng(seed + 2)
+    gz = rng.normal(size=(B, H * W, K)) + 1j * rng.normal(size=(B, H * W, K))
+    d_spec = _to_dev_target(gz, B, H, W, K)
+    outs = []
+    for tc in (False, True):
+        d_attr = torch.zeros_like(attr_d)
+        d_proj = torch.zeros_like(r.proj)
+        r.render_backward(attr_d, logT, nc, d_spec, d_attr, d_proj, tensor_cores=tc)
+        torch.cuda.synchronize()
+        outs.append((d_attr.cpu().numpy().astype(np.float64), d_proj.cpu().numpy().astype(np.float64)))
+    (fa, fp), (ta, tp) = outs
+    for j in range(4):
+        assert rel_l2(ta[..., j], fa[..., j]) <= 1e-4, ("attr", j)
+    for j in (0, 1, 4, 5, 6):
+        assert rel_l2(tp[:, j], fp[:, j]) <= 1e-4, ("proj", j)
+    ref = orender.render_bwd(g32, at32[0], H, W, K, band.f_c, band.df, gz[0])
+    if B == 1:
+        got = {"px": tp[:, 0], "py": tp[:, 1], "cxx": tp[:, 4], "cxy": tp[:, 5], "cyy": tp[:, 6],
+               "sigma": ta[0, :, 2], "a": ta[0, :, 0], "phi0": ta[0, :, 1], "L": ta[0, :, 3]}
+        for c, k in enumerate(("px", "py", "cxx", "cxy", "cyy", "sigma", "a", "phi0", "L")):
+            assert rel_l2(got[k], ref[:, c]) <= 1e-3, k
