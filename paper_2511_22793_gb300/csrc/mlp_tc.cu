@@ -36,23 +36,11 @@ template <int TERMS>
 __device__ __forceinline__ void write_row(uint8_t* tile, int r, const float* x, int n, int Kb) {
     const int Kt = Kb * TERMS;
     for (int k0 = 0; k0 < Kb; k0 += 8) {
-        uint16_t hi[8], lo[8];
+        float v8[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int k = k0 + q;
-            const float v = k < n ? x[k] : 0.f;
-            hi[q] = bf16_bits(v);
-            lo[q] = bf16_bits(v - bf16_val(hi[q]));
-        }
+        for (int q = 0; q < 8; ++q) v8[q] = (k0 + q) < n ? x[k0 + q] : 0.f;
         uint4 H, Lo;
-        H.x = hi[0] | ((uint32_t)hi[1] << 16);
-        H.y = hi[2] | ((uint32_t)hi[3] << 16);
-        H.z = hi[4] | ((uint32_t)hi[5] << 16);
-        H.w = hi[6] | ((uint32_t)hi[7] << 16);
-        Lo.x = lo[0] | ((uint32_t)lo[1] << 16);
-        Lo.y = lo[2] | ((uint32_t)lo[3] << 16);
-        Lo.z = lo[4] | ((uint32_t)lo[5] << 16);
-        Lo.w = lo[6] | ((uint32_t)lo[7] << 16);
+        split8(v8, H, Lo);
         *reinterpret_cast<uint4*>(tile + canon_off(r, k0, Kt)) = H;
         if (TERMS == 3) {
             *reinterpret_cast<uint4*>(tile + canon_off(r, Kb + k0, Kt)) = Lo;
@@ -69,12 +57,12 @@ __device__ __forceinline__ void write_weights(uint8_t* tile, const float* __rest
     for (int e = threadIdx.x; e < N * Kb; e += blockDim.x) {
         const int n = e / Kb, k = e - n * Kb;
         const float v = k < kin ? W[k * N + n] : 0.f;
-        const uint16_t hi = bf16_bits(v);
-        const uint16_t lo = bf16_bits(v - bf16_val(hi));
-        *reinterpret_cast<uint16_t*>(tile + canon_off(n, k, Kt)) = hi;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+        *reinterpret_cast<__nv_bfloat16*>(tile + canon_off(n, k, Kt)) = hi;
         if (TERMS == 3) {
-            *reinterpret_cast<uint16_t*>(tile + canon_off(n, Kb + k, Kt)) = hi;
-            *reinterpret_cast<uint16_t*>(tile + canon_off(n, 2 * Kb + k, Kt)) = lo;
+            *reinterpret_cast<__nv_bfloat16*>(tile + canon_off(n, Kb + k, Kt)) = hi;
+            *reinterpret_cast<__nv_bfloat16*>(tile + canon_off(n, 2 * Kb + k, Kt)) = lo;
         }
     }
 }

@@ -560,25 +560,17 @@ struct RTcSmem {
     static constexpr int kA = 0;                              // [stage][half] 128 x Kt bf16
     static constexpr int kBStage = kN * kTcKt * 2;
     static constexpr int kB = kA + 4 * kAHalf;                // [stage] 2S x Kt bf16
-    static constexpr int kGeo = kB + 2 * kBStage;             // float4[E]
-    static constexpr int kGeo2 = kGeo + kTcE * 16;            // float2[E]
-    static constexpr int kExt = kGeo2 + kTcE * 8;             // float2[E]
-    static constexpr int kAmp = kExt + kTcE * 8;              // float[E]
-    static constexpr int kPhi = kAmp + kTcE * 4;
-    static constexpr int kLen = kPhi + kTcE * 4;
-    static constexpr int kBar = kLen + kTcE * 4;              // 2 mbarriers + TMEM slot
+    // per-entry records, double-buffered: batch i+1 is gathered while batch i computes
+    static constexpr int kGeo = kB + 2 * kBStage;             // float4[2][E]
+    static constexpr int kGeo2 = kGeo + 2 * kTcE * 16;        // float2[2][E]
+    static constexpr int kExt = kGeo2 + 2 * kTcE * 8;         // float2[2][E]
+    static constexpr int kAmp = kExt + 2 * kTcE * 8;          // float[2][E]
+    static constexpr int kPhi = kAmp + 2 * kTcE * 4;
+    static constexpr int kLen = kPhi + 2 * kTcE * 4;
+    static constexpr int kBar = kLen + 2 * kTcE * 4;          // 2 mbarriers + TMEM slot
     static constexpr int kTotal = kBar + 32;
     static constexpr uint32_t kCols = (4 * S <= 32) ? 32 : (4 * S <= 64 ? 64 : (4 * S <= 128 ? 128 : 256));
 };
-
-__device__ __forceinline__ uint4 pack8(const uint16_t (&h)[8]) {
-    uint4 u;
-    u.x = h[0] | ((uint32_t)h[1] << 16);
-    u.y = h[2] | ((uint32_t)h[3] << 16);
-    u.z = h[4] | ((uint32_t)h[5] << 16);
-    u.w = h[6] | ((uint32_t)h[7] << 16);
-    return u;
-}
 
 template <int S>
 __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
@@ -597,6 +589,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
     const int k0 = strip * S;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int half = tid >> 7, m = tid & 127;
+    // gather of one batch's per-entry records into registers (threads tid < E), and its
+    // publication into one of the two record buffers
+    uint32_t pf_gid = 0xffffffffu;
+    float4 pf_p0 = make_float4(0.f, 0.f, 0.f, 0.f), pf_p1 = pf_p0, pf_at = pf_p0;
+    auto gather = [&](uint32_t pos, uint32_t end) {
+        if (tid < kTcE) {
+            pf_gid = pos + tid < end ? a.ids[pos + tid] : 0xffffffffu;
+            if (pf_gid < (uint32_t)a.N) {
+                pf_p0 = a.proj[2 * pf_gid];
+                pf_p1 = a.proj[2 * pf_gid + 1];
+                pf_at = a.attr[(size_t)b * a.N + pf_gid];
+            }
+        }
+    };
+    auto publish = [&](int mb) {
+        if (tid < kTcE) {
+            const int e = mb * kTcE + tid;
+            if (pf_gid < (uint32_t)a.N) {
+                s_geo[e] = make_float4(pf_p0.x, pf_p0.y, pf_p1.x, pf_p1.y);
+                s_geo2[e] = make_float2(pf_p1.z, pf_at.z);
+                s_ext[e] = make_float2(pf_p0.z, pf_p0.w);
+                s_amp[e] = pf_at.x;
+                s_phi[e] = pf_at.y;
+                s_len[e] = pf_at.w;
+            } else {
+                s_geo[e] = make_float4(0.f, 0.f, __int_as_float(0x7fc00000), 0.f);
+                s_geo2[e] = make_float2(0.f, 0.f);
+                s_ext[e] = make_float2(-1.f, -1.f);
+                s_amp[e] = 0.f;
+                s_phi[e] = 0.f;
+                s_len[e] = 0.f;
+            }
+        }
+    };
     const int tx0 = (tile % a.TW) * kTile, ty0 = (tile / a.TW) * kTile;
     const int x = tx0 + (tid & 15), y = ty0 + (tid >> 4);
     const bool inside = x < a.W && y < a.H;
@@ -630,60 +656,56 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
     uint32_t ph0 = 0, ph1 = 0;
     bool pend0 = false, pend1 = false, any_mma = false, ok = true;
     int it = 0;
+    gather(range.x, range.y);
+    publish(0);
+    volatile uint32_t* s_ok = reinterpret_cast<volatile uint32_t*>(sm + L::kBar + 20);
+    if (tid == 0) *s_ok = 1u;
     for (uint32_t bs = range.x; bs < range.y; bs += kTcE, ++it) {
-        if (__syncthreads_or(!done) == 0) break;
         const int st = it & 1;
-        // the stage's buffers are free once the MMAs issued two batches ago completed
-        bool wok = true;
-        if (st == 0 && pend0) { wok = mbar_wait(bar0, ph0); ph0 ^= 1; pend0 = false; }
-        if (st == 1 && pend1) { wok = mbar_wait(bar1, ph1); ph1 ^= 1; pend1 = false; }
-        ok = __syncthreads_and(wok && ok) != 0;
-        if (!ok) break;
-        tc_fence_after();
-        const int nb = (int)min((uint32_t)kTcE, range.y - bs);
-        if (tid < kTcE) {
-            uint32_t gid = tid < nb ? a.ids[bs + tid] : 0xffffffffu;
-            if (gid < (uint32_t)a.N) {
-                const float4 p0 = a.proj[2 * gid];
-                const float4 p1 = a.proj[2 * gid + 1];
-                const float4 at = a.attr[(size_t)b * a.N + gid];
-                s_geo[tid] = make_float4(p0.x, p0.y, p1.x, p1.y);
-                s_geo2[tid] = make_float2(p1.z, at.z);
-                s_ext[tid] = make_float2(p0.z, p0.w);
-                s_amp[tid] = at.x;
-                s_phi[tid] = at.y;
-                s_len[tid] = at.w;
-            } else {
-                s_geo[tid] = make_float4(0.f, 0.f, __int_as_float(0x7fc00000), 0.f);
-                s_geo2[tid] = make_float2(0.f, 0.f);
-                s_ext[tid] = make_float2(-1.f, -1.f);
-                s_amp[tid] = 0.f;
-                s_phi[tid] = 0.f;
-                s_len[tid] = 0.f;
-            }
+        // thread 0 waits until the MMAs issued two batches ago (same stage) completed; the one
+        // barrier below then both releases the stage and tells whether any pixel is still live
+        if (tid == 0) {
+            bool wok = true;
+            if (st == 0 && pend0) wok = mbar_wait(bar0, ph0);
+            if (st == 1 && pend1) wok = mbar_wait(bar1, ph1);
+            if (!wok) *s_ok = 0u;
         }
-        __syncthreads();
+        // every thread tracks the phases the same way (the final drain waits in all threads)
+        if (st == 0 && pend0) { ph0 ^= 1; pend0 = false; }
+        if (st == 1 && pend1) { ph1 ^= 1; pend1 = false; }
+        const int live = __syncthreads_or(!done);
+        ok = *s_ok != 0u;
+        if (!ok || live == 0) break;
+        tc_fence_after();
+        const int mb = it & 1;   // record buffer of this batch
+        gather(bs + kTcE, range.y);   // next batch's records, consumed after this batch's work
+        const float4* geo = s_geo + mb * kTcE;
+        const float2* geo2 = s_geo2 + mb * kTcE;
+        const float2* ext = s_ext + mb * kTcE;
+        const float* amp = s_amp + mb * kTcE;
+        const float* phi = s_phi + mb * kTcE;
+        const float* len = s_len + mb * kTcE;
+        const int nb = (int)min((uint32_t)kTcE, range.y - bs);
         // ---- B: amplitude-scaled phasors of the strip, [hi | hi | lo] along K
         uint8_t* Bst = sm + L::kB + st * L::kBStage;
         for (int e = tid; e < S * (kTcE / 8); e += kThreads) {
             const int kk = e % S, j0 = (e / S) * 8;
             const int k = k0 + kk;
-            uint16_t rh[8], rl[8], ih[8], il[8];
+            float re[8], im[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int j = j0 + q;
-                float re = 0.f, im = 0.f;
+                re[q] = 0.f;
+                im[q] = 0.f;
                 if (j < nb && k < a.K) {
-                    const float2 ph = unit_phasor(a, s_len[j], s_phi[j], k);
-                    re = s_amp[j] * ph.x;
-                    im = s_amp[j] * ph.y;
+                    const float2 ph = unit_phasor(a, len[j], phi[j], k);
+                    re[q] = amp[j] * ph.x;
+                    im[q] = amp[j] * ph.y;
                 }
-                rh[q] = bf16_bits(re);
-                rl[q] = bf16_bits(re - bf16_val(rh[q]));
-                ih[q] = bf16_bits(im);
-                il[q] = bf16_bits(im - bf16_val(ih[q]));
             }
-            const uint4 RH = pack8(rh), RL = pack8(rl), IH = pack8(ih), IL = pack8(il);
+            uint4 RH, RL, IH, IL;
+            split8(re, RH, RL);
+            split8(im, IH, IL);
             const int nre = 2 * kk, nim = 2 * kk + 1;
             *reinterpret_cast<uint4*>(Bst + canon_off(nre, j0, kTcKt)) = RH;
             *reinterpret_cast<uint4*>(Bst + canon_off(nre, kTcE + j0, kTcKt)) = RH;
@@ -696,7 +718,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
         float wv[kTcE];
 #pragma unroll
         for (int j = 0; j < kTcE; ++j) wv[j] = 0.f;
-        const uint64_t mask = warp_entry_mask(s_geo, s_ext, nb, wcx, wcy, a.W);
+        const uint64_t mask = warp_entry_mask(geo, ext, nb, wcx, wcy, a.W);
         if (!done) {
             // phase 1: alpha and log2(1 - alpha) of every entry, independent of each other
             float al[kTcE], nlv[kTcE];
@@ -707,7 +729,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
                 if ((mask >> j) & 1ull) {   // warp-uniform
                     float dx, dy, G, alpha;
                     bool clamped;
-                    if (eval_alpha(ux, uy, a.W, s_geo[j], s_geo2[j], dx, dy, G, alpha, clamped)) {
+                    if (eval_alpha(ux, uy, a.W, geo[j], geo2[j], dx, dy, G, alpha, clamped)) {
                         al[j] = alpha;
                         nlv[j] = lg2(__fsub_rn(1.0f, alpha));
                     }
@@ -731,17 +753,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
         uint8_t* Ast = sm + L::kA + (st * 2 + half) * L::kAHalf;
 #pragma unroll
         for (int j0 = 0; j0 < kTcE; j0 += 8) {
-            uint16_t hi[8], lo[8];
+            float w8[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                hi[q] = bf16_bits(wv[j0 + q]);
-                lo[q] = bf16_bits(wv[j0 + q] - bf16_val(hi[q]));
-            }
-            const uint4 H = pack8(hi), Lo = pack8(lo);
+            for (int q = 0; q < 8; ++q) w8[q] = wv[j0 + q];
+            uint4 H, Lo;
+            split8(w8, H, Lo);
             *reinterpret_cast<uint4*>(Ast + canon_off(m, j0, kTcKt)) = H;
             *reinterpret_cast<uint4*>(Ast + canon_off(m, kTcE + j0, kTcKt)) = Lo;
             *reinterpret_cast<uint4*>(Ast + canon_off(m, 2 * kTcE + j0, kTcKt)) = H;
         }
+        publish(mb ^ 1);   // the other buffer was last read by the previous batch
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -938,19 +959,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_bwd_tc(RenderArgs a) {
         uint8_t* Alo = sm + L::kA + (half * 2 + 1) * L::kATile;
 #pragma unroll 1
         for (int c0 = 0; c0 < 2 * S; c0 += 8) {
-            uint16_t hi[8], lo[8];
+            float g8[8];
 #pragma unroll
             for (int q = 0; q < 8; q += 2) {
                 const int k = k0 + (c0 + q) / 2;
                 float2 g = make_float2(0.f, 0.f);
                 if (inside && k < a.K) g = a.d_spectrum[((size_t)b * a.K + k) * plane + pix];
-                hi[q] = bf16_bits(g.x);
-                lo[q] = bf16_bits(g.x - bf16_val(hi[q]));
-                hi[q + 1] = bf16_bits(g.y);
-                lo[q + 1] = bf16_bits(g.y - bf16_val(hi[q + 1]));
+                g8[q] = g.x;
+                g8[q + 1] = g.y;
             }
-            *reinterpret_cast<uint4*>(Ahi + canon_off(m, c0, L::kKa)) = pack8(hi);
-            *reinterpret_cast<uint4*>(Alo + canon_off(m, c0, L::kKa)) = pack8(lo);
+            uint4 H, Lo;
+            split8(g8, H, Lo);
+            *reinterpret_cast<uint4*>(Ahi + canon_off(m, c0, L::kKa)) = H;
+            *reinterpret_cast<uint4*>(Alo + canon_off(m, c0, L::kKa)) = Lo;
         }
     }
     float logT = inside ? a.final_logT[(size_t)b * plane + pix] : 0.f;
@@ -1022,18 +1043,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_bwd_tc(RenderArgs a) {
                     r2[q] = (float)kk * u.y;
                     r2[q + 1] = -(float)kk * u.x;
                 }
-                const float* rows[3] = {r0, r1, r2};
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    uint16_t hi[8], lo[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        hi[q] = bf16_bits(rows[c][q]);
-                        lo[q] = bf16_bits(rows[c][q] - bf16_val(hi[q]));
-                    }
-                    *reinterpret_cast<uint4*>(Bhi + canon_off(3 * j + c, c0, L::kKa)) = pack8(hi);
-                    *reinterpret_cast<uint4*>(Blo + canon_off(3 * j + c, c0, L::kKa)) = pack8(lo);
-                }
+                uint4 H, Lo;
+                split8(r0, H, Lo);
+                *reinterpret_cast<uint4*>(Bhi + canon_off(3 * j + 0, c0, L::kKa)) = H;
+                *reinterpret_cast<uint4*>(Blo + canon_off(3 * j + 0, c0, L::kKa)) = Lo;
+                split8(r1, H, Lo);
+                *reinterpret_cast<uint4*>(Bhi + canon_off(3 * j + 1, c0, L::kKa)) = H;
+                *reinterpret_cast<uint4*>(Blo + canon_off(3 * j + 1, c0, L::kKa)) = Lo;
+                split8(r2, H, Lo);
+                *reinterpret_cast<uint4*>(Bhi + canon_off(3 * j + 2, c0, L::kKa)) = H;
+                *reinterpret_cast<uint4*>(Blo + canon_off(3 * j + 2, c0, L::kKa)) = Lo;
             }
             fence_async_smem();
             tc_fence_before();
