@@ -202,14 +202,9 @@ def run_ours(args, rank, world, local_rank):
                                                           scene.quats, d_proj, grads[0], grads[1],
                                                           grads[2]))
 
-    # kernels of ours launched per step: project 1, bin/sort 6 + passes, network 1, render 1,
-    # loss 1, render bwd 1, network bwd 1, projection bwd 1
-    T = r.T
-    bits = 0
-    while (1 << bits) < T:
-        bits += 1
-    passes = 4 + (bits + 7) // 8
-    launches_per_step = 1 + (6 + passes) + 1 + 1 + 1 + 1 + 1 + 1
+    # kernels of ours launched per step: project 1, bin/sort 3 (count + scan, emit, per-tile
+    # sort), network 1, render 1, loss 1, render bwd 1, network bwd 1, projection bwd 1
+    launches_per_step = 1 + 3 + 1 + 1 + 1 + 1 + 1 + 1
 
     for _ in range(args.warmup):
         step(ds, target)

@@ -136,20 +136,22 @@ int gsparc_bin_sort_workspace(const gsparc_view* view, int32_t N, int64_t pair_c
  * Tile binning and directional sorting (Algorithm 1 IntersectGaussians and
  * "sort by depth to receiver"; Sec. 1 "directional sorting").  For every
  * Gaussian, the 16x16 tiles its footprint box touches (azimuth wrapping at
- * +-pi) each get one pair with the 64-bit key (tile_id << 32) | bits(r); the
- * pairs, emitted in Gaussian-index order, are sorted stably by key with an
- * LSD radix sort (8-bit digits, one-sweep passes with decoupled look-back),
- * so every tile's list is ordered by (r, index).
+ * +-pi) each get one (Gaussian, tile) pair; every tile's list is ordered by
+ * (r, index).  The pairs are counted per tile, emitted into per-tile buckets as
+ * the unique 64-bit keys (bits(r) << 32) | index, and each bucket is radix
+ * sorted by its own thread block (8-bit digits, only the bytes that vary in
+ * the bucket), in shared memory up to 12288 pairs and in the workspace above.
  *   proj [N,8]: records from gsparc_project (only p, ext and r are read).
  *   ws: device workspace of ws_bytes >= gsparc_bin_sort_workspace().
  *   sorted_ids [pair_capacity] out: Gaussian id of each sorted pair.
- *   sorted_keys [pair_capacity] out, may be NULL: the sorted keys.
+ *   sorted_keys [pair_capacity] out, may be NULL: (tile_id << 32) | bits(r)
+ *   of each sorted pair.
  *   tile_ranges [num_tiles, 2] out: [start, end) of each tile in sorted_ids
- *   (start == end for an empty tile).
+ *   ([0, 0) for an empty tile).
  *   n_pairs [1] out (device): number of pairs.
  *   d_status [1] (device): set to GSPARC_ERR_CAPACITY if the pairs exceed
- *   pair_capacity (only the first pair_capacity are then sorted) and to
- *   GSPARC_ERR_TIMEOUT if a look-back wait expired.
+ *   pair_capacity; the tiles whose lists end at or below pair_capacity (in
+ *   tile order) are then complete and sorted, every later tile is [0, 0).
  * Pair capacity must be below 2^31.
  */
 int gsparc_bin_sort(const gsparc_view* view, int32_t N, const float* proj, int64_t pair_capacity,
@@ -163,10 +165,10 @@ int gsparc_bin_sort(const gsparc_view* view, int32_t N, const float* proj, int64
  * may not call cudaMalloc at all: a real-time loop that must not take the
  * implicit device-wide synchronisation and unbounded latency of an allocation
  * after start-up, or a plugin whose host hands it buffers but no allocator.
- * They still pass every input and output; the scratch space (counts, the
- * ping-pong key/value buffers, histograms, look-back flags) is a fixed
- * 15 MiB array in the library's own device memory, which every GPU that
- * loads the library holds until the process exits.
+ * They still pass every input and output; the scratch space (tile counters,
+ * bucket cursors, the two key buffers) is a fixed 9 MiB array in the
+ * library's own device memory, which every GPU that loads the library holds
+ * until the process exits.
  *   Limits: N <= GSPARC_NOALLOC_MAX_N and pair_capacity <=
  *   GSPARC_NOALLOC_MAX_PAIRS; larger sizes return GSPARC_ERR_TOO_LARGE before
  *   anything is enqueued.  Other arguments and errors as gsparc_bin_sort.

@@ -3,21 +3,23 @@
 // Algorithm 1: IntersectGaussians per pixel, then "sort by depth to receiver";
 // Sec. 1 names the fully parallel directional sort.  Tiled form: each
 // Gaussian's footprint box (azimuth wrapping at +-pi) gives one (Gaussian,
-// tile) pair per touched 16x16 tile with key (tile_id << 32) | bits(r); the
-// pairs, emitted in Gaussian-index order, are sorted stably by key, so every
-// tile's list comes out ordered by (r, index).
+// tile) pair per touched 16x16 tile, and every tile's list is ordered by
+// (r, index).
 //
-// Kernels (all on the caller's stream, no host synchronisation):
-//   k_count        tiles per Gaussian + block-local exclusive scan
-//   k_scan_blocks  scan of block totals, pair count, capacity check
-//   k_emit         keys / values in Gaussian-index order
-//   k_hist         digit histograms of every pass in one read of the keys,
-//                  and zeroing of the look-back flags
-//   k_hist_scan    exclusive scan of each pass's 256 bins
-//   k_onesweep     one LSD pass over 8 bits: stable in-tile ranking with
-//                  warp match, decoupled look-back across tiles (bounded
-//                  spins, GSPARC_ERR_TIMEOUT on expiry), scatter
-//   k_ranges       [start, end) of each tile from adjacent keys
+// The pairs go straight into per-tile buckets and each bucket is sorted on its
+// own, so no pass ever runs over the whole pair array:
+//   k_tile_count  pairs per tile (block-aggregated atomics); the last block to
+//                 finish scans the counts into bucket offsets, tile ranges and
+//                 the pair count, and checks the capacity
+//   k_tile_emit   every pair, as the 64-bit sort key (bits(r) << 32) | index,
+//                 into its tile's bucket (block-aggregated cursor atomics, so
+//                 the order inside a bucket is arbitrary)
+//   k_tile_sort   one CTA per tile: LSD radix sort of the bucket's keys (8-bit
+//                 digits, warp-match ranking, only the bytes that vary in the
+//                 bucket) in shared memory, or in a global ping-pong buffer for
+//                 a bucket above kSortCap keys; writes the ids (and keys)
+// The keys are unique (the index is part of the key), so any arrangement of a
+// bucket sorts to the same list: the (r, index) order, bit for bit.
 
 #include <algorithm>
 #include <cstdio>
@@ -28,30 +30,18 @@
 namespace gsparc {
 namespace {
 
-constexpr int kScanThreads = 256;
-constexpr int kOsThreads = 256;
-constexpr int kOsWarps = kOsThreads / 32;
-constexpr int kOsKpt = 8;                           // keys per thread
-constexpr int kOsTile = kOsThreads * kOsKpt;        // 2048 keys per sort tile
-constexpr uint32_t kFlagAgg = 1u << 30;
-constexpr uint32_t kFlagInc = 2u << 30;
-constexpr uint32_t kValMask = (1u << 30) - 1;
-constexpr int kSpinLimit = 1 << 20;
-constexpr int kLookWin = 8;                         // predecessors read per look-back round trip
-constexpr int kMaxPasses = 7;
+constexpr int kBinThreads = 256;
+constexpr int kSmemTiles = 4096;                    // tile counters kept in shared memory up to this T
+constexpr int kSortThreads = 512;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortCap = 24576;                     // keys per bucket sorted in shared memory
+constexpr int kSubBuckets = 4096;                   // sub-buckets of the in-tile distribution sort
+constexpr int kSubMax = 64;                         // largest sub-bucket ranked by comparison
+static_assert(kSortThreads >= 256, "the digit scan gives one thread per digit");
+static_assert(kSortWarps * 256 == kSubBuckets, "histogram array shared by both in-tile sorts");
 
 __device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
     if (status) atomicCAS(reinterpret_cast<int*>(status), 0, code);
-}
-
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
-    uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // Column / row tile ranges touched by one projection record.  Every float
@@ -102,320 +92,452 @@ __device__ __forceinline__ bool footprint(const float4 p, int H, int W, int TW, 
     return true;
 }
 
-__device__ __forceinline__ uint32_t foot_count(const Foot& f) {
-    const int cols = (f.a1 - f.a0 + 1) + (f.b1 >= f.b0 ? f.b1 - f.b0 + 1 : 0);
-    return (uint32_t)((f.ty1 - f.ty0 + 1) * cols);
-}
-
-// Block-wide exclusive scan of one value per thread (blockDim.x == 256).
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp, uint32_t& total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = v;
+// Every (Gaussian, tile) pair of the 32 lanes' Gaussians, spread evenly over the lanes
+// (a wide footprint would otherwise keep one lane looping while the others idle).  Pair
+// k of the warp belongs to the lane whose exclusive..inclusive pair prefix holds k,
+// found by a binary search over the lanes' prefixes; fn(tile, owner, active) runs on
+// every lane in rounds of 32 pairs (active false past the warp's last pair).
+template <class F>
+__device__ __forceinline__ void warp_pairs(bool valid, const Foot& f, int TW, F&& fn) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int wa = valid ? f.a1 - f.a0 + 1 : 0;
+    const int cols = valid ? wa + (f.b1 >= f.b0 ? f.b1 - f.b0 + 1 : 0) : 0;
+    const int c = valid ? (f.ty1 - f.ty0 + 1) * cols : 0;
+    int incl = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+        const int y = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += y;
     }
-    if (lane == 31) s_warp[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = lane < (kScanThreads / 32) ? s_warp[lane] : 0;
+    const int total = __shfl_sync(full, incl, 31);
+    const int excl = incl - c;
+    for (int base = 0; base < total; base += 32) {
+        const int k = base + lane;
+        int owner = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
+        for (int st = 16; st > 0; st >>= 1) {
+            const int v = __shfl_sync(full, incl, owner + st - 1);
+            if (v <= k) owner += st;
         }
-        if (lane < (kScanThreads / 32)) s_warp[lane] = w;
+        const int q = k - __shfl_sync(full, excl, owner);
+        const int ocols = __shfl_sync(full, cols, owner);
+        const int owa = __shfl_sync(full, wa, owner);
+        const int oty0 = __shfl_sync(full, valid ? f.ty0 : 0, owner);
+        const int oa0 = __shfl_sync(full, valid ? f.a0 : 0, owner);
+        const int ob0 = __shfl_sync(full, valid ? f.b0 : 0, owner);
+        const bool active = k < total;
+        int tile = 0;
+        if (active) {
+            const int row = q / ocols, cc = q - row * ocols;
+            const int tx = cc < owa ? oa0 + cc : ob0 + (cc - owa);
+            tile = (oty0 + row) * TW + tx;
+        }
+        fn(tile, owner, active);
     }
-    __syncthreads();
-    total = s_warp[kScanThreads / 32 - 1];
-    const uint32_t before = warp > 0 ? s_warp[warp - 1] : 0;
-    return before + x - v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_count(int N, int H, int W, int TW,
-                                                        const float4* __restrict__ proj,
-                                                        uint32_t* __restrict__ local,
-                                                        uint32_t* __restrict__ blk) {
-    __shared__ uint32_t s_warp[kScanThreads / 32];
-    const int i = blockIdx.x * kScanThreads + threadIdx.x;
-    uint32_t c = 0;
-    if (i < N) {
-        Foot f;
-        if (footprint(proj[2 * i], H, W, TW, f)) c = foot_count(f);
-    }
-    uint32_t total;
-    const uint32_t ex = block_exclusive_scan(c, s_warp, total);
-    if (i < N) local[i] = ex;
-    if (threadIdx.x == 0) blk[blockIdx.x] = total;
-}
-
-// One block of 1024 threads scans the block totals (in place, exclusive).
-__global__ void __launch_bounds__(1024) k_scan_blocks(int nblk, uint32_t* __restrict__ blk,
-                                                      uint32_t* __restrict__ n_pairs,
-                                                      uint32_t* __restrict__ n_sort, uint32_t cap,
-                                                      int32_t* status) {
-    __shared__ uint32_t s_warp[32];
+// Pairs per tile.  The last block to finish turns the counts into bucket offsets:
+// cursor[t] = start of tile t, tile_ranges[t] = [start, end) ([0, 0) when the bucket is
+// empty or does not fit below cap), n_pairs = total (saturated at 2^32-1), GSPARC_ERR_CAPACITY if the
+// total exceeds cap.
+__global__ void __launch_bounds__(kBinThreads) k_tile_count(int N, int H, int W, int TW, int T,
+                                                            const float4* __restrict__ proj,
+                                                            uint32_t* __restrict__ cnt,
+                                                            uint32_t* __restrict__ cursor,
+                                                            uint32_t* __restrict__ done, uint32_t cap,
+                                                            uint2* __restrict__ ranges,
+                                                            uint32_t* __restrict__ n_pairs,
+                                                            int32_t* status) {
+    __shared__ uint32_t s_cnt[kSmemTiles];
+    __shared__ uint32_t s_warp[kBinThreads / 32];
     __shared__ uint64_t s_carry;
+    __shared__ bool s_last;
+    const bool local = T <= kSmemTiles;
+    if (local) {
+        for (int t = threadIdx.x; t < T; t += kBinThreads) s_cnt[t] = 0;
+        __syncthreads();
+    }
+    const int i = blockIdx.x * kBinThreads + threadIdx.x;
+    Foot f;
+    const bool valid = i < N && footprint(proj[2 * i], H, W, TW, f);
+    warp_pairs(valid, f, TW, [&](int t, int, bool active) {
+        if (active) atomicAdd(local ? &s_cnt[t] : &cnt[t], 1u);
+    });
+    if (local) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < T; t += kBinThreads)
+            if (s_cnt[t]) atomicAdd(&cnt[t], s_cnt[t]);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
     if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int base = 0; base < nblk; base += 1024) {
-        const int i = base + threadIdx.x;
-        const uint32_t v = i < nblk ? blk[i] : 0;
+    for (int base = 0; base < T; base += kBinThreads) {
+        const int t = base + threadIdx.x;
+        const uint32_t v = t < T ? __ldcg(&cnt[t]) : 0u;
         uint32_t x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
         if (lane == 31) s_warp[warp] = x;
         __syncthreads();
-        if (warp == 0) {
-            uint32_t w = s_warp[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += y;
-            }
-            s_warp[lane] = w;
+        uint64_t before = s_carry;
+        for (int w = 0; w < warp; ++w) before += s_warp[w];
+        const uint64_t start = before + x - v, end = start + v;
+        if (t < T) {
+            const bool fits = v > 0 && end <= cap;
+            const uint32_t s0 = (uint32_t)(start < cap ? start : cap);
+            ranges[t] = fits ? make_uint2((uint32_t)start, (uint32_t)end) : make_uint2(0u, 0u);
+            cursor[t] = s0;
         }
         __syncthreads();
-        const uint64_t carry = s_carry;
-        const uint32_t before = warp > 0 ? s_warp[warp - 1] : 0;
-        const uint64_t ex = carry + before + x - v;
-        if (i < nblk) blk[i] = (uint32_t)(ex > 0xffffffffull ? 0xffffffffull : ex);
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry = carry + s_warp[31];
+        if (threadIdx.x == kBinThreads - 1) s_carry = end;
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         const uint64_t tot = s_carry;
         n_pairs[0] = (uint32_t)(tot > 0xffffffffull ? 0xffffffffull : tot);
         if (tot > cap) set_status(status, GSPARC_ERR_CAPACITY);
-        n_sort[0] = (uint32_t)(tot > cap ? cap : tot);
     }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_emit(int N, int H, int W, int TW,
-                                                       const float4* __restrict__ proj,
-                                                       const uint32_t* __restrict__ local,
-                                                       const uint32_t* __restrict__ blk, uint32_t cap,
-                                                       uint64_t* __restrict__ keys,
-                                                       uint32_t* __restrict__ vals) {
-    const int i = blockIdx.x * kScanThreads + threadIdx.x;
-    if (i >= N) return;
+// Every pair's key (bits(r) << 32) | index into its tile's bucket.  A block reserves one
+// run of each bucket with a single atomic per touched tile and fills it through shared
+// counters.  Positions at or above cap are dropped (their tiles have empty ranges).
+__global__ void __launch_bounds__(kBinThreads) k_tile_emit(int N, int H, int W, int TW, int T,
+                                                           const float4* __restrict__ proj,
+                                                           uint32_t* __restrict__ cursor, uint32_t cap,
+                                                           uint64_t* __restrict__ keys) {
+    __shared__ uint32_t s_cnt[kSmemTiles];
+    __shared__ uint32_t s_base[kSmemTiles];
+    const bool local = T <= kSmemTiles;
+    const int i = blockIdx.x * kBinThreads + threadIdx.x;
     Foot f;
-    if (!footprint(proj[2 * i], H, W, TW, f)) return;
-    const uint32_t rbits = __float_as_uint(proj[2 * i + 1].w);
-    uint64_t pos = (uint64_t)blk[blockIdx.x] + local[i];
-    for (int ty = f.ty0; ty <= f.ty1; ++ty) {
-        for (int tx = f.a0; tx <= f.a1; ++tx, ++pos) {
-            if (pos < cap) {
-                keys[pos] = ((uint64_t)(ty * TW + tx) << 32) | rbits;
-                vals[pos] = (uint32_t)i;
+    const bool valid = i < N && footprint(proj[2 * i], H, W, TW, f);
+    const uint64_t key = valid ? ((uint64_t)__float_as_uint(proj[2 * i + 1].w) << 32) | (uint32_t)i : 0;
+    if (!local) {
+        warp_pairs(valid, f, TW, [&](int t, int owner, bool active) {
+            const uint64_t k = __shfl_sync(0xffffffffu, key, owner);
+            if (active) {
+                const uint32_t pos = atomicAdd(&cursor[t], 1u);
+                if (pos < cap) keys[pos] = k;
             }
-        }
-        for (int tx = f.b0; tx <= f.b1; ++tx, ++pos) {
-            if (pos < cap) {
-                keys[pos] = ((uint64_t)(ty * TW + tx) << 32) | rbits;
-                vals[pos] = (uint32_t)i;
-            }
-        }
+        });
+        return;
     }
-}
-
-// Digit histograms for all passes, plus zeroing of the look-back flags.
-__global__ void __launch_bounds__(256) k_hist(const uint64_t* __restrict__ keys,
-                                              const uint32_t* __restrict__ n_sort, int passes,
-                                              uint32_t* __restrict__ hist, uint32_t* __restrict__ look,
-                                              int look_tiles_cap) {
-    __shared__ uint32_t s_hist[kMaxPasses][256];
-    const uint32_t n = n_sort[0];
-    for (int t = threadIdx.x; t < passes * 256; t += blockDim.x) (&s_hist[0][0])[t] = 0;
+    for (int t = threadIdx.x; t < T; t += kBinThreads) s_cnt[t] = 0;
     __syncthreads();
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-        const uint64_t k = keys[j];
-        for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(k >> (8 * p)) & 0xff], 1u);
-    }
-    // zero the look-back flags of every pass for the tiles this sort uses
-    const uint32_t ntiles = (n + kOsTile - 1) / kOsTile;
-    const uint64_t zn = (uint64_t)ntiles * 256;
-    for (int p = 0; p < passes; ++p) {
-        uint32_t* lp = look + (size_t)p * look_tiles_cap * 256;
-        for (uint64_t j = blockIdx.x * blockDim.x + threadIdx.x; j < zn; j += stride) lp[j] = 0;
+    warp_pairs(valid, f, TW, [&](int t, int, bool active) {
+        if (active) atomicAdd(&s_cnt[t], 1u);
+    });
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += kBinThreads) {
+        const uint32_t c = s_cnt[t];
+        if (c) {
+            s_base[t] = atomicAdd(&cursor[t], c);
+            s_cnt[t] = 0;
+        }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < passes * 256; t += blockDim.x) {
-        const uint32_t c = (&s_hist[0][0])[t];
-        if (c) atomicAdd(&hist[t], c);
-    }
+    warp_pairs(valid, f, TW, [&](int t, int owner, bool active) {
+        const uint64_t k = __shfl_sync(0xffffffffu, key, owner);
+        if (active) {
+            const uint32_t pos = s_base[t] + atomicAdd(&s_cnt[t], 1u);
+            if (pos < cap) keys[pos] = k;
+        }
+    });
 }
 
-__global__ void __launch_bounds__(256) k_hist_scan(int passes, uint32_t* __restrict__ hist) {
-    __shared__ uint32_t s_warp[8];
-    for (int p = 0; p < passes; ++p) {
-        const uint32_t v = hist[p * 256 + threadIdx.x];
-        uint32_t total;
-        const uint32_t ex = block_exclusive_scan(v, s_warp, total);
-        hist[p * 256 + threadIdx.x] = ex;
-        __syncthreads();
-    }
-}
+struct SortShared {
+    uint32_t hist[kSortWarps * 256];   // radix: [warp][digit] counts; distribution: sub-bucket offsets
+    uint32_t warp_sum[kSortWarps];
+    unsigned long long or_all, and_all;
+    uint32_t dmin, dmax, maxb;
+};
 
-__global__ void __launch_bounds__(kOsThreads, 2) k_onesweep(
-    int pass, const uint64_t* __restrict__ ksrc, const uint32_t* __restrict__ vsrc,
-    uint64_t* __restrict__ kdst, uint32_t* __restrict__ vdst, const uint32_t* __restrict__ n_sort,
-    uint32_t* __restrict__ ctr, uint32_t* __restrict__ look, const uint32_t* __restrict__ digit_off,
-    int32_t* status) {
-    __shared__ uint32_t s_whist[kOsWarps][256];
-    __shared__ uint32_t s_excl[256];
-    __shared__ uint32_t s_tile;
-    const uint32_t n = n_sort[0];
-    const uint32_t ntiles = (n + kOsTile - 1) / kOsTile;
-    const int shift = 8 * pass;
+// Block-wide exclusive scan of one value per thread (kSortThreads threads).
+__device__ __forceinline__ uint32_t sort_block_scan(uint32_t v, uint32_t* warp_sum) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(ctr, 1u);
-        for (int t = threadIdx.x; t < kOsWarps * 256; t += kOsThreads) (&s_whist[0][0])[t] = 0;
-        __syncthreads();
-        const uint32_t tile = s_tile;
-        if (tile >= ntiles) break;
-        const uint32_t base = tile * kOsTile + warp * (kOsKpt * 32);
-        uint64_t k[kOsKpt];
-        uint32_t v[kOsKpt];
-        uint32_t pos[kOsKpt];
+    uint32_t x = v;
 #pragma unroll
-        for (int j = 0; j < kOsKpt; ++j) {
-            const uint32_t idx = base + j * 32 + lane;
-            const bool ok = idx < n;
-            k[j] = ok ? ksrc[idx] : ~0ull;
-            v[j] = ok ? vsrc[idx] : 0u;
-        }
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[warp] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += warp_sum[w];
+    __syncthreads();
+    return before + x - v;
+}
+
+// Lanes of the warp whose 8-bit digit equals this lane's (d == 256 marks a lane without an
+// element; such lanes match only each other): one ballot per digit bit.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
+    uint32_t peers = 0xffffffffu;
 #pragma unroll
-        for (int j = 0; j < kOsKpt; ++j) {
-            const uint32_t idx = base + j * 32 + lane;
-            const uint32_t d = idx < n ? (uint32_t)((k[j] >> shift) & 0xff) : 256u;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            const uint32_t before = d < 256 ? s_whist[warp][d] : 0u;
-            pos[j] = before + __popc(peers & lt_mask);
-            __syncwarp();
-            if (d < 256 && lane == (__ffs(peers) - 1)) s_whist[warp][d] = before + __popc(peers);
-            __syncwarp();
-        }
-        __syncthreads();
-        // per digit: exclusive scan across warps, publish, look back
-        {
-            const int d = threadIdx.x;
-            uint32_t sum = 0;
+    for (int b = 0; b < 9; ++b) {
+        const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+        peers &= ((d >> b) & 1u) ? bal : ~bal;
+    }
+    return peers;
+}
+
+// One stable LSD pass over the 8-bit digit at `shift`: src[0, n) -> dst[0, n).  Warp w
+// owns the contiguous chunk [w*C, (w+1)*C) (C a multiple of 32) and walks it in rows of
+// 32, ranking equal digits within a row by ballots.  The per-warp histograms are stored
+// warp-major (lanes of a warp touch banks by digit) and scanned digit by digit across
+// warps, then over digits, which gives every (digit, warp) run its place.
+__device__ __forceinline__ void lsd_pass(const uint64_t* src, uint64_t* dst, int n, int shift,
+                                         SortShared& sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int C = ((n + kSortThreads - 1) / kSortThreads) * 32;
+    const int lo = warp * C, hi = min(n, lo + C);
+    uint32_t* wh = sh.hist + warp * 256;
+    for (int e = threadIdx.x; e < 256 * kSortWarps; e += kSortThreads) sh.hist[e] = 0;
+    __syncthreads();
+    for (int idx = lo + lane; idx < hi; idx += 32) atomicAdd(&wh[(uint32_t)(src[idx] >> shift) & 0xffu], 1u);
+    __syncthreads();
+    {
+        const int d = threadIdx.x;
+        uint32_t run = 0;
+        if (d < 256) {
 #pragma unroll
-            for (int w = 0; w < kOsWarps; ++w) {
-                const uint32_t c = s_whist[w][d];
-                s_whist[w][d] = sum;
-                sum += c;
+            for (int w = 0; w < kSortWarps; ++w) {
+                const uint32_t c = sh.hist[w * 256 + d];
+                sh.hist[w * 256 + d] = run;
+                run += c;
             }
-            uint32_t* my = look + (size_t)tile * 256 + d;
-            uint32_t prefix = 0;
-            if (tile == 0) {
-                st_relaxed(my, kFlagInc | sum);
-            } else {
-                st_relaxed(my, kFlagAgg | sum);
-                // look back over windows of kLookWin predecessors: the window's flags are
-                // loaded together (one L2 round trip per window, not per tile), then summed
-                // from the nearest tile down to the first inclusive prefix
-                int j = (int)tile - 1;
-                int spins = 0;
-                bool fin = false;
-                while (!fin) {
-                    uint32_t v[kLookWin];
+        }
+        const uint32_t off = sort_block_scan(run, sh.warp_sum);
+        if (d < 256) {
 #pragma unroll
-                    for (int q = 0; q < kLookWin; ++q)
-                        v[q] = (j - q >= 0) ? ld_relaxed(look + (size_t)(j - q) * 256 + d) : kFlagInc;
+            for (int w = 0; w < kSortWarps; ++w) sh.hist[w * 256 + d] += off;
+        }
+    }
+    __syncthreads();
+    for (int row = lo; row < hi; row += 32) {
+        const int idx = row + lane;
+        const uint64_t k = idx < hi ? src[idx] : 0ull;
+        const uint32_t d = idx < hi ? (uint32_t)(k >> shift) & 0xffu : 256u;
+        const uint32_t peers = digit_peers(d);
+        uint32_t base = 0;
+        if (d < 256) base = wh[d];
+        __syncwarp();
+        if (d < 256) {
+            dst[base + __popc(peers & lt)] = k;
+            if ((peers & lt) == 0) wh[d] = base + __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+}
+
+// Sort keys[0, n) (ping-pong with alt) over the bytes that vary; returns the buffer that
+// holds the result.
+__device__ __forceinline__ uint64_t* sort_bucket(uint64_t* a, uint64_t* b, int n, SortShared& sh) {
+    unsigned long long o = 0, z = ~0ull;
+    for (int j = threadIdx.x; j < n; j += kSortThreads) {
+        o |= a[j];
+        z &= a[j];
+    }
 #pragma unroll
-                    for (int q = 0; q < kLookWin; ++q) {
-                        if (fin) break;
-                        uint32_t s = v[q];
-                        while ((s & ~kValMask) == 0) {   // that tile has not published yet
-                            if (++spins > kSpinLimit) {
-                                set_status(status, GSPARC_ERR_TIMEOUT);
-                                s = kFlagInc;
-                                break;
-                            }
-                            __nanosleep(32);
-                            s = ld_relaxed(look + (size_t)(j - q) * 256 + d);
-                        }
-                        prefix += s & kValMask;
-                        if ((s & ~kValMask) == kFlagInc) fin = true;
-                    }
-                    j -= kLookWin;
+    for (int s = 16; s > 0; s >>= 1) {
+        o |= __shfl_xor_sync(0xffffffffu, o, s);
+        z &= __shfl_xor_sync(0xffffffffu, z, s);
+    }
+    if (threadIdx.x == 0) {
+        sh.or_all = 0;
+        sh.and_all = ~0ull;
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        atomicOr(&sh.or_all, o);
+        atomicAnd(&sh.and_all, z);
+    }
+    __syncthreads();
+    const uint64_t vary = sh.or_all ^ sh.and_all;
+    __syncthreads();
+    for (int byte = 0; byte < 8; ++byte) {
+        if (((vary >> (8 * byte)) & 0xffu) == 0) continue;
+        lsd_pass(a, b, n, 8 * byte, sh);
+        uint64_t* t = a;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Sub-bucket of a key in the tile's distribution sort: the depth bits' offset from the
+// tile's minimum, scaled to [0, kSubBuckets).  Every step (offset, round-toward-zero
+// conversion, multiplication, truncation, clamp) is monotone non-decreasing, so a key
+// never lands in an earlier sub-bucket than a smaller key.
+__device__ __forceinline__ int sub_bucket(uint64_t k, uint32_t dmin, float scale) {
+    const uint32_t x = (uint32_t)(k >> 32) - dmin;
+    return min(kSubBuckets - 1, __float2int_rz(__fmul_rn(__uint2float_rz(x), scale)));
+}
+
+// One CTA per tile (grid-stride over tiles).  A bucket of up to kSortCap keys is sorted by
+// distribution: keys are counted into kSubBuckets sub-buckets by depth, scattered to their
+// sub-bucket in shared memory (arbitrary order inside it), and each key's final place is
+// its sub-bucket's start plus the number of smaller keys in the same sub-bucket (the keys
+// are unique, so the places are distinct).  A bucket above kSortCap keys, or one whose
+// largest sub-bucket exceeds kSubMax keys (many equal depths), takes the LSD radix sort in
+// global memory with `alt` as the second buffer.
+__global__ void __launch_bounds__(kSortThreads, 1) k_tile_sort(int T, const uint2* __restrict__ ranges,
+                                                               uint64_t* __restrict__ keys,
+                                                               uint64_t* __restrict__ alt,
+                                                               uint32_t* __restrict__ sorted_ids,
+                                                               uint64_t* __restrict__ sorted_keys) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SortShared& sh = *reinterpret_cast<SortShared*>(smem_raw);
+    uint64_t* buf = reinterpret_cast<uint64_t*>(smem_raw + ((sizeof(SortShared) + 15) & ~size_t(15)));
+    const int lane = threadIdx.x & 31;
+    for (int tile = blockIdx.x; tile < T; tile += gridDim.x) {
+        const uint2 r = ranges[tile];
+        const int n = (int)(r.y - r.x);
+        if (n <= 0) continue;
+        const uint64_t* src = keys + r.x;
+        bool radix = n > kSortCap;
+        if (!radix) {
+            if (threadIdx.x == 0) {
+                sh.dmin = 0xffffffffu;
+                sh.dmax = 0u;
+                sh.maxb = 0u;
+            }
+            for (int e = threadIdx.x; e < kSubBuckets; e += kSortThreads) sh.hist[e] = 0;
+            __syncthreads();
+            uint32_t lo = 0xffffffffu, hi = 0u;
+            for (int j = threadIdx.x; j < n; j += kSortThreads) {
+                const uint32_t d = (uint32_t)(src[j] >> 32);
+                lo = min(lo, d);
+                hi = max(hi, d);
+            }
+            lo = __reduce_min_sync(0xffffffffu, lo);
+            hi = __reduce_max_sync(0xffffffffu, hi);
+            if (lane == 0) {
+                atomicMin(&sh.dmin, lo);
+                atomicMax(&sh.dmax, hi);
+            }
+            __syncthreads();
+            const uint32_t dmin = sh.dmin;
+            const float scale = (float)kSubBuckets / ((float)(sh.dmax - dmin) + 1.0f);
+            for (int j = threadIdx.x; j < n; j += kSortThreads)
+                atomicAdd(&sh.hist[sub_bucket(src[j], dmin, scale)], 1u);
+            __syncthreads();
+            {
+                constexpr int kPer = kSubBuckets / kSortThreads;
+                uint32_t c[kPer], sum = 0, mx = 0;
+#pragma unroll
+                for (int q = 0; q < kPer; ++q) {
+                    c[q] = sh.hist[threadIdx.x * kPer + q];
+                    sum += c[q];
+                    mx = max(mx, c[q]);
                 }
-                st_relaxed(my, kFlagInc | ((prefix + sum) & kValMask));
-            }
-            s_excl[d] = digit_off[d] + prefix;
-        }
-        __syncthreads();
+                mx = __reduce_max_sync(0xffffffffu, mx);
+                if (lane == 0) atomicMax(&sh.maxb, mx);
+                uint32_t off = sort_block_scan(sum, sh.warp_sum);
 #pragma unroll
-        for (int j = 0; j < kOsKpt; ++j) {
-            const uint32_t idx = base + j * 32 + lane;
-            if (idx < n) {
-                const uint32_t d = (uint32_t)((k[j] >> shift) & 0xff);
-                const uint32_t dst = s_excl[d] + s_whist[warp][d] + pos[j];
-                if (dst < n) {   // always true unless a look-back wait expired
-                    kdst[dst] = k[j];
-                    vdst[dst] = v[j];
+                for (int q = 0; q < kPer; ++q) {
+                    sh.hist[threadIdx.x * kPer + q] = off;
+                    off += c[q];
                 }
             }
+            __syncthreads();
+            radix = sh.maxb > (uint32_t)kSubMax;
+            if (!radix) {
+                for (int j = threadIdx.x; j < n; j += kSortThreads) {
+                    const uint64_t k = src[j];
+                    buf[atomicAdd(&sh.hist[sub_bucket(k, dmin, scale)], 1u)] = k;
+                }
+                __syncthreads();
+                // hist[b] is now the end of sub-bucket b (= the start of b + 1)
+                for (int p = threadIdx.x; p < n; p += kSortThreads) {
+                    const uint64_t k = buf[p];
+                    const int b = sub_bucket(k, dmin, scale);
+                    const int s0 = b > 0 ? (int)sh.hist[b - 1] : 0, e0 = (int)sh.hist[b];
+                    int rank = 0;
+                    for (int q = s0; q < e0; ++q) rank += buf[q] < k;
+                    const uint32_t dst = r.x + (uint32_t)(s0 + rank);
+                    sorted_ids[dst] = (uint32_t)k;
+                    if (sorted_keys) sorted_keys[dst] = ((uint64_t)tile << 32) | (k >> 32);
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
+        if (radix) {
+            const uint64_t* res = sort_bucket(keys + r.x, alt + r.x, n, sh);
+            for (int j = threadIdx.x; j < n; j += kSortThreads) {
+                const uint64_t k = res[j];
+                sorted_ids[r.x + j] = (uint32_t)k;
+                if (sorted_keys) sorted_keys[r.x + j] = ((uint64_t)tile << 32) | (k >> 32);
+            }
+            __syncthreads();
+        }
     }
 }
 
-__global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ keys,
-                                                const uint32_t* __restrict__ n_sort, uint32_t T,
-                                                uint2* __restrict__ ranges) {
-    const uint32_t n = n_sort[0];
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-        const uint32_t t = (uint32_t)(keys[j] >> 32);
-        if (t >= T) continue;   // only after an expired look-back wait
-        if (j == 0 || (uint32_t)(keys[j - 1] >> 32) != t) ranges[t].x = j;
-        if (j + 1 == n || (uint32_t)(keys[j + 1] >> 32) != t) ranges[t].y = j + 1;
-    }
-}
+constexpr size_t kSortSmem = ((sizeof(SortShared) + 15) & ~size_t(15)) + kSortCap * sizeof(uint64_t);
+static_assert(kSortSmem <= 232448, "tile sort shared memory above the per-block limit");
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t local, blk, k0, k1, v0, v1, hist, ctr, misc, look, total;
-    int nblk, passes, look_tiles;
+    size_t cnt, cursor, done, keys, alt, total;
+    int nblk;
 };
-
-int num_passes(int ntiles) {
-    int bits = 0;
-    while ((1ll << bits) < ntiles) ++bits;
-    return 4 + (bits + 7) / 8;
-}
 
 Layout layout(int N, int64_t cap, int ntiles) {
     Layout L;
-    L.nblk = (N + kScanThreads - 1) / kScanThreads;
-    L.passes = num_passes(ntiles);
-    L.look_tiles = (int)((cap + kOsTile - 1) / kOsTile);
+    L.nblk = (N + kBinThreads - 1) / kBinThreads;
     size_t o = 0;
-    L.local = o; o += align256((size_t)N * 4);
-    L.blk = o;   o += align256((size_t)(L.nblk + 1) * 4);
-    L.k0 = o;    o += align256((size_t)cap * 8);
-    L.k1 = o;    o += align256((size_t)cap * 8);
-    L.v0 = o;    o += align256((size_t)cap * 4);
-    L.v1 = o;    o += align256((size_t)cap * 4);
-    L.hist = o;  o += align256((size_t)kMaxPasses * 256 * 4);
-    L.ctr = o;   o += align256((size_t)kMaxPasses * 4);
-    L.misc = o;  o += align256(16);
-    L.look = o;  o += align256((size_t)L.passes * L.look_tiles * 256 * 4);
+    L.cnt = o;    o += align256((size_t)ntiles * 4);
+    L.done = o;   o += align256(16);
+    L.cursor = o; o += align256((size_t)ntiles * 4);
+    L.keys = o;   o += align256((size_t)cap * 8);
+    L.alt = o;    o += align256((size_t)cap * 8);
     L.total = o;
     return L;
+}
+
+// The launch sequence shared by both entry points.  `w` is a workspace laid out by layout().
+int bin_sort_launch(const gsparc_view* view, int N, const float* proj, int64_t pair_capacity, char* w,
+                    const Layout& L, uint32_t* sorted_ids, uint64_t* sorted_keys, uint32_t* tile_ranges,
+                    uint32_t* n_pairs, int32_t* d_status, cudaStream_t s) {
+    const int TW = tiles_x(*view), TH = tiles_y(*view), T = TW * TH;
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(w + L.cnt);
+    uint32_t* done = reinterpret_cast<uint32_t*>(w + L.done);
+    uint32_t* cursor = reinterpret_cast<uint32_t*>(w + L.cursor);
+    uint64_t* keys = reinterpret_cast<uint64_t*>(w + L.keys);
+    uint64_t* alt = reinterpret_cast<uint64_t*>(w + L.alt);
+    const uint32_t cap = (uint32_t)pair_capacity;
+    if (N == 0) {
+        if (cudaMemsetAsync(tile_ranges, 0, (size_t)T * 2 * sizeof(uint32_t), s) != cudaSuccess)
+            return GSPARC_ERR_CUDA;
+        if (cudaMemsetAsync(n_pairs, 0, sizeof(uint32_t), s) != cudaSuccess) return GSPARC_ERR_CUDA;
+        return GSPARC_OK;
+    }
+    // tile counters and the block ticket are contiguous
+    if (cudaMemsetAsync(w + L.cnt, 0, L.cursor - L.cnt, s) != cudaSuccess) return GSPARC_ERR_CUDA;
+    if (!ensure_smem_attr(k_tile_sort, (int)kSortSmem)) return GSPARC_ERR_CUDA;
+    const float4* p4 = reinterpret_cast<const float4*>(proj);
+    uint2* ranges = reinterpret_cast<uint2*>(tile_ranges);
+    k_tile_count<<<L.nblk, kBinThreads, 0, s>>>(N, view->H, view->W, TW, T, p4, cnt, cursor, done, cap,
+                                                ranges, n_pairs, d_status);
+    k_tile_emit<<<L.nblk, kBinThreads, 0, s>>>(N, view->H, view->W, TW, T, p4, cursor, cap, keys);
+    const int grid = std::min(T, num_sms() * 8);
+    k_tile_sort<<<grid, kSortThreads, kSortSmem, s>>>(T, ranges, keys, alt, sorted_ids, sorted_keys);
+    return launch_status();
 }
 
 }  // namespace
@@ -440,55 +562,12 @@ extern "C" int gsparc_bin_sort(const gsparc_view* view, int32_t N, const float* 
     if (!tile_ranges || !n_pairs || (N > 0 && !proj) || (pair_capacity > 0 && !sorted_ids))
         return GSPARC_ERR_INVALID;
     if (reinterpret_cast<uintptr_t>(proj) & 15) return GSPARC_ERR_INVALID;
-    const int TW = tiles_x(*view), TH = tiles_y(*view), T = TW * TH;
+    const int T = tiles_x(*view) * tiles_y(*view);
     const Layout L = layout(N, pair_capacity, T);
     if (!ws || ws_bytes < L.total) return GSPARC_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(ws) & 255) return GSPARC_ERR_INVALID;
-    cudaStream_t s = as_stream(stream);
-    char* w = static_cast<char*>(ws);
-    uint32_t* local = reinterpret_cast<uint32_t*>(w + L.local);
-    uint32_t* blk = reinterpret_cast<uint32_t*>(w + L.blk);
-    uint64_t* kb[2] = {reinterpret_cast<uint64_t*>(w + L.k0), reinterpret_cast<uint64_t*>(w + L.k1)};
-    uint32_t* vb[2] = {reinterpret_cast<uint32_t*>(w + L.v0), reinterpret_cast<uint32_t*>(w + L.v1)};
-    uint32_t* hist = reinterpret_cast<uint32_t*>(w + L.hist);
-    uint32_t* ctr = reinterpret_cast<uint32_t*>(w + L.ctr);
-    uint32_t* misc = reinterpret_cast<uint32_t*>(w + L.misc);
-    uint32_t* look = reinterpret_cast<uint32_t*>(w + L.look);
-    const uint32_t cap = (uint32_t)pair_capacity;
-
-    if (cudaMemsetAsync(tile_ranges, 0, (size_t)T * 2 * sizeof(uint32_t), s) != cudaSuccess)
-        return GSPARC_ERR_CUDA;
-    // hist, ctr and misc are contiguous
-    if (cudaMemsetAsync(w + L.hist, 0, L.look - L.hist, s) != cudaSuccess) return GSPARC_ERR_CUDA;
-    if (N == 0) {
-        if (cudaMemsetAsync(n_pairs, 0, sizeof(uint32_t), s) != cudaSuccess) return GSPARC_ERR_CUDA;
-        return GSPARC_OK;
-    }
-    const float4* p4 = reinterpret_cast<const float4*>(proj);
-    k_count<<<L.nblk, kScanThreads, 0, s>>>(N, view->H, view->W, TW, p4, local, blk);
-    k_scan_blocks<<<1, 1024, 0, s>>>(L.nblk, blk, n_pairs, misc, cap, d_status);
-    k_emit<<<L.nblk, kScanThreads, 0, s>>>(N, view->H, view->W, TW, p4, local, blk, cap, kb[0], vb[0]);
-    if (cudaGetLastError() != cudaSuccess) return GSPARC_ERR_CUDA;
-    if (cap == 0) return GSPARC_OK;
-
-    const int sms = num_sms();
-    const int hist_blocks = sms * 2;
-    k_hist<<<hist_blocks, 256, 0, s>>>(kb[0], misc, L.passes, hist, look, L.look_tiles);
-    k_hist_scan<<<1, 256, 0, s>>>(L.passes, hist);
-    const int os_blocks = (int)std::min<int64_t>(L.look_tiles, (int64_t)sms * 2);
-    uint64_t* kfinal = nullptr;
-    for (int p = 0; p < L.passes; ++p) {
-        const int src = p & 1, dst = src ^ 1;
-        const bool last = p == L.passes - 1;
-        uint64_t* kd = last ? (sorted_keys ? sorted_keys : kb[dst]) : kb[dst];
-        uint32_t* vd = last ? sorted_ids : vb[dst];
-        k_onesweep<<<os_blocks, kOsThreads, 0, s>>>(p, kb[src], vb[src], kd, vd, misc, ctr + p,
-                                                    look + (size_t)p * L.look_tiles * 256,
-                                                    hist + p * 256, d_status);
-        if (last) kfinal = kd;
-    }
-    k_ranges<<<sms * 4, 256, 0, s>>>(kfinal, misc, (uint32_t)T, reinterpret_cast<uint2*>(tile_ranges));
-    return launch_status();
+    return bin_sort_launch(view, N, proj, pair_capacity, static_cast<char*>(ws), L, sorted_ids,
+                           sorted_keys, tile_ranges, n_pairs, d_status, as_stream(stream));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -501,8 +580,10 @@ extern "C" int gsparc_bin_sort(const gsparc_view* view, int32_t N, const float* 
 namespace gsparc {
 namespace {
 
-constexpr size_t kNoAllocBytes = size_t(15) << 20;   // covers layout(65536, 524288, 7 passes)
-static_assert(kOsTile == 2048, "the no-alloc budget assumes 2048-key sort tiles");
+// covers layout(N, GSPARC_NOALLOC_MAX_PAIRS, T) for up to 65536 tiles
+constexpr size_t kNoAllocBytes = size_t(9) << 20;
+static_assert(size_t(GSPARC_NOALLOC_MAX_PAIRS) * 16 + 65536 * 8 + 4096 <= kNoAllocBytes,
+              "no-alloc scratch below the documented limits");
 constexpr int kMaxDevices = 64;
 
 // Host code must not use this symbol as an address: it only names the array.  The device
@@ -525,7 +606,7 @@ extern "C" int gsparc_bin_sort_noalloc(const gsparc_view* view, int32_t N, const
     if (!tile_ranges || !n_pairs || (N > 0 && !proj) || (pair_capacity > 0 && !sorted_ids))
         return GSPARC_ERR_INVALID;
     if (reinterpret_cast<uintptr_t>(proj) & 15) return GSPARC_ERR_INVALID;
-    const int TW = tiles_x(*view), TH = tiles_y(*view), T = TW * TH;
+    const int T = tiles_x(*view) * tiles_y(*view);
     const Layout L = layout(N, pair_capacity, T);
     if (L.total > kNoAllocBytes) return GSPARC_ERR_TOO_LARGE;
 
@@ -535,49 +616,8 @@ extern "C" int gsparc_bin_sort_noalloc(const gsparc_view* view, int32_t N, const
         g_noalloc_err[dev] = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_scratch);
     });
     if (g_noalloc_err[dev] != cudaSuccess || !g_noalloc_ptr[dev]) return GSPARC_ERR_CUDA;
-
-    cudaStream_t s = as_stream(stream);
-    char* w = static_cast<char*>(g_noalloc_ptr[dev]);
-    uint32_t* local = reinterpret_cast<uint32_t*>(w + L.local);
-    uint32_t* blk = reinterpret_cast<uint32_t*>(w + L.blk);
-    uint64_t* kb[2] = {reinterpret_cast<uint64_t*>(w + L.k0), reinterpret_cast<uint64_t*>(w + L.k1)};
-    uint32_t* vb[2] = {reinterpret_cast<uint32_t*>(w + L.v0), reinterpret_cast<uint32_t*>(w + L.v1)};
-    uint32_t* hist = reinterpret_cast<uint32_t*>(w + L.hist);
-    uint32_t* ctr = reinterpret_cast<uint32_t*>(w + L.ctr);
-    uint32_t* misc = reinterpret_cast<uint32_t*>(w + L.misc);
-    uint32_t* look = reinterpret_cast<uint32_t*>(w + L.look);
-    const uint32_t cap = (uint32_t)pair_capacity;
-
-    // the array keeps the previous call's contents: clear the counters, histograms and
-    // pass counters here (the look-back flags are cleared by k_hist)
-    if (cudaMemsetAsync(tile_ranges, 0, (size_t)T * 2 * sizeof(uint32_t), s) != cudaSuccess)
-        return GSPARC_ERR_CUDA;
-    if (cudaMemsetAsync(w + L.hist, 0, L.look - L.hist, s) != cudaSuccess) return GSPARC_ERR_CUDA;
-    if (N == 0) {
-        if (cudaMemsetAsync(n_pairs, 0, sizeof(uint32_t), s) != cudaSuccess) return GSPARC_ERR_CUDA;
-        return GSPARC_OK;
-    }
-    const float4* p4 = reinterpret_cast<const float4*>(proj);
-    k_count<<<L.nblk, kScanThreads, 0, s>>>(N, view->H, view->W, TW, p4, local, blk);
-    k_scan_blocks<<<1, 1024, 0, s>>>(L.nblk, blk, n_pairs, misc, cap, d_status);
-    k_emit<<<L.nblk, kScanThreads, 0, s>>>(N, view->H, view->W, TW, p4, local, blk, cap, kb[0], vb[0]);
-    if (cudaGetLastError() != cudaSuccess) return GSPARC_ERR_CUDA;
-    if (cap == 0) return GSPARC_OK;
-    const int sms = num_sms();
-    k_hist<<<sms * 2, 256, 0, s>>>(kb[0], misc, L.passes, hist, look, L.look_tiles);
-    k_hist_scan<<<1, 256, 0, s>>>(L.passes, hist);
-    const int os_blocks = (int)std::min<int64_t>(L.look_tiles, (int64_t)sms * 2);
-    uint64_t* kfinal = nullptr;
-    for (int p = 0; p < L.passes; ++p) {
-        const int src = p & 1, dst = src ^ 1;
-        const bool last = p == L.passes - 1;
-        uint64_t* kd = last ? (sorted_keys ? sorted_keys : kb[dst]) : kb[dst];
-        uint32_t* vd = last ? sorted_ids : vb[dst];
-        k_onesweep<<<os_blocks, kOsThreads, 0, s>>>(p, kb[src], vb[src], kd, vd, misc, ctr + p,
-                                                    look + (size_t)p * L.look_tiles * 256,
-                                                    hist + p * 256, d_status);
-        if (last) kfinal = kd;
-    }
-    k_ranges<<<sms * 4, 256, 0, s>>>(kfinal, misc, (uint32_t)T, reinterpret_cast<uint2*>(tile_ranges));
-    return launch_status();
+    // the array keeps the previous call's contents; bin_sort_launch clears the tile
+    // counters and the block ticket, and everything else is written before it is read
+    return bin_sort_launch(view, N, proj, pair_capacity, static_cast<char*>(g_noalloc_ptr[dev]), L,
+                           sorted_ids, sorted_keys, tile_ranges, n_pairs, d_status, as_stream(stream));
 }

@@ -97,7 +97,7 @@ def test_bin_sort_bit_exact(n, H, W, seed):
 
 
 def test_bin_sort_many_passes_and_empty():
-    # 720x180 has 540 tiles: tile ids need 10 bits, so six 8-bit passes
+    # 720x180: 540 tiles, more than one tile-id byte in the sorted keys
     rec = synth.make_proj_records(4000, 180, 720, seed=11)
     st, npairs, keys, ids, ranges = _gpu_binsort(rec, 180, 720)
     ok, ov, orng = obs.bin_sort(rec, 180, 720)
@@ -116,6 +116,41 @@ def test_bin_sort_capacity_overflow_reported():
     assert st == G.GSPARC_ERR_CAPACITY
     assert npairs == len(ov)
     assert len(ids) == cap
+    # tiles whose lists end at or below the capacity are complete and sorted, later ones empty
+    _, _, orng = obs.bin_sort(rec, 90, 360)
+    fits = orng[:, 1] <= cap
+    assert fits.any() and not fits.all()
+    assert np.array_equal(ranges[fits], orng[fits])
+    assert np.all(ranges[~fits, 0] == ranges[~fits, 1])
+    last = orng[fits][:, 1].max()
+    assert np.array_equal(ids[:last], ov[:last])
+
+
+def test_bin_sort_buckets_above_shared_memory_capacity():
+    """Every tile of a 180x45 view holds 26k-39k pairs, more than a thread block
+    sorts in shared memory (24576): those buckets are radix sorted in the workspace."""
+    rec = synth.make_proj_records(60_000, 45, 180, seed=13, frac_wide=0.6)
+    rec[:, 3] = np.where(rec[:, 3] < 0, -1.0, np.maximum(rec[:, 3], 30.0))
+    st, npairs, keys, ids, ranges = _gpu_binsort(rec, 45, 180)
+    ok, ov, orng = obs.bin_sort(rec, 45, 180)
+    assert (orng[:, 1] - orng[:, 0]).min() > 24576
+    assert st == 0 and npairs == len(ov)
+    assert np.array_equal(keys, ok)
+    assert np.array_equal(ids, ov)
+    assert np.array_equal(ranges, orng)
+
+
+def test_bin_sort_few_distinct_depths():
+    """Three distinct depths: each tile's depth sub-buckets hold far more than 64
+    keys, so the tiles take the radix path in the workspace; ties go by index."""
+    rec = synth.make_proj_records(5000, 90, 360, seed=14)
+    rec[:, 7] = np.random.default_rng(15).choice(np.float32([1.5, 2.0, 7.25]), size=len(rec))
+    st, npairs, keys, ids, ranges = _gpu_binsort(rec, 90, 360)
+    ok, ov, orng = obs.bin_sort(rec, 90, 360)
+    assert st == 0 and npairs == len(ov)
+    assert np.array_equal(keys, ok)
+    assert np.array_equal(ids, ov)
+    assert np.array_equal(ranges, orng)
 
 
 def test_bin_sort_properties_full_size_scene():
