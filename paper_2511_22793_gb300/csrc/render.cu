@@ -886,9 +886,10 @@ struct RTbSmem {
     static constexpr int kBTile = 3 * kTbE * kKa * 2;          // bytes of one (stage, term) tile
     static constexpr int kB = kA + 4 * kATile;                 // [stage][hi, lo]
     static constexpr int kMeta = kB + 4 * kBTile;
-    // per stage: geo float4, geo2 float2, ext float2, amp, phi, len, gid (E each)
+    // per-entry records of four batches (being published, built, consumed, flushed):
+    // geo float4, geo2 float2, ext float2, amp, phi, len, gid (E each)
     static constexpr int kMetaStage = kTbE * (16 + 8 + 8 + 4 + 4 + 4 + 4);
-    static constexpr int kRed = kMeta + 2 * kMetaStage;        // float [8 warps][E][9]
+    static constexpr int kRed = kMeta + 4 * kMetaStage;        // float [8 warps][E][9]
     static constexpr int kMask = kRed + 8 * kTbE * 9 * 4;      // uint64 [8]
     static constexpr int kBar = kMask + 8 * 8;                 // 2 mbarriers + TMEM slot + maxlast
     static constexpr int kTotal = kBar + 32;
@@ -957,7 +958,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_bwd_tc(RenderArgs a) {
     {
         uint8_t* Ahi = sm + L::kA + (half * 2 + 0) * L::kATile;
         uint8_t* Alo = sm + L::kA + (half * 2 + 1) * L::kATile;
-#pragma unroll 1
+#pragma unroll 4
         for (int c0 = 0; c0 < 2 * S; c0 += 8) {
             float g8[8];
 #pragma unroll
@@ -992,39 +993,64 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_bwd_tc(RenderArgs a) {
     const int nbatch = (int)((maxlast + kTbE - 1) / kTbE);
     uint32_t ph0 = 0, ph1 = 0;
     bool ok = true;
-
-    for (int i = 0; i <= nbatch && ok; ++i) {
-        if (i < nbatch) {
-            // ---- stage batch i (entries [lo, hi) of the list, walking back from maxlast)
-            const int st = i & 1;
-            const uint32_t hi_pos = maxlast - (uint32_t)i * kTbE;
-            const uint32_t lo_pos = hi_pos > (uint32_t)kTbE ? hi_pos - kTbE : 0u;
-            const int nb = (int)(hi_pos - lo_pos);
-            TbMeta md = tb_meta(sm + L::kMeta + st * L::kMetaStage);
-            if (tid < kTbE) {
-                uint32_t gid = tid < nb ? a.ids[range.x + lo_pos + tid] : 0xffffffffu;
-                if (gid < (uint32_t)a.N) {
-                    const float4 p0 = a.proj[2 * gid];
-                    const float4 p1 = a.proj[2 * gid + 1];
-                    const float4 at = a.attr[(size_t)b * a.N + gid];
-                    md.geo[tid] = make_float4(p0.x, p0.y, p1.x, p1.y);
-                    md.geo2[tid] = make_float2(p1.z, at.z);
-                    md.ext[tid] = make_float2(p0.z, p0.w);
-                    md.amp[tid] = at.x;
-                    md.phi[tid] = at.y;
-                    md.len[tid] = at.w;
-                    md.gid[tid] = gid;
-                } else {
-                    md.geo[tid] = make_float4(0.f, 0.f, __int_as_float(0x7fc00000), 0.f);
-                    md.geo2[tid] = make_float2(0.f, 0.f);
-                    md.ext[tid] = make_float2(-1.f, -1.f);
-                    md.amp[tid] = 0.f;
-                    md.phi[tid] = 0.f;
-                    md.len[tid] = 0.f;
-                    md.gid[tid] = 0;
-                }
+    // batch i holds list entries [lo_pos(i), hi_pos(i)), walking back from maxlast
+    auto batch_lo = [&](int i) {
+        const uint32_t hp = maxlast - (uint32_t)i * kTbE;
+        return hp > (uint32_t)kTbE ? hp - kTbE : 0u;
+    };
+    auto batch_n = [&](int i) { return (int)(maxlast - (uint32_t)i * kTbE - batch_lo(i)); };
+    // records of one batch gathered into registers (threads tid < E) two batches ahead, then
+    // published into that batch's record buffer one batch ahead
+    uint32_t pf_gid = 0xffffffffu;
+    float4 pf_p0 = make_float4(0.f, 0.f, 0.f, 0.f), pf_p1 = pf_p0, pf_at = pf_p0;
+    auto gather = [&](int i) {
+        if (tid < kTbE) {
+            const int nb = batch_n(i);
+            pf_gid = tid < nb ? a.ids[range.x + batch_lo(i) + tid] : 0xffffffffu;
+            if (pf_gid < (uint32_t)a.N) {
+                pf_p0 = a.proj[2 * pf_gid];
+                pf_p1 = a.proj[2 * pf_gid + 1];
+                pf_at = a.attr[(size_t)b * a.N + pf_gid];
             }
-            __syncthreads();
+        }
+    };
+    auto publish = [&](int i) {
+        if (tid < kTbE) {
+            TbMeta md = tb_meta(sm + L::kMeta + (i & 3) * L::kMetaStage);
+            if (pf_gid < (uint32_t)a.N) {
+                md.geo[tid] = make_float4(pf_p0.x, pf_p0.y, pf_p1.x, pf_p1.y);
+                md.geo2[tid] = make_float2(pf_p1.z, pf_at.z);
+                md.ext[tid] = make_float2(pf_p0.z, pf_p0.w);
+                md.amp[tid] = pf_at.x;
+                md.phi[tid] = pf_at.y;
+                md.len[tid] = pf_at.w;
+                md.gid[tid] = pf_gid;
+            } else {
+                md.geo[tid] = make_float4(0.f, 0.f, __int_as_float(0x7fc00000), 0.f);
+                md.geo2[tid] = make_float2(0.f, 0.f);
+                md.ext[tid] = make_float2(-1.f, -1.f);
+                md.amp[tid] = 0.f;
+                md.phi[tid] = 0.f;
+                md.len[tid] = 0.f;
+                md.gid[tid] = 0;
+            }
+        }
+    };
+    if (nbatch > 0) {
+        gather(0);
+        publish(0);
+    }
+    if (nbatch > 1) gather(1);
+    __syncthreads();
+
+    // Iteration i: build B of batch i, publish batch i+1's records and gather batch i+2's,
+    // one barrier, issue batch i's MMAs, consume batch i-1 from TMEM on the CUDA cores, one
+    // barrier (which also carries any expired wait), flush batch i-1's gradients.
+    for (int i = 0; i <= nbatch; ++i) {
+        if (i < nbatch) {
+            const int st = i & 1;
+            const int nb = batch_n(i);
+            TbMeta md = tb_meta(sm + L::kMeta + (i & 3) * L::kMetaStage);
             // ---- B rows of the batch: thread (j, 8 consecutive K columns) computes 4 phasors
             uint8_t* Bhi = sm + L::kB + (st * 2 + 0) * L::kBTile;
             uint8_t* Blo = sm + L::kB + (st * 2 + 1) * L::kBTile;
@@ -1054,110 +1080,121 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_bwd_tc(RenderArgs a) {
                 *reinterpret_cast<uint4*>(Bhi + canon_off(3 * j + 2, c0, L::kKa)) = H;
                 *reinterpret_cast<uint4*>(Blo + canon_off(3 * j + 2, c0, L::kKa)) = Lo;
             }
-            fence_async_smem();
-            tc_fence_before();
-            __syncthreads();
-            tc_fence_after();
-            if (tid == 0) {
-                const uint32_t bhi = b_base + (st * 2 + 0) * L::kBTile, blo = b_base + (st * 2 + 1) * L::kBTile;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t ahi = a_base + (h * 2 + 0) * L::kATile, alo = a_base + (h * 2 + 1) * L::kATile;
-                    const uint32_t d = tbase + (uint32_t)((st * 2 + h) * 3 * kTbE);
-                    // g_hi u_hi + g_lo u_hi + g_hi u_lo
-                    const uint32_t as_[3] = {ahi, alo, ahi};
-                    const uint32_t bs_[3] = {bhi, bhi, blo};
-#pragma unroll
-                    for (int t = 0; t < 3; ++t)
-#pragma unroll
-                        for (int q = 0; q < L::kKa / 16; ++q)
-                            mma_bf16(d, make_desc(as_[t] + q * 256, 128, L::kKa * 16),
-                                     make_desc(bs_[t] + q * 256, 128, L::kKa * 16), idesc,
-                                     (t > 0 || q > 0) ? 1u : 0u);
-                }
-                mma_commit(st == 0 ? bar0 : bar1);
-            }
         }
-        if (i >= 1) {
+        // batch i+1's buffer was last read by the flush of batch i-3 (two barriers ago)
+        if (i + 1 < nbatch) publish(i + 1);
+        if (i + 2 < nbatch) gather(i + 2);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (i < nbatch && tid == 0) {
+            const int st = i & 1;
+            const uint32_t bhi = b_base + (st * 2 + 0) * L::kBTile, blo = b_base + (st * 2 + 1) * L::kBTile;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t ahi = a_base + (h * 2 + 0) * L::kATile, alo = a_base + (h * 2 + 1) * L::kATile;
+                const uint32_t d = tbase + (uint32_t)((st * 2 + h) * 3 * kTbE);
+                // g_hi u_hi + g_lo u_hi + g_hi u_lo
+                const uint32_t as_[3] = {ahi, alo, ahi};
+                const uint32_t bs_[3] = {bhi, bhi, blo};
+#pragma unroll
+                for (int t = 0; t < 3; ++t)
+#pragma unroll
+                    for (int q = 0; q < L::kKa / 16; ++q)
+                        mma_bf16(d, make_desc(as_[t] + q * 256, 128, L::kKa * 16),
+                                 make_desc(bs_[t] + q * 256, 128, L::kKa * 16), idesc,
+                                 (t > 0 || q > 0) ? 1u : 0u);
+            }
+            mma_commit(st == 0 ? bar0 : bar1);
+        }
+        bool wok = true;
+        const int pi = i - 1;
+        TbMeta mdp = tb_meta(sm + L::kMeta + (pi & 3) * L::kMetaStage);
+        const int nbp = pi >= 0 ? batch_n(pi) : 0;
+        if (pi >= 0) {
             // ---- consume batch i-1 on the CUDA cores
-            const int pi = i - 1, st = pi & 1;
-            const bool wok = st == 0 ? mbar_wait(bar0, ph0) : mbar_wait(bar1, ph1);
+            const int st = pi & 1;
+            wok = st == 0 ? mbar_wait(bar0, ph0) : mbar_wait(bar1, ph1);
+            wok = __all_sync(0xffffffffu, wok);   // tcgen05.ld below is warp-collective
             if (st == 0) ph0 ^= 1;
             else ph1 ^= 1;
-            ok = __syncthreads_and(wok) != 0;
-            if (!ok) break;
-            tc_fence_after();
-            const uint32_t hi_pos = maxlast - (uint32_t)pi * kTbE;
-            const uint32_t lo_pos = hi_pos > (uint32_t)kTbE ? hi_pos - kTbE : 0u;
-            const int nb = (int)(hi_pos - lo_pos);
-            TbMeta md = tb_meta(sm + L::kMeta + st * L::kMetaStage);
-            float v[3 * kTbE];
+            const uint32_t lo_pos = batch_lo(pi);
+            if (wok) {
+                tc_fence_after();
+                float v[3 * kTbE];
 #pragma unroll
-            for (int c = 0; c < 3 * kTbE; c += 16) {
-                float t16[16];
-                tmem_ld16(tbase + (uint32_t)((st * 2 + half) * 3 * kTbE + c) + lane_base, t16);
+                for (int c = 0; c < 3 * kTbE; c += 16) {
+                    float t16[16];
+                    tmem_ld16(tbase + (uint32_t)((st * 2 + half) * 3 * kTbE + c) + lane_base, t16);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) v[c + q] = t16[q];
-            }
-            const uint64_t mask = warp_entry_mask(md.geo, md.ext, nb, wcx, wcy, a.W);
-            if (lane == 0) s_wmask[warp] = mask;
+                    for (int q = 0; q < 16; ++q) v[c + q] = t16[q];
+                }
+                const uint64_t mask = warp_entry_mask(mdp.geo, mdp.ext, nbp, wcx, wcy, a.W);
+                if (lane == 0) s_wmask[warp] = mask;
 #pragma unroll
-            for (int j = kTbE - 1; j >= 0; --j) {
-                if (!((mask >> j) & 1ull)) continue;   // warp-uniform
-                float gr[9];
+                for (int j = kTbE - 1; j >= 0; --j) {
+                    if (!((mask >> j) & 1ull)) continue;   // warp-uniform
+                    float gr[9];
 #pragma unroll
-                for (int c = 0; c < 9; ++c) gr[c] = 0.f;
-                bool contrib = false;
-                const uint32_t pos = lo_pos + (uint32_t)j;
-                if (pos < last) {
-                    const float4 gg = md.geo[j];
-                    const float2 g2 = md.geo2[j];
-                    float dx, dy, G, alpha;
-                    bool clamped;
-                    if (eval_alpha(ux, uy, a.W, gg, g2, dx, dy, G, alpha, clamped)) {
-                        contrib = true;
-                        const float nl = lg2(__fsub_rn(1.0f, alpha));
-                        const float logT_before = __fsub_rn(logT, nl);
-                        const float T = ex2(logT_before);
-                        const float w = T * alpha;
-                        const float reG = v[3 * j], imG = v[3 * j + 1], imF = v[3 * j + 2];
-                        const float amp = md.amp[j];
-                        const float reGa = amp * reG;
-                        const float dalpha = T * reGa - suffix / (1.0f - alpha);
-                        suffix = fmaf(w, reGa, suffix);
-                        gr[6] = w * reG;
-                        gr[7] = -w * amp * imG;
-                        gr[8] = w * amp * (c_f0 * imG + c_df * imF);
-                        if (!clamped) {
-                            const float sig = g2.y;
-                            gr[5] = dalpha * G;
-                            const float dq = -0.5f * dalpha * sig * G;
-                            gr[0] = dq * (-2.0f * (gg.z * dx + gg.w * dy));
-                            gr[1] = dq * (-2.0f * (gg.w * dx + g2.x * dy));
-                            gr[2] = dq * dx * dx;
-                            gr[3] = dq * 2.0f * dx * dy;
-                            gr[4] = dq * dy * dy;
+                    for (int c = 0; c < 9; ++c) gr[c] = 0.f;
+                    bool contrib = false;
+                    const uint32_t pos = lo_pos + (uint32_t)j;
+                    if (pos < last) {
+                        const float4 gg = mdp.geo[j];
+                        const float2 g2 = mdp.geo2[j];
+                        float dx, dy, G, alpha;
+                        bool clamped;
+                        if (eval_alpha(ux, uy, a.W, gg, g2, dx, dy, G, alpha, clamped)) {
+                            contrib = true;
+                            const float nl = lg2(__fsub_rn(1.0f, alpha));
+                            const float logT_before = __fsub_rn(logT, nl);
+                            const float T = ex2(logT_before);
+                            const float w = T * alpha;
+                            const float reG = v[3 * j], imG = v[3 * j + 1], imF = v[3 * j + 2];
+                            const float amp = mdp.amp[j];
+                            const float reGa = amp * reG;
+                            const float dalpha = T * reGa - suffix / (1.0f - alpha);
+                            suffix = fmaf(w, reGa, suffix);
+                            gr[6] = w * reG;
+                            gr[7] = -w * amp * imG;
+                            gr[8] = w * amp * (c_f0 * imG + c_df * imF);
+                            if (!clamped) {
+                                const float sig = g2.y;
+                                gr[5] = dalpha * G;
+                                const float dq = -0.5f * dalpha * sig * G;
+                                gr[0] = dq * (-2.0f * (gg.z * dx + gg.w * dy));
+                                gr[1] = dq * (-2.0f * (gg.w * dx + g2.x * dy));
+                                gr[2] = dq * dx * dx;
+                                gr[3] = dq * 2.0f * dx * dy;
+                                gr[4] = dq * dy * dy;
+                            }
+                            logT = logT_before;
                         }
-                        logT = logT_before;
+                    }
+                    if (__any_sync(0xffffffffu, contrib)) {
+                        const float tot = warp_reduce_scatter9(gr, lane);
+                        if ((lane & 1) == 0 && (lane >> 1) < 9) s_red[warp][j][lane >> 1] = tot;
+                    } else if (lane < 9) {
+                        s_red[warp][j][lane] = 0.f;
                     }
                 }
-                if (__any_sync(0xffffffffu, contrib)) {
-                    const float tot = warp_reduce_scatter9(gr, lane);
-                    if ((lane & 1) == 0 && (lane >> 1) < 9) s_red[warp][j][lane >> 1] = tot;
-                } else if (lane < 9) {
-                    s_red[warp][j][lane] = 0.f;
-                }
             }
-            tc_fence_before();
-            __syncthreads();
-            for (int e = tid; e < nb * 9; e += kThreads) {
+        }
+        tc_fence_before();
+        if (__syncthreads_or(!wok)) {   // an expired wait: stop without flushing
+            ok = false;
+            break;
+        }
+        if (pi >= 0) {
+            for (int e = tid; e < nbp * 9; e += kThreads) {
                 const int j = e / 9, c = e - j * 9;
                 float acc = 0.f;
 #pragma unroll
                 for (int w2 = 0; w2 < kThreads / 32; ++w2)
                     if ((s_wmask[w2] >> j) & 1ull) acc += s_red[w2][j][c];
                 if (acc != 0.f) {
-                    const uint32_t gid = md.gid[j];
+                    const uint32_t gid = mdp.gid[j];
                     if (c >= 5) {
                         float* dst = reinterpret_cast<float*>(&a.d_attr[(size_t)b * a.N + gid]);
                         const int slot = c == 5 ? 2 : (c == 6 ? 0 : (c == 7 ? 1 : 3));
@@ -1168,9 +1205,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_bwd_tc(RenderArgs a) {
                     }
                 }
             }
-            __syncthreads();
         }
     }
+    (void)ok;
     // drain a batch whose MMAs were issued but not consumed (only after an expired wait)
     tc_fence_before();
     __syncthreads();
