@@ -174,6 +174,18 @@ def run_ours(args, rank, world, local_rank):
     ev = {}
     render_fwd = G.gsparc_render_fwd_tc if args.render == "tc" else G.gsparc_render_fwd
     render_bwd = G.gsparc_render_bwd_tc if args.render == "tc" else G.gsparc_render_bwd
+    # the tensor-core configuration runs the attribute network forward and backward on the tensor
+    # cores as well (split-BF16, the same products in both, so the ReLU masks agree)
+    mlp_tc = args.render == "tc" and hidden in (16, 32)
+    mlp_prec = G.GSPARC_BF16X2 if mlp_tc else G.GSPARC_FP32
+
+    def mlp_bwd(scene):
+        if mlp_tc:
+            G.gsparc_attr_mlp_bwd_tc(txd, r.rx, scene.means, scene.opacity_logit, scene.latent, mlp_s,
+                                     G.GSPARC_BF16X2, d_attr, grads[0], grads[3], grads[4], grad_s)
+        else:
+            G.gsparc_attr_mlp_bwd(txd, r.rx, scene.means, scene.opacity_logit, scene.latent, mlp_s,
+                                  d_attr, grads[0], grads[3], grads[4], grad_s)
 
     def stage(name, fn):
         if name in ev:
@@ -189,15 +201,13 @@ def run_ours(args, rank, world, local_rank):
         stage("bin_sort", lambda: G.gsparc_bin_sort(r.view, n, r.proj, r.capacity, r.ws, r.sorted_ids,
                                                     None, r.tile_ranges, r.n_pairs, r.status))
         stage("attr_mlp", lambda: G.gsparc_attr_mlp(txd, r.rx, scene.means, scene.opacity_logit,
-                                                    scene.latent, mlp_s, G.GSPARC_FP32, attr))
+                                                    scene.latent, mlp_s, mlp_prec, attr))
         stage("render_fwd", lambda: render_fwd(r.view, r.band, B, n, r.proj, r.tile_ranges,
                                                r.sorted_ids, attr, spec, logT, nc, n_used))
         stage("l2_loss", lambda: G.gsparc_l2_loss(spec, tgt, loss, d_spec))
         stage("render_bwd", lambda: render_bwd(r.view, r.band, B, n, r.proj, r.tile_ranges,
                                                r.sorted_ids, attr, logT, nc, d_spec, d_attr, d_proj))
-        stage("attr_mlp_bwd", lambda: G.gsparc_attr_mlp_bwd(txd, r.rx, scene.means, scene.opacity_logit,
-                                                            scene.latent, mlp_s, d_attr, grads[0],
-                                                            grads[3], grads[4], grad_s))
+        stage("attr_mlp_bwd", lambda: mlp_bwd(scene))
         stage("project_bwd", lambda: G.gsparc_project_bwd(r.view, scene.means, scene.log_scales,
                                                           scene.quats, d_proj, grads[0], grads[1],
                                                           grads[2]))
@@ -329,6 +339,8 @@ def run_ours(args, rank, world, local_rank):
                    "compositing": "subcarrier sums on tensor cores (split-BF16 products, FP32 "
                                   "accumulation), transmittance and gradients FP32"
                                   if args.render == "tc" else "FP32 CUDA cores",
+                   "attribute_network": "tensor cores, split-BF16 products, FP32 accumulation "
+                                        "(forward and backward)" if mlp_tc else "FP32 CUDA cores",
                    "parallelism": "replicas x%d" % world},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "min": sorted_ms[0]},
@@ -502,7 +514,7 @@ def run_train(args):
            "higher_is_better": True, "steps": steps, "warmup": args.warmup,
            "config": {"workload": "training: 100k Gaussians fit to a 20k-Gaussian scene, 2000 training "
                                   "transmitters, batch 4, 128 subcarriers, 360x90, hidden 32",
-                      "network": "split-BF16 tensor cores forward, FP32 backward, FP32 master weights",
+                      "network": "split-BF16 tensor cores forward and backward, FP32 master weights",
                       "compositing_fwd": "tensor cores"},
            "heldout_rel_error": {"before": e0, "after": e1, "transmitters": 200},
            "loss_trace": losses}

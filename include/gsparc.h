@@ -213,6 +213,25 @@ int gsparc_attr_mlp_bwd(int32_t N, int32_t B, const float* tx, const float* rx, 
                         float* d_latent, const gsparc_mlp_grad* grads, void* stream);
 
 /*
+ * gsparc_attr_mlp_bwd with the network's matrix products on the tensor cores
+ * (Algorithm 1 Backprop through the network; same arguments plus precision,
+ * same accumulation into the outputs).  Per tile of 128 rows the forward
+ * recompute h0 W1, h1 W2 and the input gradients du2 W2^T, du1 W1^T are
+ * tcgen05 products, and the weight and bias gradients are one product over
+ * the rows, [h0 | h1 | h2 | 1]^T [du1 | du2 | dL/do], accumulated in tensor
+ * memory over all the tiles of a thread block.  Operands are split into two
+ * BF16 terms (three products, ~16-bit operands), accumulation is FP32.
+ *   precision: GSPARC_BF16X2 (the only form).  mlp->hidden: 16 or 32; other
+ *   widths return GSPARC_ERR_INVALID (use gsparc_attr_mlp_bwd).
+ *   An expired wait on the tensor cores writes NaN into grads->b3[0].
+ */
+int gsparc_attr_mlp_bwd_tc(int32_t N, int32_t B, const float* tx, const float* rx, const float* means,
+                           const float* opacity_logit, const float* latent, const gsparc_mlp* mlp,
+                           int32_t precision, const float* d_attr, float* d_means,
+                           float* d_opacity_logit, float* d_latent, const gsparc_mlp_grad* grads,
+                           void* stream);
+
+/*
  * Front-to-back compositing of complex contributions across subcarriers
  * (Sec. 4.2 compositing rule; Algorithm 1 inner loop): for every pixel u and
  * subcarrier k of every transmitter b,

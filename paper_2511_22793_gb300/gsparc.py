@@ -32,7 +32,7 @@ PROJ_STRIDE = 8
 
 EXPORTS = [
     "gsparc_num_tiles", "gsparc_project", "gsparc_project_bwd", "gsparc_bin_sort_workspace",
-    "gsparc_bin_sort", "gsparc_bin_sort_noalloc", "gsparc_attr_mlp", "gsparc_attr_mlp_bwd", "gsparc_render_fwd",
+    "gsparc_bin_sort", "gsparc_bin_sort_noalloc", "gsparc_attr_mlp", "gsparc_attr_mlp_bwd", "gsparc_attr_mlp_bwd_tc", "gsparc_render_fwd",
     "gsparc_render_fwd_tc", "gsparc_render_bwd", "gsparc_render_bwd_tc", "gsparc_l2_loss", "gsparc_adam", "gsparc_check", "gsparc_strerror",
 ]
 
@@ -87,6 +87,8 @@ def lib():
             "gsparc_attr_mlp": (ctypes.c_int, [i32, i32, vp, P(f32), vp, vp, vp, P(MLP), i32, vp, vp]),
             "gsparc_attr_mlp_bwd": (ctypes.c_int, [i32, i32, vp, P(f32), vp, vp, vp, P(MLP), vp, vp,
                                                    vp, vp, P(MLPGrad), vp]),
+            "gsparc_attr_mlp_bwd_tc": (ctypes.c_int, [i32, i32, vp, P(f32), vp, vp, vp, P(MLP), i32, vp,
+                                                      vp, vp, vp, P(MLPGrad), vp]),
             "gsparc_render_fwd": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
                                                  vp, vp, vp]),
             "gsparc_render_fwd_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
@@ -216,6 +218,14 @@ def gsparc_attr_mlp_bwd(tx, rx, means, opacity_logit, latent, mlp: MLP, d_attr, 
     rxa = (ctypes.c_float * 3)(*[float(v) for v in rx])
     _call("gsparc_attr_mlp_bwd", means.shape[0], tx.shape[0], _p(tx), rxa, _p(means),
           _p(opacity_logit), _p(latent), ctypes.byref(mlp), _p(d_attr), _p(d_means),
+          _p(d_opacity_logit), _p(d_latent), ctypes.byref(grads), _stream(stream))
+
+
+def gsparc_attr_mlp_bwd_tc(tx, rx, means, opacity_logit, latent, mlp: MLP, precision, d_attr, d_means,
+                           d_opacity_logit, d_latent, grads: MLPGrad, stream=None):
+    rxa = (ctypes.c_float * 3)(*[float(v) for v in rx])
+    _call("gsparc_attr_mlp_bwd_tc", means.shape[0], tx.shape[0], _p(tx), rxa, _p(means),
+          _p(opacity_logit), _p(latent), ctypes.byref(mlp), int(precision), _p(d_attr), _p(d_means),
           _p(d_opacity_logit), _p(d_latent), ctypes.byref(grads), _stream(stream))
 
 

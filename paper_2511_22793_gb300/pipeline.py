@@ -136,10 +136,16 @@ class Renderer:
            d_spec, d_attr, d_proj, stream)
 
     def attributes_backward(self, scene, mlp, tx, d_attr, d_means, d_ologit, d_latent, d_weights,
-                            stream=None):
-        G.gsparc_attr_mlp_bwd(tx, self.rx, scene.means, scene.opacity_logit, scene.latent,
-                              mlp.struct(), d_attr, d_means, d_ologit, d_latent,
-                              G.make_mlp_grad(*d_weights), stream)
+                            stream=None, tensor_cores=False):
+        """tensor_cores: the tcgen05 form (split-BF16 products, hidden 16 or 32)."""
+        if tensor_cores:
+            G.gsparc_attr_mlp_bwd_tc(tx, self.rx, scene.means, scene.opacity_logit, scene.latent,
+                                     mlp.struct(), G.GSPARC_BF16X2, d_attr, d_means, d_ologit, d_latent,
+                                     G.make_mlp_grad(*d_weights), stream)
+        else:
+            G.gsparc_attr_mlp_bwd(tx, self.rx, scene.means, scene.opacity_logit, scene.latent,
+                                  mlp.struct(), d_attr, d_means, d_ologit, d_latent,
+                                  G.make_mlp_grad(*d_weights), stream)
 
     def project_backward(self, scene, d_proj, d_means, d_log_scales, d_quats, stream=None):
         G.gsparc_project_bwd(self.view, scene.means, scene.log_scales, scene.quats, d_proj, d_means,

@@ -131,7 +131,8 @@ class Trainer:
                                tensor_cores=self.tensor_cores)
         g = self.grads
         self.r.attributes_backward(self.scene, self.mlp, self.tx, self.d_attr, g["means"],
-                                   g["opacity_logit"], g["latent"], [g[k] for k in MLP_KEYS])
+                                   g["opacity_logit"], g["latent"], [g[k] for k in MLP_KEYS],
+                                   tensor_cores=self.tensor_cores and self.mlp.hidden in (16, 32))
         self.r.project_backward(self.scene, self.d_proj, g["means"], g["log_scales"], g["quats"])
         self.step_count += 1
         for k, p in self.params.items():
