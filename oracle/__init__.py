@@ -16,7 +16,9 @@ Contents, each following the passage of the paper it cites:
                   subcarriers and its analytic gradient (Sec. 4.2 compositing
                   rule; Algorithm 1 inner loop)
   render.py       ctypes wrapper of render_oracle.c
-  pipeline.py     the whole forward pass, the L2 loss and the full gradient
+  csi.py          spatial-mean CSI head (Eq. 2), channel loss (Eq. 3), NMSE
+  pipeline.py     the whole forward pass, the L2 or channel loss and the full
+                  gradient
   adam.py         the Adam update (Algorithm 1, Adam step)
 
 Readings of points the paper leaves open are listed in each module header.

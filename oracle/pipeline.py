@@ -8,7 +8,8 @@ attribute network for each transmitter (attributes.py), render every
 requested pixel with the per-pixel FP64 renderer (render_oracle.c).
 
 Loss: mean over transmitters, pixels and subcarriers of |z - z_target|^2
-(complex L2; the workloads use it in place of the paper's L1+SSIM, Eq. 4).
+(complex L2; the workloads use it in place of the paper's L1+SSIM, Eq. 4), or
+the channel loss of the spatial-mean CSI head (Eq. 2, Eq. 3; csi.py).
 
 Gradient: the renderer's analytic FP64 gradient (render_oracle.c) chained by
 autograd through the float64 projection and attribute network.
@@ -19,6 +20,7 @@ import numpy as np
 import torch
 
 from . import attributes as _attr
+from . import csi as _csi
 from . import projection as _proj
 from . import render as _render
 
@@ -61,8 +63,11 @@ def forward(scene, mlp, view, band, tx, pixels=None, exact=False, threads=0):
     return dict(z=np.stack(zs), T=np.stack(Ts), n_used=np.stack(ns), geo=geo, attrs=attrs)
 
 
-def loss_and_grad(scene, mlp, view, band, tx, target, pixels=None, threads=0):
+def loss_and_grad(scene, mlp, view, band, tx, target, pixels=None, threads=0, loss_kind="l2"):
     """L2 loss against target [B, npix, K] complex and the FP64 gradient.
+
+    loss_kind "csi": the channel loss (Eq. 3) of the spatial-mean estimate (Eq. 2) against
+    target [B, K] complex (full images only); grads['h'] holds the estimate.
 
     Returns (loss, grads) with grads a dict keyed like the inputs: means,
     log_scales, quats, opacity_logit, latent, W1, b1, W2, b2, W3, b3.
@@ -85,10 +90,17 @@ def loss_and_grad(scene, mlp, view, band, tx, target, pixels=None, threads=0):
                                      band.df, pixels=pixels, threads=threads)
         zs.append(z)
     z = np.stack(zs)
-    M = z.size
-    diff = z - target
-    loss = float(np.sum(diff.real ** 2 + diff.imag ** 2) / M)
-    gz = 2.0 * diff / M
+    h_hat = None
+    if loss_kind == "csi":
+        assert pixels is None
+        h_hat = _csi.csi_head(z, view.H, view.W)
+        loss, d_h = _csi.channel_loss(h_hat, target)
+        gz = _csi.csi_head_bwd(d_h, view.H, view.W)
+    else:
+        M = z.size
+        diff = z - target
+        loss = float(np.sum(diff.real ** 2 + diff.imag ** 2) / M)
+        gz = 2.0 * diff / M
     d_geo = np.zeros((len(g["px"]), 5))
     outs, grads_out = [], []
     for b in range(B):
@@ -106,6 +118,8 @@ def loss_and_grad(scene, mlp, view, band, tx, target, pixels=None, threads=0):
     for nm, p in zip(names + wnames, params + weights):
         grads[nm] = p.grad.numpy().copy() if p.grad is not None else np.zeros(p.shape)
     grads["z"] = z
+    if h_hat is not None:
+        grads["h"] = h_hat
     return loss, grads
 
 
