@@ -478,6 +478,74 @@ def run_batched(args):
     print(json.dumps(out))
 
 
+def run_csi(args):
+    """CSI queries (Eq. 2): the 64-subcarrier channel estimate at unseen transmitter positions,
+    50k Gaussians, 360x90, hidden 32, 16 transmitters per launch, receiver fixed (geometry
+    cached).  The tensor-core forward with the spatial mean fused into its epilogue (no
+    spectrum written) against the same forward writing the spectrum and gsparc_csi_head
+    reducing it."""
+    import torch
+
+    from paper_2511_22793_gb300 import gsparc as G
+    from paper_2511_22793_gb300 import synth
+    from paper_2511_22793_gb300.pipeline import DeviceMLP, DeviceScene, Renderer
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n, B, K, H, W, hd = 50_000, 16, 64, 90, 360, 32
+    sc = synth.make_scene(n, seed=0)
+    mlp = synth.make_mlp(hd, seed=3)
+    tx = torch.tensor(synth.make_tx(B, seed=2), device=dev)
+    r = Renderer(H, W, K, n, device=dev)
+    ds = DeviceScene.from_host(sc, dev)
+    dm = DeviceMLP.from_host(mlp, dev)
+    r.geometry(ds)
+    assert r.check() == 0
+    attr = torch.empty((B, n, 4), device=dev)
+    csi_f = torch.empty((B, K, 2), device=dev)
+    csi_u = torch.empty((B, K, 2), device=dev)
+    out = r.alloc_outputs(B)
+    stream = torch.cuda.current_stream(dev)
+
+    def fused():
+        r.attributes(ds, dm, tx, G.GSPARC_BF16X2, out=attr)
+        r.render_csi(attr, csi=csi_f)
+
+    def unfused():
+        r.attributes(ds, dm, tx, G.GSPARC_BF16X2, out=attr)
+        r.render(attr, out=out, tensor_cores=True)
+        G.gsparc_csi_head(out[0], csi_u, 1.0 / (H * W))
+
+    res = {}
+    reps = max(10, min(args.steps, 200))
+    for name, fn in (("fused_csi_head", fused), ("spectrum_then_csi_head", unfused)):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms_per_launch": ms, "queries_per_s": B / (ms * 1e-3)}
+    assert r.check() == 0
+    a, b = csi_f.double(), csi_u.double()
+    agree = float((a - b).norm() / b.norm())
+    out_line = {"metric": "CSI queries/s (64-subcarrier channel estimates)",
+                "value": res["fused_csi_head"]["queries_per_s"], "unit": "queries/s", "n_gpus": 1,
+                "higher_is_better": True, "dtype": "bf16x2 network and subcarrier sums, f32 accumulation",
+                "data": "synthetic (seeded)",
+                "config": {"workload": "CSI queries, 50k Gaussians, 16 transmitters per launch, 64 subcarriers, "
+                                       "360x90, hidden 32, geometry cached",
+                           "spectrum_bytes_not_written": B * K * H * W * 8},
+                "forms": res, "fused_vs_unfused_rel_l2": agree,
+                "speedup_vs_unfused": res["spectrum_then_csi_head"]["ms_per_launch"] / res["fused_csi_head"]["ms_per_launch"]}
+    print(json.dumps(out_line))
+
+
 def run_train(args):
     """Training loop: 100,000 Gaussians fitted to spectra of a 20,000-Gaussian ground-truth scene
     at 2,000 training transmitters (uniform in the cube), 128 subcarriers, 360x90, hidden 32,
@@ -671,9 +739,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--render", default="tc", choices=["tc", "fp32"],
                     help="forward compositing: tcgen05 (default) or FP32 CUDA cores")
-    ap.add_argument("--workload", default="fwdbwd", choices=["fwdbwd", "batched", "train", "serve"],
+    ap.add_argument("--workload", default="fwdbwd", choices=["fwdbwd", "batched", "train", "serve", "csi"],
                     help="fwdbwd: the default step; batched: 64-transmitter inference with the "
-                         "tensor-core network against the plain one-query path")
+                         "tensor-core network against the plain one-query path; train: the training "
+                         "loop; serve: the continuous-batching query server; csi: channel-estimate "
+                         "queries with the fused CSI head")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -688,6 +758,10 @@ def main():
     if args.workload == "batched":
         if rank == 0:
             run_batched(args)
+        return
+    if args.workload == "csi":
+        if rank == 0:
+            run_csi(args)
         return
     if args.workload == "train":
         if rank == 0:

@@ -307,6 +307,48 @@ int gsparc_l2_loss(int64_t count, const float* z, const float* target, float* lo
                    void* stream);
 
 /*
+ * CSI head (Sec. 4.2 "Rendered Spectrum", Eq. 2): the complex channel
+ * estimate of each (transmitter, subcarrier) is the spatial mean of its
+ * spectrum plane, csi[b,k] = scale * sum_p spectrum[b,k,p] (scale = 1/(H W)
+ * for the mean).
+ *   spectrum [B,K,P,2] (complex, interleaved; P = H*W pixels); csi [B,K,2]
+ *   out (overwritten).  B*K < 65536.  Blocks add partial sums atomically:
+ *   the result may differ in the last bits from run to run.
+ */
+int gsparc_csi_head(int32_t B, int32_t K, int64_t P, const float* spectrum, float scale, float* csi,
+                    void* stream);
+
+/*
+ * Channel loss (Eq. 3, the squared error of the real and imaginary parts),
+ * averaged over the B*K (transmitter, subcarrier) entries:
+ *   loss [1] = mean |csi - target|^2 (overwritten); d_csi [B,K,2] out, may be
+ *   NULL: 2 (csi - target) / (B K) (overwritten).
+ */
+int gsparc_csi_loss(int32_t B, int32_t K, const float* csi, const float* target, float* loss,
+                    float* d_csi, void* stream);
+
+/*
+ * Gradient of gsparc_csi_head: d_spectrum[b,k,p] = scale * d_csi[b,k] at every
+ * pixel p (overwritten).  d_csi [B,K,2]; d_spectrum [B,K,P,2].
+ */
+int gsparc_csi_head_bwd(int32_t B, int32_t K, int64_t P, const float* d_csi, float scale,
+                        float* d_spectrum, void* stream);
+
+/*
+ * gsparc_render_fwd_tc with the CSI head fused into its epilogue: every
+ * thread block sums its tile's pixels of each subcarrier and adds 1/(H W)
+ * of it to csi [B,K,2] (overwritten: the call clears it first).  spectrum may
+ * be NULL, and then the spectrum is never written (8 B per pixel, subcarrier
+ * and transmitter saved) -- the form a CSI query at an unseen position needs.
+ * final_logT, n_contrib, n_used as gsparc_render_fwd (each may be NULL).
+ * Atomic partial sums: the last bits may differ from run to run.
+ */
+int gsparc_render_csi_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
+                         const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
+                         const float* attr, float* csi, float* spectrum, float* final_logT,
+                         uint32_t* n_contrib, uint32_t* n_used, void* stream);
+
+/*
  * Adam step (Algorithm 1 "Adam"): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
  * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps), in place over
  * n FP32 elements.  step >= 1.

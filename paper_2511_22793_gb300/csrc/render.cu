@@ -50,6 +50,8 @@ struct RenderArgs {
     const float2* d_spectrum;
     float4* d_attr;         // [B][N]
     float* d_proj;          // [N][8]
+    float2* csi;            // [B][K] spatial-mean accumulator (fused CSI head), or null
+    float csi_scale;        // 1 / HW
     // cycles of subcarrier k = L * (lam0_hi + lam0_lo + k * dlam), lam = f / c
     float lam0_hi, lam0_lo, dlam;
     // d(psi)/dL = -2 pi f_k / c, split as c_f0 + kk * c_df inside a strip
@@ -567,7 +569,8 @@ struct RTcSmem {
     static constexpr int kAmp = kExt + 2 * kTcE * 8;          // float[2][E]
     static constexpr int kPhi = kAmp + 2 * kTcE * 4;
     static constexpr int kLen = kPhi + 2 * kTcE * 4;
-    static constexpr int kBar = kLen + 2 * kTcE * 4;          // 2 mbarriers + TMEM slot
+    static constexpr int kCsi = kLen + 2 * kTcE * 4;          // float[8 warps][2S]: CSI partial sums
+    static constexpr int kBar = kCsi + 8 * 2 * S * 4;         // 2 mbarriers + TMEM slot
     static constexpr int kTotal = kBar + 32;
     static constexpr uint32_t kCols = (4 * S <= 32) ? 32 : (4 * S <= 64 ? 64 : (4 * S <= 128 ? 128 : 256));
 };
@@ -589,6 +592,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
     const int k0 = strip * S;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int half = tid >> 7, m = tid & 127;
+    float* s_csi = reinterpret_cast<float*>(sm + L::kCsi);   // [warp][2S], every slot written once
     // gather of one batch's per-entry records into registers (threads tid < E), and its
     // publication into one of the two record buffers
     uint32_t pf_gid = 0xffffffffu;
@@ -799,7 +803,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
 #pragma unroll
             for (int q = 0; q < 16; ++q) v[q] = 0.f;
         }
-        if (inside) {
+        if (inside && a.spectrum) {
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int k = k0 + c / 2 + q;
@@ -810,6 +814,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
                 }
             }
         }
+        if (a.csi) {
+            // Eq. 2 over the CTA's pixels: a reduce-scatter of the 16 columns over the warp's 32
+            // pixels leaves column idx(lane) summed in the lane pair (lane, lane ^ 1)
+            float w[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) w[q] = inside ? (ok ? v[q] : __int_as_float(0x7fc00000)) : 0.f;
+            const int ln = tid & 31;
+#pragma unroll
+            for (int o = 16, n = 8; o >= 2; o >>= 1, n >>= 1) {
+                const bool up = (ln & o) != 0;
+#pragma unroll
+                for (int q = 0; q < n; ++q) {
+                    const float send = up ? w[q] : w[q + n];
+                    const float keep = up ? w[q + n] : w[q];
+                    w[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                }
+            }
+            w[0] += __shfl_xor_sync(0xffffffffu, w[0], 1);
+            const int idx = ((ln >> 4) & 1) * 8 + ((ln >> 3) & 1) * 4 + ((ln >> 2) & 1) * 2 + ((ln >> 1) & 1);
+            if ((ln & 1) == 0) s_csi[warp * 2 * S + c + idx] = w[0];
+        }
     }
     if (inside && strip == 0) {
         if (a.final_logT) a.final_logT[(size_t)b * plane + pix] = logT;
@@ -818,6 +843,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
     }
     tc_fence_before();
     __syncthreads();
+    if (a.csi) {
+        for (int e = tid; e < 2 * S; e += kThreads) {
+            const int k = k0 + e / 2;
+            float sum = 0.f;
+#pragma unroll
+            for (int w2 = 0; w2 < kThreads / 32; ++w2) sum += s_csi[w2 * 2 * S + e];
+            if (k < a.K) atomicAdd(reinterpret_cast<float*>(&a.csi[(size_t)b * a.K + k]) + (e & 1), sum * a.csi_scale);
+        }
+    }
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(L::kCols) : "memory");
@@ -851,6 +885,30 @@ extern "C" int gsparc_render_fwd_tc(const gsparc_view* view, const gsparc_band* 
     a.n_used = n_used;
     const int T = tiles_x(*view) * tiles_y(*view);
     cudaStream_t s = as_stream(stream);
+    if (band->K <= 8) return launch_fwd_tc<8>(a, T, s);
+    if (band->K <= 16) return launch_fwd_tc<16>(a, T, s);
+    if (band->K <= 32) return launch_fwd_tc<32>(a, T, s);
+    return launch_fwd_tc<64>(a, T, s);
+}
+
+extern "C" int gsparc_render_csi_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
+                                    const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
+                                    const float* attr, float* csi, float* spectrum, float* final_logT,
+                                    uint32_t* n_contrib, uint32_t* n_used, void* stream) {
+    using namespace gsparc;
+    if (!common_ok(view, band, B, N, proj, tile_ranges, sorted_ids, attr) || !csi) return GSPARC_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(spectrum) | reinterpret_cast<uintptr_t>(csi)) & 7) return GSPARC_ERR_INVALID;
+    RenderArgs a{};
+    fill_args(view, band, B, N, proj, tile_ranges, sorted_ids, attr, a);
+    a.spectrum = reinterpret_cast<float2*>(spectrum);
+    a.final_logT = final_logT;
+    a.n_contrib = n_contrib;
+    a.n_used = n_used;
+    a.csi = reinterpret_cast<float2*>(csi);
+    a.csi_scale = 1.0f / ((float)view->H * (float)view->W);
+    const int T = tiles_x(*view) * tiles_y(*view);
+    cudaStream_t s = as_stream(stream);
+    if (cudaMemsetAsync(csi, 0, (size_t)B * band->K * 2 * sizeof(float), s) != cudaSuccess) return GSPARC_ERR_CUDA;
     if (band->K <= 8) return launch_fwd_tc<8>(a, T, s);
     if (band->K <= 16) return launch_fwd_tc<16>(a, T, s);
     if (band->K <= 32) return launch_fwd_tc<32>(a, T, s);

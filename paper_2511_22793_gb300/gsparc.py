@@ -32,8 +32,10 @@ PROJ_STRIDE = 8
 
 EXPORTS = [
     "gsparc_num_tiles", "gsparc_project", "gsparc_project_bwd", "gsparc_bin_sort_workspace",
-    "gsparc_bin_sort", "gsparc_bin_sort_noalloc", "gsparc_attr_mlp", "gsparc_attr_mlp_bwd", "gsparc_attr_mlp_bwd_tc", "gsparc_render_fwd",
-    "gsparc_render_fwd_tc", "gsparc_render_bwd", "gsparc_render_bwd_tc", "gsparc_l2_loss", "gsparc_adam", "gsparc_check", "gsparc_strerror",
+    "gsparc_bin_sort", "gsparc_bin_sort_noalloc", "gsparc_attr_mlp", "gsparc_attr_mlp_bwd",
+    "gsparc_attr_mlp_bwd_tc", "gsparc_render_fwd", "gsparc_render_fwd_tc", "gsparc_render_bwd",
+    "gsparc_render_bwd_tc", "gsparc_l2_loss", "gsparc_csi_head", "gsparc_csi_loss", "gsparc_csi_head_bwd",
+    "gsparc_render_csi_tc", "gsparc_adam", "gsparc_check", "gsparc_strerror",
 ]
 
 
@@ -98,6 +100,11 @@ def lib():
             "gsparc_render_bwd_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
                                                     vp, vp, vp, vp]),
             "gsparc_l2_loss": (ctypes.c_int, [i64, vp, vp, vp, vp, vp]),
+            "gsparc_csi_head": (ctypes.c_int, [i32, i32, i64, vp, f32, vp, vp]),
+            "gsparc_csi_loss": (ctypes.c_int, [i32, i32, vp, vp, vp, vp, vp]),
+            "gsparc_csi_head_bwd": (ctypes.c_int, [i32, i32, i64, vp, f32, vp, vp]),
+            "gsparc_render_csi_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
+                                                    vp, vp, vp, vp]),
             "gsparc_adam": (ctypes.c_int, [i64, vp, vp, vp, vp, f32, f32, f32, f32, i32, vp]),
             "gsparc_check": (ctypes.c_int, [vp, vp]),
             "gsparc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -260,6 +267,32 @@ def gsparc_render_bwd_tc(view, band, B, n, proj, tile_ranges, sorted_ids, attr, 
 def gsparc_l2_loss(z, target, loss, d_z=None, stream=None):
     count = z.numel() // 2
     _call("gsparc_l2_loss", count, _p(z), _p(target), _p(loss), _p(d_z), _stream(stream))
+
+
+def gsparc_csi_head(spectrum, csi, scale, stream=None):
+    """spectrum [B, K, H, W, 2] -> csi [B, K, 2] = scale * sum over pixels (Eq. 2 with 1/HW)."""
+    B, K = spectrum.shape[0], spectrum.shape[1]
+    P = spectrum.numel() // (2 * B * K)
+    _call("gsparc_csi_head", int(B), int(K), int(P), _p(spectrum), float(scale), _p(csi), _stream(stream))
+
+
+def gsparc_csi_loss(csi, target, loss, d_csi=None, stream=None):
+    B, K = csi.shape[0], csi.shape[1]
+    _call("gsparc_csi_loss", int(B), int(K), _p(csi), _p(target), _p(loss), _p(d_csi), _stream(stream))
+
+
+def gsparc_csi_head_bwd(d_csi, d_spectrum, scale, stream=None):
+    B, K = d_csi.shape[0], d_csi.shape[1]
+    P = d_spectrum.numel() // (2 * B * K)
+    _call("gsparc_csi_head_bwd", int(B), int(K), int(P), _p(d_csi), float(scale), _p(d_spectrum),
+          _stream(stream))
+
+
+def gsparc_render_csi_tc(view, band, B, n, proj, tile_ranges, sorted_ids, attr, csi, spectrum=None,
+                         final_logT=None, n_contrib=None, n_used=None, stream=None):
+    _call("gsparc_render_csi_tc", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
+          _p(tile_ranges), _p(sorted_ids), _p(attr), _p(csi), _p(spectrum), _p(final_logT), _p(n_contrib),
+          _p(n_used), _stream(stream))
 
 
 def gsparc_adam(param, grad, m, v, lr, step, b1=0.9, b2=0.999, eps=1e-15, stream=None):

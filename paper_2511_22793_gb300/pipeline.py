@@ -128,6 +128,20 @@ class Renderer:
            logT, nc, n_used, stream)
         return spec, logT, nc
 
+    def render_csi(self, attr, csi=None, out=None, n_used=None, stream=None):
+        """Spatial-mean channel estimate (Eq. 2) fused into the tensor-core forward.
+
+        csi [B, K, 2] out (allocated when None).  out: optional (spectrum, final_logT,
+        n_contrib) as render(); with out=None no spectrum is written at all (the state
+        buffers are skipped too).  Returns csi."""
+        B = int(attr.shape[0])
+        if csi is None:
+            csi = torch.empty((B, self.K, 2), dtype=torch.float32, device=self.device)
+        spec, logT, nc = out if out is not None else (None, None, None)
+        G.gsparc_render_csi_tc(self.view, self.band, B, self.n, self.proj, self.tile_ranges,
+                               self.sorted_ids, attr, csi, spec, logT, nc, n_used, stream)
+        return csi
+
     def render_backward(self, attr, logT, nc, d_spec, d_attr, d_proj, tensor_cores=False, stream=None):
         """Compositing gradient; tensor_cores selects gsparc_render_bwd_tc (same outputs)."""
         B = int(attr.shape[0])
