@@ -653,6 +653,32 @@ def run_serve(args):
     for q in burst_plain:
         q.spectrum = None
     out_rows.append({"load": "burst", "batched": latency_stats(burst), "plain": latency_stats(burst_plain)})
+    # moving receiver: every request carries its own pose (position in the cube, random heading),
+    # so its projection and bin/sort run per request; one burst, both paths
+    n_mov = min(n_req, 200)
+
+    def make_moving(n):
+        reqs = make(n)
+        for q in reqs:
+            rx = rng.uniform(-synth.CUBE_HALF, synth.CUBE_HALF, size=3)
+            yaw = rng.uniform(-np.pi, np.pi)
+            c, s_ = np.cos(yaw), np.sin(yaw)
+            q.rx = tuple(float(v) for v in rx)
+            q.V = (c, 0.0, s_, 0.0, 1.0, 0.0, -s_, 0.0, c)
+        return reqs
+
+    mov = make_moving(n_mov)
+    srv.done = []
+    srv.run(mov, np.zeros(n_mov))
+    torch.cuda.synchronize(dev)
+    for q in mov:
+        q.spectrum = None
+    mov_plain = [Request(q.rid, q.tx, q.res, q.K, rx=q.rx, V=q.V) for q in mov]
+    serve_plain(ds, dm, mov_plain, np.zeros(n_mov), res, device=dev)
+    for q in mov_plain:
+        q.spectrum = None
+    out_rows.append({"load": "burst, moving receiver", "requests": n_mov, "batched": latency_stats(mov),
+                     "plain": latency_stats(mov_plain)})
     out = {"metric": "query latency p50/p99 and spectra/s under Poisson load", "unit": "ms",
            "n_gpus": 1, "requests_per_load": n_req, "plain_saturated_spectra_per_s": sat,
            "config": {"workload": "serving: 500k-Gaussian resident scene, resolutions {180x45, 360x90, "

@@ -73,6 +73,7 @@ class Renderer:
     def __init__(self, H, W, K, n, f_c=2.4e9, df=312.5e3, rx=(0.0, 0.0, 0.0),
                  V=(1, 0, 0, 0, 1, 0, 0, 0, 1), near_dist=0.1, pair_capacity=None, device="cuda"):
         self.device = torch.device(device)
+        self.V, self.near = tuple(float(v) for v in V), float(near_dist)
         self.view = G.make_view(H, W, rx, V, near_dist)
         self.band = G.make_band(K, f_c, df)
         self.H, self.W, self.K, self.n = int(H), int(W), int(K), int(n)
@@ -89,7 +90,16 @@ class Renderer:
         ws = G.gsparc_bin_sort_workspace(self.view, self.n, self.capacity)
         self.ws = torch.empty(max(256, ws), dtype=torch.uint8, device=dev)
 
-    # -- query-independent geometry -------------------------------------------------
+    def set_receiver(self, rx, V=None):
+        """Move the receiver (position rx, world-to-receiver rotation V, row-major 3x3): the
+        next geometry() projects and bins for that pose (Sec. 4.2 "Directional Projection
+        and Splatting", receiver pose x_rx,i per sample)."""
+        if V is not None:
+            self.V = tuple(float(v) for v in V)
+        self.rx = tuple(float(v) for v in rx)
+        self.view = G.make_view(self.H, self.W, self.rx, self.V, self.near)
+
+    # -- receiver-dependent geometry (query-independent while the receiver stays) ----
     def geometry(self, scene: DeviceScene, keep_keys=False, stream=None):
         if keep_keys and self.sorted_keys is None:
             self.sorted_keys = torch.empty(max(1, self.capacity), dtype=torch.int64, device=self.device)

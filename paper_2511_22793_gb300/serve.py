@@ -1,11 +1,15 @@
 """Continuous-batching CSI query server over one resident scene.
 
-A request asks for the spectrum seen at the fixed receiver for one transmitter
+A request asks for the spectrum seen at a receiver for one transmitter
 position, at one of several hemisphere resolutions and subcarrier counts.  The
-scene stays resident on the device; its projection and bin/sort are computed
-once per resolution (the receiver is fixed, so the geometry does not depend on
-the query).  Per request the work is the attribute network and the
-compositing.
+scene stays resident on the device.  For the fixed receiver its projection and
+bin/sort are computed once per resolution (the geometry does not depend on the
+query) and per request the work is the attribute network and the compositing.
+A request may instead carry its own receiver pose (rx, and optionally the
+rotation V): the paper's moving-receiver setting, one pose per sample.  Its
+geometry is then computed for it, on its stream, into geometry buffers owned
+by that stream slot, and it runs alone (no other request shares its tile
+lists).
 
 Scheduling (`Server.poll`):
   * finished batches are detected with CUDA events (no host synchronisation)
@@ -21,7 +25,8 @@ A request that alone exceeds the budget is rejected.  Latency is measured from
 the request's arrival time to the host observing its batch's completion event.
 
 `serve_plain` is the baseline: one request at a time on one stream with the
-FP32 network and FP32 compositing.
+FP32 network and FP32 compositing (and, for a moving-receiver request, its
+geometry computed first).
 """
 from __future__ import annotations
 
@@ -46,6 +51,8 @@ class Request:
     t_done: float = -1.0
     spectrum: torch.Tensor | None = None   # [K, H, W, 2] on the device
     rejected: bool = False
+    rx: tuple | None = None                # receiver position of a moving-receiver request
+    V: tuple | None = None                 # its rotation (row-major 3x3), identity when None
 
 
 @dataclass
@@ -82,6 +89,13 @@ class Server:
             self.geom[(H, W)] = r
         self.bands = {}
         self.mlp_s = mlp.struct()
+        self.slot_geom = {}   # (slot, H, W) -> Renderer for moving-receiver requests
+
+    def _slot_renderer(self, slot, H, W):
+        key = (slot, H, W)
+        if key not in self.slot_geom:
+            self.slot_geom[key] = Renderer(H, W, 1, self.scene.n, f_c=self.f_c, df=self.df, device=self.dev)
+        return self.slot_geom[key]
 
     def request_bytes(self, H, W, K):
         return self.scene.n * 16 + K * H * W * 8 + H * W * 8
@@ -104,10 +118,17 @@ class Server:
         H, W = reqs[0].res
         K = reqs[0].K
         B = len(reqs)
-        r = self.geom[(H, W)]
         stream = self.streams[slot]
+        moving = reqs[0].rx is not None
+        if moving:
+            r = self._slot_renderer(slot, H, W)
+            r.set_receiver(reqs[0].rx, reqs[0].V if reqs[0].V is not None else (1, 0, 0, 0, 1, 0, 0, 0, 1))
+        else:
+            r = self.geom[(H, W)]
         nbytes = sum(self.request_bytes(H, W, K) for _ in reqs)
         with torch.cuda.stream(stream):
+            if moving:
+                r.geometry(self.scene, stream=stream)
             tx = torch.tensor([q.tx for q in reqs], dtype=torch.float32).pin_memory().to(self.dev,
                                                                                         non_blocking=True)
             attr = torch.empty((B, self.scene.n, 4), device=self.dev)
@@ -147,16 +168,19 @@ class Server:
             one = self.request_bytes(H, W, head.K)
             if self.used + one > self.budget:
                 break                                    # wait for memory to free up
-            group = []
-            rest = collections.deque()
-            while self.waiting:
-                q = self.waiting.popleft()
-                if (len(group) < self.max_batch and q.res == head.res and q.K == head.K
-                        and self.used + one * (len(group) + 1) <= self.budget):
-                    group.append(q)
-                else:
-                    rest.append(q)
-            self.waiting = rest
+            if head.rx is not None:
+                group = [self.waiting.popleft()]        # its own geometry: it runs alone
+            else:
+                group = []
+                rest = collections.deque()
+                while self.waiting:
+                    q = self.waiting.popleft()
+                    if (len(group) < self.max_batch and q.res == head.res and q.K == head.K
+                            and q.rx is None and self.used + one * (len(group) + 1) <= self.budget):
+                        group.append(q)
+                    else:
+                        rest.append(q)
+                self.waiting = rest
             self._launch(group, self.free_streams.pop())
         return not self.inflight and not self.waiting
 
@@ -193,6 +217,7 @@ def serve_plain(scene: DeviceScene, mlp: DeviceMLP, requests, arrivals, resoluti
     torch.cuda.synchronize(dev)
     mlp_s = mlp.struct()
     bands = {}
+    moving = {}
     t0 = time.perf_counter()
     order = np.argsort(arrivals)
     for idx in order:
@@ -202,7 +227,14 @@ def serve_plain(scene: DeviceScene, mlp: DeviceMLP, requests, arrivals, resoluti
         if now < q.t_arrival:
             time.sleep(q.t_arrival - now)
         H, W = q.res
-        r = geom[(H, W)]
+        if q.rx is not None:                       # moving receiver: its own geometry first
+            if (H, W) not in moving:
+                moving[(H, W)] = Renderer(H, W, 1, scene.n, f_c=f_c, df=df, device=dev)
+            r = moving[(H, W)]
+            r.set_receiver(q.rx, q.V if q.V is not None else (1, 0, 0, 0, 1, 0, 0, 0, 1))
+            r.geometry(scene)
+        else:
+            r = geom[(H, W)]
         if q.K not in bands:
             bands[q.K] = G.make_band(q.K, f_c, df)
         tx = torch.tensor([q.tx], dtype=torch.float32, device=dev)
