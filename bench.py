@@ -75,7 +75,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "25"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -85,6 +85,12 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def wait_first(self, timeout=3.0):
+        """Block until the first sample arrived (nvidia-smi takes a moment to start)."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -194,27 +200,65 @@ def run_ours(args, rank, world, local_rank):
         if name in ev:
             ev[name][1].record(stream)
 
-    def step(scene: DeviceScene, tgt):
+    side = torch.cuda.Stream(dev)
+
+    def step(scene: DeviceScene, tgt, concurrent=False):
+        """One training step.  concurrent: the attribute network runs on a side stream beside
+        projection and bin/sort (it needs neither), and the projection backward beside the
+        network backward (both only add into the gradients); used for the graph, while the
+        eager per-kernel timing keeps one stream."""
         gbuf.zero_()
+        cur = torch.cuda.current_stream(dev)   # the capture stream while a graph is captured
+        if concurrent:
+            fork = torch.cuda.Event()
+            fork.record(cur)
+            side.wait_event(fork)
+            G.gsparc_attr_mlp(txd, r.rx, scene.means, scene.opacity_logit, scene.latent, mlp_s, mlp_prec,
+                              attr, side)
+            joined = torch.cuda.Event()
+            joined.record(side)
         stage("project", lambda: G.gsparc_project(r.view, scene.means, scene.log_scales, scene.quats,
                                                   r.proj))
         stage("bin_sort", lambda: G.gsparc_bin_sort(r.view, n, r.proj, r.capacity, r.ws, r.sorted_ids,
                                                     None, r.tile_ranges, r.n_pairs, r.status))
-        stage("attr_mlp", lambda: G.gsparc_attr_mlp(txd, r.rx, scene.means, scene.opacity_logit,
-                                                    scene.latent, mlp_s, mlp_prec, attr))
-        stage("render_fwd", lambda: render_fwd(r.view, r.band, B, n, r.proj, r.tile_ranges,
-                                               r.sorted_ids, attr, spec, logT, nc, n_used))
-        stage("l2_loss", lambda: G.gsparc_l2_loss(spec, tgt, loss, d_spec))
+        if concurrent:
+            cur.wait_event(joined)
+        else:
+            stage("attr_mlp", lambda: G.gsparc_attr_mlp(txd, r.rx, scene.means, scene.opacity_logit,
+                                                        scene.latent, mlp_s, mlp_prec, attr))
+        if args.render == "tc":
+            # the loss fused into the forward's epilogue: it writes dL/dz, not the spectrum
+            stage("render_fwd", lambda: G.gsparc_render_fwd_l2_tc(r.view, r.band, B, n, r.proj, r.tile_ranges,
+                                                                  r.sorted_ids, attr, tgt, loss, d_spec, None,
+                                                                  logT, nc, n_used))
+        else:
+            stage("render_fwd", lambda: render_fwd(r.view, r.band, B, n, r.proj, r.tile_ranges,
+                                                   r.sorted_ids, attr, spec, logT, nc, n_used))
+            stage("l2_loss", lambda: G.gsparc_l2_loss(spec, tgt, loss, d_spec))
         stage("render_bwd", lambda: render_bwd(r.view, r.band, B, n, r.proj, r.tile_ranges,
                                                r.sorted_ids, attr, logT, nc, d_spec, d_attr, d_proj))
-        stage("attr_mlp_bwd", lambda: mlp_bwd(scene))
-        stage("project_bwd", lambda: G.gsparc_project_bwd(r.view, scene.means, scene.log_scales,
-                                                          scene.quats, d_proj, grads[0], grads[1],
-                                                          grads[2]))
+
+        def proj_bwd(s=None):
+            G.gsparc_project_bwd(r.view, scene.means, scene.log_scales, scene.quats, d_proj, grads[0],
+                                 grads[1], grads[2], s)
+
+        if concurrent:
+            fork2 = torch.cuda.Event()
+            fork2.record(cur)
+            side.wait_event(fork2)
+            proj_bwd(side)
+            joined2 = torch.cuda.Event()
+            joined2.record(side)
+            mlp_bwd(scene)
+            cur.wait_event(joined2)
+        else:
+            stage("attr_mlp_bwd", lambda: mlp_bwd(scene))
+            stage("project_bwd", proj_bwd)
 
     # kernels of ours launched per step: project 1, bin/sort 3 (count + scan, emit, per-tile
-    # sort), network 1, render 1, loss 1, render bwd 1, network bwd 1, projection bwd 1
-    launches_per_step = 1 + 3 + 1 + 1 + 1 + 1 + 1 + 1
+    # sort), network 1, render 1, loss 1 (fused into the tensor-core forward), render bwd 1,
+    # network bwd 1, projection bwd 1
+    launches_per_step = 1 + 3 + 1 + 1 + (1 if args.render != "tc" else 0) + 1 + 1 + 1
 
     for _ in range(args.warmup):
         step(ds, target)
@@ -228,8 +272,8 @@ def run_ours(args, rank, world, local_rank):
     dist = world > 1
     if dist:
         import torch.distributed as tdist
-    names = ["project", "bin_sort", "attr_mlp", "render_fwd", "l2_loss", "render_bwd", "attr_mlp_bwd",
-             "project_bwd"]
+    names = ["project", "bin_sort", "attr_mlp", "render_fwd"] + (["l2_loss"] if args.render != "tc" else []) + \
+        ["render_bwd", "attr_mlp_bwd", "project_bwd"]
     # per-kernel durations: eager steps with CUDA events around every stage (kernel time does not
     # depend on how it was launched); the headline times the whole step as one CUDA graph
     per_kernel = {k: [] for k in names}
@@ -245,7 +289,7 @@ def run_ours(args, rank, world, local_rank):
     # the step as one CUDA graph: the library only enqueues stream-ordered work, so it captures
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
-        step(ds, target)
+        step(ds, target, concurrent=True)
     for _ in range(3):
         graph.replay()
     torch.cuda.synchronize(dev)
@@ -257,6 +301,7 @@ def run_ours(args, rank, world, local_rank):
         tdist.barrier()
     torch.cuda.synchronize(dev)
     sampler.start()
+    sampler.wait_first()
     for _ in range(args.steps):
         flush.fill_(1.0)                      # evict L2 between timed steps (not timed)
         s0 = torch.cuda.Event(enable_timing=True)
@@ -267,7 +312,6 @@ def run_ours(args, rank, world, local_rank):
         s1.synchronize()
         step_ms.append(s0.elapsed_time(s1))
     torch.cuda.synchronize(dev)
-    clocks = sampler.stop()
     total_ms = sum(step_ms)
     if dist:
         t = torch.tensor([total_ms], device=dev)
@@ -298,6 +342,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.current_stream(dev).synchronize()
         if it >= args.warmup:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    clocks = sampler.stop()   # sampled over both timed regions (device-timed and end to end)
     if dist:
         t = torch.tensor([sum(e2e_ms)], device=dev)
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
@@ -348,7 +393,9 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_total / args.steps},
         "gpu_launches": launches_per_step * args.steps,
-        "launch": "whole step captured once as a CUDA graph, replayed per timed step",
+        "launch": "whole step captured once as a CUDA graph (network forward beside projection and "
+                  "bin/sort, projection backward beside network backward, on a second stream), "
+                  "replayed per timed step",
         "query_latency": latency,
         "roofline": roofline,
         "clocks": clocks,

@@ -118,8 +118,9 @@ int gsparc_project(const gsparc_view* view, int32_t N, const float* means, const
 /*
  * Gradient of gsparc_project (Sec. 4.2 map and Sigma'; Algorithm 1 Backprop).
  * d_proj [N,8] holds dL/d(p_x, p_y, -, -, c_xx, c_xy, c_yy, -) (slots 2, 3, 7
- * are ignored).  Accumulates into d_means [N,3], d_log_scales [N,3],
- * d_quats [N,4].
+ * are ignored).  Accumulates into d_means [N,3] (atomically: it may run
+ * concurrently with gsparc_attr_mlp_bwd(_tc), which also adds into d_means),
+ * d_log_scales [N,3], d_quats [N,4].
  */
 int gsparc_project_bwd(const gsparc_view* view, int32_t N, const float* means,
                        const float* log_scales, const float* quats, const float* d_proj,
@@ -343,6 +344,23 @@ int gsparc_csi_head_bwd(int32_t B, int32_t K, int64_t P, const float* d_csi, flo
  * final_logT, n_contrib, n_used as gsparc_render_fwd (each may be NULL).
  * Atomic partial sums: the last bits may differ from run to run.
  */
+/*
+ * gsparc_render_fwd_tc with the complex L2 loss of gsparc_l2_loss fused into its
+ * epilogue (the training step's loss, Algorithm 1; complex L2 in place of
+ * Eq. 4): with count = B*K*H*W,
+ *   loss [1] = mean |z - target|^2 (the call clears it first; blocks add
+ *   partial sums atomically, so the last bits may differ from run to run),
+ *   d_spectrum [B,K,H,W,2] out = 2 (z - target) / count, bit-identical to
+ *   gsparc_l2_loss on the spectrum gsparc_render_fwd_tc writes.
+ * spectrum may be NULL (then it is never written: training needs only the
+ * gradient); final_logT, n_contrib, n_used as gsparc_render_fwd.
+ */
+int gsparc_render_fwd_l2_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
+                            const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
+                            const float* attr, const float* target, float* loss, float* d_spectrum,
+                            float* spectrum, float* final_logT, uint32_t* n_contrib, uint32_t* n_used,
+                            void* stream);
+
 int gsparc_render_csi_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
                          const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
                          const float* attr, float* csi, float* spectrum, float* final_logT,

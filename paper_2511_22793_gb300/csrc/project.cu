@@ -240,10 +240,11 @@ __global__ void __launch_bounds__(256) k_project_bwd(ViewDev v, int N, const flo
         dx += gcap * g.cx;
         dz += gcap * g.cz;
     }
-    // x' = V (mu - rx): dmu = V^T dx'
-    d_means[3 * i + 0] += v.V[0] * dx + v.V[3] * dy + v.V[6] * dz;
-    d_means[3 * i + 1] += v.V[1] * dx + v.V[4] * dy + v.V[7] * dz;
-    d_means[3 * i + 2] += v.V[2] * dx + v.V[5] * dy + v.V[8] * dz;
+    // x' = V (mu - rx): dmu = V^T dx'; atomic, so that the attribute network's backward may add
+    // into the same gradient concurrently
+    atomicAdd(&d_means[3 * i + 0], v.V[0] * dx + v.V[3] * dy + v.V[6] * dz);
+    atomicAdd(&d_means[3 * i + 1], v.V[1] * dx + v.V[4] * dy + v.V[7] * dz);
+    atomicAdd(&d_means[3 * i + 2], v.V[2] * dx + v.V[5] * dy + v.V[8] * dz);
 }
 
 }  // namespace

@@ -52,6 +52,10 @@ struct RenderArgs {
     float* d_proj;          // [N][8]
     float2* csi;            // [B][K] spatial-mean accumulator (fused CSI head), or null
     float csi_scale;        // 1 / HW
+    const float2* l2_target;   // [B][K][H][W] (fused L2 loss), with:
+    float* l2_loss;            // [1] accumulator of mean |z - target|^2
+    float2* l2_grad;           // [B][K][H][W] out: 2 (z - target) / count, or null
+    float l2_inv;              // 1 / count
     // cycles of subcarrier k = L * (lam0_hi + lam0_lo + k * dlam), lam = f / c
     float lam0_hi, lam0_lo, dlam;
     // d(psi)/dL = -2 pi f_k / c, split as c_f0 + kk * c_df inside a strip
@@ -570,7 +574,8 @@ struct RTcSmem {
     static constexpr int kPhi = kAmp + 2 * kTcE * 4;
     static constexpr int kLen = kPhi + 2 * kTcE * 4;
     static constexpr int kCsi = kLen + 2 * kTcE * 4;          // float[8 warps][2S]: CSI partial sums
-    static constexpr int kBar = kCsi + 8 * 2 * S * 4;         // 2 mbarriers + TMEM slot
+    static constexpr int kL2 = kCsi + 8 * 2 * S * 4;          // float[8 warps]: loss partial sums
+    static constexpr int kBar = kL2 + 8 * 4;                  // 2 mbarriers + TMEM slot
     static constexpr int kTotal = kBar + 32;
     static constexpr uint32_t kCols = (4 * S <= 32) ? 32 : (4 * S <= 64 ? 64 : (4 * S <= 128 ? 128 : 256));
 };
@@ -787,13 +792,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
         if (st == 0) pend0 = true;
         else pend1 = true;
     }
+    const size_t plane = (size_t)a.H * a.W;
+    const size_t pix = (size_t)y * a.W + x;
+    // fused loss: this pixel's targets for the strip, all loads in flight before the last wait
+    float2 tg[S];
+    if (a.l2_grad) {
+#pragma unroll
+        for (int kk = 0; kk < S; ++kk) {
+            const int k = k0 + kk;
+            tg[kk] = (inside && k < a.K) ? __ldcs(a.l2_target + ((size_t)b * a.K + k) * plane + pix)
+                                         : make_float2(0.f, 0.f);
+        }
+    }
     bool wok = true;
     if (pend0) wok = mbar_wait(bar0, ph0) && wok;
     if (pend1) wok = mbar_wait(bar1, ph1) && wok;
     ok = __syncthreads_and(wok && ok) != 0;
     tc_fence_after();
-    const size_t plane = (size_t)a.H * a.W;
-    const size_t pix = (size_t)y * a.W + x;
+    float l2acc = 0.f;
 #pragma unroll
     for (int c = 0; c < 2 * S; c += 16) {
         float v[16];
@@ -811,6 +827,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
                     const float nan = __int_as_float(0x7fc00000);
                     a.spectrum[((size_t)b * a.K + k) * plane + pix] =
                         ok ? make_float2(v[2 * q], v[2 * q + 1]) : make_float2(nan, nan);
+                }
+            }
+        }
+        if (inside && a.l2_grad) {
+            // fused loss: the same arithmetic as gsparc_l2_loss on this spectrum
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = k0 + c / 2 + q;
+                if (k < a.K) {
+                    const size_t e = ((size_t)b * a.K + k) * plane + pix;
+                    const float2 t = tg[c / 2 + q];
+                    const float zr = ok ? v[2 * q] : __int_as_float(0x7fc00000);
+                    const float dr = zr - t.x, di = v[2 * q + 1] - t.y;
+                    l2acc = fmaf(dr, dr, fmaf(di, di, l2acc));
+                    a.l2_grad[e] = make_float2(2.f * dr * a.l2_inv, 2.f * di * a.l2_inv);
                 }
             }
         }
@@ -841,8 +872,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
         if (a.n_contrib) a.n_contrib[(size_t)b * plane + pix] = last;
         if (a.n_used) a.n_used[(size_t)b * plane + pix] = used;
     }
+    float* s_l2 = reinterpret_cast<float*>(sm + L::kL2);
+    if (a.l2_grad) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l2acc += __shfl_xor_sync(0xffffffffu, l2acc, o);
+        if ((tid & 31) == 0) s_l2[warp] = l2acc;
+    }
     tc_fence_before();
     __syncthreads();
+    if (a.l2_grad && tid == 0) {
+        float t = 0.f;
+        for (int w2 = 0; w2 < kThreads / 32; ++w2) t += s_l2[w2];
+        atomicAdd(a.l2_loss, t * a.l2_inv);
+    }
     if (a.csi) {
         for (int e = tid; e < 2 * S; e += kThreads) {
             const int k = k0 + e / 2;
@@ -885,6 +927,37 @@ extern "C" int gsparc_render_fwd_tc(const gsparc_view* view, const gsparc_band* 
     a.n_used = n_used;
     const int T = tiles_x(*view) * tiles_y(*view);
     cudaStream_t s = as_stream(stream);
+    if (band->K <= 8) return launch_fwd_tc<8>(a, T, s);
+    if (band->K <= 16) return launch_fwd_tc<16>(a, T, s);
+    if (band->K <= 32) return launch_fwd_tc<32>(a, T, s);
+    return launch_fwd_tc<64>(a, T, s);
+}
+
+extern "C" int gsparc_render_fwd_l2_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
+                                       const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
+                                       const float* attr, const float* target, float* loss, float* d_spectrum,
+                                       float* spectrum, float* final_logT, uint32_t* n_contrib, uint32_t* n_used,
+                                       void* stream) {
+    using namespace gsparc;
+    if (!common_ok(view, band, B, N, proj, tile_ranges, sorted_ids, attr)) return GSPARC_ERR_INVALID;
+    if (!target || !loss || !d_spectrum) return GSPARC_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(spectrum) | reinterpret_cast<uintptr_t>(target) |
+         reinterpret_cast<uintptr_t>(d_spectrum)) & 7)
+        return GSPARC_ERR_INVALID;
+    RenderArgs a{};
+    fill_args(view, band, B, N, proj, tile_ranges, sorted_ids, attr, a);
+    a.spectrum = reinterpret_cast<float2*>(spectrum);
+    a.final_logT = final_logT;
+    a.n_contrib = n_contrib;
+    a.n_used = n_used;
+    a.l2_target = reinterpret_cast<const float2*>(target);
+    a.l2_loss = loss;
+    a.l2_grad = reinterpret_cast<float2*>(d_spectrum);
+    const int64_t count = (int64_t)B * band->K * view->H * view->W;
+    a.l2_inv = (float)(1.0 / (double)count);
+    const int T = tiles_x(*view) * tiles_y(*view);
+    cudaStream_t s = as_stream(stream);
+    if (cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess) return GSPARC_ERR_CUDA;
     if (band->K <= 8) return launch_fwd_tc<8>(a, T, s);
     if (band->K <= 16) return launch_fwd_tc<16>(a, T, s);
     if (band->K <= 32) return launch_fwd_tc<32>(a, T, s);

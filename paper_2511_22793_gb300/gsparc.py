@@ -35,7 +35,7 @@ EXPORTS = [
     "gsparc_bin_sort", "gsparc_bin_sort_noalloc", "gsparc_attr_mlp", "gsparc_attr_mlp_bwd",
     "gsparc_attr_mlp_bwd_tc", "gsparc_render_fwd", "gsparc_render_fwd_tc", "gsparc_render_bwd",
     "gsparc_render_bwd_tc", "gsparc_l2_loss", "gsparc_csi_head", "gsparc_csi_loss", "gsparc_csi_head_bwd",
-    "gsparc_render_csi_tc", "gsparc_adam", "gsparc_check", "gsparc_strerror",
+    "gsparc_render_csi_tc", "gsparc_render_fwd_l2_tc", "gsparc_adam", "gsparc_check", "gsparc_strerror",
 ]
 
 
@@ -105,6 +105,8 @@ def lib():
             "gsparc_csi_head_bwd": (ctypes.c_int, [i32, i32, i64, vp, f32, vp, vp]),
             "gsparc_render_csi_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
                                                     vp, vp, vp, vp]),
+            "gsparc_render_fwd_l2_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
+                                                       vp, vp, vp, vp, vp, vp]),
             "gsparc_adam": (ctypes.c_int, [i64, vp, vp, vp, vp, f32, f32, f32, f32, i32, vp]),
             "gsparc_check": (ctypes.c_int, [vp, vp]),
             "gsparc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -293,6 +295,13 @@ def gsparc_render_csi_tc(view, band, B, n, proj, tile_ranges, sorted_ids, attr, 
     _call("gsparc_render_csi_tc", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
           _p(tile_ranges), _p(sorted_ids), _p(attr), _p(csi), _p(spectrum), _p(final_logT), _p(n_contrib),
           _p(n_used), _stream(stream))
+
+
+def gsparc_render_fwd_l2_tc(view, band, B, n, proj, tile_ranges, sorted_ids, attr, target, loss, d_spectrum,
+                            spectrum=None, final_logT=None, n_contrib=None, n_used=None, stream=None):
+    _call("gsparc_render_fwd_l2_tc", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
+          _p(tile_ranges), _p(sorted_ids), _p(attr), _p(target), _p(loss), _p(d_spectrum), _p(spectrum),
+          _p(final_logT), _p(n_contrib), _p(n_used), _stream(stream))
 
 
 def gsparc_adam(param, grad, m, v, lr, step, b1=0.9, b2=0.999, eps=1e-15, stream=None):

@@ -6,6 +6,8 @@ import torch
 from gpu_util import DEV
 from oracle import adam as oadam
 from paper_2511_22793_gb300 import gsparc as G
+from paper_2511_22793_gb300 import synth
+from paper_2511_22793_gb300.pipeline import DeviceMLP, DeviceScene, Renderer
 
 pytestmark = pytest.mark.gpu
 
@@ -39,3 +41,34 @@ def test_adam_matches_oracle():
         q, mm, vv = oadam.adam_step(q, g, mm, vv, step, 5e-3, eps=1e-15)
     torch.cuda.synchronize()
     np.testing.assert_allclose(pd.cpu().numpy(), q, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("n,H,W,K,B", [(3000, 90, 360, 64, 1), (2000, 45, 180, 37, 2)])
+def test_fused_l2_loss_forward_matches_unfused(n, H, W, K, B):
+    """gsparc_render_fwd_l2_tc: the gradient is bit-identical to gsparc_l2_loss on the spectrum
+    of gsparc_render_fwd_tc, the loss agrees to 1e-6 relative (summation order), the state
+    buffers are identical, and without a spectrum buffer nothing else changes."""
+    sc = synth.make_scene(n, seed=91)
+    mlp = synth.make_mlp(32, seed=92)
+    tx = synth.make_tx(B, seed=93)
+    r = Renderer(H, W, K, n, device=DEV)
+    ds, dm = DeviceScene.from_host(sc, DEV), DeviceMLP.from_host(mlp, DEV)
+    r.geometry(ds)
+    attr = r.attributes(ds, dm, torch.tensor(tx, device=DEV))
+    spec, logT, nc = r.render(attr, tensor_cores=True)
+    target = torch.randn_like(spec) * 0.01
+    loss = torch.zeros(1, device=DEV)
+    d_ref = torch.empty_like(spec)
+    G.gsparc_l2_loss(spec, target, loss, d_ref)
+    for with_spec in (True, False):
+        out = r.alloc_outputs(B)
+        loss2 = torch.full((1,), 7.0, device=DEV)
+        d2 = torch.empty_like(spec)
+        G.gsparc_render_fwd_l2_tc(r.view, r.band, B, n, r.proj, r.tile_ranges, r.sorted_ids, attr, target, loss2,
+                                  d2, out[0] if with_spec else None, out[1], out[2])
+        torch.cuda.synchronize()
+        assert torch.equal(d2, d_ref)
+        assert abs(float(loss2) - float(loss)) <= 1e-6 * float(loss)
+        assert torch.equal(out[1], logT) and torch.equal(out[2], nc)
+        if with_spec:
+            assert torch.equal(out[0], spec)
