@@ -125,8 +125,17 @@ class Trainer:
         self._gbuf.zero_()
         self.d_attr.zero_()
         self.d_proj.zero_()
-        (spec, logT, nc), attr = self.forward(self.tx)
-        G.gsparc_l2_loss(spec, target, self.loss, self.d_spec)
+        if self.tensor_cores:
+            # the loss fused into the tensor-core forward: dL/dz and the loss, no spectrum
+            prec = G.GSPARC_BF16X2
+            self.r.geometry(self.scene)
+            attr = self.r.attributes(self.scene, self.mlp, self.tx, prec, out=self.attr)
+            _, logT, nc = self.out
+            G.gsparc_render_fwd_l2_tc(self.r.view, self.r.band, self.batch, self.n, self.r.proj, self.r.tile_ranges,
+                                      self.r.sorted_ids, attr, target, self.loss, self.d_spec, None, logT, nc)
+        else:
+            (spec, logT, nc), attr = self.forward(self.tx)
+            G.gsparc_l2_loss(spec, target, self.loss, self.d_spec)
         self.r.render_backward(attr, logT, nc, self.d_spec, self.d_attr, self.d_proj,
                                tensor_cores=self.tensor_cores)
         g = self.grads
