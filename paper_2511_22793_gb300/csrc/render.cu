@@ -1003,29 +1003,12 @@ namespace {
 // (K index 2kk + {re, im} matches A = (Re g_k, Im g_k)).  Both operands are split into BF16
 // hi/lo terms and the products g_hi u_hi + g_lo u_hi + g_hi u_lo are accumulated in FP32 in
 // TMEM.  The CUDA cores then run the same back-to-front recursion as k_render_bwd on the three
-// contractions.  B and D are double-buffered: the tensor cores work on batch i while the CUDA
-// cores consume batch i-1.
+// contractions.  The kernel is warp-specialised (below): producer warps build B and issue the
+// MMAs into a ring of stages while the pixel warps consume them, with mbarriers in place of
+// block-wide barriers.
 // =============================================================================================
 
 constexpr int kTbE = 16;   // entries per backward batch
-
-template <int S>
-struct RTbSmem {
-    static constexpr int kKa = 2 * S;                          // K of one term
-    static constexpr int kATile = 128 * kKa * 2;               // bytes of one (half, term) tile
-    static constexpr int kA = 0;                               // [half][hi, lo]
-    static constexpr int kBTile = 3 * kTbE * kKa * 2;          // bytes of one (stage, term) tile
-    static constexpr int kB = kA + 4 * kATile;                 // [stage][hi, lo]
-    static constexpr int kMeta = kB + 4 * kBTile;
-    // per-entry records of four batches (being published, built, consumed, flushed):
-    // geo float4, geo2 float2, ext float2, amp, phi, len, gid (E each)
-    static constexpr int kMetaStage = kTbE * (16 + 8 + 8 + 4 + 4 + 4 + 4);
-    static constexpr int kRed = kMeta + 4 * kMetaStage;        // float [8 warps][E][9]
-    static constexpr int kMask = kRed + 8 * kTbE * 9 * 4;      // uint64 [8]
-    static constexpr int kBar = kMask + 8 * 8;                 // 2 mbarriers + TMEM slot + maxlast
-    static constexpr int kTotal = kBar + 32;
-    static constexpr uint32_t kCols = 256;                     // 2 stages x 2 halves x 3E columns
-};
 
 struct TbMeta {
     float4* geo;
@@ -1049,35 +1032,103 @@ __device__ __forceinline__ TbMeta tb_meta(uint8_t* base) {
     return m;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Warp-specialised form of the tensor-core backward.  Warps 0-7 (one pixel per thread) are
+// consumers; warps 8-11 are the producer (synchronised among themselves by a named barrier).
+// The producer gathers each batch's per-entry records,
+// builds its phasor operand B, issues its MMAs into one of kWsR stages of shared memory and
+// TMEM, and flushes the gradients of batches the consumers have finished; the consumers walk
+// the batches at their own pace, each warp signalling when it is done with a stage.  No
+// block-wide barrier sits inside the walk:
+//   full[s]  (2 arrivals): tcgen05.commit of the stage's MMAs + the producer's release of the
+//            stage's records;                     consumers wait, phase (i / kWsR) & 1
+//   empty[s] (8 arrivals): one per consumer warp after its TMEM reads and gradient writes;
+//            the producer waits before reusing the stage (and flushes that batch)
+// Every wait is bounded; an expired wait raises a shared error flag and every warp leaves
+// its loop (the gradients are then incomplete, as in the other forms).
+// ---------------------------------------------------------------------------------------------
+
+constexpr int kWsR = 3;
+constexpr int kWsProd = 128;                   // producer threads (four warps)
+constexpr int kWsThreads = kThreads + kWsProd;
+
+__device__ __forceinline__ void producer_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kWsProd) : "memory");
+}
+
+// Barrier of the producer warps that also ANDs a flag over them: every producer thread takes
+// the same branch afterwards (a warp leaving the loop alone would strand the others at the
+// next producer_sync).
+__device__ __forceinline__ bool producer_all(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kWsProd)
+        : "memory");
+    return r != 0;
+}
+
 template <int S>
-__global__ void __launch_bounds__(kThreads, 1) k_render_bwd_tc(RenderArgs a) {
-    using L = RTbSmem<S>;
+struct RWsSmem {
+    static constexpr int kKa = 2 * S;
+    static constexpr int kATile = 128 * kKa * 2;
+    static constexpr int kA = 0;                                   // [half][hi, lo]
+    static constexpr int kBTile = 3 * kTbE * kKa * 2;
+    static constexpr int kB = kA + 4 * kATile;                     // [stage][hi, lo]
+    static constexpr int kMetaStage = kTbE * (16 + 8 + 8 + 4 + 4 + 4 + 4);
+    static constexpr int kMeta = kB + kWsR * 2 * kBTile;
+    static constexpr int kRedStage = 8 * kTbE * 9 * 4;
+    static constexpr int kRed = kMeta + kWsR * kMetaStage;         // float [stage][warp][E][9]
+    static constexpr int kMask = kRed + kWsR * kRedStage;          // uint64 [stage][warp]
+    static constexpr int kBar = kMask + kWsR * 8 * 8;              // full[R], empty[R]
+    static constexpr int kTotal = kBar + 2 * kWsR * 8 + 16;        // + TMEM slot, maxlast, error
+    static constexpr uint32_t kStageCols = 2 * 3 * kTbE;           // both halves of a stage
+    static constexpr uint32_t kCols = 512;
+    static_assert(kWsR * kStageCols <= kCols, "TMEM stages");
+    static_assert(kTotal <= 232448, "shared memory per block");
+};
+
+template <int S>
+__global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
+    using L = RWsSmem<S>;
     extern __shared__ __align__(1024) uint8_t sm[];
-    float (*s_red)[kTbE][9] = reinterpret_cast<float (*)[kTbE][9]>(sm + L::kRed);
-    uint64_t* s_wmask = reinterpret_cast<uint64_t*>(sm + L::kMask);
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::kBar);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::kBar + 16);
-    uint32_t* s_maxlast = reinterpret_cast<uint32_t*>(sm + L::kBar + 20);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::kBar + 2 * kWsR * 8);
+    uint32_t* s_maxlast = tslot + 1;
+    volatile uint32_t* s_err = tslot + 2;
+    auto red_at = [&](int st, int w, int j, int c) -> float& {
+        return reinterpret_cast<float*>(sm + L::kRed + st * L::kRedStage)[(w * kTbE + j) * 9 + c];
+    };
+    auto mask_at = [&](int st, int w) -> uint64_t& { return reinterpret_cast<uint64_t*>(sm + L::kMask)[st * 8 + w]; };
+    auto full_bar = [&](int st) { return smem_u32(&bars[st]); };
+    auto empty_bar = [&](int st) { return smem_u32(&bars[kWsR + st]); };
 
     const int strip = blockIdx.x, tile = blockIdx.y, b = blockIdx.z;
     const int k0 = strip * S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int half = tid >> 7, m = tid & 127;
+    const bool producer = warp >= kThreads / 32;
+    const int prod = tid - kThreads;   // producer thread index (0..127) when producer
+    const int ptid = producer ? 0 : tid;   // pixel of a consumer thread
+    const int half = ptid >> 7, m = ptid & 127;
     const int tx0 = (tile % a.TW) * kTile, ty0 = (tile / a.TW) * kTile;
-    const int x = tx0 + (tid & 15), y = ty0 + (tid >> 4);
-    const bool inside = x < a.W && y < a.H;
+    const int x = tx0 + (ptid & 15), y = ty0 + (ptid >> 4);
+    const bool inside = !producer && x < a.W && y < a.H;
     const float ux = (float)x + 0.5f, uy = (float)y + 0.5f;
     const float wcx = (float)tx0 + 8.0f, wcy = (float)(ty0 + 2 * warp) + 1.0f;
     const uint2 range = a.ranges[tile];
     const size_t plane = (size_t)a.H * a.W;
     const size_t pix = (size_t)y * a.W + x;
 
-    const uint32_t bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
     if (tid == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar1, 1);
+        for (int st = 0; st < kWsR; ++st) {
+            mbar_init(full_bar(st), 2);
+            mbar_init(empty_bar(st), kThreads / 32);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *s_maxlast = 0;
+        *s_err = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -1085,8 +1136,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_bwd_tc(RenderArgs a) {
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // A operand: this pixel's upstream gradient over the strip, split hi / lo
-    {
+    // A operand (consumers): this pixel's upstream gradient over the strip, split hi / lo
+    if (!producer) {
         uint8_t* Ahi = sm + L::kA + (half * 2 + 0) * L::kATile;
         uint8_t* Alo = sm + L::kA + (half * 2 + 1) * L::kATile;
 #pragma unroll 4
@@ -1110,82 +1161,103 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_bwd_tc(RenderArgs a) {
     const uint32_t last = inside ? a.n_contrib[(size_t)b * plane + pix] : 0u;
     __syncthreads();
     if (last) atomicMax(s_maxlast, last);
+    fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t maxlast = min(*s_maxlast, range.y - range.x);
     const uint32_t tbase = *tslot;
-    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-    constexpr uint32_t idesc = make_idesc(128, 3 * kTbE);
-    const uint32_t a_base = smem_u32(sm + L::kA), b_base = smem_u32(sm + L::kB);
-    const float c_f0 = (float)(a.two_pi_over_c * (a.f0 + (double)k0 * a.df));
-    const float c_df = (float)(a.two_pi_over_c * a.df);
-    float suffix = 0.f;
     const int nbatch = (int)((maxlast + kTbE - 1) / kTbE);
-    uint32_t ph0 = 0, ph1 = 0;
-    bool ok = true;
-    // batch i holds list entries [lo_pos(i), hi_pos(i)), walking back from maxlast
     auto batch_lo = [&](int i) {
         const uint32_t hp = maxlast - (uint32_t)i * kTbE;
         return hp > (uint32_t)kTbE ? hp - kTbE : 0u;
     };
     auto batch_n = [&](int i) { return (int)(maxlast - (uint32_t)i * kTbE - batch_lo(i)); };
-    // records of one batch gathered into registers (threads tid < E) two batches ahead, then
-    // published into that batch's record buffer one batch ahead
-    uint32_t pf_gid = 0xffffffffu;
-    float4 pf_p0 = make_float4(0.f, 0.f, 0.f, 0.f), pf_p1 = pf_p0, pf_at = pf_p0;
-    auto gather = [&](int i) {
-        if (tid < kTbE) {
-            const int nb = batch_n(i);
-            pf_gid = tid < nb ? a.ids[range.x + batch_lo(i) + tid] : 0xffffffffu;
-            if (pf_gid < (uint32_t)a.N) {
-                pf_p0 = a.proj[2 * pf_gid];
-                pf_p1 = a.proj[2 * pf_gid + 1];
-                pf_at = a.attr[(size_t)b * a.N + pf_gid];
-            }
-        }
+    auto wait_ok = [&](uint32_t bar, uint32_t parity) {
+        bool w = (*s_err == 0u) && mbar_wait(bar, parity);
+        w = __all_sync(0xffffffffu, w);
+        if (!w && lane == 0) *s_err = 1u;
+        return w;
     };
-    auto publish = [&](int i) {
-        if (tid < kTbE) {
-            TbMeta md = tb_meta(sm + L::kMeta + (i & 3) * L::kMetaStage);
-            if (pf_gid < (uint32_t)a.N) {
-                md.geo[tid] = make_float4(pf_p0.x, pf_p0.y, pf_p1.x, pf_p1.y);
-                md.geo2[tid] = make_float2(pf_p1.z, pf_at.z);
-                md.ext[tid] = make_float2(pf_p0.z, pf_p0.w);
-                md.amp[tid] = pf_at.x;
-                md.phi[tid] = pf_at.y;
-                md.len[tid] = pf_at.w;
-                md.gid[tid] = pf_gid;
-            } else {
-                md.geo[tid] = make_float4(0.f, 0.f, __int_as_float(0x7fc00000), 0.f);
-                md.geo2[tid] = make_float2(0.f, 0.f);
-                md.ext[tid] = make_float2(-1.f, -1.f);
-                md.amp[tid] = 0.f;
-                md.phi[tid] = 0.f;
-                md.len[tid] = 0.f;
-                md.gid[tid] = 0;
-            }
-        }
-    };
-    if (nbatch > 0) {
-        gather(0);
-        publish(0);
-    }
-    if (nbatch > 1) gather(1);
-    __syncthreads();
 
-    // Iteration i: build B of batch i, publish batch i+1's records and gather batch i+2's,
-    // one barrier, issue batch i's MMAs, consume batch i-1 from TMEM on the CUDA cores, one
-    // barrier (which also carries any expired wait), flush batch i-1's gradients.
-    for (int i = 0; i <= nbatch; ++i) {
-        if (i < nbatch) {
-            const int st = i & 1;
+    if (producer) {
+        // ---------------- producer warps
+        constexpr uint32_t idesc = make_idesc(128, 3 * kTbE);
+        const uint32_t a_base = smem_u32(sm + L::kA), b_base = smem_u32(sm + L::kB);
+        const bool gatherer = prod < kTbE;   // threads 0..E-1 of the first producer warp
+        uint32_t pf_gid = 0xffffffffu;
+        float4 pf_p0 = make_float4(0.f, 0.f, 0.f, 0.f), pf_p1 = pf_p0, pf_at = pf_p0;
+        auto gather = [&](int i) {
+            if (gatherer) {
+                pf_gid = prod < batch_n(i) ? a.ids[range.x + batch_lo(i) + prod] : 0xffffffffu;
+                if (pf_gid < (uint32_t)a.N) {
+                    pf_p0 = a.proj[2 * pf_gid];
+                    pf_p1 = a.proj[2 * pf_gid + 1];
+                    pf_at = a.attr[(size_t)b * a.N + pf_gid];
+                }
+            }
+        };
+        auto flush = [&](int i, int st) {
+            TbMeta md = tb_meta(sm + L::kMeta + st * L::kMetaStage);
             const int nb = batch_n(i);
-            TbMeta md = tb_meta(sm + L::kMeta + (i & 3) * L::kMetaStage);
-            // ---- B rows of the batch: thread (j, 8 consecutive K columns) computes 4 phasors
+            for (int e = prod; e < nb * 9; e += kWsProd) {
+                const int j = e / 9, c = e - j * 9;
+                float acc = 0.f;
+#pragma unroll
+                for (int w2 = 0; w2 < kThreads / 32; ++w2)
+                    if ((mask_at(st, w2) >> j) & 1ull) acc += red_at(st, w2, j, c);
+                if (acc != 0.f) {
+                    const uint32_t gid = md.gid[j];
+                    if (c >= 5) {
+                        float* dst = reinterpret_cast<float*>(&a.d_attr[(size_t)b * a.N + gid]);
+                        const int slot = c == 5 ? 2 : (c == 6 ? 0 : (c == 7 ? 1 : 3));
+                        atomicAdd(dst + slot, acc);
+                    } else {
+                        const int slot = c < 2 ? c : c + 2;
+                        atomicAdd(a.d_proj + (size_t)gid * 8 + slot, acc);
+                    }
+                }
+            }
+        };
+        if (nbatch > 0) gather(0);
+        for (int i = 0; i < nbatch; ++i) {
+            const int st = i % kWsR;
+            if (i >= kWsR) {
+                // the consumers released the stage (batch i - R): flush that batch, then reuse
+                const bool w = wait_ok(empty_bar(st), (uint32_t)((i / kWsR) - 1) & 1u);
+                if (!producer_all(w)) break;   // uniform over the producer warps
+                tc_fence_after();
+                flush(i - kWsR, st);
+            }
+            producer_sync();   // the flush has read the stage's records
+            TbMeta md = tb_meta(sm + L::kMeta + st * L::kMetaStage);
+            if (gatherer) {
+                const int e = prod;
+                if (pf_gid < (uint32_t)a.N) {
+                    md.geo[e] = make_float4(pf_p0.x, pf_p0.y, pf_p1.x, pf_p1.y);
+                    md.geo2[e] = make_float2(pf_p1.z, pf_at.z);
+                    md.ext[e] = make_float2(pf_p0.z, pf_p0.w);
+                    md.amp[e] = pf_at.x;
+                    md.phi[e] = pf_at.y;
+                    md.len[e] = pf_at.w;
+                    md.gid[e] = pf_gid;
+                } else {
+                    md.geo[e] = make_float4(0.f, 0.f, __int_as_float(0x7fc00000), 0.f);
+                    md.geo2[e] = make_float2(0.f, 0.f);
+                    md.ext[e] = make_float2(-1.f, -1.f);
+                    md.amp[e] = 0.f;
+                    md.phi[e] = 0.f;
+                    md.len[e] = 0.f;
+                    md.gid[e] = 0;
+                }
+            }
+            if (i + 1 < nbatch) gather(i + 1);
+            producer_sync();   // the records are in place for the phasor build
+            // B rows of the batch: item (j, 8 consecutive K columns) = 4 phasors
+            const int nb = batch_n(i);
             uint8_t* Bhi = sm + L::kB + (st * 2 + 0) * L::kBTile;
             uint8_t* Blo = sm + L::kB + (st * 2 + 1) * L::kBTile;
-            for (int e = tid; e < kTbE * (L::kKa / 8); e += kThreads) {
+            for (int e = prod; e < kTbE * (L::kKa / 8); e += kWsProd) {
                 const int j = e / (L::kKa / 8), c0 = (e % (L::kKa / 8)) * 8;
                 float r0[8], r1[8], r2[8];
 #pragma unroll
@@ -1211,135 +1283,111 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_bwd_tc(RenderArgs a) {
                 *reinterpret_cast<uint4*>(Bhi + canon_off(3 * j + 2, c0, L::kKa)) = H;
                 *reinterpret_cast<uint4*>(Blo + canon_off(3 * j + 2, c0, L::kKa)) = Lo;
             }
-        }
-        // batch i+1's buffer was last read by the flush of batch i-3 (two barriers ago)
-        if (i + 1 < nbatch) publish(i + 1);
-        if (i + 2 < nbatch) gather(i + 2);
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (i < nbatch && tid == 0) {
-            const int st = i & 1;
-            const uint32_t bhi = b_base + (st * 2 + 0) * L::kBTile, blo = b_base + (st * 2 + 1) * L::kBTile;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t ahi = a_base + (h * 2 + 0) * L::kATile, alo = a_base + (h * 2 + 1) * L::kATile;
-                const uint32_t d = tbase + (uint32_t)((st * 2 + h) * 3 * kTbE);
-                // g_hi u_hi + g_lo u_hi + g_hi u_lo
-                const uint32_t as_[3] = {ahi, alo, ahi};
-                const uint32_t bs_[3] = {bhi, bhi, blo};
-#pragma unroll
-                for (int t = 0; t < 3; ++t)
-#pragma unroll
-                    for (int q = 0; q < L::kKa / 16; ++q)
-                        mma_bf16(d, make_desc(as_[t] + q * 256, 128, L::kKa * 16),
-                                 make_desc(bs_[t] + q * 256, 128, L::kKa * 16), idesc,
-                                 (t > 0 || q > 0) ? 1u : 0u);
-            }
-            mma_commit(st == 0 ? bar0 : bar1);
-        }
-        bool wok = true;
-        const int pi = i - 1;
-        TbMeta mdp = tb_meta(sm + L::kMeta + (pi & 3) * L::kMetaStage);
-        const int nbp = pi >= 0 ? batch_n(pi) : 0;
-        if (pi >= 0) {
-            // ---- consume batch i-1 on the CUDA cores
-            const int st = pi & 1;
-            wok = st == 0 ? mbar_wait(bar0, ph0) : mbar_wait(bar1, ph1);
-            wok = __all_sync(0xffffffffu, wok);   // tcgen05.ld below is warp-collective
-            if (st == 0) ph0 ^= 1;
-            else ph1 ^= 1;
-            const uint32_t lo_pos = batch_lo(pi);
-            if (wok) {
+            fence_async_smem();
+            producer_sync();   // the operand is complete
+            if (prod == 0) {
                 tc_fence_after();
-                float v[3 * kTbE];
+                const uint32_t bhi = b_base + (st * 2 + 0) * L::kBTile, blo = b_base + (st * 2 + 1) * L::kBTile;
 #pragma unroll
-                for (int c = 0; c < 3 * kTbE; c += 16) {
-                    float t16[16];
-                    tmem_ld16(tbase + (uint32_t)((st * 2 + half) * 3 * kTbE + c) + lane_base, t16);
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t ahi = a_base + (h * 2 + 0) * L::kATile, alo = a_base + (h * 2 + 1) * L::kATile;
+                    const uint32_t d = tbase + (uint32_t)(st * L::kStageCols + h * 3 * kTbE);
+                    const uint32_t as_[3] = {ahi, alo, ahi};
+                    const uint32_t bs_[3] = {bhi, bhi, blo};
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) v[c + q] = t16[q];
+                    for (int t = 0; t < 3; ++t)
+#pragma unroll
+                        for (int q = 0; q < L::kKa / 16; ++q)
+                            mma_bf16(d, make_desc(as_[t] + q * 256, 128, L::kKa * 16),
+                                     make_desc(bs_[t] + q * 256, 128, L::kKa * 16), idesc,
+                                     (t > 0 || q > 0) ? 1u : 0u);
                 }
-                const uint64_t mask = warp_entry_mask(mdp.geo, mdp.ext, nbp, wcx, wcy, a.W);
-                if (lane == 0) s_wmask[warp] = mask;
+                mma_commit(full_bar(st));
+                mbar_arrive(full_bar(st));   // the stage's records, released
+            }
+        }
+        // flush the batches still held by the stages
+        for (int i = nbatch > kWsR ? nbatch - kWsR : 0; i < nbatch; ++i) {
+            const int st = i % kWsR;
+            if (!wait_ok(empty_bar(st), (uint32_t)(i / kWsR) & 1u)) break;
+            tc_fence_after();
+            flush(i, st);
+        }
+    } else {
+        // ---------------- consumer warps: one pixel per thread
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        const float c_f0 = (float)(a.two_pi_over_c * (a.f0 + (double)k0 * a.df));
+        const float c_df = (float)(a.two_pi_over_c * a.df);
+        float suffix = 0.f;
+        for (int i = 0; i < nbatch; ++i) {
+            const int st = i % kWsR;
+            if (!wait_ok(full_bar(st), (uint32_t)(i / kWsR) & 1u)) break;
+            tc_fence_after();
+            const uint32_t lo_pos = batch_lo(i);
+            const int nbp = batch_n(i);
+            TbMeta mdp = tb_meta(sm + L::kMeta + st * L::kMetaStage);
+            float v[3 * kTbE];
 #pragma unroll
-                for (int j = kTbE - 1; j >= 0; --j) {
-                    if (!((mask >> j) & 1ull)) continue;   // warp-uniform
-                    float gr[9];
+            for (int c = 0; c < 3 * kTbE; c += 16) {
+                float t16[16];
+                tmem_ld16(tbase + (uint32_t)(st * L::kStageCols + half * 3 * kTbE + c) + lane_base, t16);
 #pragma unroll
-                    for (int c = 0; c < 9; ++c) gr[c] = 0.f;
-                    bool contrib = false;
-                    const uint32_t pos = lo_pos + (uint32_t)j;
-                    if (pos < last) {
-                        const float4 gg = mdp.geo[j];
-                        const float2 g2 = mdp.geo2[j];
-                        float dx, dy, G, alpha;
-                        bool clamped;
-                        if (eval_alpha(ux, uy, a.W, gg, g2, dx, dy, G, alpha, clamped)) {
-                            contrib = true;
-                            const float nl = lg2(__fsub_rn(1.0f, alpha));
-                            const float logT_before = __fsub_rn(logT, nl);
-                            const float T = ex2(logT_before);
-                            const float w = T * alpha;
-                            const float reG = v[3 * j], imG = v[3 * j + 1], imF = v[3 * j + 2];
-                            const float amp = mdp.amp[j];
-                            const float reGa = amp * reG;
-                            const float dalpha = T * reGa - suffix / (1.0f - alpha);
-                            suffix = fmaf(w, reGa, suffix);
-                            gr[6] = w * reG;
-                            gr[7] = -w * amp * imG;
-                            gr[8] = w * amp * (c_f0 * imG + c_df * imF);
-                            if (!clamped) {
-                                const float sig = g2.y;
-                                gr[5] = dalpha * G;
-                                const float dq = -0.5f * dalpha * sig * G;
-                                gr[0] = dq * (-2.0f * (gg.z * dx + gg.w * dy));
-                                gr[1] = dq * (-2.0f * (gg.w * dx + g2.x * dy));
-                                gr[2] = dq * dx * dx;
-                                gr[3] = dq * 2.0f * dx * dy;
-                                gr[4] = dq * dy * dy;
-                            }
-                            logT = logT_before;
+                for (int q = 0; q < 16; ++q) v[c + q] = t16[q];
+            }
+            const uint64_t mask = warp_entry_mask(mdp.geo, mdp.ext, nbp, wcx, wcy, a.W);
+            if (lane == 0) mask_at(st, warp) = mask;
+#pragma unroll
+            for (int j = kTbE - 1; j >= 0; --j) {
+                if (!((mask >> j) & 1ull)) continue;   // warp-uniform
+                float gr[9];
+#pragma unroll
+                for (int c = 0; c < 9; ++c) gr[c] = 0.f;
+                bool contrib = false;
+                const uint32_t pos = lo_pos + (uint32_t)j;
+                if (pos < last) {
+                    const float4 gg = mdp.geo[j];
+                    const float2 g2 = mdp.geo2[j];
+                    float dx, dy, G, alpha;
+                    bool clamped;
+                    if (eval_alpha(ux, uy, a.W, gg, g2, dx, dy, G, alpha, clamped)) {
+                        contrib = true;
+                        const float nl = lg2(__fsub_rn(1.0f, alpha));
+                        const float logT_before = __fsub_rn(logT, nl);
+                        const float T = ex2(logT_before);
+                        const float w = T * alpha;
+                        const float reG = v[3 * j], imG = v[3 * j + 1], imF = v[3 * j + 2];
+                        const float amp = mdp.amp[j];
+                        const float reGa = amp * reG;
+                        const float dalpha = T * reGa - suffix / (1.0f - alpha);
+                        suffix = fmaf(w, reGa, suffix);
+                        gr[6] = w * reG;
+                        gr[7] = -w * amp * imG;
+                        gr[8] = w * amp * (c_f0 * imG + c_df * imF);
+                        if (!clamped) {
+                            const float sig = g2.y;
+                            gr[5] = dalpha * G;
+                            const float dq = -0.5f * dalpha * sig * G;
+                            gr[0] = dq * (-2.0f * (gg.z * dx + gg.w * dy));
+                            gr[1] = dq * (-2.0f * (gg.w * dx + g2.x * dy));
+                            gr[2] = dq * dx * dx;
+                            gr[3] = dq * 2.0f * dx * dy;
+                            gr[4] = dq * dy * dy;
                         }
-                    }
-                    if (__any_sync(0xffffffffu, contrib)) {
-                        const float tot = warp_reduce_scatter9(gr, lane);
-                        if ((lane & 1) == 0 && (lane >> 1) < 9) s_red[warp][j][lane >> 1] = tot;
-                    } else if (lane < 9) {
-                        s_red[warp][j][lane] = 0.f;
+                        logT = logT_before;
                     }
                 }
-            }
-        }
-        tc_fence_before();
-        if (__syncthreads_or(!wok)) {   // an expired wait: stop without flushing
-            ok = false;
-            break;
-        }
-        if (pi >= 0) {
-            for (int e = tid; e < nbp * 9; e += kThreads) {
-                const int j = e / 9, c = e - j * 9;
-                float acc = 0.f;
-#pragma unroll
-                for (int w2 = 0; w2 < kThreads / 32; ++w2)
-                    if ((s_wmask[w2] >> j) & 1ull) acc += s_red[w2][j][c];
-                if (acc != 0.f) {
-                    const uint32_t gid = mdp.gid[j];
-                    if (c >= 5) {
-                        float* dst = reinterpret_cast<float*>(&a.d_attr[(size_t)b * a.N + gid]);
-                        const int slot = c == 5 ? 2 : (c == 6 ? 0 : (c == 7 ? 1 : 3));
-                        atomicAdd(dst + slot, acc);
-                    } else {
-                        const int slot = c < 2 ? c : c + 2;
-                        atomicAdd(a.d_proj + (size_t)gid * 8 + slot, acc);
-                    }
+                if (__any_sync(0xffffffffu, contrib)) {
+                    const float tot = warp_reduce_scatter9(gr, lane);
+                    if ((lane & 1) == 0 && (lane >> 1) < 9) red_at(st, warp, j, lane >> 1) = tot;
+                } else if (lane < 9) {
+                    red_at(st, warp, j, lane) = 0.f;
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty_bar(st));
         }
     }
-    (void)ok;
-    // drain a batch whose MMAs were issued but not consumed (only after an expired wait)
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -1350,10 +1398,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_bwd_tc(RenderArgs a) {
 
 template <int S>
 int launch_bwd_tc(const RenderArgs& a, int T, cudaStream_t s) {
-    using L = RTbSmem<S>;
-    if (!ensure_smem_attr(k_render_bwd_tc<S>, L::kTotal)) return GSPARC_ERR_CUDA;
+    using L = RWsSmem<S>;
+    if (!ensure_smem_attr(k_render_bwd_ws<S>, L::kTotal)) return GSPARC_ERR_CUDA;
     dim3 grid((a.K + S - 1) / S, T, a.B);
-    k_render_bwd_tc<S><<<grid, kThreads, L::kTotal, s>>>(a);
+    k_render_bwd_ws<S><<<grid, kWsThreads, L::kTotal, s>>>(a);
     return launch_status();
 }
 

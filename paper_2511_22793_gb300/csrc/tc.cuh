@@ -53,6 +53,12 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
 }
 
+// Arrive on an mbarrier (release at CTA scope: this thread's prior shared-memory writes are
+// visible to a thread whose wait observes the phase completion).
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
 // Bounded wait for the given phase parity; false when the bound expired.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     for (uint32_t it = 0; it < kSpin; ++it) {
