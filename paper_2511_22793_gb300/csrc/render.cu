@@ -1034,8 +1034,8 @@ __device__ __forceinline__ TbMeta tb_meta(uint8_t* base) {
 
 // ---------------------------------------------------------------------------------------------
 // Warp-specialised form of the tensor-core backward.  Warps 0-7 (one pixel per thread) are
-// consumers; warps 8-11 are the producer (synchronised among themselves by a named barrier).
-// The producer gathers each batch's per-entry records,
+// consumers; warps 8-10 build (synchronised among themselves by a named barrier) and warp 11
+// issues the MMAs.  The builders gather each batch's per-entry records,
 // builds its phasor operand B, issues its MMAs into one of kWsR stages of shared memory and
 // TMEM, and flushes the gradients of batches the consumers have finished; the consumers walk
 // the batches at their own pace, each warp signalling when it is done with a stage.  No
@@ -1049,8 +1049,8 @@ __device__ __forceinline__ TbMeta tb_meta(uint8_t* base) {
 // ---------------------------------------------------------------------------------------------
 
 constexpr int kWsR = 3;
-constexpr int kWsProd = 128;                   // producer threads (four warps)
-constexpr int kWsThreads = kThreads + kWsProd;
+constexpr int kWsProd = 96;                    // builder threads (three warps)
+constexpr int kWsThreads = kThreads + kWsProd + 32;   // + the MMA-issuing warp
 
 __device__ __forceinline__ void producer_sync() {
     asm volatile("bar.sync 1, %0;" ::"n"(kWsProd) : "memory");
@@ -1082,8 +1082,8 @@ struct RWsSmem {
     static constexpr int kRedStage = 8 * kTbE * 9 * 4;
     static constexpr int kRed = kMeta + kWsR * kMetaStage;         // float [stage][warp][E][9]
     static constexpr int kMask = kRed + kWsR * kRedStage;          // uint64 [stage][warp]
-    static constexpr int kBar = kMask + kWsR * 8 * 8;              // full[R], empty[R]
-    static constexpr int kTotal = kBar + 2 * kWsR * 8 + 16;        // + TMEM slot, maxlast, error
+    static constexpr int kBar = kMask + kWsR * 8 * 8;              // full[R], empty[R], bready[R]
+    static constexpr int kTotal = kBar + 3 * kWsR * 8 + 16;        // + TMEM slot, maxlast, error
     static constexpr uint32_t kStageCols = 2 * 3 * kTbE;           // both halves of a stage
     static constexpr uint32_t kCols = 512;
     static_assert(kWsR * kStageCols <= kCols, "TMEM stages");
@@ -1095,7 +1095,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
     using L = RWsSmem<S>;
     extern __shared__ __align__(1024) uint8_t sm[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::kBar);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::kBar + 2 * kWsR * 8);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::kBar + 3 * kWsR * 8);
     uint32_t* s_maxlast = tslot + 1;
     volatile uint32_t* s_err = tslot + 2;
     auto red_at = [&](int st, int w, int j, int c) -> float& {
@@ -1104,17 +1104,19 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
     auto mask_at = [&](int st, int w) -> uint64_t& { return reinterpret_cast<uint64_t*>(sm + L::kMask)[st * 8 + w]; };
     auto full_bar = [&](int st) { return smem_u32(&bars[st]); };
     auto empty_bar = [&](int st) { return smem_u32(&bars[kWsR + st]); };
+    auto bready_bar = [&](int st) { return smem_u32(&bars[2 * kWsR + st]); };
 
     const int strip = blockIdx.x, tile = blockIdx.y, b = blockIdx.z;
     const int k0 = strip * S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool producer = warp >= kThreads / 32;
-    const int prod = tid - kThreads;   // producer thread index (0..127) when producer
-    const int ptid = producer ? 0 : tid;   // pixel of a consumer thread
+    const bool issuer = warp == (kThreads + kWsProd) / 32;
+    const bool producer = warp >= kThreads / 32 && !issuer;
+    const int prod = tid - kThreads;   // builder thread index (0..95) when producer
+    const int ptid = (producer || issuer) ? 0 : tid;   // pixel of a consumer thread
     const int half = ptid >> 7, m = ptid & 127;
     const int tx0 = (tile % a.TW) * kTile, ty0 = (tile / a.TW) * kTile;
     const int x = tx0 + (ptid & 15), y = ty0 + (ptid >> 4);
-    const bool inside = !producer && x < a.W && y < a.H;
+    const bool inside = !producer && !issuer && x < a.W && y < a.H;
     const float ux = (float)x + 0.5f, uy = (float)y + 0.5f;
     const float wcx = (float)tx0 + 8.0f, wcy = (float)(ty0 + 2 * warp) + 1.0f;
     const uint2 range = a.ranges[tile];
@@ -1125,6 +1127,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
         for (int st = 0; st < kWsR; ++st) {
             mbar_init(full_bar(st), 2);
             mbar_init(empty_bar(st), kThreads / 32);
+            mbar_init(bready_bar(st), 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *s_maxlast = 0;
@@ -1137,7 +1140,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     // A operand (consumers): this pixel's upstream gradient over the strip, split hi / lo
-    if (!producer) {
+    if (!producer && !issuer) {
         uint8_t* Ahi = sm + L::kA + (half * 2 + 0) * L::kATile;
         uint8_t* Alo = sm + L::kA + (half * 2 + 1) * L::kATile;
 #pragma unroll 4
@@ -1181,9 +1184,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
     };
 
     if (producer) {
-        // ---------------- producer warps
-        constexpr uint32_t idesc = make_idesc(128, 3 * kTbE);
-        const uint32_t a_base = smem_u32(sm + L::kA), b_base = smem_u32(sm + L::kB);
+        // ---------------- builder warps
         const bool gatherer = prod < kTbE;   // threads 0..E-1 of the first producer warp
         uint32_t pf_gid = 0xffffffffu;
         float4 pf_p0 = make_float4(0.f, 0.f, 0.f, 0.f), pf_p1 = pf_p0, pf_at = pf_p0;
@@ -1285,26 +1286,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
             }
             fence_async_smem();
             producer_sync();   // the operand is complete
-            if (prod == 0) {
-                tc_fence_after();
-                const uint32_t bhi = b_base + (st * 2 + 0) * L::kBTile, blo = b_base + (st * 2 + 1) * L::kBTile;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t ahi = a_base + (h * 2 + 0) * L::kATile, alo = a_base + (h * 2 + 1) * L::kATile;
-                    const uint32_t d = tbase + (uint32_t)(st * L::kStageCols + h * 3 * kTbE);
-                    const uint32_t as_[3] = {ahi, alo, ahi};
-                    const uint32_t bs_[3] = {bhi, bhi, blo};
-#pragma unroll
-                    for (int t = 0; t < 3; ++t)
-#pragma unroll
-                        for (int q = 0; q < L::kKa / 16; ++q)
-                            mma_bf16(d, make_desc(as_[t] + q * 256, 128, L::kKa * 16),
-                                     make_desc(bs_[t] + q * 256, 128, L::kKa * 16), idesc,
-                                     (t > 0 || q > 0) ? 1u : 0u);
-                }
-                mma_commit(full_bar(st));
-                mbar_arrive(full_bar(st));   // the stage's records, released
-            }
+            if (prod == 0) mbar_arrive(bready_bar(st));   // records and B of the stage, released
         }
         // flush the batches still held by the stages
         for (int i = nbatch > kWsR ? nbatch - kWsR : 0; i < nbatch; ++i) {
@@ -1312,6 +1294,38 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
             if (!wait_ok(empty_bar(st), (uint32_t)(i / kWsR) & 1u)) break;
             tc_fence_after();
             flush(i, st);
+        }
+    } else if (issuer) {
+        // ---------------- MMA-issuing warp: waits for a stage's operand, issues its products
+        constexpr uint32_t idesc = make_idesc(128, 3 * kTbE);
+        const uint32_t a_base = smem_u32(sm + L::kA), b_base = smem_u32(sm + L::kB);
+        for (int i = 0; i < nbatch; ++i) {
+            const int st = i % kWsR;
+            if (!wait_ok(bready_bar(st), (uint32_t)(i / kWsR) & 1u)) break;
+            if (lane == 0) {
+                tc_fence_after();
+                // descriptors of the K-step-0 core matrices; a K step is 256 bytes further,
+                // i.e. +16 in the descriptor's address field (no carry: shared addresses < 256 KB)
+                const uint64_t bd[3] = {make_desc(b_base + (st * 2 + 0) * L::kBTile, 128, L::kKa * 16),
+                                        make_desc(b_base + (st * 2 + 0) * L::kBTile, 128, L::kKa * 16),
+                                        make_desc(b_base + (st * 2 + 1) * L::kBTile, 128, L::kKa * 16)};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint64_t ad[3] = {make_desc(a_base + (h * 2 + 0) * L::kATile, 128, L::kKa * 16),
+                                            make_desc(a_base + (h * 2 + 1) * L::kATile, 128, L::kKa * 16),
+                                            make_desc(a_base + (h * 2 + 0) * L::kATile, 128, L::kKa * 16)};
+                    const uint32_t d = tbase + (uint32_t)(st * L::kStageCols + h * 3 * kTbE);
+#pragma unroll
+                    for (int t = 0; t < 3; ++t)
+#pragma unroll
+                        for (int q = 0; q < L::kKa / 16; ++q)
+                            mma_bf16(d, ad[t] + (uint64_t)(q * 16), bd[t] + (uint64_t)(q * 16), idesc,
+                                     (t > 0 || q > 0) ? 1u : 0u);
+                }
+                mma_commit(full_bar(st));
+                mbar_arrive(full_bar(st));   // the builders' release, passed on to the consumers
+            }
+            __syncwarp();
         }
     } else {
         // ---------------- consumer warps: one pixel per thread
@@ -1336,51 +1350,76 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
             }
             const uint64_t mask = warp_entry_mask(mdp.geo, mdp.ext, nbp, wcx, wcy, a.W);
             if (lane == 0) mask_at(st, warp) = mask;
+            // entries in pairs (2p+1, 2p), back to front: both entries' alpha, gradient
+            // components and warp reductions sit in one block so their latencies overlap
 #pragma unroll
-            for (int j = kTbE - 1; j >= 0; --j) {
-                if (!((mask >> j) & 1ull)) continue;   // warp-uniform
-                float gr[9];
+            for (int p = kTbE / 2 - 1; p >= 0; --p) {
+                const uint32_t pm = (uint32_t)(mask >> (2 * p)) & 3u;
+                if (!pm) continue;   // warp-uniform
+                float gr[2][9], dxv[2], dyv[2], Gv[2], alv[2];
+                bool live[2], clv[2];
 #pragma unroll
-                for (int c = 0; c < 9; ++c) gr[c] = 0.f;
-                bool contrib = false;
-                const uint32_t pos = lo_pos + (uint32_t)j;
-                if (pos < last) {
+                for (int h = 0; h < 2; ++h) {
+                    const int j = 2 * p + 1 - h;
                     const float4 gg = mdp.geo[j];
                     const float2 g2 = mdp.geo2[j];
-                    float dx, dy, G, alpha;
-                    bool clamped;
-                    if (eval_alpha(ux, uy, a.W, gg, g2, dx, dy, G, alpha, clamped)) {
-                        contrib = true;
-                        const float nl = lg2(__fsub_rn(1.0f, alpha));
-                        const float logT_before = __fsub_rn(logT, nl);
-                        const float T = ex2(logT_before);
-                        const float w = T * alpha;
-                        const float reG = v[3 * j], imG = v[3 * j + 1], imF = v[3 * j + 2];
-                        const float amp = mdp.amp[j];
-                        const float reGa = amp * reG;
-                        const float dalpha = T * reGa - suffix / (1.0f - alpha);
-                        suffix = fmaf(w, reGa, suffix);
-                        gr[6] = w * reG;
-                        gr[7] = -w * amp * imG;
-                        gr[8] = w * amp * (c_f0 * imG + c_df * imF);
-                        if (!clamped) {
-                            const float sig = g2.y;
-                            gr[5] = dalpha * G;
-                            const float dq = -0.5f * dalpha * sig * G;
-                            gr[0] = dq * (-2.0f * (gg.z * dx + gg.w * dy));
-                            gr[1] = dq * (-2.0f * (gg.w * dx + g2.x * dy));
-                            gr[2] = dq * dx * dx;
-                            gr[3] = dq * 2.0f * dx * dy;
-                            gr[4] = dq * dy * dy;
-                        }
-                        logT = logT_before;
-                    }
+                    float dx = __fsub_rn(ux, gg.x);
+                    const float hw = 0.5f * (float)a.W;
+                    dx = dx >= hw ? __fsub_rn(dx, (float)a.W) : (dx < -hw ? __fadd_rn(dx, (float)a.W) : dx);
+                    const float dy = __fsub_rn(uy, gg.y);
+                    float q = __fmul_rn(__fmul_rn(g2.x, dy), dy);
+                    q = __fmaf_rn(__fmul_rn(__fmul_rn(2.0f, gg.w), dx), dy, q);
+                    q = __fmaf_rn(__fmul_rn(gg.z, dx), dx, q);
+                    const float G = ex2(__fmul_rn(-0.5f * kLog2e, q));
+                    const float a0 = __fmul_rn(g2.y, G);
+                    clv[h] = a0 > kAlphaMax;
+                    const float alpha = clv[h] ? kAlphaMax : a0;
+                    live[h] = ((pm >> (1 - h)) & 1u) && lo_pos + (uint32_t)j < last && q <= kQMax &&
+                              alpha >= kAlphaMin;
+                    alv[h] = live[h] ? alpha : 0.f;
+                    Gv[h] = live[h] ? G : 0.f;
+                    dxv[h] = live[h] ? dx : 0.f;
+                    dyv[h] = live[h] ? dy : 0.f;
                 }
-                if (__any_sync(0xffffffffu, contrib)) {
-                    const float tot = warp_reduce_scatter9(gr, lane);
-                    if ((lane & 1) == 0 && (lane >> 1) < 9) red_at(st, warp, j, lane >> 1) = tot;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = 2 * p + 1 - h;
+                    const float alpha = alv[h];
+                    const float nl = live[h] ? lg2(__fsub_rn(1.0f, alpha)) : 0.f;
+                    const float logT_before = __fsub_rn(logT, nl);
+                    const float T = ex2(logT_before);
+                    const float w = T * alpha;
+                    const float reG = v[3 * j], imG = v[3 * j + 1], imF = v[3 * j + 2];
+                    const float amp = mdp.amp[j];
+                    const float reGa = amp * reG;
+                    const float dalpha = T * reGa - suffix / (1.0f - alpha);
+                    suffix = fmaf(w, reGa, suffix);
+                    logT = logT_before;
+                    gr[h][6] = w * reG;
+                    gr[h][7] = -w * amp * imG;
+                    gr[h][8] = w * amp * (c_f0 * imG + c_df * imF);
+                    const float da = (live[h] && !clv[h]) ? dalpha : 0.f;
+                    const float4 gg = mdp.geo[j];
+                    const float2 g2 = mdp.geo2[j];
+                    const float G = Gv[h], dx = dxv[h], dy = dyv[h];
+                    gr[h][5] = da * G;
+                    const float dq = -0.5f * da * g2.y * G;
+                    gr[h][0] = dq * (-2.0f * (gg.z * dx + gg.w * dy));
+                    gr[h][1] = dq * (-2.0f * (gg.w * dx + g2.x * dy));
+                    gr[h][2] = dq * dx * dx;
+                    gr[h][3] = dq * 2.0f * dx * dy;
+                    gr[h][4] = dq * dy * dy;
+                }
+                if (__any_sync(0xffffffffu, live[0] || live[1])) {
+                    const float t1 = warp_reduce_scatter9(gr[0], lane);
+                    const float t0 = warp_reduce_scatter9(gr[1], lane);
+                    if ((lane & 1) == 0 && (lane >> 1) < 9) {
+                        red_at(st, warp, 2 * p + 1, lane >> 1) = t1;
+                        red_at(st, warp, 2 * p, lane >> 1) = t0;
+                    }
                 } else if (lane < 9) {
-                    red_at(st, warp, j, lane) = 0.f;
+                    red_at(st, warp, 2 * p + 1, lane) = 0.f;
+                    red_at(st, warp, 2 * p, lane) = 0.f;
                 }
             }
             tc_fence_before();
