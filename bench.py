@@ -359,10 +359,15 @@ def run_ours(args, rank, world, local_rank):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12      # TFLOP/s
     unit_flop = {"render_bwd": FLOP_BWD_UNIT, "render_fwd": FLOP_FWD_UNIT}
+    # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the tensor-core
+    # compositing kernels in this step (50k Gaussians, 64 subcarriers, 360x90, one transmitter),
+    # from one ncu capture of the current kernels; the forward's figure includes the fused loss
+    traffic = {"render_bwd": 17339392, "render_fwd": 17104640} if args.render == "tc" else {}
     if top in unit_flop:
         achieved = units * unit_flop[top] / (avg[top] * 1e-3) / 1e12
         roofline = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                    "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                    "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic.get(top),
+                    "traffic_unit": "bytes per launch (DRAM read + write)",
                     "peak_note": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)"
                                  % (sms, sm_max)}
     else:
