@@ -546,15 +546,37 @@ extern "C" int gsparc_render_bwd(const gsparc_view* view, const gsparc_band* ban
 // as a [128 pixels x E] x [E x 2S] product per half tile on the tensor cores, accumulating in
 // TMEM (FP32).  Both operands are split into BF16 hi/lo terms laid side by side along K
 // ([w_hi | w_lo | w_hi] . [s_hi | s_hi | s_lo]), so every product carries ~16 mantissa bits
-// and the sum is accumulated in FP32.  A and B are double-buffered: the CUDA cores build
-// batch i+1 while the tensor cores consume batch i; tcgen05.commit on a per-stage mbarrier
-// frees a stage.  Every mbarrier wait is bounded; an expired wait poisons the strip with NaN.
+// and the sum is accumulated in FP32.  A and B are double-buffered and the kernel is
+// warp-specialised (below): the pixel warps build A, builder warps build B, one warp issues the
+// MMAs; tcgen05.commit on a per-stage mbarrier frees a stage.  Every mbarrier wait is bounded;
+// an expired wait poisons the strip with NaN.
 // =============================================================================================
 
 #include "tc.cuh"
 
 namespace gsparc {
 namespace {
+
+// Warp-specialised kernels: builder warps synchronise among themselves by named barrier 1.
+constexpr int kWsProd = 96;                    // builder threads (three warps)
+
+__device__ __forceinline__ void producer_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kWsProd) : "memory");
+}
+
+// Barrier of the producer warps that also ANDs a flag over them: every producer thread takes
+// the same branch afterwards (a warp leaving the loop alone would strand the others at the
+// next producer_sync).
+__device__ __forceinline__ bool producer_all(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kWsProd)
+        : "memory");
+    return r != 0;
+}
 
 constexpr int kTcE = 32;            // list entries per batch
 constexpr int kTcKt = 3 * kTcE;     // three split-BF16 terms along K
@@ -575,14 +597,39 @@ struct RTcSmem {
     static constexpr int kLen = kPhi + 2 * kTcE * 4;
     static constexpr int kCsi = kLen + 2 * kTcE * 4;          // float[8 warps][2S]: CSI partial sums
     static constexpr int kL2 = kCsi + 8 * 2 * S * 4;          // float[8 warps]: loss partial sums
-    static constexpr int kBar = kL2 + 8 * 4;                  // 2 mbarriers + TMEM slot
-    static constexpr int kTotal = kBar + 32;
+    static constexpr int kBar = kL2 + 8 * 4;                  // start of the mbarriers
     static constexpr uint32_t kCols = (4 * S <= 32) ? 32 : (4 * S <= 64 ? 64 : (4 * S <= 128 ? 128 : 256));
 };
 
+// ---------------------------------------------------------------------------------------------
+// Warp-specialised form of the tensor-core forward.  Warps 0-7 (one pixel per thread) compute
+// the weights w = T alpha of each batch and write their rows of the A operand; warps 8-10
+// (builders) publish each batch's records and build the phasor operand B; warp 11 issues the
+// MMAs once both operands of a stage are in place.  mbarriers per stage (two stages):
+//   rec[s]    (1): the builders released the batch's records            -> pixel warps
+//   bready[s] (1): B of the batch is complete                            -> MMA warp
+//   aready[s] (8): one arrival per pixel warp after writing its A rows   -> MMA warp
+//   mdone[s]  (1): tcgen05.commit of the batch's MMAs (stage free again) -> builders, pixel warps
+// The builders end the stream (batch count in shared memory, published with rec/bready) when
+// the tile list is exhausted or every pixel warp reports all its pixels terminated; a pixel warp
+// that is done keeps writing zero rows until then.  Every wait is bounded; an expired wait
+// raises a shared error flag and the outputs are poisoned with NaN.
+// ---------------------------------------------------------------------------------------------
+
+constexpr int kFwsThreads = kThreads + kWsProd + 32;
+
 template <int S>
-__global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
+struct RFwsSmem {
+    using T = RTcSmem<S>;
+    static constexpr int kBars = T::kBar;                     // rec[2], bready[2], aready[2], mdone[2]
+    static constexpr int kMisc = kBars + 8 * 8;               // TMEM slot, done warps, batch count, error, end
+    static constexpr int kTotal = kMisc + 32;
+};
+
+template <int S>
+__global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) {
     using L = RTcSmem<S>;
+    using F = RFwsSmem<S>;
     extern __shared__ __align__(1024) uint8_t sm[];
     float4* s_geo = reinterpret_cast<float4*>(sm + L::kGeo);
     float2* s_geo2 = reinterpret_cast<float2*>(sm + L::kGeo2);
@@ -590,60 +637,46 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
     float* s_amp = reinterpret_cast<float*>(sm + L::kAmp);
     float* s_phi = reinterpret_cast<float*>(sm + L::kPhi);
     float* s_len = reinterpret_cast<float*>(sm + L::kLen);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::kBar);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::kBar + 16);
+    float* s_csi = reinterpret_cast<float*>(sm + L::kCsi);   // [warp][2S], every slot written once
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + F::kBars);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + F::kMisc);
+    volatile uint32_t* s_done = tslot + 1;
+    volatile uint32_t* s_nbat = tslot + 2;
+    volatile uint32_t* s_err = tslot + 3;
+    volatile uint32_t* s_end = tslot + 4;
+    auto rec_bar = [&](int st) { return smem_u32(&bars[st]); };
+    auto bready_bar = [&](int st) { return smem_u32(&bars[2 + st]); };
+    auto aready_bar = [&](int st) { return smem_u32(&bars[4 + st]); };
+    auto mdone_bar = [&](int st) { return smem_u32(&bars[6 + st]); };
 
     const int strip = blockIdx.x, tile = blockIdx.y, b = blockIdx.z;
     const int k0 = strip * S;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int half = tid >> 7, m = tid & 127;
-    float* s_csi = reinterpret_cast<float*>(sm + L::kCsi);   // [warp][2S], every slot written once
-    // gather of one batch's per-entry records into registers (threads tid < E), and its
-    // publication into one of the two record buffers
-    uint32_t pf_gid = 0xffffffffu;
-    float4 pf_p0 = make_float4(0.f, 0.f, 0.f, 0.f), pf_p1 = pf_p0, pf_at = pf_p0;
-    auto gather = [&](uint32_t pos, uint32_t end) {
-        if (tid < kTcE) {
-            pf_gid = pos + tid < end ? a.ids[pos + tid] : 0xffffffffu;
-            if (pf_gid < (uint32_t)a.N) {
-                pf_p0 = a.proj[2 * pf_gid];
-                pf_p1 = a.proj[2 * pf_gid + 1];
-                pf_at = a.attr[(size_t)b * a.N + pf_gid];
-            }
-        }
-    };
-    auto publish = [&](int mb) {
-        if (tid < kTcE) {
-            const int e = mb * kTcE + tid;
-            if (pf_gid < (uint32_t)a.N) {
-                s_geo[e] = make_float4(pf_p0.x, pf_p0.y, pf_p1.x, pf_p1.y);
-                s_geo2[e] = make_float2(pf_p1.z, pf_at.z);
-                s_ext[e] = make_float2(pf_p0.z, pf_p0.w);
-                s_amp[e] = pf_at.x;
-                s_phi[e] = pf_at.y;
-                s_len[e] = pf_at.w;
-            } else {
-                s_geo[e] = make_float4(0.f, 0.f, __int_as_float(0x7fc00000), 0.f);
-                s_geo2[e] = make_float2(0.f, 0.f);
-                s_ext[e] = make_float2(-1.f, -1.f);
-                s_amp[e] = 0.f;
-                s_phi[e] = 0.f;
-                s_len[e] = 0.f;
-            }
-        }
-    };
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool pixel = tid < kThreads;
+    const bool mma_warp = warp == (kThreads + kWsProd) / 32;
+    const bool builder = !pixel && !mma_warp;
+    const int prod = tid - kThreads;   // builder thread index (0..95)
+    const int ptid = pixel ? tid : 0;
+    const int half = ptid >> 7, m = ptid & 127;
     const int tx0 = (tile % a.TW) * kTile, ty0 = (tile / a.TW) * kTile;
-    const int x = tx0 + (tid & 15), y = ty0 + (tid >> 4);
-    const bool inside = x < a.W && y < a.H;
+    const int x = tx0 + (ptid & 15), y = ty0 + (ptid >> 4);
+    const bool inside = pixel && x < a.W && y < a.H;
     const float ux = (float)x + 0.5f, uy = (float)y + 0.5f;
     const float wcx = (float)tx0 + 8.0f, wcy = (float)(ty0 + 2 * warp) + 1.0f;
     const uint2 range = a.ranges[tile];
 
-    const uint32_t bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
     if (tid == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar1, 1);
+        for (int st = 0; st < 2; ++st) {
+            mbar_init(rec_bar(st), 1);
+            mbar_init(bready_bar(st), 1);
+            mbar_init(aready_bar(st), kThreads / 32);
+            mbar_init(mdone_bar(st), 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *s_done = 0u;
+        *s_nbat = 0xffffffffu;
+        *s_err = 0u;
+        *s_end = 0u;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -655,228 +688,297 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
-    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-    constexpr uint32_t idesc = make_idesc(128, 2 * S);
-    const uint32_t a_base = smem_u32(sm + L::kA), b_base = smem_u32(sm + L::kB);
+    auto wait_ok = [&](uint32_t bar, uint32_t parity) {
+        bool w = (*s_err == 0u) && mbar_wait(bar, parity);
+        w = __all_sync(0xffffffffu, w);
+        if (!w && lane == 0) *s_err = 1u;
+        return w;
+    };
 
     float logT = 0.f;
     uint32_t last = 0, used = 0;
-    bool done = !inside;
-    uint32_t ph0 = 0, ph1 = 0;
-    bool pend0 = false, pend1 = false, any_mma = false, ok = true;
-    int it = 0;
-    gather(range.x, range.y);
-    publish(0);
-    volatile uint32_t* s_ok = reinterpret_cast<volatile uint32_t*>(sm + L::kBar + 20);
-    if (tid == 0) *s_ok = 1u;
-    for (uint32_t bs = range.x; bs < range.y; bs += kTcE, ++it) {
-        const int st = it & 1;
-        // thread 0 waits until the MMAs issued two batches ago (same stage) completed; the one
-        // barrier below then both releases the stage and tells whether any pixel is still live
-        if (tid == 0) {
-            bool wok = true;
-            if (st == 0 && pend0) wok = mbar_wait(bar0, ph0);
-            if (st == 1 && pend1) wok = mbar_wait(bar1, ph1);
-            if (!wok) *s_ok = 0u;
-        }
-        // every thread tracks the phases the same way (the final drain waits in all threads)
-        if (st == 0 && pend0) { ph0 ^= 1; pend0 = false; }
-        if (st == 1 && pend1) { ph1 ^= 1; pend1 = false; }
-        const int live = __syncthreads_or(!done);
-        ok = *s_ok != 0u;
-        if (!ok || live == 0) break;
-        tc_fence_after();
-        const int mb = it & 1;   // record buffer of this batch
-        gather(bs + kTcE, range.y);   // next batch's records, consumed after this batch's work
-        const float4* geo = s_geo + mb * kTcE;
-        const float2* geo2 = s_geo2 + mb * kTcE;
-        const float2* ext = s_ext + mb * kTcE;
-        const float* amp = s_amp + mb * kTcE;
-        const float* phi = s_phi + mb * kTcE;
-        const float* len = s_len + mb * kTcE;
-        const int nb = (int)min((uint32_t)kTcE, range.y - bs);
-        // ---- B: amplitude-scaled phasors of the strip, [hi | hi | lo] along K
-        uint8_t* Bst = sm + L::kB + st * L::kBStage;
-        for (int e = tid; e < S * (kTcE / 8); e += kThreads) {
-            const int kk = e % S, j0 = (e / S) * 8;
-            const int k = k0 + kk;
-            float re[8], im[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int j = j0 + q;
-                re[q] = 0.f;
-                im[q] = 0.f;
-                if (j < nb && k < a.K) {
-                    const float2 ph = unit_phasor(a, len[j], phi[j], k);
-                    re[q] = amp[j] * ph.x;
-                    im[q] = amp[j] * ph.y;
+    if (builder) {
+        // ---------------- builder warps: records and the phasor operand
+        const bool gatherer = prod < kTcE;
+        uint32_t pf_gid = 0xffffffffu;
+        float4 pf_p0 = make_float4(0.f, 0.f, 0.f, 0.f), pf_p1 = pf_p0, pf_at = pf_p0;
+        auto gather = [&](uint32_t pos) {
+            if (gatherer) {
+                pf_gid = pos + prod < range.y ? a.ids[pos + prod] : 0xffffffffu;
+                if (pf_gid < (uint32_t)a.N) {
+                    pf_p0 = a.proj[2 * pf_gid];
+                    pf_p1 = a.proj[2 * pf_gid + 1];
+                    pf_at = a.attr[(size_t)b * a.N + pf_gid];
                 }
             }
-            uint4 RH, RL, IH, IL;
-            split8(re, RH, RL);
-            split8(im, IH, IL);
-            const int nre = 2 * kk, nim = 2 * kk + 1;
-            *reinterpret_cast<uint4*>(Bst + canon_off(nre, j0, kTcKt)) = RH;
-            *reinterpret_cast<uint4*>(Bst + canon_off(nre, kTcE + j0, kTcKt)) = RH;
-            *reinterpret_cast<uint4*>(Bst + canon_off(nre, 2 * kTcE + j0, kTcKt)) = RL;
-            *reinterpret_cast<uint4*>(Bst + canon_off(nim, j0, kTcKt)) = IH;
-            *reinterpret_cast<uint4*>(Bst + canon_off(nim, kTcE + j0, kTcKt)) = IH;
-            *reinterpret_cast<uint4*>(Bst + canon_off(nim, 2 * kTcE + j0, kTcKt)) = IL;
+        };
+        gather(range.x);
+        for (int i = 0;; ++i) {
+            const int st = i & 1;
+            if (i >= 2) {
+                // the MMAs of batch i-2 are done: the stage's A, B and records are free
+                const bool w = wait_ok(mdone_bar(st), (uint32_t)((i >> 1) - 1) & 1u);
+                if (!producer_all(w)) break;
+            }
+            const uint32_t bs = range.x + (uint32_t)i * kTcE;
+            if (prod == 0) *s_end = (bs >= range.y || *s_done >= (uint32_t)(kThreads / 32)) ? 1u : 0u;
+            producer_sync();
+            if (*s_end) {
+                if (prod == 0) {
+                    *s_nbat = (uint32_t)i;
+                    mbar_arrive(rec_bar(st));
+                    mbar_arrive(bready_bar(st));
+                }
+                break;
+            }
+            if (gatherer) {
+                const int e = st * kTcE + prod;
+                if (pf_gid < (uint32_t)a.N) {
+                    s_geo[e] = make_float4(pf_p0.x, pf_p0.y, pf_p1.x, pf_p1.y);
+                    s_geo2[e] = make_float2(pf_p1.z, pf_at.z);
+                    s_ext[e] = make_float2(pf_p0.z, pf_p0.w);
+                    s_amp[e] = pf_at.x;
+                    s_phi[e] = pf_at.y;
+                    s_len[e] = pf_at.w;
+                } else {
+                    s_geo[e] = make_float4(0.f, 0.f, __int_as_float(0x7fc00000), 0.f);
+                    s_geo2[e] = make_float2(0.f, 0.f);
+                    s_ext[e] = make_float2(-1.f, -1.f);
+                    s_amp[e] = 0.f;
+                    s_phi[e] = 0.f;
+                    s_len[e] = 0.f;
+                }
+            }
+            gather(bs + kTcE);
+            producer_sync();
+            if (prod == 0) mbar_arrive(rec_bar(st));   // the records, released to the pixel warps
+            const int nb = (int)min((uint32_t)kTcE, range.y - bs);
+            const float* amp = s_amp + st * kTcE;
+            const float* phi = s_phi + st * kTcE;
+            const float* len = s_len + st * kTcE;
+            uint8_t* Bst = sm + L::kB + st * L::kBStage;
+            for (int e = prod; e < S * (kTcE / 8); e += kWsProd) {
+                const int kk = e % S, j0 = (e / S) * 8;
+                const int k = k0 + kk;
+                float re[8], im[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int j = j0 + q;
+                    re[q] = 0.f;
+                    im[q] = 0.f;
+                    if (j < nb && k < a.K) {
+                        const float2 ph = unit_phasor(a, len[j], phi[j], k);
+                        re[q] = amp[j] * ph.x;
+                        im[q] = amp[j] * ph.y;
+                    }
+                }
+                uint4 RH, RL, IH, IL;
+                split8(re, RH, RL);
+                split8(im, IH, IL);
+                const int nre = 2 * kk, nim = 2 * kk + 1;
+                *reinterpret_cast<uint4*>(Bst + canon_off(nre, j0, kTcKt)) = RH;
+                *reinterpret_cast<uint4*>(Bst + canon_off(nre, kTcE + j0, kTcKt)) = RH;
+                *reinterpret_cast<uint4*>(Bst + canon_off(nre, 2 * kTcE + j0, kTcKt)) = RL;
+                *reinterpret_cast<uint4*>(Bst + canon_off(nim, j0, kTcKt)) = IH;
+                *reinterpret_cast<uint4*>(Bst + canon_off(nim, kTcE + j0, kTcKt)) = IH;
+                *reinterpret_cast<uint4*>(Bst + canon_off(nim, 2 * kTcE + j0, kTcKt)) = IL;
+            }
+            fence_async_smem();
+            producer_sync();
+            if (prod == 0) mbar_arrive(bready_bar(st));
         }
-        // ---- A: this pixel's weights for the batch
-        float wv[kTcE];
+    } else if (mma_warp) {
+        // ---------------- MMA warp
+        constexpr uint32_t idesc = make_idesc(128, 2 * S);
+        const uint32_t a_base = smem_u32(sm + L::kA), b_base = smem_u32(sm + L::kB);
+        for (int i = 0;; ++i) {
+            const int st = i & 1;
+            const uint32_t ph = (uint32_t)(i >> 1) & 1u;
+            if (!wait_ok(bready_bar(st), ph)) break;
+            if ((uint32_t)i >= *s_nbat) break;
+            if (!wait_ok(aready_bar(st), ph)) break;
+            if (lane == 0) {
+                tc_fence_after();
+                const uint64_t bd = make_desc(b_base + st * L::kBStage, 128, kTcKt * 16);
 #pragma unroll
-        for (int j = 0; j < kTcE; ++j) wv[j] = 0.f;
-        const uint64_t mask = warp_entry_mask(geo, ext, nb, wcx, wcy, a.W);
-        if (!done) {
-            // phase 1: alpha and log2(1 - alpha) of every entry, independent of each other
-            float al[kTcE], nlv[kTcE];
+                for (int h = 0; h < 2; ++h) {
+                    const uint64_t ad = make_desc(a_base + (st * 2 + h) * L::kAHalf, 128, kTcKt * 16);
 #pragma unroll
-            for (int j = 0; j < kTcE; ++j) {
-                al[j] = -1.f;
-                nlv[j] = 0.f;
-                if ((mask >> j) & 1ull) {   // warp-uniform
-                    float dx, dy, G, alpha;
-                    bool clamped;
-                    if (eval_alpha(ux, uy, a.W, geo[j], geo2[j], dx, dy, G, alpha, clamped)) {
-                        al[j] = alpha;
-                        nlv[j] = lg2(__fsub_rn(1.0f, alpha));
+                    for (int q = 0; q < kTcKt / 16; ++q)
+                        mma_bf16(tbase + h * 2 * S, ad + (uint64_t)(q * 16), bd + (uint64_t)(q * 16), idesc,
+                                 (i > 0 || q > 0) ? 1u : 0u);
+                }
+                mma_commit(mdone_bar(st));
+            }
+            __syncwarp();
+        }
+    } else {
+        // ---------------- pixel warps: the weights of each batch
+        bool done = !inside, counted = false;
+        for (int i = 0;; ++i) {
+            const int st = i & 1;
+            if (!wait_ok(rec_bar(st), (uint32_t)(i >> 1) & 1u)) break;
+            if ((uint32_t)i >= *s_nbat) break;
+            if (i >= 2 && !wait_ok(mdone_bar(st), (uint32_t)((i >> 1) - 1) & 1u)) break;
+            const uint32_t bs = range.x + (uint32_t)i * kTcE;
+            const int nb = (int)min((uint32_t)kTcE, range.y - bs);
+            const float4* geo = s_geo + st * kTcE;
+            const float2* geo2 = s_geo2 + st * kTcE;
+            const float2* ext = s_ext + st * kTcE;
+            float wv[kTcE];
+#pragma unroll
+            for (int j = 0; j < kTcE; ++j) wv[j] = 0.f;
+            if (__any_sync(0xffffffffu, !done)) {
+                const uint64_t mask = warp_entry_mask(geo, ext, nb, wcx, wcy, a.W);
+                if (!done) {
+                    // phase 1: alpha and log2(1 - alpha) of every entry, independent of each other
+                    float al[kTcE], nlv[kTcE];
+#pragma unroll
+                    for (int j = 0; j < kTcE; ++j) {
+                        al[j] = -1.f;
+                        nlv[j] = 0.f;
+                        if ((mask >> j) & 1ull) {   // warp-uniform
+                            float dx, dy, G, alpha;
+                            bool clamped;
+                            if (eval_alpha(ux, uy, a.W, geo[j], geo2[j], dx, dy, G, alpha, clamped)) {
+                                al[j] = alpha;
+                                nlv[j] = lg2(__fsub_rn(1.0f, alpha));
+                            }
+                        }
+                    }
+                    // phase 2: the transmittance recursion, one FADD per entry on the serial chain
+#pragma unroll
+                    for (int j = 0; j < kTcE; ++j) {
+                        if (al[j] < 0.f) continue;
+                        const float alpha = al[j], nl = nlv[j];
+                        if (__fadd_rn(logT, nl) < kLog2TMin) {
+                            done = true;
+                            break;
+                        }
+                        wv[j] = ex2(logT) * alpha;
+                        logT = __fadd_rn(logT, nl);
+                        last = bs - range.x + (uint32_t)j + 1u;
+                        ++used;
                     }
                 }
             }
-            // phase 2: the transmittance recursion, one FADD per entry on the serial chain
+            uint8_t* Ast = sm + L::kA + (st * 2 + half) * L::kAHalf;
 #pragma unroll
-            for (int j = 0; j < kTcE; ++j) {
-                if (al[j] < 0.f) continue;
-                const float alpha = al[j], nl = nlv[j];
-                if (__fadd_rn(logT, nl) < kLog2TMin) {
-                    done = true;
-                    break;
-                }
-                wv[j] = ex2(logT) * alpha;
-                logT = __fadd_rn(logT, nl);
-                last = bs - range.x + (uint32_t)j + 1u;
-                ++used;
+            for (int j0 = 0; j0 < kTcE; j0 += 8) {
+                float w8[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) w8[q] = wv[j0 + q];
+                uint4 H, Lo;
+                split8(w8, H, Lo);
+                *reinterpret_cast<uint4*>(Ast + canon_off(m, j0, kTcKt)) = H;
+                *reinterpret_cast<uint4*>(Ast + canon_off(m, kTcE + j0, kTcKt)) = Lo;
+                *reinterpret_cast<uint4*>(Ast + canon_off(m, 2 * kTcE + j0, kTcKt)) = H;
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(aready_bar(st));
+            if (!counted && __all_sync(0xffffffffu, done)) {
+                counted = true;
+                if (lane == 0) atomicAdd(const_cast<uint32_t*>(s_done), 1u);
             }
         }
-        uint8_t* Ast = sm + L::kA + (st * 2 + half) * L::kAHalf;
-#pragma unroll
-        for (int j0 = 0; j0 < kTcE; j0 += 8) {
-            float w8[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) w8[q] = wv[j0 + q];
-            uint4 H, Lo;
-            split8(w8, H, Lo);
-            *reinterpret_cast<uint4*>(Ast + canon_off(m, j0, kTcKt)) = H;
-            *reinterpret_cast<uint4*>(Ast + canon_off(m, kTcE + j0, kTcKt)) = Lo;
-            *reinterpret_cast<uint4*>(Ast + canon_off(m, 2 * kTcE + j0, kTcKt)) = H;
-        }
-        publish(mb ^ 1);   // the other buffer was last read by the previous batch
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (tid == 0) {
-            const uint32_t bst = b_base + st * L::kBStage;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t ast = a_base + (st * 2 + h) * L::kAHalf;
-#pragma unroll
-                for (int q = 0; q < kTcKt / 16; ++q)
-                    mma_bf16(tbase + h * 2 * S, make_desc(ast + q * 256, 128, kTcKt * 16),
-                             make_desc(bst + q * 256, 128, kTcKt * 16), idesc, (any_mma || q > 0) ? 1u : 0u);
-            }
-            mma_commit(st == 0 ? bar0 : bar1);
-        }
-        any_mma = true;
-        if (st == 0) pend0 = true;
-        else pend1 = true;
     }
+    // ---------------- epilogue: the accumulated spectrum of the strip
     const size_t plane = (size_t)a.H * a.W;
     const size_t pix = (size_t)y * a.W + x;
-    // fused loss: this pixel's targets for the strip, all loads in flight before the last wait
-    float2 tg[S];
-    if (a.l2_grad) {
-#pragma unroll
-        for (int kk = 0; kk < S; ++kk) {
-            const int k = k0 + kk;
-            tg[kk] = (inside && k < a.K) ? __ldcs(a.l2_target + ((size_t)b * a.K + k) * plane + pix)
-                                         : make_float2(0.f, 0.f);
-        }
+    const uint32_t nbat = *s_nbat;
+    const bool any_mma = nbat != 0xffffffffu && nbat > 0u;
+    if (pixel && any_mma) {
+        const int lb = (int)nbat - 1;
+        wait_ok(mdone_bar(lb & 1), (uint32_t)(lb >> 1) & 1u);
     }
-    bool wok = true;
-    if (pend0) wok = mbar_wait(bar0, ph0) && wok;
-    if (pend1) wok = mbar_wait(bar1, ph1) && wok;
-    ok = __syncthreads_and(wok && ok) != 0;
+    __syncthreads();
+    const bool ok = *s_err == 0u && nbat != 0xffffffffu;
     tc_fence_after();
     float l2acc = 0.f;
-#pragma unroll
-    for (int c = 0; c < 2 * S; c += 16) {
-        float v[16];
-        if (any_mma) {
-            tmem_ld16(tbase + half * 2 * S + lane_base + c, v);
-        } else {
-#pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = 0.f;
-        }
-        if (inside && a.spectrum) {
+    if (pixel) {
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        // fused loss: the targets of the next 8 subcarriers are loaded while a chunk is processed
+        float2 tg[8], tgn[8];
+        auto load_tg = [&](int c, float2 (&t)[8]) {
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int k = k0 + c / 2 + q;
-                if (k < a.K) {
-                    const float nan = __int_as_float(0x7fc00000);
-                    a.spectrum[((size_t)b * a.K + k) * plane + pix] =
-                        ok ? make_float2(v[2 * q], v[2 * q + 1]) : make_float2(nan, nan);
+                t[q] = (a.l2_grad && inside && k < a.K) ? __ldcs(a.l2_target + ((size_t)b * a.K + k) * plane + pix)
+                                                        : make_float2(0.f, 0.f);
+            }
+        };
+        load_tg(0, tg);
+#pragma unroll
+        for (int c = 0; c < 2 * S; c += 16) {
+            if (c + 16 < 2 * S) load_tg(c + 16, tgn);
+            float v[16];
+            if (any_mma) {
+                tmem_ld16(tbase + half * 2 * S + lane_base + c, v);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) v[q] = 0.f;
+            }
+            if (inside && a.spectrum) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int k = k0 + c / 2 + q;
+                    if (k < a.K) {
+                        const float nan = __int_as_float(0x7fc00000);
+                        a.spectrum[((size_t)b * a.K + k) * plane + pix] =
+                            ok ? make_float2(v[2 * q], v[2 * q + 1]) : make_float2(nan, nan);
+                    }
                 }
             }
-        }
-        if (inside && a.l2_grad) {
-            // fused loss: the same arithmetic as gsparc_l2_loss on this spectrum
+            if (inside && a.l2_grad) {
+                // fused loss: the same arithmetic as gsparc_l2_loss on this spectrum
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int k = k0 + c / 2 + q;
-                if (k < a.K) {
-                    const size_t e = ((size_t)b * a.K + k) * plane + pix;
-                    const float2 t = tg[c / 2 + q];
-                    const float zr = ok ? v[2 * q] : __int_as_float(0x7fc00000);
-                    const float dr = zr - t.x, di = v[2 * q + 1] - t.y;
-                    l2acc = fmaf(dr, dr, fmaf(di, di, l2acc));
-                    a.l2_grad[e] = make_float2(2.f * dr * a.l2_inv, 2.f * di * a.l2_inv);
+                for (int q = 0; q < 8; ++q) {
+                    const int k = k0 + c / 2 + q;
+                    if (k < a.K) {
+                        const size_t e = ((size_t)b * a.K + k) * plane + pix;
+                        const float2 t = tg[q];
+                        const float zr = ok ? v[2 * q] : __int_as_float(0x7fc00000);
+                        const float dr = zr - t.x, di = v[2 * q + 1] - t.y;
+                        l2acc = fmaf(dr, dr, fmaf(di, di, l2acc));
+                        a.l2_grad[e] = make_float2(2.f * dr * a.l2_inv, 2.f * di * a.l2_inv);
+                    }
                 }
             }
-        }
-        if (a.csi) {
-            // Eq. 2 over the CTA's pixels: a reduce-scatter of the 16 columns over the warp's 32
-            // pixels leaves column idx(lane) summed in the lane pair (lane, lane ^ 1)
-            float w[16];
+            if (a.csi) {
+                // Eq. 2 over the CTA's pixels: a reduce-scatter of the 16 columns over the warp's
+                // 32 pixels leaves column idx(lane) summed in the lane pair (lane, lane ^ 1)
+                float w[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) w[q] = inside ? (ok ? v[q] : __int_as_float(0x7fc00000)) : 0.f;
-            const int ln = tid & 31;
+                for (int q = 0; q < 16; ++q) w[q] = inside ? (ok ? v[q] : __int_as_float(0x7fc00000)) : 0.f;
 #pragma unroll
-            for (int o = 16, n = 8; o >= 2; o >>= 1, n >>= 1) {
-                const bool up = (ln & o) != 0;
+                for (int o = 16, n = 8; o >= 2; o >>= 1, n >>= 1) {
+                    const bool up = (lane & o) != 0;
 #pragma unroll
-                for (int q = 0; q < n; ++q) {
-                    const float send = up ? w[q] : w[q + n];
-                    const float keep = up ? w[q + n] : w[q];
-                    w[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                    for (int q = 0; q < n; ++q) {
+                        const float send = up ? w[q] : w[q + n];
+                        const float keep = up ? w[q + n] : w[q];
+                        w[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                    }
                 }
+                w[0] += __shfl_xor_sync(0xffffffffu, w[0], 1);
+                const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+                if ((lane & 1) == 0) s_csi[warp * 2 * S + c + idx] = w[0];
             }
-            w[0] += __shfl_xor_sync(0xffffffffu, w[0], 1);
-            const int idx = ((ln >> 4) & 1) * 8 + ((ln >> 3) & 1) * 4 + ((ln >> 2) & 1) * 2 + ((ln >> 1) & 1);
-            if ((ln & 1) == 0) s_csi[warp * 2 * S + c + idx] = w[0];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) tg[q] = tgn[q];
         }
-    }
-    if (inside && strip == 0) {
-        if (a.final_logT) a.final_logT[(size_t)b * plane + pix] = logT;
-        if (a.n_contrib) a.n_contrib[(size_t)b * plane + pix] = last;
-        if (a.n_used) a.n_used[(size_t)b * plane + pix] = used;
+        if (inside && strip == 0) {
+            if (a.final_logT) a.final_logT[(size_t)b * plane + pix] = logT;
+            if (a.n_contrib) a.n_contrib[(size_t)b * plane + pix] = last;
+            if (a.n_used) a.n_used[(size_t)b * plane + pix] = used;
+        }
     }
     float* s_l2 = reinterpret_cast<float*>(sm + L::kL2);
-    if (a.l2_grad) {
+    if (pixel && a.l2_grad) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) l2acc += __shfl_xor_sync(0xffffffffu, l2acc, o);
-        if ((tid & 31) == 0) s_l2[warp] = l2acc;
+        if (lane == 0) s_l2[warp] = l2acc;
     }
     tc_fence_before();
     __syncthreads();
@@ -886,7 +988,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
         atomicAdd(a.l2_loss, t * a.l2_inv);
     }
     if (a.csi) {
-        for (int e = tid; e < 2 * S; e += kThreads) {
+        for (int e = tid; e < 2 * S; e += kFwsThreads) {
             const int k = k0 + e / 2;
             float sum = 0.f;
 #pragma unroll
@@ -902,10 +1004,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_render_fwd_tc(RenderArgs a) {
 
 template <int S>
 int launch_fwd_tc(const RenderArgs& a, int T, cudaStream_t s) {
-    using L = RTcSmem<S>;
-    if (!ensure_smem_attr(k_render_fwd_tc<S>, L::kTotal)) return GSPARC_ERR_CUDA;
+    using F = RFwsSmem<S>;
+    if (!ensure_smem_attr(k_render_fwd_ws<S>, F::kTotal)) return GSPARC_ERR_CUDA;
     dim3 grid((a.K + S - 1) / S, T, a.B);
-    k_render_fwd_tc<S><<<grid, kThreads, L::kTotal, s>>>(a);
+    k_render_fwd_ws<S><<<grid, kFwsThreads, F::kTotal, s>>>(a);
     return launch_status();
 }
 
@@ -1049,26 +1151,7 @@ __device__ __forceinline__ TbMeta tb_meta(uint8_t* base) {
 // ---------------------------------------------------------------------------------------------
 
 constexpr int kWsR = 3;
-constexpr int kWsProd = 96;                    // builder threads (three warps)
 constexpr int kWsThreads = kThreads + kWsProd + 32;   // + the MMA-issuing warp
-
-__device__ __forceinline__ void producer_sync() {
-    asm volatile("bar.sync 1, %0;" ::"n"(kWsProd) : "memory");
-}
-
-// Barrier of the producer warps that also ANDs a flag over them: every producer thread takes
-// the same branch afterwards (a warp leaving the loop alone would strand the others at the
-// next producer_sync).
-__device__ __forceinline__ bool producer_all(bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
-        : "=r"(r)
-        : "r"((uint32_t)v), "n"(kWsProd)
-        : "memory");
-    return r != 0;
-}
 
 template <int S>
 struct RWsSmem {
