@@ -361,8 +361,8 @@ def run_ours(args, rank, world, local_rank):
     unit_flop = {"render_bwd": FLOP_BWD_UNIT, "render_fwd": FLOP_FWD_UNIT}
     # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the tensor-core
     # compositing kernels in this step (50k Gaussians, 64 subcarriers, 360x90, one transmitter),
-    # from one ncu capture of the current kernel
-    traffic = {"render_bwd": 17339392} if args.render == "tc" else {}
+    # from one ncu capture of each current kernel (the forward with its fused loss)
+    traffic = {"render_bwd": 17339392, "render_fwd": 17167104} if args.render == "tc" else {}
     if top in unit_flop:
         achieved = units * unit_flop[top] / (avg[top] * 1e-3) / 1e12
         roofline = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
