@@ -293,6 +293,10 @@ int gsparc_render_bwd(const gsparc_view* view, const gsparc_band* band, int32_t 
  * accumulation in tensor memory; the back-to-front recursion (recovered T,
  * suffix sums, alpha and conic derivatives) runs on the CUDA cores exactly as
  * in gsparc_render_bwd.  Gradients agree with gsparc_render_bwd to ~1e-5.
+ * The kernel is warp-specialised (producer warps build the phasor operand and
+ * issue the products; the pixel warps consume them through mbarriers).  An
+ * expired bounded wait leaves the gradients incomplete and adds NaN to
+ * d_attr[b,0,0] of the affected transmitter.
  */
 int gsparc_render_bwd_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
                          const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,

@@ -1512,6 +1512,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
     }
     tc_fence_before();
     __syncthreads();
+    // an expired wait left the gradients incomplete: make that visible
+    if (tid == 0 && *s_err != 0u) atomicAdd(reinterpret_cast<float*>(&a.d_attr[(size_t)b * a.N]), __int_as_float(0x7fc00000));
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(L::kCols) : "memory");
