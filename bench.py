@@ -179,7 +179,19 @@ def run_ours(args, rank, world, local_rank):
     launches_per_step = 0
     ev = {}
     render_fwd = G.gsparc_render_fwd_tc if args.render == "tc" else G.gsparc_render_fwd
-    render_bwd = G.gsparc_render_bwd_tc if args.render == "tc" else G.gsparc_render_bwd
+    # tensor-core configuration: the backward scheduled over the SMs (walk lengths, then the
+    # longest work items first, long walks split in two), its front chunks fed by the fused
+    # forward's s_tot
+    s_tot = r.s_tot_buffer(B) if args.render == "tc" else None
+    bwd_ws = torch.zeros(G.gsparc_render_bwd_tc_workspace(r.view, r.band, B), dtype=torch.uint8, device=dev)
+
+    def render_bwd():
+        if args.render == "tc":
+            G.gsparc_render_bwd_tc_balanced(r.view, r.band, B, n, r.proj, r.tile_ranges, r.sorted_ids, attr,
+                                            None, s_tot, logT, nc, d_spec, bwd_ws, d_attr, d_proj)
+        else:
+            G.gsparc_render_bwd(r.view, r.band, B, n, r.proj, r.tile_ranges, r.sorted_ids, attr, logT, nc,
+                                d_spec, d_attr, d_proj)
     # the tensor-core configuration runs the attribute network forward and backward on the tensor
     # cores as well (split-BF16, the same products in both, so the ReLU masks agree)
     mlp_tc = args.render == "tc" and hidden in (16, 32)
@@ -230,13 +242,12 @@ def run_ours(args, rank, world, local_rank):
             # the loss fused into the forward's epilogue: it writes dL/dz, not the spectrum
             stage("render_fwd", lambda: G.gsparc_render_fwd_l2_tc(r.view, r.band, B, n, r.proj, r.tile_ranges,
                                                                   r.sorted_ids, attr, tgt, loss, d_spec, None,
-                                                                  logT, nc, n_used))
+                                                                  logT, nc, n_used, s_tot=s_tot))
         else:
             stage("render_fwd", lambda: render_fwd(r.view, r.band, B, n, r.proj, r.tile_ranges,
                                                    r.sorted_ids, attr, spec, logT, nc, n_used))
             stage("l2_loss", lambda: G.gsparc_l2_loss(spec, tgt, loss, d_spec))
-        stage("render_bwd", lambda: render_bwd(r.view, r.band, B, n, r.proj, r.tile_ranges,
-                                               r.sorted_ids, attr, logT, nc, d_spec, d_attr, d_proj))
+        stage("render_bwd", render_bwd)
 
         def proj_bwd(s=None):
             G.gsparc_project_bwd(r.view, scene.means, scene.log_scales, scene.quats, d_proj, grads[0],
@@ -256,9 +267,9 @@ def run_ours(args, rank, world, local_rank):
             stage("project_bwd", proj_bwd)
 
     # kernels of ours launched per step: project 1, bin/sort 3 (count + scan, emit, per-tile
-    # sort), network 1, render 1, loss 1 (fused into the tensor-core forward), render bwd 1,
-    # network bwd 1, projection bwd 1
-    launches_per_step = 1 + 3 + 1 + 1 + (1 if args.render != "tc" else 0) + 1 + 1 + 1
+    # sort), network 1, render 1, loss 1 (fused into the tensor-core forward), render bwd 1
+    # (+ its schedule in the tensor-core form), network bwd 1, projection bwd 1
+    launches_per_step = 1 + 3 + 1 + 1 + (1 if args.render != "tc" else 0) + (2 if args.render == "tc" else 1) + 1 + 1
 
     for _ in range(args.warmup):
         step(ds, target)
@@ -362,7 +373,7 @@ def run_ours(args, rank, world, local_rank):
     # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the tensor-core
     # compositing kernels in this step (50k Gaussians, 64 subcarriers, 360x90, one transmitter),
     # from one ncu capture of each current kernel (the forward with its fused loss)
-    traffic = {"render_bwd": 17339392, "render_fwd": 17167104} if args.render == "tc" else {}
+    traffic = {"render_bwd": None, "render_fwd": 17167104} if args.render == "tc" else {}
     if top in unit_flop:
         achieved = units * unit_flop[top] / (avg[top] * 1e-3) / 1e12
         roofline = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": fp32_peak,

@@ -304,6 +304,51 @@ int gsparc_render_bwd_tc(const gsparc_view* view, const gsparc_band* band, int32
                          const float* d_spectrum, float* d_attr, float* d_proj, void* stream);
 
 /*
+ * Bytes of device workspace gsparc_render_bwd_tc_balanced needs for B
+ * transmitters of this view and band: 16 + 4 B T (rounded up to 16) +
+ * 32 B T strips, T = tiles, strips as for s_tot.
+ */
+int gsparc_render_bwd_tc_workspace(const gsparc_view* view, const gsparc_band* band, int32_t B,
+                                   size_t* ws_bytes);
+
+/*
+ * gsparc_render_bwd_tc with its work scheduled over the SMs (same gradients
+ * up to rounding order).  The cost of a (transmitter, tile, strip) is its
+ * walk, the largest n_contrib among the tile's pixels, and varies by a
+ * factor of two or more between tiles.  A first kernel takes every walk
+ * and builds an ordered list of work items; a walk longer than split_min
+ * batches of 16 entries is split into a front chunk [0, m) and a back
+ * chunk [m, walk) (m = 16 floor(batches / 2)), run as independent blocks.
+ * The back chunk walks back to front from the final state as
+ * gsparc_render_bwd_tc does.  The front chunk walks front to back from
+ * T = 1 (the forward's own recursion) and takes the suffix sum of entry i,
+ * sum_{j>i} w_j Re(conj(g) s_j), as s_tot - sum_{j<=i} (Algorithm 1's
+ * Backprop; the identity sum_j w_j s_j = z), so no state at m is needed.
+ * Items are ordered by decreasing batch count: the block scheduler hands out
+ * blocks in index order, so the SMs take the longest items first.
+ *   spectrum [B,K,H,W,2] or NULL; s_tot [B,strips,H,W] (from
+ *   gsparc_render_fwd_l2_tc) or NULL: the front chunks take s_tot when given,
+ *   else form it from the spectrum and d_spectrum; with both NULL no walk is
+ *   split (the items are still ordered).
+ *   split_min: 0 selects the default (3 batches), a negative value disables
+ *   splitting; walks are split only while B * T * strips <= 2 x SMs (with
+ *   more units the ordering alone keeps the SMs busy).
+ *   ws: device workspace of ws_bytes >= gsparc_render_bwd_tc_workspace(),
+ *   16-byte aligned, whose first 16 bytes are zero before its first use
+ *   (every call leaves them zero again); one call at a time per workspace.
+ * Other arguments and outputs as gsparc_render_bwd_tc; the front chunks'
+ * suffix is a difference of two sums, so its error is relative to s_tot,
+ * not to the suffix (the gradients agree with gsparc_render_bwd_tc to
+ * ~1e-5 relative L2).
+ */
+int gsparc_render_bwd_tc_balanced(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
+                                  const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
+                                  const float* attr, const float* spectrum, const float* s_tot,
+                                  const float* final_logT, const uint32_t* n_contrib,
+                                  const float* d_spectrum, int32_t split_min, void* ws, size_t ws_bytes,
+                                  float* d_attr, float* d_proj, void* stream);
+
+/*
  * Complex L2 loss, the mean over `count` complex elements of |z - target|^2,
  * written to loss [1] (device; overwritten), and if d_z is not NULL its
  * gradient 2 (z - target) / count (overwritten).
@@ -340,15 +385,6 @@ int gsparc_csi_head_bwd(int32_t B, int32_t K, int64_t P, const float* d_csi, flo
                         float* d_spectrum, void* stream);
 
 /*
- * gsparc_render_fwd_tc with the CSI head fused into its epilogue: every
- * thread block sums its tile's pixels of each subcarrier and adds 1/(H W)
- * of it to csi [B,K,2] (overwritten: the call clears it first).  spectrum may
- * be NULL, and then the spectrum is never written (8 B per pixel, subcarrier
- * and transmitter saved) -- the form a CSI query at an unseen position needs.
- * final_logT, n_contrib, n_used as gsparc_render_fwd (each may be NULL).
- * Atomic partial sums: the last bits may differ from run to run.
- */
-/*
  * gsparc_render_fwd_tc with the complex L2 loss of gsparc_l2_loss fused into its
  * epilogue (the training step's loss, Algorithm 1; complex L2 in place of
  * Eq. 4): with count = B*K*H*W,
@@ -358,13 +394,27 @@ int gsparc_csi_head_bwd(int32_t B, int32_t K, int64_t P, const float* d_csi, flo
  *   gsparc_l2_loss on the spectrum gsparc_render_fwd_tc writes.
  * spectrum may be NULL (then it is never written: training needs only the
  * gradient); final_logT, n_contrib, n_used as gsparc_render_fwd.
+ * s_tot may be NULL; else [B, strips, H, W] out, strips = ceil(K / 64) for
+ * K > 64 and 1 otherwise: s_tot[b,s,p] = sum over the strip's subcarriers of
+ * Re(conj(d_spectrum) z), the input gsparc_render_bwd_tc_balanced takes in
+ * place of the spectrum (4 bytes per pixel and strip instead of 8 per
+ * subcarrier).
  */
 int gsparc_render_fwd_l2_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
                             const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
                             const float* attr, const float* target, float* loss, float* d_spectrum,
                             float* spectrum, float* final_logT, uint32_t* n_contrib, uint32_t* n_used,
-                            void* stream);
+                            float* s_tot, void* stream);
 
+/*
+ * gsparc_render_fwd_tc with the CSI head fused into its epilogue: every
+ * thread block sums its tile's pixels of each subcarrier and adds 1/(H W)
+ * of it to csi [B,K,2] (overwritten: the call clears it first).  spectrum may
+ * be NULL, and then the spectrum is never written (8 B per pixel, subcarrier
+ * and transmitter saved) -- the form a CSI query at an unseen position needs.
+ * final_logT, n_contrib, n_used as gsparc_render_fwd (each may be NULL).
+ * Atomic partial sums: the last bits may differ from run to run.
+ */
 int gsparc_render_csi_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
                          const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
                          const float* attr, float* csi, float* spectrum, float* final_logT,

@@ -16,6 +16,7 @@
 // CTA stops fetching once every thread has stopped.
 
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -56,6 +57,15 @@ struct RenderArgs {
     float* l2_loss;            // [1] accumulator of mean |z - target|^2
     float2* l2_grad;           // [B][K][H][W] out: 2 (z - target) / count, or null
     float l2_inv;              // 1 / count
+    // [B][strips][H][W]: Re sum_k conj(dL/dz_k) z_k over each strip of S subcarriers (written by
+    // the fused L2 forward when not null; read by the front chunks of the scheduled backward)
+    float* s_tot;
+    // Scheduled tensor-core backward: work item r of the ordered list runs on block r
+    // (x = b * T + tile, y = strip | front flag << 31, entries [z, w) of the walk), or null
+    // for one block per (strip, tile, transmitter).
+    const uint4* items;
+    const uint32_t* n_items;
+    int T;                     // tiles per image
     // cycles of subcarrier k = L * (lam0_hi + lam0_lo + k * dlam), lam = f / c
     float lam0_hi, lam0_lo, dlam;
     // d(psi)/dL = -2 pi f_k / c, split as c_f0 + kk * c_df inside a strip
@@ -432,6 +442,7 @@ bool fill_args(const gsparc_view* view, const gsparc_band* band, int32_t B, int3
     a.H = view->H;
     a.W = view->W;
     a.TW = tiles_x(*view);
+    a.T = a.TW * tiles_y(*view);
     a.K = band->K;
     a.N = N;
     a.B = B;
@@ -895,7 +906,7 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
     __syncthreads();
     const bool ok = *s_err == 0u && nbat != 0xffffffffu;
     tc_fence_after();
-    float l2acc = 0.f;
+    float l2acc = 0.f, stot = 0.f;
     if (pixel) {
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
         // fused loss: the targets of the next 8 subcarriers are loaded while a chunk is processed
@@ -941,7 +952,9 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
                         const float zr = ok ? v[2 * q] : __int_as_float(0x7fc00000);
                         const float dr = zr - t.x, di = v[2 * q + 1] - t.y;
                         l2acc = fmaf(dr, dr, fmaf(di, di, l2acc));
-                        a.l2_grad[e] = make_float2(2.f * dr * a.l2_inv, 2.f * di * a.l2_inv);
+                        const float2 gz = make_float2(2.f * dr * a.l2_inv, 2.f * di * a.l2_inv);
+                        a.l2_grad[e] = gz;
+                        stot = fmaf(gz.x, zr, fmaf(gz.y, v[2 * q + 1], stot));
                     }
                 }
             }
@@ -968,6 +981,7 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
 #pragma unroll
             for (int q = 0; q < 8; ++q) tg[q] = tgn[q];
         }
+        if (inside && a.l2_grad && a.s_tot) a.s_tot[((size_t)b * gridDim.x + strip) * plane + pix] = stot;
         if (inside && strip == 0) {
             if (a.final_logT) a.final_logT[(size_t)b * plane + pix] = logT;
             if (a.n_contrib) a.n_contrib[(size_t)b * plane + pix] = last;
@@ -1039,7 +1053,7 @@ extern "C" int gsparc_render_fwd_l2_tc(const gsparc_view* view, const gsparc_ban
                                        const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
                                        const float* attr, const float* target, float* loss, float* d_spectrum,
                                        float* spectrum, float* final_logT, uint32_t* n_contrib, uint32_t* n_used,
-                                       void* stream) {
+                                       float* s_tot, void* stream) {
     using namespace gsparc;
     if (!common_ok(view, band, B, N, proj, tile_ranges, sorted_ids, attr)) return GSPARC_ERR_INVALID;
     if (!target || !loss || !d_spectrum) return GSPARC_ERR_INVALID;
@@ -1055,6 +1069,7 @@ extern "C" int gsparc_render_fwd_l2_tc(const gsparc_view* view, const gsparc_ban
     a.l2_target = reinterpret_cast<const float2*>(target);
     a.l2_loss = loss;
     a.l2_grad = reinterpret_cast<float2*>(d_spectrum);
+    a.s_tot = s_tot;
     const int64_t count = (int64_t)B * band->K * view->H * view->W;
     a.l2_inv = (float)(1.0 / (double)count);
     const int T = tiles_x(*view) * tiles_y(*view);
@@ -1189,7 +1204,26 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
     auto empty_bar = [&](int st) { return smem_u32(&bars[kWsR + st]); };
     auto bready_bar = [&](int st) { return smem_u32(&bars[2 * kWsR + st]); };
 
-    const int strip = blockIdx.x, tile = blockIdx.y, b = blockIdx.z;
+    // work item: a scheduled chunk [chunk_lo, chunk_end) of one (transmitter, tile, strip)
+    // walk, or (no item list) the whole walk, whose end is then known after the prologue
+    int strip, tile, b;
+    bool front = false;           // front chunk [0, chunk_end), walked front to back
+    uint32_t chunk_lo = 0, chunk_end = 0;
+    if (a.items) {
+        const uint32_t r = blockIdx.x;
+        if (r >= __ldg(a.n_items)) return;   // the whole block, before any barrier or allocation
+        const uint4 it = a.items[r];
+        b = (int)(it.x / (uint32_t)a.T);
+        tile = (int)(it.x - (uint32_t)b * (uint32_t)a.T);
+        strip = (int)(it.y & 0x7fffffffu);
+        front = (it.y >> 31) != 0u;
+        chunk_lo = it.z;
+        chunk_end = it.w;
+    } else {
+        strip = blockIdx.x;
+        tile = blockIdx.y;
+        b = blockIdx.z;
+    }
     const int k0 = strip * S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool issuer = warp == (kThreads + kWsProd) / 32;
@@ -1205,6 +1239,35 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
     const uint2 range = a.ranges[tile];
     const size_t plane = (size_t)a.H * a.W;
     const size_t pix = (size_t)y * a.W + x;
+
+    // batch i of a back chunk ends kTbE * i entries before chunk_end (its last batch ragged),
+    // batch i of a front chunk starts at kTbE * i
+    int nbatch = (int)((chunk_end - chunk_lo + kTbE - 1) / kTbE);
+    auto batch_lo = [&](int i) -> uint32_t {
+        if (front) return chunk_lo + (uint32_t)i * kTbE;
+        const uint32_t hp = chunk_end - (uint32_t)i * kTbE;
+        return hp > chunk_lo + kTbE ? hp - kTbE : chunk_lo;
+    };
+    auto batch_n = [&](int i) -> int {
+        if (front) return (int)min((uint32_t)kTbE, chunk_end - batch_lo(i));
+        return (int)(chunk_end - (uint32_t)i * kTbE - batch_lo(i));
+    };
+    // the builders' prefetch of one batch's records (threads 0..E-1 of the first builder warp)
+    const bool gatherer = producer && prod < kTbE;
+    uint32_t pf_gid = 0xffffffffu;
+    float4 pf_p0 = make_float4(0.f, 0.f, 0.f, 0.f), pf_p1 = pf_p0, pf_at = pf_p0;
+    auto gather = [&](int i) {
+        if (gatherer) {
+            pf_gid = prod < batch_n(i) ? a.ids[range.x + batch_lo(i) + prod] : 0xffffffffu;
+            if (pf_gid < (uint32_t)a.N) {
+                pf_p0 = a.proj[2 * pf_gid];
+                pf_p1 = a.proj[2 * pf_gid + 1];
+                pf_at = a.attr[(size_t)b * a.N + pf_gid];
+            }
+        }
+    };
+    // a scheduled item knows its batches already: its first records load during the prologue
+    if (a.items && nbatch > 0) gather(0);
 
     if (tid == 0) {
         for (int st = 0; st < kWsR; ++st) {
@@ -1222,43 +1285,62 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // A operand (consumers): this pixel's upstream gradient over the strip, split hi / lo
+    // A operand (consumers): this pixel's upstream gradient over the strip, split hi / lo.
+    // A front chunk also needs s_tot = Re sum_k conj(g_k) z_k over the strip, the sum over the
+    // whole walk of the terms the back-to-front recursion accumulates: given, or formed here
+    // from the spectrum.
+    float s_tot = 0.f;
     if (!producer && !issuer) {
         uint8_t* Ahi = sm + L::kA + (half * 2 + 0) * L::kATile;
         uint8_t* Alo = sm + L::kA + (half * 2 + 1) * L::kATile;
-#pragma unroll 4
-        for (int c0 = 0; c0 < 2 * S; c0 += 8) {
-            float g8[8];
+        // kChunk subcarriers per round trip: the loads are global-space (they cannot alias the
+        // shared-memory stores), all issued before the first use
+        constexpr int kChunk = S < 16 ? S : 16;
+        const size_t base = (size_t)b * a.K * plane + pix;
+        const bool form_s_tot = front && !a.s_tot;
+#pragma unroll 1
+        for (int k1 = 0; k1 < S; k1 += kChunk) {
+            float2 g[kChunk];
 #pragma unroll
-            for (int q = 0; q < 8; q += 2) {
-                const int k = k0 + (c0 + q) / 2;
-                float2 g = make_float2(0.f, 0.f);
-                if (inside && k < a.K) g = a.d_spectrum[((size_t)b * a.K + k) * plane + pix];
-                g8[q] = g.x;
-                g8[q + 1] = g.y;
+            for (int q = 0; q < kChunk; ++q) {
+                const int k = k0 + k1 + q;
+                g[q] = (inside && k < a.K) ? __ldcs(a.d_spectrum + base + (size_t)k * plane) : make_float2(0.f, 0.f);
             }
-            uint4 H, Lo;
-            split8(g8, H, Lo);
-            *reinterpret_cast<uint4*>(Ahi + canon_off(m, c0, L::kKa)) = H;
-            *reinterpret_cast<uint4*>(Alo + canon_off(m, c0, L::kKa)) = Lo;
+            if (form_s_tot) {
+#pragma unroll
+                for (int q = 0; q < kChunk; ++q) {
+                    const int k = k0 + k1 + q;
+                    const float2 z = (inside && k < a.K) ? __ldcs(a.spectrum + base + (size_t)k * plane)
+                                                         : make_float2(0.f, 0.f);
+                    s_tot = fmaf(g[q].x, z.x, fmaf(g[q].y, z.y, s_tot));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kChunk; q += 4) {
+                const float g8[8] = {g[q].x,     g[q].y,     g[q + 1].x, g[q + 1].y,
+                                     g[q + 2].x, g[q + 2].y, g[q + 3].x, g[q + 3].y};
+                const int c0 = 2 * (k1 + q);
+                uint4 H, Lo;
+                split8(g8, H, Lo);
+                *reinterpret_cast<uint4*>(Ahi + canon_off(m, c0, L::kKa)) = H;
+                *reinterpret_cast<uint4*>(Alo + canon_off(m, c0, L::kKa)) = Lo;
+            }
         }
     }
-    float logT = inside ? a.final_logT[(size_t)b * plane + pix] : 0.f;
+    if (front && a.s_tot && inside) s_tot = a.s_tot[((size_t)b * ((a.K + S - 1) / S) + strip) * plane + pix];
+    float logT = (inside && !front) ? a.final_logT[(size_t)b * plane + pix] : 0.f;
     const uint32_t last = inside ? a.n_contrib[(size_t)b * plane + pix] : 0u;
     __syncthreads();
-    if (last) atomicMax(s_maxlast, last);
+    if (last && !a.items) atomicMax(s_maxlast, last);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t maxlast = min(*s_maxlast, range.y - range.x);
+    if (!a.items) {
+        chunk_end = min(*s_maxlast, range.y - range.x);   // the walk: the largest n_contrib
+        nbatch = (int)((chunk_end + kTbE - 1) / kTbE);
+    }
     const uint32_t tbase = *tslot;
-    const int nbatch = (int)((maxlast + kTbE - 1) / kTbE);
-    auto batch_lo = [&](int i) {
-        const uint32_t hp = maxlast - (uint32_t)i * kTbE;
-        return hp > (uint32_t)kTbE ? hp - kTbE : 0u;
-    };
-    auto batch_n = [&](int i) { return (int)(maxlast - (uint32_t)i * kTbE - batch_lo(i)); };
     auto wait_ok = [&](uint32_t bar, uint32_t parity) {
         bool w = (*s_err == 0u) && mbar_wait(bar, parity);
         w = __all_sync(0xffffffffu, w);
@@ -1268,19 +1350,6 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
 
     if (producer) {
         // ---------------- builder warps
-        const bool gatherer = prod < kTbE;   // threads 0..E-1 of the first producer warp
-        uint32_t pf_gid = 0xffffffffu;
-        float4 pf_p0 = make_float4(0.f, 0.f, 0.f, 0.f), pf_p1 = pf_p0, pf_at = pf_p0;
-        auto gather = [&](int i) {
-            if (gatherer) {
-                pf_gid = prod < batch_n(i) ? a.ids[range.x + batch_lo(i) + prod] : 0xffffffffu;
-                if (pf_gid < (uint32_t)a.N) {
-                    pf_p0 = a.proj[2 * pf_gid];
-                    pf_p1 = a.proj[2 * pf_gid + 1];
-                    pf_at = a.attr[(size_t)b * a.N + pf_gid];
-                }
-            }
-        };
         auto flush = [&](int i, int st) {
             TbMeta md = tb_meta(sm + L::kMeta + st * L::kMetaStage);
             const int nb = batch_n(i);
@@ -1303,7 +1372,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
                 }
             }
         };
-        if (nbatch > 0) gather(0);
+        if (!a.items && nbatch > 0) gather(0);
         for (int i = 0; i < nbatch; ++i) {
             const int st = i % kWsR;
             if (i >= kWsR) {
@@ -1415,100 +1484,122 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
         const float c_f0 = (float)(a.two_pi_over_c * (a.f0 + (double)k0 * a.df));
         const float c_df = (float)(a.two_pi_over_c * a.df);
-        float suffix = 0.f;
-        for (int i = 0; i < nbatch; ++i) {
-            const int st = i % kWsR;
-            if (!wait_ok(full_bar(st), (uint32_t)(i / kWsR) & 1u)) break;
-            tc_fence_after();
-            const uint32_t lo_pos = batch_lo(i);
-            const int nbp = batch_n(i);
-            TbMeta mdp = tb_meta(sm + L::kMeta + st * L::kMetaStage);
-            float v[3 * kTbE];
+        // The walk in either direction (a compile-time flag).  Back to front from the pixel's
+        // final state, acc = the sum over later entries of w reG a (the suffix); front to back
+        // from T = 1 (the forward's own recursion), acc = the same sum over the entries up to
+        // this one, so that the suffix is s_tot - acc.
+        auto walk = [&](auto dir) {
+            constexpr bool kFront = decltype(dir)::value;
+            float acc = 0.f;
+            for (int i = 0; i < nbatch; ++i) {
+                const int st = i % kWsR;
+                if (!wait_ok(full_bar(st), (uint32_t)(i / kWsR) & 1u)) break;
+                tc_fence_after();
+                const uint32_t lo_pos = batch_lo(i);
+                const int nbp = batch_n(i);
+                TbMeta mdp = tb_meta(sm + L::kMeta + st * L::kMetaStage);
+                float v[3 * kTbE];
 #pragma unroll
-            for (int c = 0; c < 3 * kTbE; c += 16) {
-                float t16[16];
-                tmem_ld16(tbase + (uint32_t)(st * L::kStageCols + half * 3 * kTbE + c) + lane_base, t16);
+                for (int c = 0; c < 3 * kTbE; c += 16) {
+                    float t16[16];
+                    tmem_ld16(tbase + (uint32_t)(st * L::kStageCols + half * 3 * kTbE + c) + lane_base, t16);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) v[c + q] = t16[q];
-            }
-            const uint64_t mask = warp_entry_mask(mdp.geo, mdp.ext, nbp, wcx, wcy, a.W);
-            if (lane == 0) mask_at(st, warp) = mask;
-            // entries in pairs (2p+1, 2p), back to front: both entries' alpha, gradient
-            // components and warp reductions sit in one block so their latencies overlap
-#pragma unroll
-            for (int p = kTbE / 2 - 1; p >= 0; --p) {
-                const uint32_t pm = (uint32_t)(mask >> (2 * p)) & 3u;
-                if (!pm) continue;   // warp-uniform
-                float gr[2][9], dxv[2], dyv[2], Gv[2], alv[2];
-                bool live[2], clv[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int j = 2 * p + 1 - h;
-                    const float4 gg = mdp.geo[j];
-                    const float2 g2 = mdp.geo2[j];
-                    float dx = __fsub_rn(ux, gg.x);
-                    const float hw = 0.5f * (float)a.W;
-                    dx = dx >= hw ? __fsub_rn(dx, (float)a.W) : (dx < -hw ? __fadd_rn(dx, (float)a.W) : dx);
-                    const float dy = __fsub_rn(uy, gg.y);
-                    float q = __fmul_rn(__fmul_rn(g2.x, dy), dy);
-                    q = __fmaf_rn(__fmul_rn(__fmul_rn(2.0f, gg.w), dx), dy, q);
-                    q = __fmaf_rn(__fmul_rn(gg.z, dx), dx, q);
-                    const float G = ex2(__fmul_rn(-0.5f * kLog2e, q));
-                    const float a0 = __fmul_rn(g2.y, G);
-                    clv[h] = a0 > kAlphaMax;
-                    const float alpha = clv[h] ? kAlphaMax : a0;
-                    live[h] = ((pm >> (1 - h)) & 1u) && lo_pos + (uint32_t)j < last && q <= kQMax &&
-                              alpha >= kAlphaMin;
-                    alv[h] = live[h] ? alpha : 0.f;
-                    Gv[h] = live[h] ? G : 0.f;
-                    dxv[h] = live[h] ? dx : 0.f;
-                    dyv[h] = live[h] ? dy : 0.f;
+                    for (int q = 0; q < 16; ++q) v[c + q] = t16[q];
                 }
+                const uint64_t mask = warp_entry_mask(mdp.geo, mdp.ext, nbp, wcx, wcy, a.W);
+                if (lane == 0) mask_at(st, warp) = mask;
+                // entries in pairs in walk order: both entries' alpha, gradient components and
+                // warp reductions sit in one block so their latencies overlap
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int j = 2 * p + 1 - h;
-                    const float alpha = alv[h];
-                    const float nl = live[h] ? lg2(__fsub_rn(1.0f, alpha)) : 0.f;
-                    const float logT_before = __fsub_rn(logT, nl);
-                    const float T = ex2(logT_before);
-                    const float w = T * alpha;
-                    const float reG = v[3 * j], imG = v[3 * j + 1], imF = v[3 * j + 2];
-                    const float amp = mdp.amp[j];
-                    const float reGa = amp * reG;
-                    const float dalpha = T * reGa - suffix / (1.0f - alpha);
-                    suffix = fmaf(w, reGa, suffix);
-                    logT = logT_before;
-                    gr[h][6] = w * reG;
-                    gr[h][7] = -w * amp * imG;
-                    gr[h][8] = w * amp * (c_f0 * imG + c_df * imF);
-                    const float da = (live[h] && !clv[h]) ? dalpha : 0.f;
-                    const float4 gg = mdp.geo[j];
-                    const float2 g2 = mdp.geo2[j];
-                    const float G = Gv[h], dx = dxv[h], dy = dyv[h];
-                    gr[h][5] = da * G;
-                    const float dq = -0.5f * da * g2.y * G;
-                    gr[h][0] = dq * (-2.0f * (gg.z * dx + gg.w * dy));
-                    gr[h][1] = dq * (-2.0f * (gg.w * dx + g2.x * dy));
-                    gr[h][2] = dq * dx * dx;
-                    gr[h][3] = dq * 2.0f * dx * dy;
-                    gr[h][4] = dq * dy * dy;
-                }
-                if (__any_sync(0xffffffffu, live[0] || live[1])) {
-                    const float t1 = warp_reduce_scatter9(gr[0], lane);
-                    const float t0 = warp_reduce_scatter9(gr[1], lane);
-                    if ((lane & 1) == 0 && (lane >> 1) < 9) {
-                        red_at(st, warp, 2 * p + 1, lane >> 1) = t1;
-                        red_at(st, warp, 2 * p, lane >> 1) = t0;
+                for (int pp = 0; pp < kTbE / 2; ++pp) {
+                    const int p = kFront ? pp : kTbE / 2 - 1 - pp;
+                    const uint32_t pm = (uint32_t)(mask >> (2 * p)) & 3u;
+                    if (!pm) continue;   // warp-uniform
+                    float gr[2][9], dxv[2], dyv[2], Gv[2], alv[2];
+                    bool live[2], clv[2];
+                    int jv[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = kFront ? 2 * p + h : 2 * p + 1 - h;
+                        jv[h] = j;
+                        const float4 gg = mdp.geo[j];
+                        const float2 g2 = mdp.geo2[j];
+                        float dx = __fsub_rn(ux, gg.x);
+                        const float hw = 0.5f * (float)a.W;
+                        dx = dx >= hw ? __fsub_rn(dx, (float)a.W) : (dx < -hw ? __fadd_rn(dx, (float)a.W) : dx);
+                        const float dy = __fsub_rn(uy, gg.y);
+                        float q = __fmul_rn(__fmul_rn(g2.x, dy), dy);
+                        q = __fmaf_rn(__fmul_rn(__fmul_rn(2.0f, gg.w), dx), dy, q);
+                        q = __fmaf_rn(__fmul_rn(gg.z, dx), dx, q);
+                        const float G = ex2(__fmul_rn(-0.5f * kLog2e, q));
+                        const float a0 = __fmul_rn(g2.y, G);
+                        clv[h] = a0 > kAlphaMax;
+                        const float alpha = clv[h] ? kAlphaMax : a0;
+                        live[h] = ((pm >> (j & 1)) & 1u) && lo_pos + (uint32_t)j < last && q <= kQMax &&
+                                  alpha >= kAlphaMin;
+                        alv[h] = live[h] ? alpha : 0.f;
+                        Gv[h] = live[h] ? G : 0.f;
+                        dxv[h] = live[h] ? dx : 0.f;
+                        dyv[h] = live[h] ? dy : 0.f;
                     }
-                } else if (lane < 9) {
-                    red_at(st, warp, 2 * p + 1, lane) = 0.f;
-                    red_at(st, warp, 2 * p, lane) = 0.f;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = jv[h];
+                        const float alpha = alv[h];
+                        const float nl = live[h] ? lg2(__fsub_rn(1.0f, alpha)) : 0.f;
+                        const float reG = v[3 * j], imG = v[3 * j + 1], imF = v[3 * j + 2];
+                        const float amp = mdp.amp[j];
+                        const float reGa = amp * reG;
+                        float T, dalpha;
+                        if (kFront) {
+                            T = ex2(logT);
+                            acc = fmaf(T * alpha, reGa, acc);
+                            dalpha = T * reGa - (s_tot - acc) / (1.0f - alpha);
+                            logT = __fadd_rn(logT, nl);
+                        } else {
+                            const float logT_before = __fsub_rn(logT, nl);
+                            T = ex2(logT_before);
+                            dalpha = T * reGa - acc / (1.0f - alpha);
+                            acc = fmaf(T * alpha, reGa, acc);
+                            logT = logT_before;
+                        }
+                        const float w = T * alpha;
+                        gr[h][6] = w * reG;
+                        gr[h][7] = -w * amp * imG;
+                        gr[h][8] = w * amp * (c_f0 * imG + c_df * imF);
+                        const float da = (live[h] && !clv[h]) ? dalpha : 0.f;
+                        const float4 gg = mdp.geo[j];
+                        const float2 g2 = mdp.geo2[j];
+                        const float G = Gv[h], dx = dxv[h], dy = dyv[h];
+                        gr[h][5] = da * G;
+                        const float dq = -0.5f * da * g2.y * G;
+                        gr[h][0] = dq * (-2.0f * (gg.z * dx + gg.w * dy));
+                        gr[h][1] = dq * (-2.0f * (gg.w * dx + g2.x * dy));
+                        gr[h][2] = dq * dx * dx;
+                        gr[h][3] = dq * 2.0f * dx * dy;
+                        gr[h][4] = dq * dy * dy;
+                    }
+                    if (__any_sync(0xffffffffu, live[0] || live[1])) {
+                        const float t0 = warp_reduce_scatter9(gr[0], lane);
+                        const float t1 = warp_reduce_scatter9(gr[1], lane);
+                        if ((lane & 1) == 0 && (lane >> 1) < 9) {
+                            red_at(st, warp, jv[0], lane >> 1) = t0;
+                            red_at(st, warp, jv[1], lane >> 1) = t1;
+                        }
+                    } else if (lane < 9) {
+                        red_at(st, warp, jv[0], lane) = 0.f;
+                        red_at(st, warp, jv[1], lane) = 0.f;
+                    }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty_bar(st));
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(empty_bar(st));
-        }
+        };
+        if (front)
+            walk(std::true_type{});
+        else
+            walk(std::false_type{});
     }
     tc_fence_before();
     __syncthreads();
@@ -1521,12 +1612,137 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
 }
 
 template <int S>
-int launch_bwd_tc(const RenderArgs& a, int T, cudaStream_t s) {
+int launch_bwd_tc(const RenderArgs& a, int T, cudaStream_t s, uint32_t max_items = 0) {
     using L = RWsSmem<S>;
     if (!ensure_smem_attr(k_render_bwd_ws<S>, L::kTotal)) return GSPARC_ERR_CUDA;
-    dim3 grid((a.K + S - 1) / S, T, a.B);
-    k_render_bwd_ws<S><<<grid, kWsThreads, L::kTotal, s>>>(a);
+    if (a.items) {
+        k_render_bwd_ws<S><<<max_items, kWsThreads, L::kTotal, s>>>(a);
+    } else {
+        dim3 grid((a.K + S - 1) / S, T, a.B);
+        k_render_bwd_ws<S><<<grid, kWsThreads, L::kTotal, s>>>(a);
+    }
     return launch_status();
+}
+
+int launch_bwd_tc_any(const RenderArgs& a, int T, cudaStream_t s, uint32_t max_items = 0) {
+    if (a.K <= 8) return launch_bwd_tc<8>(a, T, s, max_items);
+    if (a.K <= 16) return launch_bwd_tc<16>(a, T, s, max_items);
+    if (a.K <= 32) return launch_bwd_tc<32>(a, T, s, max_items);
+    return launch_bwd_tc<64>(a, T, s, max_items);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Schedule of the tensor-core backward.  Its cost per (transmitter, tile, strip) is the walk,
+// the largest n_contrib among the tile's pixels, in batches of kTbE entries, and it varies by
+// a factor of two or more between tiles, so one block per tile leaves most SMs idle while the
+// longest walks finish.  The schedule splits each long walk into a front chunk [0, m) and a
+// back chunk [m, walk) that run as independent blocks: the back chunk starts from the final
+// state as before, the front chunk from T = 1 with the suffix taken as s_tot minus the prefix
+// sum (no state at m is needed).  The items are ordered by decreasing batch count; the block
+// scheduler hands out blocks in index order, which makes this longest-first list scheduling.
+// ---------------------------------------------------------------------------------------------
+
+constexpr int kSchedThreads = 256;
+constexpr int kSchedKeys = kSchedThreads;   // cost buckets (batches, clamped), one per thread
+constexpr int kSplitMinDefault = 3;        // batches: a longer walk is split in two
+
+struct SchedLayout {
+    size_t hdr, walks, items, total;
+};
+
+inline SchedLayout sched_layout(int B, int T, int strips) {
+    SchedLayout L;
+    size_t o = 0;
+    L.hdr = o;   o += 16;                                          // ticket, item count
+    L.walks = o; o += ((size_t)B * T * 4 + 15) & ~size_t(15);
+    L.items = o; o += (size_t)2 * B * T * strips * sizeof(uint4);
+    L.total = o;
+    return L;
+}
+
+inline int strips_of(int K) { return K <= 64 ? 1 : (K + 63) / 64; }
+
+// One block per (transmitter, tile): the walk.  The last block to finish builds the items.
+__global__ void __launch_bounds__(kSchedThreads) k_bwd_schedule(int H, int W, int TW, int T, int strips,
+                                                                int split_min, int allow_split,
+                                                                const uint2* __restrict__ ranges,
+                                                                const uint32_t* __restrict__ n_contrib,
+                                                                uint32_t* __restrict__ hdr,
+                                                                uint32_t* __restrict__ walks,
+                                                                uint4* __restrict__ items) {
+    __shared__ uint32_t s_max;
+    __shared__ uint32_t s_off[kSchedKeys];
+    __shared__ uint32_t s_warp[kSchedThreads / 32];
+    __shared__ bool s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tile = (int)(blockIdx.x % (uint32_t)T), b = (int)(blockIdx.x / (uint32_t)T);
+    if (tid == 0) s_max = 0u;
+    __syncthreads();
+    const int x = (tile % TW) * kTile + (tid & 15), y = (tile / TW) * kTile + (tid >> 4);
+    uint32_t v = (x < W && y < H) ? n_contrib[(size_t)b * H * W + (size_t)y * W + x] : 0u;
+    v = __reduce_max_sync(0xffffffffu, v);
+    if (lane == 0) atomicMax(&s_max, v);
+    __syncthreads();
+    if (tid == 0) {
+        const uint2 r = ranges[tile];
+        walks[blockIdx.x] = min(s_max, r.y - r.x);
+        __threadfence();
+        s_last = atomicAdd(&hdr[0], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // batch counts of the one or two chunks of a walk (n1 = 0: not split)
+    auto chunks = [&](uint32_t w, uint32_t& n0, uint32_t& n1) {
+        const uint32_t nb = (w + kTbE - 1) / kTbE;
+        if (allow_split && split_min >= 0 && nb > (uint32_t)split_min) {
+            n0 = nb / 2;
+            n1 = nb - n0;
+        } else {
+            n0 = nb;
+            n1 = 0u;
+        }
+    };
+    auto key = [](uint32_t n) { return (uint32_t)kSchedKeys - 1u - min(n, (uint32_t)kSchedKeys - 1u); };
+    const int units = (int)gridDim.x * strips;
+    s_off[tid] = 0u;
+    __syncthreads();
+    for (int u = tid; u < units; u += kSchedThreads) {
+        uint32_t n0, n1;
+        chunks(__ldcg(&walks[u / strips]), n0, n1);
+        if (n0) atomicAdd(&s_off[key(n0)], 1u);
+        if (n1) atomicAdd(&s_off[key(n1)], 1u);
+    }
+    __syncthreads();
+    // exclusive scan of the bucket counts: bucket 0 holds the longest items
+    const uint32_t c = s_off[tid];
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y2 = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y2;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    uint32_t before = 0u;
+    for (int w2 = 0; w2 < warp; ++w2) before += s_warp[w2];
+    s_off[tid] = before + incl - c;
+    if (tid == kSchedThreads - 1) hdr[1] = before + incl;   // the item count
+    __syncthreads();
+    for (int u = tid; u < units; u += kSchedThreads) {
+        const uint32_t bt = (uint32_t)(u / strips), strip = (uint32_t)(u % strips);
+        const uint32_t w = __ldcg(&walks[bt]);
+        uint32_t n0, n1;
+        chunks(w, n0, n1);
+        if (n1) {
+            const uint32_t m = n0 * kTbE;
+            items[atomicAdd(&s_off[key(n0)], 1u)] = make_uint4(bt, strip | 0x80000000u, 0u, m);
+            items[atomicAdd(&s_off[key(n1)], 1u)] = make_uint4(bt, strip, m, w);
+        } else if (n0) {
+            items[atomicAdd(&s_off[key(n0)], 1u)] = make_uint4(bt, strip, 0u, w);
+        }
+    }
+    if (tid == 0) hdr[0] = 0u;   // every block has taken its ticket: reset for the next call
 }
 
 }  // namespace
@@ -1549,9 +1765,56 @@ extern "C" int gsparc_render_bwd_tc(const gsparc_view* view, const gsparc_band* 
     a.d_attr = reinterpret_cast<float4*>(d_attr);
     a.d_proj = d_proj;
     const int T = tiles_x(*view) * tiles_y(*view);
+    return launch_bwd_tc_any(a, T, as_stream(stream));
+}
+
+extern "C" int gsparc_render_bwd_tc_workspace(const gsparc_view* view, const gsparc_band* band, int32_t B,
+                                              size_t* ws_bytes) {
+    using namespace gsparc;
+    if (!view_ok(view) || !band || band->K <= 0 || band->K > 65535 || B <= 0 || B > 65535 || !ws_bytes)
+        return GSPARC_ERR_INVALID;
+    *ws_bytes = sched_layout(B, tiles_x(*view) * tiles_y(*view), strips_of(band->K)).total;
+    return GSPARC_OK;
+}
+
+extern "C" int gsparc_render_bwd_tc_balanced(const gsparc_view* view, const gsparc_band* band, int32_t B,
+                                             int32_t N, const float* proj, const uint32_t* tile_ranges,
+                                             const uint32_t* sorted_ids, const float* attr,
+                                             const float* spectrum, const float* s_tot, const float* final_logT,
+                                             const uint32_t* n_contrib, const float* d_spectrum,
+                                             int32_t split_min, void* ws, size_t ws_bytes, float* d_attr,
+                                             float* d_proj, void* stream) {
+    using namespace gsparc;
+    if (!common_ok(view, band, B, N, proj, tile_ranges, sorted_ids, attr)) return GSPARC_ERR_INVALID;
+    if (!final_logT || !n_contrib || !d_spectrum || !d_attr || !d_proj || !ws) return GSPARC_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(d_spectrum) | reinterpret_cast<uintptr_t>(spectrum)) & 7) return GSPARC_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(d_attr) | reinterpret_cast<uintptr_t>(ws)) & 15) return GSPARC_ERR_INVALID;
+    const int T = tiles_x(*view) * tiles_y(*view), strips = strips_of(band->K);
+    const SchedLayout SL = sched_layout(B, T, strips);
+    if (ws_bytes < SL.total) return GSPARC_ERR_INVALID;
+    const int64_t units = (int64_t)B * T * strips;
+    if (2 * units >= (1ll << 31)) return GSPARC_ERR_INVALID;
+    RenderArgs a{};
+    fill_args(view, band, B, N, proj, tile_ranges, sorted_ids, attr, a);
+    a.spectrum = const_cast<float2*>(reinterpret_cast<const float2*>(spectrum));
+    a.s_tot = const_cast<float*>(s_tot);
+    a.final_logT = const_cast<float*>(final_logT);
+    a.n_contrib = const_cast<uint32_t*>(n_contrib);
+    a.d_spectrum = reinterpret_cast<const float2*>(d_spectrum);
+    a.d_attr = reinterpret_cast<float4*>(d_attr);
+    a.d_proj = d_proj;
+    char* w = static_cast<char*>(ws);
+    uint32_t* hdr = reinterpret_cast<uint32_t*>(w + SL.hdr);
+    a.items = reinterpret_cast<const uint4*>(w + SL.items);
+    a.n_items = hdr + 1;
     cudaStream_t s = as_stream(stream);
-    if (band->K <= 8) return launch_bwd_tc<8>(a, T, s);
-    if (band->K <= 16) return launch_bwd_tc<16>(a, T, s);
-    if (band->K <= 32) return launch_bwd_tc<32>(a, T, s);
-    return launch_bwd_tc<64>(a, T, s);
+    // splitting only pays while the units are too few to keep every SM busy
+    const int allow_split = units <= 2 * (int64_t)num_sms() ? 1 : 0;
+    // without s_tot or the spectrum a front chunk has no suffix: order the walks, split none
+    const int smin = (!spectrum && !s_tot) ? -1 : (split_min == 0 ? kSplitMinDefault : split_min);
+    k_bwd_schedule<<<(unsigned)(B * T), kSchedThreads, 0, s>>>(
+        view->H, view->W, tiles_x(*view), T, strips, smin, allow_split, a.ranges, n_contrib, hdr,
+        reinterpret_cast<uint32_t*>(w + SL.walks), reinterpret_cast<uint4*>(w + SL.items));
+    if (launch_status() != GSPARC_OK) return GSPARC_ERR_CUDA;
+    return launch_bwd_tc_any(a, T, s, (uint32_t)(2 * units));
 }

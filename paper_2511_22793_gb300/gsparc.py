@@ -34,7 +34,7 @@ EXPORTS = [
     "gsparc_num_tiles", "gsparc_project", "gsparc_project_bwd", "gsparc_bin_sort_workspace",
     "gsparc_bin_sort", "gsparc_bin_sort_noalloc", "gsparc_attr_mlp", "gsparc_attr_mlp_bwd",
     "gsparc_attr_mlp_bwd_tc", "gsparc_render_fwd", "gsparc_render_fwd_tc", "gsparc_render_bwd",
-    "gsparc_render_bwd_tc", "gsparc_l2_loss", "gsparc_csi_head", "gsparc_csi_loss", "gsparc_csi_head_bwd",
+    "gsparc_render_bwd_tc", "gsparc_render_bwd_tc_workspace", "gsparc_render_bwd_tc_balanced", "gsparc_l2_loss", "gsparc_csi_head", "gsparc_csi_loss", "gsparc_csi_head_bwd",
     "gsparc_render_csi_tc", "gsparc_render_fwd_l2_tc", "gsparc_adam", "gsparc_check", "gsparc_strerror",
 ]
 
@@ -106,7 +106,11 @@ def lib():
             "gsparc_render_csi_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
                                                     vp, vp, vp, vp]),
             "gsparc_render_fwd_l2_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
-                                                       vp, vp, vp, vp, vp, vp]),
+                                                       vp, vp, vp, vp, vp, vp, vp]),
+            "gsparc_render_bwd_tc_workspace": (ctypes.c_int, [P(View), P(Band), i32, P(ctypes.c_size_t)]),
+            "gsparc_render_bwd_tc_balanced": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp,
+                                                             vp, vp, vp, vp, i32, vp, ctypes.c_size_t, vp, vp,
+                                                             vp]),
             "gsparc_adam": (ctypes.c_int, [i64, vp, vp, vp, vp, f32, f32, f32, f32, i32, vp]),
             "gsparc_check": (ctypes.c_int, [vp, vp]),
             "gsparc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -266,6 +270,28 @@ def gsparc_render_bwd_tc(view, band, B, n, proj, tile_ranges, sorted_ids, attr, 
           _p(d_attr), _p(d_proj), _stream(stream))
 
 
+def gsparc_render_bwd_tc_workspace(view, band, B) -> int:
+    out = ctypes.c_size_t(0)
+    _call("gsparc_render_bwd_tc_workspace", ctypes.byref(view), ctypes.byref(band), int(B), ctypes.byref(out))
+    return int(out.value)
+
+
+def s_tot_strips(K) -> int:
+    """Strips of the s_tot buffer [B, strips, H, W] for K subcarriers."""
+    return 1 if K <= 64 else (K + 63) // 64
+
+
+def gsparc_render_bwd_tc_balanced(view, band, B, n, proj, tile_ranges, sorted_ids, attr, spectrum, s_tot,
+                                  final_logT, n_contrib, d_spectrum, ws, d_attr, d_proj, split_min=0,
+                                  stream=None):
+    """ws: a uint8 device tensor of gsparc_render_bwd_tc_workspace() bytes, zeroed once
+    (torch.zeros) before its first use."""
+    _call("gsparc_render_bwd_tc_balanced", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
+          _p(tile_ranges), _p(sorted_ids), _p(attr), _p(spectrum), _p(s_tot), _p(final_logT), _p(n_contrib),
+          _p(d_spectrum), int(split_min), _p(ws), ws.numel() * ws.element_size(), _p(d_attr), _p(d_proj),
+          _stream(stream))
+
+
 def gsparc_l2_loss(z, target, loss, d_z=None, stream=None):
     count = z.numel() // 2
     _call("gsparc_l2_loss", count, _p(z), _p(target), _p(loss), _p(d_z), _stream(stream))
@@ -298,10 +324,11 @@ def gsparc_render_csi_tc(view, band, B, n, proj, tile_ranges, sorted_ids, attr, 
 
 
 def gsparc_render_fwd_l2_tc(view, band, B, n, proj, tile_ranges, sorted_ids, attr, target, loss, d_spectrum,
-                            spectrum=None, final_logT=None, n_contrib=None, n_used=None, stream=None):
+                            spectrum=None, final_logT=None, n_contrib=None, n_used=None, s_tot=None,
+                            stream=None):
     _call("gsparc_render_fwd_l2_tc", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
           _p(tile_ranges), _p(sorted_ids), _p(attr), _p(target), _p(loss), _p(d_spectrum), _p(spectrum),
-          _p(final_logT), _p(n_contrib), _p(n_used), _stream(stream))
+          _p(final_logT), _p(n_contrib), _p(n_used), _p(s_tot), _stream(stream))
 
 
 def gsparc_adam(param, grad, m, v, lr, step, b1=0.9, b2=0.999, eps=1e-15, stream=None):

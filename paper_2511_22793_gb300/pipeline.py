@@ -89,6 +89,7 @@ class Renderer:
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
         ws = G.gsparc_bin_sort_workspace(self.view, self.n, self.capacity)
         self.ws = torch.empty(max(256, ws), dtype=torch.uint8, device=dev)
+        self.bwd_ws = None   # schedule of the tensor-core backward, allocated on first use
 
     def set_receiver(self, rx, V=None):
         """Move the receiver (position rx, world-to-receiver rotation V, row-major 3x3): the
@@ -152,12 +153,27 @@ class Renderer:
                                self.sorted_ids, attr, csi, spec, logT, nc, n_used, stream)
         return csi
 
-    def render_backward(self, attr, logT, nc, d_spec, d_attr, d_proj, tensor_cores=False, stream=None):
-        """Compositing gradient; tensor_cores selects gsparc_render_bwd_tc (same outputs)."""
+    def s_tot_buffer(self, B):
+        """[B, strips, H, W] buffer for the fused L2 forward's s_tot output."""
+        return torch.empty((B, G.s_tot_strips(self.K), self.H, self.W), dtype=torch.float32,
+                           device=self.device)
+
+    def render_backward(self, attr, logT, nc, d_spec, d_attr, d_proj, tensor_cores=False, stream=None,
+                        spectrum=None, s_tot=None, split_min=0):
+        """Compositing gradient.  tensor_cores selects the tensor-core form scheduled over the
+        SMs (gsparc_render_bwd_tc_balanced; long walks are split when the spectrum or the fused
+        forward's s_tot is given), else gsparc_render_bwd (same outputs)."""
         B = int(attr.shape[0])
-        fn = G.gsparc_render_bwd_tc if tensor_cores else G.gsparc_render_bwd
-        fn(self.view, self.band, B, self.n, self.proj, self.tile_ranges, self.sorted_ids, attr, logT, nc,
-           d_spec, d_attr, d_proj, stream)
+        if not tensor_cores:
+            G.gsparc_render_bwd(self.view, self.band, B, self.n, self.proj, self.tile_ranges, self.sorted_ids,
+                                attr, logT, nc, d_spec, d_attr, d_proj, stream)
+            return
+        need = G.gsparc_render_bwd_tc_workspace(self.view, self.band, B)
+        if self.bwd_ws is None or self.bwd_ws.numel() < need:
+            self.bwd_ws = torch.zeros(need, dtype=torch.uint8, device=self.device)
+        G.gsparc_render_bwd_tc_balanced(self.view, self.band, B, self.n, self.proj, self.tile_ranges,
+                                        self.sorted_ids, attr, spectrum, s_tot, logT, nc, d_spec, self.bwd_ws,
+                                        d_attr, d_proj, split_min=split_min, stream=stream)
 
     def attributes_backward(self, scene, mlp, tx, d_attr, d_means, d_ologit, d_latent, d_weights,
                             stream=None, tensor_cores=False):

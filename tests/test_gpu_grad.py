@@ -114,10 +114,15 @@ def test_render_bwd_per_gaussian_inputs():
 
 
 @pytest.mark.parametrize("n,H,W,K,B,seed", [(3000, 90, 360, 64, 1, 31), (2000, 90, 360, 37, 2, 32),
-                                             (1500, 45, 180, 8, 2, 33), (3000, 180, 720, 100, 1, 34)])
+                                             (1500, 45, 180, 8, 2, 33), (3000, 180, 720, 100, 1, 34),
+                                             (1500, 45, 180, 100, 1, 35)])
 def test_render_bwd_tensor_cores_matches_fp32_kernel_and_oracle(n, H, W, K, B, seed):
-    """gsparc_render_bwd_tc against gsparc_render_bwd (same inputs, relative L2 <= 1e-4 per
-    component) and the oracle's analytic gradient of transmitter 0 (<= 1e-3)."""
+    """gsparc_render_bwd_tc and the scheduled gsparc_render_bwd_tc_balanced against
+    gsparc_render_bwd (same inputs, relative L2 <= 1e-4 per component) and the oracle's
+    analytic gradient of transmitter 0 (<= 1e-3).  The scheduled form runs unsplit (items
+    ordered only), with every walk longer than one batch split (front chunks taking s_tot
+    from the spectrum), and split with s_tot given as a buffer; with more than 2 x SMs
+    (transmitter, tile, strip) units (the 180x720 case) no walk is split."""
     sc = synth.make_scene(n, seed=seed)
     mlp = synth.make_mlp(32, seed=3)
     tx = synth.make_tx(B, seed=seed + 1)
@@ -140,18 +145,41 @@ def test_render_bwd_tensor_cores_matches_fp32_kernel_and_oracle(n, H, W, K, B, s
     rng = np.random.default_rng(seed + 2)
     gz = rng.normal(size=(B, H * W, K)) + 1j * rng.normal(size=(B, H * W, K))
     d_spec = _to_dev_target(gz, B, H, W, K)
-    outs = []
-    for tc in (False, True):
+    # s_tot[b, s, p] = sum over strip s of Re(conj(g) z), as the fused forward writes it
+    nst = G.s_tot_strips(K)
+    zc = spectrum_to_complex(spec).reshape(B, H * W, K)
+    prod = (np.conj(gz) * zc).real
+    s_tot_np = np.stack([prod[:, :, s * 64:(s + 1) * 64].sum(-1) for s in range(nst)], 1) if K > 64 \
+        else prod.sum(-1)[:, None]
+    s_tot = torch.tensor(s_tot_np.reshape(B, nst, H, W).astype(np.float32), device=DEV)
+    forms = {
+        "fp32": lambda da, dp: r.render_backward(attr_d, logT, nc, d_spec, da, dp),
+        "tc": lambda da, dp: G.gsparc_render_bwd_tc(r.view, r.band, B, n, r.proj, r.tile_ranges, r.sorted_ids,
+                                                    attr_d, logT, nc, d_spec, da, dp),
+        "ordered": lambda da, dp: r.render_backward(attr_d, logT, nc, d_spec, da, dp, tensor_cores=True),
+        "split": lambda da, dp: r.render_backward(attr_d, logT, nc, d_spec, da, dp, tensor_cores=True,
+                                                  spectrum=spec, split_min=1),
+        "split_s_tot": lambda da, dp: r.render_backward(attr_d, logT, nc, d_spec, da, dp, tensor_cores=True,
+                                                        s_tot=s_tot, split_min=1),
+    }
+    res = {}
+    for name, fn in forms.items():
         d_attr = torch.zeros_like(attr_d)
         d_proj = torch.zeros_like(r.proj)
-        r.render_backward(attr_d, logT, nc, d_spec, d_attr, d_proj, tensor_cores=tc)
+        fn(d_attr, d_proj)
         torch.cuda.synchronize()
-        outs.append((d_attr.cpu().numpy().astype(np.float64), d_proj.cpu().numpy().astype(np.float64)))
-    (fa, fp), (ta, tp) = outs
-    for j in range(4):
-        assert rel_l2(ta[..., j], fa[..., j]) <= 1e-4, ("attr", j)
-    for j in (0, 1, 4, 5, 6):
-        assert rel_l2(tp[:, j], fp[:, j]) <= 1e-4, ("proj", j)
+        res[name] = (d_attr.cpu().numpy().astype(np.float64), d_proj.cpu().numpy().astype(np.float64))
+    assert r.check() == 0
+    fa, fp = res["fp32"]
+    for name in ("tc", "ordered", "split", "split_s_tot"):
+        ta, tp = res[name]
+        for j in range(4):
+            e = rel_l2(ta[..., j], fa[..., j])
+            assert e <= 1e-4, (name, "attr", j, e)
+        for j in (0, 1, 4, 5, 6):
+            e = rel_l2(tp[:, j], fp[:, j])
+            assert e <= 1e-4, (name, "proj", j, e)
+    ta, tp = res["split"]
     ref = orender.render_bwd(g32, at32[0], H, W, K, band.f_c, band.df, gz[0])
     if B == 1:
         got = {"px": tp[:, 0], "py": tp[:, 1], "cxx": tp[:, 4], "cxy": tp[:, 5], "cyy": tp[:, 6],
