@@ -138,7 +138,7 @@ def run_ours(args, rank, world, local_rank):
 
     from paper_2511_22793_gb300 import gsparc as G
     from paper_2511_22793_gb300 import synth
-    from paper_2511_22793_gb300.pipeline import DeviceMLP, DeviceScene, Renderer
+    from paper_2511_22793_gb300.pipeline import DeviceMLP, DeviceScene, PackedInputs, Renderer
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
@@ -160,7 +160,18 @@ def run_ours(args, rank, world, local_rank):
     target = rt.render(rt.attributes(dst, dm, txd))[0].clone()
     del rt, dst
 
-    ds = DeviceScene.from_host(sc, dev)
+    # the step's inputs (scene, network, transmitters, target spectrum) share one device
+    # allocation: the end-to-end step moves them from pinned host memory in one copy
+    arrays = list(sc.arrays()) + list(mlp.arrays()) + [txd, target]
+    inp = PackedInputs([tuple(np.shape(a)) if not isinstance(a, torch.Tensor) else tuple(a.shape)
+                        for a in arrays], dev)
+    for i, a in enumerate(arrays):
+        inp.set_host(i, a)
+    inp.upload()
+    torch.cuda.synchronize(dev)
+    ds = DeviceScene(*inp.views[0:5])
+    dm = DeviceMLP(hidden, *inp.views[5:11])
+    txd, target = inp.views[11], inp.views[12]
     attr = torch.empty((B, n, 4), device=dev)
     spec, logT, nc = r.alloc_outputs(B)
     n_used = torch.zeros((B, H, W), dtype=torch.int32, device=dev)
@@ -215,20 +226,23 @@ def run_ours(args, rank, world, local_rank):
     side = torch.cuda.Stream(dev)
 
     def step(scene: DeviceScene, tgt, concurrent=False):
-        """One training step.  concurrent: the attribute network runs on a side stream beside
-        projection and bin/sort (it needs neither), and the projection backward beside the
-        network backward (both only add into the gradients); used for the graph, while the
-        eager per-kernel timing keeps one stream."""
-        gbuf.zero_()
+        """One training step.  concurrent: the gradient zeroing and the attribute network run on
+        a side stream beside projection and bin/sort (they need neither), and the projection
+        backward beside the network backward (both only add into the gradients); used for the
+        graph, while the eager per-kernel timing keeps one stream."""
         cur = torch.cuda.current_stream(dev)   # the capture stream while a graph is captured
         if concurrent:
             fork = torch.cuda.Event()
             fork.record(cur)
             side.wait_event(fork)
+            with torch.cuda.stream(side):
+                gbuf.zero_()   # the gradients are first written by the compositing backward
             G.gsparc_attr_mlp(txd, r.rx, scene.means, scene.opacity_logit, scene.latent, mlp_s, mlp_prec,
                               attr, side)
             joined = torch.cuda.Event()
             joined.record(side)
+        else:
+            gbuf.zero_()
         stage("project", lambda: G.gsparc_project(r.view, scene.means, scene.log_scales, scene.quats,
                                                   r.proj))
         stage("bin_sort", lambda: G.gsparc_bin_sort(r.view, n, r.proj, r.capacity, r.ws, r.sorted_ids,
@@ -332,22 +346,20 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end: host (pinned) inputs copied into the buffers the graph reads, the step, the loss
     # read back -- all inside the timed region
-    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in sc.arrays()]
-    host_w = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in mlp.arrays()]
-    host_tgt = target.cpu().pin_memory()
-    host_tx = txd.cpu().pin_memory()
+    # (the packed inputs' pinned mirror holds the scene, network, transmitters and target)
     host_loss = torch.empty(1).pin_memory()
-    dev_in = list(ds.tensors()) + list(dm.tensors()) + [target, txd]
-    host_in = host + host_w + [host_tgt, host_tx]
-    h2d = sum(t.numel() * t.element_size() for t in host_in)
+    h2d = inp.nbytes
     d2h = host_loss.numel() * host_loss.element_size()
+    # one copy of every input from the pinned mirror, then the step's graph (the copy runs at
+    # the host link's rate, ~165 GB/s measured; overlapping the target's copy with projection
+    # and binning was measured no faster: the forward needs the target and every byte)
+    e2e_copies = "one pinned host-to-device copy of all inputs (scene, network, transmitters, target)"
     e2e_ms = []
     for it in range(args.warmup + args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        for d, h in zip(dev_in, host_in):
-            d.copy_(h, non_blocking=True)
+        inp.upload()
         graph.replay()
         host_loss.copy_(loss, non_blocking=True)
         torch.cuda.current_stream(dev).synchronize()
@@ -407,11 +419,11 @@ def run_ours(args, rank, world, local_rank):
                        "min": sorted_ms[0]},
         "kernels_ms": avg,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": e2e_total / args.steps},
+                "ms_per_step": e2e_total / args.steps, "copies": e2e_copies},
         "gpu_launches": launches_per_step * args.steps,
-        "launch": "whole step captured once as a CUDA graph (network forward beside projection and "
-                  "bin/sort, projection backward beside network backward, on a second stream), "
-                  "replayed per timed step",
+        "launch": "whole step captured once as a CUDA graph (gradient zeroing and network forward "
+                  "beside projection and bin/sort, projection backward beside network backward, on a "
+                  "second stream), replayed per timed step",
         "query_latency": latency,
         "roofline": roofline,
         "clocks": clocks,

@@ -81,19 +81,40 @@ __device__ __forceinline__ void put_row3(uint8_t* tile, int r, const float* x, i
 // B side of the three-term product, blocks [hi | hi | lo] along K: B[n][k] = W(n, k) for
 // n < Nr, k < Kr (zero elsewhere in [Nt x Kb]); W(n, k) = W[k * ld + n] when `cols`
 // (the weight stored input-major and used as W), W[n * ld + k] otherwise (used as W^T).
+// The thread's elements are loaded together (global-space loads, one round trip) before
+// the shared-memory stores.
+template <int Nt, int Kb>
 __device__ __forceinline__ void put_weights3(uint8_t* tile, const float* __restrict__ W, bool cols, int ld,
-                                             int Nr, int Kr, int Nt, int Kb) {
-    const int Kt = 3 * Kb;
-    for (int e = threadIdx.x; e < Nt * Kb; e += blockDim.x) {
+                                             int Nr, int Kr) {
+    constexpr int Kt = 3 * Kb;
+    constexpr int kPer = (Nt * Kb + kRowsB - 1) / kRowsB;
+    float v[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int e = (int)threadIdx.x + q * kRowsB;
         const int n = e / Kb, k = e - n * Kb;
-        const float v = (n < Nr && k < Kr) ? (cols ? W[k * ld + n] : W[n * ld + k]) : 0.f;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-        *reinterpret_cast<__nv_bfloat16*>(tile + canon_off(n, k, Kt)) = hi;
-        *reinterpret_cast<__nv_bfloat16*>(tile + canon_off(n, Kb + k, Kt)) = hi;
-        *reinterpret_cast<__nv_bfloat16*>(tile + canon_off(n, 2 * Kb + k, Kt)) = lo;
+        v[q] = (e < Nt * Kb && n < Nr && k < Kr) ? __ldg(cols ? W + k * ld + n : W + n * ld + k) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int e = (int)threadIdx.x + q * kRowsB;
+        if (e < Nt * Kb) {
+            const int n = e / Kb, k = e - n * Kb;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v[q]);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(v[q] - __bfloat162float(hi));
+            *reinterpret_cast<__nv_bfloat16*>(tile + canon_off(n, k, Kt)) = hi;
+            *reinterpret_cast<__nv_bfloat16*>(tile + canon_off(n, Kb + k, Kt)) = hi;
+            *reinterpret_cast<__nv_bfloat16*>(tile + canon_off(n, 2 * Kb + k, Kt)) = lo;
+        }
     }
 }
+
+// One row's inputs: transmitter, mean, latent code, upstream gradient, opacity logit.
+struct RowIn {
+    float t0, t1, t2, m0, m1, m2, olog;
+    float4 lat[GSPARC_LATENT / 4];
+    float4 da;
+};
 
 // Element (m, k) of a row-contracted operand (K = the tile's 128 rows), hi and lo terms.
 __device__ __forceinline__ void put_col(uint8_t* hi, uint8_t* lo, int m, int k, float v) {
@@ -149,10 +170,10 @@ __global__ void __launch_bounds__(kRowsB, 1) k_mlp_bwd_tc(
     uint8_t* GBhi = sm + L::kGBhi;
     uint8_t* GBlo = sm + L::kGBlo;
 
-    put_weights3(sm + L::kW1T, W1, true, HD, HD, GSPARC_MLP_IN, HD, kK0);
-    put_weights3(sm + L::kW2T, W2, true, HD, HD, HD, HD, HD);
-    put_weights3(sm + L::kW2R, W2, false, HD, HD, HD, HD, HD);
-    put_weights3(sm + L::kW1R, W1, false, HD, GSPARC_MLP_IN, HD, kK0, HD);
+    put_weights3<HD, kK0>(sm + L::kW1T, W1, true, HD, HD, GSPARC_MLP_IN);
+    put_weights3<HD, HD>(sm + L::kW2T, W2, true, HD, HD, HD);
+    put_weights3<HD, HD>(sm + L::kW2R, W2, false, HD, HD, HD);
+    put_weights3<kK0, HD>(sm + L::kW1R, W1, false, HD, GSPARC_MLP_IN, HD);
     {
         // the row-contracted operands start at zero (padding rows stay zero)
         uint4* z = reinterpret_cast<uint4*>(sm + L::kGAhi);
@@ -191,7 +212,32 @@ __global__ void __launch_bounds__(kRowsB, 1) k_mlp_bwd_tc(
 
     const int64_t rows = (int64_t)N * B;
     const int64_t tiles = (rows + kRowsB - 1) / kRowsB;
+    // the next tile's row inputs are loaded while this tile computes (global-space loads, so
+    // no shared-memory store orders them)
+    auto load_row = [&](int64_t tl) {
+        RowIn in{};
+        const int64_t row = tl * kRowsB + t;
+        if (tl < tiles && row < rows) {
+            const int bb = (int)(row / N);
+            const int i = (int)(row - (int64_t)bb * N);
+            in.t0 = __ldg(tx + 3 * bb);
+            in.t1 = __ldg(tx + 3 * bb + 1);
+            in.t2 = __ldg(tx + 3 * bb + 2);
+            in.m0 = __ldg(means + 3 * i);
+            in.m1 = __ldg(means + 3 * i + 1);
+            in.m2 = __ldg(means + 3 * i + 2);
+            in.olog = __ldg(ologit + i);
+            const float4* l4 = reinterpret_cast<const float4*>(latent + (size_t)i * GSPARC_LATENT);
+#pragma unroll
+            for (int q = 0; q < GSPARC_LATENT / 4; ++q) in.lat[q] = __ldg(l4 + q);
+            in.da = __ldg(d_attr + row);
+        }
+        return in;
+    };
+    RowIn next = load_row(blockIdx.x);
     for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const RowIn cur = next;
+        next = load_row(tile + gridDim.x);
         const int64_t row = tile * kRowsB + t;
         const bool valid = row < rows;
         int bb = 0, i = 0;
@@ -201,12 +247,12 @@ __global__ void __launch_bounds__(kRowsB, 1) k_mlp_bwd_tc(
         if (valid) {
             bb = (int)(row / N);
             i = (int)(row - (int64_t)bb * N);
-            t0 = tx[3 * bb];
-            t1 = tx[3 * bb + 1];
-            t2 = tx[3 * bb + 2];
-            m0 = means[3 * i];
-            m1 = means[3 * i + 1];
-            m2 = means[3 * i + 2];
+            t0 = cur.t0;
+            t1 = cur.t1;
+            t2 = cur.t2;
+            m0 = cur.m0;
+            m1 = cur.m1;
+            m2 = cur.m2;
             const float e0 = m0 - t0, e1 = m1 - t1, e2 = m2 - t2;
             dist = sqrtf(e0 * e0 + e1 * e1 + e2 * e2);
             d = fmaxf(dist, kDMin);
@@ -216,10 +262,9 @@ __global__ void __launch_bounds__(kRowsB, 1) k_mlp_bwd_tc(
             h0[0] = t0;
             h0[1] = t1;
             h0[2] = t2;
-            const float4* l4 = reinterpret_cast<const float4*>(latent + (size_t)i * GSPARC_LATENT);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float4 v = l4[q];
+                const float4 v = cur.lat[q];
                 h0[3 + 4 * q] = v.x;
                 h0[4 + 4 * q] = v.y;
                 h0[5 + 4 * q] = v.z;
@@ -230,8 +275,8 @@ __global__ void __launch_bounds__(kRowsB, 1) k_mlp_bwd_tc(
 #pragma unroll
             for (int f = 0; f < GSPARC_MLP_IN; ++f) h0[f] = 0.f;
         }
-        const float4 da = valid ? d_attr[row] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float olog = valid ? ologit[i] : 0.f;
+        const float4 da = valid ? cur.da : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float olog = valid ? cur.olog : 0.f;
         // ---- D1 = h0 W1
         put_row3(sm + L::kA0, t, h0, GSPARC_MLP_IN, kK0);
 #pragma unroll

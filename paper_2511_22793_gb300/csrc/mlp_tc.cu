@@ -49,20 +49,32 @@ __device__ __forceinline__ void write_row(uint8_t* tile, int r, const float* x, 
     }
 }
 
-// Weight operand B[n][k] = W[k][n] (W input-major [kin, N]) in blocks [hi | hi | lo].
-template <int TERMS>
-__device__ __forceinline__ void write_weights(uint8_t* tile, const float* __restrict__ W, int kin, int N,
-                                              int Kb) {
-    const int Kt = Kb * TERMS;
-    for (int e = threadIdx.x; e < N * Kb; e += blockDim.x) {
+// Weight operand B[n][k] = W[k][n] (W input-major [kin, N]) in blocks [hi | hi | lo].  The
+// thread's elements are loaded together (global-space loads, one round trip) before the
+// shared-memory stores.
+template <int TERMS, int N, int Kb>
+__device__ __forceinline__ void write_weights(uint8_t* tile, const float* __restrict__ W, int kin) {
+    constexpr int Kt = Kb * TERMS;
+    constexpr int kPer = (N * Kb + kRows - 1) / kRows;
+    float v[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int e = (int)threadIdx.x + q * kRows;
         const int n = e / Kb, k = e - n * Kb;
-        const float v = k < kin ? W[k * N + n] : 0.f;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-        *reinterpret_cast<__nv_bfloat16*>(tile + canon_off(n, k, Kt)) = hi;
-        if (TERMS == 3) {
-            *reinterpret_cast<__nv_bfloat16*>(tile + canon_off(n, Kb + k, Kt)) = hi;
-            *reinterpret_cast<__nv_bfloat16*>(tile + canon_off(n, 2 * Kb + k, Kt)) = lo;
+        v[q] = (e < N * Kb && k < kin) ? __ldg(W + k * N + n) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int e = (int)threadIdx.x + q * kRows;
+        if (e < N * Kb) {
+            const int n = e / Kb, k = e - n * Kb;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v[q]);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(v[q] - __bfloat162float(hi));
+            *reinterpret_cast<__nv_bfloat16*>(tile + canon_off(n, k, Kt)) = hi;
+            if (TERMS == 3) {
+                *reinterpret_cast<__nv_bfloat16*>(tile + canon_off(n, Kb + k, Kt)) = hi;
+                *reinterpret_cast<__nv_bfloat16*>(tile + canon_off(n, 2 * Kb + k, Kt)) = lo;
+            }
         }
     }
 }
@@ -100,8 +112,8 @@ __global__ void __launch_bounds__(kRows) k_mlp_tc(int N, int B, const float* __r
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + L::kMisc);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::kMisc + 8);
 
-    write_weights<TERMS>(sm + L::kB1, W1, GSPARC_MLP_IN, HD, kK1);
-    write_weights<TERMS>(sm + L::kB2, W2, HD, HD, HD);
+    write_weights<TERMS, HD, kK1>(sm + L::kB1, W1, GSPARC_MLP_IN);
+    write_weights<TERMS, HD, HD>(sm + L::kB2, W2, HD);
     for (int e = t; e < HD; e += kRows) {
         sb1[e] = b1[e];
         sb2[e] = b2[e];
@@ -136,7 +148,34 @@ __global__ void __launch_bounds__(kRows) k_mlp_tc(int N, int B, const float* __r
 
     const int64_t rows = (int64_t)N * B;
     const int64_t tiles = (rows + kRows - 1) / kRows;
+    // the next tile's row inputs are loaded while this tile computes (global-space loads, so
+    // no shared-memory store orders them)
+    struct RowIn {
+        float t0, t1, t2, m0, m1, m2;
+        float4 lat[GSPARC_LATENT / 4];
+    };
+    auto load_row = [&](int64_t tl) {
+        RowIn in{};
+        const int64_t rw = tl * kRows + t;
+        if (tl < tiles && rw < rows) {
+            const int bq = (int)(rw / N);
+            const int iq = (int)(rw - (int64_t)bq * N);
+            in.t0 = __ldg(tx + 3 * bq);
+            in.t1 = __ldg(tx + 3 * bq + 1);
+            in.t2 = __ldg(tx + 3 * bq + 2);
+            in.m0 = __ldg(means + 3 * iq);
+            in.m1 = __ldg(means + 3 * iq + 1);
+            in.m2 = __ldg(means + 3 * iq + 2);
+            const float4* l4 = reinterpret_cast<const float4*>(latent + (size_t)iq * GSPARC_LATENT);
+#pragma unroll
+            for (int q = 0; q < GSPARC_LATENT / 4; ++q) in.lat[q] = __ldg(l4 + q);
+        }
+        return in;
+    };
+    RowIn next = load_row(blockIdx.x);
     for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const RowIn cur = next;
+        next = load_row(tile + gridDim.x);
         const int64_t row = tile * kRows + t;
         const bool valid = row < rows;
         int b = 0, i = 0;
@@ -145,8 +184,8 @@ __global__ void __launch_bounds__(kRows) k_mlp_tc(int N, int B, const float* __r
         if (valid) {
             b = (int)(row / N);
             i = (int)(row - (int64_t)b * N);
-            const float t0 = tx[3 * b], t1 = tx[3 * b + 1], t2 = tx[3 * b + 2];
-            const float m0 = means[3 * i], m1 = means[3 * i + 1], m2 = means[3 * i + 2];
+            const float t0 = cur.t0, t1 = cur.t1, t2 = cur.t2;
+            const float m0 = cur.m0, m1 = cur.m1, m2 = cur.m2;
             const float e0 = m0 - t0, e1 = m1 - t1, e2 = m2 - t2;
             d = fmaxf(sqrtf(e0 * e0 + e1 * e1 + e2 * e2), kDMin);
             logd = logf(d);
@@ -155,10 +194,9 @@ __global__ void __launch_bounds__(kRows) k_mlp_tc(int N, int B, const float* __r
             h0[0] = t0;
             h0[1] = t1;
             h0[2] = t2;
-            const float4* l4 = reinterpret_cast<const float4*>(latent + (size_t)i * GSPARC_LATENT);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float4 v = l4[q];
+                const float4 v = cur.lat[q];
                 h0[3 + 4 * q] = v.x;
                 h0[4 + 4 * q] = v.y;
                 h0[5 + 4 * q] = v.z;

@@ -26,6 +26,40 @@ def _dev(a, device):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=device)
 
 
+class PackedInputs:
+    """Float32 device tensors that share one allocation (each at a 256-byte aligned offset),
+    with a pinned host mirror, so that a step's inputs move from host memory in one copy.
+
+    views[i] has shapes[i]; upload() copies the host mirror (or a run of views) to the device
+    on the current stream (asynchronously), nbytes is its size."""
+
+    def __init__(self, shapes, device="cuda"):
+        offs, o = [], 0
+        for sh in shapes:
+            offs.append(o)
+            o += (int(np.prod(sh)) * 4 + 255) // 256 * 256
+        self.offs = offs + [o]
+        self.nbytes = max(o, 256)
+        self.flat = torch.zeros(self.nbytes, dtype=torch.uint8, device=device)
+        self.host = torch.zeros(self.nbytes, dtype=torch.uint8).pin_memory()
+        self.views = [self.flat[off:off + int(np.prod(sh)) * 4].view(torch.float32).view(*sh)
+                      for off, sh in zip(offs, shapes)]
+        self.host_views = [self.host[off:off + int(np.prod(sh)) * 4].view(torch.float32).view(*sh)
+                           for off, sh in zip(offs, shapes)]
+
+    def set_host(self, i, a):
+        """Write array a into slot i of the host mirror."""
+        self.host_views[i].copy_(torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32))
+                                 if not isinstance(a, torch.Tensor) else a.detach().to("cpu", torch.float32))
+
+    def upload(self, first=0, last=None):
+        """Copy views[first:last] (one contiguous byte range; all by default) from the host
+        mirror on the current stream."""
+        last = len(self.views) if last is None else last
+        lo, hi = self.offs[first], (self.offs[last] if last < len(self.views) else self.nbytes)
+        self.flat[lo:hi].copy_(self.host[lo:hi], non_blocking=True)
+
+
 @dataclass
 class DeviceScene:
     means: torch.Tensor          # [N, 3]

@@ -135,3 +135,26 @@ def test_scheduled_backward_training_path(n, H, W, K, B, split_min):
     walks = pad.reshape(B, TH, 16, TW, 16).max(axis=(2, 4))
     smin = 3 if split_min == 0 else split_min
     assert int(((walks + 15) // 16 > smin).sum()) > 0
+
+
+def test_packed_inputs_upload_and_alignment():
+    """PackedInputs: every view starts 256-byte aligned inside one allocation, holds its array
+    after one upload, and writing one view leaves the others unchanged."""
+    from paper_2511_22793_gb300.pipeline import PackedInputs
+    rng = np.random.default_rng(7)
+    arrays = [rng.normal(size=sh).astype(np.float32) for sh in [(1001, 3), (7,), (5, 16), (1,), (2, 3, 4, 5, 2)]]
+    p = PackedInputs([a.shape for a in arrays], DEV)
+    for i, a in enumerate(arrays):
+        p.set_host(i, a)
+    p.upload()
+    torch.cuda.synchronize()
+    base = p.flat.data_ptr()
+    for v, a in zip(p.views, arrays):
+        assert (v.data_ptr() - base) % 256 == 0
+        assert v.data_ptr() + v.numel() * 4 <= base + p.nbytes
+        assert torch.equal(v.cpu(), torch.from_numpy(a))
+    p.views[2].fill_(3.0)
+    torch.cuda.synchronize()
+    for i, (v, a) in enumerate(zip(p.views, arrays)):
+        if i != 2:
+            assert torch.equal(v.cpu(), torch.from_numpy(a))
