@@ -294,6 +294,50 @@ __device__ __forceinline__ float warp_reduce_scatter9(const float (&v)[9], int l
     return d;
 }
 
+// Sums over the 32 lanes of v[0..17] (two entries' nine components), one component per
+// lane: five halving exchange rounds of 9, 5, 3, 2 and 1 shuffles (a round pads its vector
+// with a zero when it has odd length).  The lane holds component rs18_slot(lane).
+__device__ __forceinline__ float warp_reduce_scatter18(const float (&v)[18], int lane) {
+    const bool u4 = (lane >> 4) & 1, u3 = (lane >> 3) & 1, u2 = (lane >> 2) & 1, u1 = (lane >> 1) & 1;
+    const bool u0 = lane & 1;
+    float a[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float lo = v[i], hi = v[i + 9];
+        a[i] = (u4 ? hi : lo) + __shfl_xor_sync(0xffffffffu, u4 ? lo : hi, 16);
+    }
+    float b[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const float lo = a[i], hi = i + 5 < 9 ? a[i + 5] : 0.f;
+        b[i] = (u3 ? hi : lo) + __shfl_xor_sync(0xffffffffu, u3 ? lo : hi, 8);
+    }
+    float c[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float lo = b[i], hi = i + 3 < 5 ? b[i + 3] : 0.f;
+        c[i] = (u2 ? hi : lo) + __shfl_xor_sync(0xffffffffu, u2 ? lo : hi, 4);
+    }
+    float d[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float lo = c[i], hi = i + 2 < 3 ? c[i + 2] : 0.f;
+        d[i] = (u1 ? hi : lo) + __shfl_xor_sync(0xffffffffu, u1 ? lo : hi, 2);
+    }
+    return (u0 ? d[1] : d[0]) + __shfl_xor_sync(0xffffffffu, u0 ? d[0] : d[1], 1);
+}
+
+// Component of warp_reduce_scatter18 held by a lane (0..17), or -1: the kept half's index
+// through the five rounds, valid while it never falls on a padding zero.
+__device__ __forceinline__ int rs18_slot(int lane) {
+    const int sd = lane & 1;
+    const int sc = sd + 2 * ((lane >> 1) & 1);
+    const int sb = sc + 3 * ((lane >> 2) & 1);
+    const int sa = sb + 5 * ((lane >> 3) & 1);
+    const int sv = sa + 9 * ((lane >> 4) & 1);
+    return (sc <= 2 && sb <= 4 && sa <= 8) ? sv : -1;
+}
+
 template <int S>
 __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
     __shared__ float4 s_geo[kBatch];
@@ -1484,6 +1528,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
         const float c_f0 = (float)(a.two_pi_over_c * (a.f0 + (double)k0 * a.df));
         const float c_df = (float)(a.two_pi_over_c * a.df);
+        const int slot18 = rs18_slot(lane);
         // The walk in either direction (a compile-time flag).  Back to front from the pixel's
         // final state, acc = the sum over later entries of w reG a (the suffix); front to back
         // from T = 1 (the forward's own recursion), acc = the same sum over the entries up to
@@ -1551,15 +1596,16 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
                         const float amp = mdp.amp[j];
                         const float reGa = amp * reG;
                         float T, dalpha;
+                        // (1 - alpha >= 0.01: the approximate quotient is within 2 ulp)
                         if (kFront) {
                             T = ex2(logT);
                             acc = fmaf(T * alpha, reGa, acc);
-                            dalpha = T * reGa - (s_tot - acc) / (1.0f - alpha);
+                            dalpha = T * reGa - __fdividef(s_tot - acc, 1.0f - alpha);
                             logT = __fadd_rn(logT, nl);
                         } else {
                             const float logT_before = __fsub_rn(logT, nl);
                             T = ex2(logT_before);
-                            dalpha = T * reGa - acc / (1.0f - alpha);
+                            dalpha = T * reGa - __fdividef(acc, 1.0f - alpha);
                             acc = fmaf(T * alpha, reGa, acc);
                             logT = logT_before;
                         }
@@ -1580,15 +1626,18 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
                         gr[h][4] = dq * dy * dy;
                     }
                     if (__any_sync(0xffffffffu, live[0] || live[1])) {
-                        const float t0 = warp_reduce_scatter9(gr[0], lane);
-                        const float t1 = warp_reduce_scatter9(gr[1], lane);
-                        if ((lane & 1) == 0 && (lane >> 1) < 9) {
-                            red_at(st, warp, jv[0], lane >> 1) = t0;
-                            red_at(st, warp, jv[1], lane >> 1) = t1;
+                        // both entries' components reduced together, one per lane
+                        float g18[18];
+#pragma unroll
+                        for (int c = 0; c < 9; ++c) {
+                            g18[c] = gr[0][c];
+                            g18[9 + c] = gr[1][c];
                         }
-                    } else if (lane < 9) {
-                        red_at(st, warp, jv[0], lane) = 0.f;
-                        red_at(st, warp, jv[1], lane) = 0.f;
+                        const float tsum = warp_reduce_scatter18(g18, lane);
+                        if (slot18 >= 0)
+                            red_at(st, warp, slot18 < 9 ? jv[0] : jv[1], slot18 < 9 ? slot18 : slot18 - 9) = tsum;
+                    } else if (lane < 18) {
+                        red_at(st, warp, lane < 9 ? jv[0] : jv[1], lane < 9 ? lane : lane - 9) = 0.f;
                     }
                 }
                 tc_fence_before();
