@@ -754,19 +754,26 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
     uint32_t last = 0, used = 0;
     if (builder) {
         // ---------------- builder warps: records and the phasor operand
+        // records of the batch at pos (its id already in pf_nid), then the id of the next batch:
+        // the ids run one batch ahead, so that no record load waits on its id
         const bool gatherer = prod < kTcE;
-        uint32_t pf_gid = 0xffffffffu;
+        uint32_t pf_gid = 0xffffffffu, pf_nid = 0xffffffffu;
         float4 pf_p0 = make_float4(0.f, 0.f, 0.f, 0.f), pf_p1 = pf_p0, pf_at = pf_p0;
+        auto load_id = [&](uint32_t pos) -> uint32_t {
+            return pos + prod < range.y ? __ldg(a.ids + pos + prod) : 0xffffffffu;
+        };
         auto gather = [&](uint32_t pos) {
             if (gatherer) {
-                pf_gid = pos + prod < range.y ? a.ids[pos + prod] : 0xffffffffu;
+                pf_gid = pf_nid;
                 if (pf_gid < (uint32_t)a.N) {
-                    pf_p0 = a.proj[2 * pf_gid];
-                    pf_p1 = a.proj[2 * pf_gid + 1];
-                    pf_at = a.attr[(size_t)b * a.N + pf_gid];
+                    pf_p0 = __ldg(a.proj + 2 * pf_gid);
+                    pf_p1 = __ldg(a.proj + 2 * pf_gid + 1);
+                    pf_at = __ldg(a.attr + (size_t)b * a.N + pf_gid);
                 }
+                pf_nid = load_id(pos + kTcE);
             }
         };
+        if (gatherer) pf_nid = load_id(range.x);
         gather(range.x);
         for (int i = 0;; ++i) {
             const int st = i & 1;
@@ -1296,22 +1303,30 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
         if (front) return (int)min((uint32_t)kTbE, chunk_end - batch_lo(i));
         return (int)(chunk_end - (uint32_t)i * kTbE - batch_lo(i));
     };
-    // the builders' prefetch of one batch's records (threads 0..E-1 of the first builder warp)
+    // the builders' prefetch of one batch's records (threads 0..E-1 of the first builder
+    // warp); the list ids run one batch further ahead, so that no record load waits on its id
     const bool gatherer = producer && prod < kTbE;
-    uint32_t pf_gid = 0xffffffffu;
+    uint32_t pf_gid = 0xffffffffu, pf_nid = 0xffffffffu;
     float4 pf_p0 = make_float4(0.f, 0.f, 0.f, 0.f), pf_p1 = pf_p0, pf_at = pf_p0;
-    auto gather = [&](int i) {
+    auto load_id = [&](int i) -> uint32_t {
+        return (i < nbatch && prod < batch_n(i)) ? __ldg(a.ids + range.x + batch_lo(i) + prod) : 0xffffffffu;
+    };
+    auto gather = [&](int i) {   // records of batch i (its id in pf_nid), then the id of batch i + 1
         if (gatherer) {
-            pf_gid = prod < batch_n(i) ? a.ids[range.x + batch_lo(i) + prod] : 0xffffffffu;
+            pf_gid = pf_nid;
             if (pf_gid < (uint32_t)a.N) {
-                pf_p0 = a.proj[2 * pf_gid];
-                pf_p1 = a.proj[2 * pf_gid + 1];
-                pf_at = a.attr[(size_t)b * a.N + pf_gid];
+                pf_p0 = __ldg(a.proj + 2 * pf_gid);
+                pf_p1 = __ldg(a.proj + 2 * pf_gid + 1);
+                pf_at = __ldg(a.attr + (size_t)b * a.N + pf_gid);
             }
+            pf_nid = load_id(i + 1);
         }
     };
     // a scheduled item knows its batches already: its first records load during the prologue
-    if (a.items && nbatch > 0) gather(0);
+    if (a.items && nbatch > 0 && gatherer) {
+        pf_nid = load_id(0);
+        gather(0);
+    }
 
     if (tid == 0) {
         for (int st = 0; st < kWsR; ++st) {
@@ -1416,7 +1431,10 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
                 }
             }
         };
-        if (!a.items && nbatch > 0) gather(0);
+        if (!a.items && nbatch > 0 && gatherer) {
+            pf_nid = load_id(0);
+            gather(0);
+        }
         for (int i = 0; i < nbatch; ++i) {
             const int st = i % kWsR;
             if (i >= kWsR) {
