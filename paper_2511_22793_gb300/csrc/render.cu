@@ -950,6 +950,23 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
     const size_t pix = (size_t)y * a.W + x;
     const uint32_t nbat = *s_nbat;
     const bool any_mma = nbat != 0xffffffffu && nbat > 0u;
+    // fused loss: the targets of kAhead chunks of 8 subcarriers are in flight ahead of their
+    // use, the first ones already during the wait for the last products
+    constexpr int kChunks = 2 * S / 16;
+    constexpr int kAhead = kChunks < 4 ? kChunks : 4;
+    float2 tq[kAhead][8];
+    auto load_tg = [&](int c, float2 (&t)[8]) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = k0 + c / 2 + q;
+            t[q] = (a.l2_grad && inside && k < a.K) ? __ldcs(a.l2_target + ((size_t)b * a.K + k) * plane + pix)
+                                                    : make_float2(0.f, 0.f);
+        }
+    };
+    if (pixel) {
+#pragma unroll
+        for (int q = 0; q < kAhead; ++q) load_tg(16 * q, tq[q]);
+    }
     if (pixel && any_mma) {
         const int lb = (int)nbat - 1;
         wait_ok(mdone_bar(lb & 1), (uint32_t)(lb >> 1) & 1u);
@@ -960,20 +977,9 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
     float l2acc = 0.f, stot = 0.f;
     if (pixel) {
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-        // fused loss: the targets of the next 8 subcarriers are loaded while a chunk is processed
-        float2 tg[8], tgn[8];
-        auto load_tg = [&](int c, float2 (&t)[8]) {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int k = k0 + c / 2 + q;
-                t[q] = (a.l2_grad && inside && k < a.K) ? __ldcs(a.l2_target + ((size_t)b * a.K + k) * plane + pix)
-                                                        : make_float2(0.f, 0.f);
-            }
-        };
-        load_tg(0, tg);
 #pragma unroll
         for (int c = 0; c < 2 * S; c += 16) {
-            if (c + 16 < 2 * S) load_tg(c + 16, tgn);
+            float2 (&tg)[8] = tq[(c / 16) % kAhead];
             float v[16];
             if (any_mma) {
                 tmem_ld16(tbase + half * 2 * S + lane_base + c, v);
@@ -1029,8 +1035,7 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
                 const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
                 if ((lane & 1) == 0) s_csi[warp * 2 * S + c + idx] = w[0];
             }
-#pragma unroll
-            for (int q = 0; q < 8; ++q) tg[q] = tgn[q];
+            if (c / 16 + kAhead < kChunks) load_tg(c + 16 * kAhead, tg);   // the slot just used
         }
         if (inside && a.l2_grad && a.s_tot) a.s_tot[((size_t)b * gridDim.x + strip) * plane + pix] = stot;
         if (inside && strip == 0) {
