@@ -893,35 +893,55 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
             if (__any_sync(0xffffffffu, !done)) {
                 const uint64_t mask = warp_entry_mask(geo, ext, nb, wcx, wcy, a.W);
                 if (!done) {
-                    // phase 1: alpha and log2(1 - alpha) of every entry, independent of each other
+                    // phase 1: alpha and log2(1 - alpha) of every entry, independent of each other.
+                    // Groups of 8 entries that miss the warp's rows are skipped (warp-uniform);
+                    // inside a group the evaluation is branch-free so that the eight chains
+                    // overlap.  The operations are eval_alpha's, in its order (the backward
+                    // re-takes the same decisions); q > q_max or alpha < 1/255 gives al = -1.
                     float al[kTcE], nlv[kTcE];
 #pragma unroll
-                    for (int j = 0; j < kTcE; ++j) {
-                        al[j] = -1.f;
-                        nlv[j] = 0.f;
-                        if ((mask >> j) & 1ull) {   // warp-uniform
-                            float dx, dy, G, alpha;
-                            bool clamped;
-                            if (eval_alpha(ux, uy, a.W, geo[j], geo2[j], dx, dy, G, alpha, clamped)) {
-                                al[j] = alpha;
-                                nlv[j] = lg2(__fsub_rn(1.0f, alpha));
-                            }
+                    for (int g0 = 0; g0 < kTcE; g0 += 8) {
+#pragma unroll
+                        for (int j = g0; j < g0 + 8; ++j) {
+                            al[j] = -1.f;
+                            nlv[j] = 0.f;
+                        }
+                        if (((mask >> g0) & 0xffull) == 0ull) continue;   // warp-uniform
+#pragma unroll
+                        for (int j = g0; j < g0 + 8; ++j) {
+                            const float4 gg = geo[j];
+                            const float2 g2 = geo2[j];
+                            float dx = __fsub_rn(ux, gg.x);
+                            const float hw = 0.5f * (float)a.W;
+                            dx = dx >= hw ? __fsub_rn(dx, (float)a.W) : (dx < -hw ? __fadd_rn(dx, (float)a.W) : dx);
+                            const float dy = __fsub_rn(uy, gg.y);
+                            float q = __fmul_rn(__fmul_rn(g2.x, dy), dy);
+                            q = __fmaf_rn(__fmul_rn(__fmul_rn(2.0f, gg.w), dx), dy, q);
+                            q = __fmaf_rn(__fmul_rn(gg.z, dx), dx, q);
+                            const float G = ex2(__fmul_rn(-0.5f * kLog2e, q));
+                            const float a0 = __fmul_rn(g2.y, G);
+                            const float alpha = a0 > kAlphaMax ? kAlphaMax : a0;
+                            const bool ok_j = ((mask >> j) & 1ull) && q <= kQMax && alpha >= kAlphaMin;
+                            al[j] = ok_j ? alpha : -1.f;
+                            nlv[j] = ok_j ? lg2(__fsub_rn(1.0f, alpha)) : 0.f;
                         }
                     }
-                    // phase 2: the transmittance recursion, one FADD per entry on the serial chain
+                    // phase 2: the transmittance recursion, one FADD per entry on the serial
+                    // chain; branch-free, the same decisions as stopping before T < T_min
+                    bool stop = false;
 #pragma unroll
                     for (int j = 0; j < kTcE; ++j) {
-                        if (al[j] < 0.f) continue;
-                        const float alpha = al[j], nl = nlv[j];
-                        if (__fadd_rn(logT, nl) < kLog2TMin) {
-                            done = true;
-                            break;
-                        }
-                        wv[j] = ex2(logT) * alpha;
-                        logT = __fadd_rn(logT, nl);
-                        last = bs - range.x + (uint32_t)j + 1u;
-                        ++used;
+                        const float nt = __fadd_rn(logT, nlv[j]);
+                        const bool cand = !stop && al[j] >= 0.f;
+                        const bool term = cand && nt < kLog2TMin;
+                        stop = stop || term;
+                        const bool take = cand && !term;
+                        wv[j] = take ? ex2(logT) * al[j] : 0.f;
+                        logT = take ? nt : logT;
+                        last = take ? bs - range.x + (uint32_t)j + 1u : last;
+                        used += take ? 1u : 0u;
                     }
+                    done = stop;
                 }
             }
             uint8_t* Ast = sm + L::kA + (st * 2 + half) * L::kAHalf;
