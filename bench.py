@@ -192,14 +192,15 @@ def run_ours(args, rank, world, local_rank):
     render_fwd = G.gsparc_render_fwd_tc if args.render == "tc" else G.gsparc_render_fwd
     # tensor-core configuration: the backward scheduled over the SMs (walk lengths, then the
     # longest work items first, long walks split in two), its front chunks fed by the fused
-    # forward's s_tot
+    # forward's s_tot and its schedule by the forward's tile walks
     s_tot = r.s_tot_buffer(B) if args.render == "tc" else None
+    walks = r.walk_buffer(B) if args.render == "tc" else None
     bwd_ws = torch.zeros(G.gsparc_render_bwd_tc_workspace(r.view, r.band, B), dtype=torch.uint8, device=dev)
 
     def render_bwd():
         if args.render == "tc":
             G.gsparc_render_bwd_tc_balanced(r.view, r.band, B, n, r.proj, r.tile_ranges, r.sorted_ids, attr,
-                                            None, s_tot, logT, nc, d_spec, bwd_ws, d_attr, d_proj)
+                                            None, s_tot, logT, nc, d_spec, bwd_ws, d_attr, d_proj, tile_walk=walks)
         else:
             G.gsparc_render_bwd(r.view, r.band, B, n, r.proj, r.tile_ranges, r.sorted_ids, attr, logT, nc,
                                 d_spec, d_attr, d_proj)
@@ -256,7 +257,8 @@ def run_ours(args, rank, world, local_rank):
             # the loss fused into the forward's epilogue: it writes dL/dz, not the spectrum
             stage("render_fwd", lambda: G.gsparc_render_fwd_l2_tc(r.view, r.band, B, n, r.proj, r.tile_ranges,
                                                                   r.sorted_ids, attr, tgt, loss, d_spec, None,
-                                                                  logT, nc, n_used, s_tot=s_tot))
+                                                                  logT, nc, n_used, s_tot=s_tot,
+                                                                  tile_walk=walks))
         else:
             stage("render_fwd", lambda: render_fwd(r.view, r.band, B, n, r.proj, r.tile_ranges,
                                                    r.sorted_ids, attr, spec, logT, nc, n_used))
@@ -683,7 +685,7 @@ def run_serve(args):
     mlp = synth.make_mlp(32, seed=3, bf16_weights=True)
     ds = DeviceScene.from_host(sc, dev)
     dm = DeviceMLP.from_host(mlp, dev)
-    n_req = max(100, args.steps)
+    n_req = max(100, args.requests)
     rng = np.random.default_rng(4)
 
     def make(n):
@@ -838,6 +840,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=90 * 360,
                     help="pixels in the oracle CPU baseline (default: the whole image)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=2000,
+                    help="serving workload: Poisson requests per load level")
     ap.add_argument("--render", default="tc", choices=["tc", "fp32"],
                     help="forward compositing: tcgen05 (default) or FP32 CUDA cores")
     ap.add_argument("--workload", default="fwdbwd", choices=["fwdbwd", "batched", "train", "serve", "csi"],

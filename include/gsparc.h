@@ -330,6 +330,9 @@ int gsparc_render_bwd_tc_workspace(const gsparc_view* view, const gsparc_band* b
  *   gsparc_render_fwd_l2_tc) or NULL: the front chunks take s_tot when given,
  *   else form it from the spectrum and d_spectrum; with both NULL no walk is
  *   split (the items are still ordered).
+ *   tile_walk [B, T] (from gsparc_render_fwd_l2_tc) or NULL: given, the
+ *   schedule is one block that reads it; NULL, one block per tile first
+ *   takes each walk from n_contrib.
  *   split_min: 0 selects the default (3 batches), a negative value disables
  *   splitting; walks are split only while B * T * strips <= 2 x SMs (with
  *   more units the ordering alone keeps the SMs busy).
@@ -344,7 +347,7 @@ int gsparc_render_bwd_tc_workspace(const gsparc_view* view, const gsparc_band* b
 int gsparc_render_bwd_tc_balanced(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
                                   const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
                                   const float* attr, const float* spectrum, const float* s_tot,
-                                  const float* final_logT, const uint32_t* n_contrib,
+                                  const uint32_t* tile_walk, const float* final_logT, const uint32_t* n_contrib,
                                   const float* d_spectrum, int32_t split_min, void* ws, size_t ws_bytes,
                                   float* d_attr, float* d_proj, void* stream);
 
@@ -399,12 +402,15 @@ int gsparc_csi_head_bwd(int32_t B, int32_t K, int64_t P, const float* d_csi, flo
  * Re(conj(d_spectrum) z), the input gsparc_render_bwd_tc_balanced takes in
  * place of the spectrum (4 bytes per pixel and strip instead of 8 per
  * subcarrier).
+ * tile_walk may be NULL; else [B, T] out (T = tiles): per (transmitter,
+ * tile) the walk min(largest n_contrib of its pixels, list length), which
+ * gsparc_render_bwd_tc_balanced takes in place of its own walk pass.
  */
 int gsparc_render_fwd_l2_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
                             const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
                             const float* attr, const float* target, float* loss, float* d_spectrum,
                             float* spectrum, float* final_logT, uint32_t* n_contrib, uint32_t* n_used,
-                            float* s_tot, void* stream);
+                            float* s_tot, uint32_t* tile_walk, void* stream);
 
 /*
  * gsparc_render_fwd_tc with the CSI head fused into its epilogue: every

@@ -60,6 +60,9 @@ struct RenderArgs {
     // [B][strips][H][W]: Re sum_k conj(dL/dz_k) z_k over each strip of S subcarriers (written by
     // the fused L2 forward when not null; read by the front chunks of the scheduled backward)
     float* s_tot;
+    // [B][T]: the walk of each (transmitter, tile), min(largest n_contrib, list length), written
+    // by the tensor-core forward when not null (the scheduled backward's cost per tile)
+    uint32_t* tile_walk;
     // Scheduled tensor-core backward: work item r of the ordered list runs on block r
     // (x = b * T + tile, y = strip | front flag << 31, entries [z, w) of the walk), or null
     // for one block per (strip, tile, transmitter).
@@ -677,7 +680,7 @@ template <int S>
 struct RFwsSmem {
     using T = RTcSmem<S>;
     static constexpr int kBars = T::kBar;                     // rec[2], bready[2], aready[2], mdone[2]
-    static constexpr int kMisc = kBars + 8 * 8;               // TMEM slot, done warps, batch count, error, end
+    static constexpr int kMisc = kBars + 8 * 8;               // TMEM slot, done warps, batch count, error, end, walk
     static constexpr int kTotal = kMisc + 32;
 };
 
@@ -699,6 +702,7 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
     volatile uint32_t* s_nbat = tslot + 2;
     volatile uint32_t* s_err = tslot + 3;
     volatile uint32_t* s_end = tslot + 4;
+    uint32_t* s_walk = tslot + 5;
     auto rec_bar = [&](int st) { return smem_u32(&bars[st]); };
     auto bready_bar = [&](int st) { return smem_u32(&bars[2 + st]); };
     auto aready_bar = [&](int st) { return smem_u32(&bars[4 + st]); };
@@ -732,6 +736,7 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
         *s_nbat = 0xffffffffu;
         *s_err = 0u;
         *s_end = 0u;
+        *s_walk = 0u;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -1070,8 +1075,14 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
         for (int o = 16; o > 0; o >>= 1) l2acc += __shfl_xor_sync(0xffffffffu, l2acc, o);
         if (lane == 0) s_l2[warp] = l2acc;
     }
+    if (pixel && a.tile_walk) {
+        const uint32_t wmax = __reduce_max_sync(0xffffffffu, inside ? last : 0u);
+        if (lane == 0 && wmax) atomicMax(s_walk, wmax);
+    }
     tc_fence_before();
     __syncthreads();
+    if (a.tile_walk && strip == 0 && tid == 0)
+        a.tile_walk[(size_t)b * a.T + tile] = min(*s_walk, range.y - range.x);
     if (a.l2_grad && tid == 0) {
         float t = 0.f;
         for (int w2 = 0; w2 < kThreads / 32; ++w2) t += s_l2[w2];
@@ -1129,7 +1140,7 @@ extern "C" int gsparc_render_fwd_l2_tc(const gsparc_view* view, const gsparc_ban
                                        const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
                                        const float* attr, const float* target, float* loss, float* d_spectrum,
                                        float* spectrum, float* final_logT, uint32_t* n_contrib, uint32_t* n_used,
-                                       float* s_tot, void* stream) {
+                                       float* s_tot, uint32_t* tile_walk, void* stream) {
     using namespace gsparc;
     if (!common_ok(view, band, B, N, proj, tile_ranges, sorted_ids, attr)) return GSPARC_ERR_INVALID;
     if (!target || !loss || !d_spectrum) return GSPARC_ERR_INVALID;
@@ -1146,6 +1157,7 @@ extern "C" int gsparc_render_fwd_l2_tc(const gsparc_view* view, const gsparc_ban
     a.l2_loss = loss;
     a.l2_grad = reinterpret_cast<float2*>(d_spectrum);
     a.s_tot = s_tot;
+    a.tile_walk = tile_walk;
     const int64_t count = (int64_t)B * band->K * view->H * view->W;
     a.l2_inv = (float)(1.0 / (double)count);
     const int T = tiles_x(*view) * tiles_y(*view);
@@ -1754,11 +1766,14 @@ inline SchedLayout sched_layout(int B, int T, int strips) {
 
 inline int strips_of(int K) { return K <= 64 ? 1 : (K + 63) / 64; }
 
-// One block per (transmitter, tile): the walk.  The last block to finish builds the items.
-__global__ void __launch_bounds__(kSchedThreads) k_bwd_schedule(int H, int W, int TW, int T, int strips,
+// Without walks_in: one block per (transmitter, tile) takes the walk from n_contrib, and the
+// last block to finish builds the items.  With walks_in (written by the tensor-core forward):
+// one block builds the items from them.  BT = transmitters x tiles.
+__global__ void __launch_bounds__(kSchedThreads) k_bwd_schedule(int H, int W, int TW, int T, int BT, int strips,
                                                                 int split_min, int allow_split,
                                                                 const uint2* __restrict__ ranges,
                                                                 const uint32_t* __restrict__ n_contrib,
+                                                                const uint32_t* __restrict__ walks_in,
                                                                 uint32_t* __restrict__ hdr,
                                                                 uint32_t* __restrict__ walks,
                                                                 uint4* __restrict__ items) {
@@ -1767,23 +1782,26 @@ __global__ void __launch_bounds__(kSchedThreads) k_bwd_schedule(int H, int W, in
     __shared__ uint32_t s_warp[kSchedThreads / 32];
     __shared__ bool s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile = (int)(blockIdx.x % (uint32_t)T), b = (int)(blockIdx.x / (uint32_t)T);
-    if (tid == 0) s_max = 0u;
-    __syncthreads();
-    const int x = (tile % TW) * kTile + (tid & 15), y = (tile / TW) * kTile + (tid >> 4);
-    uint32_t v = (x < W && y < H) ? n_contrib[(size_t)b * H * W + (size_t)y * W + x] : 0u;
-    v = __reduce_max_sync(0xffffffffu, v);
-    if (lane == 0) atomicMax(&s_max, v);
-    __syncthreads();
-    if (tid == 0) {
-        const uint2 r = ranges[tile];
-        walks[blockIdx.x] = min(s_max, r.y - r.x);
+    if (!walks_in) {
+        const int tile = (int)(blockIdx.x % (uint32_t)T), b = (int)(blockIdx.x / (uint32_t)T);
+        if (tid == 0) s_max = 0u;
+        __syncthreads();
+        const int x = (tile % TW) * kTile + (tid & 15), y = (tile / TW) * kTile + (tid >> 4);
+        uint32_t v = (x < W && y < H) ? n_contrib[(size_t)b * H * W + (size_t)y * W + x] : 0u;
+        v = __reduce_max_sync(0xffffffffu, v);
+        if (lane == 0) atomicMax(&s_max, v);
+        __syncthreads();
+        if (tid == 0) {
+            const uint2 r = ranges[tile];
+            walks[blockIdx.x] = min(s_max, r.y - r.x);
+            __threadfence();
+            s_last = atomicAdd(&hdr[0], 1u) == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (!s_last) return;
         __threadfence();
-        s_last = atomicAdd(&hdr[0], 1u) == gridDim.x - 1;
     }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+    const uint32_t* wsrc = walks_in ? walks_in : walks;
     // batch counts of the one or two chunks of a walk (n1 = 0: not split)
     auto chunks = [&](uint32_t w, uint32_t& n0, uint32_t& n1) {
         const uint32_t nb = (w + kTbE - 1) / kTbE;
@@ -1796,12 +1814,12 @@ __global__ void __launch_bounds__(kSchedThreads) k_bwd_schedule(int H, int W, in
         }
     };
     auto key = [](uint32_t n) { return (uint32_t)kSchedKeys - 1u - min(n, (uint32_t)kSchedKeys - 1u); };
-    const int units = (int)gridDim.x * strips;
+    const int units = BT * strips;
     s_off[tid] = 0u;
     __syncthreads();
     for (int u = tid; u < units; u += kSchedThreads) {
         uint32_t n0, n1;
-        chunks(__ldcg(&walks[u / strips]), n0, n1);
+        chunks(__ldcg(&wsrc[u / strips]), n0, n1);
         if (n0) atomicAdd(&s_off[key(n0)], 1u);
         if (n1) atomicAdd(&s_off[key(n1)], 1u);
     }
@@ -1823,7 +1841,7 @@ __global__ void __launch_bounds__(kSchedThreads) k_bwd_schedule(int H, int W, in
     __syncthreads();
     for (int u = tid; u < units; u += kSchedThreads) {
         const uint32_t bt = (uint32_t)(u / strips), strip = (uint32_t)(u % strips);
-        const uint32_t w = __ldcg(&walks[bt]);
+        const uint32_t w = __ldcg(&wsrc[bt]);
         uint32_t n0, n1;
         chunks(w, n0, n1);
         if (n1) {
@@ -1834,7 +1852,7 @@ __global__ void __launch_bounds__(kSchedThreads) k_bwd_schedule(int H, int W, in
             items[atomicAdd(&s_off[key(n0)], 1u)] = make_uint4(bt, strip, 0u, w);
         }
     }
-    if (tid == 0) hdr[0] = 0u;   // every block has taken its ticket: reset for the next call
+    if (tid == 0 && !walks_in) hdr[0] = 0u;   // every block has taken its ticket: reset for the next call
 }
 
 }  // namespace
@@ -1872,10 +1890,10 @@ extern "C" int gsparc_render_bwd_tc_workspace(const gsparc_view* view, const gsp
 extern "C" int gsparc_render_bwd_tc_balanced(const gsparc_view* view, const gsparc_band* band, int32_t B,
                                              int32_t N, const float* proj, const uint32_t* tile_ranges,
                                              const uint32_t* sorted_ids, const float* attr,
-                                             const float* spectrum, const float* s_tot, const float* final_logT,
-                                             const uint32_t* n_contrib, const float* d_spectrum,
-                                             int32_t split_min, void* ws, size_t ws_bytes, float* d_attr,
-                                             float* d_proj, void* stream) {
+                                             const float* spectrum, const float* s_tot, const uint32_t* tile_walk,
+                                             const float* final_logT, const uint32_t* n_contrib,
+                                             const float* d_spectrum, int32_t split_min, void* ws, size_t ws_bytes,
+                                             float* d_attr, float* d_proj, void* stream) {
     using namespace gsparc;
     if (!common_ok(view, band, B, N, proj, tile_ranges, sorted_ids, attr)) return GSPARC_ERR_INVALID;
     if (!final_logT || !n_contrib || !d_spectrum || !d_attr || !d_proj || !ws) return GSPARC_ERR_INVALID;
@@ -1904,8 +1922,8 @@ extern "C" int gsparc_render_bwd_tc_balanced(const gsparc_view* view, const gspa
     const int allow_split = units <= 2 * (int64_t)num_sms() ? 1 : 0;
     // without s_tot or the spectrum a front chunk has no suffix: order the walks, split none
     const int smin = (!spectrum && !s_tot) ? -1 : (split_min == 0 ? kSplitMinDefault : split_min);
-    k_bwd_schedule<<<(unsigned)(B * T), kSchedThreads, 0, s>>>(
-        view->H, view->W, tiles_x(*view), T, strips, smin, allow_split, a.ranges, n_contrib, hdr,
+    k_bwd_schedule<<<tile_walk ? 1u : (unsigned)(B * T), kSchedThreads, 0, s>>>(
+        view->H, view->W, tiles_x(*view), T, B * T, strips, smin, allow_split, a.ranges, n_contrib, tile_walk, hdr,
         reinterpret_cast<uint32_t*>(w + SL.walks), reinterpret_cast<uint4*>(w + SL.items));
     if (launch_status() != GSPARC_OK) return GSPARC_ERR_CUDA;
     return launch_bwd_tc_any(a, T, s, (uint32_t)(2 * units));

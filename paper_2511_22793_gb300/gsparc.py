@@ -106,11 +106,11 @@ def lib():
             "gsparc_render_csi_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
                                                     vp, vp, vp, vp]),
             "gsparc_render_fwd_l2_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
-                                                       vp, vp, vp, vp, vp, vp, vp]),
+                                                       vp, vp, vp, vp, vp, vp, vp, vp]),
             "gsparc_render_bwd_tc_workspace": (ctypes.c_int, [P(View), P(Band), i32, P(ctypes.c_size_t)]),
             "gsparc_render_bwd_tc_balanced": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp,
-                                                             vp, vp, vp, vp, i32, vp, ctypes.c_size_t, vp, vp,
-                                                             vp]),
+                                                             vp, vp, vp, vp, vp, i32, vp, ctypes.c_size_t, vp,
+                                                             vp, vp]),
             "gsparc_adam": (ctypes.c_int, [i64, vp, vp, vp, vp, f32, f32, f32, f32, i32, vp]),
             "gsparc_check": (ctypes.c_int, [vp, vp]),
             "gsparc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -283,13 +283,13 @@ def s_tot_strips(K) -> int:
 
 def gsparc_render_bwd_tc_balanced(view, band, B, n, proj, tile_ranges, sorted_ids, attr, spectrum, s_tot,
                                   final_logT, n_contrib, d_spectrum, ws, d_attr, d_proj, split_min=0,
-                                  stream=None):
+                                  tile_walk=None, stream=None):
     """ws: a uint8 device tensor of gsparc_render_bwd_tc_workspace() bytes, zeroed once
     (torch.zeros) before its first use."""
     _call("gsparc_render_bwd_tc_balanced", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
-          _p(tile_ranges), _p(sorted_ids), _p(attr), _p(spectrum), _p(s_tot), _p(final_logT), _p(n_contrib),
-          _p(d_spectrum), int(split_min), _p(ws), ws.numel() * ws.element_size(), _p(d_attr), _p(d_proj),
-          _stream(stream))
+          _p(tile_ranges), _p(sorted_ids), _p(attr), _p(spectrum), _p(s_tot), _p(tile_walk), _p(final_logT),
+          _p(n_contrib), _p(d_spectrum), int(split_min), _p(ws), ws.numel() * ws.element_size(), _p(d_attr),
+          _p(d_proj), _stream(stream))
 
 
 def gsparc_l2_loss(z, target, loss, d_z=None, stream=None):
@@ -325,10 +325,10 @@ def gsparc_render_csi_tc(view, band, B, n, proj, tile_ranges, sorted_ids, attr, 
 
 def gsparc_render_fwd_l2_tc(view, band, B, n, proj, tile_ranges, sorted_ids, attr, target, loss, d_spectrum,
                             spectrum=None, final_logT=None, n_contrib=None, n_used=None, s_tot=None,
-                            stream=None):
+                            tile_walk=None, stream=None):
     _call("gsparc_render_fwd_l2_tc", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
           _p(tile_ranges), _p(sorted_ids), _p(attr), _p(target), _p(loss), _p(d_spectrum), _p(spectrum),
-          _p(final_logT), _p(n_contrib), _p(n_used), _p(s_tot), _stream(stream))
+          _p(final_logT), _p(n_contrib), _p(n_used), _p(s_tot), _p(tile_walk), _stream(stream))
 
 
 def gsparc_adam(param, grad, m, v, lr, step, b1=0.9, b2=0.999, eps=1e-15, stream=None):

@@ -192,8 +192,12 @@ class Renderer:
         return torch.empty((B, G.s_tot_strips(self.K), self.H, self.W), dtype=torch.float32,
                            device=self.device)
 
+    def walk_buffer(self, B):
+        """[B, T] buffer for the fused L2 forward's per-tile walk output."""
+        return torch.empty((B, self.T), dtype=torch.int32, device=self.device)
+
     def render_backward(self, attr, logT, nc, d_spec, d_attr, d_proj, tensor_cores=False, stream=None,
-                        spectrum=None, s_tot=None, split_min=0):
+                        spectrum=None, s_tot=None, split_min=0, tile_walk=None):
         """Compositing gradient.  tensor_cores selects the tensor-core form scheduled over the
         SMs (gsparc_render_bwd_tc_balanced; long walks are split when the spectrum or the fused
         forward's s_tot is given), else gsparc_render_bwd (same outputs)."""
@@ -207,7 +211,7 @@ class Renderer:
             self.bwd_ws = torch.zeros(need, dtype=torch.uint8, device=self.device)
         G.gsparc_render_bwd_tc_balanced(self.view, self.band, B, self.n, self.proj, self.tile_ranges,
                                         self.sorted_ids, attr, spectrum, s_tot, logT, nc, d_spec, self.bwd_ws,
-                                        d_attr, d_proj, split_min=split_min, stream=stream)
+                                        d_attr, d_proj, split_min=split_min, tile_walk=tile_walk, stream=stream)
 
     def attributes_backward(self, scene, mlp, tx, d_attr, d_means, d_ologit, d_latent, d_weights,
                             stream=None, tensor_cores=False):

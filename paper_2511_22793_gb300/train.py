@@ -59,7 +59,8 @@ class Trainer:
         self.H, self.W, self.K, self.n, self.batch = H, W, K, n, batch
         self.total_steps = total_steps
         self.tensor_cores = tensor_cores
-        self.s_tot = None   # fused forward's s_tot for the scheduled backward (tensor-core form)
+        self.s_tot = None   # fused forward's s_tot and tile walks for the scheduled backward
+        self.walks = None
         if init is None:
             sc = init_scene(n, seed=seed)
             mlp = synth.make_mlp(hidden, seed=seed + 1)
@@ -134,14 +135,16 @@ class Trainer:
             _, logT, nc = self.out
             if self.s_tot is None:
                 self.s_tot = self.r.s_tot_buffer(self.batch)
+                self.walks = self.r.walk_buffer(self.batch)
             G.gsparc_render_fwd_l2_tc(self.r.view, self.r.band, self.batch, self.n, self.r.proj, self.r.tile_ranges,
                                       self.r.sorted_ids, attr, target, self.loss, self.d_spec, None, logT, nc,
-                                      s_tot=self.s_tot)
+                                      s_tot=self.s_tot, tile_walk=self.walks)
         else:
             (spec, logT, nc), attr = self.forward(self.tx)
             G.gsparc_l2_loss(spec, target, self.loss, self.d_spec)
         self.r.render_backward(attr, logT, nc, self.d_spec, self.d_attr, self.d_proj,
-                               tensor_cores=self.tensor_cores, s_tot=self.s_tot)
+                               tensor_cores=self.tensor_cores, s_tot=self.s_tot,
+                               tile_walk=self.walks if self.tensor_cores else None)
         g = self.grads
         self.r.attributes_backward(self.scene, self.mlp, self.tx, self.d_attr, g["means"],
                                    g["opacity_logit"], g["latent"], [g[k] for k in MLP_KEYS],

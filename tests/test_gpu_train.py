@@ -105,36 +105,41 @@ def test_scheduled_backward_training_path(n, H, W, K, B, split_min):
     target = torch.randn((B, K, H, W, 2), device=DEV) * 0.01
     loss = torch.zeros(1, device=DEV)
     d_spec = torch.empty_like(target)
-    s_tot = r.s_tot_buffer(B)
+    s_tot, tile_walk = r.s_tot_buffer(B), r.walk_buffer(B)
     G.gsparc_render_fwd_l2_tc(r.view, r.band, B, n, r.proj, r.tile_ranges, r.sorted_ids, attr, target, loss,
-                              d_spec, None, logT, nc, s_tot=s_tot)
+                              d_spec, None, logT, nc, s_tot=s_tot, tile_walk=tile_walk)
     res = []
-    for balanced in (False, True):
+    for form in ("plain", "balanced", "balanced_walks"):
         d_attr = torch.zeros_like(attr)
         d_proj = torch.zeros_like(r.proj)
-        if balanced:
-            r.render_backward(attr, logT, nc, d_spec, d_attr, d_proj, tensor_cores=True, s_tot=s_tot,
-                              split_min=split_min)
-        else:
+        if form == "plain":
             G.gsparc_render_bwd_tc(r.view, r.band, B, n, r.proj, r.tile_ranges, r.sorted_ids, attr, logT, nc,
                                    d_spec, d_attr, d_proj)
+        else:
+            r.render_backward(attr, logT, nc, d_spec, d_attr, d_proj, tensor_cores=True, s_tot=s_tot,
+                              split_min=split_min, tile_walk=tile_walk if form == "balanced_walks" else None)
         torch.cuda.synchronize()
         res.append((d_attr.cpu().numpy().astype(np.float64), d_proj.cpu().numpy().astype(np.float64)))
     assert r.check() == 0
-    (ua, up), (ba, bp) = res
-    for j in range(4):
-        e = np.linalg.norm(ba[..., j] - ua[..., j]) / np.linalg.norm(ua[..., j])
-        assert e <= 1e-4, ("attr", j, e)
-    for j in (0, 1, 4, 5, 6):
-        e = np.linalg.norm(bp[:, j] - up[:, j]) / np.linalg.norm(up[:, j])
-        assert e <= 1e-4, ("proj", j, e)
-    # the schedule had walks to split: some tile's walk spans more than split_min batches
+    ua, up = res[0]
+    for ba, bp in res[1:]:
+        for j in range(4):
+            e = np.linalg.norm(ba[..., j] - ua[..., j]) / np.linalg.norm(ua[..., j])
+            assert e <= 1e-4, ("attr", j, e)
+        for j in (0, 1, 4, 5, 6):
+            e = np.linalg.norm(bp[:, j] - up[:, j]) / np.linalg.norm(up[:, j])
+            assert e <= 1e-4, ("proj", j, e)
+    # the forward's tile walks: min(largest n_contrib of the tile's pixels, list length), bit-exact
     TH, TW = (H + 15) // 16, (W + 15) // 16
     pad = np.zeros((B, TH * 16, TW * 16), np.int64)
     pad[:, :H, :W] = nc.cpu().numpy()
-    walks = pad.reshape(B, TH, 16, TW, 16).max(axis=(2, 4))
+    walks = pad.reshape(B, TH, 16, TW, 16).max(axis=(2, 4)).reshape(B, -1)
+    rng_ = r.tile_ranges.cpu().numpy().astype(np.int64)
+    want = np.minimum(walks, (rng_[:, 1] - rng_[:, 0])[None, :])
+    assert np.array_equal(tile_walk.cpu().numpy().astype(np.int64), want)
+    # the schedule had walks to split: some tile's walk spans more than split_min batches
     smin = 3 if split_min == 0 else split_min
-    assert int(((walks + 15) // 16 > smin).sum()) > 0
+    assert int(((want + 15) // 16 > smin).sum()) > 0
 
 
 def test_packed_inputs_upload_and_alignment():
