@@ -462,7 +462,7 @@ def run_ours(args, rank, world, local_rank):
     # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the tensor-core
     # compositing kernels in this step (50k Gaussians, 64 subcarriers, 360x90, one transmitter),
     # from one ncu capture of each current kernel (the forward with its fused loss)
-    traffic = {"render_bwd": 17510912, "render_fwd": 17191680} if args.render == "tc" else {}
+    traffic = {"render_bwd": 17510912, "render_fwd": 17157888} if args.render == "tc" else {}
     if top in unit_flop:
         achieved = units * unit_flop[top] / (avg[top] * 1e-3) / 1e12
         roofline = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
