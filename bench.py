@@ -771,13 +771,13 @@ def run_serve(args):
 
     # saturated rate of the plain path: the same kind of requests back to back
     probe = make(100)
-    serve_plain(ds, dm, probe, np.zeros(len(probe)), res, device=dev)
+    serve_plain(ds, dm, probe, np.zeros(len(probe)), res, device=dev, keep_results=False)
     for q in probe:
         q.spectrum = None
     st = latency_stats(probe)
     sat = st["spectra_per_s"]
     out_rows = []
-    srv = Server(ds, dm, res, mem_budget_bytes=24 << 30, max_batch=8, n_streams=4, device=dev)
+    srv = Server(ds, dm, res, mem_budget_bytes=24 << 30, max_batch=8, n_streams=4, device=dev, keep_results=False)
     for frac in (0.25, 0.5, 0.75, 0.9, 1.25, 2.0):
         lam = frac * sat
         reqs = make(n_req)
@@ -789,7 +789,7 @@ def run_serve(args):
             q.spectrum = None
         a = latency_stats(reqs)
         plain = [Request(q.rid, q.tx, q.res, q.K) for q in reqs]
-        serve_plain(ds, dm, plain, arr, res, device=dev)
+        serve_plain(ds, dm, plain, arr, res, device=dev, keep_results=False)
         for q in plain:
             q.spectrum = None
         b = latency_stats(plain)
@@ -802,7 +802,7 @@ def run_serve(args):
     for q in burst:
         q.spectrum = None
     burst_plain = [Request(q.rid, q.tx, q.res, q.K) for q in burst]
-    serve_plain(ds, dm, burst_plain, np.zeros(n_req), res, device=dev)
+    serve_plain(ds, dm, burst_plain, np.zeros(n_req), res, device=dev, keep_results=False)
     for q in burst_plain:
         q.spectrum = None
     out_rows.append({"load": "burst", "batched": latency_stats(burst), "plain": latency_stats(burst_plain)})
@@ -827,7 +827,7 @@ def run_serve(args):
     for q in mov:
         q.spectrum = None
     mov_plain = [Request(q.rid, q.tx, q.res, q.K, rx=q.rx, V=q.V) for q in mov]
-    serve_plain(ds, dm, mov_plain, np.zeros(n_mov), res, device=dev)
+    serve_plain(ds, dm, mov_plain, np.zeros(n_mov), res, device=dev, keep_results=False)
     for q in mov_plain:
         q.spectrum = None
     out_rows.append({"load": "burst, moving receiver", "requests": n_mov, "batched": latency_stats(mov),

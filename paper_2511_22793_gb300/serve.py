@@ -67,8 +67,11 @@ class _Batch:
 class Server:
     def __init__(self, scene: DeviceScene, mlp: DeviceMLP, resolutions, mem_budget_bytes=16 << 30,
                  max_batch=8, n_streams=4, precision=G.GSPARC_BF16X2, tensor_cores=True,
-                 f_c=2.4e9, df=312.5e3, device="cuda"):
+                 f_c=2.4e9, df=312.5e3, device="cuda", keep_results=True):
+        """keep_results=False: a finished request drops its spectrum (the client has taken
+        it), so the device memory of retired batches is released as the budget assumes."""
         self.dev = torch.device(device)
+        self.keep_results = keep_results
         self.scene, self.mlp = scene, mlp
         self.precision, self.tensor_cores = precision, tensor_cores
         self.f_c, self.df = f_c, df
@@ -156,6 +159,8 @@ class Server:
                 now = time.perf_counter()
                 for q in bt.reqs:
                     q.t_done = now
+                    if not self.keep_results:
+                        q.spectrum = None
                     self.done.append(q)
                 self.used -= bt.nbytes
                 self.free_streams.append(self.streams.index(bt.stream))
@@ -206,8 +211,9 @@ class Server:
 
 
 def serve_plain(scene: DeviceScene, mlp: DeviceMLP, requests, arrivals, resolutions, f_c=2.4e9,
-                df=312.5e3, device="cuda"):
-    """Baseline: one request at a time, FP32 network and FP32 compositing, one stream."""
+                df=312.5e3, device="cuda", keep_results=True):
+    """Baseline: one request at a time, FP32 network and FP32 compositing, one stream.
+    keep_results=False: each request's spectrum is dropped once it is done."""
     dev = torch.device(device)
     geom = {}
     for (H, W) in resolutions:
@@ -247,7 +253,7 @@ def serve_plain(scene: DeviceScene, mlp: DeviceMLP, requests, arrivals, resoluti
                             logT, nc)
         torch.cuda.current_stream(dev).synchronize()
         q.t_done = time.perf_counter()
-        q.spectrum = spec[0]
+        q.spectrum = spec[0] if keep_results else None
     return requests
 
 
