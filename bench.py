@@ -5,7 +5,8 @@ Workload (one step = one pass of the whole path over one query):
   around the receiver, upper hemisphere; log-scales N(-1.5, 0.5); random unit
   quaternions; opacity logits N(0,1); 16-dim latents N(0,1)), one transmitter,
   64 subcarriers 312.5 kHz apart about 2.4 GHz, 360x90 hemisphere (1-degree
-  bins, 16x16 tiles), attribute network 20 -> 32 -> 32 -> 3 in FP32.
+  bins, 16x16 tiles), attribute network 20 -> 32 -> 32 -> 3 (split-BF16 on
+  the tensor cores in the default configuration, FP32 with --render fp32).
   Step = project -> bin/sort -> attribute network -> render forward ->
   complex L2 loss against a target spectrum (rendered by the same path from a
   second seeded scene, once, outside the timed region) -> render backward ->
@@ -17,9 +18,12 @@ kernel's per-pixel counter) for one subcarrier; fwd+bwd per step.
 
 `value` times the step on the device with inputs resident in HBM (CUDA
 events on the launching stream, L2 flushed by a 256 MiB write between timed
-steps); `e2e` times the same step through the C ABI with the scene, network
-and target copied from pinned host memory and the loss read back, inside the
-timed region.  `roofline` reports the dominant kernel against the FP32 ALU
+steps; the loss fused into the forward).  `e2e` times the step through the C
+ABI with the scene, network, transmitters and target copied from pinned host
+memory and the loss read back, inside the timed region; its graph overlaps
+the target's copy with projection, binning and the forward (which then writes
+the spectrum, and the loss follows once the target is in), and it is checked
+against the device-resident step's loss and gradients before timing.  `roofline` reports the dominant kernel against the FP32 ALU
 peak; `cpu_baseline` times the FP64 oracle on a bounded pixel sample.
 
 Multi-GPU: queries are independent, so N ranks run N replicas on their own

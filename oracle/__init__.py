@@ -10,6 +10,8 @@ Contents, each following the passage of the paper it cites:
                   covariance J V Sigma V^T J^T (Sec. 4.2 "Directional
                   Projection and Splatting"; Sec. 3.2 for Sigma = R S S^T R^T)
   attributes.py   attribute network with the log-distance feature (Eq. 1)
+  emission.py     the per-Gaussian emission network R^3 -> R^2 of Eq. 1 with its
+                  element-wise sigmoid (Sec. 4.3 form) and the 1/d toggle
   binsort.py      tile binning and front-to-back (receiver distance) ordering
                   (Algorithm 1, IntersectGaussians / Sort by depth)
   render_oracle.c per-pixel compositing of complex contributions across
