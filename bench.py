@@ -635,6 +635,77 @@ def run_batched(args):
     print(json.dumps(out))
 
 
+def run_emission(args):
+    """Per-Gaussian emission network (Eq. 1 in the paper's own form, Sec. 4.3; the Sec. 7 width
+    sweep and 1/d toggle): forward and backward of gsparc_emission_fwd/_bwd on 50k Gaussians at
+    hidden widths 8, 16 and 64, one and 16 transmitters, CUDA events, L2 flushed between
+    launches.  Each Gaussian has its own weights, so the pass is a stream over the flat
+    buffer: the achieved HBM bandwidth (weights + means + logits in, attributes out; the
+    backward also reads d_attr and reads and writes the weight gradients) is reported against
+    the measured copy peak."""
+    import torch
+
+    from paper_2511_22793_gb300 import gsparc as G
+    from paper_2511_22793_gb300 import synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n = 50_000
+    sc = synth.make_scene(n, seed=0)
+    means = torch.tensor(sc.means, device=dev)
+    ologit = torch.tensor(sc.opacity_logit, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, device=dev)
+    peak = float(measured_peaks().get("hbm_gbs", 6800.0))
+    rows = []
+    for h in (8, 16, 64):
+        stride = G.gsparc_emission_stride(h)
+        rng = np.random.default_rng(h)
+        w = np.zeros((n, stride), np.float32)
+        w[:, :6 * h + 2] = rng.normal(size=(n, 6 * h + 2)) / np.sqrt(max(h, 3))
+        wd = torch.tensor(w, device=dev)
+        dw = torch.zeros_like(wd)
+        dm, do = torch.zeros((n, 3), device=dev), torch.zeros(n, device=dev)
+        for B in (1, 16):
+            tx = torch.tensor(synth.make_tx(B, seed=2), device=dev)
+            attr = torch.empty((B, n, 4), device=dev)
+            d_attr = torch.randn((B, n, 4), device=dev)
+            for inv_d in ((True, False) if (h == 16 and B == 1) else (True,)):
+                def timed(fn, reps=30):
+                    ts = []
+                    for it in range(reps + 3):
+                        flush.fill_(1.0)
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        fn()
+                        e1.record()
+                        e1.synchronize()
+                        if it >= 3:
+                            ts.append(e0.elapsed_time(e1) * 1e3)
+                    return float(np.median(ts))
+                fwd_us = timed(lambda: G.gsparc_emission_fwd(tx, (0.0, 0.0, 0.0), means, ologit, wd, h, attr,
+                                                             inv_d=inv_d))
+                bwd_us = timed(lambda: G.gsparc_emission_bwd(tx, (0.0, 0.0, 0.0), means, ologit, wd, h, d_attr,
+                                                             dm, do, dw, inv_d=inv_d))
+                fwd_bytes = n * (stride * 4 + 16) + B * n * 16
+                bwd_bytes = n * (stride * 4 + 16) + B * n * 16 + n * (2 * stride * 4 + 32)
+                rows.append({"hidden": h, "transmitters": B, "inv_d": inv_d,
+                             "fwd_us": fwd_us, "bwd_us": bwd_us,
+                             "fwd_gaussian_tx_per_s": n * B / (fwd_us * 1e-6),
+                             "fwd_hbm_gbs": fwd_bytes / (fwd_us * 1e-6) / 1e9,
+                             "fwd_hbm_frac": fwd_bytes / (fwd_us * 1e-6) / 1e9 / peak,
+                             "bwd_hbm_gbs": bwd_bytes / (bwd_us * 1e-6) / 1e9,
+                             "bwd_hbm_frac": bwd_bytes / (bwd_us * 1e-6) / 1e9 / peak})
+    torch.cuda.synchronize(dev)
+    out = {"metric": "per-Gaussian emission network forward and backward (Gaussian x transmitter / s)",
+           "unit": "us", "n_gpus": 1, "dtype": "f32", "data": "synthetic (seeded)",
+           "config": {"workload": "per-Gaussian emission network 3 -> h -> 2, 50k Gaussians, "
+                                  "widths 8/16/64, 1 or 16 transmitters, L2 flushed between launches",
+                      "hbm_peak_gbs": peak},
+           "rows": rows}
+    print(json.dumps(out))
+
+
 def run_csi(args):
     """CSI queries (Eq. 2): the 64-subcarrier channel estimate at unseen transmitter positions,
     50k Gaussians, 360x90, hidden 32, 16 transmitters per launch, receiver fixed (geometry
@@ -924,11 +995,13 @@ def main():
                     help="serving workload: Poisson requests per load level")
     ap.add_argument("--render", default="tc", choices=["tc", "fp32"],
                     help="forward compositing: tcgen05 (default) or FP32 CUDA cores")
-    ap.add_argument("--workload", default="fwdbwd", choices=["fwdbwd", "batched", "train", "serve", "csi"],
+    ap.add_argument("--workload", default="fwdbwd",
+                    choices=["fwdbwd", "batched", "train", "serve", "csi", "emission"],
                     help="fwdbwd: the default step; batched: 64-transmitter inference with the "
                          "tensor-core network against the plain one-query path; train: the training "
                          "loop; serve: the continuous-batching query server; csi: channel-estimate "
-                         "queries with the fused CSI head")
+                         "queries with the fused CSI head; emission: the per-Gaussian emission "
+                         "network's width sweep")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -947,6 +1020,10 @@ def main():
     if args.workload == "csi":
         if rank == 0:
             run_csi(args)
+        return
+    if args.workload == "emission":
+        if rank == 0:
+            run_emission(args)
         return
     if args.workload == "train":
         if rank == 0:

@@ -233,6 +233,44 @@ int gsparc_attr_mlp_bwd_tc(int32_t N, int32_t B, const float* tx, const float* r
                            void* stream);
 
 /*
+ * Per-Gaussian emission network, the paper's own form of Eq. 1 (Sec. 4.3:
+ * every Gaussian carries a network R^3 -> R^2 with one hidden layer, 16 units
+ * in the paper, 8..64 in its Sec. 7 sweep).  For transmitter x = tx[b] and
+ * Gaussian i with hidden width h:
+ *   o = W2_i^T relu(W1_i^T x + b1_i) + b2_i,  d = max(|mu_i - x|, 0.01),
+ *   s = sigmoid(o_0 - ln d) + j sigmoid(o_1 - ln d)   (element-wise, Eq. 1),
+ *   attr[b,i] = (a, phi0, sigma, L) = (|s| / d, arg s, sigmoid(logit_i),
+ *               d + |mu_i - rx|),
+ * with |s| in place of |s| / d when inv_d is 0 (the 1/d term of the Sec. 4.2
+ * compositing rule switched off, the Sec. 7 ablation), so that a e^{j phi0} =
+ * s / d feeds the renderer unchanged.
+ *   weights [N, stride] device, stride = gsparc_emission_stride(h): row i is
+ *   W1 [3, h] (input-major), b1 [h], W2 [h, 2] (input-major), b2 [2], then
+ *   padding to a multiple of 4 floats (ignored); 16-byte aligned.
+ *   tx [B,3] device; rx [3] HOST; means [N,3]; opacity_logit [N];
+ *   attr [B,N,4] out (16-byte aligned).  hidden in 1..64.
+ * One thread per Gaussian over every transmitter, the block's weight rows
+ * staged in shared memory (the pass streams 4 * stride bytes per Gaussian).
+ */
+int32_t gsparc_emission_stride(int32_t hidden);
+int gsparc_emission_fwd(int32_t N, int32_t B, int32_t hidden, const float* tx, const float* rx,
+                        const float* means, const float* opacity_logit, const float* weights,
+                        int32_t inv_d, float* attr, void* stream);
+
+/*
+ * Gradient of gsparc_emission_fwd for the upstream d_attr [B,N,4]
+ * (dL/d(a, phi0, sigma, L)): ADDS into d_means [N,3] and d_opacity_logit [N]
+ * (atomically, so another kernel may add into them concurrently) and into
+ * d_weights [N, stride] (the padding untouched); summed over the B
+ * transmitters.  The distance clamp passes no gradient; the ReLU's derivative
+ * at 0 is 0.
+ */
+int gsparc_emission_bwd(int32_t N, int32_t B, int32_t hidden, const float* tx, const float* rx,
+                        const float* means, const float* opacity_logit, const float* weights,
+                        int32_t inv_d, const float* d_attr, float* d_means, float* d_opacity_logit,
+                        float* d_weights, void* stream);
+
+/*
  * Front-to-back compositing of complex contributions across subcarriers
  * (Sec. 4.2 compositing rule; Algorithm 1 inner loop): for every pixel u and
  * subcarrier k of every transmitter b,

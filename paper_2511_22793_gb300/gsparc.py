@@ -33,7 +33,7 @@ PROJ_STRIDE = 8
 EXPORTS = [
     "gsparc_num_tiles", "gsparc_project", "gsparc_project_bwd", "gsparc_bin_sort_workspace",
     "gsparc_bin_sort", "gsparc_bin_sort_noalloc", "gsparc_attr_mlp", "gsparc_attr_mlp_bwd",
-    "gsparc_attr_mlp_bwd_tc", "gsparc_render_fwd", "gsparc_render_fwd_tc", "gsparc_render_bwd",
+    "gsparc_attr_mlp_bwd_tc", "gsparc_emission_stride", "gsparc_emission_fwd", "gsparc_emission_bwd", "gsparc_render_fwd", "gsparc_render_fwd_tc", "gsparc_render_bwd",
     "gsparc_render_bwd_tc", "gsparc_render_bwd_tc_workspace", "gsparc_render_bwd_tc_balanced", "gsparc_l2_loss", "gsparc_csi_head", "gsparc_csi_loss", "gsparc_csi_head_bwd",
     "gsparc_render_csi_tc", "gsparc_render_fwd_l2_tc", "gsparc_adam", "gsparc_check", "gsparc_strerror",
 ]
@@ -91,6 +91,10 @@ def lib():
                                                    vp, vp, P(MLPGrad), vp]),
             "gsparc_attr_mlp_bwd_tc": (ctypes.c_int, [i32, i32, vp, P(f32), vp, vp, vp, P(MLP), i32, vp,
                                                       vp, vp, vp, P(MLPGrad), vp]),
+            "gsparc_emission_stride": (i32, [i32]),
+            "gsparc_emission_fwd": (ctypes.c_int, [i32, i32, i32, vp, P(f32), vp, vp, vp, i32, vp, vp]),
+            "gsparc_emission_bwd": (ctypes.c_int, [i32, i32, i32, vp, P(f32), vp, vp, vp, i32, vp, vp, vp, vp,
+                                                   vp]),
             "gsparc_render_fwd": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
                                                  vp, vp, vp]),
             "gsparc_render_fwd_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
@@ -268,6 +272,32 @@ def gsparc_render_bwd_tc(view, band, B, n, proj, tile_ranges, sorted_ids, attr, 
     _call("gsparc_render_bwd_tc", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
           _p(tile_ranges), _p(sorted_ids), _p(attr), _p(final_logT), _p(n_contrib), _p(d_spectrum),
           _p(d_attr), _p(d_proj), _stream(stream))
+
+
+def gsparc_emission_stride(hidden) -> int:
+    """Floats per Gaussian in the emission buffer (6 hidden + 2, rounded up to a multiple of 4)."""
+    v = int(lib().gsparc_emission_stride(int(hidden)))
+    if v <= 0:
+        raise GsparcError("gsparc_emission_stride", -1)
+    return v
+
+
+def gsparc_emission_fwd(tx, rx, means, opacity_logit, weights, hidden, attr, inv_d=True, stream=None):
+    """tx [B,3] device, rx 3 host floats, weights [N, stride] -> attr [B,N,4]."""
+    n, B = int(means.shape[0]), int(tx.shape[0])
+    rxa = (ctypes.c_float * 3)(*[float(v) for v in rx])
+    _call("gsparc_emission_fwd", n, B, int(hidden), _p(tx), rxa, _p(means), _p(opacity_logit), _p(weights),
+          1 if inv_d else 0, _p(attr), _stream(stream))
+
+
+def gsparc_emission_bwd(tx, rx, means, opacity_logit, weights, hidden, d_attr, d_means, d_opacity_logit,
+                        d_weights, inv_d=True, stream=None):
+    """Adds the gradients of gsparc_emission_fwd for d_attr [B,N,4] into d_means, d_opacity_logit and
+    d_weights."""
+    n, B = int(means.shape[0]), int(tx.shape[0])
+    rxa = (ctypes.c_float * 3)(*[float(v) for v in rx])
+    _call("gsparc_emission_bwd", n, B, int(hidden), _p(tx), rxa, _p(means), _p(opacity_logit), _p(weights),
+          1 if inv_d else 0, _p(d_attr), _p(d_means), _p(d_opacity_logit), _p(d_weights), _stream(stream))
 
 
 def gsparc_render_bwd_tc_workspace(view, band, B) -> int:

@@ -72,6 +72,21 @@ def test_invalid_arguments_rejected_on_host(L):
         G.GSPARC_ERR_INVALID
 
 
+def test_emission_stride_and_arguments(L):
+    """Per-Gaussian emission buffer: 6h + 2 floats rounded up to a multiple of 4; widths outside
+    1..64 and misaligned buffers are rejected on the host."""
+    assert [L.gsparc_emission_stride(h) for h in (1, 5, 8, 16, 64)] == [8, 32, 52, 100, 388]
+    assert L.gsparc_emission_stride(0) == 0 and L.gsparc_emission_stride(65) == 0
+    vp = ctypes.c_void_p
+    rx = (ctypes.c_float * 3)(0, 0, 0)
+    assert L.gsparc_emission_fwd(10, 1, 0, vp(256), rx, vp(256), vp(256), vp(256), 1, vp(256), None) == \
+        G.GSPARC_ERR_INVALID
+    assert L.gsparc_emission_fwd(10, 1, 16, vp(256), rx, vp(256), vp(256), vp(264), 1, vp(256), None) == \
+        G.GSPARC_ERR_INVALID
+    assert L.gsparc_emission_bwd(10, 1, 16, vp(256), rx, vp(256), vp(256), vp(256), 1, None, vp(256), vp(256),
+                                 vp(256), None) == G.GSPARC_ERR_INVALID
+
+
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(G, "_lib", None)
     monkeypatch.setattr(G, "LIB_PATH", str(tmp_path / "missing.so"))
