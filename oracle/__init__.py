@@ -19,6 +19,7 @@ Contents, each following the passage of the paper it cites:
                   rule; Algorithm 1 inner loop)
   render.py       ctypes wrapper of render_oracle.c
   csi.py          spatial-mean CSI head (Eq. 2), channel loss (Eq. 3), NMSE
+  spectrum_loss.py  magnitude-spectrum loss L1 + SSIM (Eq. 4) and its gradient
   pipeline.py     the whole forward pass, the L2 or channel loss and the full
                   gradient
   adam.py         the Adam update (Algorithm 1, Adam step)
