@@ -706,6 +706,53 @@ def run_emission(args):
     print(json.dumps(out))
 
 
+def run_spectrum_loss(args):
+    """Magnitude-spectrum loss (Eq. 4, L1 + SSIM) and its gradient on the default step's
+    spectrum size (one transmitter, 64 subcarriers, 360x90): CUDA events, L2 flushed between
+    launches; the effective bandwidth counts the algorithmic bytes of the four passes (44 B of
+    maps written and read per pixel and plane, the spectrum and target read twice, dL/dz
+    written: 132 B)."""
+    import torch
+
+    from paper_2511_22793_gb300 import gsparc as G
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    B, K, H, W = 1, 64, 90, 360
+    g = torch.Generator(device=dev).manual_seed(0)
+    z = torch.randn((B, K, H, W, 2), device=dev, generator=g)
+    y = (z.square().sum(-1).sqrt() * (1 + 0.3 * torch.randn((B, K, H, W), device=dev, generator=g))).clamp_min(0)
+    ws = torch.empty(G.gsparc_spectrum_loss_workspace(B, K, H, W), dtype=torch.uint8, device=dev)
+    loss = torch.zeros(1, device=dev)
+    dz = torch.empty_like(z)
+    flush = torch.empty(64 * 1024 * 1024, device=dev)
+    peak = float(measured_peaks().get("hbm_gbs", 6800.0))
+
+    def timed(fn, reps=50):
+        ts = []
+        for it in range(reps + 3):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            if it >= 3:
+                ts.append(e0.elapsed_time(e1) * 1e3)
+        return float(np.median(ts))
+
+    both = timed(lambda: G.gsparc_spectrum_loss(z, y, ws, loss, dz))
+    fwd = timed(lambda: G.gsparc_spectrum_loss(z, y, ws, loss, None))
+    n = B * K * H * W
+    out = {"metric": "magnitude-spectrum loss (L1 + SSIM) and gradient", "unit": "us", "n_gpus": 1,
+           "dtype": "f32", "data": "synthetic (seeded)",
+           "config": {"workload": "Eq. 4 loss, 1 transmitter, 64 subcarriers, 360x90, L2 flushed"},
+           "loss_and_grad_us": both, "loss_only_us": fwd,
+           "effective_gbs": 132 * n / (both * 1e-6) / 1e9, "hbm_frac": 132 * n / (both * 1e-6) / 1e9 / peak}
+    print(json.dumps(out))
+
+
 def run_csi(args):
     """CSI queries (Eq. 2): the 64-subcarrier channel estimate at unseen transmitter positions,
     50k Gaussians, 360x90, hidden 32, 16 transmitters per launch, receiver fixed (geometry
@@ -996,12 +1043,12 @@ def main():
     ap.add_argument("--render", default="tc", choices=["tc", "fp32"],
                     help="forward compositing: tcgen05 (default) or FP32 CUDA cores")
     ap.add_argument("--workload", default="fwdbwd",
-                    choices=["fwdbwd", "batched", "train", "serve", "csi", "emission"],
+                    choices=["fwdbwd", "batched", "train", "serve", "csi", "emission", "spectrum_loss"],
                     help="fwdbwd: the default step; batched: 64-transmitter inference with the "
                          "tensor-core network against the plain one-query path; train: the training "
                          "loop; serve: the continuous-batching query server; csi: channel-estimate "
                          "queries with the fused CSI head; emission: the per-Gaussian emission "
-                         "network's width sweep")
+                         "network's width sweep; spectrum_loss: the L1 + SSIM loss of Eq. 4")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -1024,6 +1071,10 @@ def main():
     if args.workload == "emission":
         if rank == 0:
             run_emission(args)
+        return
+    if args.workload == "spectrum_loss":
+        if rank == 0:
+            run_spectrum_loss(args)
         return
     if args.workload == "train":
         if rank == 0:

@@ -426,6 +426,29 @@ int gsparc_csi_head_bwd(int32_t B, int32_t K, int64_t P, const float* d_csi, flo
                         float* d_spectrum, void* stream);
 
 /*
+ * Magnitude-spectrum loss (Eq. 4): L = (1 - lambda) L1(|z|, y) + lambda (1 -
+ * SSIM(|z|, y)), the paper's loss when the target is a magnitude spectrum
+ * (lambda_1 = 0.2 in the paper).  L1 is the mean |x - y| over every
+ * (transmitter, subcarrier, pixel), x = |z|; SSIM is taken per (transmitter,
+ * subcarrier) plane with an 11 x 11 Gaussian window (sigma 1.5, normalised),
+ * zero padding with the output the size of the plane, C1 = 0.01^2,
+ * C2 = 0.03^2, as the mean of the SSIM map, averaged over planes.
+ *   spectrum [B,K,H,W,2] (complex); target [B,K,H,W] (real magnitudes);
+ *   loss [1] out (overwritten); d_spectrum [B,K,H,W,2] out (overwritten) or
+ *   NULL: dL/dRe z, dL/dIm z = dL/dx z / |z|, 0 where z = 0 (and the L1
+ *   term's derivative 0 where x = y).
+ *   ws: device workspace of ws_bytes >= gsparc_spectrum_loss_workspace()
+ *   (44 B per pixel and plane + 256), 16-byte aligned.
+ * Separable filtering in four passes over whole maps (HBM-bound); sums
+ * accumulate in double atomically, so the last bits of the loss may differ
+ * between runs.
+ */
+int gsparc_spectrum_loss_workspace(int32_t B, int32_t K, int32_t H, int32_t W, size_t* ws_bytes);
+int gsparc_spectrum_loss(int32_t B, int32_t K, int32_t H, int32_t W, const float* spectrum,
+                         const float* target, float lambda, void* ws, size_t ws_bytes, float* loss,
+                         float* d_spectrum, void* stream);
+
+/*
  * gsparc_render_fwd_tc with the complex L2 loss of gsparc_l2_loss fused into its
  * epilogue (the training step's loss, Algorithm 1; complex L2 in place of
  * Eq. 4): with count = B*K*H*W,

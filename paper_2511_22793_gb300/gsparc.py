@@ -34,7 +34,9 @@ EXPORTS = [
     "gsparc_num_tiles", "gsparc_project", "gsparc_project_bwd", "gsparc_bin_sort_workspace",
     "gsparc_bin_sort", "gsparc_bin_sort_noalloc", "gsparc_attr_mlp", "gsparc_attr_mlp_bwd",
     "gsparc_attr_mlp_bwd_tc", "gsparc_emission_stride", "gsparc_emission_fwd", "gsparc_emission_bwd", "gsparc_render_fwd", "gsparc_render_fwd_tc", "gsparc_render_bwd",
-    "gsparc_render_bwd_tc", "gsparc_render_bwd_tc_workspace", "gsparc_render_bwd_tc_balanced", "gsparc_l2_loss", "gsparc_csi_head", "gsparc_csi_loss", "gsparc_csi_head_bwd",
+    "gsparc_render_bwd_tc", "gsparc_render_bwd_tc_workspace", "gsparc_render_bwd_tc_balanced",
+    "gsparc_l2_loss", "gsparc_csi_head", "gsparc_csi_loss", "gsparc_csi_head_bwd",
+    "gsparc_spectrum_loss_workspace", "gsparc_spectrum_loss",
     "gsparc_render_csi_tc", "gsparc_render_fwd_l2_tc", "gsparc_adam", "gsparc_check", "gsparc_strerror",
 ]
 
@@ -107,6 +109,9 @@ def lib():
             "gsparc_csi_head": (ctypes.c_int, [i32, i32, i64, vp, f32, vp, vp]),
             "gsparc_csi_loss": (ctypes.c_int, [i32, i32, vp, vp, vp, vp, vp]),
             "gsparc_csi_head_bwd": (ctypes.c_int, [i32, i32, i64, vp, f32, vp, vp]),
+            "gsparc_spectrum_loss_workspace": (ctypes.c_int, [i32, i32, i32, i32, P(ctypes.c_size_t)]),
+            "gsparc_spectrum_loss": (ctypes.c_int, [i32, i32, i32, i32, vp, vp, f32, vp, ctypes.c_size_t, vp, vp,
+                                                    vp]),
             "gsparc_render_csi_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
                                                     vp, vp, vp, vp]),
             "gsparc_render_fwd_l2_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
@@ -325,6 +330,19 @@ def gsparc_render_bwd_tc_balanced(view, band, B, n, proj, tile_ranges, sorted_id
 def gsparc_l2_loss(z, target, loss, d_z=None, stream=None):
     count = z.numel() // 2
     _call("gsparc_l2_loss", count, _p(z), _p(target), _p(loss), _p(d_z), _stream(stream))
+
+
+def gsparc_spectrum_loss_workspace(B, K, H, W) -> int:
+    out = ctypes.c_size_t(0)
+    _call("gsparc_spectrum_loss_workspace", int(B), int(K), int(H), int(W), ctypes.byref(out))
+    return int(out.value)
+
+
+def gsparc_spectrum_loss(spectrum, target, ws, loss, d_spectrum=None, lam=0.2, stream=None):
+    """spectrum [B,K,H,W,2], target [B,K,H,W] magnitudes -> loss [1] (Eq. 4, L1 + SSIM) and dL/dz."""
+    B, K, H, W = (int(v) for v in target.shape)
+    _call("gsparc_spectrum_loss", B, K, H, W, _p(spectrum), _p(target), float(lam), _p(ws),
+          ws.numel() * ws.element_size(), _p(loss), _p(d_spectrum), _stream(stream))
 
 
 def gsparc_csi_head(spectrum, csi, scale, stream=None):
