@@ -248,7 +248,8 @@ int gsparc_attr_mlp_bwd_tc(int32_t N, int32_t B, const float* tx, const float* r
  *   W1 [3, h] (input-major), b1 [h], W2 [h, 2] (input-major), b2 [2], then
  *   padding to a multiple of 4 floats (ignored); 16-byte aligned.
  *   tx [B,3] device; rx [3] HOST; means [N,3]; opacity_logit [N];
- *   attr [B,N,4] out (16-byte aligned).  hidden in 1..64.
+ *   attr [B,N,4] out (16-byte aligned).  hidden in 1..64; N < 2^26 and
+ *   N * B < 2^31 (GSPARC_ERR_INVALID otherwise).
  * One thread per Gaussian over every transmitter, the block's weight rows
  * staged in shared memory (the pass streams 4 * stride bytes per Gaussian).
  */

@@ -299,6 +299,7 @@ bool em_args_ok(int32_t N, int32_t B, int32_t hidden, const float* tx, const flo
                 const float* ologit, const float* weights) {
     if (N < 0 || B <= 0 || B > 65535 || hidden < 1 || hidden > kEmMaxHidden || !rx) return false;
     if ((int64_t)N * B >= (1ll << 31)) return false;
+    if ((int64_t)N * 32 >= (1ll << 31)) return false;   // thread index N * G in 32 bits
     if (N > 0 && (!tx || !means || !ologit || !weights)) return false;
     if (reinterpret_cast<uintptr_t>(weights) & 15) return false;
     return true;

@@ -85,6 +85,26 @@ def test_emission_stride_and_arguments(L):
         G.GSPARC_ERR_INVALID
     assert L.gsparc_emission_bwd(10, 1, 16, vp(256), rx, vp(256), vp(256), vp(256), 1, None, vp(256), vp(256),
                                  vp(256), None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_emission_fwd(70_000_000, 1, 16, vp(256), rx, vp(256), vp(256), vp(256), 1, vp(256),
+                                 None) == G.GSPARC_ERR_INVALID
+
+
+def test_spectrum_loss_workspace_and_arguments(L):
+    """Magnitude-spectrum loss: workspace 44 B per pixel and plane (rounded) + 256; lambda outside
+    [0, 1], missing buffers and a too-small workspace are rejected on the host."""
+    out = ctypes.c_size_t(0)
+    assert L.gsparc_spectrum_loss_workspace(1, 64, 90, 360, ctypes.byref(out)) == 0
+    n = 64 * 90 * 360
+    assert out.value >= 44 * n + 256 and out.value < 44 * n + 256 + 1024
+    assert L.gsparc_spectrum_loss_workspace(0, 64, 90, 360, ctypes.byref(out)) == G.GSPARC_ERR_INVALID
+    vp = ctypes.c_void_p
+    f32 = ctypes.c_float
+    assert L.gsparc_spectrum_loss(1, 1, 8, 8, vp(256), vp(256), f32(1.5), vp(256), 1 << 20, vp(256), None,
+                                  None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_spectrum_loss(1, 1, 8, 8, None, vp(256), f32(0.2), vp(256), 1 << 20, vp(256), None,
+                                  None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_spectrum_loss(1, 1, 8, 8, vp(256), vp(256), f32(0.2), vp(256), 16, vp(256), None,
+                                  None) == G.GSPARC_ERR_INVALID
 
 
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
