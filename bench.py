@@ -636,8 +636,8 @@ def run_batched(args):
 
 
 def run_emission(args):
-    """Per-Gaussian emission network (Eq. 1 in the paper's own form, Sec. 4.3; the Sec. 7 width
-    sweep and 1/d toggle): forward and backward of gsparc_emission_fwd/_bwd on 50k Gaussians at
+    """Per-Gaussian emission network (Eq. 1 in the paper's own form, Sec. 4.1 and the Sec. 4.2
+    implementation notes; the Sec. 7 width sweep and 1/d toggle): forward and backward of gsparc_emission_fwd/_bwd on 50k Gaussians at
     hidden widths 8, 16 and 64, one and 16 transmitters, CUDA events, L2 flushed between
     launches.  Each Gaussian has its own weights, so the pass is a stream over the flat
     buffer: the achieved HBM bandwidth (weights + means + logits in, attributes out; the

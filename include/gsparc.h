@@ -233,9 +233,10 @@ int gsparc_attr_mlp_bwd_tc(int32_t N, int32_t B, const float* tx, const float* r
                            void* stream);
 
 /*
- * Per-Gaussian emission network, the paper's own form of Eq. 1 (Sec. 4.3:
- * every Gaussian carries a network R^3 -> R^2 with one hidden layer, 16 units
- * in the paper, 8..64 in its Sec. 7 sweep).  For transmitter x = tx[b] and
+ * Per-Gaussian emission network, the paper's own form of Eq. 1 (Sec. 4.1;
+ * by the Sec. 4.2 implementation notes every Gaussian carries a network
+ * R^3 -> R^2 with one hidden layer, 16 units in the paper, 8..64 in its Sec. 7
+ * sweep).  For transmitter x = tx[b] and
  * Gaussian i with hidden width h:
  *   o = W2_i^T relu(W1_i^T x + b1_i) + b2_i,  d = max(|mu_i - x|, 0.01),
  *   s = sigmoid(o_0 - ln d) + j sigmoid(o_1 - ln d)   (element-wise, Eq. 1),

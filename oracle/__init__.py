@@ -11,7 +11,7 @@ Contents, each following the passage of the paper it cites:
                   Projection and Splatting"; Sec. 3.2 for Sigma = R S S^T R^T)
   attributes.py   attribute network with the log-distance feature (Eq. 1)
   emission.py     the per-Gaussian emission network R^3 -> R^2 of Eq. 1 with its
-                  element-wise sigmoid (Sec. 4.3 form) and the 1/d toggle
+                  element-wise sigmoid (Sec. 4.1, per Gaussian) and the 1/d toggle
   binsort.py      tile binning and front-to-back (receiver distance) ordering
                   (Algorithm 1, IntersectGaussians / Sort by depth)
   render_oracle.c per-pixel compositing of complex contributions across
@@ -20,6 +20,7 @@ Contents, each following the passage of the paper it cites:
   render.py       ctypes wrapper of render_oracle.c
   csi.py          spatial-mean CSI head (Eq. 2), channel loss (Eq. 3), NMSE
   spectrum_loss.py  magnitude-spectrum loss L1 + SSIM (Eq. 4) and its gradient
+  confidence.py   confidence-weighted objective C L_task - alpha log C (Eq. 5)
   pipeline.py     the whole forward pass, the L2 or channel loss and the full
                   gradient
   adam.py         the Adam update (Algorithm 1, Adam step)

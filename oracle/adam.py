@@ -1,4 +1,4 @@
-"""Oracle Adam update (Algorithm 1, "Adam" step; Sec. 4.3 optimisation).
+"""Oracle Adam update (Algorithm 1, "Adam" step; Sec. 4.2 optimisation).
 
 TEST INFRASTRUCTURE (see the package docstring).  float64 NumPy.
 

@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE (see the package docstring).  Plain PyTorch CPU ops in
 float64; autograd on these ops supplies the oracle's gradient.
 
 Follows Eq. 1, s_i = sigmoid(f_i(x) - log d_i) with the sigmoid applied to the
-real and imaginary parts separately, the Sec. 4.3 implementation notes (every
+real and imaginary parts separately, the Sec. 4.2 implementation notes (every
 Gaussian carries its own network R^3 -> R^2 with 16 hidden units, stored in a
 flat per-Gaussian buffer; widths 8, 16 and 64 in the Sec. 7 ablation) and the
 s_i / d_i term of the Sec. 4.2 compositing rule, which the Sec. 7 ablation

@@ -1,5 +1,6 @@
-// Per-Gaussian emission network (Eq. 1 in the paper's own form, Sec. 4.3): every Gaussian i
-// carries a network f_i: R^3 -> R^2 with one hidden ReLU layer of width h, evaluated at the
+// Per-Gaussian emission network (Eq. 1 in the paper's own form, Sec. 4.1; one per Gaussian as
+// the Sec. 4.2 implementation notes give it): every Gaussian i carries a network
+// f_i: R^3 -> R^2 with one hidden ReLU layer of width h, evaluated at the
 // query (transmitter) position x, and emits s_i = sigmoid(o_0 - ln d_i) + j sigmoid(o_1 - ln d_i)
 // (the sigmoid element-wise on Re and Im), d_i = max(|x - mu_i|, 0.01).  The renderer's
 // attributes follow: a = |s| / d (|s| with the 1/d term of the compositing rule switched off),

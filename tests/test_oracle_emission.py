@@ -1,4 +1,4 @@
-"""Pins of the oracle's per-Gaussian emission network (Eq. 1 per Gaussian, Sec. 4.3 form):
+"""Pins of the oracle's per-Gaussian emission network (Eq. 1 per Gaussian, Sec. 4.1 and 4.2):
 closed forms worked by hand, the 1/d toggle, the distance clamp, independence of the
 Gaussians, and central finite differences of its FP64 gradient."""
 import math
