@@ -143,6 +143,7 @@ def run_ours(args, rank, world, local_rank):
     from paper_2511_22793_gb300 import gsparc as G
     from paper_2511_22793_gb300 import synth
     from paper_2511_22793_gb300.pipeline import DeviceMLP, DeviceScene, PackedInputs, Renderer
+    from paper_2511_22793_gb300.replicas import job_totals, rank_queries, throughput
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
@@ -150,7 +151,7 @@ def run_ours(args, rank, world, local_rank):
     n, K, H, W, hidden, B = wl["n"], wl["K"], wl["H"], wl["W"], wl["hidden"], wl["B"]
     sc = synth.make_scene(n, seed=0)
     mlp = synth.make_mlp(hidden, seed=3)
-    tx = synth.make_tx(B + world, seed=2)[rank:rank + B]
+    tx = rank_queries(synth.make_tx(B * world, seed=2), B, rank, world)
     r = Renderer(H, W, K, n, f_c=wl["f_c"], df=wl["df"], device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -388,11 +389,9 @@ def run_ours(args, rank, world, local_rank):
         s1.synchronize()
         step_ms.append(s0.elapsed_time(s1))
     torch.cuda.synchronize(dev)
-    total_ms = sum(step_ms)
+    # whole job: the units all ranks processed over the slowest rank's time
+    job_units, total_ms = job_totals(units * args.steps, sum(step_ms), device=dev)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        total_ms = float(t.item())
         tdist.barrier()
 
     # end to end: host (pinned) inputs copied into the buffers the graph reads, the step, the loss
@@ -435,6 +434,8 @@ def run_ours(args, rank, world, local_rank):
     e2e_ms = []
     for it in range(args.warmup + args.steps):
         flush.fill_(1.0)
+        if dist and it == args.warmup:
+            tdist.barrier()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         if graph_e2e is not None:
@@ -447,12 +448,7 @@ def run_ours(args, rank, world, local_rank):
         if it >= args.warmup:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     clocks = sampler.stop()   # sampled over both timed regions (device-timed and end to end)
-    if dist:
-        t = torch.tensor([sum(e2e_ms)], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    else:
-        e2e_total = sum(e2e_ms)
+    job_units_e2e, e2e_total = job_totals(units * len(e2e_ms), sum(e2e_ms), device=dev)
 
     # dominant kernel and its roofline
     avg = {k: statistics.mean(v) for k, v in per_kernel.items()}
@@ -479,8 +475,8 @@ def run_ours(args, rank, world, local_rank):
                     "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s", "frac": None,
                     "traffic": None}
 
-    value = units * args.steps * world / (total_ms * 1e-3)
-    e2e_value = units * args.steps * world / (e2e_total * 1e-3)
+    value = throughput(job_units, total_ms)
+    e2e_value = throughput(job_units_e2e, e2e_total)
     sorted_ms = sorted(step_ms)
     latency = query_latency(dev, queries=max(50, min(args.steps, 400)))
     out = {
@@ -489,7 +485,7 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
         "config": {"workload": wl["name"], "n_gaussians": n, "subcarriers": K, "H": H, "W": W,
                    "hidden": hidden, "transmitters_per_step": B, "pairs": n_pairs,
-                   "units_per_step": units, "l2": "flushed (256 MiB write) between timed steps",
+                   "units_per_step": job_units // args.steps, "l2": "flushed (256 MiB write) between timed steps",
                    "compositing": "subcarrier sums on tensor cores (split-BF16 products, FP32 "
                                   "accumulation), transmittance and gradients FP32"
                                   if args.render == "tc" else "FP32 CUDA cores",
