@@ -2,16 +2,25 @@
 that part, so that the pins are not vacuous.  Every mistake is planted in the oracle, on the
 CPU: a patched copy of the C renderer compiled into a temporary library, or a monkeypatched
 Python function; the real oracle is restored afterwards."""
+import numpy as np
 import pytest
 import torch
 
+import test_oracle_adam as TAD
 import test_oracle_attributes as TA
+import test_oracle_binsort as TB
+import test_oracle_confidence as TCF
+import test_oracle_csi as TC
 import test_oracle_emission as TE
 import test_oracle_grad as TG
 import test_oracle_projection as TP
 import test_oracle_render as TR
 import test_oracle_spectrum_loss as TS
+from oracle import adam as AD
 from oracle import attributes as A
+from oracle import binsort as B
+from oracle import confidence as CF
+from oracle import csi as CS
 from oracle import emission as E
 from oracle import projection as P
 from oracle import render as R
@@ -76,3 +85,39 @@ def test_planted_ssim_padding_mistake_fails_its_pin(monkeypatch):
     monkeypatch.setattr(S, "_filter", replicate)
     with pytest.raises(AssertionError):
         TS.test_ssim_map_against_brute_force()
+
+
+def test_planted_adam_bias_correction_mistake_fails_its_pin(monkeypatch):
+    orig = AD.adam_step
+    # no bias correction: 1 - b^t taken as 1
+    monkeypatch.setattr(AD, "adam_step", lambda p, g, m, v, t, lr, **k: orig(p, g, m, v, 10 ** 9, lr, **k))
+    with pytest.raises(AssertionError):
+        TAD.test_adam_matches_torch_fp64()
+
+
+def test_planted_pixel_centre_mistake_fails_its_pin(monkeypatch):
+    orig = B.footprint_tiles
+
+    def integer_centres(rec, H, W):
+        shifted = np.array(rec, dtype=np.float32, copy=True)
+        shifted[:, :2] += np.float32(0.5)     # pixel centres at (x, y) instead of (x + 0.5, y + 0.5)
+        return orig(shifted, H, W)
+
+    monkeypatch.setattr(B, "footprint_tiles", integer_centres)
+    with pytest.raises(AssertionError):
+        TB.test_footprint_matches_pixel_bruteforce()
+
+
+def test_planted_csi_mean_mistake_fails_its_pin(monkeypatch):
+    orig = CS.csi_head
+    # the spatial sum instead of the mean of Eq. 2
+    monkeypatch.setattr(CS, "csi_head", lambda z, H, W: orig(z, H, W) * (H * W))
+    with pytest.raises(AssertionError):
+        TC.test_csi_head_closed_forms()
+
+
+def test_planted_confidence_offset_mistake_fails_its_pin(monkeypatch):
+    # C = exp(g) without the offset that keeps it above 1
+    monkeypatch.setattr(CF, "confidence", lambda pos, w: torch.exp(CF.network(pos, *w)))
+    with pytest.raises(AssertionError):
+        TCF.test_confidence_exceeds_one()
