@@ -962,7 +962,10 @@ def run_serve(args):
 
 
 def cpu_baseline(sample_pixels, seed=0, threads=0, sc=None, mlp=None, tx=None):
-    """FP64 oracle, fwd + bwd, on a seeded pixel sample of the same workload."""
+    """FP64 oracle, fwd + bwd, on a seeded pixel sample of the same workload, on `threads`
+    host threads (0: every core), both for its C renderer and its PyTorch CPU parts."""
+    import torch
+
     from oracle import pipeline as opl
     from oracle import render as orender
     from paper_2511_22793_gb300 import synth
@@ -978,14 +981,19 @@ def cpu_baseline(sample_pixels, seed=0, threads=0, sc=None, mlp=None, tx=None):
     rng = np.random.default_rng(seed)
     pix = np.sort(rng.choice(H * W, size=sample_pixels, replace=False)).astype(np.int32)
     view, band = synth.View(H=H, W=W), synth.Band(K=K, f_c=wl["f_c"], df=wl["df"])
-    # unit count of the sample (untimed): Gaussians composited per pixel x K
-    counted = opl.forward(sc, mlp, view, band, tx[:1], pixels=pix, threads=threads)
-    units = int(counted["n_used"].sum()) * K
-    target = np.zeros((1, sample_pixels, K), dtype=np.complex128)
-    t0 = time.perf_counter()
-    opl.loss_and_grad(sc, mlp, view, band, tx[:1], target, pixels=pix, threads=threads)
-    dt = time.perf_counter() - t0
     cores = threads if threads > 0 else (os.cpu_count() or 1)
+    torch_threads = torch.get_num_threads()
+    torch.set_num_threads(cores)
+    try:
+        # unit count of the sample (untimed): Gaussians composited per pixel x K
+        counted = opl.forward(sc, mlp, view, band, tx[:1], pixels=pix, threads=cores)
+        units = int(counted["n_used"].sum()) * K
+        target = np.zeros((1, sample_pixels, K), dtype=np.complex128)
+        t0 = time.perf_counter()
+        opl.loss_and_grad(sc, mlp, view, band, tx[:1], target, pixels=pix, threads=cores)
+        dt = time.perf_counter() - t0
+    finally:
+        torch.set_num_threads(torch_threads)
     what = "the full %dx%d image" % (W, H) if sample_pixels == H * W else \
         "%d seeded pixels of the %dx%d image" % (sample_pixels, W, H)
     return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -1092,6 +1100,11 @@ def main():
             out["cpu_baseline"] = cpu_baseline(args.cpu_sample, sc=sc, mlp=mlp, tx=tx)
             out["cpu_baseline"].pop("units", None)
             out["cpu_baseline"]["seconds"] = round(out["cpu_baseline"]["seconds"], 3)
+            # the same oracle on one host thread, on a smaller sample
+            one = cpu_baseline(min(args.cpu_sample, 1024), seed=1, threads=1, sc=sc, mlp=mlp, tx=tx)
+            out["cpu_baseline"]["single_thread"] = {"value": one["value"], "unit": UNIT, "cores": 1,
+                                                    "sample": one["sample"],
+                                                    "seconds": round(one["seconds"], 3)}
         else:
             out["cpu_baseline"] = None
         print(json.dumps(out))
