@@ -107,6 +107,61 @@ def test_spectrum_loss_workspace_and_arguments(L):
                                   None) == G.GSPARC_ERR_INVALID
 
 
+def test_scheduled_backward_workspace_and_arguments(L):
+    """Scheduled backward: workspace = 16 B header + per-(transmitter, tile) walks (rounded to
+    16 B) + two 16 B items per (transmitter, tile, 64-subcarrier strip); missing or misaligned
+    buffers and a too-small workspace are rejected on the host."""
+    v = G.make_view(90, 360)
+    T = 23 * 6
+    for B, K in [(1, 64), (3, 64), (2, 128), (1, 200)]:
+        strips = 1 if K <= 64 else (K + 63) // 64
+        walks = (B * T * 4 + 15) // 16 * 16
+        assert G.gsparc_render_bwd_tc_workspace(v, G.make_band(K), B) == 16 + walks + 2 * B * T * strips * 16
+    out = ctypes.c_size_t(0)
+    band = G.make_band(64)
+    assert L.gsparc_render_bwd_tc_workspace(ctypes.byref(v), ctypes.byref(band), 0, ctypes.byref(out)) == \
+        G.GSPARC_ERR_INVALID
+    bad_band = G.make_band(0)
+    assert L.gsparc_render_bwd_tc_workspace(ctypes.byref(v), ctypes.byref(bad_band), 1, ctypes.byref(out)) == \
+        G.GSPARC_ERR_INVALID
+    need = G.gsparc_render_bwd_tc_workspace(v, band, 1)
+    vp = ctypes.c_void_p
+
+    def call(ws=vp(4096), ws_bytes=need, d_attr=vp(4096), d_spectrum=vp(4096)):
+        return L.gsparc_render_bwd_tc_balanced(ctypes.byref(v), ctypes.byref(band), 1, 10, vp(4096), vp(4096),
+                                               vp(4096), vp(4096), vp(4096), None, None, vp(4096), vp(4096),
+                                               d_spectrum, 0, ws, ws_bytes, d_attr, vp(4096), None)
+
+    assert call(ws=None) == G.GSPARC_ERR_INVALID
+    assert call(ws_bytes=need - 16) == G.GSPARC_ERR_INVALID
+    assert call(d_attr=vp(4104)) == G.GSPARC_ERR_INVALID
+    assert call(ws=vp(4104)) == G.GSPARC_ERR_INVALID
+    assert call(d_spectrum=vp(4100)) == G.GSPARC_ERR_INVALID
+    assert call(d_spectrum=None) == G.GSPARC_ERR_INVALID
+
+
+def test_csi_and_fused_loss_arguments(L):
+    """CSI head, channel loss and head backward reject bad sizes and misaligned complex buffers;
+    the fused forward + L2 rejects a missing target, loss or gradient buffer."""
+    vp = ctypes.c_void_p
+    f32 = ctypes.c_float
+    assert L.gsparc_csi_head(0, 4, 100, vp(256), f32(0.01), vp(256), None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_csi_head(256, 256, 100, vp(256), f32(0.01), vp(256), None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_csi_head(1, 4, 100, None, f32(0.01), vp(256), None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_csi_head(1, 4, 100, vp(260), f32(0.01), vp(256), None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_csi_loss(1, 4, vp(256), None, vp(256), None, None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_csi_loss(1, 4, vp(256), vp(256), vp(256), vp(252), None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_csi_head_bwd(1, 4, 100, vp(256), f32(0.01), None, None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_csi_head_bwd(1, 4, -1, vp(256), f32(0.01), vp(256), None) == G.GSPARC_ERR_INVALID
+    v = G.make_view(90, 360)
+    band = G.make_band(64)
+    for target, loss, grad in [(None, vp(256), vp(256)), (vp(256), None, vp(256)), (vp(256), vp(256), None),
+                               (vp(260), vp(256), vp(256))]:
+        assert L.gsparc_render_fwd_l2_tc(ctypes.byref(v), ctypes.byref(band), 1, 10, vp(256), vp(256), vp(256),
+                                         vp(256), target, loss, grad, vp(256), vp(256), vp(256), None, None,
+                                         None, None) == G.GSPARC_ERR_INVALID
+
+
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(G, "_lib", None)
     monkeypatch.setattr(G, "LIB_PATH", str(tmp_path / "missing.so"))
