@@ -21,6 +21,8 @@ Contents, each following the passage of the paper it cites:
   csi.py          spatial-mean CSI head (Eq. 2), channel loss (Eq. 3), NMSE
   spectrum_loss.py  magnitude-spectrum loss L1 + SSIM (Eq. 4) and its gradient
   confidence.py   confidence-weighted objective C L_task - alpha log C (Eq. 5)
+  densify.py      adaptive density control: clone, split, prune, opacity reset
+                  (Algorithm 1, densification branch)
   pipeline.py     the whole forward pass, the L2 or channel loss and the full
                   gradient
   adam.py         the Adam update (Algorithm 1, Adam step)

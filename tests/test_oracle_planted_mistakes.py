@@ -11,6 +11,7 @@ import test_oracle_attributes as TA
 import test_oracle_binsort as TB
 import test_oracle_confidence as TCF
 import test_oracle_csi as TC
+import test_oracle_densify as TD
 import test_oracle_emission as TE
 import test_oracle_grad as TG
 import test_oracle_projection as TP
@@ -21,6 +22,7 @@ from oracle import attributes as A
 from oracle import binsort as B
 from oracle import confidence as CF
 from oracle import csi as CS
+from oracle import densify as DN
 from oracle import emission as E
 from oracle import projection as P
 from oracle import render as R
@@ -121,3 +123,31 @@ def test_planted_confidence_offset_mistake_fails_its_pin(monkeypatch):
     monkeypatch.setattr(CF, "confidence", lambda pos, w: torch.exp(CF.network(pos, *w)))
     with pytest.raises(AssertionError):
         TCF.test_confidence_exceeds_one()
+
+
+def _patched_module(monkeypatch, mod, old, new):
+    """A copy of an oracle module with one line changed, loaded as a sibling in the package."""
+    import sys
+    import types
+
+    src = open(mod.__file__).read()
+    assert src.count(old) == 1, "the line to plant the mistake in is gone"
+    planted = types.ModuleType(mod.__name__ + "_planted")
+    planted.__package__ = "oracle"
+    planted.__file__ = mod.__file__
+    monkeypatch.setitem(sys.modules, planted.__name__, planted)
+    exec(compile(src.replace(old, new), mod.__file__, "exec"), planted.__dict__)
+    return planted
+
+
+@pytest.mark.parametrize("old,new,pin", [
+    # children scaled by 1/N instead of 1/(0.8 N)
+    ("math.log(0.8 * th.n_split)", "math.log(th.n_split)", lambda: TD.test_split_scale_rule(2)),
+    # children offset by diag(s) R xi instead of R diag(s) xi
+    ("R[i] @ (scale[i] * xi[k, c])", "scale[i] * (R[i] @ xi[k, c])",
+     TD.test_split_children_at_mahalanobis_distance_xi),
+])
+def test_planted_densify_mistake_fails_its_pin(monkeypatch, old, new, pin):
+    monkeypatch.setattr(TD, "D", _patched_module(monkeypatch, DN, old, new))
+    with pytest.raises(AssertionError):
+        pin()
