@@ -490,6 +490,26 @@ int gsparc_render_csi_tc(const gsparc_view* view, const gsparc_band* band, int32
                          uint32_t* n_contrib, uint32_t* n_used, void* stream);
 
 /*
+ * Confidence-weighted objective (Eq. 5, Sec. 4.2 confidence-weighted
+ * optimisation): a network g: R^3 -> R with one ReLU hidden layer maps each
+ * sample's query position to the confidence C_b = 1 + exp(g(pos_b)) > 1, and
+ * the objective is mean_b (C_b L_b - alpha ln C_b) (alpha = 0.3 and 32 hidden
+ * units in the paper).  One call writes the objective, C and dObj/dL_b, and
+ * accumulates the weight gradients.
+ *   B >= 0 samples (B = 0: objective 0, nothing else written); hidden 1..32;
+ *   pos [B,3], task_loss [B] in; weights: W1 [3,hidden] (input-major), b1
+ *   [hidden], W2 [hidden], b2 [1] = 5 hidden + 1 floats; alpha >= 0;
+ *   objective [1] out (overwritten); confidence [B] out, d_task_loss [B] out
+ *   (C_b / B), both overwritten, may be NULL; d_weights [5 hidden + 1]
+ *   accumulated (+=), may be NULL.
+ * One block of 8 warps with a fixed summation order: results are the same
+ * from run to run.
+ */
+int gsparc_confidence(int32_t B, int32_t hidden, const float* pos, const float* task_loss,
+                      const float* weights, float alpha, float* confidence, float* objective,
+                      float* d_task_loss, float* d_weights, void* stream);
+
+/*
  * Adam step (Algorithm 1 "Adam"): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
  * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps), in place over
  * n FP32 elements.  step >= 1.

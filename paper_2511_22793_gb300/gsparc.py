@@ -37,7 +37,7 @@ EXPORTS = [
     "gsparc_render_bwd_tc", "gsparc_render_bwd_tc_workspace", "gsparc_render_bwd_tc_balanced",
     "gsparc_l2_loss", "gsparc_csi_head", "gsparc_csi_loss", "gsparc_csi_head_bwd",
     "gsparc_spectrum_loss_workspace", "gsparc_spectrum_loss",
-    "gsparc_render_csi_tc", "gsparc_render_fwd_l2_tc", "gsparc_adam", "gsparc_check", "gsparc_strerror",
+    "gsparc_render_csi_tc", "gsparc_render_fwd_l2_tc", "gsparc_confidence", "gsparc_adam", "gsparc_check", "gsparc_strerror",
 ]
 
 
@@ -120,6 +120,7 @@ def lib():
             "gsparc_render_bwd_tc_balanced": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp,
                                                              vp, vp, vp, vp, vp, i32, vp, ctypes.c_size_t, vp,
                                                              vp, vp]),
+            "gsparc_confidence": (ctypes.c_int, [i32, i32, vp, vp, vp, f32, vp, vp, vp, vp, vp]),
             "gsparc_adam": (ctypes.c_int, [i64, vp, vp, vp, vp, f32, f32, f32, f32, i32, vp]),
             "gsparc_check": (ctypes.c_int, [vp, vp]),
             "gsparc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -343,6 +344,15 @@ def gsparc_spectrum_loss(spectrum, target, ws, loss, d_spectrum=None, lam=0.2, s
     B, K, H, W = (int(v) for v in target.shape)
     _call("gsparc_spectrum_loss", B, K, H, W, _p(spectrum), _p(target), float(lam), _p(ws),
           ws.numel() * ws.element_size(), _p(loss), _p(d_spectrum), _stream(stream))
+
+
+def gsparc_confidence(pos, task_loss, weights, hidden, objective, confidence=None, d_task_loss=None,
+                      d_weights=None, alpha=0.3, stream=None):
+    """Eq. 5: pos [B,3], task_loss [B], weights [5 hidden + 1] -> objective [1] = mean (C L - alpha
+    ln C), C = 1 + exp(g(pos)) [B], dObj/dL [B] (written) and the weight gradients (accumulated)."""
+    B = int(task_loss.shape[0])
+    _call("gsparc_confidence", B, int(hidden), _p(pos), _p(task_loss), _p(weights), float(alpha),
+          _p(confidence), _p(objective), _p(d_task_loss), _p(d_weights), _stream(stream))
 
 
 def gsparc_csi_head(spectrum, csi, scale, stream=None):

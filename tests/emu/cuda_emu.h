@@ -1,0 +1,129 @@
+// Test-only host shim that runs a CUDA kernel's source on CPU threads, one std::thread per
+// CUDA thread, blocks one after another.  It exists to check the logic of the library's plain
+// (non-tensor-core) kernels on a machine without a GPU: index arithmetic, warp shuffles,
+// block barriers and the order of sums.  It is not a CUDA implementation: no memory model
+// beyond sequential consistency, no timing, and nothing of the library links against it.
+//
+// Semantics kept from CUDA: __syncthreads() waits for every thread of the block that has not
+// exited (exited threads leave the barrier's count); __shfl_*_sync exchange values among the
+// 32 lanes of a warp and record a violation when a lane of the warp has already exited;
+// atomics are atomic.  `__shared__` variables are function statics, valid because one block
+// runs at a time.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <atomic>
+#include <barrier>
+#include <memory>
+#include <thread>
+#include <vector>
+
+struct emu_dim3 {
+    unsigned x = 1, y = 1, z = 1;
+};
+
+inline thread_local emu_dim3 threadIdx, blockIdx;
+inline emu_dim3 blockDim, gridDim;
+
+#define __global__
+#define __device__
+#define __host__
+#define __forceinline__ inline
+#define __launch_bounds__(...)
+#define __shared__ static
+
+struct EmuWarp {
+    std::unique_ptr<std::barrier<>> bar;
+    std::atomic<int> alive{0};
+    uint64_t slot[32];
+};
+
+struct EmuBlockState {
+    std::unique_ptr<std::barrier<>> bar;
+    std::vector<std::unique_ptr<EmuWarp>> warps;
+};
+
+inline EmuBlockState* g_emu_block = nullptr;
+inline std::atomic<int> g_emu_violations{0};
+
+inline void __syncthreads() { g_emu_block->bar->arrive_and_wait(); }
+
+template <typename T, typename F>
+inline T emu_exchange(T v, F src_of) {
+    static_assert(sizeof(T) <= 8, "shuffle of a value wider than 64 bits");
+    const int t = (int)threadIdx.x, w = t / 32, l = t % 32;
+    EmuWarp& wp = *g_emu_block->warps[w];
+    if (wp.alive.load() != 32) g_emu_violations.fetch_add(1);
+    uint64_t bits = 0;
+    memcpy(&bits, &v, sizeof(T));
+    wp.slot[l] = bits;
+    wp.bar->arrive_and_wait();
+    const int src = src_of(l);
+    uint64_t got = wp.slot[(src >= 0 && src < 32) ? src : l];
+    wp.bar->arrive_and_wait();
+    T r;
+    memcpy(&r, &got, sizeof(T));
+    return r;
+}
+
+template <typename T>
+inline T __shfl_xor_sync(unsigned, T v, int mask) {
+    return emu_exchange(v, [mask](int l) { return l ^ mask; });
+}
+template <typename T>
+inline T __shfl_sync(unsigned, T v, int src) {
+    return emu_exchange(v, [src](int) { return src & 31; });
+}
+template <typename T>
+inline T __shfl_up_sync(unsigned, T v, int d) {
+    return emu_exchange(v, [d](int l) { return l >= d ? l - d : l; });
+}
+template <typename T>
+inline T __shfl_down_sync(unsigned, T v, int d) {
+    return emu_exchange(v, [d](int l) { return l + d < 32 ? l + d : l; });
+}
+
+template <typename T>
+inline T atomicAdd(T* p, T v) {
+    return std::atomic_ref<T>(*p).fetch_add(v);
+}
+
+// Runs kernel(args...) over grid x block (1D blocks of whole warps, up to a 2D grid).
+template <typename K, typename... A>
+inline void emu_launch(emu_dim3 grid, unsigned threads, K kernel, A... args) {
+    if (threads % 32 != 0) {
+        g_emu_violations.fetch_add(1);
+        return;
+    }
+    gridDim = grid;
+    blockDim = emu_dim3{threads, 1, 1};
+    for (unsigned by = 0; by < grid.y; ++by)
+        for (unsigned bx = 0; bx < grid.x; ++bx) {
+            EmuBlockState st;
+            st.bar = std::make_unique<std::barrier<>>((std::ptrdiff_t)threads);
+            for (unsigned w = 0; w < threads / 32; ++w) {
+                auto wp = std::make_unique<EmuWarp>();
+                wp->bar = std::make_unique<std::barrier<>>(32);
+                wp->alive = 32;
+                st.warps.push_back(std::move(wp));
+            }
+            g_emu_block = &st;
+            std::vector<std::thread> pool;
+            pool.reserve(threads);
+            for (unsigned t = 0; t < threads; ++t)
+                pool.emplace_back([&, t, bx, by] {
+                    threadIdx = emu_dim3{t, 0, 0};
+                    blockIdx = emu_dim3{bx, by, 0};
+                    kernel(args...);
+                    EmuWarp& wp = *st.warps[t / 32];
+                    wp.alive.fetch_sub(1);
+                    wp.bar->arrive_and_drop();
+                    st.bar->arrive_and_drop();
+                });
+            for (auto& th : pool) th.join();
+            g_emu_block = nullptr;
+        }
+}

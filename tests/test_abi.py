@@ -162,6 +162,23 @@ def test_csi_and_fused_loss_arguments(L):
                                          None, None) == G.GSPARC_ERR_INVALID
 
 
+def test_confidence_arguments(L):
+    """Confidence objective: widths outside 1..32, a negative batch, missing weights, objective,
+    positions or losses, and a negative or NaN alpha are rejected on the host."""
+    vp = ctypes.c_void_p
+    f32 = ctypes.c_float
+    ok = dict(B=4, hidden=32, pos=vp(256), loss=vp(256), w=vp(256), alpha=f32(0.3), obj=vp(256))
+
+    def call(**kw):
+        a = dict(ok, **kw)
+        return L.gsparc_confidence(a["B"], a["hidden"], a["pos"], a["loss"], a["w"], a["alpha"], None,
+                                   a["obj"], None, None, None)
+
+    for bad in (dict(hidden=0), dict(hidden=33), dict(B=-1), dict(w=None), dict(obj=None), dict(pos=None),
+                dict(loss=None), dict(alpha=f32(-0.1)), dict(alpha=f32(float("nan")))):
+        assert call(**bad) == G.GSPARC_ERR_INVALID, bad
+
+
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(G, "_lib", None)
     monkeypatch.setattr(G, "LIB_PATH", str(tmp_path / "missing.so"))
