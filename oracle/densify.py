@@ -12,11 +12,13 @@ footprint above r_max are pruned; every Delta_reset steps every opacity becomes 
 
 Readings (the paper gives none of the thresholds and leaves the details open):
   - the statistic is the mean of ||dL/dmu_i|| over the steps since the last densification in
-    which Gaussian i was visible (in some tile list); a Gaussian never visible is not a candidate;
+    which Gaussian i was visible, i.e. its projection was not culled (footprint radius > 0); a
+    Gaussian never visible is not a candidate;
   - max(Sigma_i) is the largest per-axis scale exp(l_i); the scale rule divides the per-axis
     scales by 0.8 N, i.e. log-scales minus ln(0.8 N);
   - a child of a split sits at mu_i + R_i diag(exp(l_i)) xi, xi ~ N(0, I_3) drawn from the
-    parent's own distribution; the draws are inputs [n_split, N, 3]; a child copies the parent's
+    parent's own distribution; the draws are inputs [N, n_split, 3], row i serving Gaussian i
+    if it splits (a row per Gaussian keeps the draws independent of the decisions); a child copies the parent's
     rotation, opacity and per-Gaussian payload (latent or emission buffer); the parent goes;
   - a clone is an exact copy;
   - output order: parents in index order, each emitting in place its kept self, then its
@@ -85,25 +87,23 @@ def decide(norm_sum, count, log_scales, th: Thresholds):
 def densify_and_prune(g, radius, action, xi, th: Thresholds):
     """One densification of the Gaussian set g (dict of float64 arrays: means [N,3], log_scales
     [N,3], quats [N,4], opacity_logit [N], payload [N,P]) given each Gaussian's last footprint
-    radius [N] in pixels, its action from `decide`, and the split draws xi [n_split, N_children, 3]
-    (one row per split parent, in index order).  Returns the new set and, for each output, the
-    index of its parent."""
+    radius [N] in pixels, its action from `decide`, and the split draws xi [N, n_split, 3] (row i
+    used if Gaussian i splits).  Returns the new set and, for each output, the index of its
+    parent."""
     n = g["means"].shape[0]
     R = P.quat_to_rotmat(torch.tensor(g["quats"], dtype=torch.float64)).numpy() if n else np.zeros((0, 3, 3))
     scale = np.exp(g["log_scales"])
     rows, parent, fresh = [], [], []
-    k = 0
     for i in range(n):
         one = {key: g[key][i] for key in g}
         if action[i] == 2:
             for c in range(th.n_split):
                 child = dict(one)
-                child["means"] = g["means"][i] + R[i] @ (scale[i] * xi[k, c])
+                child["means"] = g["means"][i] + R[i] @ (scale[i] * xi[i, c])
                 child["log_scales"] = g["log_scales"][i] - math.log(0.8 * th.n_split)
                 rows.append(child)
                 parent.append(i)
                 fresh.append(True)
-            k += 1
             continue
         rows.append(one)
         parent.append(i)

@@ -45,7 +45,7 @@ def test_statistics_and_decision_by_hand():
 def test_nothing_qualifies_is_the_identity():
     g = _set(50, 1)
     th = D.Thresholds(sigma_min=0.0, r_max=math.inf)
-    out, parent = D.densify_and_prune(g, np.full(50, 7.0), np.zeros(50, dtype=int), np.zeros((0, 2, 3)), th)
+    out, parent = D.densify_and_prune(g, np.full(50, 7.0), np.zeros(50, dtype=int), np.zeros((50, 2, 3)), th)
     assert list(parent) == list(range(50))
     for k in g:
         assert np.array_equal(out[k], g[k]), k
@@ -54,7 +54,7 @@ def test_nothing_qualifies_is_the_identity():
 def test_clone_by_hand():
     g = _set(3, 2)
     g["opacity_logit"][:] = 0.0
-    out, parent = D.densify_and_prune(g, np.zeros(3), np.array([0, 1, 0]), np.zeros((0, 2, 3)), D.Thresholds())
+    out, parent = D.densify_and_prune(g, np.zeros(3), np.array([0, 1, 0]), np.zeros((3, 2, 3)), D.Thresholds())
     assert list(parent) == [0, 1, 1, 2]
     for k in g:
         assert np.array_equal(out[k][[0, 1, 3]], g[k]) and np.array_equal(out[k][2], g[k][1]), k
@@ -67,20 +67,18 @@ def test_split_children_against_an_independent_rotation():
     g["opacity_logit"][:] = 1.0
     act = np.array([2, 0, 2, 2, 0, 2])
     th = D.Thresholds(n_split=3)
-    xi = np.random.default_rng(4).normal(size=(4, 3, 3))
+    xi = np.random.default_rng(4).normal(size=(6, 3, 3))
     out, parent = D.densify_and_prune(g, np.zeros(6), act, xi, th)
     assert list(parent) == [0, 0, 0, 1, 2, 2, 2, 3, 3, 3, 4, 5, 5, 5]
-    k = 0
     for i in np.flatnonzero(act == 2):
         w, x, y, z = g["quats"][i]
         R = Rot.from_quat([x, y, z, w]).as_matrix()
         rows = np.flatnonzero(parent == i)
         for c, j in enumerate(rows):
-            expect = g["means"][i] + R @ (np.exp(g["log_scales"][i]) * xi[k, c])
+            expect = g["means"][i] + R @ (np.exp(g["log_scales"][i]) * xi[i, c])
             assert np.allclose(out["means"][j], expect, rtol=0, atol=1e-12)
             for key in ("quats", "opacity_logit", "payload"):
                 assert np.array_equal(out[key][j], g[key][i])
-        k += 1
 
 
 def test_split_children_at_mahalanobis_distance_xi():
@@ -104,7 +102,7 @@ def test_split_scale_rule(n_split):
     parent's mean."""
     g = _set(4, 7)
     g["opacity_logit"][:] = 0.0
-    out, parent = D.densify_and_prune(g, np.zeros(4), np.array([0, 2, 0, 0]), np.zeros((1, n_split, 3)),
+    out, parent = D.densify_and_prune(g, np.zeros(4), np.array([0, 2, 0, 0]), np.zeros((4, n_split, 3)),
                                       D.Thresholds(n_split=n_split))
     rows = np.flatnonzero(parent == 1)
     assert len(rows) == n_split and out["means"].shape[0] == 3 + n_split
@@ -123,7 +121,7 @@ def test_pruning_boundaries():
     g["opacity_logit"][:] = [lg - 1e-6, lg + 1e-6, 2.0, 2.0, 2.0, lg - 1.0]
     radius = np.array([0.0, 0.0, 20.0, 20.0 + 1e-9, 25.0, 0.0])
     act = np.array([0, 0, 0, 0, 1, 1])
-    out, parent = D.densify_and_prune(g, radius, act, np.zeros((0, 2, 3)), D.Thresholds(sigma_min=smin, r_max=20.0))
+    out, parent = D.densify_and_prune(g, radius, act, np.zeros((6, 2, 3)), D.Thresholds(sigma_min=smin, r_max=20.0))
     # 0 faint; 1 kept; 2 at r_max kept; 3 wide; 4 wide but its clone stays; 5 and its clone faint
     assert list(parent) == [1, 2, 4]
     assert np.array_equal(out["means"][2], g["means"][4])
@@ -147,7 +145,7 @@ def test_output_count_on_a_random_scene():
     act = D.decide(s, c, g["log_scales"], th)
     assert (act == 1).any() and (act == 2).any() and (act == 0).any()
     radius = rng.uniform(0.0, 20.0, size=n)
-    xi = rng.normal(size=(int((act == 2).sum()), th.n_split, 3))
+    xi = rng.normal(size=(n, th.n_split, 3))
     out, parent = D.densify_and_prune(g, radius, act, xi, th)
     sig = 1.0 / (1.0 + np.exp(-g["opacity_logit"]))
     faint = sig < th.sigma_min

@@ -144,7 +144,7 @@ def _patched_module(monkeypatch, mod, old, new):
     # children scaled by 1/N instead of 1/(0.8 N)
     ("math.log(0.8 * th.n_split)", "math.log(th.n_split)", lambda: TD.test_split_scale_rule(2)),
     # children offset by diag(s) R xi instead of R diag(s) xi
-    ("R[i] @ (scale[i] * xi[k, c])", "scale[i] * (R[i] @ xi[k, c])",
+    ("R[i] @ (scale[i] * xi[i, c])", "scale[i] * (R[i] @ xi[i, c])",
      TD.test_split_children_at_mahalanobis_distance_xi),
 ])
 def test_planted_densify_mistake_fails_its_pin(monkeypatch, old, new, pin):
