@@ -510,6 +510,75 @@ int gsparc_confidence(int32_t B, int32_t hidden, const float* pos, const float* 
                       float* d_task_loss, float* d_weights, void* stream);
 
 /*
+ * Adaptive density control (Algorithm 1, densification branch; Sec. 4.2
+ * "Densification, Pruning, and Implementation").  The paper gives no
+ * thresholds; the fields hold them (proposed values in brackets, 3D Gaussian
+ * Splatting conventions where it has one).
+ */
+typedef struct gsparc_densify_params {
+    float tau_grad;    /* mean ||dL/dmu|| at or above which a Gaussian grows [2e-4] */
+    float clone_scale; /* eps * r_scene: a growing Gaussian whose largest per-axis
+                          scale (m) is at most this is cloned, else split [0.01 * 5 sqrt 3] */
+    float sigma_min;   /* opacity below which a Gaussian is pruned [0.005]           */
+    float r_max;       /* footprint radius (px) above which a Gaussian is pruned [20] */
+    int32_t n_split;   /* children of a split, 1..8 [2]                               */
+} gsparc_densify_params;
+
+/*
+ * Statistic of the densification: every Gaussian whose projection record (as
+ * written by gsparc_project: [N,8], ext_x and ext_y at offsets 2 and 3, -1 when
+ * culled) has a footprint radius max(ext_x, ext_y) > 0 adds ||d_means[i]|| to
+ * norm_sum[i] and 1 to count[i].
+ *   proj [N,8], d_means [N,3] in; norm_sum [N] FP32 and count [N] u32
+ *   accumulated (zero them after each densification).  N * 8 < 2^31.
+ */
+int gsparc_densify_accumulate(int32_t N, const float* proj, const float* d_means, float* norm_sum,
+                              uint32_t* count, void* stream);
+
+/* Workspace of gsparc_densify for N Gaussians: 4 B per 256 Gaussians, rounded up to 256 B. */
+int gsparc_densify_workspace(int32_t N, size_t* ws_bytes);
+
+/*
+ * One densification: grow = count > 0 and norm_sum / count >= tau_grad;
+ * a growing Gaussian with exp(max log-scale) <= clone_scale is cloned (an
+ * exact copy), any other growing one is split into n_split children at
+ * mu + R diag(exp(l)) xi[i, c] with log-scales l - ln(0.8 n_split), the rest
+ * copied, the parent removed; then every output whose opacity sigmoid(logit)
+ * is below sigma_min goes, and every Gaussian that existed before this call
+ * whose footprint radius max(ext_x, ext_y) in proj exceeds r_max goes (clones
+ * and children stay).  Outputs keep parent-index order, each parent's rows in
+ * place: itself, then its clone; or its children in order.
+ *   Inputs [N,...]: means [N,3], log_scales [N,3], quats [N,4] (w,x,y,z),
+ *   opacity_logit [N], payload [N,P] (per-Gaussian values copied along, e.g.
+ *   latents or emission weights; may be NULL when P = 0), proj [N,8],
+ *   norm_sum [N], count [N], xi [N, n_split, 3] standard-normal draws (row i
+ *   serves Gaussian i if it splits).
+ *   Outputs, `capacity` rows each, must not alias the inputs: out_means,
+ *   out_log_scales, out_quats, out_opacity_logit, out_payload [capacity,P],
+ *   out_parent [capacity] (the input index each row came from); n_out [1]
+ *   (device u32) = the number of rows the densification produces.  Rows past
+ *   the capacity are not written and the status word gets
+ *   GSPARC_ERR_CAPACITY.  ws: gsparc_densify_workspace bytes, 4-byte aligned
+ *   (GSPARC_ERR_WORKSPACE when smaller).
+ * Three launches (count per block, one block scanning the block counts,
+ * scatter); decisions in FP32; the result is the same from run to run.
+ */
+int gsparc_densify(int32_t N, int32_t P, const float* means, const float* log_scales, const float* quats,
+                   const float* opacity_logit, const float* payload, const float* proj,
+                   const float* norm_sum, const uint32_t* count, const float* xi,
+                   const gsparc_densify_params* params, int32_t capacity, void* ws, size_t ws_bytes,
+                   float* out_means, float* out_log_scales, float* out_quats, float* out_opacity_logit,
+                   float* out_payload, uint32_t* out_parent, uint32_t* n_out, int32_t* d_status,
+                   void* stream);
+
+/*
+ * Periodic opacity reset (Algorithm 1): sigma <- min(sigma, max_opacity) for
+ * every Gaussian, on the logits: logit <- min(logit, ln(m / (1 - m))), in
+ * place.  0 < max_opacity < 1 (0.01 in the paper).
+ */
+int gsparc_opacity_reset(int32_t N, float max_opacity, float* opacity_logit, void* stream);
+
+/*
  * Adam step (Algorithm 1 "Adam"): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
  * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps), in place over
  * n FP32 elements.  step >= 1.

@@ -120,9 +120,8 @@ def densify_and_prune(g, radius, action, xi, th: Thresholds):
         keep.append(not (too_faint or too_wide))
     out = {}
     for key in g:
-        shape = g[key].shape[1:]
-        out[key] = np.array([row[key] for j, row in enumerate(rows) if keep[j]], dtype=np.float64).reshape(
-            (-1,) + shape)
+        kept = [row[key] for j, row in enumerate(rows) if keep[j]]
+        out[key] = np.array(kept, dtype=np.float64).reshape((len(kept),) + g[key].shape[1:])
     return out, np.array([p for j, p in enumerate(parent) if keep[j]], dtype=np.int64)
 
 

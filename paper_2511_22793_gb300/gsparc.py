@@ -37,7 +37,8 @@ EXPORTS = [
     "gsparc_render_bwd_tc", "gsparc_render_bwd_tc_workspace", "gsparc_render_bwd_tc_balanced",
     "gsparc_l2_loss", "gsparc_csi_head", "gsparc_csi_loss", "gsparc_csi_head_bwd",
     "gsparc_spectrum_loss_workspace", "gsparc_spectrum_loss",
-    "gsparc_render_csi_tc", "gsparc_render_fwd_l2_tc", "gsparc_confidence", "gsparc_adam", "gsparc_check", "gsparc_strerror",
+    "gsparc_render_csi_tc", "gsparc_render_fwd_l2_tc", "gsparc_confidence", "gsparc_densify_accumulate",
+    "gsparc_densify_workspace", "gsparc_densify", "gsparc_opacity_reset", "gsparc_adam", "gsparc_check", "gsparc_strerror",
 ]
 
 
@@ -60,6 +61,11 @@ class Band(ctypes.Structure):
 class MLP(ctypes.Structure):
     _fields_ = [("hidden", ctypes.c_int32), ("reserved", ctypes.c_int32)] + \
                [(n, ctypes.c_void_p) for n in ("W1", "b1", "W2", "b2", "W3", "b3")]
+
+
+class DensifyParams(ctypes.Structure):
+    _fields_ = [("tau_grad", ctypes.c_float), ("clone_scale", ctypes.c_float), ("sigma_min", ctypes.c_float),
+                ("r_max", ctypes.c_float), ("n_split", ctypes.c_int32)]
 
 
 class MLPGrad(ctypes.Structure):
@@ -121,6 +127,11 @@ def lib():
                                                              vp, vp, vp, vp, vp, i32, vp, ctypes.c_size_t, vp,
                                                              vp, vp]),
             "gsparc_confidence": (ctypes.c_int, [i32, i32, vp, vp, vp, f32, vp, vp, vp, vp, vp]),
+            "gsparc_densify_accumulate": (ctypes.c_int, [i32, vp, vp, vp, vp, vp]),
+            "gsparc_densify_workspace": (ctypes.c_int, [i32, P(ctypes.c_size_t)]),
+            "gsparc_densify": (ctypes.c_int, [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, P(DensifyParams), i32,
+                                              vp, ctypes.c_size_t, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "gsparc_opacity_reset": (ctypes.c_int, [i32, f32, vp, vp]),
             "gsparc_adam": (ctypes.c_int, [i64, vp, vp, vp, vp, f32, f32, f32, f32, i32, vp]),
             "gsparc_check": (ctypes.c_int, [vp, vp]),
             "gsparc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -353,6 +364,46 @@ def gsparc_confidence(pos, task_loss, weights, hidden, objective, confidence=Non
     B = int(task_loss.shape[0])
     _call("gsparc_confidence", B, int(hidden), _p(pos), _p(task_loss), _p(weights), float(alpha),
           _p(confidence), _p(objective), _p(d_task_loss), _p(d_weights), _stream(stream))
+
+
+def densify_params(tau_grad=2e-4, clone_scale=0.01 * 5.0 * 3.0 ** 0.5, sigma_min=0.005, r_max=20.0,
+                   n_split=2) -> DensifyParams:
+    p = DensifyParams()
+    p.tau_grad, p.clone_scale, p.sigma_min, p.r_max = float(tau_grad), float(clone_scale), float(sigma_min), \
+        float(r_max)
+    p.n_split = int(n_split)
+    return p
+
+
+def gsparc_densify_accumulate(proj, d_means, norm_sum, count, stream=None):
+    """Adds ||dL/dmu|| and 1 for every Gaussian whose projection record [N,8] was not culled."""
+    _call("gsparc_densify_accumulate", int(norm_sum.shape[0]), _p(proj), _p(d_means), _p(norm_sum), _p(count),
+          _stream(stream))
+
+
+def gsparc_densify_workspace(N) -> int:
+    out = ctypes.c_size_t(0)
+    _call("gsparc_densify_workspace", int(N), ctypes.byref(out))
+    return int(out.value)
+
+
+def gsparc_densify(means, log_scales, quats, opacity_logit, payload, proj, norm_sum, count, xi, params, ws,
+                   out, n_out, d_status=None, stream=None):
+    """Algorithm 1's clone / split / prune over N Gaussians.  payload [N,P] or None; out: dict of
+    preallocated outputs (means, log_scales, quats, opacity_logit, payload, parent), capacity rows
+    each; n_out [1] int32/uint32 device count of the rows produced."""
+    N = int(means.shape[0])
+    P = 0 if payload is None else int(payload.shape[1])
+    cap = int(out["parent"].shape[0])
+    _call("gsparc_densify", N, P, _p(means), _p(log_scales), _p(quats), _p(opacity_logit), _p(payload), _p(proj),
+          _p(norm_sum), _p(count), _p(xi), ctypes.byref(params), cap, _p(ws), ws.numel() * ws.element_size(),
+          _p(out["means"]), _p(out["log_scales"]), _p(out["quats"]), _p(out["opacity_logit"]),
+          _p(out.get("payload")), _p(out["parent"]), _p(n_out), _p(d_status), _stream(stream))
+
+
+def gsparc_opacity_reset(opacity_logit, max_opacity=0.01, stream=None):
+    _call("gsparc_opacity_reset", int(opacity_logit.numel()), float(max_opacity), _p(opacity_logit),
+          _stream(stream))
 
 
 def gsparc_csi_head(spectrum, csi, scale, stream=None):

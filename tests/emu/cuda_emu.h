@@ -91,6 +91,12 @@ inline T atomicAdd(T* p, T v) {
     return std::atomic_ref<T>(*p).fetch_add(v);
 }
 
+template <typename T>
+inline T atomicCAS(T* p, T cmp, T val) {
+    std::atomic_ref<T>(*p).compare_exchange_strong(cmp, val);
+    return cmp;
+}
+
 // Runs kernel(args...) over grid x block (1D blocks of whole warps, up to a 2D grid).
 template <typename K, typename... A>
 inline void emu_launch(emu_dim3 grid, unsigned threads, K kernel, A... args) {

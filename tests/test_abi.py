@@ -179,6 +179,46 @@ def test_confidence_arguments(L):
         assert call(**bad) == G.GSPARC_ERR_INVALID, bad
 
 
+def test_densify_workspace_and_arguments(L):
+    """Densification: 4 B of workspace per 256 Gaussians (rounded to 256 B); n_split outside 1..8,
+    negative or NaN thresholds, missing inputs or outputs and a small workspace are rejected on the
+    host; the opacity reset wants 0 < max_opacity < 1."""
+    assert G.gsparc_densify_workspace(0) == 0
+    assert G.gsparc_densify_workspace(1) == 256
+    assert G.gsparc_densify_workspace(256 * 64) == 256
+    assert G.gsparc_densify_workspace(256 * 65) == 512
+    vp = ctypes.c_void_p
+    good = G.densify_params()
+    need = G.gsparc_densify_workspace(1000)
+
+    def call(params=good, N=1000, P=4, cap=3000, ws=vp(4096), ws_bytes=need, payload=vp(4096), out_means=vp(4096),
+             xi=vp(4096), n_out=vp(4096)):
+        return L.gsparc_densify(N, P, vp(4096), vp(4096), vp(4096), vp(4096), payload, vp(4096), vp(4096), vp(4096),
+                                xi, ctypes.byref(params), cap, ws, ws_bytes, out_means, vp(4096), vp(4096), vp(4096),
+                                vp(4096), vp(4096), n_out, None, None)
+
+    for field, value in (("n_split", 0), ("n_split", 9), ("tau_grad", -1.0), ("r_max", float("nan")),
+                         ("sigma_min", -0.1), ("clone_scale", float("nan"))):
+        bad = G.densify_params()
+        setattr(bad, field, value)
+        assert call(params=bad) == G.GSPARC_ERR_INVALID, field
+    assert call(N=-1) == G.GSPARC_ERR_INVALID
+    assert call(cap=-1) == G.GSPARC_ERR_INVALID
+    assert call(payload=None) == G.GSPARC_ERR_INVALID
+    assert call(xi=None) == G.GSPARC_ERR_INVALID
+    assert call(out_means=None) == G.GSPARC_ERR_INVALID
+    assert call(n_out=None) == G.GSPARC_ERR_INVALID
+    assert call(ws_bytes=need - 1) == G.GSPARC_ERR_WORKSPACE
+    assert call(ws=None) == G.GSPARC_ERR_WORKSPACE
+    assert call(ws=vp(4098)) == G.GSPARC_ERR_INVALID
+    f32 = ctypes.c_float
+    for m in (0.0, 1.0, -0.5, float("nan")):
+        assert L.gsparc_opacity_reset(10, f32(m), vp(4096), None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_opacity_reset(10, f32(0.01), None, None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_densify_accumulate(10, vp(4096), None, vp(4096), vp(4096), None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_densify_accumulate(-1, vp(4096), vp(4096), vp(4096), vp(4096), None) == G.GSPARC_ERR_INVALID
+
+
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(G, "_lib", None)
     monkeypatch.setattr(G, "LIB_PATH", str(tmp_path / "missing.so"))

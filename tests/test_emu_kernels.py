@@ -10,11 +10,13 @@ import subprocess
 import numpy as np
 import pytest
 
-from extras_cases import conf_case, conf_oracle
+from extras_cases import (accumulate_check, conf_case, conf_oracle, dens_case, dens_check, dens_oracle,
+                          reset_check)
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2511_22793_gb300", "csrc")
 EMU = os.path.join(ROOT, "tests", "emu")
+INCLUDE = os.path.join(ROOT, "include")
 
 
 @pytest.fixture(scope="module")
@@ -27,7 +29,7 @@ def emu_bin(tmp_path_factory):
     def build(name):
         exe = out / name
         if not exe.exists():
-            subprocess.run([gxx, "-std=c++20", "-O1", "-pthread", "-I", CSRC, "-I", EMU,
+            subprocess.run([gxx, "-std=c++20", "-O1", "-pthread", "-I", CSRC, "-I", INCLUDE, "-I", EMU,
                             os.path.join(EMU, name + ".cpp"), "-o", str(exe)], check=True)
         return str(exe)
 
@@ -61,3 +63,65 @@ def test_confidence_kernel_logic(emu_bin, tmp_path, B, hidden):
     assert np.allclose(dL, o_dL, rtol=2e-6, atol=0)
     g = dw.astype(np.float64) - dw0
     assert np.linalg.norm(g - o_dw) <= 1e-5 * np.linalg.norm(o_dw)
+
+
+def _dens_run(exe, tmp_path, c, th, cap):
+    N, P = c["payload"].shape
+    n_split = th.n_split
+    lc = float(np.log(0.01 / 0.99))
+    hdr = np.array([N, P, cap, n_split], np.int32).tobytes() + np.array(
+        [th.tau_grad, th.eps * th.r_scene, th.sigma_min, th.r_max, np.log(0.8 * n_split), lc], np.float32).tobytes()
+    body = b"".join(np.ascontiguousarray(c[k]).tobytes() for k in
+                    ("means", "log_scales", "quats", "opacity_logit", "payload", "proj", "norm_sum", "count", "xi",
+                     "d_means"))
+    raw = _run(exe, tmp_path, hdr + body)
+    off = 0
+
+    def take(dtype, n, shape=None):
+        nonlocal off
+        a = np.frombuffer(raw, dtype=dtype, count=n, offset=off)
+        off += 4 * n
+        return a.reshape(shape) if shape else a
+
+    res = {"n_out": int(take(np.uint32, 1)[0]), "status": int(take(np.int32, 1)[0])}
+    res["means"] = take(np.float32, 3 * cap, (cap, 3))
+    res["log_scales"] = take(np.float32, 3 * cap, (cap, 3))
+    res["quats"] = take(np.float32, 4 * cap, (cap, 4))
+    res["opacity_logit"] = take(np.float32, cap)
+    res["payload"] = take(np.float32, cap * P, (cap, P))
+    res["parent"] = take(np.uint32, cap)
+    acc_norm, acc_count, reset = take(np.float32, N), take(np.uint32, N), take(np.float32, N)
+    assert int(take(np.int32, 1)[0]) == 0        # no shim violation
+    return res, acc_norm, acc_count, reset
+
+
+@pytest.mark.parametrize("N,P,n_split,cap_frac,seed", [(3000, 5, 2, 2.0, 0), (3000, 0, 3, 2.0, 1),
+                                                        (257, 16, 2, 0.5, 2), (1, 3, 4, 4.0, 3),
+                                                        (700, 2, 8, 0.0, 4)])
+def test_densify_kernels_logic(emu_bin, tmp_path, N, P, n_split, cap_frac, seed):
+    """Count, scan and scatter passes, the accumulation and the opacity reset, against the
+    oracle: ragged blocks, no payload, a capacity below the row count (and zero), n_split 2-8."""
+    c, th = dens_case(N, P, n_split, seed)
+    o = dens_oracle(c, th)
+    cap = int(cap_frac * N)
+    res, acc_norm, acc_count, reset = _dens_run(emu_bin("densify_emu"), tmp_path, c, th, cap)
+    dens_check(res, o, c, cap)
+    accumulate_check(acc_norm, acc_count, o)
+    reset_check(reset, o)
+
+
+def test_densify_block_scan_over_several_chunks(emu_bin, tmp_path):
+    """The one-block scan of the block row counts with more blocks than its 1,024 threads."""
+    exe = emu_bin("densify_emu")
+    rows = np.random.default_rng(5).integers(0, 513, size=2500).astype(np.uint32)
+    src, dst = tmp_path / "in.bin", tmp_path / "out.bin"
+    for cap in (int(rows.sum()), int(rows.sum()) - 1):
+        src.write_bytes(np.array([rows.size, cap], np.int32).tobytes() + rows.tobytes())
+        subprocess.run([exe, str(src), str(dst), "scan"], check=True, timeout=120)
+        raw = dst.read_bytes()
+        n_out, status = np.frombuffer(raw[:4], np.uint32)[0], np.frombuffer(raw[4:8], np.int32)[0]
+        scanned = np.frombuffer(raw[8:8 + 4 * rows.size], np.uint32)
+        assert int(np.frombuffer(raw[-4:], np.int32)[0]) == 0
+        assert n_out == rows.sum()
+        assert np.array_equal(scanned, np.concatenate([[0], np.cumsum(rows)[:-1]]).astype(np.uint32))
+        assert status == (0 if cap >= rows.sum() else -5)
