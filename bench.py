@@ -749,6 +749,79 @@ def run_spectrum_loss(args):
     print(json.dumps(out))
 
 
+def run_train_extras(args):
+    """Training extras: one densification of 500k resident Gaussians with 16-float payloads
+    (Algorithm 1: count, one-block scan, scatter), and the confidence objective of Eq. 5 at a
+    training batch of 4 samples and at 4,096.  CUDA events, L2 flushed between launches; the
+    densification's effective bandwidth counts every input once (84 + 4P B per Gaussian, the
+    split draws included) and every output row once (48 + 4P B)."""
+    import torch
+
+    from paper_2511_22793_gb300 import gsparc as G
+    from paper_2511_22793_gb300 import synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    N, P, H, W = 500_000, 16, 90, 360
+    rng = np.random.default_rng(0)
+    sc = synth.make_scene(N, seed=0)
+    d = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
+    proj = d(synth.make_proj_records(N, H, W, seed=5))
+    count = rng.integers(0, 5, size=N).astype(np.int32)
+    norm = (count * 2e-4 * np.exp(rng.normal(0.0, 0.7, size=N))).astype(np.float32)
+    xi = d(rng.normal(size=(N, 2, 3)).astype(np.float32))
+    means, ls, quats, ologit, payload = (d(a) for a in (sc.means, sc.log_scales, sc.quats, sc.opacity_logit,
+                                                        sc.latent))
+    norm_t, count_t = d(norm), d(count)
+    cap = 2 * N
+    out = {"means": torch.empty((cap, 3), device=dev), "log_scales": torch.empty((cap, 3), device=dev),
+           "quats": torch.empty((cap, 4), device=dev), "opacity_logit": torch.empty(cap, device=dev),
+           "payload": torch.empty((cap, P), device=dev),
+           "parent": torch.empty(cap, dtype=torch.int32, device=dev)}
+    n_out = torch.zeros(1, dtype=torch.int32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(G.gsparc_densify_workspace(N), dtype=torch.uint8, device=dev)
+    params = G.densify_params()
+    flush = torch.empty(64 * 1024 * 1024, device=dev)
+    peak = float(measured_peaks().get("hbm_gbs", 6800.0))
+
+    def timed(fn, reps=50):
+        ts = []
+        for it in range(reps + 3):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            if it >= 3:
+                ts.append(e0.elapsed_time(e1) * 1e3)
+        return float(np.median(ts))
+
+    dens_us = timed(lambda: G.gsparc_densify(means, ls, quats, ologit, payload, proj, norm_t, count_t, xi, params,
+                                             ws, out, n_out, status))
+    rows = int(n_out.item())
+    if int(status.item()) != 0:
+        raise RuntimeError("densification status %d" % int(status.item()))
+    nbytes = N * (84 + 4 * P) + rows * (48 + 4 * P)
+    conf = {}
+    for B in (4, 4096):
+        pos = d(synth.make_tx(B, seed=2))
+        L = d(rng.uniform(0.01, 0.6, size=B).astype(np.float32))
+        w = d((0.3 * rng.normal(size=5 * 32 + 1)).astype(np.float32))
+        obj = torch.zeros(1, device=dev)
+        C, dL, dw = torch.empty(B, device=dev), torch.empty(B, device=dev), torch.zeros(5 * 32 + 1, device=dev)
+        conf["batch_%d_us" % B] = timed(lambda: G.gsparc_confidence(pos, L, w, 32, obj, C, dL, dw))
+    line = {"metric": "densification and confidence objective", "unit": "us", "n_gpus": 1, "dtype": "f32",
+            "data": "synthetic (seeded)",
+            "config": {"workload": "densify 500k Gaussians (payload 16 floats, 2 children per split); "
+                                   "confidence 3->32->1 at batch 4 and 4096; L2 flushed"},
+            "densify_us": dens_us, "rows_out": rows, "densify_effective_gbs": nbytes / (dens_us * 1e-6) / 1e9,
+            "densify_hbm_frac": nbytes / (dens_us * 1e-6) / 1e9 / peak, "confidence": conf}
+    print(json.dumps(line))
+
+
 def run_csi(args):
     """CSI queries (Eq. 2): the 64-subcarrier channel estimate at unseen transmitter positions,
     50k Gaussians, 360x90, hidden 32, 16 transmitters per launch, receiver fixed (geometry
@@ -1047,12 +1120,14 @@ def main():
     ap.add_argument("--render", default="tc", choices=["tc", "fp32"],
                     help="forward compositing: tcgen05 (default) or FP32 CUDA cores")
     ap.add_argument("--workload", default="fwdbwd",
-                    choices=["fwdbwd", "batched", "train", "serve", "csi", "emission", "spectrum_loss"],
+                    choices=["fwdbwd", "batched", "train", "serve", "csi", "emission", "spectrum_loss",
+                             "train_extras"],
                     help="fwdbwd: the default step; batched: 64-transmitter inference with the "
                          "tensor-core network against the plain one-query path; train: the training "
                          "loop; serve: the continuous-batching query server; csi: channel-estimate "
                          "queries with the fused CSI head; emission: the per-Gaussian emission "
-                         "network's width sweep; spectrum_loss: the L1 + SSIM loss of Eq. 4")
+                         "network's width sweep; spectrum_loss: the L1 + SSIM loss of Eq. 4; train_extras: "
+                         "densification (Algorithm 1) and the confidence objective (Eq. 5)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -1079,6 +1154,10 @@ def main():
     if args.workload == "spectrum_loss":
         if rank == 0:
             run_spectrum_loss(args)
+        return
+    if args.workload == "train_extras":
+        if rank == 0:
+            run_train_extras(args)
         return
     if args.workload == "train":
         if rank == 0:
