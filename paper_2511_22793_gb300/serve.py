@@ -11,7 +11,7 @@ geometry is then computed for it, on its stream, into geometry buffers owned
 by that stream slot, and it runs alone (no other request shares its tile
 lists).
 
-Scheduling (`Server.poll`):
+Scheduling (`Server.poll`, admission in `admit`):
   * finished batches are detected with CUDA events (no host synchronisation)
     and release their stream slot and their memory reservation;
   * waiting requests are admitted oldest first while a stream slot is free and
@@ -62,6 +62,34 @@ class _Batch:
     event: torch.cuda.Event
     nbytes: int
     bufs: tuple = field(default_factory=tuple)
+
+
+def admit(waiting, used, budget, max_batch, request_bytes):
+    """Admission of the oldest waiting request and the batch it leads (host logic only).
+
+    The head is admitted if its bytes fit beside `used` within `budget`; a moving-receiver head
+    (its own geometry) runs alone; otherwise every later waiting request of the same
+    (resolution, subcarrier count) with the fixed receiver joins, oldest first, while the batch
+    has fewer than `max_batch` requests and its bytes still fit.  Returns (batch, the requests
+    left waiting in their order), or None when the head does not fit (nothing is taken)."""
+    head = waiting[0]
+    H, W = head.res
+    one = request_bytes(H, W, head.K)
+    if used + one > budget:
+        return None
+    rest = collections.deque(waiting)
+    if head.rx is not None:
+        return [rest.popleft()], rest
+    group = []
+    left = collections.deque()
+    while rest:
+        q = rest.popleft()
+        if (len(group) < max_batch and q.res == head.res and q.K == head.K and q.rx is None
+                and used + one * (len(group) + 1) <= budget):
+            group.append(q)
+        else:
+            left.append(q)
+    return group, left
 
 
 class Server:
@@ -168,24 +196,10 @@ class Server:
                 still.append(bt)
         self.inflight = still
         while self.waiting and self.free_streams:
-            head = self.waiting[0]
-            H, W = head.res
-            one = self.request_bytes(H, W, head.K)
-            if self.used + one > self.budget:
+            picked = admit(self.waiting, self.used, self.budget, self.max_batch, self.request_bytes)
+            if picked is None:
                 break                                    # wait for memory to free up
-            if head.rx is not None:
-                group = [self.waiting.popleft()]        # its own geometry: it runs alone
-            else:
-                group = []
-                rest = collections.deque()
-                while self.waiting:
-                    q = self.waiting.popleft()
-                    if (len(group) < self.max_batch and q.res == head.res and q.K == head.K
-                            and q.rx is None and self.used + one * (len(group) + 1) <= self.budget):
-                        group.append(q)
-                    else:
-                        rest.append(q)
-                self.waiting = rest
+            group, self.waiting = picked
             self._launch(group, self.free_streams.pop())
         return not self.inflight and not self.waiting
 

@@ -1,0 +1,63 @@
+"""Host logic of the query server's admission (no GPU): oldest request first, batches of one
+(resolution, subcarrier count) up to max_batch within the memory budget, moving-receiver
+requests alone, the order of the requests left waiting, and a head that does not fit blocks
+admission until memory frees up."""
+import collections
+
+from paper_2511_22793_gb300.serve import Request, admit
+
+
+def _bytes(H, W, K):
+    return H * W * K          # a stand-in size: what matters is the arithmetic of the budget
+
+
+def _q(rid, res=(90, 360), K=1, rx=None):
+    return Request(rid=rid, tx=(0.0, 0.0, 0.0), res=res, K=K, rx=rx)
+
+
+def _ids(qs):
+    return [q.rid for q in qs]
+
+
+def test_batches_same_shape_oldest_first_and_keeps_the_rest_in_order():
+    w = collections.deque([_q(0), _q(1, K=64), _q(2), _q(3, res=(45, 180)), _q(4), _q(5)])
+    group, left = admit(w, used=0, budget=10 ** 9, max_batch=3, request_bytes=_bytes)
+    assert _ids(group) == [0, 2, 4]
+    assert _ids(left) == [1, 3, 5]
+    assert _ids(w) == [0, 1, 2, 3, 4, 5]          # the caller's queue is not consumed
+
+
+def test_budget_limits_the_batch_and_blocks_a_head_that_does_not_fit():
+    one = _bytes(90, 360, 1)
+    w = collections.deque([_q(i) for i in range(5)])
+    group, left = admit(w, used=one, budget=3 * one, max_batch=8, request_bytes=_bytes)
+    assert _ids(group) == [0, 1] and _ids(left) == [2, 3, 4]
+    assert admit(w, used=3 * one - 1, budget=3 * one, max_batch=8, request_bytes=_bytes) is None
+
+
+def test_moving_receiver_runs_alone_and_is_not_joined():
+    w = collections.deque([_q(0, rx=(1.0, 0.0, 0.0)), _q(1), _q(2)])
+    group, left = admit(w, used=0, budget=10 ** 9, max_batch=8, request_bytes=_bytes)
+    assert _ids(group) == [0] and _ids(left) == [1, 2]
+    w = collections.deque([_q(0), _q(1, rx=(1.0, 0.0, 0.0)), _q(2)])
+    group, left = admit(w, used=0, budget=10 ** 9, max_batch=8, request_bytes=_bytes)
+    assert _ids(group) == [0, 2] and _ids(left) == [1]
+
+
+def test_draining_a_queue_serves_every_request_once():
+    import numpy as np
+
+    rng = np.random.default_rng(0)
+    shapes = [((45, 180), 1), ((90, 360), 64), ((180, 720), 256)]
+    w = collections.deque()
+    for i in range(200):
+        res, K = shapes[rng.integers(0, 3)]
+        w.append(_q(i, res=res, K=K, rx=(1.0, 2.0, 0.5) if rng.uniform() < 0.1 else None))
+    seen = []
+    while w:
+        group, w = admit(w, used=0, budget=10 ** 12, max_batch=8, request_bytes=_bytes)
+        assert 1 <= len(group) <= 8
+        assert len({(q.res, q.K) for q in group}) == 1
+        assert all(q.rx is None for q in group) or len(group) == 1
+        seen += _ids(group)
+    assert sorted(seen) == list(range(200))
