@@ -8,21 +8,10 @@
 #include <mutex>
 #include <utility>
 
+#include "device_common.cuh"
 #include "gsparc.h"
 
 namespace gsparc {
-
-// Footprint cut-off q_max = 2 ln 255: the kernel exp(-q/2) falls to 1/255.
-constexpr float kQMax = 11.082527090f;         // 2 * ln(255)
-constexpr float kAlphaMin = 1.0f / 255.0f;
-constexpr float kAlphaMax = 0.99f;
-constexpr float kLog2TMin = -13.287712f;      // log2(1e-4)
-constexpr float kDilation = 0.3f;             // px^2 added to diag(Sigma')
-constexpr float kRhoFloor = 1e-3f;            // zenith floor on rho, relative to r
-constexpr float kDMin = 0.01f;                // metres, floor on the transmitter distance
-constexpr double kCLight = 299792458.0;       // m/s
-constexpr float kPi = 3.14159265358979f;
-constexpr int kTile = GSPARC_TILE;
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -63,14 +52,6 @@ inline bool ensure_smem_attr(Kernel k, int bytes) {
     done[key] = bytes;
     return true;
 }
-
-// Device-side view constants passed by value to kernels.
-struct ViewDev {
-    int H, W;
-    float rx0, rx1, rx2;
-    float V[9];
-    float near_dist;
-};
 
 inline ViewDev to_dev(const gsparc_view& v) {
     ViewDev d;

@@ -26,6 +26,15 @@ struct emu_dim3 {
 };
 
 inline thread_local emu_dim3 threadIdx, blockIdx;
+
+struct alignas(8) float2 {
+    float x, y;
+};
+struct alignas(16) float4 {
+    float x, y, z, w;
+};
+inline float2 make_float2(float x, float y) { return float2{x, y}; }
+inline float4 make_float4(float x, float y, float z, float w) { return float4{x, y, z, w}; }
 inline emu_dim3 blockDim, gridDim;
 
 #define __global__
