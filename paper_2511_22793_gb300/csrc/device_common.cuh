@@ -18,6 +18,11 @@ constexpr double kCLight = 299792458.0;       // m/s
 constexpr float kPi = 3.14159265358979f;
 constexpr int kTile = GSPARC_TILE;
 
+// A kernel's dynamic shared memory (the test suite's host shim gives it a per-block buffer).
+#ifndef GSPARC_DYNAMIC_SMEM
+#define GSPARC_DYNAMIC_SMEM(name) extern __shared__ __align__(16) unsigned char name[]
+#endif
+
 // Device-side view constants passed by value to kernels.
 struct ViewDev {
     int H, W;

@@ -15,11 +15,15 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <barrier>
 #include <memory>
 #include <thread>
 #include <vector>
+
+using std::max;   // CUDA's device min / max overloads
+using std::min;
 
 struct emu_dim3 {
     unsigned x = 1, y = 1, z = 1;
@@ -33,8 +37,12 @@ struct alignas(8) float2 {
 struct alignas(16) float4 {
     float x, y, z, w;
 };
+struct alignas(8) uint2 {
+    unsigned x, y;
+};
 inline float2 make_float2(float x, float y) { return float2{x, y}; }
 inline float4 make_float4(float x, float y, float z, float w) { return float4{x, y, z, w}; }
+inline uint2 make_uint2(unsigned x, unsigned y) { return uint2{x, y}; }
 inline emu_dim3 blockDim, gridDim;
 
 #define __global__
@@ -43,6 +51,33 @@ inline emu_dim3 blockDim, gridDim;
 #define __forceinline__ inline
 #define __launch_bounds__(...)
 #define __shared__ static
+#define __align__(n) alignas(n)
+
+// dynamic shared memory: one buffer per launch, handed to every block in turn
+inline unsigned char* g_emu_dyn_smem = nullptr;
+#define GSPARC_DYNAMIC_SMEM(name) unsigned char* name = g_emu_dyn_smem
+
+// single float operations in round-to-nearest (SSE arithmetic on x86-64 and AArch64 alike)
+inline float __fadd_rn(float a, float b) { return a + b; }
+inline float __fsub_rn(float a, float b) { return a - b; }
+inline float __fmul_rn(float a, float b) { return a * b; }
+inline float __uint2float_rz(unsigned x) {
+    float f = (float)x;
+    if ((double)f > (double)x) f = nextafterf(f, 0.0f);
+    return f;
+}
+inline int __float2int_rz(float f) { return (int)f; }
+inline unsigned __float_as_uint(float f) {
+    unsigned u;
+    memcpy(&u, &f, 4);
+    return u;
+}
+inline int __popc(unsigned x) { return __builtin_popcount(x); }
+template <typename T>
+inline T __ldcg(const T* p) {
+    return *p;
+}
+inline void __threadfence() { std::atomic_thread_fence(std::memory_order_seq_cst); }
 
 struct EmuWarp {
     std::unique_ptr<std::barrier<>> bar;
@@ -78,6 +113,46 @@ inline T emu_exchange(T v, F src_of) {
     return r;
 }
 
+// every lane's value, for warp-wide votes and reductions
+template <typename T>
+inline void emu_gather(T v, T out[32]) {
+    static_assert(sizeof(T) <= 8, "value wider than 64 bits");
+    const int t = (int)threadIdx.x, w = t / 32, l = t % 32;
+    EmuWarp& wp = *g_emu_block->warps[w];
+    if (wp.alive.load() != 32) g_emu_violations.fetch_add(1);
+    uint64_t bits = 0;
+    memcpy(&bits, &v, sizeof(T));
+    wp.slot[l] = bits;
+    wp.bar->arrive_and_wait();
+    for (int k = 0; k < 32; ++k) memcpy(&out[k], &wp.slot[k], sizeof(T));
+    wp.bar->arrive_and_wait();
+}
+
+inline unsigned __ballot_sync(unsigned, int pred) {
+    int all[32];
+    emu_gather(pred ? 1 : 0, all);
+    unsigned m = 0;
+    for (int k = 0; k < 32; ++k) m |= (unsigned)all[k] << k;
+    return m;
+}
+template <typename T>
+inline T __reduce_min_sync(unsigned, T v) {
+    T all[32];
+    emu_gather(v, all);
+    return *std::min_element(all, all + 32);
+}
+template <typename T>
+inline T __reduce_max_sync(unsigned, T v) {
+    T all[32];
+    emu_gather(v, all);
+    return *std::max_element(all, all + 32);
+}
+inline void __syncwarp(unsigned = 0xffffffffu) {
+    EmuWarp& wp = *g_emu_block->warps[(int)threadIdx.x / 32];
+    if (wp.alive.load() != 32) g_emu_violations.fetch_add(1);
+    wp.bar->arrive_and_wait();
+}
+
 template <typename T>
 inline T __shfl_xor_sync(unsigned, T v, int mask) {
     return emu_exchange(v, [mask](int l) { return l ^ mask; });
@@ -101,18 +176,46 @@ inline T atomicAdd(T* p, T v) {
 }
 
 template <typename T>
+inline T atomicOr(T* p, T v) {
+    return std::atomic_ref<T>(*p).fetch_or(v);
+}
+template <typename T>
+inline T atomicAnd(T* p, T v) {
+    return std::atomic_ref<T>(*p).fetch_and(v);
+}
+template <typename T>
+inline T atomicMin(T* p, T v) {
+    std::atomic_ref<T> a(*p);
+    T cur = a.load();
+    while (v < cur && !a.compare_exchange_weak(cur, v)) {
+    }
+    return cur;
+}
+template <typename T>
+inline T atomicMax(T* p, T v) {
+    std::atomic_ref<T> a(*p);
+    T cur = a.load();
+    while (v > cur && !a.compare_exchange_weak(cur, v)) {
+    }
+    return cur;
+}
+
+template <typename T>
 inline T atomicCAS(T* p, T cmp, T val) {
     std::atomic_ref<T>(*p).compare_exchange_strong(cmp, val);
     return cmp;
 }
 
-// Runs kernel(args...) over grid x block (1D blocks of whole warps, up to a 2D grid).
+// Runs kernel(args...) over grid x block (1D blocks of whole warps, up to a 2D grid), with
+// `smem_bytes` of dynamic shared memory.
 template <typename K, typename... A>
-inline void emu_launch(emu_dim3 grid, unsigned threads, K kernel, A... args) {
+inline void emu_launch_smem(emu_dim3 grid, unsigned threads, size_t smem_bytes, K kernel, A... args) {
     if (threads % 32 != 0) {
         g_emu_violations.fetch_add(1);
         return;
     }
+    std::vector<uint64_t> dyn((smem_bytes + 7) / 8 + 2);   // 16-byte aligned start below
+    g_emu_dyn_smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dyn.data()) + 15) & ~uintptr_t(15));
     gridDim = grid;
     blockDim = emu_dim3{threads, 1, 1};
     for (unsigned by = 0; by < grid.y; ++by)
@@ -141,4 +244,10 @@ inline void emu_launch(emu_dim3 grid, unsigned threads, K kernel, A... args) {
             for (auto& th : pool) th.join();
             g_emu_block = nullptr;
         }
+    g_emu_dyn_smem = nullptr;
+}
+
+template <typename K, typename... A>
+inline void emu_launch(emu_dim3 grid, unsigned threads, K kernel, A... args) {
+    emu_launch_smem(grid, threads, 0, kernel, args...);
 }

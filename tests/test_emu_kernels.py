@@ -184,3 +184,62 @@ def test_projection_kernels_logic(emu_bin, tmp_path, n, H, W, seed, rot):
     om, ol, oq = (x.numpy() for x in torch.autograd.grad(loss, [m, ls, q]))
     for got, want in ((dm, om), (dl, ol), (dq, oq)):
         assert np.linalg.norm(got - want) <= 1e-3 * np.linalg.norm(want)
+
+
+def _binsort_run(exe, tmp_path, rec, H, W, cap):
+    n = rec.shape[0]
+    raw = _run(exe, tmp_path, np.array([n, H, W, cap], np.int32).tobytes() + np.ascontiguousarray(
+        rec, np.float32).tobytes())
+    T = ((W + 15) // 16) * ((H + 15) // 16)
+    n_pairs, status = int(np.frombuffer(raw[:4], np.uint32)[0]), int(np.frombuffer(raw[4:8], np.int32)[0])
+    off = 8
+    ranges = np.frombuffer(raw, np.uint32, count=2 * T, offset=off).reshape(T, 2)
+    off += 8 * T
+    ids = np.frombuffer(raw, np.uint32, count=cap, offset=off)
+    off += 4 * cap
+    keys = np.frombuffer(raw, np.uint64, count=cap, offset=off)
+    assert int(np.frombuffer(raw[-4:], np.int32)[0]) == 0
+    return n_pairs, status, ranges, ids, keys
+
+
+@pytest.mark.parametrize("n,H,W,seed,case", [(1, 90, 360, 1, "plain"), (17, 90, 360, 2, "plain"),
+                                             (1000, 90, 360, 3, "plain"), (800, 180, 720, 5, "plain"),
+                                             (3000, 45, 180, 6, "plain"), (1500, 45, 180, 14, "three_depths"),
+                                             (1500, 45, 180, 17, "one_depth"),
+                                             (2000, 90, 360, 12, "overflow"), (400, 90, 360, 16, "culled")])
+def test_binsort_kernels_logic(emu_bin, tmp_path, n, H, W, seed, case):
+    """k_tile_count, k_tile_emit and k_tile_sort (the library's source under the host shim)
+    against the oracle's stable (tile, r, index) sort, bit for bit: ragged grids, 1 to 3,000
+    records, the shared-memory distribution sort, three distinct depths and a single depth (tiles
+    whose depth sub-buckets exceed 64 keys take the radix path; ties by index), a capacity below
+    the pair count, every record culled.  Larger scenes and buckets above the
+    shared-memory capacity are the GPU tests' (the shim runs a warp vote as two thread
+    barriers, which makes those sizes slow on the CPU)."""
+    from oracle import binsort as obs
+    from paper_2511_22793_gb300 import synth
+
+    exe = emu_bin("binsort_emu")
+    rec = synth.make_proj_records(n, H, W, seed=seed)
+    if case == "three_depths":
+        rec[:, 7] = np.random.default_rng(15).choice(np.float32([1.5, 2.0, 7.25]), size=len(rec))
+    if case == "one_depth":       # every key of a tile in one depth sub-bucket: the radix path, ties by index
+        rec[:, 7] = np.float32(2.0)
+    if case == "culled":
+        rec[:, 2:4] = -1
+    ok, ov, orng = obs.bin_sort(rec, H, W)
+    cap = len(ov) // 2 if case == "overflow" else max(16, len(ov))
+    n_pairs, status, ranges, ids, keys = _binsort_run(exe, tmp_path, rec, H, W, cap)
+    assert n_pairs == len(ov)
+    if case == "overflow":
+        assert status == -5
+        fits = orng[:, 1] <= cap
+        assert fits.any() and not fits.all()
+        assert np.array_equal(ranges[fits], orng[fits])
+        assert np.all(ranges[~fits, 0] == ranges[~fits, 1])
+        last = orng[fits][:, 1].max()
+        assert np.array_equal(ids[:last], ov[:last])
+        return
+    assert status == 0
+    assert np.array_equal(ranges, orng)
+    assert np.array_equal(ids[:len(ov)], ov)
+    assert np.array_equal(keys[:len(ov)], ok)
