@@ -23,6 +23,9 @@ constexpr int kTile = GSPARC_TILE;
 #define GSPARC_DYNAMIC_SMEM(name) extern __shared__ __align__(16) unsigned char name[]
 #endif
 
+inline int tiles_x(const gsparc_view& v) { return (v.W + kTile - 1) / kTile; }
+inline int tiles_y(const gsparc_view& v) { return (v.H + kTile - 1) / kTile; }
+
 // Device-side view constants passed by value to kernels.
 struct ViewDev {
     int H, W;

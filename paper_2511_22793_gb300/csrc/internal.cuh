@@ -20,8 +20,6 @@ inline int launch_status() {
     return e == cudaSuccess ? GSPARC_OK : GSPARC_ERR_CUDA;
 }
 
-inline int tiles_x(const gsparc_view& v) { return (v.W + kTile - 1) / kTile; }
-inline int tiles_y(const gsparc_view& v) { return (v.H + kTile - 1) / kTile; }
 
 inline bool view_ok(const gsparc_view* v) {
     return v && v->H > 0 && v->W > 0 && v->H <= 32768 && v->W <= 32768;

@@ -11,6 +11,8 @@
 // runs at a time.
 #pragma once
 
+#define GSPARC_HOST_SHIM 1
+
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -40,6 +42,9 @@ struct alignas(16) float4 {
 struct alignas(8) uint2 {
     unsigned x, y;
 };
+struct alignas(16) uint4 {
+    unsigned x, y, z, w;
+};
 inline float2 make_float2(float x, float y) { return float2{x, y}; }
 inline float4 make_float4(float x, float y, float z, float w) { return float4{x, y, z, w}; }
 inline uint2 make_uint2(unsigned x, unsigned y) { return uint2{x, y}; }
@@ -51,7 +56,7 @@ inline emu_dim3 blockDim, gridDim;
 #define __forceinline__ inline
 #define __launch_bounds__(...)
 #define __shared__ static
-#define __align__(n) alignas(n)
+#define __align__(n) __attribute__((aligned(n)))
 
 // dynamic shared memory: one buffer per launch, handed to every block in turn
 inline unsigned char* g_emu_dyn_smem = nullptr;
@@ -61,6 +66,15 @@ inline unsigned char* g_emu_dyn_smem = nullptr;
 inline float __fadd_rn(float a, float b) { return a + b; }
 inline float __fsub_rn(float a, float b) { return a - b; }
 inline float __fmul_rn(float a, float b) { return a * b; }
+inline float __fmaf_rn(float a, float b, float c) { return fmaf(a, b, c); }
+inline void __sincosf(float x, float* s, float* c) { sincosf(x, s, c); }
+inline float __int_as_float(int i) {
+    float f;
+    memcpy(&f, &i, 4);
+    return f;
+}
+inline int __ffsll(long long x) { return __builtin_ffsll(x); }
+inline int __clzll(long long x) { return x == 0 ? 64 : __builtin_clzll((unsigned long long)x); }
 inline float __uint2float_rz(unsigned x) {
     float f = (float)x;
     if ((double)f > (double)x) f = nextafterf(f, 0.0f);
@@ -88,12 +102,27 @@ struct EmuWarp {
 struct EmuBlockState {
     std::unique_ptr<std::barrier<>> bar;
     std::vector<std::unique_ptr<EmuWarp>> warps;
+    std::atomic<int> vote[3] = {0, 0, 0};  // __syncthreads_or, see below
 };
 
 inline EmuBlockState* g_emu_block = nullptr;
 inline std::atomic<int> g_emu_violations{0};
 
 inline void __syncthreads() { g_emu_block->bar->arrive_and_wait(); }
+
+// Call c of a block uses slot c % 3; between its two barriers every thread clears slot
+// (c + 1) % 3, which nobody reads then and nobody sets before the second barrier.
+inline thread_local int tl_vote_calls = 0;
+inline int __syncthreads_or(int pred) {
+    EmuBlockState& st = *g_emu_block;
+    const int c = tl_vote_calls++;
+    if (pred) st.vote[c % 3].fetch_or(1);
+    st.bar->arrive_and_wait();
+    const int r = st.vote[c % 3].load();
+    st.vote[(c + 1) % 3].store(0);
+    st.bar->arrive_and_wait();
+    return r;
+}
 
 template <typename T, typename F>
 inline T emu_exchange(T v, F src_of) {
@@ -126,6 +155,14 @@ inline void emu_gather(T v, T out[32]) {
     wp.bar->arrive_and_wait();
     for (int k = 0; k < 32; ++k) memcpy(&out[k], &wp.slot[k], sizeof(T));
     wp.bar->arrive_and_wait();
+}
+
+inline int __any_sync(unsigned, int pred) {
+    int all[32];
+    emu_gather(pred ? 1 : 0, all);
+    for (int k = 0; k < 32; ++k)
+        if (all[k]) return 1;
+    return 0;
 }
 
 inline unsigned __ballot_sync(unsigned, int pred) {
@@ -206,7 +243,7 @@ inline T atomicCAS(T* p, T cmp, T val) {
     return cmp;
 }
 
-// Runs kernel(args...) over grid x block (1D blocks of whole warps, up to a 2D grid), with
+// Runs kernel(args...) over grid x block (1D blocks of whole warps, a 3D grid), with
 // `smem_bytes` of dynamic shared memory.
 template <typename K, typename... A>
 inline void emu_launch_smem(emu_dim3 grid, unsigned threads, size_t smem_bytes, K kernel, A... args) {
@@ -218,6 +255,7 @@ inline void emu_launch_smem(emu_dim3 grid, unsigned threads, size_t smem_bytes, 
     g_emu_dyn_smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dyn.data()) + 15) & ~uintptr_t(15));
     gridDim = grid;
     blockDim = emu_dim3{threads, 1, 1};
+    for (unsigned bz = 0; bz < grid.z; ++bz)
     for (unsigned by = 0; by < grid.y; ++by)
         for (unsigned bx = 0; bx < grid.x; ++bx) {
             EmuBlockState st;
@@ -232,9 +270,9 @@ inline void emu_launch_smem(emu_dim3 grid, unsigned threads, size_t smem_bytes, 
             std::vector<std::thread> pool;
             pool.reserve(threads);
             for (unsigned t = 0; t < threads; ++t)
-                pool.emplace_back([&, t, bx, by] {
+                pool.emplace_back([&, t, bx, by, bz] {
                     threadIdx = emu_dim3{t, 0, 0};
-                    blockIdx = emu_dim3{bx, by, 0};
+                    blockIdx = emu_dim3{bx, by, bz};
                     kernel(args...);
                     EmuWarp& wp = *st.warps[t / 32];
                     wp.alive.fetch_sub(1);

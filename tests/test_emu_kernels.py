@@ -243,3 +243,55 @@ def test_binsort_kernels_logic(emu_bin, tmp_path, n, H, W, seed, case):
     assert np.array_equal(ranges, orng)
     assert np.array_equal(ids[:len(ov)], ov)
     assert np.array_equal(keys[:len(ov)], ok)
+
+
+@pytest.mark.parametrize("n,H,W,K,B,seed", [(300, 45, 180, 8, 2, 41), (200, 45, 180, 37, 1, 42),
+                                             (150, 45, 180, 1, 1, 43)])
+def test_render_fp32_kernels_logic(emu_bin, tmp_path, n, H, W, K, B, seed):
+    """k_render_fwd and k_render_bwd (the library's FP32 compositing, under the host shim) on the
+    oracle's projection and attributes rounded to FP32, with the oracle's bit-exact tile lists:
+    each spectrum within 1e-3 relative L2 of the oracle's renderer and every gradient component
+    (p, conic, sigma, a, phi0, L) within 1e-3 of its analytic gradient (the GPU tests' bars);
+    strips of 1, 8 and 32 (ragged: K = 37) subcarriers, one and two transmitters, ragged tiles."""
+    from oracle import binsort as obs
+    from oracle import render as orender
+    from paper_2511_22793_gb300 import synth
+    from gpu_util_host import oracle_inputs_fp32
+
+    exe = emu_bin("render_emu")
+    view, band = synth.View(H=H, W=W), synth.Band(K=K)
+    g32, at32, proj, attr = oracle_inputs_fp32(n, view, B, seed)
+    _, ids, ranges = obs.bin_sort(proj, H, W)
+    rng = np.random.default_rng(seed + 5)
+    gz = rng.normal(size=(B, H * W, K)) + 1j * rng.normal(size=(B, H * W, K))
+    dspec = np.stack([gz.real, gz.imag], -1).reshape(B, H, W, K, 2).transpose(0, 3, 1, 2, 4).astype(np.float32)
+    payload = np.array([H, W, K, n, B, len(ids)], np.int32).tobytes() + np.array([band.f_c, band.df]).tobytes() + \
+        proj.tobytes() + ranges.astype(np.uint32).tobytes() + ids.astype(np.uint32).tobytes() + attr.tobytes() + \
+        np.ascontiguousarray(dspec).tobytes()
+    raw = _run(exe, tmp_path, payload, timeout=300)
+    assert int(np.frombuffer(raw[-4:], np.int32)[0]) == 0
+    P = H * W
+    off = 0
+
+    def take(dtype, count):
+        nonlocal off
+        a = np.frombuffer(raw, dtype=dtype, count=count, offset=off)
+        off += np.dtype(dtype).itemsize * count
+        return a
+
+    spec = take(np.float32, 2 * B * K * P).reshape(B, K, H, W, 2).astype(np.float64)
+    take(np.float32, B * P)
+    take(np.uint32, 2 * B * P)
+    dattr = take(np.float32, 4 * B * n).reshape(B, n, 4).astype(np.float64)
+    dproj = take(np.float32, 8 * n).reshape(n, 8).astype(np.float64)
+    z = (spec[..., 0] + 1j * spec[..., 1]).transpose(0, 2, 3, 1).reshape(B, P, K)
+    for b in range(B):
+        zo, _, _ = orender.render_fwd(g32, at32[b], H, W, K, band.f_c, band.df)
+        assert np.linalg.norm(z[b] - zo) <= 1e-3 * np.linalg.norm(zo)
+    refs = [orender.render_bwd(g32, at32[b], H, W, K, band.f_c, band.df, gz[b]) for b in range(B)]
+    ref_p = sum(refs)                     # d_proj sums over the transmitters
+    for c, col in enumerate((0, 1, 4, 5, 6)):          # p_x, p_y, c_xx, c_xy, c_yy
+        assert np.linalg.norm(dproj[:, col] - ref_p[:, c]) <= 1e-3 * np.linalg.norm(ref_p[:, c]), c
+    for b in range(B):
+        for c, col in ((5, 2), (6, 0), (7, 1), (8, 3)):      # sigma, a, phi0, L
+            assert np.linalg.norm(dattr[b, :, col] - refs[b][:, c]) <= 1e-3 * np.linalg.norm(refs[b][:, c]), (b, c)
