@@ -295,3 +295,53 @@ def test_render_fp32_kernels_logic(emu_bin, tmp_path, n, H, W, K, B, seed):
     for b in range(B):
         for c, col in ((5, 2), (6, 0), (7, 1), (8, 3)):      # sigma, a, phi0, L
             assert np.linalg.norm(dattr[b, :, col] - refs[b][:, c]) <= 1e-3 * np.linalg.norm(refs[b][:, c]), (b, c)
+
+
+@pytest.mark.parametrize("n,B,hidden,seed", [(300, 1, 32, 51), (130, 2, 8, 52), (200, 1, 64, 53),
+                                             (70, 3, 16, 54)])
+def test_attribute_network_fp32_kernels_logic(emu_bin, tmp_path, n, B, hidden, seed):
+    """k_mlp_fwd and k_mlp_bwd (the library's FP32 attribute network, under the host shim; the
+    backward as two persistent CTAs taking several 128-row passes each) against the oracle's
+    attributes (2e-5 relative per component) and its vector-Jacobian product (1e-4 relative L2
+    for the means, logits, latents and every weight block); the seeds keep every hidden
+    pre-activation more than 1e-5 from the ReLU kink, so both sides take the same decisions."""
+    from oracle import attributes as oattr
+    from paper_2511_22793_gb300 import synth
+
+    exe = emu_bin("mlp_emu")
+    sc = synth.make_scene(n, seed=seed)
+    mlp = synth.make_mlp(hidden, seed=seed + 1)
+    tx = synth.make_tx(B, seed=seed + 2)
+    rx = np.zeros(3, np.float32)
+    d_attr = np.random.default_rng(seed + 3).normal(size=(B, n, 4)).astype(np.float32)
+    payload = np.array([n, B, hidden], np.int32).tobytes() + tx.tobytes() + rx.tobytes() + sc.means.tobytes() + \
+        sc.opacity_logit.tobytes() + sc.latent.tobytes() + b"".join(a.tobytes() for a in mlp.arrays()) + \
+        d_attr.tobytes()
+    raw = _run(exe, tmp_path, payload)
+    assert int(np.frombuffer(raw[-4:], np.int32)[0]) == 0
+    f = np.frombuffer(raw[:-4], np.float32).astype(np.float64)
+    sizes = [4 * B * n, 3 * n, n, 16 * n] + [a.size for a in mlp.arrays()]
+    parts = np.split(f, np.cumsum(sizes)[:-1])
+    attr = parts[0].reshape(B, n, 4)
+
+    t = lambda a: torch.tensor(np.asarray(a, np.float64), requires_grad=True)
+    m, ol, lat = t(sc.means), t(sc.opacity_logit), t(sc.latent)
+    ws = [t(a) for a in mlp.arrays()]
+    total = torch.zeros((), dtype=torch.float64)
+    kink = np.inf
+    for b in range(B):
+        at = oattr.attributes(m, ol, lat, ws, torch.tensor(tx[b], dtype=torch.float64), rx)
+        stacked = torch.stack([at["a"], at["phi0"], at["sigma"], at["L"]], -1)
+        want = stacked.detach().numpy()
+        assert np.allclose(attr[b], want, rtol=2e-5, atol=2e-6 * np.abs(want).max(axis=0))
+        total = total + (stacked * torch.tensor(d_attr[b].astype(np.float64))).sum()
+        d = torch.clamp(torch.linalg.norm(m - torch.tensor(tx[b], dtype=torch.float64), dim=1), min=0.01)
+        h0 = torch.cat([torch.tensor(tx[b], dtype=torch.float64).expand(n, 3), lat, torch.log(d)[:, None]], 1)
+        pre1 = h0 @ ws[0] + ws[1]
+        pre2 = torch.relu(pre1) @ ws[2] + ws[3]
+        kink = min(kink, float(pre1.detach().abs().min()), float(pre2.detach().abs().min()))
+    assert kink > 1e-5            # no ReLU decision within FP32 rounding of the kink in these seeds
+    grads = torch.autograd.grad(total, [m, ol, lat] + ws)
+    for k, (got, want) in enumerate(zip(parts[1:], grads)):
+        want = want.numpy().reshape(-1)
+        assert np.linalg.norm(got - want) <= 1e-4 * np.linalg.norm(want), k
