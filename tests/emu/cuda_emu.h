@@ -91,6 +91,10 @@ template <typename T>
 inline T __ldcg(const T* p) {
     return *p;
 }
+template <typename T>
+inline T __ldg(const T* p) {
+    return *p;
+}
 inline void __threadfence() { std::atomic_thread_fence(std::memory_order_seq_cst); }
 
 struct EmuWarp {

@@ -345,3 +345,58 @@ def test_attribute_network_fp32_kernels_logic(emu_bin, tmp_path, n, B, hidden, s
     for k, (got, want) in enumerate(zip(parts[1:], grads)):
         want = want.numpy().reshape(-1)
         assert np.linalg.norm(got - want) <= 1e-4 * np.linalg.norm(want), k
+
+
+@pytest.mark.parametrize("n,h,B,inv_d", [(77, 16, 3, True), (50, 64, 2, False), (130, 5, 1, True),
+                                         (40, 8, 9, False)])
+def test_emission_kernels_logic(emu_bin, tmp_path, n, h, B, inv_d):
+    """k_emission_fwd and k_emission_bwd (the library's per-Gaussian emission network, under the
+    host shim) against the oracle's attributes (1e-5 relative L2 per component) and its
+    vector-Jacobian product (1e-4; the padding of every row untouched): groups of 4 to 32 lanes,
+    two hidden units per lane at width 64, transmitters in several chunks (B = 9 > G = 8), the
+    1/d toggle."""
+    from oracle import emission as E
+    from paper_2511_22793_gb300 import synth
+
+    exe = emu_bin("emission_emu")
+    rng = np.random.default_rng(80 + h)
+    sc = synth.make_scene(n, seed=81)
+    P = E.n_params(h)
+    flat = np.zeros((n, P))
+    flat[:, :3 * h] = rng.normal(size=(n, 3 * h)) / np.sqrt(3.0)
+    flat[:, 3 * h:4 * h] = 0.1 * rng.normal(size=(n, h))
+    flat[:, 4 * h:6 * h] = rng.normal(size=(n, 2 * h)) / np.sqrt(h)
+    flat[:, 6 * h:] = 0.1 * rng.normal(size=(n, 2))
+    flat = flat.astype(np.float32)
+    stride = (6 * h + 2 + 3) // 4 * 4
+    buf = np.zeros((n, stride), np.float32)
+    buf[:, :P] = flat
+    txs = synth.make_tx(B, seed=82)
+    g = rng.normal(size=(B, n, 4)).astype(np.float32)
+    rx = np.zeros(3, np.float32)
+    payload = np.array([n, B, h, int(inv_d)], np.int32).tobytes() + txs.tobytes() + rx.tobytes() + \
+        sc.means.tobytes() + sc.opacity_logit.tobytes() + buf.tobytes() + g.tobytes()
+    raw = _run(exe, tmp_path, payload)
+    assert int(np.frombuffer(raw[-4:], np.int32)[0]) == 0
+    f = np.frombuffer(raw[:-4], np.float32).astype(np.float64)
+    attr, dm, do, dw = np.split(f, np.cumsum([4 * B * n, 3 * n, n]))
+    attr, dm, dw = attr.reshape(B, n, 4), dm.reshape(n, 3), dw.reshape(n, stride)
+    t64 = lambda a: torch.tensor(np.asarray(a, np.float64))
+    W1 = t64(flat)[:, :3 * h].reshape(n, 3, h)
+    b1 = t64(flat)[:, 3 * h:4 * h]
+    for t in txs:
+        pre = torch.einsum("k,nkj->nj", t64(t), W1) + b1
+        assert float(pre.abs().min()) > 1e-5      # no ReLU decision within FP32 rounding of the kink
+        at = E.attributes(t64(sc.means), t64(sc.opacity_logit), t64(flat), h, t, tuple(rx), inv_d=inv_d)
+        want = np.stack([at[k].numpy() for k in ("a", "phi0", "sigma", "L")], -1)
+        b = list(map(tuple, txs)).index(tuple(t))
+        for c in range(4):
+            assert np.linalg.norm(attr[b, :, c] - want[:, c]) <= 1e-5 * np.linalg.norm(want[:, c]), c
+    gm, go, gf = E.attributes_vjp(sc.means.astype(np.float64), sc.opacity_logit.astype(np.float64),
+                                  flat.astype(np.float64), h, txs.astype(np.float64), tuple(rx), g.astype(np.float64),
+                                  inv_d=inv_d)
+    assert np.all(dw[:, P:] == 0.0)
+    assert np.linalg.norm(dm - gm) <= 1e-4 * np.linalg.norm(gm)
+    assert np.linalg.norm(do - go) <= 1e-5 * np.linalg.norm(go)
+    for lo, hi in ((0, 3 * h), (3 * h, 4 * h), (4 * h, 6 * h), (6 * h, 6 * h + 2)):
+        assert np.linalg.norm(dw[:, lo:hi] - gf[:, lo:hi]) <= 1e-4 * np.linalg.norm(gf[:, lo:hi]), (lo, hi)
