@@ -95,6 +95,14 @@ template <typename T>
 inline T __ldg(const T* p) {
     return *p;
 }
+template <typename T>
+inline T __ldcs(const T* p) {
+    return *p;
+}
+template <typename T>
+inline void __stcs(T* p, T v) {
+    *p = v;
+}
 inline void __threadfence() { std::atomic_thread_fence(std::memory_order_seq_cst); }
 
 struct EmuWarp {
@@ -247,14 +255,10 @@ inline T atomicCAS(T* p, T cmp, T val) {
     return cmp;
 }
 
-// Runs kernel(args...) over grid x block (1D blocks of whole warps, a 3D grid), with
+// Runs kernel(args...) over grid x block (1D blocks, a 3D grid), with
 // `smem_bytes` of dynamic shared memory.
 template <typename K, typename... A>
 inline void emu_launch_smem(emu_dim3 grid, unsigned threads, size_t smem_bytes, K kernel, A... args) {
-    if (threads % 32 != 0) {
-        g_emu_violations.fetch_add(1);
-        return;
-    }
     std::vector<uint64_t> dyn((smem_bytes + 7) / 8 + 2);   // 16-byte aligned start below
     g_emu_dyn_smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dyn.data()) + 15) & ~uintptr_t(15));
     gridDim = grid;
@@ -264,10 +268,12 @@ inline void emu_launch_smem(emu_dim3 grid, unsigned threads, size_t smem_bytes, 
         for (unsigned bx = 0; bx < grid.x; ++bx) {
             EmuBlockState st;
             st.bar = std::make_unique<std::barrier<>>((std::ptrdiff_t)threads);
-            for (unsigned w = 0; w < threads / 32; ++w) {
+            for (unsigned w = 0; w < (threads + 31) / 32; ++w) {
+                // a last, partial warp has fewer lanes: a full-warp shuffle there counts as a violation
+                const int lanes = (int)std::min(32u, threads - 32 * w);
                 auto wp = std::make_unique<EmuWarp>();
-                wp->bar = std::make_unique<std::barrier<>>(32);
-                wp->alive = 32;
+                wp->bar = std::make_unique<std::barrier<>>(lanes);
+                wp->alive = lanes;
                 st.warps.push_back(std::move(wp));
             }
             g_emu_block = &st;

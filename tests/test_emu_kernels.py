@@ -400,3 +400,77 @@ def test_emission_kernels_logic(emu_bin, tmp_path, n, h, B, inv_d):
     assert np.linalg.norm(do - go) <= 1e-5 * np.linalg.norm(go)
     for lo, hi in ((0, 3 * h), (3 * h, 4 * h), (4 * h, 6 * h), (6 * h, 6 * h + 2)):
         assert np.linalg.norm(dw[:, lo:hi] - gf[:, lo:hi]) <= 1e-4 * np.linalg.norm(gf[:, lo:hi]), (lo, hi)
+
+
+@pytest.mark.parametrize("B,K,H,W", [(1, 2, 16, 16), (2, 1, 7, 9), (1, 3, 20, 45)])
+def test_spectrum_loss_kernels_logic(emu_bin, tmp_path, B, K, H, W):
+    """The four separable passes of the L1 + SSIM loss (Eq. 4) and their gradient (the library's
+    source under the host shim) against the oracle: the loss within 1e-5 relative, dL/dz within
+    1e-4 relative L2, planes smaller than the window among the cases; targets 6-36% away from
+    the magnitudes so that both sides take the L1 term's sign alike."""
+    from oracle import spectrum_loss as S
+
+    exe = emu_bin("ssim_emu")
+    rng = np.random.default_rng(90 + H)
+    mag = 0.1 + rng.uniform(size=(B, K, H, W))
+    z = mag * np.exp(2j * np.pi * rng.uniform(size=(B, K, H, W)))
+    y = mag * (1.0 + 0.3 * np.sign(rng.normal(size=mag.shape)) * (0.2 + rng.uniform(size=mag.shape)))
+    z32 = np.stack([z.real, z.imag], -1).astype(np.float32)
+    y32 = y.astype(np.float32)
+    payload = np.array([B, K, H, W, 1], np.int32).tobytes() + np.array([0.2], np.float32).tobytes() + \
+        z32.tobytes() + y32.tobytes()
+    raw = _run(exe, tmp_path, payload)
+    assert int(np.frombuffer(raw[-4:], np.int32)[0]) == 0
+    loss = float(np.frombuffer(raw[:4], np.float32)[0])
+    dz = np.frombuffer(raw[4:-4], np.float32).reshape(B, K, H, W, 2).astype(np.float64)
+    zc = z32.astype(np.float64) @ np.array([1.0, 1j])
+    L, gre, gim = S.loss_and_grad(zc, y32.astype(np.float64))
+    assert abs(loss - L) <= 1e-5 * abs(L)
+    assert np.linalg.norm(dz[..., 0] - gre) <= 1e-4 * np.linalg.norm(gre)
+    assert np.linalg.norm(dz[..., 1] - gim) <= 1e-4 * np.linalg.norm(gim)
+
+
+@pytest.mark.parametrize("B,K,H,W,count,n,step", [(2, 3, 17, 23, 3001, 700, 1), (1, 1, 90, 360, 257, 1, 5)])
+def test_heads_loss_and_adam_kernels_logic(emu_bin, tmp_path, B, K, H, W, count, n, step):
+    """CSI head (Eq. 2), channel loss (Eq. 3) and head backward, the training step's complex L2
+    loss and Adam (the library's source under the host shim, with its entry points' launch
+    shapes on 152 SMs) against the oracle: the spatial means and the losses within 1e-6
+    relative, the gradients and the Adam state within FP32 rounding."""
+    from oracle import adam as OA
+    from oracle import csi as OC
+
+    exe = emu_bin("heads_emu")
+    rng = np.random.default_rng(100 + H)
+    P = H * W
+    spec = rng.normal(size=(B, K, P, 2)).astype(np.float32)
+    tcsi = rng.normal(size=(B, K, 2)).astype(np.float32)
+    z = rng.normal(size=(count, 2)).astype(np.float32)
+    tz = rng.normal(size=(count, 2)).astype(np.float32)
+    p, g = rng.normal(size=n).astype(np.float32), rng.normal(size=n).astype(np.float32)
+    m, v = (0.1 * rng.normal(size=n)).astype(np.float32), rng.uniform(0, 0.1, size=n).astype(np.float32)
+    scale, lr, b1, b2, eps = 1.0 / P, 5e-3, 0.9, 0.999, 1e-15
+    payload = np.array([B, K, P, count, n, step], np.int32).tobytes() + \
+        np.array([scale, lr, b1, b2, eps], np.float32).tobytes() + b"".join(
+            a.tobytes() for a in (spec, tcsi, z, tz, p, g, m, v))
+    raw = _run(exe, tmp_path, payload)
+    assert int(np.frombuffer(raw[-4:], np.int32)[0]) == 0
+    f = np.frombuffer(raw[:-4], np.float32).astype(np.float64)
+    csi, closs, dcsi, dspec, l2, dz, p1, m1, v1 = np.split(
+        f, np.cumsum([2 * B * K, 1, 2 * B * K, 2 * B * K * P, 1, 2 * count, n, n]))
+    c = lambda a: a[..., 0] + 1j * a[..., 1]
+    spec_c = c(spec.astype(np.float64)).transpose(0, 2, 1)                      # [B, P, K]
+    h = OC.csi_head(spec_c, H, W)
+    assert np.allclose(c(csi.reshape(B, K, 2)), h, rtol=0, atol=1e-6 * np.abs(h).max())
+    L, dh = OC.channel_loss(c(csi.reshape(B, K, 2)), c(tcsi.astype(np.float64)))
+    assert abs(float(closs[0]) - L) <= 1e-6 * L
+    assert np.allclose(c(dcsi.reshape(B, K, 2)), dh, rtol=1e-6, atol=1e-9)
+    back = OC.csi_head_bwd(c(dcsi.reshape(B, K, 2)), H, W)                      # [B, P, K]
+    assert np.allclose(c(dspec.reshape(B, K, P, 2)).transpose(0, 2, 1), back, rtol=1e-6, atol=1e-12)
+    d = c(z.astype(np.float64)) - c(tz.astype(np.float64))
+    assert abs(float(l2[0]) - np.mean(np.abs(d) ** 2)) <= 1e-6 * np.mean(np.abs(d) ** 2)
+    assert np.allclose(c(dz.reshape(count, 2)), 2 * d / count, rtol=1e-6, atol=1e-12)
+    f32 = lambda x: float(np.float32(x))         # the hyperparameters as the kernel receives them
+    q, mo, vo = OA.adam_step(p.astype(np.float64), g.astype(np.float64), m.astype(np.float64),
+                             v.astype(np.float64), step, f32(lr), b1=f32(b1), b2=f32(b2), eps=f32(eps))
+    assert np.allclose(m1, mo, rtol=1e-6, atol=1e-7) and np.allclose(v1, vo, rtol=1e-6, atol=1e-9)
+    assert np.allclose(p1, q, rtol=1e-6, atol=1e-6 * lr)
