@@ -474,3 +474,60 @@ def test_heads_loss_and_adam_kernels_logic(emu_bin, tmp_path, B, K, H, W, count,
                              v.astype(np.float64), step, f32(lr), b1=f32(b1), b2=f32(b2), eps=f32(eps))
     assert np.allclose(m1, mo, rtol=1e-6, atol=1e-7) and np.allclose(v1, vo, rtol=1e-6, atol=1e-9)
     assert np.allclose(p1, q, rtol=1e-6, atol=1e-6 * lr)
+
+
+@pytest.mark.parametrize("H,W,B,strips,split_min,allow,have_walks", [
+    (45, 180, 2, 1, 3, 1, False), (90, 360, 1, 2, 3, 1, True), (45, 180, 1, 1, 1, 1, False),
+    (45, 180, 2, 1, 3, 0, True), (90, 360, 1, 1, -1, 1, False)])
+def test_backward_schedule_logic(emu_bin, tmp_path, H, W, B, strips, split_min, allow, have_walks):
+    """k_bwd_schedule (under the host shim) against the rules it implements: a (transmitter,
+    tile) walk is min(largest n_contrib over the tile's pixels, list length); every (walk, strip)
+    unit with a nonzero walk gets one item [0, walk), or, when splitting is allowed and its
+    16-entry batch count nb exceeds split_min, a front item [0, m) (flagged) and a back item
+    [m, walk) with m = 16 floor(nb / 2); items are ordered by non-increasing batch count (counts
+    above 255 share a bucket); the item count is in the header and the ticket is left at zero."""
+    exe = emu_bin("schedule_emu")
+    rng = np.random.default_rng(H + W + B + strips + split_min)
+    TW, TH = (W + 15) // 16, (H + 15) // 16
+    T = TW * TH
+    lens = rng.integers(0, 900, size=T)
+    lens[rng.integers(0, T, size=3)] = 0                     # empty tiles
+    starts = np.concatenate([[0], np.cumsum(lens)[:-1]])
+    ranges = np.stack([starts, starts + lens], 1).astype(np.uint32)
+    nc = rng.integers(0, 1000, size=(B, H, W)).astype(np.uint32)
+    walks_in = rng.integers(0, 1200, size=(B, T)).astype(np.uint32)
+    payload = np.array([H, W, B, strips, split_min, allow, int(have_walks)], np.int32).tobytes() + \
+        ranges.tobytes() + nc.tobytes() + walks_in.tobytes()
+    raw = _run(exe, tmp_path, payload)
+    assert int(np.frombuffer(raw[-4:], np.int32)[0]) == 0
+    hdr = np.frombuffer(raw, np.uint32, count=4)
+    walks_out = np.frombuffer(raw, np.uint32, count=B * T, offset=16)
+    items = np.frombuffer(raw, np.uint32, count=4 * 2 * B * T * strips, offset=16 + 4 * B * T).reshape(-1, 4)
+    if have_walks:
+        walks = walks_in.reshape(-1).astype(np.int64)
+    else:
+        walks = np.zeros(B * T, np.int64)
+        for b in range(B):
+            for t in range(T):
+                ty, tx = divmod(t, TW)
+                mx = int(nc[b, ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16].max())
+                walks[b * T + t] = min(mx, int(lens[t]))
+        assert np.array_equal(walks_out.astype(np.int64), walks)
+    expect = []
+    for u in range(B * T * strips):
+        bt, strip = divmod(u, strips)
+        w = int(walks[bt])
+        nb = (w + 15) // 16
+        if nb == 0:
+            continue
+        if allow and split_min >= 0 and nb > split_min:
+            m = 16 * (nb // 2)
+            expect += [(bt, strip | 0x80000000, 0, m), (bt, strip, m, w)]
+        else:
+            expect.append((bt, strip, 0, w))
+    n_items = int(hdr[1])
+    assert n_items == len(expect) and hdr[0] == 0
+    got = [tuple(int(x) for x in r) for r in items[:n_items]]
+    assert sorted(got) == sorted(expect)
+    cost = [min((r[3] - r[2] + 15) // 16, 255) for r in got]
+    assert all(a >= b for a, b in zip(cost, cost[1:]))
