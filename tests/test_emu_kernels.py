@@ -531,3 +531,44 @@ def test_backward_schedule_logic(emu_bin, tmp_path, H, W, B, strips, split_min, 
     assert sorted(got) == sorted(expect)
     cost = [min((r[3] - r[2] + 15) // 16, 255) for r in got]
     assert all(a >= b for a, b in zip(cost, cost[1:]))
+
+
+@pytest.mark.parametrize("n,H,W,K,B,hidden,seed", [(200, 45, 180, 3, 2, 16, 62)])
+def test_fp32_training_step_chain(emu_bin, tmp_path, n, H, W, K, B, hidden, seed):
+    """One FP32 training step, every stage a library kernel under the host shim, each reading what
+    the previous wrote (projection, bin/sort, network, compositing, L2 loss and the three
+    backward passes), against the oracle's whole pipeline: the loss and every spectrum within
+    1e-3 relative, every parameter gradient within 5e-3 relative L2 (the GPU tests' bars for the
+    same chain)."""
+    from oracle import pipeline as opl
+    from paper_2511_22793_gb300 import synth
+
+    exe = emu_bin("chain_emu")
+    sc = synth.make_scene(n, seed=seed)
+    mlp = synth.make_mlp(hidden, seed=3)
+    tx = synth.make_tx(B, seed=seed + 1)
+    view, band = synth.View(H=H, W=W), synth.Band(K=K)
+    rng = np.random.default_rng(seed + 2)
+    target = 0.05 * (rng.normal(size=(B, H * W, K)) + 1j * rng.normal(size=(B, H * W, K)))
+    t_dev = target.reshape(B, H, W, K).transpose(0, 3, 1, 2)
+    t32 = np.stack([t_dev.real, t_dev.imag], -1).astype(np.float32)
+    payload = np.array([n, H, W, K, hidden, B], np.int32).tobytes() + np.array([band.f_c, band.df]).tobytes() + \
+        b"".join(np.ascontiguousarray(a).tobytes() for a in sc.arrays()) + \
+        b"".join(a.tobytes() for a in mlp.arrays()) + tx.tobytes() + t32.tobytes()
+    raw = _run(exe, tmp_path, payload, timeout=300)
+    assert int(np.frombuffer(raw[-4:], np.int32)[0]) == 0
+    f = np.frombuffer(raw[:-8], np.float32).astype(np.float64)
+    names = ["means", "log_scales", "quats", "opacity_logit", "latent", "W1", "b1", "W2", "b2", "W3", "b3"]
+    sizes = [1, 2 * B * K * H * W] + [a.size for a in sc.arrays()] + [a.size for a in mlp.arrays()]
+    parts = np.split(f, np.cumsum(sizes)[:-1])
+    loss, spec = float(parts[0][0]), parts[1].reshape(B, K, H, W, 2)
+    t64 = t32.astype(np.float64)
+    target64 = (t64[..., 0] + 1j * t64[..., 1]).transpose(0, 2, 3, 1).reshape(B, H * W, K)
+    ref_loss, ref = opl.loss_and_grad(sc, mlp, view, band, tx, target64)
+    assert abs(loss - ref_loss) <= 1e-3 * ref_loss
+    z = (spec[..., 0] + 1j * spec[..., 1]).transpose(0, 2, 3, 1).reshape(B, H * W, K)
+    for b in range(B):
+        assert np.linalg.norm(z[b] - ref["z"][b]) <= 1e-3 * np.linalg.norm(ref["z"][b])
+    for k, got in zip(names, parts[2:]):
+        want = ref[k].reshape(-1)
+        assert np.linalg.norm(got - want) <= 5e-3 * np.linalg.norm(want), k
