@@ -40,7 +40,7 @@ extern "C" {
 #define GSPARC_ERR_WORKSPACE (-2) /* workspace smaller than the query returned    */
 #define GSPARC_ERR_CUDA (-3)      /* a CUDA runtime call or launch failed         */
 #define GSPARC_ERR_TIMEOUT (-4)   /* a bounded device-side wait gave up           */
-#define GSPARC_ERR_CAPACITY (-5)  /* more (Gaussian, tile) pairs than capacity    */
+#define GSPARC_ERR_CAPACITY (-5)  /* more pairs (or densified rows) than capacity */
 #define GSPARC_ERR_TOO_LARGE (-6) /* sizes above a fixed-scratch entry point's cap */
 
 /* ---- fixed sizes ------------------------------------------------------- */
