@@ -18,7 +18,7 @@ extern "C" const char* gsparc_strerror(int status) {
         case GSPARC_ERR_WORKSPACE: return "workspace too small";
         case GSPARC_ERR_CUDA: return "CUDA error";
         case GSPARC_ERR_TIMEOUT: return "bounded device wait expired";
-        case GSPARC_ERR_CAPACITY: return "pair capacity exceeded";
+        case GSPARC_ERR_CAPACITY: return "capacity exceeded (tile pairs or densified rows)";
         case GSPARC_ERR_TOO_LARGE: return "size above the fixed scratch limit";
         default: return "unknown status";
     }
