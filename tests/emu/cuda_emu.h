@@ -1,14 +1,16 @@
-// Test-only host shim that runs a CUDA kernel's source on CPU threads, one std::thread per
-// CUDA thread, blocks one after another.  It exists to check the logic of the library's plain
-// (non-tensor-core) kernels on a machine without a GPU: index arithmetic, warp shuffles,
-// block barriers and the order of sums.  It is not a CUDA implementation: no memory model
-// beyond sequential consistency, no timing, and nothing of the library links against it.
+// Test-only host shim that runs a CUDA kernel's source on the CPU: every CUDA thread of a block
+// is a fiber (ucontext) of one host thread, switched at barriers and warp exchanges; blocks run
+// one after another.  It exists to check the logic of the library's plain (non-tensor-core)
+// kernels on a machine without a GPU: index arithmetic, warp shuffles, block barriers and the
+// order of sums.  It is not a CUDA implementation: no memory model beyond sequential
+// consistency, no timing, and nothing of the library links against it.
 //
 // Semantics kept from CUDA: __syncthreads() waits for every thread of the block that has not
-// exited (exited threads leave the barrier's count); __shfl_*_sync exchange values among the
-// 32 lanes of a warp and record a violation when a lane of the warp has already exited;
-// atomics are atomic.  `__shared__` variables are function statics, valid because one block
-// runs at a time.
+// exited (exited threads leave the barrier's count); __shfl_*_sync, votes and __syncwarp
+// exchange among the lanes of a warp and record a violation when a lane of the warp has
+// already exited; a barrier that can never complete (threads waiting at different barriers)
+// records a violation and ends the block.  `__shared__` variables are function statics, valid
+// because one block runs at a time.
 #pragma once
 
 #define GSPARC_HOST_SHIM 1
@@ -17,11 +19,12 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <ucontext.h>
+
 #include <algorithm>
 #include <atomic>
-#include <barrier>
+#include <functional>
 #include <memory>
-#include <thread>
 #include <vector>
 
 using std::max;   // CUDA's device min / max overloads
@@ -31,7 +34,7 @@ struct emu_dim3 {
     unsigned x = 1, y = 1, z = 1;
 };
 
-inline thread_local emu_dim3 threadIdx, blockIdx;
+inline emu_dim3 threadIdx, blockIdx;
 
 struct alignas(8) float2 {
     float x, y;
@@ -106,50 +109,69 @@ inline void __stcs(T* p, T v) {
 }
 inline void __threadfence() { std::atomic_thread_fence(std::memory_order_seq_cst); }
 
-struct EmuWarp {
-    std::unique_ptr<std::barrier<>> bar;
-    std::atomic<int> alive{0};
-    uint64_t slot[32];
+enum EmuState { kEmuRun = 0, kEmuAtBlockBarrier = 1, kEmuAtWarpBarrier = 2, kEmuDone = 3 };
+
+struct EmuFiber {
+    ucontext_t ctx;
+    std::unique_ptr<char[]> stack;
+    int state = kEmuRun;
+    int votes = 0;   // __syncthreads_or calls made
 };
 
 struct EmuBlockState {
-    std::unique_ptr<std::barrier<>> bar;
-    std::vector<std::unique_ptr<EmuWarp>> warps;
-    std::atomic<int> vote[3] = {0, 0, 0};  // __syncthreads_or, see below
+    std::vector<EmuFiber> fib;
+    ucontext_t sched;
+    int cur = -1;
+    std::vector<uint64_t> slot;   // warp exchange slots, 32 per warp
+    int vote[3] = {0, 0, 0};      // __syncthreads_or, see below
+    std::function<void()> body;
 };
 
 inline EmuBlockState* g_emu_block = nullptr;
 inline std::atomic<int> g_emu_violations{0};
 
-inline void __syncthreads() { g_emu_block->bar->arrive_and_wait(); }
+inline void emu_wait(int state) {
+    EmuBlockState& b = *g_emu_block;
+    b.fib[b.cur].state = state;
+    swapcontext(&b.fib[b.cur].ctx, &b.sched);
+}
 
-// Call c of a block uses slot c % 3; between its two barriers every thread clears slot
+inline int emu_warp_alive(int w) {
+    EmuBlockState& b = *g_emu_block;
+    int n = 0;
+    const int hi = std::min<int>((int)b.fib.size(), 32 * (w + 1));
+    for (int t = 32 * w; t < hi; ++t) n += b.fib[t].state != kEmuDone;
+    return n;
+}
+
+inline void __syncthreads() { emu_wait(kEmuAtBlockBarrier); }
+
+// Call c of a thread uses slot c % 3; between its two barriers every thread clears slot
 // (c + 1) % 3, which nobody reads then and nobody sets before the second barrier.
-inline thread_local int tl_vote_calls = 0;
 inline int __syncthreads_or(int pred) {
-    EmuBlockState& st = *g_emu_block;
-    const int c = tl_vote_calls++;
-    if (pred) st.vote[c % 3].fetch_or(1);
-    st.bar->arrive_and_wait();
-    const int r = st.vote[c % 3].load();
-    st.vote[(c + 1) % 3].store(0);
-    st.bar->arrive_and_wait();
+    EmuBlockState& b = *g_emu_block;
+    const int c = b.fib[b.cur].votes++;
+    if (pred) b.vote[c % 3] = 1;
+    __syncthreads();
+    const int r = b.vote[c % 3];
+    b.vote[(c + 1) % 3] = 0;
+    __syncthreads();
     return r;
 }
 
 template <typename T, typename F>
 inline T emu_exchange(T v, F src_of) {
     static_assert(sizeof(T) <= 8, "shuffle of a value wider than 64 bits");
-    const int t = (int)threadIdx.x, w = t / 32, l = t % 32;
-    EmuWarp& wp = *g_emu_block->warps[w];
-    if (wp.alive.load() != 32) g_emu_violations.fetch_add(1);
+    EmuBlockState& b = *g_emu_block;
+    const int t = b.cur, w = t / 32, l = t % 32;
+    if (emu_warp_alive(w) != 32) g_emu_violations.fetch_add(1);
     uint64_t bits = 0;
     memcpy(&bits, &v, sizeof(T));
-    wp.slot[l] = bits;
-    wp.bar->arrive_and_wait();
+    b.slot[32 * w + l] = bits;
+    emu_wait(kEmuAtWarpBarrier);
     const int src = src_of(l);
-    uint64_t got = wp.slot[(src >= 0 && src < 32) ? src : l];
-    wp.bar->arrive_and_wait();
+    const uint64_t got = b.slot[32 * w + ((src >= 0 && src < 32) ? src : l)];
+    emu_wait(kEmuAtWarpBarrier);
     T r;
     memcpy(&r, &got, sizeof(T));
     return r;
@@ -159,15 +181,15 @@ inline T emu_exchange(T v, F src_of) {
 template <typename T>
 inline void emu_gather(T v, T out[32]) {
     static_assert(sizeof(T) <= 8, "value wider than 64 bits");
-    const int t = (int)threadIdx.x, w = t / 32, l = t % 32;
-    EmuWarp& wp = *g_emu_block->warps[w];
-    if (wp.alive.load() != 32) g_emu_violations.fetch_add(1);
+    EmuBlockState& b = *g_emu_block;
+    const int t = b.cur, w = t / 32, l = t % 32;
+    if (emu_warp_alive(w) != 32) g_emu_violations.fetch_add(1);
     uint64_t bits = 0;
     memcpy(&bits, &v, sizeof(T));
-    wp.slot[l] = bits;
-    wp.bar->arrive_and_wait();
-    for (int k = 0; k < 32; ++k) memcpy(&out[k], &wp.slot[k], sizeof(T));
-    wp.bar->arrive_and_wait();
+    b.slot[32 * w + l] = bits;
+    emu_wait(kEmuAtWarpBarrier);
+    for (int k = 0; k < 32; ++k) memcpy(&out[k], &b.slot[32 * w + k], sizeof(T));
+    emu_wait(kEmuAtWarpBarrier);
 }
 
 inline int __any_sync(unsigned, int pred) {
@@ -198,9 +220,9 @@ inline T __reduce_max_sync(unsigned, T v) {
     return *std::max_element(all, all + 32);
 }
 inline void __syncwarp(unsigned = 0xffffffffu) {
-    EmuWarp& wp = *g_emu_block->warps[(int)threadIdx.x / 32];
-    if (wp.alive.load() != 32) g_emu_violations.fetch_add(1);
-    wp.bar->arrive_and_wait();
+    EmuBlockState& b = *g_emu_block;
+    if (emu_warp_alive(b.cur / 32) != 32) g_emu_violations.fetch_add(1);
+    emu_wait(kEmuAtWarpBarrier);
 }
 
 template <typename T>
@@ -256,43 +278,85 @@ inline T atomicCAS(T* p, T cmp, T val) {
     return cmp;
 }
 
-// Runs kernel(args...) over grid x block (1D blocks, a 3D grid), with
-// `smem_bytes` of dynamic shared memory.
+// Runs kernel(args...) over grid x block (1D blocks, a 3D grid), with `smem_bytes` of dynamic
+// shared memory.  Within a block the fibers run round-robin until each waits or exits; a
+// barrier is released when every thread that has not exited waits at it (for a warp barrier,
+// every such lane of the warp).
+inline void emu_fiber_entry() {
+    EmuBlockState& b = *g_emu_block;
+    b.body();
+    b.fib[b.cur].state = kEmuDone;   // returns to the scheduler through uc_link
+}
+
 template <typename K, typename... A>
 inline void emu_launch_smem(emu_dim3 grid, unsigned threads, size_t smem_bytes, K kernel, A... args) {
+    constexpr size_t kStack = 256 * 1024;
     std::vector<uint64_t> dyn((smem_bytes + 7) / 8 + 2);   // 16-byte aligned start below
     g_emu_dyn_smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dyn.data()) + 15) & ~uintptr_t(15));
     gridDim = grid;
     blockDim = emu_dim3{threads, 1, 1};
+    const int nw = (int)((threads + 31) / 32);
     for (unsigned bz = 0; bz < grid.z; ++bz)
-    for (unsigned by = 0; by < grid.y; ++by)
-        for (unsigned bx = 0; bx < grid.x; ++bx) {
-            EmuBlockState st;
-            st.bar = std::make_unique<std::barrier<>>((std::ptrdiff_t)threads);
-            for (unsigned w = 0; w < (threads + 31) / 32; ++w) {
-                // a last, partial warp has fewer lanes: a full-warp shuffle there counts as a violation
-                const int lanes = (int)std::min(32u, threads - 32 * w);
-                auto wp = std::make_unique<EmuWarp>();
-                wp->bar = std::make_unique<std::barrier<>>(lanes);
-                wp->alive = lanes;
-                st.warps.push_back(std::move(wp));
+        for (unsigned by = 0; by < grid.y; ++by)
+            for (unsigned bx = 0; bx < grid.x; ++bx) {
+                EmuBlockState st;
+                st.fib.resize(threads);
+                st.slot.assign(32 * (size_t)nw, 0);
+                st.body = [&] { kernel(args...); };
+                blockIdx = emu_dim3{bx, by, bz};
+                for (unsigned t = 0; t < threads; ++t) {
+                    EmuFiber& f = st.fib[t];
+                    f.stack.reset(new char[kStack]);
+                    getcontext(&f.ctx);
+                    f.ctx.uc_stack.ss_sp = f.stack.get();
+                    f.ctx.uc_stack.ss_size = kStack;
+                    f.ctx.uc_link = &st.sched;
+                    makecontext(&f.ctx, emu_fiber_entry, 0);
+                }
+                g_emu_block = &st;
+                for (;;) {
+                    for (unsigned t = 0; t < threads; ++t) {
+                        if (st.fib[t].state != kEmuRun) continue;
+                        st.cur = (int)t;
+                        threadIdx = emu_dim3{t, 0, 0};
+                        swapcontext(&st.sched, &st.fib[t].ctx);
+                    }
+                    // release the barriers that every live participant has reached
+                    bool alive = false, all_block = true, released = false;
+                    for (unsigned t = 0; t < threads; ++t) {
+                        const int s = st.fib[t].state;
+                        if (s == kEmuDone) continue;
+                        alive = true;
+                        if (s != kEmuAtBlockBarrier) all_block = false;
+                    }
+                    if (!alive) break;
+                    if (all_block) {
+                        for (auto& f : st.fib)
+                            if (f.state == kEmuAtBlockBarrier) f.state = kEmuRun;
+                        released = true;
+                    }
+                    for (int w = 0; w < nw && !all_block; ++w) {
+                        const unsigned lo = 32u * w, hi = std::min(threads, 32u * (w + 1));
+                        bool any = false, all_warp = true;
+                        for (unsigned t = lo; t < hi; ++t) {
+                            const int s = st.fib[t].state;
+                            if (s == kEmuDone) continue;
+                            any = true;
+                            if (s != kEmuAtWarpBarrier) all_warp = false;
+                        }
+                        if (any && all_warp) {
+                            for (unsigned t = lo; t < hi; ++t)
+                                if (st.fib[t].state == kEmuAtWarpBarrier) st.fib[t].state = kEmuRun;
+                            released = true;
+                        }
+                    }
+                    if (!released) {   // threads wait at barriers that can never complete
+                        g_emu_violations.fetch_add(1);
+                        break;
+                    }
+                }
+                g_emu_block = nullptr;
             }
-            g_emu_block = &st;
-            std::vector<std::thread> pool;
-            pool.reserve(threads);
-            for (unsigned t = 0; t < threads; ++t)
-                pool.emplace_back([&, t, bx, by, bz] {
-                    threadIdx = emu_dim3{t, 0, 0};
-                    blockIdx = emu_dim3{bx, by, bz};
-                    kernel(args...);
-                    EmuWarp& wp = *st.warps[t / 32];
-                    wp.alive.fetch_sub(1);
-                    wp.bar->arrive_and_drop();
-                    st.bar->arrive_and_drop();
-                });
-            for (auto& th : pool) th.join();
-            g_emu_block = nullptr;
-        }
     g_emu_dyn_smem = nullptr;
 }
 

@@ -203,18 +203,19 @@ def _binsort_run(exe, tmp_path, rec, H, W, cap):
 
 
 @pytest.mark.parametrize("n,H,W,seed,case", [(1, 90, 360, 1, "plain"), (17, 90, 360, 2, "plain"),
-                                             (1000, 90, 360, 3, "plain"), (800, 180, 720, 5, "plain"),
+                                             (1000, 90, 360, 3, "plain"), (20_011, 90, 360, 4, "plain"),
+                                             (5000, 180, 720, 5, "plain"),
                                              (3000, 45, 180, 6, "plain"), (1500, 45, 180, 14, "three_depths"),
                                              (1500, 45, 180, 17, "one_depth"),
                                              (2000, 90, 360, 12, "overflow"), (400, 90, 360, 16, "culled")])
 def test_binsort_kernels_logic(emu_bin, tmp_path, n, H, W, seed, case):
     """k_tile_count, k_tile_emit and k_tile_sort (the library's source under the host shim)
-    against the oracle's stable (tile, r, index) sort, bit for bit: ragged grids, 1 to 3,000
+    against the oracle's stable (tile, r, index) sort, bit for bit: ragged grids, 1 to 20,011
     records, the shared-memory distribution sort, three distinct depths and a single depth (tiles
     whose depth sub-buckets exceed 64 keys take the radix path; ties by index), a capacity below
-    the pair count, every record culled.  Larger scenes and buckets above the
-    shared-memory capacity are the GPU tests' (the shim runs a warp vote as two thread
-    barriers, which makes those sizes slow on the CPU)."""
+    the pair count, every record culled.  Buckets above the shared-memory capacity (the same
+    radix code on larger buckets) are the GPU tests': every warp vote is a scheduling round in
+    the shim, which makes those sizes slow on the CPU."""
     from oracle import binsort as obs
     from paper_2511_22793_gb300 import synth
 
