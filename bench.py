@@ -470,6 +470,9 @@ def run_ours(args, rank, world, local_rank):
                     "traffic_unit": "bytes per launch (DRAM read + write)",
                     "peak_note": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)"
                                  % (sms, sm_max)}
+        if clocks and clocks.get("sm_mhz"):
+            # the same peak at the median SM clock sampled under load
+            roofline["frac_at_measured_clock"] = achieved / (fp32_peak * float(clocks["sm_mhz"]) / sm_max)
     else:
         roofline = {"kernel": top, "bound": "hbm", "achieved": None,
                     "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s", "frac": None,
