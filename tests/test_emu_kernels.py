@@ -573,3 +573,40 @@ def test_fp32_training_step_chain(emu_bin, tmp_path, n, H, W, K, B, hidden, seed
     for k, got in zip(names, parts[2:]):
         want = ref[k].reshape(-1)
         assert np.linalg.norm(got - want) <= 5e-3 * np.linalg.norm(want), k
+
+
+def test_projection_kernel_edge_cases(emu_bin, tmp_path):
+    """k_project under the host shim on the special positions: inside the near distance
+    (culled: extents -1), exactly at the zenith and next to it (the capped 1/rho), on the
+    +-pi seam, on the horizon; the records that are not culled against the oracle's map."""
+    from oracle import projection as oproj
+    from paper_2511_22793_gb300 import synth
+
+    exe = emu_bin("project_emu")
+    means = np.array([[0.0, 0.05, 0.0], [0.0, 3.0, 0.0], [1e-6, 3.0, 1e-6], [0.0, 1.0, -2.0],
+                      [-1e-5, 1.0, -2.0], [2.0, 0.0, 1.0], [0.03, 0.02, 0.06]], dtype=np.float32)
+    n = means.shape[0]
+    ls = np.full((n, 3), -1.5, np.float32)
+    quats = np.tile(np.array([[1, 0, 0, 0]], np.float32), (n, 1))
+    view = synth.View(H=90, W=360)
+    payload = np.array([n, 90, 360], np.int32).tobytes() + np.array(
+        list(view.rx) + list(view.V) + [view.near], np.float32).tobytes() + means.tobytes() + ls.tobytes() + \
+        quats.tobytes() + np.zeros((n, 8), np.float32).tobytes()
+    raw = _run(exe, tmp_path, payload)
+    assert int(np.frombuffer(raw[-4:], np.int32)[0]) == 0
+    p = np.frombuffer(raw[:-4], np.float32)[:8 * n].reshape(n, 8).astype(np.float64)
+    culled = np.linalg.norm(means.astype(np.float64), axis=1) < view.near
+    assert list(culled) == [True, False, False, False, False, False, True]
+    assert np.all(p[culled, 2] == -1) and np.all(p[culled, 3] == -1)
+    assert np.all(np.isfinite(p[~culled]))
+    assert abs(p[1, 1] - 90.0) < 1e-3 and p[1, 2] >= 180.0        # zenith row, every column
+    assert abs(p[3, 0] - 360.0) < 1e-3 or abs(p[3, 0]) < 1e-3       # on the seam
+    assert abs(p[5, 1]) < 1e-4                                       # on the horizon
+    t = lambda a: torch.tensor(np.asarray(a, np.float64))
+    g = oproj.project(t(means), t(ls), t(quats), view)
+    v = ~culled
+    d = p[v, 0] - g["px"].numpy()[v]
+    assert np.max(np.abs(d - 360 * np.round(d / 360))) < 2e-4
+    assert np.max(np.abs(p[v, 1] - g["py"].numpy()[v])) < 2e-4
+    for j, k in ((2, "ext_x"), (3, "ext_y"), (7, "r")):
+        np.testing.assert_allclose(p[v, j], g[k].numpy()[v], rtol=2e-5)
