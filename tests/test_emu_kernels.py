@@ -610,3 +610,77 @@ def test_projection_kernel_edge_cases(emu_bin, tmp_path):
     assert np.max(np.abs(p[v, 1] - g["py"].numpy()[v])) < 2e-4
     for j, k in ((2, "ext_x"), (3, "ext_y"), (7, "r")):
         np.testing.assert_allclose(p[v, j], g[k].numpy()[v], rtol=2e-5)
+
+
+def _records(g, W):
+    """FP32 projection records [n, 8] from oracle-style per-Gaussian values (extents from the
+    inverse of the conic, q_max = 2 ln 255)."""
+    n = len(g["px"])
+    det = g["cxx"] * g["cyy"] - g["cxy"] ** 2
+    sxx, syy = g["cyy"] / det, g["cxx"] / det
+    rec = np.zeros((n, 8), np.float32)
+    rec[:, 0], rec[:, 1] = g["px"], g["py"]
+    rec[:, 2] = np.where(g["valid"], np.sqrt(2 * np.log(255) * sxx), -1)
+    rec[:, 3] = np.where(g["valid"], np.sqrt(2 * np.log(255) * syy), -1)
+    rec[:, 4], rec[:, 5], rec[:, 6], rec[:, 7] = g["cxx"], g["cxy"], g["cyy"], g["r"]
+    return rec
+
+
+@pytest.mark.parametrize("case", ["coincident", "dense"])
+def test_render_fp32_kernels_termination(emu_bin, tmp_path, case):
+    """k_render_fwd / k_render_bwd under the host shim where compositing stops early: 40
+    coincident Gaussians of alpha 0.3 (the pixel composites 25 of them, then T would fall below
+    1e-4: the oracle's geometric series) and 400 random Gaussians packed into a 32 x 16 image
+    (most pixels terminate, whole CTAs stop fetching); spectra, counts and gradients against
+    the oracle on the same FP32 values."""
+    from oracle import binsort as obs
+    from oracle import render as orender
+
+    exe = emu_bin("render_emu")
+    H, W, K = 16, 32, 4
+    rng = np.random.default_rng(7)
+    if case == "coincident":
+        n = 40
+        g = dict(px=np.full(n, 5.5), py=np.full(n, 5.5), cxx=np.full(n, 0.5), cxy=np.zeros(n),
+                 cyy=np.full(n, 0.5), r=np.linspace(1.0, 2.0, n), valid=np.ones(n, bool))
+        at = dict(sigma=np.full(n, 0.3), a=np.full(n, 0.4), phi0=np.full(n, 0.2), L=np.full(n, 3.0))
+    else:
+        n = 400
+        g = dict(px=rng.uniform(0, W, n), py=rng.uniform(-2, H + 2, n), cxx=rng.uniform(0.05, 0.6, n),
+                 cyy=rng.uniform(0.05, 0.6, n), r=rng.uniform(0.5, 8, n), valid=rng.uniform(size=n) > 0.05)
+        g["cxy"] = rng.uniform(-0.8, 0.8, n) * np.sqrt(g["cxx"] * g["cyy"])
+        at = dict(sigma=rng.uniform(0.02, 0.99, n), a=rng.uniform(0.01, 0.3, n), phi0=rng.normal(size=n),
+                  L=rng.uniform(1, 15, n))
+    rec = _records(g, W)
+    g32 = {k: (np.asarray(v, np.float32).astype(np.float64) if k != "valid" else v) for k, v in g.items()}
+    at32 = {k: np.asarray(v, np.float32).astype(np.float64) for k, v in at.items()}
+    attr = np.stack([at32["a"], at32["phi0"], at32["sigma"], at32["L"]], -1).astype(np.float32)[None]
+    _, ids, ranges = obs.bin_sort(rec, H, W)
+    gz = rng.normal(size=(H * W, K)) + 1j * rng.normal(size=(H * W, K))
+    dspec = np.stack([gz.real, gz.imag], -1).reshape(H, W, K, 2).transpose(2, 0, 1, 3)[None].astype(np.float32)
+    f_c, df = 2.4e9, 1e6
+    payload = np.array([H, W, K, n, 1, len(ids)], np.int32).tobytes() + np.array([f_c, df]).tobytes() + \
+        rec.tobytes() + ranges.astype(np.uint32).tobytes() + ids.astype(np.uint32).tobytes() + attr.tobytes() + \
+        np.ascontiguousarray(dspec).tobytes()
+    raw = _run(exe, tmp_path, payload, timeout=300)
+    assert int(np.frombuffer(raw[-4:], np.int32)[0]) == 0
+    P = H * W
+    spec = np.frombuffer(raw, np.float32, count=2 * K * P).reshape(K, H, W, 2).astype(np.float64)
+    off = 8 * K * P + 4 * P + 4 * P
+    used = np.frombuffer(raw, np.uint32, count=P, offset=off)
+    off += 4 * P
+    dattr = np.frombuffer(raw, np.float32, count=4 * n, offset=off).reshape(n, 4).astype(np.float64)
+    dproj = np.frombuffer(raw, np.float32, count=8 * n, offset=off + 16 * n).reshape(n, 8).astype(np.float64)
+    z = (spec[..., 0] + 1j * spec[..., 1]).transpose(1, 2, 0).reshape(P, K)
+    zo, To, no = orender.render_fwd(g32, at32, H, W, K, f_c, df)
+    assert np.linalg.norm(z - zo) <= 1e-3 * np.linalg.norm(zo)
+    if case == "coincident":
+        assert used[5 * W + 5] == 25 == no[5 * W + 5]
+    else:
+        assert np.mean(To < 1e-3) > 0.3                          # most pixels terminate
+        assert np.mean(used.astype(np.int64) == no) > 0.99
+    ref = orender.render_bwd(g32, at32, H, W, K, f_c, df, gz)
+    for c, col in enumerate((0, 1, 4, 5, 6)):
+        assert np.linalg.norm(dproj[:, col] - ref[:, c]) <= 1e-3 * np.linalg.norm(ref[:, c]), c
+    for c, col in ((5, 2), (6, 0), (7, 1), (8, 3)):
+        assert np.linalg.norm(dattr[:, col] - ref[:, c]) <= 1e-3 * np.linalg.norm(ref[:, c]), c
