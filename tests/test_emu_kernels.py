@@ -135,12 +135,13 @@ def _wrapdiff(a, b, W):
 
 
 @pytest.mark.parametrize("n,H,W,seed,rot", [(3001, 90, 360, 0, False), (777, 180, 720, 4, True),
-                                            (256, 45, 180, 9, False)])
+                                            (256, 45, 180, 9, False), (500, 60, 100, 7, False)])
 def test_projection_kernels_logic(emu_bin, tmp_path, n, H, W, seed, rot):
     """k_project and k_project_bwd (the library's source under the host shim) against the oracle's
     projection and its vector-Jacobian product: positions within a few FP32 ulps of W, extents
     and distances 2e-5 relative, the conic 1e-4 of its scale, and the gradients of means,
-    log-scales and quaternions 1e-3 relative L2 (the GPU tests' bars)."""
+    log-scales and quaternions 1e-3 relative L2 (the GPU tests' bars); a 60 x 100 grid, where
+    the azimuth and elevation scales differ, among the cases."""
     from oracle import projection as oproj
     from paper_2511_22793_gb300 import synth
 

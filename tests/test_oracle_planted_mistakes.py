@@ -59,7 +59,7 @@ def test_planted_renderer_mistake_fails_its_pin(tmp_path, monkeypatch, old, new,
 def test_planted_dilation_mistake_fails_its_pin(monkeypatch):
     monkeypatch.setattr(P, "DILATION", 0.0)
     with pytest.raises(AssertionError):
-        TP.test_isotropic_closed_form_random_directions()
+        TP.test_isotropic_closed_form_random_directions(90, 360)
 
 
 def test_planted_network_input_mistake_fails_its_pin(monkeypatch):
@@ -151,3 +151,22 @@ def test_planted_densify_mistake_fails_its_pin(monkeypatch, old, new, pin):
     monkeypatch.setattr(TD, "D", _patched_module(monkeypatch, DN, old, new))
     with pytest.raises(AssertionError):
         pin()
+
+
+@pytest.mark.parametrize("old,new,pin", [
+    # the azimuth and elevation scales of the Jacobian swapped (equal on the W = 4H grids)
+    ("    sx = W / (2.0 * math.pi)\n    sy = 2.0 * H / math.pi\n", "    sy = W / (2.0 * math.pi)\n    sx = 2.0 * H / math.pi\n",
+     lambda: TP.test_jacobian_matches_central_differences(60, 100)),
+])
+def test_planted_projection_scale_mistake_fails_its_pin(monkeypatch, old, new, pin):
+    monkeypatch.setattr(TP, "P", _patched_module(monkeypatch, P, old, new))
+    with pytest.raises(AssertionError):
+        pin()
+
+
+def test_planted_spectrum_loss_weight_mistake_fails_its_pin(monkeypatch):
+    # the weights of L1 and SSIM in Eq. 4 exchanged
+    monkeypatch.setattr(TS, "S", _patched_module(monkeypatch, S, "    return (1.0 - lam) * l1 + lam * (1.0 - ssim)",
+                                                 "    return lam * l1 + (1.0 - lam) * (1.0 - ssim)"))
+    with pytest.raises(AssertionError):
+        TS.test_l1_part_by_hand()

@@ -47,11 +47,13 @@ def test_isotropic_footprint_golden():
     np.testing.assert_allclose(out["syy"].numpy(), g[:, 6], rtol=1e-13)
 
 
-def test_isotropic_closed_form_random_directions():
+@pytest.mark.parametrize("H,W", [(90, 360), (60, 100)])
+def test_isotropic_closed_form_random_directions(H, W):
     """Sigma' = diag(s^2 s_x^2/rho^2, s^2 s_y^2/r^2) + 0.3 I for any direction
-    and any rotation quaternion (an isotropic Sigma ignores the rotation)."""
+    and any rotation quaternion (an isotropic Sigma ignores the rotation).  With W = 4H (the
+    1-degree grids) s_x = s_y; the 60 x 100 grid tells the two scales apart."""
     rng = np.random.default_rng(11)
-    n, H, W = 200, 90, 360
+    n = 200
     means = rng.uniform(-5, 5, (n, 3))
     means[:, 1] = rng.uniform(0.2, 5, n)
     s = np.exp(rng.normal(-1.5, 0.5, n))
@@ -67,17 +69,18 @@ def test_isotropic_closed_form_random_directions():
     np.testing.assert_allclose(out["sxy"].numpy(), 0.0, atol=1e-9 * (s * s * sx * sy).max())
 
 
-def test_jacobian_matches_central_differences():
+@pytest.mark.parametrize("H,W", [(90, 360), (60, 100)])
+def test_jacobian_matches_central_differences(H, W):
     rng = np.random.default_rng(12)
     xp = rng.uniform(-5, 5, (64, 3))
     xp[:, 1] = rng.uniform(0.1, 5, 64)
-    J = P.map_jacobian(torch.tensor(xp), 90, 360).numpy()
+    J = P.map_jacobian(torch.tensor(xp), H, W).numpy()
     h = 1e-6
     for c in range(3):
         e = np.zeros(3)
         e[c] = h
-        pp = P.equirect_map(torch.tensor(xp + e), 90, 360)
-        pm = P.equirect_map(torch.tensor(xp - e), 90, 360)
+        pp = P.equirect_map(torch.tensor(xp + e), H, W)
+        pm = P.equirect_map(torch.tensor(xp - e), H, W)
         dpx = (pp[0] - pm[0]).numpy() / (2 * h)
         dpy = (pp[1] - pm[1]).numpy() / (2 * h)
         np.testing.assert_allclose(J[:, 0, c], dpx, rtol=1e-6, atol=1e-6)
