@@ -3,7 +3,7 @@
 Each .cu file under csrc/ is compiled to an object in parallel, then the
 objects are linked into one shared library next to this file.  Only the
 CUDA runtime is linked (statically, nvcc's default), so the library needs
-nothing beyond the driver at load time.
+nothing beyond the CUDA driver at load time.
 """
 from __future__ import annotations
 
