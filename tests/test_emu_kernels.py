@@ -685,3 +685,53 @@ def test_render_fp32_kernels_termination(emu_bin, tmp_path, case):
         assert np.linalg.norm(dproj[:, col] - ref[:, c]) <= 1e-3 * np.linalg.norm(ref[:, c]), c
     for c, col in ((5, 2), (6, 0), (7, 1), (8, 3)):
         assert np.linalg.norm(dattr[:, col] - ref[:, c]) <= 1e-3 * np.linalg.norm(ref[:, c]), c
+
+
+def test_render_fp32_kernel_skips_ids_outside_the_scene(emu_bin, tmp_path):
+    """An id past the scene in a tile list (inconsistent inputs) is skipped: k_render_fwd under
+    the host shim gives the spectrum of the list without it, and k_render_bwd no gradient to
+    anything else than the oracle's."""
+    from oracle import binsort as obs
+    from oracle import render as orender
+
+    exe = emu_bin("render_emu")
+    H, W, K, n = 16, 32, 2, 120
+    rng = np.random.default_rng(9)
+    g = dict(px=rng.uniform(0, W, n), py=rng.uniform(0, H, n), cxx=rng.uniform(0.05, 0.6, n),
+             cyy=rng.uniform(0.05, 0.6, n), r=rng.uniform(0.5, 8, n), valid=np.ones(n, bool))
+    g["cxy"] = rng.uniform(-0.8, 0.8, n) * np.sqrt(g["cxx"] * g["cyy"])
+    at = dict(sigma=rng.uniform(0.02, 0.9, n), a=rng.uniform(0.01, 0.3, n), phi0=rng.normal(size=n),
+              L=rng.uniform(1, 15, n))
+    rec = _records(g, W)
+    g32 = {k: (np.asarray(v, np.float32).astype(np.float64) if k != "valid" else v) for k, v in g.items()}
+    at32 = {k: np.asarray(v, np.float32).astype(np.float64) for k, v in at.items()}
+    attr = np.stack([at32["a"], at32["phi0"], at32["sigma"], at32["L"]], -1).astype(np.float32)[None]
+    _, ids, ranges = obs.bin_sort(rec, H, W)
+    # one id past the scene after the third entry of every nonempty list
+    new_ids, new_ranges, pos = [], np.zeros_like(ranges), 0
+    for t in range(ranges.shape[0]):
+        lo, hi = ranges[t]
+        lst = list(ids[lo:hi])
+        if lst:
+            lst.insert(min(3, len(lst)), n + 7)
+        new_ranges[t] = (pos, pos + len(lst)) if lst else (0, 0)
+        new_ids += lst
+        pos += len(lst)
+    new_ids = np.array(new_ids, np.uint32)
+    gz = rng.normal(size=(H * W, K)) + 1j * rng.normal(size=(H * W, K))
+    dspec = np.stack([gz.real, gz.imag], -1).reshape(H, W, K, 2).transpose(2, 0, 1, 3)[None].astype(np.float32)
+    f_c, df = 2.4e9, 1e6
+    payload = np.array([H, W, K, n, 1, len(new_ids)], np.int32).tobytes() + np.array([f_c, df]).tobytes() + \
+        rec.tobytes() + new_ranges.astype(np.uint32).tobytes() + new_ids.tobytes() + attr.tobytes() + \
+        np.ascontiguousarray(dspec).tobytes()
+    raw = _run(exe, tmp_path, payload, timeout=300)
+    assert int(np.frombuffer(raw[-4:], np.int32)[0]) == 0
+    P = H * W
+    spec = np.frombuffer(raw, np.float32, count=2 * K * P).reshape(K, H, W, 2).astype(np.float64)
+    off = 8 * K * P + 12 * P
+    dattr = np.frombuffer(raw, np.float32, count=4 * n, offset=off).reshape(n, 4).astype(np.float64)
+    z = (spec[..., 0] + 1j * spec[..., 1]).transpose(1, 2, 0).reshape(P, K)
+    zo, _, _ = orender.render_fwd(g32, at32, H, W, K, f_c, df)
+    assert np.linalg.norm(z - zo) <= 1e-3 * np.linalg.norm(zo)
+    ref = orender.render_bwd(g32, at32, H, W, K, f_c, df, gz)
+    assert np.linalg.norm(dattr[:, 0] - ref[:, 6]) <= 1e-3 * np.linalg.norm(ref[:, 6])
