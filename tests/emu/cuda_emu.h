@@ -16,6 +16,7 @@
 #define GSPARC_HOST_SHIM 1
 
 #include <math.h>
+#include <stdlib.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -291,8 +292,12 @@ inline void emu_fiber_entry() {
 template <typename K, typename... A>
 inline void emu_launch_smem(emu_dim3 grid, unsigned threads, size_t smem_bytes, K kernel, A... args) {
     constexpr size_t kStack = 256 * 1024;
-    std::vector<uint64_t> dyn((smem_bytes + 7) / 8 + 2);   // 16-byte aligned start below
-    g_emu_dyn_smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dyn.data()) + 15) & ~uintptr_t(15));
+    // exactly the bytes asked for (rounded up to the 16-byte alignment), so that the sanitizer
+    // sees an access past them
+    const size_t dyn_bytes = smem_bytes ? (smem_bytes + 15) / 16 * 16 : 16;
+    std::unique_ptr<unsigned char, void (*)(void*)> dyn(static_cast<unsigned char*>(aligned_alloc(16, dyn_bytes)),
+                                                         free);
+    g_emu_dyn_smem = dyn.get();
     gridDim = grid;
     blockDim = emu_dim3{threads, 1, 1};
     const int nw = (int)((threads + 31) / 32);
