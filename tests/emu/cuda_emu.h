@@ -283,6 +283,16 @@ inline T atomicCAS(T* p, T cmp, T val) {
 // shared memory.  Within a block the fibers run round-robin until each waits or exits; a
 // barrier is released when every thread that has not exited waits at it (for a warp barrier,
 // every such lane of the warp).
+// EMU_ORDER=reverse runs each sweep from the last thread to the first: a read that is missing
+// its barrier after another thread's write sees the stale value in one of the two orders.
+inline bool emu_reverse_order() {
+    static const bool rev = [] {
+        const char* e = getenv("EMU_ORDER");
+        return e && strcmp(e, "reverse") == 0;
+    }();
+    return rev;
+}
+
 inline void emu_fiber_entry() {
     EmuBlockState& b = *g_emu_block;
     b.body();
@@ -320,7 +330,8 @@ inline void emu_launch_smem(emu_dim3 grid, unsigned threads, size_t smem_bytes, 
                 }
                 g_emu_block = &st;
                 for (;;) {
-                    for (unsigned t = 0; t < threads; ++t) {
+                    for (unsigned k = 0; k < threads; ++k) {
+                        const unsigned t = emu_reverse_order() ? threads - 1 - k : k;
                         if (st.fib[t].state != kEmuRun) continue;
                         st.cur = (int)t;
                         threadIdx = emu_dim3{t, 0, 0};

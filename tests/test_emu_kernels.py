@@ -741,3 +741,26 @@ def test_render_fp32_kernel_skips_ids_outside_the_scene(emu_bin, tmp_path):
     assert np.linalg.norm(z - zo) <= 1e-3 * np.linalg.norm(zo)
     ref = orender.render_bwd(g32, at32, H, W, K, f_c, df, gz)
     assert np.linalg.norm(dattr[:, 0] - ref[:, 6]) <= 1e-3 * np.linalg.norm(ref[:, 6])
+
+
+
+@pytest.mark.parametrize("name,args", [
+    ("test_confidence_kernel_logic", (37, 32)),
+    ("test_densify_kernels_logic", (257, 16, 2, 0.5, 2)),
+    ("test_projection_kernels_logic", (256, 45, 180, 9, False)),
+    ("test_binsort_kernels_logic", (1500, 45, 180, 17, "one_depth")),
+    ("test_binsort_kernels_logic", (1000, 90, 360, 3, "plain")),
+    ("test_render_fp32_kernels_logic", (150, 45, 180, 1, 1, 43)),
+    ("test_render_fp32_kernels_termination", ("dense",)),
+    ("test_attribute_network_fp32_kernels_logic", (130, 2, 8, 52)),
+    ("test_emission_kernels_logic", (40, 8, 9, False)),
+    ("test_spectrum_loss_kernels_logic", (1, 2, 16, 16)),
+    ("test_heads_loss_and_adam_kernels_logic", (2, 3, 17, 23, 3001, 700, 1)),
+    ("test_backward_schedule_logic", (45, 180, 2, 1, 3, 1, False)),
+])
+def test_reverse_thread_order(emu_bin, tmp_path, monkeypatch, name, args):
+    """The same checks with every scheduling sweep of the shim running from the last thread of a
+    block to the first: a read that lacks its barrier after another thread's write sees the
+    stale value in one of the two orders."""
+    monkeypatch.setitem(SAN_ENV, "EMU_ORDER", "reverse")
+    globals()[name](emu_bin, tmp_path, *args)
