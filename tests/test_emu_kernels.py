@@ -356,13 +356,13 @@ def test_attribute_network_fp32_kernels_logic(emu_bin, tmp_path, n, B, hidden, s
 
 
 @pytest.mark.parametrize("n,h,B,inv_d", [(77, 16, 3, True), (50, 64, 2, False), (130, 5, 1, True),
-                                         (40, 8, 9, False)])
+                                         (40, 8, 9, False), (33, 1, 2, True), (45, 33, 2, False)])
 def test_emission_kernels_logic(emu_bin, tmp_path, n, h, B, inv_d):
     """k_emission_fwd and k_emission_bwd (the library's per-Gaussian emission network, under the
     host shim) against the oracle's attributes (1e-5 relative L2 per component) and its
-    vector-Jacobian product (1e-4; the padding of every row untouched): groups of 4 to 32 lanes,
-    two hidden units per lane at width 64, transmitters in several chunks (B = 9 > G = 8), the
-    1/d toggle."""
+    vector-Jacobian product (1e-4; the padding of every row untouched): groups of 1 to 32 lanes,
+    two hidden units per lane at widths 33 and 64 (the second one partly idle at 33),
+    transmitters in several chunks (B = 9 > G = 8), the 1/d toggle."""
     from oracle import emission as E
     from paper_2511_22793_gb300 import synth
 
