@@ -170,3 +170,29 @@ def test_planted_spectrum_loss_weight_mistake_fails_its_pin(monkeypatch):
                                                  "    return lam * l1 + (1.0 - lam) * (1.0 - ssim)"))
     with pytest.raises(AssertionError):
         TS.test_l1_part_by_hand()
+
+
+def test_planted_attribute_output_order_mistake_fails_its_pin(monkeypatch):
+    # phase and opacity read from each other's network output
+    monkeypatch.setattr(TA, "A", _patched_module(
+        monkeypatch, A, "    phi0 = o[:, 1]\n    sigma = torch.sigmoid(opacity_logit + o[:, 2])",
+        "    phi0 = o[:, 2]\n    sigma = torch.sigmoid(opacity_logit + o[:, 1])"))
+    with pytest.raises(AssertionError):
+        TA.test_constant_network_closed_form()
+
+
+def test_planted_channel_loss_gradient_mistake_fails_its_pin(monkeypatch):
+    # the derivative of the squared error without its factor 2
+    monkeypatch.setattr(TC, "C", _patched_module(monkeypatch, CS, "    return loss, 2.0 * d / m",
+                                                 "    return loss, d / m"))
+    with pytest.raises(AssertionError):
+        TC.test_channel_loss_closed_forms_and_gradient()
+
+
+def test_planted_tie_order_mistake_fails_its_pin(monkeypatch):
+    # equal distances ordered by descending Gaussian index
+    monkeypatch.setattr(TB, "B", _patched_module(
+        monkeypatch, B, '    order = np.argsort(keys, kind="stable")',
+        '    keys, vals = keys[::-1], vals[::-1]\n    order = np.argsort(keys, kind="stable")'))
+    with pytest.raises(AssertionError):
+        TB.test_ties_keep_index_order()
