@@ -33,6 +33,47 @@ def test_every_declared_symbol_is_exported(L):
     assert sorted(G.EXPORTS) == names
 
 
+def _declarations():
+    """name -> (return type, [parameter declarations]) of every function in include/gsparc.h."""
+    txt = open(os.path.join(ROOT, "include", "gsparc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    out = {}
+    for m in re.finditer(r"(int32_t|int|const char\s*\*)\s*(gsparc_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", txt):
+        params = [" ".join(p.split()) for p in m.group(3).split(",") if p.strip() and p.strip() != "void"]
+        out[m.group(2)] = (" ".join(m.group(1).split()), params)
+    return out
+
+
+def test_binding_signatures_match_the_header(L):
+    """Every binding's ctypes argument list against the header: the same number of arguments,
+    the same scalar type at every scalar position, a pointer at every pointer position (a
+    pointer to the named struct where the header names one), and the return type."""
+    scalars = {"int32_t": ctypes.c_int32, "int": ctypes.c_int, "int64_t": ctypes.c_int64,
+               "float": ctypes.c_float, "size_t": ctypes.c_size_t}
+    structs = {"gsparc_view": G.View, "gsparc_band": G.Band, "gsparc_mlp": G.MLP,
+               "gsparc_mlp_grad": G.MLPGrad, "gsparc_densify_params": G.DensifyParams,
+               "size_t": ctypes.c_size_t, "float": ctypes.c_float}
+    decls = _declarations()
+    assert sorted(decls) == sorted(G.EXPORTS)
+    for name, (ret, params) in decls.items():
+        fn = getattr(L, name)
+        assert len(fn.argtypes) == len(params), name
+        want_ret = {"int": ctypes.c_int, "int32_t": ctypes.c_int32, "const char *": ctypes.c_char_p,
+                    "const char*": ctypes.c_char_p}[ret]
+        assert fn.restype is want_ret, name
+        for k, (decl, got) in enumerate(zip(params, fn.argtypes)):
+            if "*" not in decl:
+                ctype = decl.rsplit(" ", 1)[0].replace("const ", "")
+                assert got is scalars[ctype], (name, k, decl, got)
+                continue
+            base = decl.split("*")[0].replace("const ", "").strip()
+            if got is ctypes.c_void_p:
+                assert base not in ("gsparc_view", "gsparc_band", "gsparc_mlp", "gsparc_mlp_grad",
+                                    "gsparc_densify_params"), (name, k, decl)
+            else:
+                assert getattr(got, "_type_", None) is structs[base], (name, k, decl, got)
+
+
 def test_strerror_and_tiles(L):
     assert G.strerror(G.GSPARC_ERR_TIMEOUT) == "bounded device wait expired"
     assert G.gsparc_num_tiles(G.make_view(90, 360)) == 23 * 6
