@@ -265,3 +265,65 @@ def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(G, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         G.lib()
+
+
+def test_wrappers_pass_arguments_in_header_order(monkeypatch):
+    """The Python wrappers of the training extras, the spectrum loss and the emission network
+    marshal every tensor to the header parameter of the same meaning, in order, and derive the
+    sizes from the tensors' shapes (host only: the C call is recorded, not made)."""
+    import torch
+
+    decls = _declarations()
+    calls = []
+    names = {}
+
+    def t(name, *shape, dtype=torch.float32):
+        x = torch.zeros(shape, dtype=dtype)
+        names[id(x)] = name
+        return x
+
+    monkeypatch.setattr(G, "_p", lambda x: None if x is None else names[id(x)])
+    monkeypatch.setattr(G, "_stream", lambda s=None: "stream")
+    monkeypatch.setattr(G, "_call", lambda fn, *args: calls.append((fn, args)))
+
+    def check(expect_sizes):
+        fn, args = calls.pop()
+        params = [p.split()[-1].lstrip("*") for p in decls[fn][1]]
+        assert len(args) == len(params), fn
+        for p, a in zip(params, args):
+            if p in expect_sizes:
+                assert a == expect_sizes[p], (fn, p, a)
+            elif isinstance(a, str):
+                assert a == p, (fn, p, a)
+
+    G.gsparc_confidence(t("pos", 5, 3), t("task_loss", 5), t("weights", 161), 32, t("objective", 1),
+                        t("confidence", 5), t("d_task_loss", 5), t("d_weights", 161), alpha=0.25)
+    check({"B": 5, "hidden": 32, "alpha": 0.25})
+    out = {"means": t("out_means", 9, 3), "log_scales": t("out_log_scales", 9, 3), "quats": t("out_quats", 9, 4),
+           "opacity_logit": t("out_opacity_logit", 9), "payload": t("out_payload", 9, 2),
+           "parent": t("out_parent", 9, dtype=torch.int32)}
+    params = G.densify_params()
+    G.gsparc_densify(t("means", 4, 3), t("log_scales", 4, 3), t("quats", 4, 4), t("opacity_logit", 4),
+                     t("payload", 4, 2), t("proj", 4, 8), t("norm_sum", 4), t("count", 4, dtype=torch.int32),
+                     t("xi", 4, 2, 3), params, t("ws", 256, dtype=torch.uint8), out,
+                     t("n_out", 1, dtype=torch.int32), t("d_status", 1, dtype=torch.int32))
+    fn, args = calls[-1]
+    assert args[11]._obj is params
+    check({"N": 4, "P": 2, "capacity": 9, "ws_bytes": 256, "params": args[11]})
+    G.gsparc_densify_accumulate(t("proj", 6, 8), t("d_means", 6, 3), t("norm_sum", 6), t("count", 6))
+    check({"N": 6})
+    G.gsparc_opacity_reset(t("opacity_logit", 7), 0.02)
+    check({"N": 7, "max_opacity": 0.02})
+    G.gsparc_spectrum_loss(t("spectrum", 2, 3, 4, 5, 2), t("target", 2, 3, 4, 5), t("ws", 512, dtype=torch.uint8),
+                           t("loss", 1), t("d_spectrum", 2, 3, 4, 5, 2), lam=0.3)
+    check({"B": 2, "K": 3, "H": 4, "W": 5, "lambda": 0.3, "ws_bytes": 512})
+    G.gsparc_emission_fwd(t("tx", 3, 3), (0.0, 1.0, 2.0), t("means", 8, 3), t("opacity_logit", 8),
+                          t("weights", 8, 100), 16, t("attr", 3, 8, 4), inv_d=False)
+    fn, args = calls[-1]
+    assert list(args[4]) == [0.0, 1.0, 2.0]
+    check({"N": 8, "B": 3, "hidden": 16, "rx": args[4], "inv_d": 0})
+    G.gsparc_emission_bwd(t("tx", 2, 3), (0.5, 0.0, 0.0), t("means", 8, 3), t("opacity_logit", 8),
+                          t("weights", 8, 100), 16, t("d_attr", 2, 8, 4), t("d_means", 8, 3),
+                          t("d_opacity_logit", 8), t("d_weights", 8, 100))
+    fn, args = calls[-1]
+    check({"N": 8, "B": 2, "hidden": 16, "rx": args[4], "inv_d": 1})
