@@ -21,7 +21,8 @@ Scheduling (`Server.poll`, admission in `admit`):
     `max_batch`, so one launch serves several transmitters;
   * batches run on separate CUDA streams, so work admitted while others are on
     the GPU overlaps with them.
-A request that alone exceeds the budget is rejected.  Latency is measured from
+A request that alone exceeds the budget is rejected; a waiting request can be withdrawn
+(`Server.cancel`).  Latency is measured from
 the request's arrival time to the host observing its batch's completion event.
 
 `serve_plain` is the baseline: one request at a time on one stream with the
@@ -51,6 +52,7 @@ class Request:
     t_done: float = -1.0
     spectrum: torch.Tensor | None = None   # [K, H, W, 2] on the device
     rejected: bool = False
+    cancelled: bool = False
     rx: tuple | None = None                # receiver position of a moving-receiver request
     V: tuple | None = None                 # its rotation (row-major 3x3), identity when None
 
@@ -139,6 +141,18 @@ class Server:
             self.done.append(req)
             return
         self.waiting.append(req)
+
+    def cancel(self, rid) -> bool:
+        """Withdraw request `rid` if it is still waiting (one already on the GPU runs to
+        completion); it is marked cancelled and counted as done.  Returns whether it was waiting."""
+        for q in self.waiting:
+            if q.rid == rid:
+                self.waiting.remove(q)
+                q.cancelled = True
+                q.t_done = time.perf_counter()
+                self.done.append(q)
+                return True
+        return False
 
     def _band(self, K):
         if K not in self.bands:
@@ -272,10 +286,10 @@ def serve_plain(scene: DeviceScene, mlp: DeviceMLP, requests, arrivals, resoluti
 
 
 def latency_stats(reqs):
-    lat = np.array([(q.t_done - q.t_arrival) * 1e3 for q in reqs if not q.rejected])
+    lat = np.array([(q.t_done - q.t_arrival) * 1e3 for q in reqs if not q.rejected and not q.cancelled])
     if lat.size == 0:
         return {}
     span = max(q.t_done for q in reqs) - min(q.t_arrival for q in reqs)
     return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "spectra_per_s": len(lat) / span, "served": int(lat.size),
-            "rejected": int(sum(q.rejected for q in reqs))}
+            "rejected": int(sum(q.rejected for q in reqs)), "cancelled": int(sum(q.cancelled for q in reqs))}

@@ -1,8 +1,11 @@
-"""Host logic of the query server's admission (no GPU): oldest request first, batches of one
+"""Host logic of the query server (no GPU): admission oldest request first, batches of one
 (resolution, subcarrier count) up to max_batch within the memory budget, moving-receiver
-requests alone, the order of the requests left waiting, and a head that does not fit blocks
-admission until memory frees up."""
+requests alone, the order of the requests left waiting, a head that does not fit blocking
+admission until memory frees up; rejection of a request larger than the budget; cancellation of
+a waiting request; latency statistics without rejected or cancelled requests."""
 import collections
+
+import pytest
 
 from paper_2511_22793_gb300.serve import Request, admit
 
@@ -61,3 +64,49 @@ def test_draining_a_queue_serves_every_request_once():
         assert all(q.rx is None for q in group) or len(group) == 1
         seen += _ids(group)
     assert sorted(seen) == list(range(200))
+
+
+def _server_state(budget=10 ** 9):
+    """The host state Server.submit and Server.cancel work on, without a device."""
+    import types
+
+    from paper_2511_22793_gb300.serve import Server
+
+    st = types.SimpleNamespace(budget=budget, waiting=collections.deque(), done=[])
+    st.request_bytes = lambda H, W, K: _bytes(H, W, K)
+    return Server, st
+
+
+def test_submit_rejects_a_request_larger_than_the_budget():
+    Server, st = _server_state(budget=90 * 360 * 64 - 1)
+    big, small = _q(0, K=64), _q(1, K=1)
+    Server.submit(st, big)
+    Server.submit(st, small)
+    assert big.rejected and big.t_done > 0 and st.done == [big]
+    assert not small.rejected and list(st.waiting) == [small]
+
+
+def test_cancel_withdraws_only_waiting_requests():
+    Server, st = _server_state()
+    qs = [_q(i) for i in range(4)]
+    for q in qs:
+        Server.submit(st, q)
+    assert Server.cancel(st, 2) is True
+    assert qs[2].cancelled and st.done == [qs[2]] and _ids(st.waiting) == [0, 1, 3]
+    assert Server.cancel(st, 2) is False           # no longer waiting
+    assert Server.cancel(st, 99) is False          # unknown (or already on the GPU)
+    group, left = admit(st.waiting, used=0, budget=10 ** 9, max_batch=8, request_bytes=_bytes)
+    assert _ids(group) == [0, 1, 3] and not left
+
+
+def test_latency_stats_leave_out_rejected_and_cancelled_requests():
+    from paper_2511_22793_gb300.serve import latency_stats
+
+    qs = [_q(i) for i in range(4)]
+    for i, q in enumerate(qs):
+        q.t_arrival, q.t_done = 0.0, 0.001 * (i + 1)
+    qs[1].rejected = True
+    qs[2].cancelled = True
+    st = latency_stats(qs)
+    assert st["served"] == 2 and st["rejected"] == 1 and st["cancelled"] == 1
+    assert st["p50_ms"] == pytest.approx(2.5)
