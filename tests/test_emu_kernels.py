@@ -254,13 +254,14 @@ def test_binsort_kernels_logic(emu_bin, tmp_path, n, H, W, seed, case):
 
 
 @pytest.mark.parametrize("n,H,W,K,B,seed", [(200, 45, 180, 8, 2, 41), (200, 45, 180, 37, 1, 42),
-                                             (150, 45, 180, 1, 1, 43)])
+                                             (150, 45, 180, 1, 1, 43), (80, 45, 180, 100, 1, 44)])
 def test_render_fp32_kernels_logic(emu_bin, tmp_path, n, H, W, K, B, seed):
     """k_render_fwd and k_render_bwd (the library's FP32 compositing, under the host shim) on the
     oracle's projection and attributes rounded to FP32, with the oracle's bit-exact tile lists:
     each spectrum within 1e-3 relative L2 of the oracle's renderer and every gradient component
     (p, conic, sigma, a, phi0, L) within 1e-3 of its analytic gradient (the GPU tests' bars);
-    strips of 1, 8 and 32 (ragged: K = 37) subcarriers, one and two transmitters, ragged tiles."""
+    strips of 1, 8 and 32 subcarriers (ragged: K = 37; four strips: K = 100), one and two
+    transmitters, ragged tiles."""
     from oracle import binsort as obs
     from oracle import render as orender
     from paper_2511_22793_gb300 import synth
