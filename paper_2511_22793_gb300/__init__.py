@@ -2,7 +2,10 @@
 
 The compute path is the C-ABI library libgsparc.so (hand-written sm_103a
 CUDA, declared in include/gsparc.h).  `gsparc` is its thin Python binding;
-`autograd` wraps the forward/backward chain in a torch.autograd.Function.
-`synth` holds the seeded input generators.
+`pipeline` owns the buffers of one view / band / scene size; `autograd` wraps
+the forward/backward chain in a torch.autograd.Function; `train` is the
+training loop, `serve` the continuous-batching query server, `replicas` the
+host logic of the multi-GPU form; `synth` holds the seeded input generators
+and `build` compiles the library.
 """
-__all__ = ["gsparc", "autograd", "synth"]
+__all__ = ["gsparc", "pipeline", "autograd", "train", "serve", "replicas", "synth", "build"]
