@@ -8,7 +8,9 @@
  *   - Every pointer argument named like a tensor is DEVICE memory owned by the
  *     caller, unless the comment says host.  The library never allocates
  *     device memory; scratch space comes from a caller-provided workspace
- *     whose size a *_workspace query returns.
+ *     whose size a *_workspace query returns.  One exception:
+ *     gsparc_bin_sort_noalloc keeps its scratch in a fixed array of the
+ *     library's own device memory (see its comment).
  *   - Every call takes a CUDA stream (cudaStream_t passed as void*, NULL for
  *     the legacy default stream), only enqueues work on it and returns without
  *     synchronising.  Argument errors are detected on the host before anything
@@ -42,6 +44,7 @@ extern "C" {
 #define GSPARC_ERR_TIMEOUT (-4)   /* a bounded device-side wait gave up           */
 #define GSPARC_ERR_CAPACITY (-5)  /* more pairs (or densified rows) than capacity */
 #define GSPARC_ERR_TOO_LARGE (-6) /* sizes above a fixed-scratch entry point's cap */
+#define GSPARC_ERR_INPUT (-7)     /* the device found an input out of its domain     */
 
 /* ---- fixed sizes ------------------------------------------------------- */
 #define GSPARC_TILE 16       /* pixels per tile side                              */
@@ -109,11 +112,14 @@ int32_t gsparc_num_tiles(const gsparc_view* view);
  *   the conic (Sigma' + 0.3 I)^-1, ext the footprint half extents
  *   sqrt(2 ln 255 * diag(Sigma' + 0.3 I)) in pixels and r = |x'|.  Culled
  *   Gaussians (r < near_dist) get ext_x = ext_y = -1.
+ *   d_status [1] (device, may be NULL): set to GSPARC_ERR_INPUT when a
+ *   Gaussian has a non-finite mean or log-scale or a zero quaternion; such a
+ *   Gaussian is culled (ext = -1) and gsparc_project_bwd passes it no gradient.
  * Errors: GSPARC_ERR_INVALID for N < 0, a null pointer with N > 0 or a
  * non-positive H or W.
  */
 int gsparc_project(const gsparc_view* view, int32_t N, const float* means, const float* log_scales,
-                   const float* quats, float* proj, void* stream);
+                   const float* quats, float* proj, int32_t* d_status, void* stream);
 
 /*
  * Gradient of gsparc_project (Sec. 4.2 map and Sigma'; Algorithm 1 Backprop).
@@ -135,13 +141,17 @@ int gsparc_bin_sort_workspace(const gsparc_view* view, int32_t N, int64_t pair_c
 
 /*
  * Tile binning and directional sorting (Algorithm 1 IntersectGaussians and
- * "sort by depth to receiver"; Sec. 1 "directional sorting").  For every
- * Gaussian, the 16x16 tiles its footprint box touches (azimuth wrapping at
- * +-pi) each get one (Gaussian, tile) pair; every tile's list is ordered by
- * (r, index).  The pairs are counted per tile, emitted into per-tile buckets as
- * the unique 64-bit keys (bits(r) << 32) | index, and each bucket is radix
- * sorted by its own thread block (8-bit digits, only the bytes that vary in
- * the bucket), in shared memory up to 12288 pairs and in the workspace above.
+ * its depth sort step, depth = distance to the receiver; Sec. 1 "directional
+ * sorting").  For every Gaussian, the 16x16 tiles its footprint box touches
+ * (azimuth wrapping at +-pi) each get one (Gaussian, tile) pair; every tile's
+ * list is ordered by (r, index).  The pairs are counted per tile, emitted into
+ * per-tile buckets as the unique 64-bit keys (bits(r) << 32) | index, and
+ * each bucket is sorted by its own thread block: in shared memory up to
+ * 24576 pairs, by a distribution sort over 4096 depth sub-buckets (each key
+ * ranked against the few keys of its sub-bucket), and by an LSD radix sort
+ * (8-bit digits, only the bytes that vary in the bucket) for larger buckets,
+ * in the workspace, or when the depths are too concentrated for the
+ * sub-buckets.
  *   proj [N,8]: records from gsparc_project (only p, ext and r are read).
  *   ws: device workspace of ws_bytes >= gsparc_bin_sort_workspace().
  *   sorted_ids [pair_capacity] out: Gaussian id of each sorted pair.
@@ -175,7 +185,9 @@ int gsparc_bin_sort(const gsparc_view* view, int32_t N, const float* proj, int64
  *   anything is enqueued.  Other arguments and errors as gsparc_bin_sort.
  *   The first call on each device looks up that device's address of the
  *   array (with the device current); make that first call before any stream
- *   capture.  The call allocates nothing.
+ *   capture.  If that lookup fails (GSPARC_ERR_CUDA, e.g. a pending error of
+ *   an earlier launch), nothing is cached and the next call tries again.
+ *   The call allocates nothing.
  *   Every call on a device shares the one array and it keeps what the last
  *   call left there: the call clears what must start at zero itself, but two
  *   calls whose work overlaps on the GPU (different streams, no ordering
@@ -289,11 +301,13 @@ int gsparc_emission_bwd(int32_t N, int32_t B, int32_t hidden, const float* tx, c
  *   of the last Gaussian composited, 0 if none.  gsparc_render_bwd needs both.
  *   n_used [B,H,W] out, may be NULL: number of Gaussians composited at the
  *   pixel (the algorithmic work per pixel and subcarrier).
+ *   d_status [1] (device, may be NULL): set to GSPARC_ERR_INPUT when a tile
+ *   list holds an id >= N (inconsistent inputs); that entry is skipped.
  */
 int gsparc_render_fwd(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
                       const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
                       const float* attr, float* spectrum, float* final_logT, uint32_t* n_contrib,
-                      uint32_t* n_used, void* stream);
+                      uint32_t* n_used, int32_t* d_status, void* stream);
 
 /*
  * gsparc_render_fwd with the subcarrier sum on the tensor cores (same
@@ -305,11 +319,15 @@ int gsparc_render_fwd(const gsparc_view* view, const gsparc_band* band, int32_t 
  * split into two BF16 terms (three products, ~16-bit operands) and FP32
  * accumulation in tensor memory.  Spectra agree with gsparc_render_fwd to
  * ~1e-5 relative.
+ *   d_status [1] (device, may be NULL): GSPARC_ERR_INPUT as gsparc_render_fwd;
+ *   GSPARC_ERR_TIMEOUT when a bounded wait of the kernel's pipeline expired
+ *   (the affected strips of the spectrum are then NaN).  The kernel always
+ *   lets its tensor-core products finish before it frees its tensor memory.
  */
 int gsparc_render_fwd_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
                          const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
                          const float* attr, float* spectrum, float* final_logT,
-                         uint32_t* n_contrib, uint32_t* n_used, void* stream);
+                         uint32_t* n_contrib, uint32_t* n_used, int32_t* d_status, void* stream);
 
 /*
  * Gradient of gsparc_render_fwd (Algorithm 1 Backprop through compositing and
@@ -318,11 +336,13 @@ int gsparc_render_fwd_tc(const gsparc_view* view, const gsparc_band* band, int32
  * per-pair state is stored.  d_spectrum [B,K,H,W,2] holds dL/dRe z, dL/dIm z.
  * Accumulates dL/d(a, phi0, sigma, L) into d_attr [B,N,4] and
  * dL/d(p_x, p_y, -, -, c_xx, c_xy, c_yy, -) into d_proj [N,8].
+ * d_status [1] (device, may be NULL): GSPARC_ERR_INPUT as gsparc_render_fwd.
  */
 int gsparc_render_bwd(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
                       const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
                       const float* attr, const float* final_logT, const uint32_t* n_contrib,
-                      const float* d_spectrum, float* d_attr, float* d_proj, void* stream);
+                      const float* d_spectrum, float* d_attr, float* d_proj, int32_t* d_status,
+                      void* stream);
 
 /*
  * gsparc_render_bwd with its three per-(pixel, Gaussian) subcarrier sums on the
@@ -335,13 +355,17 @@ int gsparc_render_bwd(const gsparc_view* view, const gsparc_band* band, int32_t 
  * in gsparc_render_bwd.  Gradients agree with gsparc_render_bwd to ~1e-5.
  * The kernel is warp-specialised (producer warps build the phasor operand and
  * issue the products; the pixel warps consume them through mbarriers).  An
- * expired bounded wait leaves the gradients incomplete and adds NaN to
- * d_attr[b,0,0] of the affected transmitter.
+ * expired bounded wait leaves the gradients incomplete, adds NaN to
+ * d_attr[b,0,0] of the affected transmitter and sets d_status [1] (device,
+ * may be NULL) to GSPARC_ERR_TIMEOUT; GSPARC_ERR_INPUT as gsparc_render_fwd.
+ * The kernel always lets its tensor-core products finish before it frees its
+ * tensor memory.
  */
 int gsparc_render_bwd_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
                          const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
                          const float* attr, const float* final_logT, const uint32_t* n_contrib,
-                         const float* d_spectrum, float* d_attr, float* d_proj, void* stream);
+                         const float* d_spectrum, float* d_attr, float* d_proj, int32_t* d_status,
+                         void* stream);
 
 /*
  * Bytes of device workspace gsparc_render_bwd_tc_balanced needs for B
@@ -379,17 +403,17 @@ int gsparc_render_bwd_tc_workspace(const gsparc_view* view, const gsparc_band* b
  *   ws: device workspace of ws_bytes >= gsparc_render_bwd_tc_workspace(),
  *   16-byte aligned, whose first 16 bytes are zero before its first use
  *   (every call leaves them zero again); one call at a time per workspace.
- * Other arguments and outputs as gsparc_render_bwd_tc; the front chunks'
- * suffix is a difference of two sums, so its error is relative to s_tot,
- * not to the suffix (the gradients agree with gsparc_render_bwd_tc to
- * ~1e-5 relative L2).
+ * Other arguments, outputs and the status word as gsparc_render_bwd_tc; the
+ * front chunks' suffix is a difference of two sums, so its error is relative
+ * to s_tot, not to the suffix (the gradients agree with gsparc_render_bwd_tc
+ * to ~1e-5 relative L2).
  */
 int gsparc_render_bwd_tc_balanced(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
                                   const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
                                   const float* attr, const float* spectrum, const float* s_tot,
                                   const uint32_t* tile_walk, const float* final_logT, const uint32_t* n_contrib,
                                   const float* d_spectrum, int32_t split_min, void* ws, size_t ws_bytes,
-                                  float* d_attr, float* d_proj, void* stream);
+                                  float* d_attr, float* d_proj, int32_t* d_status, void* stream);
 
 /*
  * Complex L2 loss, the mean over `count` complex elements of |z - target|^2,
@@ -468,12 +492,13 @@ int gsparc_spectrum_loss(int32_t B, int32_t K, int32_t H, int32_t W, const float
  * tile_walk may be NULL; else [B, T] out (T = tiles): per (transmitter,
  * tile) the walk min(largest n_contrib of its pixels, list length), which
  * gsparc_render_bwd_tc_balanced takes in place of its own walk pass.
+ * d_status as gsparc_render_fwd_tc (an expired wait makes the loss NaN).
  */
 int gsparc_render_fwd_l2_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
                             const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
                             const float* attr, const float* target, float* loss, float* d_spectrum,
                             float* spectrum, float* final_logT, uint32_t* n_contrib, uint32_t* n_used,
-                            float* s_tot, uint32_t* tile_walk, void* stream);
+                            float* s_tot, uint32_t* tile_walk, int32_t* d_status, void* stream);
 
 /*
  * gsparc_render_fwd_tc with the CSI head fused into its epilogue: every
@@ -482,12 +507,13 @@ int gsparc_render_fwd_l2_tc(const gsparc_view* view, const gsparc_band* band, in
  * be NULL, and then the spectrum is never written (8 B per pixel, subcarrier
  * and transmitter saved) -- the form a CSI query at an unseen position needs.
  * final_logT, n_contrib, n_used as gsparc_render_fwd (each may be NULL).
- * Atomic partial sums: the last bits may differ from run to run.
+ * Atomic partial sums: the last bits may differ from run to run.  d_status as
+ * gsparc_render_fwd_tc (an expired wait makes the estimate NaN).
  */
 int gsparc_render_csi_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
                          const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
                          const float* attr, float* csi, float* spectrum, float* final_logT,
-                         uint32_t* n_contrib, uint32_t* n_used, void* stream);
+                         uint32_t* n_contrib, uint32_t* n_used, int32_t* d_status, void* stream);
 
 /*
  * Confidence-weighted objective (Eq. 5, Sec. 4.2 confidence-weighted
@@ -585,6 +611,17 @@ int gsparc_opacity_reset(int32_t N, float max_opacity, float* opacity_logit, voi
  */
 int gsparc_adam(int64_t n, float* param, const float* grad, float* m, float* v, float lr, float b1,
                 float b2, float eps, int32_t step, void* stream);
+
+/*
+ * Polls a pipeline wait of the tensor-core compositing kernels
+ * (gsparc_render_fwd_tc, gsparc_render_fwd_l2_tc, gsparc_render_csi_tc,
+ * gsparc_render_bwd_tc, gsparc_render_bwd_tc_balanced) makes before it gives up
+ * and the call reports GSPARC_ERR_TIMEOUT; 0 restores the default (2^22 polls,
+ * well above any wait of a healthy launch).  Process-wide; read when a call
+ * enqueues its kernel.  Returns the previous setting.  Meant for tests of the
+ * timeout path: a small bound makes a wait expire without a fault or a hang.
+ */
+uint32_t gsparc_set_wait_limit(uint32_t polls);
 
 /*
  * Synchronise `stream`, then return the value of the device status word

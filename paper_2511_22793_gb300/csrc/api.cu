@@ -1,6 +1,23 @@
 // Status helpers of the C ABI.
 
+#include <atomic>
+
 #include "internal.cuh"
+
+namespace gsparc {
+namespace {
+std::atomic<uint32_t> g_wait_limit{0};
+}  // namespace
+
+uint32_t wait_limit(uint32_t dflt) {
+    const uint32_t v = g_wait_limit.load(std::memory_order_relaxed);
+    return v ? v : dflt;
+}
+}  // namespace gsparc
+
+extern "C" uint32_t gsparc_set_wait_limit(uint32_t polls) {
+    return gsparc::g_wait_limit.exchange(polls, std::memory_order_relaxed);
+}
 
 extern "C" int gsparc_check(const int32_t* d_status, void* stream) {
     cudaStream_t s = gsparc::as_stream(stream);
@@ -20,6 +37,7 @@ extern "C" const char* gsparc_strerror(int status) {
         case GSPARC_ERR_TIMEOUT: return "bounded device wait expired";
         case GSPARC_ERR_CAPACITY: return "capacity exceeded (tile pairs or densified rows)";
         case GSPARC_ERR_TOO_LARGE: return "size above the fixed scratch limit";
+        case GSPARC_ERR_INPUT: return "input out of domain (found on the device)";
         default: return "unknown status";
     }
 }

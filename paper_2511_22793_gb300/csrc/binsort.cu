@@ -111,9 +111,24 @@ constexpr int kMaxDevices = 64;
 // address comes from cudaGetSymbolAddress, once per device, with that device current.
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-std::once_flag g_noalloc_once[kMaxDevices];
+// Device address of the array per device, stored only once a lookup succeeded: a failed lookup
+// (an earlier asynchronous error reported by the runtime call, or a lookup inside a stream
+// capture) is retried by the next call instead of being kept for the life of the process.
+std::mutex g_noalloc_mutex;
 void* g_noalloc_ptr[kMaxDevices];
-cudaError_t g_noalloc_err[kMaxDevices];
+
+void* noalloc_scratch(int dev) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+            (void)cudaGetLastError();   // clear a non-sticky error so that a retry can succeed
+            return nullptr;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    return g_noalloc_ptr[dev];
+}
 
 }  // namespace
 }  // namespace gsparc
@@ -133,12 +148,10 @@ extern "C" int gsparc_bin_sort_noalloc(const gsparc_view* view, int32_t N, const
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GSPARC_ERR_CUDA;
-    std::call_once(g_noalloc_once[dev], [dev]() {
-        g_noalloc_err[dev] = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_scratch);
-    });
-    if (g_noalloc_err[dev] != cudaSuccess || !g_noalloc_ptr[dev]) return GSPARC_ERR_CUDA;
+    char* scratch = static_cast<char*>(noalloc_scratch(dev));
+    if (!scratch) return GSPARC_ERR_CUDA;
     // the array keeps the previous call's contents; bin_sort_launch clears the tile
     // counters and the block ticket, and everything else is written before it is read
-    return bin_sort_launch(view, N, proj, pair_capacity, static_cast<char*>(g_noalloc_ptr[dev]), L,
+    return bin_sort_launch(view, N, proj, pair_capacity, scratch, L,
                            sorted_ids, sorted_keys, tile_ranges, n_pairs, d_status, as_stream(stream));
 }

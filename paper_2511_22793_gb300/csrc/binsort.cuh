@@ -1,7 +1,8 @@
 // Tile binning and directional (receiver-distance) sorting.
 //
-// Algorithm 1: IntersectGaussians per pixel, then "sort by depth to receiver";
-// Sec. 1 names the fully parallel directional sort.  Tiled form: each
+// Algorithm 1: IntersectGaussians per pixel followed by its depth sort step
+// (depth = distance to the receiver); Sec. 1: the fully parallel directional
+// sort.  Tiled form: each
 // Gaussian's footprint box (azimuth wrapping at +-pi) gives one (Gaussian,
 // tile) pair per touched 16x16 tile, and every tile's list is ordered by
 // (r, index).
@@ -14,10 +15,13 @@
 //   k_tile_emit   every pair, as the 64-bit sort key (bits(r) << 32) | index,
 //                 into its tile's bucket (block-aggregated cursor atomics, so
 //                 the order inside a bucket is arbitrary)
-//   k_tile_sort   one CTA per tile: LSD radix sort of the bucket's keys (8-bit
-//                 digits, warp-match ranking, only the bytes that vary in the
-//                 bucket) in shared memory, or in a global ping-pong buffer for
-//                 a bucket above kSortCap keys; writes the ids (and keys)
+//   k_tile_sort   one CTA per tile: up to kSortCap keys in shared memory, a
+//                 distribution sort over kSubBuckets depth sub-buckets (each
+//                 key ranked against the few keys of its sub-bucket); above
+//                 that, or when a sub-bucket holds more than kSubMax keys, an
+//                 LSD radix sort (8-bit digits, warp-match ranking, only the
+//                 bytes that vary in the bucket), in a global ping-pong buffer
+//                 for a bucket above kSortCap keys; writes the ids (and keys)
 // The keys are unique (the index is part of the key), so any arrangement of a
 // bucket sorts to the same list: the (r, index) order, bit for bit.
 //
@@ -43,10 +47,6 @@ constexpr int kSubBuckets = 4096;                   // sub-buckets of the in-til
 constexpr int kSubMax = 64;                         // largest sub-bucket ranked by comparison
 static_assert(kSortThreads >= 256, "the digit scan gives one thread per digit");
 static_assert(kSortWarps * 256 == kSubBuckets, "histogram array shared by both in-tile sorts");
-
-__device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
-    if (status) atomicCAS(reinterpret_cast<int*>(status), 0, code);
-}
 
 // Column / row tile ranges touched by one projection record.  Every float
 // step is a single correctly rounded operation (explicit _rn intrinsics keep

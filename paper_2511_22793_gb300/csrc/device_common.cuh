@@ -23,6 +23,12 @@ constexpr int kTile = GSPARC_TILE;
 #define GSPARC_DYNAMIC_SMEM(name) extern __shared__ __align__(16) unsigned char name[]
 #endif
 
+// First device-detected condition of a call, into the caller's status word (may be null); a
+// later condition never overwrites an earlier one.
+__device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
+    if (status) atomicCAS(reinterpret_cast<int*>(status), 0, code);
+}
+
 inline int tiles_x(const gsparc_view& v) { return (v.W + kTile - 1) / kTile; }
 inline int tiles_y(const gsparc_view& v) { return (v.H + kTile - 1) / kTile; }
 

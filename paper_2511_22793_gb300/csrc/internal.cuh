@@ -21,6 +21,10 @@ inline int launch_status() {
 }
 
 
+// Polls before a pipeline wait of the tensor-core compositing kernels gives up: the value set by
+// gsparc_set_wait_limit, or dflt when none is set.
+uint32_t wait_limit(uint32_t dflt);
+
 inline bool view_ok(const gsparc_view* v) {
     return v && v->H > 0 && v->W > 0 && v->H <= 32768 && v->W <= 32768;
 }

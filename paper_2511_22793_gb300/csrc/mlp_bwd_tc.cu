@@ -52,7 +52,7 @@ struct BtSmem {
     static constexpr int kGBhi = kGAlo + kGA;
     static constexpr int kGBlo = kGBhi + kGB;
     static constexpr int kF = kGBlo + kGB;                   // fp32: b1, b2, W3, b3
-    static constexpr int kMisc = kF + (5 * HD + 4) * 4;      // mbarrier, TMEM slot
+    static constexpr int kMisc = kF + (5 * HD + 4) * 4;      // mbarrier, TMEM slot, drain mbarrier
     static constexpr int kTotal = kMisc + 32;
     // TMEM columns: D1 | D2 | D3 (HD each) | D4 (32) | Dg (kNG)
     static constexpr uint32_t kD1 = 0, kD2 = HD, kD3 = 2 * HD, kD4 = 3 * HD, kDg = 3 * HD + 32;
@@ -60,6 +60,7 @@ struct BtSmem {
     static_assert(kDg + kNG <= kCols, "accumulators fit the TMEM allocation");
     static_assert(kFOne < 128, "feature rows fit M = 128");
     static_assert(kTotal <= 232448, "shared memory per block");
+    static_assert(kMisc % 8 == 0, "mbarriers 8-byte aligned");
 };
 
 // x split into hi / lo terms laid out [hi | lo | hi] along K (Kb columns each) in row r of a
@@ -433,6 +434,8 @@ __global__ void __launch_bounds__(kRowsB, 1) k_mlp_bwd_tc(
         }
     }
     if (!ok && t == 0) atomicAdd(&g.b3[0], __int_as_float(0x7fc00000));   // an expired wait poisons the result
+    // no product still in flight when the TMEM is freed (an expired wait skipped the last ones)
+    if (t == 0) tc_drain(smem_u32(sm + L::kMisc + 16));
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {

@@ -88,8 +88,9 @@ struct TcSmem {
     static constexpr int kB1 = kA2 + kRows * kKt2 * 2;             // [HD x Kt1]
     static constexpr int kB2 = kB1 + HD * kKt1 * 2;                // [HD x Kt2]
     static constexpr int kF = kB2 + HD * kKt2 * 2;                 // fp32: b1, b2, W3, b3
-    static constexpr int kMisc = kF + (2 * HD + 3 * HD + 4) * 4;   // mbarrier, tmem addr
+    static constexpr int kMisc = kF + (2 * HD + 3 * HD + 4) * 4;   // mbarrier, tmem addr, drain mbarrier
     static constexpr int kTotal = kMisc + 32;
+    static_assert(kMisc % 8 == 0, "mbarriers 8-byte aligned");
 };
 
 template <int HD, int TERMS>
@@ -272,6 +273,8 @@ __global__ void __launch_bounds__(kRows) k_mlp_tc(int N, int B, const float* __r
             }
         }
     }
+    // no product still in flight when the TMEM is freed (an expired wait skipped the last ones)
+    if (t == 0) tc_drain(smem_u32(sm + L::kMisc + 16));
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {

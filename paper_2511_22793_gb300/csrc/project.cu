@@ -11,7 +11,8 @@ extern "C" int32_t gsparc_num_tiles(const gsparc_view* view) {
 }
 
 extern "C" int gsparc_project(const gsparc_view* view, int32_t N, const float* means,
-                              const float* log_scales, const float* quats, float* proj, void* stream) {
+                              const float* log_scales, const float* quats, float* proj, int32_t* d_status,
+                              void* stream) {
     if (!view_ok(view) || N < 0) return GSPARC_ERR_INVALID;
     if (N == 0) return GSPARC_OK;
     if (!means || !log_scales || !quats || !proj) return GSPARC_ERR_INVALID;
@@ -21,7 +22,7 @@ extern "C" int gsparc_project(const gsparc_view* view, int32_t N, const float* m
     const int blocks = (N + threads - 1) / threads;
     k_project<<<blocks, threads, 0, as_stream(stream)>>>(to_dev(*view), N, means, log_scales,
                                                          reinterpret_cast<const float4*>(quats),
-                                                         reinterpret_cast<float4*>(proj));
+                                                         reinterpret_cast<float4*>(proj), d_status);
     return launch_status();
 }
 

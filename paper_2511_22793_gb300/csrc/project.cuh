@@ -112,16 +112,27 @@ __device__ __forceinline__ bool geometry(const ViewDev& v, int i, const float* _
     return true;
 }
 
+// A kept Gaussian whose covariance is not a finite positive-definite matrix (a non-finite mean
+// or log-scale, a zero quaternion) has no footprint: the projection culls it and reports
+// GSPARC_ERR_INPUT, and the backward passes it no gradient.
+__device__ __forceinline__ bool record_ok(const Geo& g) {
+    return g.qnorm > 0.f && isfinite(g.qnorm) && isfinite(g.sxx) && isfinite(g.sxy) && isfinite(g.syy) &&
+           g.det > 0.f && isfinite(g.inv);
+}
+
 __global__ void __launch_bounds__(256) k_project(ViewDev v, int N, const float* __restrict__ means,
                                                  const float* __restrict__ ls,
                                                  const float4* __restrict__ quats,
-                                                 float4* __restrict__ proj) {
+                                                 float4* __restrict__ proj, int32_t* status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     Geo g;
-    if (!geometry(v, i, means, ls, quats, g)) {
+    const bool kept = geometry(v, i, means, ls, quats, g);
+    if (!kept || !record_ok(g)) {
+        // culled: behind the near distance, or (reported) a non-finite or degenerate input
+        if (kept || !isfinite(g.r)) set_status(status, GSPARC_ERR_INPUT);
         proj[2 * i + 0] = make_float4(0.f, 0.f, -1.f, -1.f);
-        proj[2 * i + 1] = make_float4(0.f, 0.f, 0.f, g.r);
+        proj[2 * i + 1] = make_float4(0.f, 0.f, 0.f, isfinite(g.r) ? g.r : 0.f);
         return;
     }
     const float px = (atan2f(g.x, g.z) / kPi + 1.0f) * (0.5f * (float)v.W);
@@ -144,7 +155,7 @@ __global__ void __launch_bounds__(256) k_project_bwd(ViewDev v, int N, const flo
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     Geo g;
-    if (!geometry(v, i, means, ls, quats, g)) return;
+    if (!geometry(v, i, means, ls, quats, g) || !record_ok(g)) return;
     const float4 d0 = dproj[2 * i + 0];
     const float4 d1 = dproj[2 * i + 1];
     const float dpx = d0.x, dpy = d0.y, dcxx = d1.x, dcxy = d1.y, dcyy = d1.z;

@@ -43,12 +43,13 @@ extern "C" int gsparc_render_fwd(const gsparc_view* view, const gsparc_band* ban
                                  int32_t N, const float* proj, const uint32_t* tile_ranges,
                                  const uint32_t* sorted_ids, const float* attr, float* spectrum,
                                  float* final_logT, uint32_t* n_contrib, uint32_t* n_used,
-                                 void* stream) {
+                                 int32_t* d_status, void* stream) {
     if (!common_ok(view, band, B, N, proj, tile_ranges, sorted_ids, attr) || !spectrum)
         return GSPARC_ERR_INVALID;
     if (reinterpret_cast<uintptr_t>(spectrum) & 7) return GSPARC_ERR_INVALID;
     RenderArgs a{};
     fill_args(view, band, B, N, proj, tile_ranges, sorted_ids, attr, a);
+    a.status = d_status;
     a.spectrum = reinterpret_cast<float2*>(spectrum);
     a.final_logT = final_logT;
     a.n_contrib = n_contrib;
@@ -71,13 +72,14 @@ extern "C" int gsparc_render_bwd(const gsparc_view* view, const gsparc_band* ban
                                  const uint32_t* sorted_ids, const float* attr,
                                  const float* final_logT, const uint32_t* n_contrib,
                                  const float* d_spectrum, float* d_attr, float* d_proj,
-                                 void* stream) {
+                                 int32_t* d_status, void* stream) {
     if (!common_ok(view, band, B, N, proj, tile_ranges, sorted_ids, attr)) return GSPARC_ERR_INVALID;
     if (!final_logT || !n_contrib || !d_spectrum || !d_attr || !d_proj) return GSPARC_ERR_INVALID;
     if ((reinterpret_cast<uintptr_t>(d_spectrum) & 7) || (reinterpret_cast<uintptr_t>(d_attr) & 15))
         return GSPARC_ERR_INVALID;
     RenderArgs a{};
     fill_args(view, band, B, N, proj, tile_ranges, sorted_ids, attr, a);
+    a.status = d_status;
     a.final_logT = const_cast<float*>(final_logT);
     a.n_contrib = const_cast<uint32_t*>(n_contrib);
     a.d_spectrum = reinterpret_cast<const float2*>(d_spectrum);
@@ -182,8 +184,8 @@ constexpr int kFwsThreads = kThreads + kWsProd + 32;
 template <int S>
 struct RFwsSmem {
     using T = RTcSmem<S>;
-    static constexpr int kBars = T::kBar;                     // rec[2], bready[2], aready[2], mdone[2]
-    static constexpr int kMisc = kBars + 8 * 8;               // TMEM slot, done warps, batch count, error, end, walk
+    static constexpr int kBars = T::kBar;                     // rec[2], bready[2], aready[2], mdone[2], drain
+    static constexpr int kMisc = kBars + 9 * 8;               // TMEM slot, done warps, batch count, error, end, walk
     static constexpr int kTotal = kMisc + 32;
 };
 
@@ -210,6 +212,7 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
     auto bready_bar = [&](int st) { return smem_u32(&bars[2 + st]); };
     auto aready_bar = [&](int st) { return smem_u32(&bars[4 + st]); };
     auto mdone_bar = [&](int st) { return smem_u32(&bars[6 + st]); };
+    const uint32_t drain_bar = smem_u32(&bars[8]);
 
     const int strip = blockIdx.x, tile = blockIdx.y, b = blockIdx.z;
     const int k0 = strip * S;
@@ -252,7 +255,7 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
     tc_fence_after();
     const uint32_t tbase = *tslot;
     auto wait_ok = [&](uint32_t bar, uint32_t parity) {
-        bool w = (*s_err == 0u) && mbar_wait(bar, parity);
+        bool w = (*s_err == 0u) && mbar_wait(bar, parity, a.spin ? a.spin : kSpin);
         w = __all_sync(0xffffffffu, w);
         if (!w && lane == 0) *s_err = 1u;
         return w;
@@ -277,6 +280,8 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
                     pf_p0 = __ldg(a.proj + 2 * pf_gid);
                     pf_p1 = __ldg(a.proj + 2 * pf_gid + 1);
                     pf_at = __ldg(a.attr + (size_t)b * a.N + pf_gid);
+                } else if (pf_gid != 0xffffffffu) {
+                    set_status(a.status, GSPARC_ERR_INPUT);   // a list id outside the scene: skipped
                 }
                 pf_nid = load_id(pos + kTcE);
             }
@@ -382,6 +387,10 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
             }
             __syncwarp();
         }
+        // no product may still be in flight when the CTA frees its TMEM (after an expired wait
+        // the other warps leave without waiting for the last commit)
+        if (lane == 0) tc_drain(drain_bar);
+        __syncwarp();
     } else {
         // ---------------- pixel warps: the weights of each batch
         bool done = !inside, counted = false;
@@ -600,6 +609,7 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
             if (k < a.K) atomicAdd(reinterpret_cast<float*>(&a.csi[(size_t)b * a.K + k]) + (e & 1), sum * a.csi_scale);
         }
     }
+    if (tid == 0 && *s_err != 0u) set_status(a.status, GSPARC_ERR_TIMEOUT);
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(L::kCols) : "memory");
@@ -621,12 +631,14 @@ int launch_fwd_tc(const RenderArgs& a, int T, cudaStream_t s) {
 extern "C" int gsparc_render_fwd_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
                                     const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
                                     const float* attr, float* spectrum, float* final_logT, uint32_t* n_contrib,
-                                    uint32_t* n_used, void* stream) {
+                                    uint32_t* n_used, int32_t* d_status, void* stream) {
     using namespace gsparc;
     if (!common_ok(view, band, B, N, proj, tile_ranges, sorted_ids, attr) || !spectrum) return GSPARC_ERR_INVALID;
     if (reinterpret_cast<uintptr_t>(spectrum) & 7) return GSPARC_ERR_INVALID;
     RenderArgs a{};
     fill_args(view, band, B, N, proj, tile_ranges, sorted_ids, attr, a);
+    a.status = d_status;
+    a.spin = wait_limit(kSpin);
     a.spectrum = reinterpret_cast<float2*>(spectrum);
     a.final_logT = final_logT;
     a.n_contrib = n_contrib;
@@ -643,7 +655,7 @@ extern "C" int gsparc_render_fwd_l2_tc(const gsparc_view* view, const gsparc_ban
                                        const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
                                        const float* attr, const float* target, float* loss, float* d_spectrum,
                                        float* spectrum, float* final_logT, uint32_t* n_contrib, uint32_t* n_used,
-                                       float* s_tot, uint32_t* tile_walk, void* stream) {
+                                       float* s_tot, uint32_t* tile_walk, int32_t* d_status, void* stream) {
     using namespace gsparc;
     if (!common_ok(view, band, B, N, proj, tile_ranges, sorted_ids, attr)) return GSPARC_ERR_INVALID;
     if (!target || !loss || !d_spectrum) return GSPARC_ERR_INVALID;
@@ -652,6 +664,8 @@ extern "C" int gsparc_render_fwd_l2_tc(const gsparc_view* view, const gsparc_ban
         return GSPARC_ERR_INVALID;
     RenderArgs a{};
     fill_args(view, band, B, N, proj, tile_ranges, sorted_ids, attr, a);
+    a.status = d_status;
+    a.spin = wait_limit(kSpin);
     a.spectrum = reinterpret_cast<float2*>(spectrum);
     a.final_logT = final_logT;
     a.n_contrib = n_contrib;
@@ -675,12 +689,14 @@ extern "C" int gsparc_render_fwd_l2_tc(const gsparc_view* view, const gsparc_ban
 extern "C" int gsparc_render_csi_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
                                     const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
                                     const float* attr, float* csi, float* spectrum, float* final_logT,
-                                    uint32_t* n_contrib, uint32_t* n_used, void* stream) {
+                                    uint32_t* n_contrib, uint32_t* n_used, int32_t* d_status, void* stream) {
     using namespace gsparc;
     if (!common_ok(view, band, B, N, proj, tile_ranges, sorted_ids, attr) || !csi) return GSPARC_ERR_INVALID;
     if ((reinterpret_cast<uintptr_t>(spectrum) | reinterpret_cast<uintptr_t>(csi)) & 7) return GSPARC_ERR_INVALID;
     RenderArgs a{};
     fill_args(view, band, B, N, proj, tile_ranges, sorted_ids, attr, a);
+    a.status = d_status;
+    a.spin = wait_limit(kSpin);
     a.spectrum = reinterpret_cast<float2*>(spectrum);
     a.final_logT = final_logT;
     a.n_contrib = n_contrib;
@@ -770,8 +786,8 @@ struct RWsSmem {
     static constexpr int kRedStage = 8 * kTbE * 9 * 4;
     static constexpr int kRed = kMeta + kWsR * kMetaStage;         // float [stage][warp][E][9]
     static constexpr int kMask = kRed + kWsR * kRedStage;          // uint64 [stage][warp]
-    static constexpr int kBar = kMask + kWsR * 8 * 8;              // full[R], empty[R], bready[R]
-    static constexpr int kTotal = kBar + 3 * kWsR * 8 + 16;        // + TMEM slot, maxlast, error
+    static constexpr int kBar = kMask + kWsR * 8 * 8;              // full[R], empty[R], bready[R], drain
+    static constexpr int kTotal = kBar + 3 * kWsR * 8 + 8 + 16;    // + TMEM slot, maxlast, error
     static constexpr uint32_t kStageCols = 2 * 3 * kTbE;           // both halves of a stage
     static constexpr uint32_t kCols = 512;
     static_assert(kWsR * kStageCols <= kCols, "TMEM stages");
@@ -783,7 +799,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
     using L = RWsSmem<S>;
     extern __shared__ __align__(1024) uint8_t sm[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::kBar);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::kBar + 3 * kWsR * 8);
+    const uint32_t drain_bar = smem_u32(sm + L::kBar + 3 * kWsR * 8);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::kBar + 3 * kWsR * 8 + 8);
     uint32_t* s_maxlast = tslot + 1;
     volatile uint32_t* s_err = tslot + 2;
     auto red_at = [&](int st, int w, int j, int c) -> float& {
@@ -857,6 +874,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
                 pf_p0 = __ldg(a.proj + 2 * pf_gid);
                 pf_p1 = __ldg(a.proj + 2 * pf_gid + 1);
                 pf_at = __ldg(a.attr + (size_t)b * a.N + pf_gid);
+            } else if (pf_gid != 0xffffffffu) {
+                set_status(a.status, GSPARC_ERR_INPUT);   // a list id outside the scene: skipped
             }
             pf_nid = load_id(i + 1);
         }
@@ -940,7 +959,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
     }
     const uint32_t tbase = *tslot;
     auto wait_ok = [&](uint32_t bar, uint32_t parity) {
-        bool w = (*s_err == 0u) && mbar_wait(bar, parity);
+        bool w = (*s_err == 0u) && mbar_wait(bar, parity, a.spin ? a.spin : kSpin);
         w = __all_sync(0xffffffffu, w);
         if (!w && lane == 0) *s_err = 1u;
         return w;
@@ -1080,6 +1099,10 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
             }
             __syncwarp();
         }
+        // no product may still be in flight when the CTA frees its TMEM (after an expired wait
+        // the consumers leave without waiting for the last stage)
+        if (lane == 0) tc_drain(drain_bar);
+        __syncwarp();
     } else {
         // ---------------- consumer warps: one pixel per thread
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
@@ -1210,7 +1233,10 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
     tc_fence_before();
     __syncthreads();
     // an expired wait left the gradients incomplete: make that visible
-    if (tid == 0 && *s_err != 0u) atomicAdd(reinterpret_cast<float*>(&a.d_attr[(size_t)b * a.N]), __int_as_float(0x7fc00000));
+    if (tid == 0 && *s_err != 0u) {
+        set_status(a.status, GSPARC_ERR_TIMEOUT);
+        atomicAdd(reinterpret_cast<float*>(&a.d_attr[(size_t)b * a.N]), __int_as_float(0x7fc00000));
+    }
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(L::kCols) : "memory");
@@ -1243,7 +1269,7 @@ int launch_bwd_tc_any(const RenderArgs& a, int T, cudaStream_t s, uint32_t max_i
 extern "C" int gsparc_render_bwd_tc(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
                                     const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
                                     const float* attr, const float* final_logT, const uint32_t* n_contrib,
-                                    const float* d_spectrum, float* d_attr, float* d_proj, void* stream) {
+                                    const float* d_spectrum, float* d_attr, float* d_proj, int32_t* d_status, void* stream) {
     using namespace gsparc;
     if (!common_ok(view, band, B, N, proj, tile_ranges, sorted_ids, attr)) return GSPARC_ERR_INVALID;
     if (!final_logT || !n_contrib || !d_spectrum || !d_attr || !d_proj) return GSPARC_ERR_INVALID;
@@ -1251,6 +1277,8 @@ extern "C" int gsparc_render_bwd_tc(const gsparc_view* view, const gsparc_band* 
         return GSPARC_ERR_INVALID;
     RenderArgs a{};
     fill_args(view, band, B, N, proj, tile_ranges, sorted_ids, attr, a);
+    a.status = d_status;
+    a.spin = wait_limit(kSpin);
     a.final_logT = const_cast<float*>(final_logT);
     a.n_contrib = const_cast<uint32_t*>(n_contrib);
     a.d_spectrum = reinterpret_cast<const float2*>(d_spectrum);
@@ -1275,7 +1303,7 @@ extern "C" int gsparc_render_bwd_tc_balanced(const gsparc_view* view, const gspa
                                              const float* spectrum, const float* s_tot, const uint32_t* tile_walk,
                                              const float* final_logT, const uint32_t* n_contrib,
                                              const float* d_spectrum, int32_t split_min, void* ws, size_t ws_bytes,
-                                             float* d_attr, float* d_proj, void* stream) {
+                                             float* d_attr, float* d_proj, int32_t* d_status, void* stream) {
     using namespace gsparc;
     if (!common_ok(view, band, B, N, proj, tile_ranges, sorted_ids, attr)) return GSPARC_ERR_INVALID;
     if (!final_logT || !n_contrib || !d_spectrum || !d_attr || !d_proj || !ws) return GSPARC_ERR_INVALID;
@@ -1288,6 +1316,8 @@ extern "C" int gsparc_render_bwd_tc_balanced(const gsparc_view* view, const gspa
     if (2 * units >= (1ll << 31)) return GSPARC_ERR_INVALID;
     RenderArgs a{};
     fill_args(view, band, B, N, proj, tile_ranges, sorted_ids, attr, a);
+    a.status = d_status;
+    a.spin = wait_limit(kSpin);
     a.spectrum = const_cast<float2*>(reinterpret_cast<const float2*>(spectrum));
     a.s_tot = const_cast<float*>(s_tot);
     a.final_logT = const_cast<float*>(final_logT);

@@ -83,6 +83,11 @@ struct RenderArgs {
     const uint4* items;
     const uint32_t* n_items;
     int T;                     // tiles per image
+    // caller's status word (may be null): GSPARC_ERR_INPUT for a list id outside the scene,
+    // GSPARC_ERR_TIMEOUT for an expired wait of the tensor-core kernels
+    int32_t* status;
+    // polls before a pipeline wait of the tensor-core kernels gives up
+    uint32_t spin;
     // cycles of subcarrier k = L * (lam0_hi + lam0_lo + k * dlam), lam = f / c
     float lam0_hi, lam0_lo, dlam;
     // d(psi)/dL = -2 pi f_k / c, split as c_f0 + kk * c_df inside a strip
@@ -152,7 +157,8 @@ __device__ __forceinline__ void stage_batch(const RenderArgs& a, int b, uint32_t
             s_L[tid] = at.w;
         } else {
             // an id outside the scene (inconsistent inputs): a NaN conic makes
-            // every pixel skip it, and it receives no gradient
+            // every pixel skip it, it receives no gradient, and the status word says so
+            set_status(a.status, GSPARC_ERR_INPUT);
             s_geo[tid] = make_float4(0.f, 0.f, __int_as_float(0x7fc00000), 0.f);
             s_geo2[tid] = make_float2(0.f, 0.f);
             s_ext[tid] = make_float2(-1.f, -1.f);

@@ -8,7 +8,9 @@
 
 namespace gsparc {
 
-// Bound on mbarrier polls before a wait reports failure (never hang the GPU).
+// Bound on mbarrier polls before a wait reports failure (never hang the GPU).  Entry points may
+// pass a smaller bound (gsparc_set_wait_limit) to the kernels' pipeline waits; the drain below
+// always takes this one.
 constexpr uint32_t kSpin = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -59,9 +61,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
-// Bounded wait for the given phase parity; false when the bound expired.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (uint32_t it = 0; it < kSpin; ++it) {
+// Bounded wait for the given phase parity; false when `polls` polls found it incomplete.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t polls = kSpin) {
+    for (uint32_t it = 0; it < polls; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -72,6 +74,20 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
         if (done) return true;
     }
     return false;
+}
+
+// Wait until no tcgen05 operation issued by this thread is still in flight: a fresh mbarrier
+// (count 1, at an address no pipeline uses) receives one tcgen05.commit, which arrives once every
+// earlier tcgen05 operation of the thread has completed.  The issuing thread calls it before the
+// CTA frees its tensor memory and exits, so that no product still writes TMEM or reads shared
+// memory after an expired pipeline wait made the CTA leave its loop early.  Bounded by kSpin.
+__device__ __forceinline__ bool tc_drain(uint32_t bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+    return mbar_wait(bar, 0u, kSpin);
 }
 
 __device__ __forceinline__ void fence_async_smem() {

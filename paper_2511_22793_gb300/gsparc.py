@@ -24,6 +24,7 @@ GSPARC_ERR_CUDA = -3
 GSPARC_ERR_TIMEOUT = -4
 GSPARC_ERR_CAPACITY = -5
 GSPARC_ERR_TOO_LARGE = -6
+GSPARC_ERR_INPUT = -7
 GSPARC_NOALLOC_MAX_N = 65536
 GSPARC_NOALLOC_MAX_PAIRS = 524288
 GSPARC_FP32, GSPARC_BF16, GSPARC_BF16X2 = 0, 1, 2
@@ -38,7 +39,8 @@ EXPORTS = [
     "gsparc_l2_loss", "gsparc_csi_head", "gsparc_csi_loss", "gsparc_csi_head_bwd",
     "gsparc_spectrum_loss_workspace", "gsparc_spectrum_loss",
     "gsparc_render_csi_tc", "gsparc_render_fwd_l2_tc", "gsparc_confidence", "gsparc_densify_accumulate",
-    "gsparc_densify_workspace", "gsparc_densify", "gsparc_opacity_reset", "gsparc_adam", "gsparc_check", "gsparc_strerror",
+    "gsparc_densify_workspace", "gsparc_densify", "gsparc_opacity_reset", "gsparc_adam", "gsparc_set_wait_limit",
+    "gsparc_check", "gsparc_strerror",
 ]
 
 
@@ -88,7 +90,7 @@ def lib():
         P = ctypes.POINTER
         sig = {
             "gsparc_num_tiles": (i32, [P(View)]),
-            "gsparc_project": (ctypes.c_int, [P(View), i32, vp, vp, vp, vp, vp]),
+            "gsparc_project": (ctypes.c_int, [P(View), i32, vp, vp, vp, vp, vp, vp]),
             "gsparc_project_bwd": (ctypes.c_int, [P(View), i32, vp, vp, vp, vp, vp, vp, vp, vp]),
             "gsparc_bin_sort_workspace": (ctypes.c_int, [P(View), i32, i64, P(ctypes.c_size_t)]),
             "gsparc_bin_sort": (ctypes.c_int, [P(View), i32, vp, i64, vp, ctypes.c_size_t, vp, vp, vp,
@@ -104,13 +106,13 @@ def lib():
             "gsparc_emission_bwd": (ctypes.c_int, [i32, i32, i32, vp, P(f32), vp, vp, vp, i32, vp, vp, vp, vp,
                                                    vp]),
             "gsparc_render_fwd": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
-                                                 vp, vp, vp]),
-            "gsparc_render_fwd_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
-                                                    vp, vp, vp]),
-            "gsparc_render_bwd": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
                                                  vp, vp, vp, vp]),
-            "gsparc_render_bwd_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
+            "gsparc_render_fwd_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
                                                     vp, vp, vp, vp]),
+            "gsparc_render_bwd": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
+                                                 vp, vp, vp, vp, vp]),
+            "gsparc_render_bwd_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
+                                                    vp, vp, vp, vp, vp]),
             "gsparc_l2_loss": (ctypes.c_int, [i64, vp, vp, vp, vp, vp]),
             "gsparc_csi_head": (ctypes.c_int, [i32, i32, i64, vp, f32, vp, vp]),
             "gsparc_csi_loss": (ctypes.c_int, [i32, i32, vp, vp, vp, vp, vp]),
@@ -119,13 +121,13 @@ def lib():
             "gsparc_spectrum_loss": (ctypes.c_int, [i32, i32, i32, i32, vp, vp, f32, vp, ctypes.c_size_t, vp, vp,
                                                     vp]),
             "gsparc_render_csi_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
-                                                    vp, vp, vp, vp]),
+                                                    vp, vp, vp, vp, vp]),
             "gsparc_render_fwd_l2_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
-                                                       vp, vp, vp, vp, vp, vp, vp, vp]),
+                                                       vp, vp, vp, vp, vp, vp, vp, vp, vp]),
             "gsparc_render_bwd_tc_workspace": (ctypes.c_int, [P(View), P(Band), i32, P(ctypes.c_size_t)]),
             "gsparc_render_bwd_tc_balanced": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp,
                                                              vp, vp, vp, vp, vp, i32, vp, ctypes.c_size_t, vp,
-                                                             vp, vp]),
+                                                             vp, vp, vp]),
             "gsparc_confidence": (ctypes.c_int, [i32, i32, vp, vp, vp, f32, vp, vp, vp, vp, vp]),
             "gsparc_densify_accumulate": (ctypes.c_int, [i32, vp, vp, vp, vp, vp]),
             "gsparc_densify_workspace": (ctypes.c_int, [i32, P(ctypes.c_size_t)]),
@@ -133,6 +135,7 @@ def lib():
                                               vp, ctypes.c_size_t, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
             "gsparc_opacity_reset": (ctypes.c_int, [i32, f32, vp, vp]),
             "gsparc_adam": (ctypes.c_int, [i64, vp, vp, vp, vp, f32, f32, f32, f32, i32, vp]),
+            "gsparc_set_wait_limit": (ctypes.c_uint32, [ctypes.c_uint32]),
             "gsparc_check": (ctypes.c_int, [vp, vp]),
             "gsparc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         }
@@ -208,9 +211,9 @@ def gsparc_num_tiles(view: View) -> int:
     return int(lib().gsparc_num_tiles(ctypes.byref(view)))
 
 
-def gsparc_project(view, means, log_scales, quats, proj, stream=None):
+def gsparc_project(view, means, log_scales, quats, proj, stream=None, d_status=None):
     _call("gsparc_project", ctypes.byref(view), means.shape[0], _p(means), _p(log_scales), _p(quats),
-          _p(proj), _stream(stream))
+          _p(proj), _p(d_status), _stream(stream))
 
 
 def gsparc_project_bwd(view, means, log_scales, quats, d_proj, d_means, d_log_scales, d_quats,
@@ -264,31 +267,31 @@ def gsparc_attr_mlp_bwd_tc(tx, rx, means, opacity_logit, latent, mlp: MLP, preci
 
 
 def gsparc_render_fwd(view, band, B, n, proj, tile_ranges, sorted_ids, attr, spectrum,
-                      final_logT=None, n_contrib=None, n_used=None, stream=None):
+                      final_logT=None, n_contrib=None, n_used=None, stream=None, d_status=None):
     _call("gsparc_render_fwd", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
           _p(tile_ranges), _p(sorted_ids), _p(attr), _p(spectrum), _p(final_logT), _p(n_contrib),
-          _p(n_used), _stream(stream))
+          _p(n_used), _p(d_status), _stream(stream))
 
 
 def gsparc_render_fwd_tc(view, band, B, n, proj, tile_ranges, sorted_ids, attr, spectrum,
-                         final_logT=None, n_contrib=None, n_used=None, stream=None):
+                         final_logT=None, n_contrib=None, n_used=None, stream=None, d_status=None):
     _call("gsparc_render_fwd_tc", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
           _p(tile_ranges), _p(sorted_ids), _p(attr), _p(spectrum), _p(final_logT), _p(n_contrib),
-          _p(n_used), _stream(stream))
+          _p(n_used), _p(d_status), _stream(stream))
 
 
 def gsparc_render_bwd(view, band, B, n, proj, tile_ranges, sorted_ids, attr, final_logT, n_contrib,
-                      d_spectrum, d_attr, d_proj, stream=None):
+                      d_spectrum, d_attr, d_proj, stream=None, d_status=None):
     _call("gsparc_render_bwd", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
           _p(tile_ranges), _p(sorted_ids), _p(attr), _p(final_logT), _p(n_contrib), _p(d_spectrum),
-          _p(d_attr), _p(d_proj), _stream(stream))
+          _p(d_attr), _p(d_proj), _p(d_status), _stream(stream))
 
 
 def gsparc_render_bwd_tc(view, band, B, n, proj, tile_ranges, sorted_ids, attr, final_logT, n_contrib,
-                         d_spectrum, d_attr, d_proj, stream=None):
+                         d_spectrum, d_attr, d_proj, stream=None, d_status=None):
     _call("gsparc_render_bwd_tc", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
           _p(tile_ranges), _p(sorted_ids), _p(attr), _p(final_logT), _p(n_contrib), _p(d_spectrum),
-          _p(d_attr), _p(d_proj), _stream(stream))
+          _p(d_attr), _p(d_proj), _p(d_status), _stream(stream))
 
 
 def gsparc_emission_stride(hidden) -> int:
@@ -330,13 +333,13 @@ def s_tot_strips(K) -> int:
 
 def gsparc_render_bwd_tc_balanced(view, band, B, n, proj, tile_ranges, sorted_ids, attr, spectrum, s_tot,
                                   final_logT, n_contrib, d_spectrum, ws, d_attr, d_proj, split_min=0,
-                                  tile_walk=None, stream=None):
+                                  tile_walk=None, stream=None, d_status=None):
     """ws: a uint8 device tensor of gsparc_render_bwd_tc_workspace() bytes, zeroed once
     (torch.zeros) before its first use."""
     _call("gsparc_render_bwd_tc_balanced", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
           _p(tile_ranges), _p(sorted_ids), _p(attr), _p(spectrum), _p(s_tot), _p(tile_walk), _p(final_logT),
           _p(n_contrib), _p(d_spectrum), int(split_min), _p(ws), ws.numel() * ws.element_size(), _p(d_attr),
-          _p(d_proj), _stream(stream))
+          _p(d_proj), _p(d_status), _stream(stream))
 
 
 def gsparc_l2_loss(z, target, loss, d_z=None, stream=None):
@@ -426,23 +429,29 @@ def gsparc_csi_head_bwd(d_csi, d_spectrum, scale, stream=None):
 
 
 def gsparc_render_csi_tc(view, band, B, n, proj, tile_ranges, sorted_ids, attr, csi, spectrum=None,
-                         final_logT=None, n_contrib=None, n_used=None, stream=None):
+                         final_logT=None, n_contrib=None, n_used=None, stream=None, d_status=None):
     _call("gsparc_render_csi_tc", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
           _p(tile_ranges), _p(sorted_ids), _p(attr), _p(csi), _p(spectrum), _p(final_logT), _p(n_contrib),
-          _p(n_used), _stream(stream))
+          _p(n_used), _p(d_status), _stream(stream))
 
 
 def gsparc_render_fwd_l2_tc(view, band, B, n, proj, tile_ranges, sorted_ids, attr, target, loss, d_spectrum,
                             spectrum=None, final_logT=None, n_contrib=None, n_used=None, s_tot=None,
-                            tile_walk=None, stream=None):
+                            tile_walk=None, stream=None, d_status=None):
     _call("gsparc_render_fwd_l2_tc", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
           _p(tile_ranges), _p(sorted_ids), _p(attr), _p(target), _p(loss), _p(d_spectrum), _p(spectrum),
-          _p(final_logT), _p(n_contrib), _p(n_used), _p(s_tot), _p(tile_walk), _stream(stream))
+          _p(final_logT), _p(n_contrib), _p(n_used), _p(s_tot), _p(tile_walk), _p(d_status), _stream(stream))
 
 
 def gsparc_adam(param, grad, m, v, lr, step, b1=0.9, b2=0.999, eps=1e-15, stream=None):
     _call("gsparc_adam", param.numel(), _p(param), _p(grad), _p(m), _p(v), float(lr), float(b1),
           float(b2), float(eps), int(step), _stream(stream))
+
+
+def gsparc_set_wait_limit(polls: int) -> int:
+    """Polls before a pipeline wait of the tensor-core compositing kernels gives up (0: the
+    default); returns the previous setting.  For tests of the timeout path."""
+    return int(lib().gsparc_set_wait_limit(int(polls)))
 
 
 def gsparc_check(d_status=None, stream=None) -> int:

@@ -138,13 +138,15 @@ class Renderer:
     def geometry(self, scene: DeviceScene, keep_keys=False, stream=None):
         if keep_keys and self.sorted_keys is None:
             self.sorted_keys = torch.empty(max(1, self.capacity), dtype=torch.int64, device=self.device)
-        G.gsparc_project(self.view, scene.means, scene.log_scales, scene.quats, self.proj, stream)
+        G.gsparc_project(self.view, scene.means, scene.log_scales, scene.quats, self.proj, stream,
+                         d_status=self.status)
         G.gsparc_bin_sort(self.view, self.n, self.proj, self.capacity, self.ws, self.sorted_ids,
                           self.sorted_keys if keep_keys else None, self.tile_ranges, self.n_pairs,
                           self.status, stream)
 
     def check(self, stream=None) -> int:
-        """Synchronise and return the device status (0 when every wait and capacity held)."""
+        """Synchronise and return the device status (0 when every wait, capacity and device-side
+        input check held; the first condition raised by any of this renderer's calls otherwise)."""
         return G.gsparc_check(self.status, stream)
 
     # -- per-query attributes and compositing ---------------------------------------
@@ -170,7 +172,7 @@ class Renderer:
         spec, logT, nc = out if out is not None else self.alloc_outputs(B)
         fn = G.gsparc_render_fwd_tc if tensor_cores else G.gsparc_render_fwd
         fn(self.view, self.band, B, self.n, self.proj, self.tile_ranges, self.sorted_ids, attr, spec,
-           logT, nc, n_used, stream)
+           logT, nc, n_used, stream, d_status=self.status)
         return spec, logT, nc
 
     def render_csi(self, attr, csi=None, out=None, n_used=None, stream=None):
@@ -184,7 +186,7 @@ class Renderer:
             csi = torch.empty((B, self.K, 2), dtype=torch.float32, device=self.device)
         spec, logT, nc = out if out is not None else (None, None, None)
         G.gsparc_render_csi_tc(self.view, self.band, B, self.n, self.proj, self.tile_ranges,
-                               self.sorted_ids, attr, csi, spec, logT, nc, n_used, stream)
+                               self.sorted_ids, attr, csi, spec, logT, nc, n_used, stream, d_status=self.status)
         return csi
 
     def s_tot_buffer(self, B):
@@ -204,14 +206,15 @@ class Renderer:
         B = int(attr.shape[0])
         if not tensor_cores:
             G.gsparc_render_bwd(self.view, self.band, B, self.n, self.proj, self.tile_ranges, self.sorted_ids,
-                                attr, logT, nc, d_spec, d_attr, d_proj, stream)
+                                attr, logT, nc, d_spec, d_attr, d_proj, stream, d_status=self.status)
             return
         need = G.gsparc_render_bwd_tc_workspace(self.view, self.band, B)
         if self.bwd_ws is None or self.bwd_ws.numel() < need:
             self.bwd_ws = torch.zeros(need, dtype=torch.uint8, device=self.device)
         G.gsparc_render_bwd_tc_balanced(self.view, self.band, B, self.n, self.proj, self.tile_ranges,
                                         self.sorted_ids, attr, spectrum, s_tot, logT, nc, d_spec, self.bwd_ws,
-                                        d_attr, d_proj, split_min=split_min, tile_walk=tile_walk, stream=stream)
+                                        d_attr, d_proj, split_min=split_min, tile_walk=tile_walk, stream=stream,
+                                        d_status=self.status)
 
     def attributes_backward(self, scene, mlp, tx, d_attr, d_means, d_ologit, d_latent, d_weights,
                             stream=None, tensor_cores=False):

@@ -88,7 +88,7 @@ int main(int argc, char** argv) {
     std::vector<float4> proj(2 * (size_t)n);
     const unsigned pblk = (unsigned)((n + 255) / 256);
     emu_launch(emu_dim3{pblk, 1, 1}, 256, k_project, vd, n, (const float*)means.data(), (const float*)ls.data(),
-               (const float4*)quats.data(), proj.data());
+               (const float4*)quats.data(), proj.data(), static_cast<int32_t*>(nullptr));
     // binning and sort
     const int TW = tiles_x(view), T = TW * tiles_y(view);
     const uint32_t cap = 64u * (uint32_t)n + 64u;

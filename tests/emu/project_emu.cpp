@@ -40,7 +40,7 @@ int main(int argc, char** argv) {
     const unsigned blocks = (unsigned)((N + 255) / 256);
     if (N > 0) {
         emu_launch(emu_dim3{blocks, 1, 1}, 256, gsparc::k_project, v, N, (const float*)means.data(),
-                   (const float*)ls.data(), (const float4*)quats.data(), proj.data());
+                   (const float*)ls.data(), (const float4*)quats.data(), proj.data(), static_cast<int32_t*>(nullptr));
         emu_launch(emu_dim3{blocks, 1, 1}, 256, gsparc::k_project_bwd, v, N, (const float*)means.data(),
                    (const float*)ls.data(), (const float4*)quats.data(), (const float4*)dproj.data(), dm.data(),
                    dl.data(), dq.data());

@@ -38,7 +38,7 @@ def _declarations():
     txt = open(os.path.join(ROOT, "include", "gsparc.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     out = {}
-    for m in re.finditer(r"(int32_t|int|const char\s*\*)\s*(gsparc_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", txt):
+    for m in re.finditer(r"(uint32_t|int32_t|int|const char\s*\*)\s*(gsparc_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", txt):
         params = [" ".join(p.split()) for p in m.group(3).split(",") if p.strip() and p.strip() != "void"]
         out[m.group(2)] = (" ".join(m.group(1).split()), params)
     return out
@@ -48,7 +48,7 @@ def test_binding_signatures_match_the_header(L):
     """Every binding's ctypes argument list against the header: the same number of arguments,
     the same scalar type at every scalar position, a pointer at every pointer position (a
     pointer to the named struct where the header names one), and the return type."""
-    scalars = {"int32_t": ctypes.c_int32, "int": ctypes.c_int, "int64_t": ctypes.c_int64,
+    scalars = {"int32_t": ctypes.c_int32, "uint32_t": ctypes.c_uint32, "int": ctypes.c_int, "int64_t": ctypes.c_int64,
                "float": ctypes.c_float, "size_t": ctypes.c_size_t}
     structs = {"gsparc_view": G.View, "gsparc_band": G.Band, "gsparc_mlp": G.MLP,
                "gsparc_mlp_grad": G.MLPGrad, "gsparc_densify_params": G.DensifyParams,
@@ -58,7 +58,8 @@ def test_binding_signatures_match_the_header(L):
     for name, (ret, params) in decls.items():
         fn = getattr(L, name)
         assert len(fn.argtypes) == len(params), name
-        want_ret = {"int": ctypes.c_int, "int32_t": ctypes.c_int32, "const char *": ctypes.c_char_p,
+        want_ret = {"int": ctypes.c_int, "int32_t": ctypes.c_int32, "uint32_t": ctypes.c_uint32,
+                    "const char *": ctypes.c_char_p,
                     "const char*": ctypes.c_char_p}[ret]
         assert fn.restype is want_ret, name
         for k, (decl, got) in enumerate(zip(params, fn.argtypes)):
@@ -93,16 +94,16 @@ def test_workspace_query_grows_with_capacity(L):
 def test_invalid_arguments_rejected_on_host(L):
     v = G.make_view(90, 360)
     vp = ctypes.c_void_p
-    assert L.gsparc_project(ctypes.byref(v), -1, None, None, None, None, None) == G.GSPARC_ERR_INVALID
-    assert L.gsparc_project(ctypes.byref(v), 5, None, None, None, None, None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_project(ctypes.byref(v), -1, None, None, None, None, None, None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_project(ctypes.byref(v), 5, None, None, None, None, None, None) == G.GSPARC_ERR_INVALID
     bad = G.make_view(0, 360)
-    assert L.gsparc_project(ctypes.byref(bad), 0, None, None, None, None, None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_project(ctypes.byref(bad), 0, None, None, None, None, None, None) == G.GSPARC_ERR_INVALID
     out = ctypes.c_size_t(0)
     assert L.gsparc_bin_sort_workspace(ctypes.byref(v), 10, 1 << 31, ctypes.byref(out)) == \
         G.GSPARC_ERR_INVALID
     band = G.make_band(0)
     assert L.gsparc_render_fwd(ctypes.byref(v), ctypes.byref(band), 1, 0, None, vp(256), vp(256), None,
-                               vp(256), None, None, None, None) == G.GSPARC_ERR_INVALID
+                               vp(256), None, None, None, None, None) == G.GSPARC_ERR_INVALID
     m = G.MLP()
     m.hidden = 12
     rx = (ctypes.c_float * 3)(0, 0, 0)
@@ -171,7 +172,7 @@ def test_scheduled_backward_workspace_and_arguments(L):
     def call(ws=vp(4096), ws_bytes=need, d_attr=vp(4096), d_spectrum=vp(4096)):
         return L.gsparc_render_bwd_tc_balanced(ctypes.byref(v), ctypes.byref(band), 1, 10, vp(4096), vp(4096),
                                                vp(4096), vp(4096), vp(4096), None, None, vp(4096), vp(4096),
-                                               d_spectrum, 0, ws, ws_bytes, d_attr, vp(4096), None)
+                                               d_spectrum, 0, ws, ws_bytes, d_attr, vp(4096), None, None)
 
     assert call(ws=None) == G.GSPARC_ERR_INVALID
     assert call(ws_bytes=need - 16) == G.GSPARC_ERR_INVALID
@@ -200,7 +201,7 @@ def test_csi_and_fused_loss_arguments(L):
                                (vp(260), vp(256), vp(256))]:
         assert L.gsparc_render_fwd_l2_tc(ctypes.byref(v), ctypes.byref(band), 1, 10, vp(256), vp(256), vp(256),
                                          vp(256), target, loss, grad, vp(256), vp(256), vp(256), None, None,
-                                         None, None) == G.GSPARC_ERR_INVALID
+                                         None, None, None) == G.GSPARC_ERR_INVALID
 
 
 def test_confidence_arguments(L):
