@@ -1,38 +1,40 @@
 """Benchmark of the splatting hot path on one GB300 (or N independent replicas).
 
-Workload (one step = one pass of the whole path over one query):
-  50,000 Gaussians (seeded synthetic scene: means uniform in a 10 m cube
-  around the receiver, upper hemisphere; log-scales N(-1.5, 0.5); random unit
-  quaternions; opacity logits N(0,1); 16-dim latents N(0,1)), one transmitter,
-  64 subcarriers 312.5 kHz apart about 2.4 GHz, 360x90 hemisphere (1-degree
-  bins, 16x16 tiles), attribute network 20 -> 32 -> 32 -> 3 (split-BF16 on
-  the tensor cores in the default configuration, FP32 with --render fp32).
-  Step = project -> bin/sort -> attribute network -> render forward ->
-  complex L2 loss against a target spectrum (rendered by the same path from a
-  second seeded scene, once, outside the timed region) -> render backward ->
-  network backward -> projection backward.
+Headline workload (one step = one pass of the whole path over one query):
+  50,000 Gaussians (seeded synthetic scene: means uniform in a 10 m cube around the receiver,
+  upper hemisphere; log-scales N(-1.5, 0.5); random unit quaternions; opacity logits N(0,1);
+  16-dim latents N(0,1)), one transmitter, 64 subcarriers 312.5 kHz apart about 2.4 GHz,
+  360x90 hemisphere (1-degree bins, 16x16 tiles), attribute network 20 -> 32 -> 32 -> 3.
+  Step = project -> bin/sort -> attribute network -> render forward -> complex L2 loss against a
+  target spectrum (rendered once, outside the timed region, from a second seeded scene) ->
+  render backward -> network backward -> projection backward.  The headline arithmetic is FP32
+  on the CUDA cores throughout (`--render fp32`, the default); the tensor-core form (split-BF16
+  products with FP32 accumulation for the subcarrier contractions and the network, FP32
+  transmittance) is timed beside it and reported under `forms`.
 
-Metric: Gaussian-pixel-subcarrier units per second, where a unit is one
-Gaussian composited at one pixel (counted up to termination by the forward
-kernel's per-pixel counter) for one subcarrier; fwd+bwd per step.
+Metric: Gaussian-pixel-subcarrier units per second, where a unit is one Gaussian composited at
+one pixel (counted up to termination by the forward kernel's per-pixel counter) for one
+subcarrier; fwd+bwd per step.
 
-`value` times the step on the device with inputs resident in HBM (CUDA
-events on the launching stream, L2 flushed by a 256 MiB write between timed
-steps; the loss fused into the forward).  `e2e` times the step through the C
-ABI with the scene, network, transmitters and target copied from pinned host
-memory and the loss read back, inside the timed region; its graph overlaps
-the target's copy with projection, binning and the forward (which then writes
-the spectrum, and the loss follows once the target is in), and it is checked
-against the device-resident step's loss and gradients before timing.  `roofline` reports the dominant kernel against the FP32 ALU
-peak; `cpu_baseline` times the FP64 oracle on a bounded pixel sample.
+`value` times the step on the device with inputs resident in HBM (CUDA events on the launching
+stream, L2 flushed by a 256 MiB write between timed steps).  `e2e` times the same step through
+the C ABI with the scene, network, transmitters and target copied from pinned host memory and
+the loss read back, inside the timed region (the target's copy overlaps projection, binning and
+the forward).  `roofline` reports the dominant kernel against the FP32 ALU peak; `cpu_baseline`
+times the FP64 oracle on a bounded pixel sample and reports the GPU spectra's error against it.
+The default line also carries the other configurations: `c1_query_latency` (single query),
+`c3_batched` (64 transmitters per launch vs the plain path), `c4_train` (training loop steps/s
+and held-out error), `c5_serve` (continuous batching vs the plain path under Poisson load) and
+`probes` (FMA and ex2 throughput measured on this GPU).
 
-Multi-GPU: queries are independent, so N ranks run N replicas on their own
-transmitters (weak scaling) with no data-path collective; timing is the max
-over ranks.  `--impl reference` times the FP64 CPU oracle as the reference arm.
+Multi-GPU: queries are independent, so N ranks run N replicas on their own transmitters (weak
+scaling) with no data-path collective; timing is the max over ranks.  `--impl reference` times
+the FP64 CPU oracle as the reference arm.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -51,8 +53,14 @@ METRIC = "Gaussian·pixel·subcarrier/s fwd+bwd and p50/p99 spectrum latency vs 
 UNIT = "Gaussian·pixel·subcarrier/s"
 WORKLOAD = dict(name="fwd+bwd, 50k Gaussians, 64 subcarriers, 360x90, hidden 32, 1 transmitter",
                 n=50_000, K=64, H=90, W=360, hidden=32, B=1, f_c=2.4e9, df=312.5e3)
-FLOP_FWD_UNIT = 4     # z += w * e^{j psi}: two FMAs per (pixel, Gaussian, subcarrier)
-FLOP_BWD_UNIT = 12    # Re, Im and frequency-weighted Im of conj(g) e^{j psi}: six FMAs
+# Algorithmic work per unit (one Gaussian composited at one pixel for one subcarrier), as the
+# scope table counts it: forward ~10 flop (the complex product of w = T alpha with the emission
+# a e^{j psi} and its accumulation), backward ~20 flop (the conjugate products of dL/dz with
+# the emission for the alpha, amplitude, phase and path-length derivatives).  The kernels hoist
+# the per-(Gaussian, subcarrier) phasor out of the pixel loop and execute 2 and 6 FMAs per unit.
+FLOP_FWD_UNIT = 10
+FLOP_BWD_UNIT = 20
+FMA_FWD_UNIT, FMA_BWD_UNIT = 2, 6
 FP32_LANES_PER_SM = 128
 
 
@@ -133,29 +141,76 @@ def measured_peaks():
     return {}
 
 
-# --------------------------------------------------------------------------------------------
-# our arm
-# --------------------------------------------------------------------------------------------
-
-def run_ours(args, rank, world, local_rank):
+def probe_peaks(dev, local_rank):
+    """FMA and ex2 throughput of this GPU (libgsparc_probe.so): 8 independent chains per thread,
+    8 blocks of 256 threads per SM, best of 5 launches of ~20 ms, CUDA events; the SM clock is
+    sampled meanwhile.  Returns per-second rates, their value per SM per clock at the sampled
+    clock, and the FP32 peak they imply at the maximum clock."""
     import torch
 
-    from paper_2511_22793_gb300 import gsparc as G
+    path = os.path.join(ROOT, "paper_2511_22793_gb300", "libgsparc_probe.so")
+    if not os.path.exists(path):
+        raise RuntimeError("libgsparc_probe.so is not built; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    lib.gsparc_probe_launch.restype = ctypes.c_int64
+    lib.gsparc_probe_launch.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = sms * 8
+    out = torch.empty(blocks * 256, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    sampler.wait_first()
+    res = {}
+    for kind, name, iters in ((0, "fma", 6000), (1, "ex2", 1500)):
+        best = None
+        for rep in range(6):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ops = lib.gsparc_probe_launch(kind, blocks, iters, ctypes.c_void_p(out.data_ptr()),
+                                          ctypes.c_void_p(stream.cuda_stream))
+            e1.record(stream)
+            e1.synchronize()
+            if ops < 0:
+                raise RuntimeError("probe launch failed")
+            if rep == 0:
+                continue
+            rate = ops / (e0.elapsed_time(e1) * 1e-3)
+            best = rate if best is None else max(best, rate)
+        res[name] = best
+    clocks = sampler.stop()
+    mhz = float(clocks["sm_mhz"]) if clocks else None
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    out_d = {"fma_per_s": res["fma"], "ex2_per_s": res["ex2"], "clocks": clocks, "sms": sms,
+             "method": "8 independent chains per thread, %d blocks x 256 threads, best of 5 launches, CUDA events"
+                       % blocks}
+    if mhz:
+        out_d["fma_per_sm_per_clk"] = res["fma"] / (sms * mhz * 1e6)
+        out_d["ex2_per_sm_per_clk"] = res["ex2"] / (sms * mhz * 1e6)
+        out_d["fp32_tflops_at_max_clock"] = 2 * out_d["fma_per_sm_per_clk"] * sms * sm_max * 1e6 / 1e12
+    return out_d
+
+
+# --------------------------------------------------------------------------------------------
+# our arm: the headline training step
+# --------------------------------------------------------------------------------------------
+
+def _make_inputs(dev, rank, world):
+    """Seeded scene, network, transmitter of this rank and the target spectrum (rendered by the
+    FP32 path from the seed-1 scene, not timed), as views of one device allocation with a pinned
+    host mirror (the end-to-end step copies them from there)."""
+    import torch
+
     from paper_2511_22793_gb300 import synth
     from paper_2511_22793_gb300.pipeline import DeviceMLP, DeviceScene, PackedInputs, Renderer
-    from paper_2511_22793_gb300.replicas import job_totals, rank_queries, throughput
+    from paper_2511_22793_gb300.replicas import rank_queries
 
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
     wl = WORKLOAD
     n, K, H, W, hidden, B = wl["n"], wl["K"], wl["H"], wl["W"], wl["hidden"], wl["B"]
     sc = synth.make_scene(n, seed=0)
     mlp = synth.make_mlp(hidden, seed=3)
     tx = rank_queries(synth.make_tx(B * world, seed=2), B, rank, world)
-    r = Renderer(H, W, K, n, f_c=wl["f_c"], df=wl["df"], device=dev)
-    stream = torch.cuda.current_stream(dev)
-
-    # target spectrum: the same path on a second seeded scene (not timed)
     sc_t = synth.make_scene(n, seed=1)
     rt = Renderer(H, W, K, n, f_c=wl["f_c"], df=wl["df"], device=dev)
     dst = DeviceScene.from_host(sc_t, dev)
@@ -163,10 +218,10 @@ def run_ours(args, rank, world, local_rank):
     txd = torch.tensor(tx, device=dev)
     rt.geometry(dst)
     target = rt.render(rt.attributes(dst, dm, txd))[0].clone()
+    torch.cuda.synchronize(dev)
+    if rt.check() != 0:
+        raise RuntimeError("target render failed")
     del rt, dst
-
-    # the step's inputs (scene, network, transmitters, target spectrum) share one device
-    # allocation: the end-to-end step moves them from pinned host memory in one copy
     arrays = list(sc.arrays()) + list(mlp.arrays()) + [txd, target]
     inp = PackedInputs([tuple(np.shape(a)) if not isinstance(a, torch.Tensor) else tuple(a.shape)
                         for a in arrays], dev)
@@ -174,212 +229,57 @@ def run_ours(args, rank, world, local_rank):
         inp.set_host(i, a)
     inp.upload()
     torch.cuda.synchronize(dev)
+    return sc, mlp, tx, inp
+
+
+def time_form(args, dev, form, inp, steps, flush, sampler=None, dist=False):
+    """Build the step of `form` on the packed inputs, check it, time its kernels (eager, per
+    stage), the step graph (device-resident inputs) and the host-input graph (end to end)."""
+    import torch
+
+    from paper_2511_22793_gb300 import gsparc as G
+    from paper_2511_22793_gb300.pipeline import DeviceMLP, DeviceScene, Renderer
+    from paper_2511_22793_gb300.step import TrainStep
+
+    wl = WORKLOAD
+    n, K, H, W, hidden = wl["n"], wl["K"], wl["H"], wl["W"], wl["hidden"]
     ds = DeviceScene(*inp.views[0:5])
     dm = DeviceMLP(hidden, *inp.views[5:11])
     txd, target = inp.views[11], inp.views[12]
-    attr = torch.empty((B, n, 4), device=dev)
-    spec, logT, nc = r.alloc_outputs(B)
-    n_used = torch.zeros((B, H, W), dtype=torch.int32, device=dev)
-    loss = torch.zeros(1, device=dev)
-    d_spec = torch.empty_like(spec)
-    # every gradient buffer is a view of one flat allocation, zeroed by one memset per step
-    shapes = [attr.shape, r.proj.shape] + [t.shape for t in ds.tensors()] + [t.shape for t in dm.tensors()]
-    sizes = [int(np.prod(sh)) for sh in shapes]
-    offs = np.cumsum([0] + [(z + 63) // 64 * 64 for z in sizes])
-    gbuf = torch.zeros(int(offs[-1]), device=dev)
-    views = [gbuf[int(o):int(o) + z].view(sh) for o, z, sh in zip(offs[:-1], sizes, shapes)]
-    d_attr, d_proj, grads = views[0], views[1], views[2:]
-    mlp_s = dm.struct()
-    grad_s = G.make_mlp_grad(*grads[5:])
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    launches_per_step = 0
-    ev = {}
-    render_fwd = G.gsparc_render_fwd_tc if args.render == "tc" else G.gsparc_render_fwd
-    # tensor-core configuration: the backward scheduled over the SMs (walk lengths, then the
-    # longest work items first, long walks split in two), its front chunks fed by the fused
-    # forward's s_tot and its schedule by the forward's tile walks
-    s_tot = r.s_tot_buffer(B) if args.render == "tc" else None
-    walks = r.walk_buffer(B) if args.render == "tc" else None
-    bwd_ws = torch.zeros(G.gsparc_render_bwd_tc_workspace(r.view, r.band, B), dtype=torch.uint8, device=dev)
-
-    def render_bwd():
-        if args.render == "tc":
-            G.gsparc_render_bwd_tc_balanced(r.view, r.band, B, n, r.proj, r.tile_ranges, r.sorted_ids, attr,
-                                            None, s_tot, logT, nc, d_spec, bwd_ws, d_attr, d_proj, tile_walk=walks)
-        else:
-            G.gsparc_render_bwd(r.view, r.band, B, n, r.proj, r.tile_ranges, r.sorted_ids, attr, logT, nc,
-                                d_spec, d_attr, d_proj)
-    # the tensor-core configuration runs the attribute network forward and backward on the tensor
-    # cores as well (split-BF16, the same products in both, so the ReLU masks agree)
-    mlp_tc = args.render == "tc" and hidden in (16, 32)
-    mlp_prec = G.GSPARC_BF16X2 if mlp_tc else G.GSPARC_FP32
-
-    def mlp_bwd(scene):
-        if mlp_tc:
-            G.gsparc_attr_mlp_bwd_tc(txd, r.rx, scene.means, scene.opacity_logit, scene.latent, mlp_s,
-                                     G.GSPARC_BF16X2, d_attr, grads[0], grads[3], grads[4], grad_s)
-        else:
-            G.gsparc_attr_mlp_bwd(txd, r.rx, scene.means, scene.opacity_logit, scene.latent, mlp_s,
-                                  d_attr, grads[0], grads[3], grads[4], grad_s)
-
-    def stage(name, fn):
-        if name in ev:
-            ev[name][0].record(stream)
-        fn()
-        if name in ev:
-            ev[name][1].record(stream)
-
-    side = torch.cuda.Stream(dev)
-
-    def step(scene: DeviceScene, tgt, concurrent=False):
-        """One training step.  concurrent: the gradient zeroing and the attribute network run on
-        a side stream beside projection and bin/sort (they need neither), and the projection
-        backward beside the network backward (both only add into the gradients); used for the
-        graph, while the eager per-kernel timing keeps one stream."""
-        cur = torch.cuda.current_stream(dev)   # the capture stream while a graph is captured
-        if concurrent:
-            fork = torch.cuda.Event()
-            fork.record(cur)
-            side.wait_event(fork)
-            with torch.cuda.stream(side):
-                gbuf.zero_()   # the gradients are first written by the compositing backward
-            G.gsparc_attr_mlp(txd, r.rx, scene.means, scene.opacity_logit, scene.latent, mlp_s, mlp_prec,
-                              attr, side)
-            joined = torch.cuda.Event()
-            joined.record(side)
-        else:
-            gbuf.zero_()
-        stage("project", lambda: G.gsparc_project(r.view, scene.means, scene.log_scales, scene.quats,
-                                                  r.proj))
-        stage("bin_sort", lambda: G.gsparc_bin_sort(r.view, n, r.proj, r.capacity, r.ws, r.sorted_ids,
-                                                    None, r.tile_ranges, r.n_pairs, r.status))
-        if concurrent:
-            cur.wait_event(joined)
-        else:
-            stage("attr_mlp", lambda: G.gsparc_attr_mlp(txd, r.rx, scene.means, scene.opacity_logit,
-                                                        scene.latent, mlp_s, mlp_prec, attr))
-        if args.render == "tc":
-            # the loss fused into the forward's epilogue: it writes dL/dz, not the spectrum
-            stage("render_fwd", lambda: G.gsparc_render_fwd_l2_tc(r.view, r.band, B, n, r.proj, r.tile_ranges,
-                                                                  r.sorted_ids, attr, tgt, loss, d_spec, None,
-                                                                  logT, nc, n_used, s_tot=s_tot,
-                                                                  tile_walk=walks))
-        else:
-            stage("render_fwd", lambda: render_fwd(r.view, r.band, B, n, r.proj, r.tile_ranges,
-                                                   r.sorted_ids, attr, spec, logT, nc, n_used))
-            stage("l2_loss", lambda: G.gsparc_l2_loss(spec, tgt, loss, d_spec))
-        stage("render_bwd", render_bwd)
-
-        def proj_bwd(s=None):
-            G.gsparc_project_bwd(r.view, scene.means, scene.log_scales, scene.quats, d_proj, grads[0],
-                                 grads[1], grads[2], s)
-
-        if concurrent:
-            fork2 = torch.cuda.Event()
-            fork2.record(cur)
-            side.wait_event(fork2)
-            proj_bwd(side)
-            joined2 = torch.cuda.Event()
-            joined2.record(side)
-            mlp_bwd(scene)
-            cur.wait_event(joined2)
-        else:
-            stage("attr_mlp_bwd", lambda: mlp_bwd(scene))
-            stage("project_bwd", proj_bwd)
-
-    copy_s = torch.cuda.Stream(dev)
-    spec_e2e = spec
-
-    def step_e2e(scene: DeviceScene, tgt):
-        """The tensor-core step with host-resident inputs, its copies captured with it: scene,
-        network and transmitters first, then the 16.6 MB target spectrum on a third stream,
-        overlapping projection, binning and the forward.  The forward therefore writes the
-        spectrum and gsparc_l2_loss forms the loss and dL/dz once the target is in (the fused
-        form would hold the forward until the whole target had crossed the host link); the
-        backward's front chunks form s_tot from the spectrum.  Same loss, same gradients."""
-        cur = torch.cuda.current_stream(dev)
-        inp.upload(0, len(inp.views) - 1)
-        scene_in = torch.cuda.Event()
-        scene_in.record(cur)
-        copy_s.wait_event(scene_in)
-        with torch.cuda.stream(copy_s):
-            inp.upload(len(inp.views) - 1)
-        tgt_in = torch.cuda.Event()
-        tgt_in.record(copy_s)
-        side.wait_event(scene_in)
-        with torch.cuda.stream(side):
-            gbuf.zero_()
-        G.gsparc_attr_mlp(txd, r.rx, scene.means, scene.opacity_logit, scene.latent, mlp_s, mlp_prec, attr, side)
-        joined = torch.cuda.Event()
-        joined.record(side)
-        G.gsparc_project(r.view, scene.means, scene.log_scales, scene.quats, r.proj)
-        G.gsparc_bin_sort(r.view, n, r.proj, r.capacity, r.ws, r.sorted_ids, None, r.tile_ranges, r.n_pairs,
-                          r.status)
-        cur.wait_event(joined)
-        G.gsparc_render_fwd_tc(r.view, r.band, B, n, r.proj, r.tile_ranges, r.sorted_ids, attr, spec_e2e, logT,
-                               nc, n_used)
-        cur.wait_event(tgt_in)
-        G.gsparc_l2_loss(spec_e2e, tgt, loss, d_spec)
-        G.gsparc_render_bwd_tc_balanced(r.view, r.band, B, n, r.proj, r.tile_ranges, r.sorted_ids, attr, spec_e2e,
-                                        None, logT, nc, d_spec, bwd_ws, d_attr, d_proj)
-        fork2 = torch.cuda.Event()
-        fork2.record(cur)
-        side.wait_event(fork2)
-        G.gsparc_project_bwd(r.view, scene.means, scene.log_scales, scene.quats, d_proj, grads[0], grads[1],
-                             grads[2], side)
-        joined2 = torch.cuda.Event()
-        joined2.record(side)
-        mlp_bwd(scene)
-        cur.wait_event(joined2)
-
-    # kernels of ours launched per step: project 1, bin/sort 3 (count + scan, emit, per-tile
-    # sort), network 1, render 1, loss 1 (fused into the tensor-core forward), render bwd 1
-    # (+ its schedule in the tensor-core form), network bwd 1, projection bwd 1
-    launches_per_step = 1 + 3 + 1 + 1 + (1 if args.render != "tc" else 0) + (2 if args.render == "tc" else 1) + 1 + 1
-
+    r = Renderer(H, W, K, n, f_c=wl["f_c"], df=wl["df"], device=dev)
+    st = TrainStep(r, ds, dm, txd, target, form=form)
+    stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
-        step(ds, target)
+        st.enqueue()
     torch.cuda.synchronize(dev)
-    st = r.check()
-    if st != 0:
-        raise RuntimeError("device status %d after warm-up" % st)
-    units = int(n_used.sum().item()) * K
+    if r.check() != 0:
+        raise RuntimeError("device status %d after warm-up (%s)" % (r.check(), form))
+    units = int(st.n_used.sum().item()) * K
     n_pairs = int(r.n_pairs.item())
-
-    dist = world > 1
-    if dist:
-        import torch.distributed as tdist
-    names = ["project", "bin_sort", "attr_mlp", "render_fwd"] + (["l2_loss"] if args.render != "tc" else []) + \
-        ["render_bwd", "attr_mlp_bwd", "project_bwd"]
-    # per-kernel durations: eager steps with CUDA events around every stage (kernel time does not
-    # depend on how it was launched); the headline times the whole step as one CUDA graph
-    per_kernel = {k: [] for k in names}
-    for _ in range(min(args.steps, 50)):
+    # per-kernel durations: eager steps with CUDA events around every stage (one stream)
+    per_kernel = {k: [] for k in st.stages}
+    for _ in range(min(steps, 50)):
         flush.fill_(1.0)
-        for k in names:
-            ev[k] = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-        step(ds, target)
+        ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in st.stages}
+        st.enqueue(events=ev)
         torch.cuda.synchronize(dev)
-        for k in names:
+        for k in st.stages:
             per_kernel[k].append(ev[k][0].elapsed_time(ev[k][1]))
-    ev.clear()
-    # the step as one CUDA graph: the library only enqueues stream-ordered work, so it captures
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        step(ds, target, concurrent=True)
+    graph = st.capture()
     for _ in range(3):
         graph.replay()
     torch.cuda.synchronize(dev)
     if r.check() != 0:
-        raise RuntimeError("device status after graph warm-up")
-    step_ms = []
-    sampler = ClockSampler(local_rank)
+        raise RuntimeError("device status after graph warm-up (%s)" % form)
     if dist:
+        import torch.distributed as tdist
         tdist.barrier()
     torch.cuda.synchronize(dev)
-    sampler.start()
-    sampler.wait_first()
-    for _ in range(args.steps):
+    if sampler is not None:
+        sampler.start()
+        sampler.wait_first()
+    step_ms = []
+    for _ in range(steps):
         flush.fill_(1.0)                      # evict L2 between timed steps (not timed)
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
@@ -389,127 +289,167 @@ def run_ours(args, rank, world, local_rank):
         s1.synchronize()
         step_ms.append(s0.elapsed_time(s1))
     torch.cuda.synchronize(dev)
-    # whole job: the units all ranks processed over the slowest rank's time
-    job_units, total_ms = job_totals(units * args.steps, sum(step_ms), device=dev)
-    if dist:
-        tdist.barrier()
-
-    # end to end: host (pinned) inputs copied into the buffers the graph reads, the step, the loss
-    # read back -- all inside the timed region
-    # (the packed inputs' pinned mirror holds the scene, network, transmitters and target)
-    host_loss = torch.empty(1).pin_memory()
-    h2d = inp.nbytes
-    d2h = host_loss.numel() * host_loss.element_size()
-    # every input copied from the pinned mirror inside the timed step.  The host link moves
-    # ~165 GB/s (measured), so the 22 MB take ~0.13 ms: the tensor-core step overlaps the
-    # target's copy with projection, binning and the forward (step_e2e, one graph); the FP32
-    # configuration copies first, then replays its step graph.
-    graph_e2e = None
-    e2e_agree = None
-    e2e_copies = "one pinned host-to-device copy of all inputs (scene, network, transmitters, target), " \
-                 "then the step's graph"
-    if args.render == "tc":
-        graph_e2e = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph_e2e):
-            step_e2e(ds, target)
-        for _ in range(3):
-            graph_e2e.replay()
-        torch.cuda.synchronize(dev)
-        if r.check() != 0:
-            raise RuntimeError("device status after the end-to-end graph's warm-up")
-        # the two step graphs compute the same loss and gradients (not timed)
-        graph.replay()
-        torch.cuda.synchronize(dev)
-        loss_a, grad_a = float(loss), gbuf.clone()
+    loss_a, grad_a = float(st.loss), st.gbuf.clone()
+    # end to end: host (pinned) inputs copied inside the step's graph, the loss read back
+    graph_e2e = st.capture(inp)
+    for _ in range(3):
         graph_e2e.replay()
-        torch.cuda.synchronize(dev)
-        loss_b, grad_b = float(loss), gbuf.clone()
-        e2e_agree = {"loss_rel": abs(loss_a - loss_b) / abs(loss_a),
-                     "grad_rel_l2": float((grad_a - grad_b).norm() / grad_a.norm())}
-        if e2e_agree["loss_rel"] > 1e-5 or e2e_agree["grad_rel_l2"] > 1e-4:
-            raise RuntimeError("end-to-end step disagrees with the step graph: %s" % e2e_agree)
-        e2e_copies = "inside the step's graph: scene, network and transmitters first, the target spectrum " \
-                     "on a third stream beside projection, binning and the forward (spectrum written, " \
-                     "loss by gsparc_l2_loss once the target is in)"
+    torch.cuda.synchronize(dev)
+    if r.check() != 0:
+        raise RuntimeError("device status after the end-to-end graph's warm-up (%s)" % form)
+    loss_b, grad_b = float(st.loss), st.gbuf.clone()
+    agree = {"loss_rel": abs(loss_a - loss_b) / abs(loss_a),
+             "grad_rel_l2": float((grad_a - grad_b).norm() / grad_a.norm())}
+    if agree["loss_rel"] > 1e-5 or agree["grad_rel_l2"] > 1e-4:
+        raise RuntimeError("end-to-end step disagrees with the step graph (%s): %s" % (form, agree))
+    host_loss = torch.empty(1).pin_memory()
     e2e_ms = []
-    for it in range(args.warmup + args.steps):
+    for it in range(args.warmup + steps):
         flush.fill_(1.0)
         if dist and it == args.warmup:
+            import torch.distributed as tdist
             tdist.barrier()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        if graph_e2e is not None:
-            graph_e2e.replay()
-        else:
-            inp.upload()
-            graph.replay()
-        host_loss.copy_(loss, non_blocking=True)
+        graph_e2e.replay()
+        host_loss.copy_(st.loss, non_blocking=True)
         torch.cuda.current_stream(dev).synchronize()
         if it >= args.warmup:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    clocks = sampler.stop()   # sampled over both timed regions (device-timed and end to end)
-    job_units_e2e, e2e_total = job_totals(units * len(e2e_ms), sum(e2e_ms), device=dev)
+    clocks = sampler.stop() if sampler is not None else None
+    # the step's spectrum (the tensor-core step's fused forward does not store it): the same
+    # forward kernel once more with the spectrum stored, for the accuracy comparison
+    if form == "tc":
+        G.gsparc_render_fwd_l2_tc(r.view, r.band, st.B, n, r.proj, r.tile_ranges, r.sorted_ids, st.attr, target,
+                                  st.loss, st.d_spec, st.spec, st.logT, st.nc)
+    spec = st.spec.detach().cpu()
+    torch.cuda.synchronize(dev)
+    return {"st": st, "r": r, "units": units, "n_pairs": n_pairs, "step_ms": step_ms, "e2e_ms": e2e_ms,
+            "kernels_ms": {k: statistics.mean(v) for k, v in per_kernel.items()}, "agree": agree,
+            "clocks": clocks, "spec": spec, "h2d": inp.nbytes, "d2h": host_loss.numel() * host_loss.element_size()}
 
-    # dominant kernel and its roofline
-    avg = {k: statistics.mean(v) for k, v in per_kernel.items()}
+
+def roofline(form_res, dev, probes):
+    """Dominant kernel of the step against the FP32 ALU peak (SMs x 128 lanes x 2 flop x the
+    maximum SM clock), with the scope table's flop per unit; also against the FMA rate the probe
+    measured on this GPU, and as FMA-pipe issue (the FMAs the kernel executes per unit)."""
+    import torch
+
+    avg = form_res["kernels_ms"]
     top = max(avg, key=avg.get)
     peaks = measured_peaks()
-    props = torch.cuda.get_device_properties(dev)
-    sms = props.multi_processor_count
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12      # TFLOP/s
-    unit_flop = {"render_bwd": FLOP_BWD_UNIT, "render_fwd": FLOP_FWD_UNIT}
-    # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the tensor-core
-    # compositing kernels in this step (50k Gaussians, 64 subcarriers, 360x90, one transmitter),
-    # from one ncu capture of each current kernel (the forward with its fused loss)
-    traffic = {"render_bwd": 17510912, "render_fwd": 17157888} if args.render == "tc" else {}
-    if top in unit_flop:
-        achieved = units * unit_flop[top] / (avg[top] * 1e-3) / 1e12
-        roofline = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                    "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic.get(top),
-                    "traffic_unit": "bytes per launch (DRAM read + write)",
-                    "peak_note": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)"
-                                 % (sms, sm_max)}
-        if clocks and clocks.get("sm_mhz"):
-            # the same peak at the median SM clock sampled under load
-            roofline["frac_at_measured_clock"] = achieved / (fp32_peak * float(clocks["sm_mhz"]) / sm_max)
-    else:
-        roofline = {"kernel": top, "bound": "hbm", "achieved": None,
-                    "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s", "frac": None,
-                    "traffic": None}
+    units = form_res["units"]
+    flop = {"render_bwd": FLOP_BWD_UNIT, "render_fwd": FLOP_FWD_UNIT}
+    fma = {"render_bwd": FMA_BWD_UNIT, "render_fwd": FMA_FWD_UNIT}
+    out = {}
+    for k in ("render_bwd", "render_fwd"):
+        ms = avg[k]
+        achieved = units * flop[k] / (ms * 1e-3) / 1e12
+        d = {"kernel": k, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+             "frac": achieved / fp32_peak, "kernel_ms": ms,
+             "flop_per_unit": flop[k], "units_per_launch": units,
+             "peak_note": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % (sms, sm_max)}
+        if probes and probes.get("fp32_tflops_at_max_clock"):
+            d["peak_probe"] = probes["fp32_tflops_at_max_clock"]
+            d["frac_vs_probe"] = achieved / probes["fp32_tflops_at_max_clock"]
+        # FMA-pipe issue: the FMAs executed per unit against the pipe's lane rate
+        d["fma_issue_frac"] = units * fma[k] / (ms * 1e-3) / (sms * FP32_LANES_PER_SM * sm_max * 1e6)
+        out[k] = d
+    dom = dict(out[top]) if top in out else {"kernel": top, "bound": "hbm", "achieved": None,
+                                             "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s",
+                                             "frac": None}
+    return dom, out
 
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2511_22793_gb300.replicas import job_totals, throughput
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    wl = WORKLOAD
+    dist = world > 1
+    sc, mlp, tx, inp = _make_inputs(dev, rank, world)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    head = time_form(args, dev, args.render, inp, args.steps, flush, sampler=ClockSampler(local_rank), dist=dist)
+    units, step_ms, e2e_ms = head["units"], head["step_ms"], head["e2e_ms"]
+    # whole job: the units all ranks processed over the slowest rank's time
+    job_units, total_ms = job_totals(units * args.steps, sum(step_ms), device=dev)
+    job_units_e2e, e2e_total = job_totals(units * len(e2e_ms), sum(e2e_ms), device=dev)
     value = throughput(job_units, total_ms)
     e2e_value = throughput(job_units_e2e, e2e_total)
-    sorted_ms = sorted(step_ms)
-    latency = query_latency(dev, queries=max(50, min(args.steps, 400)))
+    probes = probe_peaks(dev, local_rank) if world == 1 else None
+    dom, rl = roofline(head, dev, probes)
+    st = head["st"]
+    tc_head = args.render == "tc"
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
-        "config": {"workload": wl["name"], "n_gaussians": n, "subcarriers": K, "H": H, "W": W,
-                   "hidden": hidden, "transmitters_per_step": B, "pairs": n_pairs,
-                   "units_per_step": job_units // args.steps, "l2": "flushed (256 MiB write) between timed steps",
-                   "compositing": "subcarrier sums on tensor cores (split-BF16 products, FP32 "
-                                  "accumulation), transmittance and gradients FP32"
-                                  if args.render == "tc" else "FP32 CUDA cores",
-                   "attribute_network": "tensor cores, split-BF16 products, FP32 accumulation "
-                                        "(forward and backward)" if mlp_tc else "FP32 CUDA cores",
+        "config": {"workload": wl["name"], "n_gaussians": wl["n"], "subcarriers": wl["K"], "H": wl["H"],
+                   "W": wl["W"], "hidden": wl["hidden"], "transmitters_per_step": wl["B"],
+                   "pairs": head["n_pairs"], "units_per_step": job_units // args.steps,
+                   "l2": "flushed (256 MiB write) between timed steps",
+                   "compositing": ("subcarrier sums on tensor cores (split-BF16 products, FP32 accumulation), "
+                                   "transmittance and gradients FP32") if tc_head else "FP32 CUDA cores",
+                   "attribute_network": ("tensor cores, split-BF16 products, FP32 accumulation"
+                                         if tc_head else "FP32 CUDA cores"),
+                   "target": "spectrum of a second seeded scene rendered by the FP32 path (not timed)",
                    "parallelism": "replicas x%d" % world},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
-                       "min": sorted_ms[0]},
-        "kernels_ms": avg,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": e2e_total / args.steps, "copies": e2e_copies,
-                "agrees_with_step_graph": e2e_agree},
-        "gpu_launches": launches_per_step * args.steps,
-        "launch": "whole step captured once as a CUDA graph (gradient zeroing and network forward "
-                  "beside projection and bin/sort, projection backward beside network backward, on a "
-                  "second stream), replayed per timed step",
-        "query_latency": latency,
-        "roofline": roofline,
-        "clocks": clocks,
+                       "min": float(min(step_ms))},
+        "kernels_ms": head["kernels_ms"],
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": head["h2d"],
+                "d2h_bytes_per_step": head["d2h"], "ms_per_step": e2e_total / args.steps,
+                "copies": "inside the step's graph: scene, network and transmitters first, the target spectrum "
+                          "on a third stream beside projection, binning and the forward (spectrum written, "
+                          "loss by gsparc_l2_loss once the target is in)",
+                "agrees_with_step_graph": head["agree"]},
+        "gpu_launches": st.launches * args.steps,
+        "launch": "whole step captured once as a CUDA graph (gradient zeroing and network forward beside "
+                  "projection and bin/sort, projection backward beside network backward, on a second "
+                  "stream), replayed per timed step",
+        "roofline": dom,
+        "roofline_kernels": rl,
+        "clocks": head["clocks"],
     }
-    return out, units, sc, mlp, tx
+    spectra = {args.render: head["spec"]}
+    if world == 1:
+        other = "fp32" if tc_head else "tc"
+        res_o = time_form(args, dev, other, inp, min(args.steps, 100), flush)
+        tot_o = sum(res_o["step_ms"])
+        dom_o, _ = roofline(res_o, dev, probes)
+        spectra[other] = res_o["spec"]
+        d_head = head["spec"].double()
+        d_o = res_o["spec"].double()
+        out["forms"] = {
+            ("tc_split_bf16" if other == "tc" else "fp32"): {
+                "value": res_o["units"] * len(res_o["step_ms"]) / (tot_o * 1e-3),
+                "unit": UNIT, "ms_per_step": tot_o / len(res_o["step_ms"]),
+                "e2e_ms_per_step": statistics.mean(res_o["e2e_ms"]),
+                "dtype": "split-BF16 operands (hi + lo, three products), FP32 accumulation" if other == "tc"
+                         else "f32",
+                "compositing": "subcarrier sums on tcgen05 tensor cores, alpha / transmittance / recursions FP32"
+                               if other == "tc" else "FP32 CUDA cores",
+                "attribute_network": "tcgen05, split-BF16, forward and backward" if other == "tc"
+                                     else "FP32 CUDA cores",
+                "kernels_ms": res_o["kernels_ms"], "roofline": dom_o,
+                "spectrum_rel_l2_vs_headline_form": float((d_o - d_head).norm() / d_head.norm()),
+                "gpu_launches_per_step": res_o["st"].launches,
+                "speedup_vs_headline": (total_ms / args.steps) / (tot_o / len(res_o["step_ms"])),
+            }}
+        del res_o
+        out["probes"] = probes
+        out["c1_query_latency"] = query_latency(dev, queries=max(50, min(args.steps, 400)))
+        if not args.quick:
+            out["c3_batched"] = run_batched(args, dev, emit=False)
+            out["c4_train"] = run_train(args, dev, emit=False)
+            out["c5_serve"] = run_serve(args, dev, emit=False, loads=(0.25, 0.5, 0.75, 0.9))
+    return out, spectra, sc, mlp, tx
 
 
 def query_latency(dev, queries=200):
@@ -564,74 +504,12 @@ def query_latency(dev, queries=200):
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
         res[name] = {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99))}
+    if r.check() != 0:
+        raise RuntimeError("single-query path status")
     res["workload"] = ("1,024 Gaussians, 1 subcarrier, 360x90, hidden 32, FP32, one query at a time, "
                        "each query's launches replayed as one CUDA graph")
     res["queries"] = queries
     return res
-
-
-def run_batched(args):
-    """Batched inference: 200,000 Gaussians, 64 transmitters in one launch, 256 subcarriers,
-    720x180, hidden 64; BF16X2 tensor-core network + FP32 compositing, against the plain path
-    (FP32 network, one transmitter per launch) on the same queries."""
-    import torch
-
-    from paper_2511_22793_gb300 import gsparc as G
-    from paper_2511_22793_gb300 import synth
-    from paper_2511_22793_gb300.pipeline import DeviceMLP, DeviceScene, Renderer
-
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    n, B, K, H, W, hd = 200_000, 64, 256, 180, 720, 64
-    sc = synth.make_scene(n, seed=0, bf16_latent=True)
-    mlp = synth.make_mlp(hd, seed=3, bf16_weights=True)
-    tx = torch.tensor(synth.make_tx(B, seed=2), device=dev)
-    r = Renderer(H, W, K, n, device=dev)
-    ds = DeviceScene.from_host(sc, dev)
-    dm = DeviceMLP.from_host(mlp, dev)
-    r.geometry(ds)
-    assert r.check() == 0
-    attr = torch.empty((B, n, 4), device=dev)
-    spec, logT, nc = r.alloc_outputs(B)
-    n_used = torch.empty((B, H, W), dtype=torch.int32, device=dev)
-    stream = torch.cuda.current_stream(dev)
-
-    def batched():
-        r.attributes(ds, dm, tx, G.GSPARC_BF16X2, out=attr)
-        r.render(attr, out=(spec, logT, nc), n_used=n_used)
-
-    attr1 = torch.empty((1, n, 4), device=dev)
-    out1 = r.alloc_outputs(1)
-
-    def plain():
-        for b in range(B):
-            r.attributes(ds, dm, tx[b:b + 1], G.GSPARC_FP32, out=attr1)
-            r.render(attr1, out=out1)
-
-    batched()
-    torch.cuda.synchronize(dev)
-    units = int(n_used.sum().item()) * K
-    res = {}
-    for name, fn, reps in (("batched_bf16x2", batched, args.steps), ("plain_fp32_one_query", plain, 1)):
-        fn()
-        torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            fn()
-        e1.record(stream)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        res[name] = {"ms_per_64_queries": ms, "units_per_s": units / (ms * 1e-3)}
-    out = {"metric": "Gaussian·pixel·subcarrier/s forward, batched", "value": res["batched_bf16x2"]["units_per_s"],
-           "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "bf16x2 network, f32 compositing",
-           "data": "synthetic (seeded)",
-           "config": {"workload": "batched inference, 200k Gaussians, 64 transmitters per launch, 256 subcarriers, "
-                                  "720x180, hidden 64", "units_per_launch": units, "pairs": int(r.n_pairs.item())},
-           "forms": res,
-           "speedup_vs_plain": res["plain_fp32_one_query"]["ms_per_64_queries"] / res["batched_bf16x2"]["ms_per_64_queries"]}
-    print(json.dumps(out))
 
 
 def run_emission(args):
@@ -893,50 +771,235 @@ def run_csi(args):
     print(json.dumps(out_line))
 
 
-def run_train(args):
+def _pix_sample(H, W, npix, seed):
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(H * W, size=npix, replace=False)).astype(np.int64)
+
+
+def _spec_at(spec_b, pix, W):
+    """[K, H, W, 2] device tensor -> [npix, K] complex128 (host) at linear pixel ids pix."""
+    import torch
+
+    ys = torch.as_tensor(pix // W, device=spec_b.device)
+    xs = torch.as_tensor(pix % W, device=spec_b.device)
+    z = spec_b[:, ys, xs].double().cpu().numpy()          # [K, npix, 2]
+    return (z[..., 0] + 1j * z[..., 1]).T
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def run_batched(args, dev=None, emit=True):
+    """Batched inference: 200,000 Gaussians, 64 transmitters in one launch, 256 subcarriers,
+    720x180, hidden 64; BF16X2 tensor-core network + tensor-core compositing, against the plain
+    path (FP32 network and FP32 compositing, one transmitter per launch) on the same queries.
+    Accuracy: every batched spectrum against the plain path's on the whole image, and (the
+    oracle leg, timed as a CPU baseline) both against the FP64 oracle on 128 seeded pixels of
+    8 of the transmitters."""
+    import torch
+
+    from paper_2511_22793_gb300 import gsparc as G
+    from paper_2511_22793_gb300 import synth
+    from paper_2511_22793_gb300.pipeline import DeviceMLP, DeviceScene, Renderer
+
+    if dev is None:
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+    n, B, K, H, W, hd = 200_000, 64, 256, 180, 720, 64
+    sc = synth.make_scene(n, seed=0, bf16_latent=True)
+    mlp = synth.make_mlp(hd, seed=3, bf16_weights=True)
+    txh = synth.make_tx(B, seed=2)
+    tx = torch.tensor(txh, device=dev)
+    r = Renderer(H, W, K, n, device=dev)
+    ds = DeviceScene.from_host(sc, dev)
+    dm = DeviceMLP.from_host(mlp, dev)
+    r.geometry(ds)
+    if r.check() != 0:
+        raise RuntimeError("batched geometry status")
+    attr = torch.empty((B, n, 4), device=dev)
+    spec, logT, nc = r.alloc_outputs(B)
+    n_used = torch.empty((B, H, W), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def batched():
+        r.attributes(ds, dm, tx, G.GSPARC_BF16X2, out=attr)
+        r.render(attr, out=(spec, logT, nc), n_used=n_used, tensor_cores=True)
+
+    attr1 = torch.empty((1, n, 4), device=dev)
+    out1 = r.alloc_outputs(1)
+
+    def plain(check=None):
+        for b in range(B):
+            r.attributes(ds, dm, tx[b:b + 1], G.GSPARC_FP32, out=attr1)
+            r.render(attr1, out=out1)
+            if check is not None:
+                check(b)
+
+    batched()
+    torch.cuda.synchronize(dev)
+    units = int(n_used.sum().item()) * K
+    res = {}
+    for name, fn, reps in (("batched_bf16x2", batched, 10), ("plain_fp32_one_query", plain, 2)):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms_per_64_queries": ms, "units_per_s": units / (ms * 1e-3)}
+    if r.check() != 0:
+        raise RuntimeError("batched status")
+    # accuracy: each batched spectrum against the plain FP32 path's, whole image
+    batched()
+    torch.cuda.synchronize(dev)
+    sel = list(range(0, B, B // 8))
+    pix = _pix_sample(H, W, 128, seed=30)
+    rel_plain, z_b, z_p = [], {}, {}
+
+    def check(b):
+        d = (spec[b].double() - out1[0][0].double()).norm() / out1[0][0].double().norm()
+        rel_plain.append(float(d))
+        if b in sel:
+            z_b[b] = _spec_at(spec[b], pix, W)
+            z_p[b] = _spec_at(out1[0][0], pix, W)
+
+    plain(check)
+    torch.cuda.synchronize(dev)
+    # the oracle leg: FP64 oracle spectra of 8 transmitters on 128 seeded pixels (host cores)
+    from oracle import attributes as oattr
+    from oracle import projection as oproj
+    from oracle import render as orender
+
+    orender.build()
+    view, band = synth.View(H=H, W=W), synth.Band(K=K)
+    f64 = lambda a: torch.tensor(np.asarray(a), dtype=torch.float64)
+    t0 = time.perf_counter()
+    geo = oproj.project(f64(sc.means), f64(sc.log_scales), f64(sc.quats), view)
+    g = {k: geo[k].numpy() for k in ("px", "py", "cxx", "cxy", "cyy", "r", "valid")}
+    weights = [f64(a) for a in mlp.arrays()]
+    err_b, err_p, n_units = [], [], 0
+    for b in sel:
+        at = oattr.attributes(f64(sc.means), f64(sc.opacity_logit), f64(sc.latent), weights, f64(txh[b]), view.rx)
+        at = {k: at[k].numpy() for k in ("sigma", "a", "phi0", "L")}
+        z_or, _, nu = orender.render_fwd(g, at, H, W, K, band.f_c, band.df, pixels=pix.astype(np.int32))
+        n_units += int(nu.sum()) * K
+        err_b.append(_rel(z_b[b], z_or))
+        err_p.append(_rel(z_p[b], z_or))
+    oracle_s = time.perf_counter() - t0
+    out = {"metric": "Gaussian·pixel·subcarrier/s forward, batched", "value": res["batched_bf16x2"]["units_per_s"],
+           "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+           "dtype": "bf16x2 network and compositing products, f32 accumulation and transmittance",
+           "data": "synthetic (seeded)",
+           "config": {"workload": "batched inference, 200k Gaussians, 64 transmitters per launch, 256 subcarriers, "
+                                  "720x180, hidden 64", "units_per_launch": units, "pairs": int(r.n_pairs.item())},
+           "forms": res,
+           "speedup_vs_plain": res["plain_fp32_one_query"]["ms_per_64_queries"] / res["batched_bf16x2"]["ms_per_64_queries"],
+           "rel_l2_vs_plain_per_spectrum": {"max": max(rel_plain), "median": float(np.median(rel_plain)),
+                                            "spectra": len(rel_plain), "pixels": "whole image"},
+           "rel_l2_vs_oracle_per_spectrum": {"batched_max": max(err_b), "batched_median": float(np.median(err_b)),
+                                             "plain_max": max(err_p), "plain_median": float(np.median(err_p)),
+                                             "spectra": len(sel), "pixels": 128},
+           "cpu_baseline": {"value": n_units / oracle_s, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+                            "sample": "128 seeded pixels of 8 transmitters (forward, projection and network "
+                                      "of all 200k Gaussians included)", "seconds": oracle_s}}
+    if emit:
+        print(json.dumps(out))
+    return out
+
+
+def run_train(args, dev=None, emit=True):
     """Training loop: 100,000 Gaussians fitted to spectra of a 20,000-Gaussian ground-truth scene
     at 2,000 training transmitters (uniform in the cube), 128 subcarriers, 360x90, hidden 32,
-    split-BF16 tensor-core network with FP32 master weights, Adam; held-out error on 200 other
-    transmitters before and after."""
+    split-BF16 tensor-core network with FP32 master weights, Adam, recompute in the backward.
+    steps/s over the timed steps; held-out relative error on 200 other transmitters against the
+    ground truth rendered by the FP32 path (whole images) and, in the oracle leg, against the
+    FP64 oracle's render of the ground truth on 64 seeded pixels, before and after."""
     import torch
 
     from paper_2511_22793_gb300 import synth
     from paper_2511_22793_gb300.train import Trainer
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
+    if dev is None:
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+    H, W, K = 90, 360, 128
     gt = synth.make_scene(20_000, seed=1)
     gt_mlp = synth.make_mlp(32, seed=7)
     train_tx = synth.make_tx(2000, seed=2)
     held = synth.make_tx(200, seed=8)
-    steps = args.steps
-    tr = Trainer(100_000, gt, gt_mlp, train_tx, H=90, W=360, K=128, hidden=32, batch=4,
-                 total_steps=steps, device=dev)
+    steps = args.c4_steps
+    tr = Trainer(100_000, gt, gt_mlp, train_tx, H=H, W=W, K=K, hidden=32, batch=4,
+                 total_steps=steps + args.warmup, device=dev)
+    pix = _pix_sample(H, W, 64, seed=31)
+
+    def predict_at():
+        txs = torch.tensor(np.asarray(held, dtype=np.float32), device=dev)
+        out = []
+        for s in range(0, txs.shape[0], tr.batch):
+            (spec, _, _), _ = tr.forward(txs[s:s + tr.batch])
+            for b in range(spec.shape[0]):
+                out.append(_spec_at(spec[b], pix, W))
+        return np.stack(out)
+
     e0 = tr.evaluate(held)
+    p0 = predict_at()
     for _ in range(args.warmup):
         tr.step()
     torch.cuda.synchronize(dev)
+    trace = []
+    t_train = 0.0
+    done = 0
+    chunk = max(1, steps // 4)
+    while done < steps:
+        m = min(chunk, steps - done)
+        t0 = time.perf_counter()
+        for _ in range(m):
+            loss = tr.step()
+        torch.cuda.synchronize(dev)
+        t_train += time.perf_counter() - t0
+        done += m
+        trace.append({"step": done + args.warmup, "loss": float(loss), "heldout_rel_error": tr.evaluate(held)})
+    if tr.r.check() != 0:
+        raise RuntimeError("training status")
+    p1 = predict_at()
+    # the oracle leg: ground-truth spectra of the held-out transmitters on 64 seeded pixels
+    from oracle import pipeline as opl
+
     t0 = time.perf_counter()
-    losses = []
-    for i in range(steps):
-        loss = tr.step()
-        if i % 50 == 0 or i == steps - 1:
-            losses.append(float(loss))
-    torch.cuda.synchronize(dev)
-    dt = time.perf_counter() - t0
-    e1 = tr.evaluate(held)
-    out = {"metric": "training steps/s", "value": steps / dt, "unit": "steps/s", "n_gpus": 1,
+    ref = opl.forward(gt, gt_mlp, synth.View(H=H, W=W), synth.Band(K=K), held, pixels=pix.astype(np.int32))
+    oracle_s = time.perf_counter() - t0
+    z_or = ref["z"]
+    oracle_units = int(ref["n_used"].sum()) * K
+    err = lambda p: float(np.linalg.norm(p - z_or) / np.linalg.norm(z_or))
+    out = {"metric": "training steps/s", "value": steps / t_train, "unit": "steps/s", "n_gpus": 1,
            "higher_is_better": True, "steps": steps, "warmup": args.warmup,
            "config": {"workload": "training: 100k Gaussians fit to a 20k-Gaussian scene, 2000 training "
                                   "transmitters, batch 4, 128 subcarriers, 360x90, hidden 32",
                       "network": "split-BF16 tensor cores forward and backward, FP32 master weights",
-                      "compositing_fwd": "tensor cores"},
-           "heldout_rel_error": {"before": e0, "after": e1, "transmitters": 200},
-           "loss_trace": losses}
-    print(json.dumps(out))
+                      "compositing": "tensor cores forward (loss fused) and scheduled backward",
+                      "init": "geometry-agnostic (uniform centres, isotropic 0.2 m, opacity 0.1)",
+                      "training_targets": "ground truth rendered by the FP32 path per sampled batch"},
+           "heldout_rel_error": {"before": e0, "after": trace[-1]["heldout_rel_error"], "transmitters": 200,
+                                 "pixels": "whole image", "against": "FP32-path render of the ground truth"},
+           "trace": trace,
+           "cpu_baseline": {"value": oracle_units / oracle_s, "unit": UNIT, "cores": os.cpu_count() or 1,
+                            "kind": "oracle",
+                            "sample": "ground truth (20k Gaussians) at the 200 held-out transmitters, 64 seeded "
+                                      "pixels, forward (projection and network of every Gaussian included)",
+                            "seconds": oracle_s,
+                            "heldout_rel_error_vs_oracle": {"before": err(p0), "after": err(p1),
+                                                            "transmitters": 200, "pixels": 64}}}
+    if emit:
+        print(json.dumps(out))
+    return out
 
 
-def run_serve(args):
+def run_serve(args, dev=None, emit=True, loads=(0.25, 0.5, 0.75, 0.9, 1.25, 2.0)):
     """Serving: 500,000-Gaussian resident scene; Poisson streams of queries (transmitters uniform
     in the cube, resolutions from {180x45, 360x90, 720x180}, subcarriers from {1, 64, 256, 1024})
     at fractions of the plain path's saturated rate; continuous batching (split-BF16 tensor-core
@@ -947,8 +1010,9 @@ def run_serve(args):
     from paper_2511_22793_gb300.pipeline import DeviceMLP, DeviceScene
     from paper_2511_22793_gb300.serve import Request, Server, latency_stats, serve_plain
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
+    if dev is None:
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
     res = [(45, 180), (90, 360), (180, 720)]
     Ks = [1, 64, 256, 1024]
     sc = synth.make_scene(500_000, seed=0, bf16_latent=True)
@@ -966,26 +1030,22 @@ def run_serve(args):
     # saturated rate of the plain path: the same kind of requests back to back
     probe = make(100)
     serve_plain(ds, dm, probe, np.zeros(len(probe)), res, device=dev, keep_results=False)
-    for q in probe:
-        q.spectrum = None
     st = latency_stats(probe)
     sat = st["spectra_per_s"]
     out_rows = []
     srv = Server(ds, dm, res, mem_budget_bytes=24 << 30, max_batch=8, n_streams=4, device=dev, keep_results=False)
-    for frac in (0.25, 0.5, 0.75, 0.9, 1.25, 2.0):
+    srv.run(make(50), np.zeros(50))          # warm-up: every (resolution, subcarrier count) seen once
+    torch.cuda.synchronize(dev)
+    for frac in loads:
         lam = frac * sat
         reqs = make(n_req)
         arr = np.cumsum(rng.exponential(1.0 / lam, size=n_req))
         srv.done = []
         srv.run(reqs, arr)
         torch.cuda.synchronize(dev)
-        for q in reqs:
-            q.spectrum = None
         a = latency_stats(reqs)
         plain = [Request(q.rid, q.tx, q.res, q.K) for q in reqs]
         serve_plain(ds, dm, plain, arr, res, device=dev, keep_results=False)
-        for q in plain:
-            q.spectrum = None
         b = latency_stats(plain)
         out_rows.append({"load": frac, "rate_per_s": lam, "batched": a, "plain": b})
     # saturated: every request queued at once
@@ -993,12 +1053,8 @@ def run_serve(args):
     srv.done = []
     srv.run(burst, np.zeros(n_req))
     torch.cuda.synchronize(dev)
-    for q in burst:
-        q.spectrum = None
     burst_plain = [Request(q.rid, q.tx, q.res, q.K) for q in burst]
     serve_plain(ds, dm, burst_plain, np.zeros(n_req), res, device=dev, keep_results=False)
-    for q in burst_plain:
-        q.spectrum = None
     out_rows.append({"load": "burst", "batched": latency_stats(burst), "plain": latency_stats(burst_plain)})
     # moving receiver: every request carries its own pose (position in the cube, random heading),
     # so its projection and bin/sort run per request; one burst, both paths
@@ -1018,12 +1074,8 @@ def run_serve(args):
     srv.done = []
     srv.run(mov, np.zeros(n_mov))
     torch.cuda.synchronize(dev)
-    for q in mov:
-        q.spectrum = None
     mov_plain = [Request(q.rid, q.tx, q.res, q.K, rx=q.rx, V=q.V) for q in mov]
     serve_plain(ds, dm, mov_plain, np.zeros(n_mov), res, device=dev, keep_results=False)
-    for q in mov_plain:
-        q.spectrum = None
     out_rows.append({"load": "burst, moving receiver", "requests": n_mov, "batched": latency_stats(mov),
                      "plain": latency_stats(mov_plain)})
     out = {"metric": "query latency p50/p99 and spectra/s under Poisson load", "unit": "ms",
@@ -1032,14 +1084,19 @@ def run_serve(args):
                                   "720x180}, subcarriers {1, 64, 256, 1024}, transmitters uniform in the cube",
                       "server": "continuous batching, up to 8 queries per launch, 4 streams, 24 GiB budget, "
                                 "split-BF16 tensor-core network, tensor-core compositing",
-                      "plain": "one query at a time, FP32 network, FP32 compositing"},
+                      "plain": "one query at a time, FP32 network, FP32 compositing",
+                      "latency": "arrival to the host observing the completion event"},
            "loads": out_rows}
-    print(json.dumps(out))
+    if emit:
+        print(json.dumps(out))
+    return out
 
 
-def cpu_baseline(sample_pixels, seed=0, threads=0, sc=None, mlp=None, tx=None):
+def cpu_baseline(sample_pixels, seed=0, threads=0, sc=None, mlp=None, tx=None, spectra=None):
     """FP64 oracle, fwd + bwd, on a seeded pixel sample of the same workload, on `threads`
-    host threads (0: every core), both for its C renderer and its PyTorch CPU parts."""
+    host threads (0: every core), both for its C renderer and its PyTorch CPU parts.  spectra:
+    optional form -> [1, K, H, W, 2] GPU spectrum (host tensor) of the same scene and
+    transmitter, each compared with the oracle's on the sample."""
     import torch
 
     from oracle import pipeline as opl
@@ -1066,15 +1123,23 @@ def cpu_baseline(sample_pixels, seed=0, threads=0, sc=None, mlp=None, tx=None):
         units = int(counted["n_used"].sum()) * K
         target = np.zeros((1, sample_pixels, K), dtype=np.complex128)
         t0 = time.perf_counter()
-        opl.loss_and_grad(sc, mlp, view, band, tx[:1], target, pixels=pix, threads=cores)
+        _, g = opl.loss_and_grad(sc, mlp, view, band, tx[:1], target, pixels=pix, threads=cores)
         dt = time.perf_counter() - t0
     finally:
         torch.set_num_threads(torch_threads)
     what = "the full %dx%d image" % (W, H) if sample_pixels == H * W else \
         "%d seeded pixels of the %dx%d image" % (sample_pixels, W, H)
-    return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%s, one transmitter, forward + FP64 analytic backward (loss and all "
-                      "parameter gradients)" % what, "seconds": dt, "units": units}
+    out = {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "%s, one transmitter, forward + FP64 analytic backward (loss and all "
+                     "parameter gradients)" % what, "seconds": dt, "units": units}
+    if spectra:
+        z_or = g["z"][0]
+        out["gpu_spectrum_rel_l2_vs_oracle"] = {}
+        for form, s in spectra.items():
+            z = s[0].double().numpy()
+            zc = (z[..., 0] + 1j * z[..., 1]).transpose(1, 2, 0).reshape(H * W, K)[pix]
+            out["gpu_spectrum_rel_l2_vs_oracle"]["tc_split_bf16" if form == "tc" else form] = _rel(zc, z_or)
+    return out
 
 
 def run_reference(args):
@@ -1118,15 +1183,18 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=90 * 360,
                     help="pixels in the oracle CPU baseline (default: the whole image)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="headline step (both forms), probes and the single-query latency only")
     ap.add_argument("--requests", type=int, default=2000,
                     help="serving workload: Poisson requests per load level")
-    ap.add_argument("--render", default="tc", choices=["tc", "fp32"],
-                    help="forward compositing: tcgen05 (default) or FP32 CUDA cores")
+    ap.add_argument("--c4-steps", type=int, default=1500, help="training workload: timed steps")
+    ap.add_argument("--render", default="fp32", choices=["fp32", "tc"],
+                    help="headline arithmetic: FP32 CUDA cores (default) or the tensor-core form")
     ap.add_argument("--workload", default="fwdbwd",
                     choices=["fwdbwd", "batched", "train", "serve", "csi", "emission", "spectrum_loss",
                              "train_extras"],
-                    help="fwdbwd: the default step; batched: 64-transmitter inference with the "
-                         "tensor-core network against the plain one-query path; train: the training "
+                    help="fwdbwd: the default line (headline step and every configuration); batched: "
+                         "64-transmitter inference against the plain one-query path; train: the training "
                          "loop; serve: the continuous-batching query server; csi: channel-estimate "
                          "queries with the fused CSI head; emission: the per-Gaussian emission "
                          "network's width sweep; spectrum_loss: the L1 + SSIM loss of Eq. 4; train_extras: "
@@ -1142,33 +1210,12 @@ def main():
         if rank == 0:
             run_reference(args)
         return
-    if args.workload == "batched":
+    single = {"batched": run_batched, "csi": run_csi, "emission": run_emission,
+              "spectrum_loss": run_spectrum_loss, "train_extras": run_train_extras, "train": run_train,
+              "serve": run_serve}
+    if args.workload in single:
         if rank == 0:
-            run_batched(args)
-        return
-    if args.workload == "csi":
-        if rank == 0:
-            run_csi(args)
-        return
-    if args.workload == "emission":
-        if rank == 0:
-            run_emission(args)
-        return
-    if args.workload == "spectrum_loss":
-        if rank == 0:
-            run_spectrum_loss(args)
-        return
-    if args.workload == "train_extras":
-        if rank == 0:
-            run_train_extras(args)
-        return
-    if args.workload == "train":
-        if rank == 0:
-            run_train(args)
-        return
-    if args.workload == "serve":
-        if rank == 0:
-            run_serve(args)
+            single[args.workload](args)
         return
 
     if world > 1:
@@ -1176,10 +1223,10 @@ def main():
         import torch.distributed as tdist
         torch.cuda.set_device(local_rank)
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    out, units, sc, mlp, tx = run_ours(args, rank, world, local_rank)
+    out, spectra, sc, mlp, tx = run_ours(args, rank, world, local_rank)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(args.cpu_sample, sc=sc, mlp=mlp, tx=tx)
+            out["cpu_baseline"] = cpu_baseline(args.cpu_sample, sc=sc, mlp=mlp, tx=tx, spectra=spectra)
             out["cpu_baseline"].pop("units", None)
             out["cpu_baseline"]["seconds"] = round(out["cpu_baseline"]["seconds"], 3)
             # the same oracle on one host thread, on a smaller sample

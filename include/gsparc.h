@@ -613,6 +613,19 @@ int gsparc_adam(int64_t n, float* param, const float* grad, float* m, float* v, 
                 float b2, float eps, int32_t step, void* stream);
 
 /*
+ * gsparc_adam over several parameter groups of one flat buffer in one launch
+ * (Algorithm 1 "Adam" with the per-group learning rates of the paper's
+ * hyperparameter table): group s covers elements [seg_end[s-1], seg_end[s])
+ * (seg_end[-1] = 0) and takes learning rate seg_lr[s].  seg_end and seg_lr
+ * are HOST arrays of n_seg (1..32) entries, seg_end non-decreasing with
+ * seg_end[n_seg-1] = n; the same update and bias correction as gsparc_adam
+ * otherwise.
+ */
+int gsparc_adam_segments(int64_t n, float* param, const float* grad, float* m, float* v, int32_t n_seg,
+                         const int64_t* seg_end, const float* seg_lr, float b1, float b2, float eps,
+                         int32_t step, void* stream);
+
+/*
  * Polls a pipeline wait of the tensor-core compositing kernels
  * (gsparc_render_fwd_tc, gsparc_render_fwd_l2_tc, gsparc_render_csi_tc,
  * gsparc_render_bwd_tc, gsparc_render_bwd_tc_balanced) makes before it gives up

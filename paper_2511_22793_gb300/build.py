@@ -20,6 +20,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libgsparc.so")
+# FMA / ex2 throughput probes of the benchmark (measurement only, not the library's ABI)
+PROBE_SRC = os.path.join(HERE, "probe", "peaks.cu")
+PROBE_LIB = os.path.join(HERE, "libgsparc_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]
@@ -70,6 +73,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         for out in ex.map(compile_one, zip(srcs, objs)):
             if verbose and out:
                 print(out, file=sys.stderr)
+    if force or not os.path.exists(PROBE_LIB) or os.path.getmtime(PROBE_SRC) > os.path.getmtime(PROBE_LIB):
+        tmp = PROBE_LIB + ".%d.tmp" % os.getpid()
+        r = subprocess.run([nvcc] + ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-o", tmp,
+                                            PROBE_SRC], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed on %s:\n%s%s" % (PROBE_SRC, r.stdout, r.stderr))
+        os.replace(tmp, PROBE_LIB)
     need_link = force or not os.path.exists(LIB) or any(
         os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs)
     if need_link:

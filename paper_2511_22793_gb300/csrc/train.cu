@@ -36,3 +36,26 @@ extern "C" int gsparc_adam(int64_t n, float* param, const float* grad, float* m,
     k_adam<<<blocks, 256, 0, as_stream(stream)>>>(n, param, grad, m, v, lr, b1, b2, eps, bc1, bc2);
     return launch_status();
 }
+
+extern "C" int gsparc_adam_segments(int64_t n, float* param, const float* grad, float* m, float* v, int32_t n_seg,
+                                    const int64_t* seg_end, const float* seg_lr, float b1, float b2, float eps,
+                                    int32_t step, void* stream) {
+    if (n < 0 || step < 1 || n_seg < 1 || n_seg > kAdamMaxSeg || !seg_end || !seg_lr) return GSPARC_ERR_INVALID;
+    AdamSegments seg{};
+    seg.n_seg = n_seg;
+    int64_t prev = 0;
+    for (int s = 0; s < n_seg; ++s) {
+        if (seg_end[s] < prev) return GSPARC_ERR_INVALID;
+        seg.end[s] = seg_end[s];
+        seg.lr[s] = seg_lr[s];
+        prev = seg_end[s];
+    }
+    if (prev != n) return GSPARC_ERR_INVALID;
+    if (n == 0) return GSPARC_OK;
+    if (!param || !grad || !m || !v) return GSPARC_ERR_INVALID;
+    const float bc1 = (float)(1.0 - std::pow((double)b1, (double)step));
+    const float bc2 = (float)(1.0 - std::pow((double)b2, (double)step));
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);
+    k_adam_seg<<<blocks, 256, 0, as_stream(stream)>>>(n, param, grad, m, v, seg, b1, b2, eps, bc1, bc2);
+    return launch_status();
+}

@@ -51,5 +51,37 @@ __global__ void __launch_bounds__(256) k_adam(int64_t n, float* __restrict__ p, 
     }
 }
 
+// Parameter groups of one flat buffer for k_adam_seg: segment s covers [end[s-1], end[s])
+// (end[-1] = 0) and takes learning rate lr[s].
+constexpr int kAdamMaxSeg = 32;
+struct AdamSegments {
+    int n_seg;
+    int64_t end[kAdamMaxSeg];
+    float lr[kAdamMaxSeg];
+};
+
+// The same update as k_adam over every group of a flat buffer in one launch: the element's
+// group is found by a binary search over the (kernel-parameter) segment ends.
+__global__ void __launch_bounds__(256) k_adam_seg(int64_t n, float* __restrict__ p, const float* __restrict__ g,
+                                                  float* __restrict__ m, float* __restrict__ v, AdamSegments seg,
+                                                  float b1, float b2, float eps, float bc1, float bc2) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        int lo = 0, hi = seg.n_seg - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (j < seg.end[mid]) hi = mid;
+            else lo = mid + 1;
+        }
+        const float lr = seg.lr[lo];
+        const float gj = g[j];
+        const float mj = b1 * m[j] + (1.f - b1) * gj;
+        const float vj = b2 * v[j] + (1.f - b2) * gj * gj;
+        m[j] = mj;
+        v[j] = vj;
+        p[j] -= lr * (mj / bc1) / (sqrtf(vj / bc2) + eps);
+    }
+}
+
 }  // namespace
 }  // namespace gsparc

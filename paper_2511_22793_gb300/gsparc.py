@@ -39,7 +39,7 @@ EXPORTS = [
     "gsparc_l2_loss", "gsparc_csi_head", "gsparc_csi_loss", "gsparc_csi_head_bwd",
     "gsparc_spectrum_loss_workspace", "gsparc_spectrum_loss",
     "gsparc_render_csi_tc", "gsparc_render_fwd_l2_tc", "gsparc_confidence", "gsparc_densify_accumulate",
-    "gsparc_densify_workspace", "gsparc_densify", "gsparc_opacity_reset", "gsparc_adam", "gsparc_set_wait_limit",
+    "gsparc_densify_workspace", "gsparc_densify", "gsparc_opacity_reset", "gsparc_adam", "gsparc_adam_segments", "gsparc_set_wait_limit",
     "gsparc_check", "gsparc_strerror",
 ]
 
@@ -135,6 +135,8 @@ def lib():
                                               vp, ctypes.c_size_t, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
             "gsparc_opacity_reset": (ctypes.c_int, [i32, f32, vp, vp]),
             "gsparc_adam": (ctypes.c_int, [i64, vp, vp, vp, vp, f32, f32, f32, f32, i32, vp]),
+            "gsparc_adam_segments": (ctypes.c_int, [i64, vp, vp, vp, vp, i32, P(i64), P(f32), f32, f32, f32, i32,
+                                                    vp]),
             "gsparc_set_wait_limit": (ctypes.c_uint32, [ctypes.c_uint32]),
             "gsparc_check": (ctypes.c_int, [vp, vp]),
             "gsparc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -445,6 +447,16 @@ def gsparc_render_fwd_l2_tc(view, band, B, n, proj, tile_ranges, sorted_ids, att
 
 def gsparc_adam(param, grad, m, v, lr, step, b1=0.9, b2=0.999, eps=1e-15, stream=None):
     _call("gsparc_adam", param.numel(), _p(param), _p(grad), _p(m), _p(v), float(lr), float(b1),
+          float(b2), float(eps), int(step), _stream(stream))
+
+
+def gsparc_adam_segments(param, grad, m, v, seg_end, seg_lr, step, b1=0.9, b2=0.999, eps=1e-15, stream=None):
+    """One Adam launch over a flat buffer whose groups end at seg_end (host ints, the last = numel)
+    with learning rates seg_lr (host floats)."""
+    k = len(seg_end)
+    ends = (ctypes.c_int64 * k)(*[int(e) for e in seg_end])
+    lrs = (ctypes.c_float * k)(*[float(x) for x in seg_lr])
+    _call("gsparc_adam_segments", param.numel(), _p(param), _p(grad), _p(m), _p(v), k, ends, lrs, float(b1),
           float(b2), float(eps), int(step), _stream(stream))
 
 

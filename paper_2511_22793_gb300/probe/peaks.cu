@@ -1,0 +1,72 @@
+// Throughput probes of the two pipes that bound the FP32 compositing kernels: FP32 FMA and the
+// SFU's ex2.  Measurement infrastructure of the benchmark (libgsparc_probe.so), not part of the
+// splatting library's ABI.
+//
+// Each thread runs kChains independent dependency chains for `iters` iterations, so that the
+// pipe, not the latency of one chain, sets the rate; the grid is blocks_per_sm x SMs blocks of
+// 256 threads.  The result of every chain is folded into one store per thread so that no
+// operation is dead code.
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace {
+
+constexpr int kChains = 8;
+
+__global__ void __launch_bounds__(256) k_fma(int iters, float a, float b, float* out) {
+    float x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = (float)(threadIdx.x + c);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) x[c] = fmaf(x[c], a, b);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__device__ __forceinline__ float ex2a(float x) {
+    float y;
+    asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// x <- ex2(-x) keeps every chain in (0.5, 1]; the negation folds into the instruction's operand
+__global__ void __launch_bounds__(256) k_ex2(int iters, float* out) {
+    float x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = 0.1f * (float)(c + 1);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) x[c] = ex2a(-x[c]);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace
+
+// kind 0: FMA (returns the FMAs issued), 1: ex2 (returns the ex2 issued).  out must hold
+// blocks * 256 floats.  Launches once on `stream` and returns the operation count, or -1 when
+// the launch failed.  The caller times it (CUDA events around the call).
+extern "C" int64_t gsparc_probe_launch(int kind, int blocks, int iters, float* out, void* stream) {
+    if (blocks <= 0 || iters <= 0 || !out) return -1;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (kind == 0)
+        k_fma<<<blocks, 256, 0, s>>>(iters, 0.9999f, 1e-4f, out);
+    else if (kind == 1)
+        k_ex2<<<blocks, 256, 0, s>>>(iters, out);
+    else
+        return -1;
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    return (int64_t)blocks * 256 * iters * 4 * kChains;
+}

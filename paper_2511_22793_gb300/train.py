@@ -7,7 +7,7 @@ targets, runs the hand-written backward (per-pixel state recomputed from the
 stored final log-transmittance, network activations recomputed) and updates
 every parameter group with Adam at the learning rates of the paper's
 hyperparameter table (position rate annealed exponentially from 1.6e-4 to
-1.6e-7 over the run).  Densification, pruning and the confidence network are
+1.6e-7 over the run), in one launch over the flat parameter buffer.  Densification, pruning and the confidence network are
 not part of this loop.
 
 Targets are spectra of a ground-truth scene rendered by the same FP32 path
@@ -68,14 +68,17 @@ class Trainer:
             sc, mlp = init
             n = sc.n
             self.n = n
-        self.scene = DeviceScene.from_host(sc, self.dev)
-        self.mlp = DeviceMLP.from_host(mlp, self.dev)
-        self.params = dict(zip(SCENE_KEYS, self.scene.tensors()))
-        self.params.update(zip(MLP_KEYS, self.mlp.tensors()))
-        # gradient buffers and Adam moments: one flat allocation each, views per parameter
-        self.grads, self._gbuf = self._flat_like()
-        self.m, self._mbuf = self._flat_like()
-        self.v, self._vbuf = self._flat_like()
+        # parameters, gradients and Adam moments: one flat allocation each, with the same layout
+        # (every group at a 64-float boundary), so that one launch updates every group
+        shapes = {k: np.shape(a) for k, a in zip(SCENE_KEYS + MLP_KEYS, list(sc.arrays()) + list(mlp.arrays()))}
+        self.params, self._pbuf = self._flat(shapes)
+        for k, a in zip(SCENE_KEYS + MLP_KEYS, list(sc.arrays()) + list(mlp.arrays())):
+            self.params[k].copy_(torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)))
+        self.scene = DeviceScene(*[self.params[k] for k in SCENE_KEYS])
+        self.mlp = DeviceMLP(mlp.hidden, *[self.params[k] for k in MLP_KEYS])
+        self.grads, self._gbuf = self._flat(shapes)
+        self.m, self._mbuf = self._flat(shapes)
+        self.v, self._vbuf = self._flat(shapes)
         self.step_count = 0
         self.rng = np.random.default_rng(seed + 2)
         self.r = Renderer(H, W, K, n, device=self.dev)
@@ -95,12 +98,13 @@ class Trainer:
         self.train_tx = torch.tensor(np.asarray(train_tx, dtype=np.float32), device=self.dev)
         self.tx = torch.empty((batch, 3), device=self.dev)
 
-    def _flat_like(self):
-        sizes = [p.numel() for p in self.params.values()]
-        offs = np.cumsum([0] + [(s + 63) // 64 * 64 for s in sizes])
+    def _flat(self, shapes):
+        sizes = [int(np.prod(sh)) for sh in shapes.values()]
+        offs = np.cumsum([0] + [(z + 63) // 64 * 64 for z in sizes])
         buf = torch.zeros(int(offs[-1]), device=self.dev)
-        views = {k: buf[int(o):int(o) + p.numel()].view(p.shape)
-                 for (k, p), o in zip(self.params.items(), offs[:-1])}
+        views = {k: buf[int(o):int(o) + z].view(sh) for (k, sh), o, z in zip(shapes.items(), offs[:-1], sizes)}
+        # the groups' ends in the flat buffer (the padding after a group belongs to it)
+        self._seg_end = [int(o) for o in offs[1:]]
         return views, buf
 
     def pos_lr(self):
@@ -151,9 +155,9 @@ class Trainer:
                                    tensor_cores=self.tensor_cores and self.mlp.hidden in (16, 32))
         self.r.project_backward(self.scene, self.d_proj, g["means"], g["log_scales"], g["quats"])
         self.step_count += 1
-        for k, p in self.params.items():
-            lr = self.pos_lr() if k == "means" else LR[k]
-            G.gsparc_adam(p, g[k], self.m[k], self.v[k], lr, self.step_count)
+        # one Adam launch over every group, each at its learning rate
+        lrs = [self.pos_lr() if k == "means" else LR[k] for k in self.params]
+        G.gsparc_adam_segments(self._pbuf, self._gbuf, self._mbuf, self._vbuf, self._seg_end, lrs, self.step_count)
         return self.loss
 
     def evaluate(self, tx_all, chunk=None):

@@ -52,7 +52,7 @@ def test_binding_signatures_match_the_header(L):
                "float": ctypes.c_float, "size_t": ctypes.c_size_t}
     structs = {"gsparc_view": G.View, "gsparc_band": G.Band, "gsparc_mlp": G.MLP,
                "gsparc_mlp_grad": G.MLPGrad, "gsparc_densify_params": G.DensifyParams,
-               "size_t": ctypes.c_size_t, "float": ctypes.c_float}
+               "size_t": ctypes.c_size_t, "float": ctypes.c_float, "int64_t": ctypes.c_int64}
     decls = _declarations()
     assert sorted(decls) == sorted(G.EXPORTS)
     for name, (ret, params) in decls.items():

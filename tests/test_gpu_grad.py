@@ -188,6 +188,32 @@ def test_render_bwd_tensor_cores_matches_fp32_kernel_and_oracle(n, H, W, K, B, s
             assert rel_l2(got[k], ref[:, c]) <= 1e-3, k
 
 
+def _relu_margin(sc, mlp, tx):
+    """Per Gaussian, min over transmitters and hidden units of |u| - bound(u), with u the FP64
+    pre-activation of a hidden unit and bound(u) what the split-BF16 products can move it: each
+    operand is carried as hi + lo BF16 terms (8 significant bits each, so the representation
+    error is at most 2^-17 relative), the dropped lo*lo product is at most 2^-18 relative and
+    the FP32 accumulation adds 2^-24 per term, so one product is off by at most 2^-15.5 of
+    |a b|; four times that over sum |a b| bounds a layer, and layer 2 also inherits layer 1's
+    bound through |W2|.  A ReLU decision can differ from FP64 only where the margin is <= 0."""
+    f64 = lambda a: torch.tensor(np.asarray(a), dtype=torch.float64)
+    means, latent = f64(sc.means), f64(sc.latent)
+    W1, b1, W2, b2 = (f64(a) for a in mlp.arrays()[:4])
+    eps = 4.0 * 2.0 ** -15.5
+    out = torch.full((sc.n,), float("inf"), dtype=torch.float64)
+    for t in np.asarray(tx, dtype=np.float64):
+        d = torch.clamp(torch.linalg.norm(means - f64(t), dim=1), min=0.01)
+        h0 = torch.cat([f64(t).reshape(1, 3).expand(sc.n, 3), latent, torch.log(d).reshape(-1, 1)], 1)
+        u1 = h0 @ W1 + b1
+        bnd1 = eps * (h0.abs() @ W1.abs() + b1.abs())
+        h1 = torch.relu(u1)
+        u2 = h1 @ W2 + b2
+        bnd2 = eps * (h1.abs() @ W2.abs() + b2.abs()) + bnd1 @ W2.abs()
+        m = torch.minimum((u1.abs() - bnd1).min(1).values, (u2.abs() - bnd2).min(1).values)
+        out = torch.minimum(out, m)
+    return out.numpy()
+
+
 def _row_err(got, want):
     g = got.reshape(got.shape[0], -1)
     w = want.reshape(want.shape[0], -1)
@@ -246,6 +272,11 @@ def test_attr_mlp_bwd_tensor_cores(n, B, hidden, seed):
     for c in range(3):
         flipped |= (_row_err(tc[c], fp[c]) > 1e-3) | (_row_err(tc[c], ref[c]) > 1e-3)
     assert flipped.mean() <= 1e-3, "%d of %d rows differ" % (flipped.sum(), n)
+    # every excluded row must really sit at a ReLU kink: some hidden pre-activation (of some
+    # transmitter) within the split-BF16 rounding bound of zero
+    margin = _relu_margin(sc, mlp, tx)
+    for i in np.flatnonzero(flipped):
+        assert margin[i] <= 0.0, "row %d excluded but its nearest kink is %.3e beyond the bound" % (i, margin[i])
     d_attr_np[:, flipped] = 0.0
     fp, tc = (_mlp_grads_gpu(r, ds, dm, txd, d_attr_np, t) for t in (False, True))
     ref = _mlp_grads_oracle(sc, mlp, tx, d_attr_np)
