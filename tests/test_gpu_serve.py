@@ -42,12 +42,16 @@ def test_results_same_alone_and_in_the_mix():
     mixed = {q.rid: q.spectrum.clone() for q in reqs}
     batched = sum(1 for q in reqs) > len(set((q.res, q.K) for q in reqs))
     assert batched
+    for q in reqs:
+        srv.release(q)
+    assert srv.used == 0                           # every block back in the arena
+    alone = Server(ds, dm, RES, mem_budget_bytes=1 << 30, max_batch=1, n_streams=1)
     for q in reqs:                                 # each alone, same arithmetic
-        alone = Server(ds, dm, [q.res], mem_budget_bytes=4 << 30, max_batch=1, n_streams=1)
         solo = Request(q.rid, q.tx, q.res, q.K)
         alone.run([solo], np.zeros(1))
         torch.cuda.synchronize()
         assert _rel(mixed[q.rid], solo.spectrum) <= 1e-6
+        alone.release(solo)
     plain = _requests(30, 43)
     serve_plain(ds, dm, plain, np.zeros(len(plain)), RES)
     for q, p in zip(reqs, plain):
@@ -62,7 +66,20 @@ def test_memory_admission_and_rejection():
     assert big.rejected
     one = srv.request_bytes(180, 720, 64)
     reqs = [Request(i, (0.5 * i, 1.0, -1.0), (180, 720), 64) for i in range(6)]
-    srv = Server(ds, dm, RES, mem_budget_bytes=one + one // 2, max_batch=4, n_streams=2)
+    srv = Server(ds, dm, RES, mem_budget_bytes=one + one // 2, max_batch=4, n_streams=2, keep_results=False)
     srv.run(reqs, np.zeros(len(reqs)))
-    assert all(not q.rejected and q.spectrum is not None for q in reqs)
+    assert all(not q.rejected and q.t_done >= q.t_arrival for q in reqs)
     assert srv.used == 0
+    # kept results hold their memory until released: with room for one, a second request waits
+    # for the first one's release, and the server says so instead of waiting forever
+    srv = Server(ds, dm, RES, mem_budget_bytes=one + one // 2, max_batch=4, n_streams=2)
+    a, b = Request(10, (1.0, 1.0, 1.0), (180, 720), 64), Request(11, (2.0, 1.0, 1.0), (180, 720), 64)
+    srv.run([a], np.zeros(1))
+    assert a.spectrum is not None and srv.used > 0
+    with pytest.raises(RuntimeError):
+        srv.run([b], np.zeros(1))
+    srv.release(a)
+    assert srv.used == 0
+    srv.waiting.clear()
+    srv.run([Request(12, (2.0, 1.0, 1.0), (180, 720), 64)], np.zeros(1))
+    assert srv.used > 0

@@ -72,7 +72,9 @@ def _server_state(budget=10 ** 9):
 
     from paper_2511_22793_gb300.serve import Server
 
-    st = types.SimpleNamespace(budget=budget, waiting=collections.deque(), done=[])
+    st = types.SimpleNamespace(budget=budget, waiting=collections.deque(), done=[],
+                               geom={(90, 360): None, (45, 180): None, (180, 720): None},
+                               slot_geom={(0, 90, 360): None})
     st.request_bytes = lambda H, W, K: _bytes(H, W, K)
     return Server, st
 
@@ -84,6 +86,10 @@ def test_submit_rejects_a_request_larger_than_the_budget():
     Server.submit(st, small)
     assert big.rejected and big.t_done > 0 and st.done == [big]
     assert not small.rejected and list(st.waiting) == [small]
+    # a resolution the server has no geometry for is rejected too
+    odd = _q(2, res=(30, 120))
+    Server.submit(st, odd)
+    assert odd.rejected and st.done == [big, odd]
 
 
 def test_cancel_withdraws_only_waiting_requests():
@@ -110,3 +116,57 @@ def test_latency_stats_leave_out_rejected_and_cancelled_requests():
     st = latency_stats(qs)
     assert st["served"] == 2 and st["rejected"] == 1 and st["cancelled"] == 1
     assert st["p50_ms"] == pytest.approx(2.5)
+
+
+def test_arena_first_fit_alignment_and_merging():
+    from paper_2511_22793_gb300.serve import Arena
+
+    a = Arena(4096, align=256)
+    x = a.alloc(100)
+    y = a.alloc(300)
+    z = a.alloc(256)
+    assert (x, y, z) == (0, 256, 768) and a.used == 1024
+    assert a.alloc(4096) is None and a.fits(3072) and not a.fits(3073)
+    a.free(y)                      # a 512-byte hole between x and z
+    assert a.alloc(600) == 1024    # does not fit the hole: first fit goes past it
+    assert a.alloc(512) == 256     # fills the hole exactly
+    a.free(x)
+    a.free(256)
+    a.free(z)                      # x, the hole's block and z merge into one free block at 0
+    assert a.free_list[0] == (0, 1024)
+    a.free(1024)
+    assert a.free_list == [(0, 4096)] and a.used == 0 and not a.taken
+
+
+def test_admission_shrinks_a_batch_to_a_contiguous_block():
+    one = _bytes(90, 360, 1)
+    w = collections.deque([_q(i) for i in range(6)])
+    # budget for six, but the largest contiguous block holds only four
+    group, left = admit(w, used=0, budget=10 * one, max_batch=8, request_bytes=_bytes,
+                        fits=lambda n: n <= 4 * one)
+    assert _ids(group) == [0, 1, 2, 3] and _ids(left) == [4, 5]
+    assert admit(w, used=0, budget=10 * one, max_batch=8, request_bytes=_bytes, fits=lambda n: False) is None
+
+
+def test_arena_random_traffic_never_overlaps():
+    import numpy as np
+
+    from paper_2511_22793_gb300.serve import Arena
+
+    rng = np.random.default_rng(3)
+    a = Arena(1 << 20, align=256)
+    live = {}
+    for _ in range(2000):
+        if live and rng.uniform() < 0.45:
+            off = list(live)[rng.integers(len(live))]
+            a.free(off)
+            del live[off]
+        else:
+            n = int(rng.integers(1, 50_000))
+            off = a.alloc(n)
+            if off is not None:
+                assert off % 256 == 0 and off + n <= a.size
+                for o, m in live.items():
+                    assert off + n <= o or o + m <= off
+                live[off] = n
+    assert a.used == sum((m + 255) // 256 * 256 for m in live.values())
