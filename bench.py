@@ -317,12 +317,8 @@ def time_form(args, dev, form, inp, steps, flush, sampler=None, dist=False):
         if it >= args.warmup:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     clocks = sampler.stop() if sampler is not None else None
-    # the step's spectrum (the tensor-core step's fused forward does not store it): the same
-    # forward kernel once more with the spectrum stored, for the accuracy comparison
-    if form == "tc":
-        G.gsparc_render_fwd_l2_tc(r.view, r.band, st.B, n, r.proj, r.tile_ranges, r.sorted_ids, st.attr, target,
-                                  st.loss, st.d_spec, st.spec, st.logT, st.nc)
-    spec = st.spec.detach().cpu()
+    # the step's spectrum (its fused forward does not store it), for the accuracy comparison
+    spec = st.spectrum().detach().cpu()
     torch.cuda.synchronize(dev)
     return {"st": st, "r": r, "units": units, "n_pairs": n_pairs, "step_ms": step_ms, "e2e_ms": e2e_ms,
             "kernels_ms": {k: statistics.mean(v) for k, v in per_kernel.items()}, "agree": agree,

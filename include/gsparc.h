@@ -310,6 +310,28 @@ int gsparc_render_fwd(const gsparc_view* view, const gsparc_band* band, int32_t 
                       uint32_t* n_used, int32_t* d_status, void* stream);
 
 /*
+ * gsparc_render_fwd with the complex L2 loss of gsparc_l2_loss fused into its
+ * epilogue (the training step's loss, Algorithm 1; complex L2 in place of
+ * Eq. 4), all arithmetic FP32 on the CUDA cores.  With count = B*K*H*W,
+ *   loss [1] = mean |z - target|^2 (the call clears it first; blocks add
+ *   partial sums atomically, so the last bits may differ from run to run),
+ *   d_spectrum [B,K,H,W,2] out = 2 (z - target) / count, bit-identical to
+ *   gsparc_l2_loss on the spectrum gsparc_render_fwd writes.
+ * spectrum may be NULL (then it is never written).  s_tot may be NULL; else
+ * [B, strips, H, W] out with strips = 1 for K <= 32 and ceil(K / 32) above:
+ * s_tot[b,s,p] = sum over strip s's subcarriers of Re(conj(d_spectrum) z), the
+ * input gsparc_render_bwd_balanced takes in place of the spectrum.  tile_walk
+ * may be NULL; else [B, T] out: per (transmitter, tile) min(largest n_contrib
+ * of its pixels, list length).  final_logT, n_contrib, n_used and d_status as
+ * gsparc_render_fwd.
+ */
+int gsparc_render_fwd_l2(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
+                         const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
+                         const float* attr, const float* target, float* loss, float* d_spectrum,
+                         float* spectrum, float* final_logT, uint32_t* n_contrib, uint32_t* n_used,
+                         float* s_tot, uint32_t* tile_walk, int32_t* d_status, void* stream);
+
+/*
  * gsparc_render_fwd with the subcarrier sum on the tensor cores (same
  * arguments, same outputs).  The per-pixel weights w_i = T_i alpha_i are taken
  * exactly as in gsparc_render_fwd (identical alpha, log2 T, cut-off and
@@ -414,6 +436,40 @@ int gsparc_render_bwd_tc_balanced(const gsparc_view* view, const gsparc_band* ba
                                   const uint32_t* tile_walk, const float* final_logT, const uint32_t* n_contrib,
                                   const float* d_spectrum, int32_t split_min, void* ws, size_t ws_bytes,
                                   float* d_attr, float* d_proj, int32_t* d_status, void* stream);
+
+/*
+ * Bytes of device workspace gsparc_render_bwd_balanced needs for B
+ * transmitters of this view and band: 16 + 4 B T (rounded up to 16) +
+ * 32 B T strips, T = tiles, strips as for the s_tot of gsparc_render_fwd_l2.
+ */
+int gsparc_render_bwd_workspace(const gsparc_view* view, const gsparc_band* band, int32_t B,
+                                size_t* ws_bytes);
+
+/*
+ * gsparc_render_bwd with its work scheduled over the SMs, in FP32 on the CUDA
+ * cores (same gradients up to rounding order).  The schedule is that of
+ * gsparc_render_bwd_tc_balanced: every (transmitter, tile, strip of up to 32
+ * subcarriers) walk, the largest n_contrib among the tile's pixels, becomes one
+ * work item, or, when longer than split_min batches of 16 entries, a front
+ * chunk [0, m) walked front to back from T = 1 with the suffix sum taken as
+ * s_tot minus the prefix, and a back chunk [m, walk) walked back to front from
+ * the final state; items run longest first.  Splitting is on while the
+ * (transmitter, tile, strip) units are at most four times the SM count.
+ *   spectrum [B,K,H,W,2] or NULL; s_tot (from gsparc_render_fwd_l2) or NULL:
+ *   the front chunks take s_tot when given, else form it from the spectrum;
+ *   with both NULL no walk is split.  tile_walk [B, T] or NULL as in
+ *   gsparc_render_bwd_tc_balanced.  split_min: 0 the default (3), < 0 none.
+ *   ws: gsparc_render_bwd_workspace() bytes, 16-byte aligned, its first 16
+ *   bytes zero before first use (every call leaves them zero); one call at a
+ *   time per workspace.
+ * Other arguments, outputs and the status word as gsparc_render_bwd.
+ */
+int gsparc_render_bwd_balanced(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
+                               const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
+                               const float* attr, const float* spectrum, const float* s_tot,
+                               const uint32_t* tile_walk, const float* final_logT, const uint32_t* n_contrib,
+                               const float* d_spectrum, int32_t split_min, void* ws, size_t ws_bytes,
+                               float* d_attr, float* d_proj, int32_t* d_status, void* stream);
 
 /*
  * Complex L2 loss, the mean over `count` complex elements of |z - target|^2,

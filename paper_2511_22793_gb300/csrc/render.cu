@@ -12,15 +12,54 @@ namespace gsparc {
 namespace {
 
 template <int S>
-void launch_fwd(const RenderArgs& a, int T, cudaStream_t s) {
+int launch_fwd(const RenderArgs& a, int T, cudaStream_t s) {
+    constexpr int smem = F32Smem<S>::kTotal;
+    if (!ensure_smem_attr(k_render_fwd<S>, smem)) return GSPARC_ERR_CUDA;
     dim3 grid((a.K + S - 1) / S, T, a.B);
-    k_render_fwd<S><<<grid, kThreads, 0, s>>>(a);
+    k_render_fwd<S><<<grid, kThreads, smem, s>>>(a);
+    return launch_status();
 }
 
+// max_items > 0: a scheduled launch (a.items), one CTA per item
 template <int S>
-void launch_bwd(const RenderArgs& a, int T, cudaStream_t s) {
-    dim3 grid((a.K + S - 1) / S, T, a.B);
-    k_render_bwd<S><<<grid, kThreads, 0, s>>>(a);
+int launch_bwd(const RenderArgs& a, int T, cudaStream_t s, uint32_t max_items = 0) {
+    constexpr int smem = F32Smem<S>::kTotal;
+    if (!ensure_smem_attr(k_render_bwd<S>, smem)) return GSPARC_ERR_CUDA;
+    if (max_items) {
+        k_render_bwd<S><<<max_items, kThreads, smem, s>>>(a);
+    } else {
+        dim3 grid((a.K + S - 1) / S, T, a.B);
+        k_render_bwd<S><<<grid, kThreads, smem, s>>>(a);
+    }
+    return launch_status();
+}
+
+int launch_fwd_any(const RenderArgs& a, int T, cudaStream_t s) {
+    switch (pick_strip(a.K, (int64_t)T * a.B)) {
+        case 1: return launch_fwd<1>(a, T, s);
+        case 2: return launch_fwd<2>(a, T, s);
+        case 4: return launch_fwd<4>(a, T, s);
+        case 8: return launch_fwd<8>(a, T, s);
+        case 16: return launch_fwd<16>(a, T, s);
+        default: return launch_fwd<32>(a, T, s);
+    }
+}
+
+int launch_bwd_any(const RenderArgs& a, int T, cudaStream_t s, uint32_t max_items = 0) {
+    switch (pick_strip(a.K, (int64_t)T * a.B)) {
+        case 1: return launch_bwd<1>(a, T, s, max_items);
+        case 2: return launch_bwd<2>(a, T, s, max_items);
+        case 4: return launch_bwd<4>(a, T, s, max_items);
+        case 8: return launch_bwd<8>(a, T, s, max_items);
+        case 16: return launch_bwd<16>(a, T, s, max_items);
+        default: return launch_bwd<32>(a, T, s, max_items);
+    }
+}
+
+// strips of the FP32 kernels (the s_tot layout of gsparc_render_fwd_l2)
+int fp32_strips(int K) {
+    const int S = pick_strip(K, 0);
+    return (K + S - 1) / S;
 }
 
 bool common_ok(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
@@ -54,17 +93,38 @@ extern "C" int gsparc_render_fwd(const gsparc_view* view, const gsparc_band* ban
     a.final_logT = final_logT;
     a.n_contrib = n_contrib;
     a.n_used = n_used;
-    const int T = tiles_x(*view) * tiles_y(*view);
+    a.T = tiles_x(*view) * tiles_y(*view);
+    return launch_fwd_any(a, a.T, as_stream(stream));
+}
+
+extern "C" int gsparc_render_fwd_l2(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
+                                    const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
+                                    const float* attr, const float* target, float* loss, float* d_spectrum,
+                                    float* spectrum, float* final_logT, uint32_t* n_contrib, uint32_t* n_used,
+                                    float* s_tot, uint32_t* tile_walk, int32_t* d_status, void* stream) {
+    if (!common_ok(view, band, B, N, proj, tile_ranges, sorted_ids, attr)) return GSPARC_ERR_INVALID;
+    if (!target || !loss || !d_spectrum) return GSPARC_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(spectrum) | reinterpret_cast<uintptr_t>(target) |
+         reinterpret_cast<uintptr_t>(d_spectrum)) & 7)
+        return GSPARC_ERR_INVALID;
+    RenderArgs a{};
+    fill_args(view, band, B, N, proj, tile_ranges, sorted_ids, attr, a);
+    a.status = d_status;
+    a.spectrum = reinterpret_cast<float2*>(spectrum);
+    a.final_logT = final_logT;
+    a.n_contrib = n_contrib;
+    a.n_used = n_used;
+    a.l2_target = reinterpret_cast<const float2*>(target);
+    a.l2_loss = loss;
+    a.l2_grad = reinterpret_cast<float2*>(d_spectrum);
+    a.s_tot = s_tot;
+    a.tile_walk = tile_walk;
+    const int64_t count = (int64_t)B * band->K * view->H * view->W;
+    a.l2_inv = (float)(1.0 / (double)count);
+    a.T = tiles_x(*view) * tiles_y(*view);
     cudaStream_t s = as_stream(stream);
-    switch (pick_strip(band->K, (int64_t)T * B)) {
-        case 1: launch_fwd<1>(a, T, s); break;
-        case 2: launch_fwd<2>(a, T, s); break;
-        case 4: launch_fwd<4>(a, T, s); break;
-        case 8: launch_fwd<8>(a, T, s); break;
-        case 16: launch_fwd<16>(a, T, s); break;
-        default: launch_fwd<32>(a, T, s); break;
-    }
-    return launch_status();
+    if (cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess) return GSPARC_ERR_CUDA;
+    return launch_fwd_any(a, a.T, s);
 }
 
 extern "C" int gsparc_render_bwd(const gsparc_view* view, const gsparc_band* band, int32_t B,
@@ -85,17 +145,8 @@ extern "C" int gsparc_render_bwd(const gsparc_view* view, const gsparc_band* ban
     a.d_spectrum = reinterpret_cast<const float2*>(d_spectrum);
     a.d_attr = reinterpret_cast<float4*>(d_attr);
     a.d_proj = d_proj;
-    const int T = tiles_x(*view) * tiles_y(*view);
-    cudaStream_t s = as_stream(stream);
-    switch (pick_strip(band->K, (int64_t)T * B)) {
-        case 1: launch_bwd<1>(a, T, s); break;
-        case 2: launch_bwd<2>(a, T, s); break;
-        case 4: launch_bwd<4>(a, T, s); break;
-        case 8: launch_bwd<8>(a, T, s); break;
-        case 16: launch_bwd<16>(a, T, s); break;
-        default: launch_bwd<32>(a, T, s); break;
-    }
-    return launch_status();
+    a.T = tiles_x(*view) * tiles_y(*view);
+    return launch_bwd_any(a, a.T, as_stream(stream));
 }
 
 // =============================================================================================
@@ -1339,4 +1390,55 @@ extern "C" int gsparc_render_bwd_tc_balanced(const gsparc_view* view, const gspa
         reinterpret_cast<uint32_t*>(w + SL.walks), reinterpret_cast<uint4*>(w + SL.items));
     if (launch_status() != GSPARC_OK) return GSPARC_ERR_CUDA;
     return launch_bwd_tc_any(a, T, s, (uint32_t)(2 * units));
+}
+
+extern "C" int gsparc_render_bwd_workspace(const gsparc_view* view, const gsparc_band* band, int32_t B,
+                                           size_t* ws_bytes) {
+    using namespace gsparc;
+    if (!view_ok(view) || !band || band->K <= 0 || band->K > 65535 || B <= 0 || B > 65535 || !ws_bytes)
+        return GSPARC_ERR_INVALID;
+    *ws_bytes = sched_layout(B, tiles_x(*view) * tiles_y(*view), fp32_strips(band->K)).total;
+    return GSPARC_OK;
+}
+
+extern "C" int gsparc_render_bwd_balanced(const gsparc_view* view, const gsparc_band* band, int32_t B, int32_t N,
+                                          const float* proj, const uint32_t* tile_ranges, const uint32_t* sorted_ids,
+                                          const float* attr, const float* spectrum, const float* s_tot,
+                                          const uint32_t* tile_walk, const float* final_logT, const uint32_t* n_contrib,
+                                          const float* d_spectrum, int32_t split_min, void* ws, size_t ws_bytes,
+                                          float* d_attr, float* d_proj, int32_t* d_status, void* stream) {
+    using namespace gsparc;
+    if (!common_ok(view, band, B, N, proj, tile_ranges, sorted_ids, attr)) return GSPARC_ERR_INVALID;
+    if (!final_logT || !n_contrib || !d_spectrum || !d_attr || !d_proj || !ws) return GSPARC_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(d_spectrum) | reinterpret_cast<uintptr_t>(spectrum)) & 7) return GSPARC_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(d_attr) | reinterpret_cast<uintptr_t>(ws)) & 15) return GSPARC_ERR_INVALID;
+    const int T = tiles_x(*view) * tiles_y(*view), strips = fp32_strips(band->K);
+    const SchedLayout SL = sched_layout(B, T, strips);
+    if (ws_bytes < SL.total) return GSPARC_ERR_INVALID;
+    const int64_t units = (int64_t)B * T * strips;
+    if (2 * units >= (1ll << 31)) return GSPARC_ERR_INVALID;
+    RenderArgs a{};
+    fill_args(view, band, B, N, proj, tile_ranges, sorted_ids, attr, a);
+    a.status = d_status;
+    a.spectrum = const_cast<float2*>(reinterpret_cast<const float2*>(spectrum));
+    a.s_tot = const_cast<float*>(s_tot);
+    a.final_logT = const_cast<float*>(final_logT);
+    a.n_contrib = const_cast<uint32_t*>(n_contrib);
+    a.d_spectrum = reinterpret_cast<const float2*>(d_spectrum);
+    a.d_attr = reinterpret_cast<float4*>(d_attr);
+    a.d_proj = d_proj;
+    a.T = T;
+    char* w = static_cast<char*>(ws);
+    uint32_t* hdr = reinterpret_cast<uint32_t*>(w + SL.hdr);
+    a.items = reinterpret_cast<const uint4*>(w + SL.items);
+    a.n_items = hdr + 1;
+    cudaStream_t s = as_stream(stream);
+    // two CTAs per SM: splitting pays while the units are too few to fill them twice over
+    const int allow_split = units <= 4 * (int64_t)num_sms() ? 1 : 0;
+    const int smin = (!spectrum && !s_tot) ? -1 : (split_min == 0 ? kSplitMinDefault : split_min);
+    k_bwd_schedule<<<tile_walk ? 1u : (unsigned)(B * T), kSchedThreads, 0, s>>>(
+        view->H, view->W, tiles_x(*view), T, B * T, strips, smin, allow_split, a.ranges, n_contrib, tile_walk, hdr,
+        reinterpret_cast<uint32_t*>(w + SL.walks), reinterpret_cast<uint4*>(w + SL.items));
+    if (launch_status() != GSPARC_OK) return GSPARC_ERR_CUDA;
+    return launch_bwd_any(a, T, s, (uint32_t)(2 * units));
 }

@@ -9,11 +9,13 @@
 // Work item = (transmitter b, 16x16 tile, strip of S subcarriers); one CTA of
 // 256 threads per item, one pixel per thread, S complex accumulators per
 // thread.  Gaussian batches of the tile's sorted list are staged in shared
-// memory together with their unit phasors e^{j psi_ik} for the strip, so the
+// memory by bulk asynchronous copies (one batch ahead of the compositing)
+// together with their unit phasors e^{j psi_ik} for the strip, so the
 // per-(pixel, Gaussian, subcarrier) work is two FFMAs (forward) or six
 // (backward) against broadcast shared-memory reads.  Transmittance is carried
 // as log2 T in FP32; a thread stops before T would fall below 1e-4 and the
-// CTA stops fetching once every thread has stopped.
+// CTA stops fetching once every thread has stopped.  The backward can run as
+// scheduled chunks of the walks (the items of k_bwd_schedule).
 //
 // This header holds what the FP32 kernels and the tensor-core kernels share (arguments, alpha,
 // unit phasors, batch staging) and the FP32 kernels themselves, as device code with no runtime
@@ -25,6 +27,7 @@
 
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "device_common.cuh"
 
@@ -135,49 +138,141 @@ __device__ __forceinline__ float2 unit_phasor(const RenderArgs& a, float L, floa
     return make_float2(cs, -sn);   // e^{j psi} = e^{-j 2 pi c}
 }
 
-// Stage batch entries [list_pos, list_pos + nb) of the tile list, and the
-// unit phasors of the strip's subcarriers.
-template <int S>
-__device__ __forceinline__ void stage_batch(const RenderArgs& a, int b, uint32_t list_pos, int nb,
-                                            int k0, float4* s_geo, float2* s_geo2, float2* s_ext,
-                                            float* s_amp, float2 (*s_tab)[S], uint32_t* s_gid) {
-    const int tid = threadIdx.x;
-    __shared__ float s_L[kBatch], s_phi[kBatch];
-    if (tid < nb) {
-        uint32_t gid = a.ids[list_pos + tid];
-        if (gid < (uint32_t)a.N) {
-            const float4 p0 = a.proj[2 * gid];
-            const float4 p1 = a.proj[2 * gid + 1];
-            const float4 at = a.attr[(size_t)b * a.N + gid];
-            s_geo[tid] = make_float4(p0.x, p0.y, p1.x, p1.y);
-            s_geo2[tid] = make_float2(p1.z, at.z);
-            s_ext[tid] = make_float2(p0.z, p0.w);
-            s_amp[tid] = at.x;
-            s_phi[tid] = at.y;
-            s_L[tid] = at.w;
-        } else {
-            // an id outside the scene (inconsistent inputs): a NaN conic makes
-            // every pixel skip it, it receives no gradient, and the status word says so
-            set_status(a.status, GSPARC_ERR_INPUT);
-            s_geo[tid] = make_float4(0.f, 0.f, __int_as_float(0x7fc00000), 0.f);
-            s_geo2[tid] = make_float2(0.f, 0.f);
-            s_ext[tid] = make_float2(-1.f, -1.f);
-            s_amp[tid] = 0.f;
-            s_phi[tid] = 0.f;
-            s_L[tid] = 0.f;
-            gid = 0;
-        }
-        s_gid[tid] = gid;
+// ---------------------------------------------------------------------------------------------
+// Staging of a batch's records for the FP32 kernels.  Entry j of a batch is its 32-byte
+// projection record and 16-byte attribute record, brought into shared memory by two 1-D bulk
+// asynchronous copies (cp.async.bulk, the TMA engine) that complete on the batch's mbarrier.
+// The records are double-buffered: the copies of batch i + 1 are issued once every warp has
+// finished batch i - 1 and fly while batch i is composited.  Under the test suite's host shim the
+// copies are plain copies and the barrier is already complete.
+// ---------------------------------------------------------------------------------------------
+
+struct StageRec {
+    float4 p0;   // p_x, p_y, ext_x, ext_y
+    float4 p1;   // c_xx, c_xy, c_yy, r
+    float4 at;   // a, phi0, sigma, L
+};
+
+#ifndef GSPARC_HOST_SHIM
+__device__ __forceinline__ uint32_t smem_addr32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// one arrival per entry slot of a batch (kBatch), each with the bytes of its copies
+__device__ __forceinline__ void stage_bar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr32(bar)), "n"(kBatch) : "memory");
+}
+__device__ __forceinline__ void stage_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// generic-proxy accesses to the buffer before this point are ordered before the copies after it
+__device__ __forceinline__ void stage_proxy_fence() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// the one arrival of the batch's phase, with the bytes its copies will deliver
+__device__ __forceinline__ void stage_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void stage_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr32(bar))
+                 : "memory");
+}
+// bounded wait for the phase of the given parity; false when `polls` polls found it incomplete
+__device__ __forceinline__ bool stage_wait(uint64_t* bar, uint32_t parity, uint32_t polls) {
+    const uint32_t addr = smem_addr32(bar);
+    for (uint32_t it = 0; it < polls; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
     }
+    return false;
+}
+#else
+inline void stage_bar_init(uint64_t* bar) { *bar = 0; }
+inline void stage_init_fence() {}
+inline void stage_proxy_fence() {}
+inline void stage_expect(uint64_t*, uint32_t) {}
+inline void stage_copy(void* dst, const void* src, uint32_t bytes, uint64_t*) { memcpy(dst, src, bytes); }
+// every thread of the block waits at the same program point, so a block barrier stands for the
+// mbarrier: each copy was made when its issuing thread ran
+inline bool stage_wait(uint64_t*, uint32_t, uint32_t) {
     __syncthreads();
-    for (int e = tid; e < nb * S; e += kThreads) {
+    return true;
+}
+#endif
+
+constexpr uint32_t kStagePolls = 1u << 22;   // bound of a staging wait (far above a healthy copy)
+
+// Stage batch entries [list_pos, list_pos + nb) of the tile list (their ids already loaded,
+// one per thread in `gid`, tid < nb) into rec: every thread tid < kBatch makes one arrival on the
+// batch's mbarrier (initialised for kBatch arrivals), a thread with an entry announcing the 48
+// bytes its two bulk copies deliver.  An id outside the scene (inconsistent inputs) gets a record
+// with a NaN conic instead, so that every pixel skips it and it receives no gradient, and the
+// status word says so.
+__device__ __forceinline__ void stage_issue(const RenderArgs& a, int b, int nb, uint32_t gid, StageRec* rec,
+                                            uint32_t* s_gid, uint64_t* bar) {
+    const int tid = threadIdx.x;
+    if (tid >= kBatch) return;
+    if (tid < nb && gid < (uint32_t)a.N) {
+        s_gid[tid] = gid;
+        stage_expect(bar, 48u);
+        stage_copy(&rec[tid].p0, a.proj + 2 * (size_t)gid, 32u, bar);
+        stage_copy(&rec[tid].at, a.attr + (size_t)b * a.N + gid, 16u, bar);
+    } else {
+        if (tid < nb) {
+            set_status(a.status, GSPARC_ERR_INPUT);
+            rec[tid].p0 = make_float4(0.f, 0.f, -1.f, -1.f);
+            rec[tid].p1 = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+            rec[tid].at = make_float4(0.f, 0.f, 0.f, 0.f);
+            s_gid[tid] = 0u;
+        }
+        stage_expect(bar, 0u);
+    }
+}
+
+// Unit phasors of the strip's subcarriers for the nb entries of rec (every thread), into tab.
+template <int S>
+__device__ __forceinline__ void stage_phasors(const RenderArgs& a, const StageRec* rec, int nb, int k0,
+                                              float2 (*tab)[S]) {
+    for (int e = threadIdx.x; e < nb * S; e += kThreads) {
         const int j = e / S, kk = e - j * S;
         const int k = k0 + kk;
         float2 ph = make_float2(0.f, 0.f);
-        if (k < a.K) ph = unit_phasor(a, s_L[j], s_phi[j], k);
-        s_tab[j][kk] = ph;
+        if (k < a.K) ph = unit_phasor(a, rec[j].at.w, rec[j].at.y, k);
+        tab[j][kk] = ph;
     }
-    __syncthreads();
+}
+
+// warp_entry_mask over staged records (see warp_entry_mask).
+__device__ __forceinline__ uint64_t warp_entry_mask_rec(const StageRec* rec, int nb, float wcx, float wcy, int W) {
+    const int lane = threadIdx.x & 31;
+    const float hw = 0.5f * (float)W;
+    bool h0 = false, h1 = false;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int j = lane + 32 * half;
+        bool hit = false;
+        if (j < nb) {
+            const float4 p = rec[j].p0;
+            float dx = wcx - p.x;
+            if (dx >= hw) dx -= (float)W;
+            else if (dx < -hw) dx += (float)W;
+            const float dy = wcy - p.y;
+            hit = p.z >= 0.f && fabsf(dx) <= p.z + 7.51f && fabsf(dy) <= p.w + 0.51f;
+        }
+        if (half == 0) h0 = hit;
+        else h1 = hit;
+    }
+    const uint32_t lo = __ballot_sync(0xffffffffu, h0);
+    const uint32_t hi = __ballot_sync(0xffffffffu, h1);
+    return ((uint64_t)hi << 32) | lo;
 }
 
 // Bit j set when staged entry j's footprint box reaches the warp's 16x2 block of
@@ -207,78 +302,6 @@ __device__ __forceinline__ uint64_t warp_entry_mask(const float4* s_geo, const f
     const uint32_t lo = __ballot_sync(0xffffffffu, h0);
     const uint32_t hi = __ballot_sync(0xffffffffu, h1);
     return ((uint64_t)hi << 32) | lo;
-}
-
-template <int S>
-__global__ void __launch_bounds__(kThreads, 2) k_render_fwd(RenderArgs a) {
-    __shared__ float4 s_geo[kBatch];
-    __shared__ float2 s_geo2[kBatch];
-    __shared__ float2 s_ext[kBatch];
-    __shared__ float s_amp[kBatch];
-    __shared__ uint32_t s_gid[kBatch];
-    __shared__ __align__(16) float2 s_tab[kBatch][S];
-
-    const int strip = blockIdx.x, tile = blockIdx.y, b = blockIdx.z;
-    const int k0 = strip * S;
-    const int tid = threadIdx.x;
-    const int tx0 = (tile % a.TW) * kTile, ty0 = (tile / a.TW) * kTile;
-    const int x = tx0 + (tid & 15);
-    const int y = ty0 + (tid >> 4);
-    const bool inside = x < a.W && y < a.H;
-    const float ux = (float)x + 0.5f, uy = (float)y + 0.5f;
-    const float wcx = (float)tx0 + 8.0f, wcy = (float)(ty0 + 2 * (tid >> 5)) + 1.0f;
-    const uint2 range = a.ranges[tile];
-
-    float2 acc[S];
-#pragma unroll
-    for (int kk = 0; kk < S; ++kk) acc[kk] = make_float2(0.f, 0.f);
-    float logT = 0.f;
-    uint32_t last = 0, used = 0;
-    bool done = !inside;
-
-    for (uint32_t bs = range.x; bs < range.y; bs += kBatch) {
-        if (__syncthreads_or(!done) == 0) break;
-        const int nb = (int)min((uint32_t)kBatch, range.y - bs);
-        stage_batch<S>(a, b, bs, nb, k0, s_geo, s_geo2, s_ext, s_amp, s_tab, s_gid);
-        uint64_t mask = warp_entry_mask(s_geo, s_ext, nb, wcx, wcy, a.W);
-        if (!done) {
-            while (mask) {
-                const int j = __ffsll((long long)mask) - 1;
-                mask &= mask - 1;
-                float dx, dy, G, alpha;
-                bool clamped;
-                if (!eval_alpha(ux, uy, a.W, s_geo[j], s_geo2[j], dx, dy, G, alpha, clamped)) continue;
-                const float nl = lg2(__fsub_rn(1.0f, alpha));
-                if (__fadd_rn(logT, nl) < kLog2TMin) {
-                    done = true;
-                    break;
-                }
-                const float wa = ex2(logT) * alpha * s_amp[j];
-#pragma unroll
-                for (int kk = 0; kk < S; ++kk) {
-                    const float2 t = s_tab[j][kk];
-                    acc[kk].x = fmaf(wa, t.x, acc[kk].x);
-                    acc[kk].y = fmaf(wa, t.y, acc[kk].y);
-                }
-                logT = __fadd_rn(logT, nl);
-                last = bs - range.x + (uint32_t)j + 1u;
-                ++used;
-            }
-        }
-    }
-    if (!inside) return;
-    const size_t plane = (size_t)a.H * a.W;
-    const size_t pix = (size_t)y * a.W + x;
-#pragma unroll
-    for (int kk = 0; kk < S; ++kk) {
-        const int k = k0 + kk;
-        if (k < a.K) a.spectrum[((size_t)b * a.K + k) * plane + pix] = acc[kk];
-    }
-    if (strip == 0) {
-        if (a.final_logT) a.final_logT[(size_t)b * plane + pix] = logT;
-        if (a.n_contrib) a.n_contrib[(size_t)b * plane + pix] = last;
-        if (a.n_used) a.n_used[(size_t)b * plane + pix] = used;
-    }
 }
 
 // Sum of v[c] over the 32 lanes of the warp for c < 9, returned in lane 2c (and
@@ -361,20 +384,236 @@ __device__ __forceinline__ int rs18_slot(int lane) {
     return (sc <= 2 && sb <= 4 && sa <= 8) ? sv : -1;
 }
 
+// Shared memory of the FP32 kernels (dynamic): records, phasor tables and ids of two batches,
+// the two staging mbarriers, and (backward) the per-warp gradient partial sums of a batch.
 template <int S>
-__global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
-    __shared__ float4 s_geo[kBatch];
-    __shared__ float2 s_geo2[kBatch];
-    __shared__ float2 s_ext[kBatch];
-    __shared__ float s_amp[kBatch];
-    __shared__ uint32_t s_gid[kBatch];
-    __shared__ __align__(16) float2 s_tab[kBatch][S];
-    __shared__ float s_red[kThreads / 32][kBatch][9];
-    __shared__ uint64_t s_wmask[kThreads / 32];
-    __shared__ uint32_t s_maxlast;
+struct F32Smem {
+    static constexpr int kRec = 0;                                        // StageRec[2][kBatch]
+    static constexpr int kTab = kRec + 2 * kBatch * (int)sizeof(StageRec);  // float2[2][kBatch][S]
+    static constexpr int kGid = kTab + 2 * kBatch * S * 8;                // uint32[2][kBatch]
+    static constexpr int kBar = kGid + 2 * kBatch * 4;                    // uint64[2]
+    static constexpr int kRed = kBar + 16;                                // float[8][kBatch][9]
+    static constexpr int kMask = kRed + 8 * kBatch * 9 * 4;               // uint64[8]
+    static constexpr int kMisc = kMask + 8 * 8;                           // float[8], uint32[4]
+    static constexpr int kTotal = kMisc + 48;
+    static_assert(kTab % 16 == 0 && kBar % 8 == 0 && kMask % 8 == 0, "shared-memory alignment");
+};
+
+// Batch i of a walk over list positions [lo, end): front to back from lo, or back to front
+// from end (the last batch then the ragged one).
+__device__ __forceinline__ void batch_span(bool front, uint32_t lo, uint32_t end, int i, uint32_t& b_lo, int& nb) {
+    if (front) {
+        b_lo = lo + (uint32_t)i * kBatch;
+        nb = (int)min((uint32_t)kBatch, end - b_lo);
+    } else {
+        const uint32_t hp = end - (uint32_t)i * kBatch;
+        b_lo = hp > lo + kBatch ? hp - kBatch : lo;
+        nb = (int)(hp - b_lo);
+    }
+}
+
+// The forward: one CTA per (strip of S subcarriers, tile, transmitter), one pixel per thread, S
+// complex accumulators per thread.  With a.l2_grad the complex L2 loss is fused into the
+// epilogue (dL/dz written, bit-identical to gsparc_l2_loss on this spectrum; the loss added
+// atomically), with s_tot and the tile walks written for the scheduled backward when given.
+template <int S>
+__global__ void __launch_bounds__(kThreads, 2) k_render_fwd(RenderArgs a) {
+    using L = F32Smem<S>;
+    GSPARC_DYNAMIC_SMEM(sm);
+    StageRec* s_rec = reinterpret_cast<StageRec*>(sm + L::kRec);
+    float2(*s_tab)[kBatch][S] = reinterpret_cast<float2(*)[kBatch][S]>(sm + L::kTab);
+    uint32_t* s_gid = reinterpret_cast<uint32_t*>(sm + L::kGid);
+    uint64_t* s_bar = reinterpret_cast<uint64_t*>(sm + L::kBar);
+    float* s_part = reinterpret_cast<float*>(sm + L::kMisc);
+    uint32_t* s_walk = reinterpret_cast<uint32_t*>(sm + L::kMisc + 32);
+    uint32_t* s_err = s_walk + 1;
 
     const int strip = blockIdx.x, tile = blockIdx.y, b = blockIdx.z;
     const int k0 = strip * S;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx0 = (tile % a.TW) * kTile, ty0 = (tile / a.TW) * kTile;
+    const int x = tx0 + (tid & 15);
+    const int y = ty0 + (tid >> 4);
+    const bool inside = x < a.W && y < a.H;
+    const float ux = (float)x + 0.5f, uy = (float)y + 0.5f;
+    const float wcx = (float)tx0 + 8.0f, wcy = (float)(ty0 + 2 * warp) + 1.0f;
+    const uint2 range = a.ranges[tile];
+    const uint32_t len = range.y - range.x;
+    const int nbatch = (int)((len + kBatch - 1) / kBatch);
+
+    if (tid == 0) {
+        stage_bar_init(&s_bar[0]);
+        stage_bar_init(&s_bar[1]);
+        stage_init_fence();
+        *s_walk = 0u;
+        *s_err = 0u;
+    }
+    // list ids one batch ahead of the copies
+    auto load_id = [&](int i) -> uint32_t {
+        const uint32_t p = (uint32_t)i * kBatch + (uint32_t)tid;
+        return (tid < kBatch && i < nbatch && p < len) ? a.ids[range.x + p] : 0xffffffffu;
+    };
+    uint32_t pf_id = load_id(0);
+    __syncthreads();
+    if (nbatch > 0) stage_issue(a, b, (int)min((uint32_t)kBatch, len), pf_id, s_rec, s_gid, &s_bar[0]);
+    pf_id = load_id(1);
+
+    float2 acc[S];
+#pragma unroll
+    for (int kk = 0; kk < S; ++kk) acc[kk] = make_float2(0.f, 0.f);
+    float logT = 0.f;
+    uint32_t last = 0, used = 0;
+    bool done = !inside;
+
+    for (int i = 0; i < nbatch; ++i) {
+        const int buf = i & 1;
+        const uint32_t bs = (uint32_t)i * kBatch;
+        const int nb = (int)min((uint32_t)kBatch, len - bs);
+        if (!stage_wait(&s_bar[buf], (uint32_t)(i >> 1) & 1u, kStagePolls)) {
+            *s_err = 1u;
+            stage_wait(&s_bar[buf], (uint32_t)(i >> 1) & 1u, kStagePolls);   // copies still in flight
+        }
+        stage_phasors<S>(a, s_rec + buf * kBatch, nb, k0, s_tab[buf]);
+        // phasors of batch i in place; every warp has finished batch i - 1, whose buffers the
+        // copies of batch i + 1 now take over
+        if (__syncthreads_or(!done) == 0 || *s_err) break;
+        if (i + 1 < nbatch) {
+            if (tid < kBatch) stage_proxy_fence();
+            stage_issue(a, b, (int)min((uint32_t)kBatch, len - bs - kBatch), pf_id, s_rec + (buf ^ 1) * kBatch,
+                        s_gid + (buf ^ 1) * kBatch, &s_bar[buf ^ 1]);
+            pf_id = load_id(i + 2);
+        }
+        const StageRec* rec = s_rec + buf * kBatch;
+        uint64_t mask = warp_entry_mask_rec(rec, nb, wcx, wcy, a.W);
+        if (!done) {
+            while (mask) {
+                const int j = __ffsll((long long)mask) - 1;
+                mask &= mask - 1;
+                const StageRec& r = rec[j];
+                float dx, dy, G, alpha;
+                bool clamped;
+                if (!eval_alpha(ux, uy, a.W, make_float4(r.p0.x, r.p0.y, r.p1.x, r.p1.y),
+                                make_float2(r.p1.z, r.at.z), dx, dy, G, alpha, clamped))
+                    continue;
+                const float nl = lg2(__fsub_rn(1.0f, alpha));
+                if (__fadd_rn(logT, nl) < kLog2TMin) {
+                    done = true;
+                    break;
+                }
+                const float wa = ex2(logT) * alpha * r.at.x;
+#pragma unroll
+                for (int kk = 0; kk < S; ++kk) {
+                    const float2 t = s_tab[buf][j][kk];
+                    acc[kk].x = fmaf(wa, t.x, acc[kk].x);
+                    acc[kk].y = fmaf(wa, t.y, acc[kk].y);
+                }
+                logT = __fadd_rn(logT, nl);
+                last = bs + (uint32_t)j + 1u;
+                ++used;
+            }
+        }
+    }
+    if (*s_err) set_status(a.status, GSPARC_ERR_TIMEOUT);
+    // epilogue: the spectrum, and with the fused loss dL/dz, the loss and s_tot
+    const size_t plane = (size_t)a.H * a.W;
+    const size_t pix = (size_t)y * a.W + x;
+    float l2acc = 0.f, stot = 0.f;
+    if (inside) {
+#pragma unroll
+        for (int k8 = 0; k8 < S; k8 += 8) {
+            float2 t[8];
+#pragma unroll
+            for (int q = 0; q < 8 && k8 + q < S; ++q) {
+                const int k = k0 + k8 + q;
+                t[q] = (a.l2_grad && k < a.K) ? a.l2_target[((size_t)b * a.K + k) * plane + pix]
+                                              : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 8 && k8 + q < S; ++q) {
+                const int k = k0 + k8 + q;
+                if (k >= a.K) continue;
+                const size_t e = ((size_t)b * a.K + k) * plane + pix;
+                const float2 z = acc[k8 + q];
+                if (a.spectrum) a.spectrum[e] = z;
+                if (a.l2_grad) {
+                    const float dr = z.x - t[q].x, di = z.y - t[q].y;
+                    l2acc = fmaf(dr, dr, fmaf(di, di, l2acc));
+                    const float2 gz = make_float2(2.f * dr * a.l2_inv, 2.f * di * a.l2_inv);
+                    a.l2_grad[e] = gz;
+                    stot = fmaf(gz.x, z.x, fmaf(gz.y, z.y, stot));
+                }
+            }
+        }
+        if (a.l2_grad && a.s_tot) a.s_tot[((size_t)b * gridDim.x + strip) * plane + pix] = stot;
+        if (strip == 0) {
+            if (a.final_logT) a.final_logT[(size_t)b * plane + pix] = logT;
+            if (a.n_contrib) a.n_contrib[(size_t)b * plane + pix] = last;
+            if (a.n_used) a.n_used[(size_t)b * plane + pix] = used;
+        }
+    }
+    if (a.l2_grad) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l2acc += __shfl_xor_sync(0xffffffffu, l2acc, o);
+        if (lane == 0) s_part[warp] = l2acc;
+    }
+    if (a.tile_walk && strip == 0) {
+        uint32_t wmax = inside ? last : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+        if (lane == 0 && wmax) atomicMax(s_walk, wmax);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (a.l2_grad) {
+            float t = 0.f;
+            for (int w2 = 0; w2 < kThreads / 32; ++w2) t += s_part[w2];
+            atomicAdd(a.l2_loss, t * a.l2_inv);
+        }
+        if (a.tile_walk && strip == 0) a.tile_walk[(size_t)b * a.T + tile] = min(*s_walk, len);
+    }
+}
+
+// The backward.  Work item: one (transmitter, tile, strip of S subcarriers) walk over the list
+// positions [0, walk), back to front from each pixel's final state (no item list: one CTA per
+// walk), or a scheduled chunk of it (a.items: item r on CTA r): a back chunk [m, walk) back to
+// front, or a front chunk [0, m) front to back from T = 1 with the suffix sum taken as
+// s_tot - prefix (s_tot = Re sum_k conj(dL/dz_k) z_k over the strip, given or formed here from
+// the spectrum).  Per list entry every pixel's nine gradient components are reduced over the
+// warp in one reduce-scatter; after each batch one atomic per (Gaussian, component) adds the
+// CTA's sum.
+template <int S>
+__global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
+    using L = F32Smem<S>;
+    GSPARC_DYNAMIC_SMEM(sm);
+    StageRec* s_rec = reinterpret_cast<StageRec*>(sm + L::kRec);
+    float2(*s_tab)[kBatch][S] = reinterpret_cast<float2(*)[kBatch][S]>(sm + L::kTab);
+    uint32_t* s_gid = reinterpret_cast<uint32_t*>(sm + L::kGid);
+    uint64_t* s_bar = reinterpret_cast<uint64_t*>(sm + L::kBar);
+    float* s_red = reinterpret_cast<float*>(sm + L::kRed);              // [warp][kBatch][9]
+    uint64_t* s_wmask = reinterpret_cast<uint64_t*>(sm + L::kMask);
+    uint32_t* s_maxlast = reinterpret_cast<uint32_t*>(sm + L::kMisc + 32);
+    uint32_t* s_err = s_maxlast + 1;
+
+    int strip, tile, b;
+    bool front = false;
+    uint32_t lo = 0, end = 0;
+    if (a.items) {
+        const uint32_t r = blockIdx.x;
+        if (r >= *a.n_items) return;   // the whole block, before any barrier
+        const uint4 it = a.items[r];
+        b = (int)(it.x / (uint32_t)a.T);
+        tile = (int)(it.x - (uint32_t)b * (uint32_t)a.T);
+        strip = (int)(it.y & 0x7fffffffu);
+        front = (it.y >> 31) != 0u;
+        lo = it.z;
+        end = it.w;
+    } else {
+        strip = blockIdx.x;
+        tile = blockIdx.y;
+        b = blockIdx.z;
+    }
+    const int k0 = strip * S;
+    const int strips = (a.K + S - 1) / S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tx0 = (tile % a.TW) * kTile, ty0 = (tile / a.TW) * kTile;
     const int x = tx0 + (tid & 15);
@@ -390,95 +629,153 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
 #pragma unroll
     for (int kk = 0; kk < S; ++kk) {
         const int k = k0 + kk;
-        g[kk] = (inside && k < a.K) ? a.d_spectrum[((size_t)b * a.K + k) * plane + pix]
-                                    : make_float2(0.f, 0.f);
+        g[kk] = (inside && k < a.K) ? a.d_spectrum[((size_t)b * a.K + k) * plane + pix] : make_float2(0.f, 0.f);
     }
-    float logT = inside ? a.final_logT[(size_t)b * plane + pix] : 0.f;
+    float s_tot = 0.f;
+    if (front && inside) {
+        if (a.s_tot) {
+            s_tot = a.s_tot[((size_t)b * strips + strip) * plane + pix];
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < S; ++kk) {
+                const int k = k0 + kk;
+                if (k < a.K) {
+                    const float2 z = a.spectrum[((size_t)b * a.K + k) * plane + pix];
+                    s_tot = fmaf(g[kk].x, z.x, fmaf(g[kk].y, z.y, s_tot));
+                }
+            }
+        }
+    }
+    float logT = (inside && !front) ? a.final_logT[(size_t)b * plane + pix] : 0.f;
     const uint32_t last = inside ? a.n_contrib[(size_t)b * plane + pix] : 0u;
-    if (tid == 0) s_maxlast = 0;
+    if (tid == 0) {
+        stage_bar_init(&s_bar[0]);
+        stage_bar_init(&s_bar[1]);
+        stage_init_fence();
+        *s_maxlast = 0u;
+        *s_err = 0u;
+    }
     __syncthreads();
-    if (last) atomicMax(&s_maxlast, last);
-    __syncthreads();
-    const uint32_t maxlast = min(s_maxlast, range.y - range.x);
+    if (!a.items) {
+        if (last) atomicMax(s_maxlast, last);
+        __syncthreads();
+        end = min(*s_maxlast, range.y - range.x);   // the walk: the largest n_contrib
+    }
+    const int nbatch = (int)((end - lo + kBatch - 1) / kBatch);
+    auto load_id = [&](int i) -> uint32_t {
+        if (tid >= kBatch || i >= nbatch) return 0xffffffffu;
+        uint32_t b_lo;
+        int nb;
+        batch_span(front, lo, end, i, b_lo, nb);
+        return tid < nb ? a.ids[range.x + b_lo + tid] : 0xffffffffu;
+    };
+    uint32_t pf_id = load_id(0);
+    if (nbatch > 0) {
+        uint32_t b_lo;
+        int nb;
+        batch_span(front, lo, end, 0, b_lo, nb);
+        stage_issue(a, b, nb, pf_id, s_rec, s_gid, &s_bar[0]);
+    }
+    pf_id = load_id(1);
     // dpsi/dL = -(2 pi / c) (f_strip0 + kk df)
     const float c_f0 = (float)(a.two_pi_over_c * (a.f0 + (double)k0 * a.df));
     const float c_df = (float)(a.two_pi_over_c * a.df);
-    float suffix = 0.f;   // sum over later composited m of w_m a_m Re(conj(g) e^{j psi_m})
-
-    for (uint32_t bend = maxlast; bend > 0;) {
-        const uint32_t bstart = bend > (uint32_t)kBatch ? bend - kBatch : 0u;
-        const int nb = (int)(bend - bstart);
-        __syncthreads();
-        stage_batch<S>(a, b, range.x + bstart, nb, k0, s_geo, s_geo2, s_ext, s_amp, s_tab, s_gid);
-        uint64_t mask = warp_entry_mask(s_geo, s_ext, nb, wcx, wcy, a.W);
+    // Back to front: acc = the sum over later composited entries of w a Re(conj(g) e^{j psi})
+    // (the suffix); front to back: the same sum over the entries up to this one (suffix =
+    // s_tot - acc).  The two directions differ in a few selects, not in code paths.
+    float acc = 0.f;
+    for (int i = 0; i < nbatch; ++i) {
+        const int buf = i & 1;
+        uint32_t b_lo;
+        int nb;
+        batch_span(front, lo, end, i, b_lo, nb);
+        if (!stage_wait(&s_bar[buf], (uint32_t)(i >> 1) & 1u, kStagePolls)) {
+            *s_err = 1u;
+            stage_wait(&s_bar[buf], (uint32_t)(i >> 1) & 1u, kStagePolls);   // copies still in flight
+        }
+        stage_phasors<S>(a, s_rec + buf * kBatch, nb, k0, s_tab[buf]);
+        __syncthreads();   // phasors in place; the previous batch's flush is done
+        if (*s_err) break;
+        if (i + 1 < nbatch) {
+            uint32_t n_lo;
+            int nn;
+            batch_span(front, lo, end, i + 1, n_lo, nn);
+            if (tid < kBatch) stage_proxy_fence();
+            stage_issue(a, b, nn, pf_id, s_rec + (buf ^ 1) * kBatch, s_gid + (buf ^ 1) * kBatch, &s_bar[buf ^ 1]);
+            pf_id = load_id(i + 2);
+        }
+        const StageRec* rec = s_rec + buf * kBatch;
+        const uint64_t mask = warp_entry_mask_rec(rec, nb, wcx, wcy, a.W);
         if (lane == 0) s_wmask[warp] = mask;
-        while (mask) {
-            const int j = 63 - __clzll((long long)mask);
-            mask ^= 1ull << j;
+        for (int jj = 0; jj < kBatch; ++jj) {
+            const int j = front ? jj : kBatch - 1 - jj;
+            if (!((mask >> j) & 1ull)) continue;   // warp-uniform: the entry misses the warp
+            const StageRec& r = rec[j];
+            const float4 gg = make_float4(r.p0.x, r.p0.y, r.p1.x, r.p1.y);
+            const float2 g2 = make_float2(r.p1.z, r.at.z);
+            float dx = 0.f, dy = 0.f, G = 0.f, alpha = 0.f;
+            bool clamped = false;
+            const bool live = b_lo + (uint32_t)j < last && eval_alpha(ux, uy, a.W, gg, g2, dx, dy, G, alpha, clamped);
+            if (!__any_sync(0xffffffffu, live)) {
+                if (lane < 9) s_red[(warp * kBatch + j) * 9 + lane] = 0.f;
+                continue;
+            }
+            float reG = 0.f, imG = 0.f, imF = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < S; ++kk) {
+                const float2 t = s_tab[buf][j][kk];
+                reG = fmaf(g[kk].x, t.x, fmaf(g[kk].y, t.y, reG));
+                const float pi_ = fmaf(g[kk].x, t.y, -g[kk].y * t.x);
+                imG += pi_;
+                imF = fmaf((float)kk, pi_, imF);
+            }
             float gr[9];
 #pragma unroll
             for (int c = 0; c < 9; ++c) gr[c] = 0.f;
-            bool contrib = false;
-            const uint32_t pos = bstart + (uint32_t)j;
-            if (pos < last) {
-                const float4 gg = s_geo[j];
-                const float2 g2 = s_geo2[j];
-                float dx, dy, G, alpha;
-                bool clamped;
-                if (eval_alpha(ux, uy, a.W, gg, g2, dx, dy, G, alpha, clamped)) {
-                    contrib = true;
-                    const float nl = lg2(__fsub_rn(1.0f, alpha));
-                    const float logT_before = __fsub_rn(logT, nl);
-                    const float T = ex2(logT_before);
-                    const float w = T * alpha;
-                    float reG = 0.f, imG = 0.f, imF = 0.f;
-#pragma unroll
-                    for (int kk = 0; kk < S; ++kk) {
-                        const float2 t = s_tab[j][kk];
-                        reG = fmaf(g[kk].x, t.x, fmaf(g[kk].y, t.y, reG));
-                        const float pi_ = fmaf(g[kk].x, t.y, -g[kk].y * t.x);
-                        imG += pi_;
-                        imF = fmaf((float)kk, pi_, imF);
-                    }
-                    const float amp = s_amp[j];
-                    const float reGa = amp * reG;
-                    const float dalpha = T * reGa - suffix / (1.0f - alpha);
-                    suffix = fmaf(w, reGa, suffix);
-                    gr[6] = w * reG;                                  // d a
-                    gr[7] = -w * amp * imG;                           // d phi0
-                    gr[8] = w * amp * (c_f0 * imG + c_df * imF);      // d L
-                    if (!clamped) {
-                        const float sig = g2.y;
-                        gr[5] = dalpha * G;                           // d sigma
-                        const float dq = -0.5f * dalpha * sig * G;
-                        gr[0] = dq * (-2.0f * (gg.z * dx + gg.w * dy));   // d p_x
-                        gr[1] = dq * (-2.0f * (gg.w * dx + g2.x * dy));   // d p_y
-                        gr[2] = dq * dx * dx;                             // d c_xx
-                        gr[3] = dq * 2.0f * dx * dy;                      // d c_xy
-                        gr[4] = dq * dy * dy;                             // d c_yy
-                    }
-                    logT = logT_before;
+            if (live) {
+                const float nl = lg2(__fsub_rn(1.0f, alpha));
+                const float amp = r.at.x;
+                const float reGa = amp * reG;
+                // front: T before the entry is the running one, then T *= 1 - alpha; back: T
+                // before the entry is recovered from the one after it
+                const float logT_next = front ? __fadd_rn(logT, nl) : __fsub_rn(logT, nl);
+                const float T = ex2(front ? logT : logT_next);
+                const float w = T * alpha;
+                const float acc_next = fmaf(w, reGa, acc);
+                const float suffix = front ? s_tot - acc_next : acc;
+                const float dalpha = T * reGa - suffix / (1.0f - alpha);
+                acc = acc_next;
+                logT = logT_next;
+                gr[6] = w * reG;                                  // d a
+                gr[7] = -w * amp * imG;                           // d phi0
+                gr[8] = w * amp * (c_f0 * imG + c_df * imF);      // d L
+                if (!clamped) {
+                    const float sig = g2.y;
+                    gr[5] = dalpha * G;                           // d sigma
+                    const float dq = -0.5f * dalpha * sig * G;
+                    gr[0] = dq * (-2.0f * (gg.z * dx + gg.w * dy));   // d p_x
+                    gr[1] = dq * (-2.0f * (gg.w * dx + g2.x * dy));   // d p_y
+                    gr[2] = dq * dx * dx;                             // d c_xx
+                    gr[3] = dq * 2.0f * dx * dy;                      // d c_xy
+                    gr[4] = dq * dy * dy;                             // d c_yy
                 }
             }
-            if (__any_sync(0xffffffffu, contrib)) {
-                // reduce-scatter of the 9 components over the warp: lane l ends with the
-                // warp total of component l >> 1
-                const float tot = warp_reduce_scatter9(gr, lane);
-                if ((lane & 1) == 0 && (lane >> 1) < 9) s_red[warp][j][lane >> 1] = tot;
-            } else if (lane < 9) {
-                s_red[warp][j][lane] = 0.f;
-            }
+            // reduce-scatter of the 9 components over the warp: lane l ends with the warp total
+            // of component l >> 1
+            const float tot = warp_reduce_scatter9(gr, lane);
+            if ((lane & 1) == 0 && (lane >> 1) < 9) s_red[(warp * kBatch + j) * 9 + (lane >> 1)] = tot;
         }
         __syncthreads();
         // one atomic per (Gaussian, component) for the whole CTA
+        const uint32_t* gids = s_gid + buf * kBatch;
         for (int e = tid; e < nb * 9; e += kThreads) {
             const int j = e / 9, c = e - j * 9;
             float v = 0.f;
 #pragma unroll
             for (int w2 = 0; w2 < kThreads / 32; ++w2)
-                if ((s_wmask[w2] >> j) & 1ull) v += s_red[w2][j][c];
+                if ((s_wmask[w2] >> j) & 1ull) v += s_red[(w2 * kBatch + j) * 9 + c];
             if (v != 0.f) {
-                const uint32_t gid = s_gid[j];
+                const uint32_t gid = gids[j];
                 if (c >= 5) {
                     float* dst = reinterpret_cast<float*>(&a.d_attr[(size_t)b * a.N + gid]);
                     // attr slots: 0 a, 1 phi0, 2 sigma, 3 L
@@ -490,8 +787,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
                 }
             }
         }
-        bend = bstart;
     }
+    if (*s_err && tid == 0) set_status(a.status, GSPARC_ERR_TIMEOUT);
 }
 
 // Subcarriers per thread: the smallest power of two covering K, at most 32.

@@ -34,7 +34,8 @@ PROJ_STRIDE = 8
 EXPORTS = [
     "gsparc_num_tiles", "gsparc_project", "gsparc_project_bwd", "gsparc_bin_sort_workspace",
     "gsparc_bin_sort", "gsparc_bin_sort_noalloc", "gsparc_attr_mlp", "gsparc_attr_mlp_bwd",
-    "gsparc_attr_mlp_bwd_tc", "gsparc_emission_stride", "gsparc_emission_fwd", "gsparc_emission_bwd", "gsparc_render_fwd", "gsparc_render_fwd_tc", "gsparc_render_bwd",
+    "gsparc_attr_mlp_bwd_tc", "gsparc_emission_stride", "gsparc_emission_fwd", "gsparc_emission_bwd", "gsparc_render_fwd", "gsparc_render_fwd_l2", "gsparc_render_fwd_tc",
+    "gsparc_render_bwd", "gsparc_render_bwd_workspace", "gsparc_render_bwd_balanced",
     "gsparc_render_bwd_tc", "gsparc_render_bwd_tc_workspace", "gsparc_render_bwd_tc_balanced",
     "gsparc_l2_loss", "gsparc_csi_head", "gsparc_csi_loss", "gsparc_csi_head_bwd",
     "gsparc_spectrum_loss_workspace", "gsparc_spectrum_loss",
@@ -109,6 +110,12 @@ def lib():
                                                  vp, vp, vp, vp]),
             "gsparc_render_fwd_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
                                                     vp, vp, vp, vp]),
+            "gsparc_render_fwd_l2": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
+                                                    vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "gsparc_render_bwd_workspace": (ctypes.c_int, [P(View), P(Band), i32, P(ctypes.c_size_t)]),
+            "gsparc_render_bwd_balanced": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp,
+                                                          vp, vp, vp, vp, vp, i32, vp, ctypes.c_size_t, vp,
+                                                          vp, vp, vp]),
             "gsparc_render_bwd": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
                                                  vp, vp, vp, vp, vp]),
             "gsparc_render_bwd_tc": (ctypes.c_int, [P(View), P(Band), i32, i32, vp, vp, vp, vp, vp, vp,
@@ -320,6 +327,37 @@ def gsparc_emission_bwd(tx, rx, means, opacity_logit, weights, hidden, d_attr, d
     rxa = (ctypes.c_float * 3)(*[float(v) for v in rx])
     _call("gsparc_emission_bwd", n, B, int(hidden), _p(tx), rxa, _p(means), _p(opacity_logit), _p(weights),
           1 if inv_d else 0, _p(d_attr), _p(d_means), _p(d_opacity_logit), _p(d_weights), _stream(stream))
+
+
+def gsparc_render_fwd_l2(view, band, B, n, proj, tile_ranges, sorted_ids, attr, target, loss, d_spectrum,
+                         spectrum=None, final_logT=None, n_contrib=None, n_used=None, s_tot=None, tile_walk=None,
+                         stream=None, d_status=None):
+    """FP32 forward with the complex L2 loss fused (dL/dz, loss, optional s_tot and tile walks)."""
+    _call("gsparc_render_fwd_l2", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
+          _p(tile_ranges), _p(sorted_ids), _p(attr), _p(target), _p(loss), _p(d_spectrum), _p(spectrum),
+          _p(final_logT), _p(n_contrib), _p(n_used), _p(s_tot), _p(tile_walk), _p(d_status), _stream(stream))
+
+
+def gsparc_render_bwd_workspace(view, band, B) -> int:
+    out = ctypes.c_size_t(0)
+    _call("gsparc_render_bwd_workspace", ctypes.byref(view), ctypes.byref(band), int(B), ctypes.byref(out))
+    return int(out.value)
+
+
+def fp32_strips(K) -> int:
+    """Strips of the FP32 kernels' s_tot buffer [B, strips, H, W] for K subcarriers."""
+    return 1 if K <= 32 else (K + 31) // 32
+
+
+def gsparc_render_bwd_balanced(view, band, B, n, proj, tile_ranges, sorted_ids, attr, spectrum, s_tot,
+                               final_logT, n_contrib, d_spectrum, ws, d_attr, d_proj, split_min=0,
+                               tile_walk=None, stream=None, d_status=None):
+    """FP32 backward scheduled over the SMs.  ws: a uint8 device tensor of
+    gsparc_render_bwd_workspace() bytes, zeroed once (torch.zeros) before its first use."""
+    _call("gsparc_render_bwd_balanced", ctypes.byref(view), ctypes.byref(band), int(B), int(n), _p(proj),
+          _p(tile_ranges), _p(sorted_ids), _p(attr), _p(spectrum), _p(s_tot), _p(tile_walk), _p(final_logT),
+          _p(n_contrib), _p(d_spectrum), int(split_min), _p(ws), ws.numel() * ws.element_size(), _p(d_attr),
+          _p(d_proj), _p(d_status), _stream(stream))
 
 
 def gsparc_render_bwd_tc_workspace(view, band, B) -> int:

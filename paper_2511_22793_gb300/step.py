@@ -4,8 +4,9 @@
 projection -> bin/sort -> attribute network -> compositing forward -> complex L2 loss ->
 compositing backward -> network backward -> projection backward.  Two arithmetic forms:
 
-  form="fp32": every stage on the CUDA cores in FP32 (gsparc_attr_mlp FP32,
-               gsparc_render_fwd, gsparc_l2_loss, gsparc_render_bwd, gsparc_attr_mlp_bwd);
+  form="fp32": every stage on the CUDA cores in FP32 (gsparc_attr_mlp FP32, the loss fused into
+               gsparc_render_fwd_l2, the scheduled gsparc_render_bwd_balanced fed by its s_tot
+               and tile walks, gsparc_attr_mlp_bwd);
   form="tc":   the subcarrier contractions and the network's products on the tensor cores with
                split-BF16 operands and FP32 accumulation (gsparc_attr_mlp BF16X2, the loss fused
                into gsparc_render_fwd_l2_tc, the scheduled gsparc_render_bwd_tc_balanced fed by
@@ -27,9 +28,7 @@ from . import gsparc as G
 from .pipeline import DeviceMLP, DeviceScene, Renderer
 
 PARAM_NAMES = ("means", "log_scales", "quats", "opacity_logit", "latent", "W1", "b1", "W2", "b2", "W3", "b3")
-STAGES_FP32 = ("project", "bin_sort", "attr_mlp", "render_fwd", "l2_loss", "render_bwd", "attr_mlp_bwd",
-               "project_bwd")
-STAGES_TC = ("project", "bin_sort", "attr_mlp", "render_fwd", "render_bwd", "attr_mlp_bwd", "project_bwd")
+STAGES = ("project", "bin_sort", "attr_mlp", "render_fwd", "render_bwd", "attr_mlp_bwd", "project_bwd")
 
 
 class TrainStep:
@@ -59,16 +58,28 @@ class TrainStep:
         tc = form == "tc"
         self.mlp_tc = tc and mlp.hidden in (16, 32)
         self.mlp_prec = G.GSPARC_BF16X2 if tc else G.GSPARC_FP32
-        self.s_tot = r.s_tot_buffer(B) if tc else None
-        self.walks = r.walk_buffer(B) if tc else None
-        self.bwd_ws = torch.zeros(G.gsparc_render_bwd_tc_workspace(r.view, r.band, B), dtype=torch.uint8,
-                                  device=dev) if tc else None
+        strips = G.s_tot_strips(r.K) if tc else G.fp32_strips(r.K)
+        self.s_tot = torch.empty((B, strips, r.H, r.W), dtype=torch.float32, device=dev)
+        self.walks = r.walk_buffer(B)
+        ws = G.gsparc_render_bwd_tc_workspace(r.view, r.band, B) if tc else \
+            G.gsparc_render_bwd_workspace(r.view, r.band, B)
+        self.bwd_ws = torch.zeros(ws, dtype=torch.uint8, device=dev)
         self.side = torch.cuda.Stream(dev)
-        self.stages = STAGES_TC if tc else STAGES_FP32
-        # kernels of the library launched by one step: project 1, bin/sort 3, network 1,
-        # forward 1 (+ the loss 1 in the FP32 form, fused in the tensor-core forward), backward 1
-        # (+ its schedule 1 in the tensor-core form), network backward 1, projection backward 1
-        self.launches = 1 + 3 + 1 + 1 + (0 if tc else 1) + (2 if tc else 1) + 1 + 1
+        self.stages = STAGES
+        # kernels of the library launched by one step: project 1, bin/sort 3, network 1, forward
+        # with the loss fused 1, backward 2 (its schedule and the scheduled walks), network
+        # backward 1, projection backward 1
+        self.launches = 1 + 3 + 1 + 1 + 2 + 1 + 1
+
+    def spectrum(self, out=None):
+        """The step's spectrum [B,K,H,W,2] (the step itself stores only dL/dz): the same forward
+        kernel once more with the spectrum stored, on the current stream."""
+        r, B = self.r, self.B
+        z = out if out is not None else self.spec
+        fn = G.gsparc_render_fwd_l2_tc if self.form == "tc" else G.gsparc_render_fwd_l2
+        fn(r.view, r.band, B, r.n, r.proj, r.tile_ranges, r.sorted_ids, self.attr, self.target, self.loss,
+           self.d_spec, z, self.logT, self.nc, d_status=r.status)
+        return z
 
     def gradients(self):
         """Name -> gradient view (the flat buffer's views, valid after a step)."""
@@ -100,8 +111,10 @@ class TrainStep:
                                       self.target, self.loss, self.d_spec, None, self.logT, self.nc, self.n_used,
                                       s_tot=self.s_tot, tile_walk=self.walks, d_status=r.status)
         else:
-            G.gsparc_render_fwd(r.view, r.band, B, r.n, r.proj, r.tile_ranges, r.sorted_ids, self.attr, self.spec,
-                                self.logT, self.nc, self.n_used, d_status=r.status)
+            # dL/dz and the loss, no spectrum (training needs only the gradient)
+            G.gsparc_render_fwd_l2(r.view, r.band, B, r.n, r.proj, r.tile_ranges, r.sorted_ids, self.attr,
+                                   self.target, self.loss, self.d_spec, None, self.logT, self.nc, self.n_used,
+                                   s_tot=self.s_tot, tile_walk=self.walks, d_status=r.status)
 
     def _render_bwd(self):
         r, B = self.r, self.B
@@ -110,8 +123,9 @@ class TrainStep:
                                             None, self.s_tot, self.logT, self.nc, self.d_spec, self.bwd_ws,
                                             self.d_attr, self.d_proj, tile_walk=self.walks, d_status=r.status)
         else:
-            G.gsparc_render_bwd(r.view, r.band, B, r.n, r.proj, r.tile_ranges, r.sorted_ids, self.attr, self.logT,
-                                self.nc, self.d_spec, self.d_attr, self.d_proj, d_status=r.status)
+            G.gsparc_render_bwd_balanced(r.view, r.band, B, r.n, r.proj, r.tile_ranges, r.sorted_ids, self.attr,
+                                         None, self.s_tot, self.logT, self.nc, self.d_spec, self.bwd_ws,
+                                         self.d_attr, self.d_proj, tile_walk=self.walks, d_status=r.status)
 
     def enqueue(self, concurrent=False, events=None):
         """Enqueue one step on the current stream.  events: optional dict stage -> (start, end)
@@ -146,8 +160,6 @@ class TrainStep:
         else:
             stage("attr_mlp", self._mlp_fwd)
         stage("render_fwd", self._render_fwd)
-        if self.form == "fp32":
-            stage("l2_loss", lambda: G.gsparc_l2_loss(self.spec, self.target, self.loss, self.d_spec))
         stage("render_bwd", self._render_bwd)
         if concurrent:
             fork2 = torch.cuda.Event()
@@ -200,12 +212,9 @@ class TrainStep:
                                 self.logT, self.nc, self.n_used, d_status=r.status)
         cur.wait_event(tgt_in)
         G.gsparc_l2_loss(self.spec, self.target, self.loss, self.d_spec)
-        if self.form == "tc":
-            G.gsparc_render_bwd_tc_balanced(r.view, r.band, B, r.n, r.proj, r.tile_ranges, r.sorted_ids, self.attr,
-                                            self.spec, None, self.logT, self.nc, self.d_spec, self.bwd_ws,
-                                            self.d_attr, self.d_proj, d_status=r.status)
-        else:
-            self._render_bwd()
+        fn = G.gsparc_render_bwd_tc_balanced if self.form == "tc" else G.gsparc_render_bwd_balanced
+        fn(r.view, r.band, B, r.n, r.proj, r.tile_ranges, r.sorted_ids, self.attr, self.spec, None, self.logT,
+           self.nc, self.d_spec, self.bwd_ws, self.d_attr, self.d_proj, d_status=r.status)
         fork2 = torch.cuda.Event()
         fork2.record(cur)
         self.side.wait_event(fork2)

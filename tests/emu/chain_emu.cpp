@@ -27,13 +27,13 @@ static std::vector<T> rd(FILE* f, size_t n) {
 
 template <int S>
 static void render_fwd(const gsparc::RenderArgs& a, int T) {
-    emu_launch(emu_dim3{(unsigned)((a.K + S - 1) / S), (unsigned)T, (unsigned)a.B}, gsparc::kThreads,
-               gsparc::k_render_fwd<S>, a);
+    emu_launch_smem(emu_dim3{(unsigned)((a.K + S - 1) / S), (unsigned)T, (unsigned)a.B}, gsparc::kThreads,
+                    gsparc::F32Smem<S>::kTotal, gsparc::k_render_fwd<S>, a);
 }
 template <int S>
 static void render_bwd(const gsparc::RenderArgs& a, int T) {
-    emu_launch(emu_dim3{(unsigned)((a.K + S - 1) / S), (unsigned)T, (unsigned)a.B}, gsparc::kThreads,
-               gsparc::k_render_bwd<S>, a);
+    emu_launch_smem(emu_dim3{(unsigned)((a.K + S - 1) / S), (unsigned)T, (unsigned)a.B}, gsparc::kThreads,
+                    gsparc::F32Smem<S>::kTotal, gsparc::k_render_bwd<S>, a);
 }
 template <int HD>
 static void mlp(int n, int B, const float* tx, const float* means, const float* ologit, const float* latent,

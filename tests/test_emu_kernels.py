@@ -770,3 +770,109 @@ def test_reverse_thread_order(emu_bin, tmp_path, monkeypatch, name, args):
     stale value in one of the two orders."""
     monkeypatch.setitem(SAN_ENV, "EMU_ORDER", "reverse")
     globals()[name](emu_bin, tmp_path, *args)
+
+
+@pytest.mark.parametrize("n,H,W,K,B,seed", [(200, 45, 180, 8, 2, 141), (200, 45, 180, 37, 1, 142),
+                                             (200, 45, 180, 100, 1, 144)])
+def test_render_fp32_fused_loss_and_scheduled_backward(emu_bin, tmp_path, n, H, W, K, B, seed):
+    """The FP32 training-step compositing under the host shim with the launch shapes of
+    gsparc_render_fwd_l2 and gsparc_render_bwd_balanced: the forward with the complex L2 loss
+    fused (loss and dL/dz against their definitions on the oracle's spectrum, s_tot against its
+    definition on the kernel's own dL/dz and the oracle's spectrum, tile walks exactly), the
+    schedule with every walk longer than one 16-entry batch split in two (items checked against
+    the rule: each walk once, as one chunk or as [0, m) front + [m, walk) back, m = 16 floor(nb /
+    2)), and the backward over those items against the oracle's analytic gradient for the same
+    dL/dz (1e-3 relative L2 per component, the GPU tests' bar)."""
+    from oracle import binsort as obs
+    from oracle import render as orender
+    from paper_2511_22793_gb300 import synth
+    from gpu_util_host import oracle_inputs_fp32
+
+    exe = emu_bin("render_sched_emu")
+    view, band = synth.View(H=H, W=W), synth.Band(K=K)
+    g32, at32, proj, attr = oracle_inputs_fp32(n, view, B, seed)
+    _, ids, ranges = obs.bin_sort(proj, H, W)
+    rng = np.random.default_rng(seed + 5)
+    P = H * W
+    zo = [orender.render_fwd(g32, at32[b], H, W, K, band.f_c, band.df)[0] for b in range(B)]
+    scale = max(np.sqrt(np.mean(np.abs(z) ** 2)) for z in zo)
+    tgt = [z + 0.3 * scale * (rng.normal(size=z.shape) + 1j * rng.normal(size=z.shape)) for z in zo]
+    tgt_dev = np.stack([np.stack([t.real, t.imag], -1).reshape(H, W, K, 2).transpose(2, 0, 1, 3) for t in tgt])
+    payload = np.array([H, W, K, n, B, len(ids), 1], np.int32).tobytes() + np.array([band.f_c, band.df]).tobytes() + \
+        proj.tobytes() + ranges.astype(np.uint32).tobytes() + ids.astype(np.uint32).tobytes() + attr.tobytes() + \
+        np.ascontiguousarray(tgt_dev.astype(np.float32)).tobytes()
+    raw = _run(exe, tmp_path, payload, timeout=300)
+    assert int(np.frombuffer(raw[-4:], np.int32)[0]) == 0
+    S = 1
+    while S < K and S < 32:
+        S <<= 1
+    strips = (K + S - 1) // S
+    T = ((W + 15) // 16) * ((H + 15) // 16)
+    off = 0
+
+    def take(dtype, count):
+        nonlocal off
+        a = np.frombuffer(raw, dtype=dtype, count=count, offset=off)
+        off += np.dtype(dtype).itemsize * count
+        return a
+
+    loss = float(take(np.float32, 1)[0])
+    ds = take(np.float32, 2 * B * K * P).reshape(B, K, H, W, 2).astype(np.float64)
+    stot = take(np.float32, B * strips * P).reshape(B, strips, P).astype(np.float64)
+    take(np.float32, B * P)
+    nc = take(np.uint32, B * P).reshape(B, P)
+    walks = take(np.uint32, B * T).reshape(B, T)
+    n_items = int(take(np.uint32, 1)[0])
+    items = take(np.uint32, 4 * n_items).reshape(n_items, 4)
+    dattr = take(np.float32, 4 * B * n).reshape(B, n, 4).astype(np.float64)
+    dproj = take(np.float32, 8 * n).reshape(n, 8).astype(np.float64)
+    count = B * K * P
+    t32 = [(tgt_dev[b].astype(np.float32).astype(np.float64)) for b in range(B)]
+    t32 = [(t[..., 0] + 1j * t[..., 1]).transpose(1, 2, 0).reshape(P, K) for t in t32]
+    ref_loss = sum(float(np.sum(np.abs(zo[b] - t32[b]) ** 2)) for b in range(B)) / count
+    assert abs(loss - ref_loss) <= 1e-5 * ref_loss
+    gz = (ds[..., 0] + 1j * ds[..., 1]).transpose(0, 2, 3, 1).reshape(B, P, K)
+    for b in range(B):
+        want = 2.0 * (zo[b] - t32[b]) / count
+        assert np.linalg.norm(gz[b] - want) <= 1e-5 * np.linalg.norm(want)
+        for s in range(strips):
+            ks = slice(s * S, min(K, (s + 1) * S))
+            st = np.sum(gz[b][:, ks].real * zo[b][:, ks].real + gz[b][:, ks].imag * zo[b][:, ks].imag, axis=1)
+            assert np.linalg.norm(stot[b, s] - st) <= 1e-4 * np.linalg.norm(st), (b, s)
+    TW = (W + 15) // 16
+    rg = ranges.reshape(T, 2)
+    for b in range(B):
+        for t in range(T):
+            ty, tx = divmod(t, TW)
+            ys = np.arange(ty * 16, min(H, ty * 16 + 16))
+            xs = np.arange(tx * 16, min(W, tx * 16 + 16))
+            m = int(nc[b].reshape(H, W)[np.ix_(ys, xs)].max())
+            assert walks[b, t] == min(m, int(rg[t, 1] - rg[t, 0]))
+    # the items: every (transmitter, tile, strip) walk once, split by the rule
+    seen = {}
+    for it in items:
+        bt, sv, lo, end = (int(v) for v in it)
+        seen.setdefault((bt, sv & 0x7fffffff), []).append((bool(sv >> 31), lo, end))
+    n_front = 0
+    for b in range(B):
+        for t in range(T):
+            w = int(walks[b, t])
+            for s in range(strips):
+                ch = sorted(seen.get((b * T + t, s), []), key=lambda c: c[1])
+                nb = (w + 15) // 16
+                if w == 0:
+                    assert ch == []
+                elif nb > 1:
+                    m = 16 * (nb // 2)
+                    assert ch == [(True, 0, m), (False, m, w)], (b, t, s, ch)
+                    n_front += 1
+                else:
+                    assert ch == [(False, 0, w)], (b, t, s, ch)
+    assert n_front > 0
+    refs = [orender.render_bwd(g32, at32[b], H, W, K, band.f_c, band.df, gz[b]) for b in range(B)]
+    ref_p = sum(refs)
+    for c, col in enumerate((0, 1, 4, 5, 6)):
+        assert np.linalg.norm(dproj[:, col] - ref_p[:, c]) <= 1e-3 * np.linalg.norm(ref_p[:, c]), c
+    for b in range(B):
+        for c, col in ((5, 2), (6, 0), (7, 1), (8, 3)):
+            assert np.linalg.norm(dattr[b, :, col] - refs[b][:, c]) <= 1e-3 * np.linalg.norm(refs[b][:, c]), (b, c)

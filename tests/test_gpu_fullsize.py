@@ -49,12 +49,7 @@ def _c2(form):
     torch.cuda.synchronize()
     assert r.check() == 0
     # the step's own spectrum: the same forward kernel, spectrum stored
-    z = torch.empty_like(st.spec)
-    if form == "tc":
-        G.gsparc_render_fwd_l2_tc(r.view, r.band, 1, N, r.proj, r.tile_ranges, r.sorted_ids, st.attr, target,
-                                  st.loss, st.d_spec, z, st.logT, st.nc)
-    else:
-        G.gsparc_render_fwd(r.view, r.band, 1, N, r.proj, r.tile_ranges, r.sorted_ids, st.attr, z, st.logT, st.nc)
+    z = st.spectrum(torch.empty_like(st.spec))
     torch.cuda.synchronize()
     zc = spectrum_to_complex(z)[0]                                 # [HW, K]
     rng = np.random.default_rng(512)
@@ -144,6 +139,7 @@ def test_c2_finite_differences_through_gpu_loss():
 
     def loss_at():
         graph.replay()
+        st.spectrum()
         torch.cuda.synchronize()
         zz = spectrum_to_complex(st.spec)[0][pix]
         nu = st.n_used.view(-1)[torch.as_tensor(pix, device=DEV)].cpu().numpy()
