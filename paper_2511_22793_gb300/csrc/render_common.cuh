@@ -484,32 +484,54 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_fwd(RenderArgs a) {
             pf_id = load_id(i + 2);
         }
         const StageRec* rec = s_rec + buf * kBatch;
-        uint64_t mask = warp_entry_mask_rec(rec, nb, wcx, wcy, a.W);
-        if (!done) {
-            while (mask) {
-                const int j = __ffsll((long long)mask) - 1;
-                mask &= mask - 1;
-                const StageRec& r = rec[j];
-                float dx, dy, G, alpha;
-                bool clamped;
-                if (!eval_alpha(ux, uy, a.W, make_float4(r.p0.x, r.p0.y, r.p1.x, r.p1.y),
-                                make_float2(r.p1.z, r.at.z), dx, dy, G, alpha, clamped))
-                    continue;
-                const float nl = lg2(__fsub_rn(1.0f, alpha));
-                if (__fadd_rn(logT, nl) < kLog2TMin) {
-                    done = true;
-                    break;
-                }
-                const float wa = ex2(logT) * alpha * r.at.x;
+        const uint64_t mask = warp_entry_mask_rec(rec, nb, wcx, wcy, a.W);
+        if (__any_sync(0xffffffffu, !done)) {
+            // groups of 8 entries: alpha and log2(1 - alpha) of the group branch-free, so that the
+            // eight evaluations overlap (eval_alpha's operations in its order: the backward re-takes
+            // the same decisions; a skipped entry gets al = -1), then the transmittance recursion
+            // and the accumulation in list order.  A group that misses the warp's rows is skipped.
+#pragma unroll 1
+            for (int g0 = 0; g0 < kBatch; g0 += 8) {
+                if (((mask >> g0) & 0xffull) == 0ull) continue;   // warp-uniform
+                float al[8], nlv[8];
 #pragma unroll
-                for (int kk = 0; kk < S; ++kk) {
-                    const float2 t = s_tab[buf][j][kk];
-                    acc[kk].x = fmaf(wa, t.x, acc[kk].x);
-                    acc[kk].y = fmaf(wa, t.y, acc[kk].y);
+                for (int q = 0; q < 8; ++q) {
+                    const int j = g0 + q;
+                    const StageRec& r = rec[j];
+                    float dx = __fsub_rn(ux, r.p0.x);
+                    const float hw = 0.5f * (float)a.W;
+                    dx = dx >= hw ? __fsub_rn(dx, (float)a.W) : (dx < -hw ? __fadd_rn(dx, (float)a.W) : dx);
+                    const float dy = __fsub_rn(uy, r.p0.y);
+                    float qf = __fmul_rn(__fmul_rn(r.p1.z, dy), dy);
+                    qf = __fmaf_rn(__fmul_rn(__fmul_rn(2.0f, r.p1.y), dx), dy, qf);
+                    qf = __fmaf_rn(__fmul_rn(r.p1.x, dx), dx, qf);
+                    const float G = ex2(__fmul_rn(-0.5f * kLog2e, qf));
+                    const float a0 = __fmul_rn(r.at.z, G);
+                    const float alpha = a0 > kAlphaMax ? kAlphaMax : a0;
+                    const bool ok = ((mask >> j) & 1ull) && qf <= kQMax && alpha >= kAlphaMin;
+                    al[q] = ok ? alpha : -1.f;
+                    nlv[q] = ok ? lg2(__fsub_rn(1.0f, alpha)) : 0.f;
                 }
-                logT = __fadd_rn(logT, nl);
-                last = bs + (uint32_t)j + 1u;
-                ++used;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int j = g0 + q;
+                    const float nt = __fadd_rn(logT, nlv[q]);
+                    const bool cand = !done && al[q] >= 0.f;
+                    const bool term = cand && nt < kLog2TMin;
+                    done = done || term;
+                    const bool take = cand && !term;
+                    if (!__any_sync(0xffffffffu, take)) continue;
+                    const float wa = take ? ex2(logT) * al[q] * rec[j].at.x : 0.f;
+#pragma unroll
+                    for (int kk = 0; kk < S; ++kk) {
+                        const float2 t = s_tab[buf][j][kk];
+                        acc[kk].x = fmaf(wa, t.x, acc[kk].x);
+                        acc[kk].y = fmaf(wa, t.y, acc[kk].y);
+                    }
+                    logT = take ? nt : logT;
+                    last = take ? bs + (uint32_t)j + 1u : last;
+                    used += take ? 1u : 0u;
+                }
             }
         }
     }
@@ -720,15 +742,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
                 if (lane < 9) s_red[(warp * kBatch + j) * 9 + lane] = 0.f;
                 continue;
             }
-            float reG = 0.f, imG = 0.f, imF = 0.f;
+            // Re as two independent FMA chains (the real and the imaginary products), so that no
+            // sum is a chain of two dependent FMAs per subcarrier
+            float reA = 0.f, reB = 0.f, imG = 0.f, imF = 0.f;
 #pragma unroll
             for (int kk = 0; kk < S; ++kk) {
                 const float2 t = s_tab[buf][j][kk];
-                reG = fmaf(g[kk].x, t.x, fmaf(g[kk].y, t.y, reG));
+                reA = fmaf(g[kk].x, t.x, reA);
+                reB = fmaf(g[kk].y, t.y, reB);
                 const float pi_ = fmaf(g[kk].x, t.y, -g[kk].y * t.x);
                 imG += pi_;
                 imF = fmaf((float)kk, pi_, imF);
             }
+            const float reG = reA + reB;
             float gr[9];
 #pragma unroll
             for (int c = 0; c < 9; ++c) gr[c] = 0.f;
