@@ -445,6 +445,7 @@ def run_ours(args, rank, world, local_rank):
             out["c3_batched"] = run_batched(args, dev, emit=False)
             out["c4_train"] = run_train(args, dev, emit=False)
             out["c5_serve"] = run_serve(args, dev, emit=False, loads=(0.25, 0.5, 0.75, 0.9))
+            out["c5_binsort"] = run_binsort_scale(args, dev, emit=False)
     return out, spectra, sc, mlp, tx
 
 
@@ -910,11 +911,14 @@ def run_batched(args, dev=None, emit=True):
 
 def run_train(args, dev=None, emit=True):
     """Training loop: 100,000 Gaussians fitted to spectra of a 20,000-Gaussian ground-truth scene
-    at 2,000 training transmitters (uniform in the cube), 128 subcarriers, 360x90, hidden 32,
-    split-BF16 tensor-core network with FP32 master weights, Adam, recompute in the backward.
-    steps/s over the timed steps; held-out relative error on 200 other transmitters against the
-    ground truth rendered by the FP32 path (whole images) and, in the oracle leg, against the
-    FP64 oracle's render of the ground truth on 64 seeded pixels, before and after."""
+    at 2,000 training transmitters (uniform in the cube, their targets resident in HBM), 128
+    subcarriers, 360x90, hidden 32, split-BF16 tensor-core network with FP32 master weights, Adam,
+    recompute in the backward, the paper's loss for spectrum targets (Eq. 4: L1 + SSIM on
+    magnitudes).  steps/s over the timed steps; held-out relative error (of |z|, and of z) on 200
+    other transmitters against the ground truth rendered by the FP32 path (whole images) and, in
+    the oracle leg, against the FP64 oracle's render of the ground truth on 64 seeded pixels,
+    before and after.  A second run adds Algorithm 1's densification (every 100 steps) and the
+    Eq. 5 confidence objective."""
     import torch
 
     from paper_2511_22793_gb300 import synth
@@ -929,11 +933,13 @@ def run_train(args, dev=None, emit=True):
     train_tx = synth.make_tx(2000, seed=2)
     held = synth.make_tx(200, seed=8)
     steps = args.c4_steps
-    tr = Trainer(100_000, gt, gt_mlp, train_tx, H=H, W=W, K=K, hidden=32, batch=4,
-                 total_steps=steps + args.warmup, device=dev)
     pix = _pix_sample(H, W, 64, seed=31)
 
-    def predict_at():
+    def make(**kw):
+        return Trainer(100_000, gt, gt_mlp, train_tx, H=H, W=W, K=K, hidden=32, batch=4,
+                       total_steps=steps + args.warmup, device=dev, loss="l1ssim", **kw)
+
+    def predict_at(tr):
         txs = torch.tensor(np.asarray(held, dtype=np.float32), device=dev)
         out = []
         for s in range(0, txs.shape[0], tr.batch):
@@ -942,27 +948,41 @@ def run_train(args, dev=None, emit=True):
                 out.append(_spec_at(spec[b], pix, W))
         return np.stack(out)
 
-    e0 = tr.evaluate(held)
-    p0 = predict_at()
-    for _ in range(args.warmup):
-        tr.step()
-    torch.cuda.synchronize(dev)
-    trace = []
-    t_train = 0.0
-    done = 0
-    chunk = max(1, steps // 4)
-    while done < steps:
-        m = min(chunk, steps - done)
-        t0 = time.perf_counter()
-        for _ in range(m):
-            loss = tr.step()
+    def timed_run(tr, n_steps, checkpoints):
+        trace, t_train, done = [], 0.0, 0
+        for _ in range(args.warmup):
+            tr.step()
         torch.cuda.synchronize(dev)
-        t_train += time.perf_counter() - t0
-        done += m
-        trace.append({"step": done + args.warmup, "loss": float(loss), "heldout_rel_error": tr.evaluate(held)})
-    if tr.r.check() != 0:
-        raise RuntimeError("training status")
-    p1 = predict_at()
+        chunk = max(1, n_steps // checkpoints)
+        while done < n_steps:
+            m = min(chunk, n_steps - done)
+            t0 = time.perf_counter()
+            for _ in range(m):
+                loss = tr.step()
+            torch.cuda.synchronize(dev)
+            t_train += time.perf_counter() - t0
+            done += m
+            trace.append({"step": done + args.warmup, "loss": float(loss), "gaussians": tr.n,
+                          "heldout_rel_error_magnitude": tr.evaluate(held, magnitude=True)})
+        if tr.r.check() != 0:
+            raise RuntimeError("training status")
+        return n_steps / t_train, trace
+
+    tr = make()
+    e0 = {"magnitude": tr.evaluate(held, magnitude=True), "complex": tr.evaluate(held)}
+    p0 = predict_at(tr)
+    rate, trace = timed_run(tr, steps, 5)
+    e1 = {"magnitude": trace[-1]["heldout_rel_error_magnitude"], "complex": tr.evaluate(held)}
+    p1 = predict_at(tr)
+    del tr
+    torch.cuda.empty_cache()
+    # the same loop with densification and the confidence objective
+    ex_steps = max(200, steps // 3)
+    tr = make(densify_every=100, confidence=True)
+    x0 = tr.evaluate(held, magnitude=True)
+    ex_rate, ex_trace = timed_run(tr, ex_steps, 2)
+    del tr
+    torch.cuda.empty_cache()
     # the oracle leg: ground-truth spectra of the held-out transmitters on 64 seeded pixels
     from oracle import pipeline as opl
 
@@ -971,25 +991,95 @@ def run_train(args, dev=None, emit=True):
     oracle_s = time.perf_counter() - t0
     z_or = ref["z"]
     oracle_units = int(ref["n_used"].sum()) * K
-    err = lambda p: float(np.linalg.norm(p - z_or) / np.linalg.norm(z_or))
-    out = {"metric": "training steps/s", "value": steps / t_train, "unit": "steps/s", "n_gpus": 1,
+    err_c = lambda p: float(np.linalg.norm(p - z_or) / np.linalg.norm(z_or))
+    err_m = lambda p: float(np.linalg.norm(np.abs(p) - np.abs(z_or)) / np.linalg.norm(np.abs(z_or)))
+    out = {"metric": "training steps/s", "value": rate, "unit": "steps/s", "n_gpus": 1,
            "higher_is_better": True, "steps": steps, "warmup": args.warmup,
            "config": {"workload": "training: 100k Gaussians fit to a 20k-Gaussian scene, 2000 training "
                                   "transmitters, batch 4, 128 subcarriers, 360x90, hidden 32",
                       "network": "split-BF16 tensor cores forward and backward, FP32 master weights",
-                      "compositing": "tensor cores forward (loss fused) and scheduled backward",
+                      "compositing": "tensor cores forward and scheduled backward",
+                      "loss": "Eq. 4, L1 + SSIM on magnitude spectra (lambda_1 = 0.2)",
                       "init": "geometry-agnostic (uniform centres, isotropic 0.2 m, opacity 0.1)",
-                      "training_targets": "ground truth rendered by the FP32 path per sampled batch"},
-           "heldout_rel_error": {"before": e0, "after": trace[-1]["heldout_rel_error"], "transmitters": 200,
-                                 "pixels": "whole image", "against": "FP32-path render of the ground truth"},
+                      "training_targets": "ground truth rendered by the FP32 path once, resident in HBM "
+                                          "(2000 x 128 x 360 x 90 magnitudes, 33 GB)"},
+           "heldout_rel_error": {"before": e0, "after": e1, "transmitters": 200, "pixels": "whole image",
+                                 "against": "FP32-path render of the ground truth"},
            "trace": trace,
+           "with_densification_and_confidence": {
+               "value": ex_rate, "unit": "steps/s", "steps": ex_steps, "densify_every": 100,
+               "objective": "Eq. 5 over the batch of Eq. 4 losses", "heldout_rel_error_magnitude_before": x0,
+               "trace": ex_trace},
            "cpu_baseline": {"value": oracle_units / oracle_s, "unit": UNIT, "cores": os.cpu_count() or 1,
                             "kind": "oracle",
                             "sample": "ground truth (20k Gaussians) at the 200 held-out transmitters, 64 seeded "
                                       "pixels, forward (projection and network of every Gaussian included)",
                             "seconds": oracle_s,
-                            "heldout_rel_error_vs_oracle": {"before": err(p0), "after": err(p1),
-                                                            "transmitters": 200, "pixels": 64}}}
+                            "heldout_rel_error_vs_oracle": {
+                                "magnitude": {"before": err_m(p0), "after": err_m(p1)},
+                                "complex": {"before": err_c(p0), "after": err_c(p1)},
+                                "transmitters": 200, "pixels": 64}}}
+    if emit:
+        print(json.dumps(out))
+    return out
+
+
+def run_binsort_scale(args, dev=None, emit=True, reps=20):
+    """Projection and tile binning + directional sort at serving scale: the 500,000-Gaussian
+    resident scene at 180x45, 360x90 and 720x180, each pass timed with CUDA events on its stream
+    (L2 flushed before each), achieved bandwidth on the algorithmic bytes: projection 40 B read
+    (mean, log-scales, quaternion) + 32 B written per Gaussian; bin/sort 36 B read per Gaussian
+    (the footprint box twice, the distance once) + 8 B written per pair (the keys), 8 B read + 4 B
+    written per pair (the per-tile sort)."""
+    import torch
+
+    from paper_2511_22793_gb300 import gsparc as G
+    from paper_2511_22793_gb300 import synth
+    from paper_2511_22793_gb300.pipeline import DeviceScene, Renderer
+
+    if dev is None:
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+    n = 500_000
+    ds = DeviceScene.from_host(synth.make_scene(n, seed=0, bf16_latent=True), dev)
+    peak = float(measured_peaks().get("hbm_gbs", 6800.0))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for (H, W) in ((45, 180), (90, 360), (180, 720)):
+        r = Renderer(H, W, 1, n, device=dev)
+        proj_fn = lambda: G.gsparc_project(r.view, ds.means, ds.log_scales, ds.quats, r.proj, d_status=r.status)
+        bin_fn = lambda: G.gsparc_bin_sort(r.view, n, r.proj, r.capacity, r.ws, r.sorted_ids, None, r.tile_ranges,
+                                           r.n_pairs, r.status)
+        for _ in range(3):
+            proj_fn()
+            bin_fn()
+        torch.cuda.synchronize(dev)
+        if r.check() != 0:
+            raise RuntimeError("bin/sort status at %dx%d" % (W, H))
+        pairs = int(r.n_pairs.item())
+        t = {}
+        for name, fn in (("project", proj_fn), ("bin_sort", bin_fn)):
+            ms = []
+            for _ in range(reps):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            t[name] = statistics.median(ms)
+        b_proj = 72 * n
+        b_bin = 36 * n + 20 * pairs
+        rows.append({"resolution": "%dx%d" % (W, H), "pairs": pairs,
+                     "project": {"ms": t["project"], "bytes": b_proj, "gbs": b_proj / (t["project"] * 1e6),
+                                 "frac": b_proj / (t["project"] * 1e6) / peak},
+                     "bin_sort": {"ms": t["bin_sort"], "bytes": b_bin, "gbs": b_bin / (t["bin_sort"] * 1e6),
+                                  "frac": b_bin / (t["bin_sort"] * 1e6) / peak, "launches": 3}})
+        del r
+    out = {"metric": "projection and bin/sort bandwidth", "unit": "GB/s", "n_gaussians": n, "peak_gbs": peak,
+           "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json)", "resolutions": rows}
     if emit:
         print(json.dumps(out))
     return out
@@ -1187,7 +1277,7 @@ def main():
     ap.add_argument("--render", default="fp32", choices=["fp32", "tc"],
                     help="headline arithmetic: FP32 CUDA cores (default) or the tensor-core form")
     ap.add_argument("--workload", default="fwdbwd",
-                    choices=["fwdbwd", "batched", "train", "serve", "csi", "emission", "spectrum_loss",
+                    choices=["fwdbwd", "batched", "train", "serve", "binsort", "csi", "emission", "spectrum_loss",
                              "train_extras"],
                     help="fwdbwd: the default line (headline step and every configuration); batched: "
                          "64-transmitter inference against the plain one-query path; train: the training "
@@ -1206,7 +1296,7 @@ def main():
         if rank == 0:
             run_reference(args)
         return
-    single = {"batched": run_batched, "csi": run_csi, "emission": run_emission,
+    single = {"batched": run_batched, "csi": run_csi, "emission": run_emission, "binsort": run_binsort_scale,
               "spectrum_loss": run_spectrum_loss, "train_extras": run_train_extras, "train": run_train,
               "serve": run_serve}
     if args.workload in single:

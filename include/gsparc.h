@@ -682,6 +682,13 @@ int gsparc_adam_segments(int64_t n, float* param, const float* grad, float* m, f
                          int32_t step, void* stream);
 
 /*
+ * x[r * per + j] *= w[r] for r < rows, j < per (device arrays; w [rows]): each
+ * sample's block of a batched gradient scaled by its weight, e.g. dL_b/dz by
+ * the dObj/dL_b that gsparc_confidence writes (Eq. 5).
+ */
+int gsparc_scale_rows(int32_t rows, int64_t per, const float* w, float* x, void* stream);
+
+/*
  * Polls a pipeline wait of the tensor-core compositing kernels
  * (gsparc_render_fwd_tc, gsparc_render_fwd_l2_tc, gsparc_render_csi_tc,
  * gsparc_render_bwd_tc, gsparc_render_bwd_tc_balanced) makes before it gives up

@@ -486,51 +486,62 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_fwd(RenderArgs a) {
         const StageRec* rec = s_rec + buf * kBatch;
         const uint64_t mask = warp_entry_mask_rec(rec, nb, wcx, wcy, a.W);
         if (__any_sync(0xffffffffu, !done)) {
-            // groups of 8 entries: alpha and log2(1 - alpha) of the group branch-free, so that the
-            // eight evaluations overlap (eval_alpha's operations in its order: the backward re-takes
-            // the same decisions; a skipped entry gets al = -1), then the transmittance recursion
-            // and the accumulation in list order.  A group that misses the warp's rows is skipped.
+            // groups of 8 entries.  alpha and log2(1 - alpha): eval_alpha's operations in its order
+            // (the backward re-takes the same decisions; a skipped entry gets al = -1), branch-free
+            // over the whole group when three or more of its entries reach the warp's rows (the
+            // eight evaluations overlap), entry by entry otherwise.  Then the transmittance
+            // recursion and the accumulation in list order.  A group that misses the warp is skipped.
+            auto alpha_of = [&](int j, float& al, float& nlv) {
+                const StageRec& r = rec[j];
+                float dx = __fsub_rn(ux, r.p0.x);
+                const float hw = 0.5f * (float)a.W;
+                dx = dx >= hw ? __fsub_rn(dx, (float)a.W) : (dx < -hw ? __fadd_rn(dx, (float)a.W) : dx);
+                const float dy = __fsub_rn(uy, r.p0.y);
+                float qf = __fmul_rn(__fmul_rn(r.p1.z, dy), dy);
+                qf = __fmaf_rn(__fmul_rn(__fmul_rn(2.0f, r.p1.y), dx), dy, qf);
+                qf = __fmaf_rn(__fmul_rn(r.p1.x, dx), dx, qf);
+                const float G = ex2(__fmul_rn(-0.5f * kLog2e, qf));
+                const float a0 = __fmul_rn(r.at.z, G);
+                const float alpha = a0 > kAlphaMax ? kAlphaMax : a0;
+                const bool ok = ((mask >> j) & 1ull) && qf <= kQMax && alpha >= kAlphaMin;
+                al = ok ? alpha : -1.f;
+                nlv = ok ? lg2(__fsub_rn(1.0f, alpha)) : 0.f;
+            };
+            auto composite = [&](int j, float al, float nlv) {
+                const float nt = __fadd_rn(logT, nlv);
+                const bool cand = !done && al >= 0.f;
+                const bool term = cand && nt < kLog2TMin;
+                done = done || term;
+                const bool take = cand && !term;
+                if (!__any_sync(0xffffffffu, take)) return;
+                const float wa = take ? ex2(logT) * al * rec[j].at.x : 0.f;
+#pragma unroll
+                for (int kk = 0; kk < S; ++kk) {
+                    const float2 t = s_tab[buf][j][kk];
+                    acc[kk].x = fmaf(wa, t.x, acc[kk].x);
+                    acc[kk].y = fmaf(wa, t.y, acc[kk].y);
+                }
+                logT = take ? nt : logT;
+                last = take ? bs + (uint32_t)j + 1u : last;
+                used += take ? 1u : 0u;
+            };
 #pragma unroll 1
             for (int g0 = 0; g0 < kBatch; g0 += 8) {
-                if (((mask >> g0) & 0xffull) == 0ull) continue;   // warp-uniform
-                float al[8], nlv[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int j = g0 + q;
-                    const StageRec& r = rec[j];
-                    float dx = __fsub_rn(ux, r.p0.x);
-                    const float hw = 0.5f * (float)a.W;
-                    dx = dx >= hw ? __fsub_rn(dx, (float)a.W) : (dx < -hw ? __fadd_rn(dx, (float)a.W) : dx);
-                    const float dy = __fsub_rn(uy, r.p0.y);
-                    float qf = __fmul_rn(__fmul_rn(r.p1.z, dy), dy);
-                    qf = __fmaf_rn(__fmul_rn(__fmul_rn(2.0f, r.p1.y), dx), dy, qf);
-                    qf = __fmaf_rn(__fmul_rn(r.p1.x, dx), dx, qf);
-                    const float G = ex2(__fmul_rn(-0.5f * kLog2e, qf));
-                    const float a0 = __fmul_rn(r.at.z, G);
-                    const float alpha = a0 > kAlphaMax ? kAlphaMax : a0;
-                    const bool ok = ((mask >> j) & 1ull) && qf <= kQMax && alpha >= kAlphaMin;
-                    al[q] = ok ? alpha : -1.f;
-                    nlv[q] = ok ? lg2(__fsub_rn(1.0f, alpha)) : 0.f;
-                }
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int j = g0 + q;
-                    const float nt = __fadd_rn(logT, nlv[q]);
-                    const bool cand = !done && al[q] >= 0.f;
-                    const bool term = cand && nt < kLog2TMin;
-                    done = done || term;
-                    const bool take = cand && !term;
-                    if (!__any_sync(0xffffffffu, take)) continue;
-                    const float wa = take ? ex2(logT) * al[q] * rec[j].at.x : 0.f;
-#pragma unroll
-                    for (int kk = 0; kk < S; ++kk) {
-                        const float2 t = s_tab[buf][j][kk];
-                        acc[kk].x = fmaf(wa, t.x, acc[kk].x);
-                        acc[kk].y = fmaf(wa, t.y, acc[kk].y);
+                const uint32_t gbits = (uint32_t)(mask >> g0) & 0xffu;
+                if (gbits == 0u) continue;   // warp-uniform
+                if (__popc(gbits) <= 2) {
+                    for (uint32_t bits = gbits; bits; bits &= bits - 1u) {
+                        const int j = g0 + __ffs((int)bits) - 1;
+                        float al, nlv;
+                        alpha_of(j, al, nlv);
+                        composite(j, al, nlv);
                     }
-                    logT = take ? nt : logT;
-                    last = take ? bs + (uint32_t)j + 1u : last;
-                    used += take ? 1u : 0u;
+                } else {
+                    float al[8], nlv[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) alpha_of(g0 + q, al[q], nlv[q]);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) composite(g0 + q, al[q], nlv[q]);
                 }
             }
         }

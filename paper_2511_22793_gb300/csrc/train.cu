@@ -59,3 +59,13 @@ extern "C" int gsparc_adam_segments(int64_t n, float* param, const float* grad, 
     k_adam_seg<<<blocks, 256, 0, as_stream(stream)>>>(n, param, grad, m, v, seg, b1, b2, eps, bc1, bc2);
     return launch_status();
 }
+
+extern "C" int gsparc_scale_rows(int32_t rows, int64_t per, const float* w, float* x, void* stream) {
+    if (rows < 0 || per < 0) return GSPARC_ERR_INVALID;
+    if (rows == 0 || per == 0) return GSPARC_OK;
+    if (!w || !x) return GSPARC_ERR_INVALID;
+    const int64_t n = (int64_t)rows * per;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);
+    k_scale_rows<<<blocks, 256, 0, as_stream(stream)>>>(rows, per, w, x);
+    return launch_status();
+}

@@ -51,6 +51,14 @@ __global__ void __launch_bounds__(256) k_adam(int64_t n, float* __restrict__ p, 
     }
 }
 
+// x[r * per + j] *= w[r]: each sample's block of a batched array scaled by its weight.
+__global__ void __launch_bounds__(256) k_scale_rows(int rows, int64_t per, const float* __restrict__ w,
+                                                    float* __restrict__ x) {
+    const int64_t n = (int64_t)rows * per;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) x[j] *= w[j / per];
+}
+
 // Parameter groups of one flat buffer for k_adam_seg: segment s covers [end[s-1], end[s])
 // (end[-1] = 0) and takes learning rate lr[s].
 constexpr int kAdamMaxSeg = 32;

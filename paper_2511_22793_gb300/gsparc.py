@@ -40,7 +40,8 @@ EXPORTS = [
     "gsparc_l2_loss", "gsparc_csi_head", "gsparc_csi_loss", "gsparc_csi_head_bwd",
     "gsparc_spectrum_loss_workspace", "gsparc_spectrum_loss",
     "gsparc_render_csi_tc", "gsparc_render_fwd_l2_tc", "gsparc_confidence", "gsparc_densify_accumulate",
-    "gsparc_densify_workspace", "gsparc_densify", "gsparc_opacity_reset", "gsparc_adam", "gsparc_adam_segments", "gsparc_set_wait_limit",
+    "gsparc_densify_workspace", "gsparc_densify", "gsparc_opacity_reset", "gsparc_adam", "gsparc_adam_segments", "gsparc_scale_rows",
+    "gsparc_set_wait_limit",
     "gsparc_check", "gsparc_strerror",
 ]
 
@@ -144,6 +145,7 @@ def lib():
             "gsparc_adam": (ctypes.c_int, [i64, vp, vp, vp, vp, f32, f32, f32, f32, i32, vp]),
             "gsparc_adam_segments": (ctypes.c_int, [i64, vp, vp, vp, vp, i32, P(i64), P(f32), f32, f32, f32, i32,
                                                     vp]),
+            "gsparc_scale_rows": (ctypes.c_int, [i32, i64, vp, vp, vp]),
             "gsparc_set_wait_limit": (ctypes.c_uint32, [ctypes.c_uint32]),
             "gsparc_check": (ctypes.c_int, [vp, vp]),
             "gsparc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -496,6 +498,12 @@ def gsparc_adam_segments(param, grad, m, v, seg_end, seg_lr, step, b1=0.9, b2=0.
     lrs = (ctypes.c_float * k)(*[float(x) for x in seg_lr])
     _call("gsparc_adam_segments", param.numel(), _p(param), _p(grad), _p(m), _p(v), k, ends, lrs, float(b1),
           float(b2), float(eps), int(step), _stream(stream))
+
+
+def gsparc_scale_rows(x, w, stream=None):
+    """x [rows, ...] scaled in place row by row by w [rows] (device)."""
+    rows = int(x.shape[0])
+    _call("gsparc_scale_rows", rows, x.numel() // max(rows, 1), _p(w), _p(x), _stream(stream))
 
 
 def gsparc_set_wait_limit(polls: int) -> int:

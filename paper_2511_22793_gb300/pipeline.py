@@ -199,22 +199,25 @@ class Renderer:
         return torch.empty((B, self.T), dtype=torch.int32, device=self.device)
 
     def render_backward(self, attr, logT, nc, d_spec, d_attr, d_proj, tensor_cores=False, stream=None,
-                        spectrum=None, s_tot=None, split_min=0, tile_walk=None):
-        """Compositing gradient.  tensor_cores selects the tensor-core form scheduled over the
-        SMs (gsparc_render_bwd_tc_balanced; long walks are split when the spectrum or the fused
-        forward's s_tot is given), else gsparc_render_bwd (same outputs)."""
+                        spectrum=None, s_tot=None, split_min=0, tile_walk=None, ws=None):
+        """Compositing gradient scheduled over the SMs: gsparc_render_bwd_tc_balanced
+        (tensor_cores) or gsparc_render_bwd_balanced (FP32); long walks are split when the
+        spectrum or the fused forward's s_tot is given.  ws: the schedule's workspace (zeroed
+        before first use), allocated here when None."""
         B = int(attr.shape[0])
-        if not tensor_cores:
-            G.gsparc_render_bwd(self.view, self.band, B, self.n, self.proj, self.tile_ranges, self.sorted_ids,
-                                attr, logT, nc, d_spec, d_attr, d_proj, stream, d_status=self.status)
-            return
-        need = G.gsparc_render_bwd_tc_workspace(self.view, self.band, B)
-        if self.bwd_ws is None or self.bwd_ws.numel() < need:
-            self.bwd_ws = torch.zeros(need, dtype=torch.uint8, device=self.device)
-        G.gsparc_render_bwd_tc_balanced(self.view, self.band, B, self.n, self.proj, self.tile_ranges,
-                                        self.sorted_ids, attr, spectrum, s_tot, logT, nc, d_spec, self.bwd_ws,
-                                        d_attr, d_proj, split_min=split_min, tile_walk=tile_walk, stream=stream,
-                                        d_status=self.status)
+        if tensor_cores:
+            need = G.gsparc_render_bwd_tc_workspace(self.view, self.band, B)
+            fn = G.gsparc_render_bwd_tc_balanced
+        else:
+            need = G.gsparc_render_bwd_workspace(self.view, self.band, B)
+            fn = G.gsparc_render_bwd_balanced
+        if ws is None:
+            if self.bwd_ws is None or self.bwd_ws.numel() < need:
+                self.bwd_ws = torch.zeros(need, dtype=torch.uint8, device=self.device)
+            ws = self.bwd_ws
+        fn(self.view, self.band, B, self.n, self.proj, self.tile_ranges, self.sorted_ids, attr, spectrum, s_tot,
+           logT, nc, d_spec, ws, d_attr, d_proj, split_min=split_min, tile_walk=tile_walk, stream=stream,
+           d_status=self.status)
 
     def attributes_backward(self, scene, mlp, tx, d_attr, d_means, d_ologit, d_latent, d_weights,
                             stream=None, tensor_cores=False):

@@ -79,6 +79,7 @@ inline float __int_as_float(int i) {
     return f;
 }
 inline int __ffsll(long long x) { return __builtin_ffsll(x); }
+inline int __ffs(int x) { return __builtin_ffs(x); }
 inline int __clzll(long long x) { return x == 0 ? 64 : __builtin_clzll((unsigned long long)x); }
 inline float __uint2float_rz(unsigned x) {
     float f = (float)x;

@@ -261,7 +261,7 @@ def test_trainer_step_matches_oracle_pipeline_and_adam(tensor_cores):
         torch.cuda.synchronize()
         assert tr.r.check() == 0
         tx = tr.tx.cpu().numpy().astype(np.float64)
-        tgt = spectrum_to_complex(tr.target[0][:tr.batch])
+        tgt = spectrum_to_complex(tr.batch_target)
         sc0 = synth.Scene(*[theta0[k].astype(np.float32) for k in SCENE_KEYS])
         mlp0 = synth.MLPWeights(32, *[theta0[k].astype(np.float32) for k in MLP_KEYS])
         _, g_or = opl.loss_and_grad(sc0, mlp0, view, band, tx, tgt)

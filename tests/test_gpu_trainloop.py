@@ -56,3 +56,54 @@ def test_checkpoint_resume_reproduces_trajectory():
     b = [float(tr.step()) for _ in range(10)]
     # gradient sums use float atomics, so the last bits may differ between runs
     np.testing.assert_allclose(a, b, rtol=1e-4)
+
+
+def test_eq4_loss_fits_heldout_magnitudes():
+    """The paper's loss for spectrum targets (Eq. 4, L1 + SSIM on magnitudes) from the
+    geometry-agnostic initialisation: the magnitude error on unseen transmitters falls."""
+    gt = synth.make_scene(600, seed=31)
+    gt.log_scales = gt.log_scales + np.float32(0.5)
+    gt_mlp = synth.make_mlp(16, seed=32)
+    tr = Trainer(3000, gt, gt_mlp, synth.make_tx(64, seed=33), H=45, W=180, K=8, hidden=16, batch=4,
+                 total_steps=600, seed=34, loss="l1ssim")
+    held = synth.make_tx(16, seed=35)
+    e0 = tr.evaluate(held, magnitude=True)
+    losses = [float(tr.step()) for _ in range(600)]
+    assert np.isfinite(losses).all()
+    e1 = tr.evaluate(held, magnitude=True)
+    assert e1 < 0.85 * e0, (e0, e1)
+
+
+@pytest.mark.parametrize("tensor_cores", [False, True])
+def test_densification_and_confidence_in_the_loop(tensor_cores):
+    """Algorithm 1's densification branch and the Eq. 5 objective wired into the step: after a
+    densification every row's Adam moments are its parent row's (gathered through the kernel's
+    payload) and the Gaussian count changes; training goes on over the new set (and densifies on
+    its schedule inside step()), the objective stays finite and the confidence network's weights
+    move."""
+    from paper_2511_22793_gb300 import gsparc as G
+
+    gt = synth.make_scene(600, seed=31)
+    gt.log_scales = gt.log_scales + np.float32(0.5)
+    gt_mlp = synth.make_mlp(16, seed=32)
+    tr = Trainer(2000, gt, gt_mlp, synth.make_tx(64, seed=33), H=45, W=180, K=8, hidden=16, batch=4,
+                 total_steps=200, seed=34, loss="l1ssim", confidence=True, densify_every=40, densify_until=200,
+                 opacity_reset_every=60, tensor_cores=tensor_cores, densify_params=G.densify_params(tau_grad=1e-7))
+    w0 = tr.params["conf"].clone()
+    for _ in range(30):
+        assert np.isfinite(float(tr.step()))
+    n0 = tr.n
+    m_before = {k: tr.m[k].clone() for k in ("means", "log_scales", "latent")}
+    v_before = {k: tr.v[k].clone() for k in ("means", "log_scales", "latent")}
+    lat_before = tr.params["latent"].clone()
+    tr.densify()
+    par = tr.last_parent.long()
+    assert tr.n != n0 and par.numel() == tr.n
+    for k in m_before:
+        assert torch.equal(tr.m[k], m_before[k][par]), k
+        assert torch.equal(tr.v[k], v_before[k][par]), k
+    assert torch.equal(tr.params["latent"], lat_before[par])
+    for _ in range(50):           # steps 31..80: one densification (step 40) and one reset (step 60)
+        assert np.isfinite(float(tr.step()))
+    assert not torch.equal(tr.params["conf"], w0)
+    assert tr.r.check() == 0
