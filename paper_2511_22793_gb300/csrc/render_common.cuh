@@ -49,10 +49,21 @@ __device__ __forceinline__ float lg2(float x) {
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// Two FP32 FMAs in one instruction (fma.rn.f32x2): d.x = fma(a.x, b.x, c.x), d.y = fma(a.y, b.y,
+// c.y), each an IEEE single-precision fused multiply-add, as fmaf.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
 #else
 // the test suite's host shim: the library's exact counterparts of the SFU approximations
 inline float ex2(float x) { return exp2f(x); }
 inline float lg2(float x) { return log2f(x); }
+inline float2 fma2(float2 a, float2 b, float2 c) { return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y)); }
 #endif
 
 struct RenderArgs {
@@ -515,12 +526,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_fwd(RenderArgs a) {
                 const bool take = cand && !term;
                 if (!__any_sync(0xffffffffu, take)) return;
                 const float wa = take ? ex2(logT) * al * rec[j].at.x : 0.f;
+                const float2 w2 = make_float2(wa, wa);
 #pragma unroll
-                for (int kk = 0; kk < S; ++kk) {
-                    const float2 t = s_tab[buf][j][kk];
-                    acc[kk].x = fmaf(wa, t.x, acc[kk].x);
-                    acc[kk].y = fmaf(wa, t.y, acc[kk].y);
-                }
+                for (int kk = 0; kk < S; ++kk) acc[kk] = fma2(w2, s_tab[buf][j][kk], acc[kk]);
                 logT = take ? nt : logT;
                 last = take ? bs + (uint32_t)j + 1u : last;
                 used += take ? 1u : 0u;
@@ -755,17 +763,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
             }
             // Re as two independent FMA chains (the real and the imaginary products), so that no
             // sum is a chain of two dependent FMAs per subcarrier
-            float reA = 0.f, reB = 0.f, imG = 0.f, imF = 0.f;
+            // (the two Re chains and the Im, kk-weighted Im pair each as one paired FMA)
+            float2 re2 = make_float2(0.f, 0.f), im2 = make_float2(0.f, 0.f);   // (Re a, Re b), (Im G, Im F)
 #pragma unroll
             for (int kk = 0; kk < S; ++kk) {
                 const float2 t = s_tab[buf][j][kk];
-                reA = fmaf(g[kk].x, t.x, reA);
-                reB = fmaf(g[kk].y, t.y, reB);
+                re2 = fma2(g[kk], t, re2);
                 const float pi_ = fmaf(g[kk].x, t.y, -g[kk].y * t.x);
-                imG += pi_;
-                imF = fmaf((float)kk, pi_, imF);
+                im2 = fma2(make_float2(pi_, pi_), make_float2(1.0f, (float)kk), im2);
             }
-            const float reG = reA + reB;
+            const float reG = re2.x + re2.y, imG = im2.x, imF = im2.y;
             float gr[9];
 #pragma unroll
             for (int c = 0; c < 9; ++c) gr[c] = 0.f;
