@@ -15,10 +15,11 @@
 //   k_tile_emit   every pair, as the 64-bit sort key (bits(r) << 32) | index,
 //                 into its tile's bucket (block-aggregated cursor atomics, so
 //                 the order inside a bucket is arbitrary)
-//   k_tile_sort   one CTA per tile: up to kSortCap keys in shared memory, a
-//                 distribution sort over kSubBuckets depth sub-buckets (each
-//                 key ranked against the few keys of its sub-bucket); above
-//                 that, or when a sub-bucket holds more than kSubMax keys, an
+//   k_tile_sort   one CTA per tile: a distribution sort by depth (each key ranked
+//                 against the few keys of its sub-bucket), up to kSortCap keys in
+//                 shared memory over kSubBuckets sub-buckets, above that over
+//                 kSubBig sub-buckets with the keys scattered in global memory;
+//                 when a sub-bucket holds too many keys (many equal depths), an
 //                 LSD radix sort (8-bit digits, warp-match ranking, only the
 //                 bytes that vary in the bucket), in a global ping-pong buffer
 //                 for a bucket above kSortCap keys; writes the ids (and keys)
@@ -45,6 +46,8 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortCap = 24576;                     // keys per bucket sorted in shared memory
 constexpr int kSubBuckets = 4096;                   // sub-buckets of the in-tile distribution sort
 constexpr int kSubMax = 64;                         // largest sub-bucket ranked by comparison
+constexpr int kSubBig = 16384;                      // sub-buckets of a bucket above kSortCap keys
+constexpr int kSubMaxBig = 256;                     // largest such sub-bucket ranked by comparison
 static_assert(kSortThreads >= 256, "the digit scan gives one thread per digit");
 static_assert(kSortWarps * 256 == kSubBuckets, "histogram array shared by both in-tile sorts");
 
@@ -383,12 +386,89 @@ __device__ __forceinline__ uint64_t* sort_bucket(uint64_t* a, uint64_t* b, int n
 }
 
 // Sub-bucket of a key in the tile's distribution sort: the depth bits' offset from the
-// tile's minimum, scaled to [0, kSubBuckets).  Every step (offset, round-toward-zero
-// conversion, multiplication, truncation, clamp) is monotone non-decreasing, so a key
-// never lands in an earlier sub-bucket than a smaller key.
-__device__ __forceinline__ int sub_bucket(uint64_t k, uint32_t dmin, float scale) {
+// tile's minimum, scaled to [0, nsub).  Every step (offset, round-toward-zero conversion,
+// multiplication, truncation, clamp) is monotone non-decreasing, so a key never lands in an
+// earlier sub-bucket than a smaller key.
+__device__ __forceinline__ int sub_bucket(uint64_t k, uint32_t dmin, float scale, int nsub = kSubBuckets) {
     const uint32_t x = (uint32_t)(k >> 32) - dmin;
-    return min(kSubBuckets - 1, __float2int_rz(__fmul_rn(__uint2float_rz(x), scale)));
+    return min(nsub - 1, __float2int_rz(__fmul_rn(__uint2float_rz(x), scale)));
+}
+
+// The distribution sort of a bucket above kSortCap keys: the same steps as the in-tile sort,
+// with kSubBig sub-buckets counted in shared memory (hist, the block's key buffer) and the keys
+// scattered into their sub-buckets in global memory (alt); each key's place is its sub-bucket's
+// start plus the number of smaller keys there.  Returns false, having written nothing, when a
+// sub-bucket holds more than kSubMaxBig keys (then the radix sort takes the bucket).
+__device__ __forceinline__ bool sort_big_bucket(const uint64_t* src, uint64_t* alt, int n, uint32_t base,
+                                                int tile, SortShared& sh, uint32_t* hist, uint32_t* sorted_ids,
+                                                uint64_t* sorted_keys) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        sh.dmin = 0xffffffffu;
+        sh.dmax = 0u;
+        sh.maxb = 0u;
+    }
+    for (int e = threadIdx.x; e < kSubBig; e += kSortThreads) hist[e] = 0;
+    __syncthreads();
+    uint32_t lo = 0xffffffffu, hi = 0u;
+    for (int j = threadIdx.x; j < n; j += kSortThreads) {
+        const uint32_t d = (uint32_t)(src[j] >> 32);
+        lo = min(lo, d);
+        hi = max(hi, d);
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) {
+        atomicMin(&sh.dmin, lo);
+        atomicMax(&sh.dmax, hi);
+    }
+    __syncthreads();
+    const uint32_t dmin = sh.dmin;
+    const float scale = (float)kSubBig / ((float)(sh.dmax - dmin) + 1.0f);
+    for (int j = threadIdx.x; j < n; j += kSortThreads) atomicAdd(&hist[sub_bucket(src[j], dmin, scale, kSubBig)], 1u);
+    __syncthreads();
+    {
+        constexpr int kPer = kSubBig / kSortThreads;
+        uint32_t sum = 0, mx = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t c = hist[threadIdx.x * kPer + q];
+            sum += c;
+            mx = max(mx, c);
+        }
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if (lane == 0) atomicMax(&sh.maxb, mx);
+        uint32_t off = sort_block_scan(sum, sh.warp_sum);
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t c = hist[threadIdx.x * kPer + q];
+            hist[threadIdx.x * kPer + q] = off;
+            off += c;
+        }
+    }
+    __syncthreads();
+    if (sh.maxb > (uint32_t)kSubMaxBig) {
+        __syncthreads();
+        return false;
+    }
+    for (int j = threadIdx.x; j < n; j += kSortThreads) {
+        const uint64_t k = src[j];
+        alt[atomicAdd(&hist[sub_bucket(k, dmin, scale, kSubBig)], 1u)] = k;
+    }
+    __syncthreads();
+    // hist[b] is now the end of sub-bucket b (= the start of b + 1)
+    for (int p = threadIdx.x; p < n; p += kSortThreads) {
+        const uint64_t k = alt[p];
+        const int b = sub_bucket(k, dmin, scale, kSubBig);
+        const int s0 = b > 0 ? (int)hist[b - 1] : 0, e0 = (int)hist[b];
+        int rank = 0;
+        for (int q = s0; q < e0; ++q) rank += alt[q] < k;
+        const uint32_t dst = base + (uint32_t)(s0 + rank);
+        sorted_ids[dst] = (uint32_t)k;
+        if (sorted_keys) sorted_keys[dst] = ((uint64_t)tile << 32) | (k >> 32);
+    }
+    __syncthreads();
+    return true;
 }
 
 // One CTA per tile (grid-stride over tiles).  A bucket of up to kSortCap keys is sorted by
@@ -479,6 +559,10 @@ __global__ void __launch_bounds__(kSortThreads, 1) k_tile_sort(int T, const uint
             }
             __syncthreads();
         }
+        if (radix && n > kSortCap &&
+            sort_big_bucket(src, alt + r.x, n, r.x, tile, sh, reinterpret_cast<uint32_t*>(buf), sorted_ids,
+                            sorted_keys))
+            radix = false;
         if (radix) {
             const uint64_t* res = sort_bucket(keys + r.x, alt + r.x, n, sh);
             for (int j = threadIdx.x; j < n; j += kSortThreads) {
@@ -492,6 +576,8 @@ __global__ void __launch_bounds__(kSortThreads, 1) k_tile_sort(int T, const uint
 }
 
 constexpr size_t kSortSmem = ((sizeof(SortShared) + 15) & ~size_t(15)) + kSortCap * sizeof(uint64_t);
+static_assert(kSubBig * sizeof(uint32_t) <= kSortCap * sizeof(uint64_t), "large-bucket histogram in the key buffer");
+static_assert(kSubBig % kSortThreads == 0, "histogram scan: a whole number of entries per thread");
 static_assert(kSortSmem <= 232448, "tile sort shared memory above the per-block limit");
 
 }  // namespace

@@ -219,15 +219,17 @@ def _binsort_run(exe, tmp_path, rec, H, W, cap):
                                              (1000, 90, 360, 3, "plain"), (5000, 180, 720, 5, "plain"),
                                              (3000, 45, 180, 6, "plain"), (1500, 45, 180, 14, "three_depths"),
                                              (1500, 45, 180, 17, "one_depth"),
-                                             (2000, 90, 360, 12, "overflow"), (400, 90, 360, 16, "culled")])
+                                             (2000, 90, 360, 12, "overflow"), (400, 90, 360, 16, "culled"),
+                                             (30000, 16, 32, 18, "big")])
 def test_binsort_kernels_logic(emu_bin, tmp_path, n, H, W, seed, case):
     """k_tile_count, k_tile_emit and k_tile_sort (the library's source under the host shim)
     against the oracle's stable (tile, r, index) sort, bit for bit: ragged grids, 1 to 5,000
     records, the shared-memory distribution sort, three distinct depths and a single depth (tiles
     whose depth sub-buckets exceed 64 keys take the radix path; ties by index), a capacity below
-    the pair count, every record culled.  Buckets above the shared-memory capacity (the same
-    radix code on larger buckets) are the GPU tests': every warp vote is a scheduling round in
-    the shim, which makes those sizes slow on the CPU."""
+    the pair count, every record culled, and buckets above the shared-memory capacity (two tiles
+    of ~30k pairs: the distribution sort with its keys scattered in global memory).  The radix
+    path on such large buckets is the GPU tests': every warp vote is a scheduling round in the
+    shim, which makes those sizes slow on the CPU."""
     from oracle import binsort as obs
     from paper_2511_22793_gb300 import synth
 

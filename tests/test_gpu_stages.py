@@ -126,11 +126,16 @@ def test_bin_sort_capacity_overflow_reported():
     assert np.array_equal(ids[:last], ov[:last])
 
 
-def test_bin_sort_buckets_above_shared_memory_capacity():
+@pytest.mark.parametrize("depths", ["spread", "few"])
+def test_bin_sort_buckets_above_shared_memory_capacity(depths):
     """Every tile of a 180x45 view holds 26k-39k pairs, more than a thread block
-    sorts in shared memory (24576): those buckets are radix sorted in the workspace."""
+    sorts in shared memory (24576).  Spread depths: those buckets take the
+    distribution sort with the keys scattered in the workspace.  Three distinct
+    depths: its sub-buckets overflow and the buckets are radix sorted there."""
     rec = synth.make_proj_records(60_000, 45, 180, seed=13, frac_wide=0.6)
     rec[:, 3] = np.where(rec[:, 3] < 0, -1.0, np.maximum(rec[:, 3], 30.0))
+    if depths == "few":
+        rec[:, 7] = np.random.default_rng(16).choice(np.float32([1.5, 2.0, 7.25]), size=len(rec))
     st, npairs, keys, ids, ranges = _gpu_binsort(rec, 45, 180)
     ok, ov, orng = obs.bin_sort(rec, 45, 180)
     assert (orng[:, 1] - orng[:, 0]).min() > 24576
@@ -151,6 +156,37 @@ def test_bin_sort_few_distinct_depths():
     assert np.array_equal(keys, ok)
     assert np.array_equal(ids, ov)
     assert np.array_equal(ranges, orng)
+
+
+def test_bin_sort_serving_scale_sampled_tiles():
+    """The 500k-Gaussian serving scene at 720x180 (about 11M pairs; the densest tiles
+    above the shared-memory capacity): the GPU's own projection records binned and
+    sorted, every tile's pair count against the oracle's footprint rule, and the full
+    (r, id) lists of the 8 largest tiles and 8 random ones bit for bit."""
+    sc = synth.make_scene(500_000, seed=0, bf16_latent=True)
+    ds = DeviceScene.from_host(sc, DEV)
+    r = Renderer(180, 720, 1, sc.n, device=DEV)
+    r.geometry(ds)
+    assert r.check() == 0
+    npairs = int(r.n_pairs.item())
+    rec = r.proj.cpu().numpy()
+    ids = r.sorted_ids[:npairs].cpu().numpy().view(np.uint32)
+    rng = r.tile_ranges.cpu().numpy().view(np.uint32).astype(np.int64)
+    tiles = obs.footprint_tiles(rec, 180, 720)
+    lens = np.fromiter((len(t) for t in tiles), dtype=np.int64, count=len(tiles))
+    flat = np.fromiter((t for ts in tiles for t in ts), dtype=np.int64, count=int(lens.sum()))
+    owner = np.repeat(np.arange(len(tiles), dtype=np.int64), lens)
+    counts = np.bincount(flat, minlength=r.T)
+    assert npairs == len(flat)
+    assert np.array_equal(rng[:, 1] - rng[:, 0], counts)
+    assert counts.max() > 24576
+    pick = np.unique(np.concatenate([np.argsort(counts)[-8:],
+                                     np.random.default_rng(17).choice(r.T, 8, replace=False)]))
+    rr = rec[:, 7]
+    for t in pick:
+        mem = owner[flat == t]
+        want = mem[np.lexsort((mem, rr[mem].astype(np.float64)))]
+        assert np.array_equal(ids[rng[t, 0]:rng[t, 1]], want.astype(np.uint32)), t
 
 
 def test_bin_sort_properties_full_size_scene():
