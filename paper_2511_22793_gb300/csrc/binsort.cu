@@ -13,12 +13,15 @@ namespace {
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// bcnt (the per-block tile counts that spare k_tile_emit its counting pass) is laid out when the
+// counts are kept in shared memory (ntiles <= kSmemTiles) and with_bcnt is set; bcnt == 0 then
+// means "not laid out".
 struct Layout {
-    size_t cnt, cursor, done, keys, alt, total;
+    size_t cnt, cursor, done, keys, alt, bcnt, total;
     int nblk;
 };
 
-Layout layout(int N, int64_t cap, int ntiles) {
+Layout layout(int N, int64_t cap, int ntiles, bool with_bcnt = true) {
     Layout L;
     L.nblk = (N + kBinThreads - 1) / kBinThreads;
     size_t o = 0;
@@ -27,6 +30,11 @@ Layout layout(int N, int64_t cap, int ntiles) {
     L.cursor = o; o += align256((size_t)ntiles * 4);
     L.keys = o;   o += align256((size_t)cap * 8);
     L.alt = o;    o += align256((size_t)cap * 8);
+    L.bcnt = 0;
+    if (with_bcnt && ntiles <= kSmemTiles && N > 0) {
+        L.bcnt = o;
+        o += align256((size_t)L.nblk * (size_t)ntiles * 4);
+    }
     L.total = o;
     return L;
 }
@@ -41,6 +49,7 @@ int bin_sort_launch(const gsparc_view* view, int N, const float* proj, int64_t p
     uint32_t* cursor = reinterpret_cast<uint32_t*>(w + L.cursor);
     uint64_t* keys = reinterpret_cast<uint64_t*>(w + L.keys);
     uint64_t* alt = reinterpret_cast<uint64_t*>(w + L.alt);
+    uint32_t* bcnt = L.bcnt ? reinterpret_cast<uint32_t*>(w + L.bcnt) : nullptr;
     const uint32_t cap = (uint32_t)pair_capacity;
     if (N == 0) {
         if (cudaMemsetAsync(tile_ranges, 0, (size_t)T * 2 * sizeof(uint32_t), s) != cudaSuccess)
@@ -53,9 +62,9 @@ int bin_sort_launch(const gsparc_view* view, int N, const float* proj, int64_t p
     if (!ensure_smem_attr(k_tile_sort, (int)kSortSmem)) return GSPARC_ERR_CUDA;
     const float4* p4 = reinterpret_cast<const float4*>(proj);
     uint2* ranges = reinterpret_cast<uint2*>(tile_ranges);
-    k_tile_count<<<L.nblk, kBinThreads, 0, s>>>(N, view->H, view->W, TW, T, p4, cnt, cursor, done, cap,
+    k_tile_count<<<L.nblk, kBinThreads, 0, s>>>(N, view->H, view->W, TW, T, p4, cnt, bcnt, cursor, done, cap,
                                                 ranges, n_pairs, d_status);
-    k_tile_emit<<<L.nblk, kBinThreads, 0, s>>>(N, view->H, view->W, TW, T, p4, cursor, cap, keys);
+    k_tile_emit<<<L.nblk, kBinThreads, 0, s>>>(N, view->H, view->W, TW, T, p4, bcnt, cursor, cap, keys);
     const int grid = std::min(T, num_sms() * 8);
     k_tile_sort<<<grid, kSortThreads, kSortSmem, s>>>(T, ranges, keys, alt, sorted_ids, sorted_keys);
     return launch_status();
@@ -143,7 +152,8 @@ extern "C" int gsparc_bin_sort_noalloc(const gsparc_view* view, int32_t N, const
         return GSPARC_ERR_INVALID;
     if (reinterpret_cast<uintptr_t>(proj) & 15) return GSPARC_ERR_INVALID;
     const int T = tiles_x(*view) * tiles_y(*view);
-    const Layout L = layout(N, pair_capacity, T);
+    Layout L = layout(N, pair_capacity, T);
+    if (L.total > kNoAllocBytes) L = layout(N, pair_capacity, T, false);   // emit counts for itself
     if (L.total > kNoAllocBytes) return GSPARC_ERR_TOO_LARGE;
 
     int dev = 0;

@@ -41,10 +41,10 @@ namespace {
 
 constexpr int kBinThreads = 256;
 constexpr int kSmemTiles = 4096;                    // tile counters kept in shared memory up to this T
-constexpr int kSortThreads = 512;
+constexpr int kSortThreads = 1024;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortCap = 24576;                     // keys per bucket sorted in shared memory
-constexpr int kSubBuckets = 4096;                   // sub-buckets of the in-tile distribution sort
+constexpr int kSubBuckets = 8192;                   // sub-buckets of the in-tile distribution sort
 constexpr int kSubMax = 64;                         // largest sub-bucket ranked by comparison
 constexpr int kSubBig = 16384;                      // sub-buckets of a bucket above kSortCap keys
 constexpr int kSubMaxBig = 256;                     // largest such sub-bucket ranked by comparison
@@ -111,6 +111,8 @@ __device__ __forceinline__ void warp_pairs(bool valid, const Foot& f, int TW, F&
     const int wa = valid ? f.a1 - f.a0 + 1 : 0;
     const int cols = valid ? wa + (f.b1 >= f.b0 ? f.b1 - f.b0 + 1 : 0) : 0;
     const int c = valid ? (f.ty1 - f.ty0 + 1) * cols : 0;
+    // ceil(2^32 / cols): the row of pair q is the high word of q * inv, or one less (fixed below)
+    const uint64_t inv = cols > 0 ? ((1ull << 32) + (uint64_t)cols - 1) / (uint64_t)cols : 0ull;
     int incl = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -129,6 +131,7 @@ __device__ __forceinline__ void warp_pairs(bool valid, const Foot& f, int TW, F&
         }
         const int q = k - __shfl_sync(full, excl, owner);
         const int ocols = __shfl_sync(full, cols, owner);
+        const uint64_t oinv = __shfl_sync(full, inv, owner);
         const int owa = __shfl_sync(full, wa, owner);
         const int oty0 = __shfl_sync(full, valid ? f.ty0 : 0, owner);
         const int oa0 = __shfl_sync(full, valid ? f.a0 : 0, owner);
@@ -136,7 +139,11 @@ __device__ __forceinline__ void warp_pairs(bool valid, const Foot& f, int TW, F&
         const bool active = k < total;
         int tile = 0;
         if (active) {
-            const int row = q / ocols, cc = q - row * ocols;
+            // q / ocols without a division: q * ceil(2^32 / ocols) / 2^32 exceeds q / ocols by
+            // less than q / 2^32 < 1, so it is the quotient or one above it
+            int row = (int)(((uint64_t)(uint32_t)q * oinv) >> 32);
+            if (row * ocols > q) --row;
+            const int cc = q - row * ocols;
             const int tx = cc < owa ? oa0 + cc : ob0 + (cc - owa);
             tile = (oty0 + row) * TW + tx;
         }
@@ -144,13 +151,16 @@ __device__ __forceinline__ void warp_pairs(bool valid, const Foot& f, int TW, F&
     }
 }
 
-// Pairs per tile.  The last block to finish turns the counts into bucket offsets:
+// Pairs per tile, and with bcnt also per (block, tile) (bcnt[block * T + t], for emit to skip its
+// own counting pass; only when the counts are kept in shared memory, T <= kSmemTiles).  The last
+// block to finish turns the counts into bucket offsets:
 // cursor[t] = start of tile t, tile_ranges[t] = [start, end) ([0, 0) when the bucket is
 // empty or does not fit below cap), n_pairs = total (saturated at 2^32-1), GSPARC_ERR_CAPACITY if the
 // total exceeds cap.
 __global__ void __launch_bounds__(kBinThreads) k_tile_count(int N, int H, int W, int TW, int T,
                                                             const float4* __restrict__ proj,
                                                             uint32_t* __restrict__ cnt,
+                                                            uint32_t* __restrict__ bcnt,
                                                             uint32_t* __restrict__ cursor,
                                                             uint32_t* __restrict__ done, uint32_t cap,
                                                             uint2* __restrict__ ranges,
@@ -173,8 +183,12 @@ __global__ void __launch_bounds__(kBinThreads) k_tile_count(int N, int H, int W,
     });
     if (local) {
         __syncthreads();
-        for (int t = threadIdx.x; t < T; t += kBinThreads)
-            if (s_cnt[t]) atomicAdd(&cnt[t], s_cnt[t]);
+        uint32_t* mine = bcnt ? bcnt + (size_t)blockIdx.x * T : nullptr;
+        for (int t = threadIdx.x; t < T; t += kBinThreads) {
+            const uint32_t c = s_cnt[t];
+            if (c) atomicAdd(&cnt[t], c);
+            if (mine) mine[t] = c;
+        }
     }
     __threadfence();
     __syncthreads();
@@ -218,9 +232,12 @@ __global__ void __launch_bounds__(kBinThreads) k_tile_count(int N, int H, int W,
 
 // Every pair's key (bits(r) << 32) | index into its tile's bucket.  A block reserves one
 // run of each bucket with a single atomic per touched tile and fills it through shared
-// counters.  Positions at or above cap are dropped (their tiles have empty ranges).
+// counters; the block's count per tile comes from k_tile_count (bcnt) or, without it, from a
+// counting pass of its own.  Positions at or above cap are dropped (their tiles have empty
+// ranges).
 __global__ void __launch_bounds__(kBinThreads) k_tile_emit(int N, int H, int W, int TW, int T,
                                                            const float4* __restrict__ proj,
+                                                           const uint32_t* __restrict__ bcnt,
                                                            uint32_t* __restrict__ cursor, uint32_t cap,
                                                            uint64_t* __restrict__ keys) {
     __shared__ uint32_t s_cnt[kSmemTiles];
@@ -240,17 +257,26 @@ __global__ void __launch_bounds__(kBinThreads) k_tile_emit(int N, int H, int W, 
         });
         return;
     }
-    for (int t = threadIdx.x; t < T; t += kBinThreads) s_cnt[t] = 0;
-    __syncthreads();
-    warp_pairs(valid, f, TW, [&](int t, int, bool active) {
-        if (active) atomicAdd(&s_cnt[t], 1u);
-    });
-    __syncthreads();
-    for (int t = threadIdx.x; t < T; t += kBinThreads) {
-        const uint32_t c = s_cnt[t];
-        if (c) {
-            s_base[t] = atomicAdd(&cursor[t], c);
+    if (bcnt) {
+        const uint32_t* mine = bcnt + (size_t)blockIdx.x * T;
+        for (int t = threadIdx.x; t < T; t += kBinThreads) {
+            const uint32_t c = mine[t];
+            if (c) s_base[t] = atomicAdd(&cursor[t], c);
             s_cnt[t] = 0;
+        }
+    } else {
+        for (int t = threadIdx.x; t < T; t += kBinThreads) s_cnt[t] = 0;
+        __syncthreads();
+        warp_pairs(valid, f, TW, [&](int t, int, bool active) {
+            if (active) atomicAdd(&s_cnt[t], 1u);
+        });
+        __syncthreads();
+        for (int t = threadIdx.x; t < T; t += kBinThreads) {
+            const uint32_t c = s_cnt[t];
+            if (c) {
+                s_base[t] = atomicAdd(&cursor[t], c);
+                s_cnt[t] = 0;
+            }
         }
     }
     __syncthreads();
@@ -385,13 +411,44 @@ __device__ __forceinline__ uint64_t* sort_bucket(uint64_t* a, uint64_t* b, int n
     return a;
 }
 
-// Sub-bucket of a key in the tile's distribution sort: the depth bits' offset from the
-// tile's minimum, scaled to [0, nsub).  Every step (offset, round-toward-zero conversion,
-// multiplication, truncation, clamp) is monotone non-decreasing, so a key never lands in an
-// earlier sub-bucket than a smaller key.
-__device__ __forceinline__ int sub_bucket(uint64_t k, uint32_t dmin, float scale, int nsub = kSubBuckets) {
-    const uint32_t x = (uint32_t)(k >> 32) - dmin;
-    return min(nsub - 1, __float2int_rz(__fmul_rn(__uint2float_rz(x), scale)));
+// Sub-buckets of a tile's distribution sort over its depth range [dmin, dmax] (float bits of r).
+// When every depth is a finite non-negative float (bits below those of +inf), the sub-bucket is
+// linear in r: (r - r_min) * nsub / (r_max - r_min).  Otherwise (or when that scale would not
+// be finite) it is linear in the bits, (bits - dmin) * nsub / (dmax - dmin + 1).  Receiver
+// distances in a volume have a density that grows with r, so a map linear in r (rather than in
+// the bits, i.e. nearly in log r) keeps the sub-buckets of the far end small.
+struct SubMap {
+    uint32_t dmin;
+    float rmin, scale;
+    bool lin;
+};
+
+__device__ __forceinline__ SubMap sub_map(uint32_t dmin, uint32_t dmax, int nsub) {
+    SubMap m;
+    m.dmin = dmin;
+    m.rmin = __uint_as_float(dmin);
+    m.lin = false;
+    if (dmax < 0x7f800000u) {
+        const float range = __fsub_rn(__uint_as_float(dmax), m.rmin);
+        const float sc = (float)nsub / range;
+        if (range > 0.f && sc < 1e30f) {
+            m.scale = sc;
+            m.lin = true;
+            return m;
+        }
+    }
+    m.scale = (float)nsub / ((float)(dmax - dmin) + 1.0f);
+    return m;
+}
+
+// Every step (offset, conversion, multiplication, clamp, truncation) is monotone
+// non-decreasing, so a key never lands in an earlier sub-bucket than a smaller key; the clamp
+// keeps the truncated value in [0, nsub - 1].
+__device__ __forceinline__ int sub_bucket(uint64_t k, const SubMap& m, int nsub = kSubBuckets) {
+    const uint32_t d = (uint32_t)(k >> 32);
+    const float x = m.lin ? __fmul_rn(__fsub_rn(__uint_as_float(d), m.rmin), m.scale)
+                          : __fmul_rn(__uint2float_rz(d - m.dmin), m.scale);
+    return __float2int_rz(fminf(x, (float)(nsub - 1)));
 }
 
 // The distribution sort of a bucket above kSortCap keys: the same steps as the in-tile sort,
@@ -423,9 +480,8 @@ __device__ __forceinline__ bool sort_big_bucket(const uint64_t* src, uint64_t* a
         atomicMax(&sh.dmax, hi);
     }
     __syncthreads();
-    const uint32_t dmin = sh.dmin;
-    const float scale = (float)kSubBig / ((float)(sh.dmax - dmin) + 1.0f);
-    for (int j = threadIdx.x; j < n; j += kSortThreads) atomicAdd(&hist[sub_bucket(src[j], dmin, scale, kSubBig)], 1u);
+    const SubMap sm = sub_map(sh.dmin, sh.dmax, kSubBig);
+    for (int j = threadIdx.x; j < n; j += kSortThreads) atomicAdd(&hist[sub_bucket(src[j], sm, kSubBig)], 1u);
     __syncthreads();
     {
         constexpr int kPer = kSubBig / kSortThreads;
@@ -453,13 +509,13 @@ __device__ __forceinline__ bool sort_big_bucket(const uint64_t* src, uint64_t* a
     }
     for (int j = threadIdx.x; j < n; j += kSortThreads) {
         const uint64_t k = src[j];
-        alt[atomicAdd(&hist[sub_bucket(k, dmin, scale, kSubBig)], 1u)] = k;
+        alt[atomicAdd(&hist[sub_bucket(k, sm, kSubBig)], 1u)] = k;
     }
     __syncthreads();
     // hist[b] is now the end of sub-bucket b (= the start of b + 1)
     for (int p = threadIdx.x; p < n; p += kSortThreads) {
         const uint64_t k = alt[p];
-        const int b = sub_bucket(k, dmin, scale, kSubBig);
+        const int b = sub_bucket(k, sm, kSubBig);
         const int s0 = b > 0 ? (int)hist[b - 1] : 0, e0 = (int)hist[b];
         int rank = 0;
         for (int q = s0; q < e0; ++q) rank += alt[q] < k;
@@ -514,10 +570,9 @@ __global__ void __launch_bounds__(kSortThreads, 1) k_tile_sort(int T, const uint
                 atomicMax(&sh.dmax, hi);
             }
             __syncthreads();
-            const uint32_t dmin = sh.dmin;
-            const float scale = (float)kSubBuckets / ((float)(sh.dmax - dmin) + 1.0f);
+            const SubMap sm = sub_map(sh.dmin, sh.dmax, kSubBuckets);
             for (int j = threadIdx.x; j < n; j += kSortThreads)
-                atomicAdd(&sh.hist[sub_bucket(src[j], dmin, scale)], 1u);
+                atomicAdd(&sh.hist[sub_bucket(src[j], sm)], 1u);
             __syncthreads();
             {
                 constexpr int kPer = kSubBuckets / kSortThreads;
@@ -542,13 +597,13 @@ __global__ void __launch_bounds__(kSortThreads, 1) k_tile_sort(int T, const uint
             if (!radix) {
                 for (int j = threadIdx.x; j < n; j += kSortThreads) {
                     const uint64_t k = src[j];
-                    buf[atomicAdd(&sh.hist[sub_bucket(k, dmin, scale)], 1u)] = k;
+                    buf[atomicAdd(&sh.hist[sub_bucket(k, sm)], 1u)] = k;
                 }
                 __syncthreads();
                 // hist[b] is now the end of sub-bucket b (= the start of b + 1)
                 for (int p = threadIdx.x; p < n; p += kSortThreads) {
                     const uint64_t k = buf[p];
-                    const int b = sub_bucket(k, dmin, scale);
+                    const int b = sub_bucket(k, sm);
                     const int s0 = b > 0 ? (int)sh.hist[b - 1] : 0, e0 = (int)sh.hist[b];
                     int rank = 0;
                     for (int q = s0; q < e0; ++q) rank += buf[q] < k;

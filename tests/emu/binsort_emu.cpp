@@ -3,8 +3,11 @@
 // k_tile_emit over blocks of kBinThreads records, k_tile_sort over min(T, 4) blocks (its
 // grid-stride loop over the tiles; the library launches min(T, 8 x SMs)) with the
 // kernel's dynamic shared memory.
-// Input: int32 N, H, W, capacity; float proj[8N].  Output: uint32 n_pairs; int32 status; uint32
-// tile_ranges[2T]; uint32 sorted_ids[capacity]; uint64 sorted_keys[capacity]; int32 violations.
+// With with_bcnt, k_tile_count also writes the per-(block, tile) counts and k_tile_emit takes
+// them instead of counting for itself (the library's path when T <= kSmemTiles).
+// Input: int32 N, H, W, capacity, with_bcnt; float proj[8N].  Output: uint32 n_pairs; int32
+// status; uint32 tile_ranges[2T]; uint32 sorted_ids[capacity]; uint64 sorted_keys[capacity];
+// int32 violations.
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -15,8 +18,8 @@ int main(int argc, char** argv) {
     if (argc != 3) return 2;
     FILE* f = fopen(argv[1], "rb");
     if (!f) return 2;
-    int32_t hdr[4];
-    if (fread(hdr, 4, 4, f) != 4) return 2;
+    int32_t hdr[5];
+    if (fread(hdr, 4, 5, f) != 5) return 2;
     const int N = hdr[0], H = hdr[1], W = hdr[2];
     const uint32_t cap = (uint32_t)hdr[3];
     std::vector<float4> proj(2 * (size_t)N);
@@ -34,10 +37,13 @@ int main(int argc, char** argv) {
     } else {
         using namespace gsparc;
         const unsigned nblk = (unsigned)((N + kBinThreads - 1) / kBinThreads);
+        const bool with_bcnt = hdr[4] != 0 && T <= kSmemTiles;
+        std::vector<uint32_t> bcnt(with_bcnt ? (size_t)nblk * T : 1, 0xdeadbeefu);   // written before read
+        uint32_t* bc = with_bcnt ? bcnt.data() : nullptr;
         emu_launch(emu_dim3{nblk, 1, 1}, kBinThreads, k_tile_count, N, H, W, TW, T, (const float4*)proj.data(),
-                   cnt.data(), cursor.data(), done.data(), cap, ranges.data(), &n_pairs, &status);
+                   cnt.data(), bc, cursor.data(), done.data(), cap, ranges.data(), &n_pairs, &status);
         emu_launch(emu_dim3{nblk, 1, 1}, kBinThreads, k_tile_emit, N, H, W, TW, T, (const float4*)proj.data(),
-                   cursor.data(), cap, keys.data());
+                   (const uint32_t*)bc, cursor.data(), cap, keys.data());
         const unsigned grid = (unsigned)std::min(T, 4);     // grid-stride over the tiles
         emu_launch_smem(emu_dim3{grid, 1, 1}, kSortThreads, kSortSmem, k_tile_sort, T, (const uint2*)ranges.data(),
                         keys.data(), alt.data(), ids.data(), skeys.data());

@@ -98,10 +98,11 @@ int main(int argc, char** argv) {
     uint32_t n_pairs = 0;
     int32_t status = 0;
     const unsigned nblk = (unsigned)((n + kBinThreads - 1) / kBinThreads);
+    std::vector<uint32_t> bcnt((size_t)nblk * T);   // T <= kSmemTiles here: emit takes the blocks' counts
     emu_launch(emu_dim3{nblk, 1, 1}, kBinThreads, k_tile_count, n, H, W, TW, T, (const float4*)proj.data(), cnt.data(),
-               cursor.data(), done.data(), cap, ranges.data(), &n_pairs, &status);
+               bcnt.data(), cursor.data(), done.data(), cap, ranges.data(), &n_pairs, &status);
     emu_launch(emu_dim3{nblk, 1, 1}, kBinThreads, k_tile_emit, n, H, W, TW, T, (const float4*)proj.data(),
-               cursor.data(), cap, keys.data());
+               (const uint32_t*)bcnt.data(), cursor.data(), cap, keys.data());
     emu_launch_smem(emu_dim3{(unsigned)std::min(T, 152 * 8), 1, 1}, kSortThreads, kSortSmem, k_tile_sort, T,
                     (const uint2*)ranges.data(), keys.data(), alt.data(), ids.data(), (uint64_t*)nullptr);
     // attribute network

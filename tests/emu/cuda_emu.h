@@ -78,6 +78,11 @@ inline float __int_as_float(int i) {
     memcpy(&f, &i, 4);
     return f;
 }
+inline float __uint_as_float(unsigned u) {
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
 inline int __ffsll(long long x) { return __builtin_ffsll(x); }
 inline int __ffs(int x) { return __builtin_ffs(x); }
 inline int __clzll(long long x) { return x == 0 ? 64 : __builtin_clzll((unsigned long long)x); }

@@ -199,9 +199,9 @@ def test_projection_kernels_logic(emu_bin, tmp_path, n, H, W, seed, rot):
         assert np.linalg.norm(got - want) <= 1e-3 * np.linalg.norm(want)
 
 
-def _binsort_run(exe, tmp_path, rec, H, W, cap):
+def _binsort_run(exe, tmp_path, rec, H, W, cap, bcnt=True):
     n = rec.shape[0]
-    raw = _run(exe, tmp_path, np.array([n, H, W, cap], np.int32).tobytes() + np.ascontiguousarray(
+    raw = _run(exe, tmp_path, np.array([n, H, W, cap, int(bcnt)], np.int32).tobytes() + np.ascontiguousarray(
         rec, np.float32).tobytes())
     T = ((W + 15) // 16) * ((H + 15) // 16)
     n_pairs, status = int(np.frombuffer(raw[:4], np.uint32)[0]), int(np.frombuffer(raw[4:8], np.int32)[0])
@@ -229,7 +229,9 @@ def test_binsort_kernels_logic(emu_bin, tmp_path, n, H, W, seed, case):
     the pair count, every record culled, and buckets above the shared-memory capacity (two tiles
     of ~30k pairs: the distribution sort with its keys scattered in global memory).  The radix
     path on such large buckets is the GPU tests': every warp vote is a scheduling round in the
-    shim, which makes those sizes slow on the CPU."""
+    shim, which makes those sizes slow on the CPU.  Each case runs with the per-block counts
+    handed from k_tile_count to k_tile_emit (the library's path at these tile counts); the larger
+    plain and overflow cases also with k_tile_emit counting for itself."""
     from oracle import binsort as obs
     from paper_2511_22793_gb300 import synth
 
@@ -243,21 +245,22 @@ def test_binsort_kernels_logic(emu_bin, tmp_path, n, H, W, seed, case):
         rec[:, 2:4] = -1
     ok, ov, orng = obs.bin_sort(rec, H, W)
     cap = len(ov) // 2 if case == "overflow" else max(16, len(ov))
-    n_pairs, status, ranges, ids, keys = _binsort_run(exe, tmp_path, rec, H, W, cap)
-    assert n_pairs == len(ov)
-    if case == "overflow":
-        assert status == -5
-        fits = orng[:, 1] <= cap
-        assert fits.any() and not fits.all()
-        assert np.array_equal(ranges[fits], orng[fits])
-        assert np.all(ranges[~fits, 0] == ranges[~fits, 1])
-        last = orng[fits][:, 1].max()
-        assert np.array_equal(ids[:last], ov[:last])
-        return
-    assert status == 0
-    assert np.array_equal(ranges, orng)
-    assert np.array_equal(ids[:len(ov)], ov)
-    assert np.array_equal(keys[:len(ov)], ok)
+    for bcnt in ((True, False) if case in ("plain", "overflow") and n >= 1000 else (True,)):
+        n_pairs, status, ranges, ids, keys = _binsort_run(exe, tmp_path, rec, H, W, cap, bcnt)
+        assert n_pairs == len(ov)
+        if case == "overflow":
+            assert status == -5
+            fits = orng[:, 1] <= cap
+            assert fits.any() and not fits.all()
+            assert np.array_equal(ranges[fits], orng[fits])
+            assert np.all(ranges[~fits, 0] == ranges[~fits, 1])
+            last = orng[fits][:, 1].max()
+            assert np.array_equal(ids[:last], ov[:last])
+            continue
+        assert status == 0
+        assert np.array_equal(ranges, orng)
+        assert np.array_equal(ids[:len(ov)], ov)
+        assert np.array_equal(keys[:len(ov)], ok)
 
 
 @pytest.mark.parametrize("n,H,W,K,B,seed", [(200, 45, 180, 8, 2, 41), (200, 45, 180, 37, 1, 42),

@@ -43,11 +43,19 @@ def test_adam_matches_oracle():
     np.testing.assert_allclose(pd.cpu().numpy(), q, rtol=1e-5, atol=1e-6)
 
 
+def _s_tot_buffer(r, B, form):
+    strips = G.s_tot_strips(r.K) if form == "tc" else G.fp32_strips(r.K)
+    return torch.empty((B, strips, r.H, r.W), dtype=torch.float32, device=DEV)
+
+
+@pytest.mark.parametrize("form", ["tc", "fp32"])
 @pytest.mark.parametrize("n,H,W,K,B", [(3000, 90, 360, 64, 1), (2000, 45, 180, 37, 2)])
-def test_fused_l2_loss_forward_matches_unfused(n, H, W, K, B):
-    """gsparc_render_fwd_l2_tc: the gradient is bit-identical to gsparc_l2_loss on the spectrum
-    of gsparc_render_fwd_tc, the loss agrees to 1e-5 relative (summation order), the state
-    buffers are identical, and without a spectrum buffer nothing else changes."""
+def test_fused_l2_loss_forward_matches_unfused(n, H, W, K, B, form):
+    """gsparc_render_fwd_l2_tc / gsparc_render_fwd_l2: the gradient is bit-identical to
+    gsparc_l2_loss on the spectrum of gsparc_render_fwd_tc / gsparc_render_fwd, the loss agrees
+    to 1e-5 relative (summation order), the state buffers are identical, s_tot is the strip sum
+    of Re(conj(dL/dz) z), and without a spectrum buffer nothing else changes."""
+    tc = form == "tc"
     sc = synth.make_scene(n, seed=91)
     mlp = synth.make_mlp(32, seed=92)
     tx = synth.make_tx(B, seed=93)
@@ -55,7 +63,7 @@ def test_fused_l2_loss_forward_matches_unfused(n, H, W, K, B):
     ds, dm = DeviceScene.from_host(sc, DEV), DeviceMLP.from_host(mlp, DEV)
     r.geometry(ds)
     attr = r.attributes(ds, dm, torch.tensor(tx, device=DEV))
-    spec, logT, nc = r.render(attr, tensor_cores=True)
+    spec, logT, nc = r.render(attr, tensor_cores=tc)
     target = torch.randn_like(spec) * 0.01
     loss = torch.zeros(1, device=DEV)
     d_ref = torch.empty_like(spec)
@@ -64,17 +72,18 @@ def test_fused_l2_loss_forward_matches_unfused(n, H, W, K, B):
     z64, g64 = spec.double(), d_ref.double()
     prod = (z64 * g64).sum(-1)                                     # [B, K, H, W]
     mag = (z64.abs() * g64.abs()).sum(-1)
-    nst = G.s_tot_strips(K)
-    width = K if K <= 64 else 64
+    nst = G.s_tot_strips(K) if tc else G.fp32_strips(K)
+    width = (K if K <= 64 else 64) if tc else (K if K <= 32 else 32)
     want = torch.stack([prod[:, s * width:(s + 1) * width].sum(1) for s in range(nst)], 1)
     scale = torch.stack([mag[:, s * width:(s + 1) * width].sum(1) for s in range(nst)], 1)
     for with_spec in (True, False):
         out = r.alloc_outputs(B)
         loss2 = torch.full((1,), 7.0, device=DEV)
         d2 = torch.empty_like(spec)
-        s_tot = r.s_tot_buffer(B)
-        G.gsparc_render_fwd_l2_tc(r.view, r.band, B, n, r.proj, r.tile_ranges, r.sorted_ids, attr, target, loss2,
-                                  d2, out[0] if with_spec else None, out[1], out[2], s_tot=s_tot)
+        s_tot = _s_tot_buffer(r, B, form)
+        fn = G.gsparc_render_fwd_l2_tc if tc else G.gsparc_render_fwd_l2
+        fn(r.view, r.band, B, n, r.proj, r.tile_ranges, r.sorted_ids, attr, target, loss2, d2,
+           out[0] if with_spec else None, out[1], out[2], s_tot=s_tot)
         torch.cuda.synchronize()
         assert torch.equal(d2, d_ref)
         # the blocks' partial sums are added atomically in FP32, in no fixed order
@@ -85,39 +94,43 @@ def test_fused_l2_loss_forward_matches_unfused(n, H, W, K, B):
         assert float(((s_tot.double() - want).abs() - 1e-5 * scale).max()) <= 0.0
 
 
+@pytest.mark.parametrize("form", ["tc", "fp32"])
 @pytest.mark.parametrize("n,H,W,K,B,split_min", [(50_000, 90, 360, 64, 1, 0), (3000, 45, 180, 100, 2, 1),
                                                    (4000, 90, 360, 16, 1, 2)])
-def test_scheduled_backward_training_path(n, H, W, K, B, split_min):
-    """The training step's backward: fused-loss forward writing s_tot, then
-    gsparc_render_bwd_tc_balanced (long walks split, front chunks fed by s_tot) against
-    gsparc_render_bwd_tc on the same inputs (relative L2 <= 1e-4 per gradient component).
-    The first case is the 50k-Gaussian, 64-subcarrier, 360x90 training workload with the
-    default split rule; the schedule splits some walks there (checked on the host from
-    n_contrib)."""
+def test_scheduled_backward_training_path(n, H, W, K, B, split_min, form):
+    """The training step's backward: fused-loss forward writing s_tot, then the scheduled
+    backward (gsparc_render_bwd_tc_balanced / gsparc_render_bwd_balanced: long walks split,
+    front chunks fed by s_tot) against the unscheduled call of the same form
+    (gsparc_render_bwd_tc / gsparc_render_bwd) on the same inputs (relative L2 <= 1e-4 per
+    gradient component).  The first case is the 50k-Gaussian, 64-subcarrier, 360x90 training
+    workload with the default split rule; the schedule splits some walks there (checked on the
+    host from n_contrib)."""
+    tc = form == "tc"
     sc = synth.make_scene(n, seed=95)
     mlp = synth.make_mlp(32, seed=96)
     tx = synth.make_tx(B, seed=97)
     r = Renderer(H, W, K, n, device=DEV)
     ds, dm = DeviceScene.from_host(sc, DEV), DeviceMLP.from_host(mlp, DEV)
     r.geometry(ds)
-    attr = r.attributes(ds, dm, torch.tensor(tx, device=DEV), G.GSPARC_BF16X2)
+    attr = r.attributes(ds, dm, torch.tensor(tx, device=DEV), G.GSPARC_BF16X2 if tc else G.GSPARC_FP32)
     _, logT, nc = r.alloc_outputs(B)
     target = torch.randn((B, K, H, W, 2), device=DEV) * 0.01
     loss = torch.zeros(1, device=DEV)
     d_spec = torch.empty_like(target)
-    s_tot, tile_walk = r.s_tot_buffer(B), r.walk_buffer(B)
-    G.gsparc_render_fwd_l2_tc(r.view, r.band, B, n, r.proj, r.tile_ranges, r.sorted_ids, attr, target, loss,
-                              d_spec, None, logT, nc, s_tot=s_tot, tile_walk=tile_walk)
+    s_tot, tile_walk = _s_tot_buffer(r, B, form), r.walk_buffer(B)
+    fwd = G.gsparc_render_fwd_l2_tc if tc else G.gsparc_render_fwd_l2
+    fwd(r.view, r.band, B, n, r.proj, r.tile_ranges, r.sorted_ids, attr, target, loss, d_spec, None, logT, nc,
+        s_tot=s_tot, tile_walk=tile_walk)
     res = []
-    for form in ("plain", "balanced", "balanced_walks"):
+    for kind in ("plain", "balanced", "balanced_walks"):
         d_attr = torch.zeros_like(attr)
         d_proj = torch.zeros_like(r.proj)
-        if form == "plain":
-            G.gsparc_render_bwd_tc(r.view, r.band, B, n, r.proj, r.tile_ranges, r.sorted_ids, attr, logT, nc,
-                                   d_spec, d_attr, d_proj)
+        if kind == "plain":
+            bwd = G.gsparc_render_bwd_tc if tc else G.gsparc_render_bwd
+            bwd(r.view, r.band, B, n, r.proj, r.tile_ranges, r.sorted_ids, attr, logT, nc, d_spec, d_attr, d_proj)
         else:
-            r.render_backward(attr, logT, nc, d_spec, d_attr, d_proj, tensor_cores=True, s_tot=s_tot,
-                              split_min=split_min, tile_walk=tile_walk if form == "balanced_walks" else None)
+            r.render_backward(attr, logT, nc, d_spec, d_attr, d_proj, tensor_cores=tc, s_tot=s_tot,
+                              split_min=split_min, tile_walk=tile_walk if kind == "balanced_walks" else None)
         torch.cuda.synchronize()
         res.append((d_attr.cpu().numpy().astype(np.float64), d_proj.cpu().numpy().astype(np.float64)))
     assert r.check() == 0
