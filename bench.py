@@ -62,6 +62,13 @@ FLOP_FWD_UNIT = 10
 FLOP_BWD_UNIT = 20
 FMA_FWD_UNIT, FMA_BWD_UNIT = 2, 6
 FP32_LANES_PER_SM = 128
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the compositing
+# kernels on this workload, from one `ncu --set full --clock-control none` capture of the
+# kernels as they are now (one launch each, L2 flushed before the step); set an entry to None
+# when its kernel changes until it is captured again.  Algorithmic bytes for comparison: the
+# 16.6 MB upstream gradient (backward) or target (forward) read once, plus per-pixel state.
+NCU_TRAFFIC = {("fp32", "render_bwd"): 17_568_512 + 512, ("fp32", "render_fwd"): 17_780_736 + 768,
+               ("tc", "render_bwd"): 17_510_912, ("tc", "render_fwd"): 17_175_040}
 
 
 def _env_int(k, d):
@@ -325,7 +332,7 @@ def time_form(args, dev, form, inp, steps, flush, sampler=None, dist=False):
             "clocks": clocks, "spec": spec, "h2d": inp.nbytes, "d2h": host_loss.numel() * host_loss.element_size()}
 
 
-def roofline(form_res, dev, probes):
+def roofline(form_res, dev, probes, form="fp32"):
     """Dominant kernel of the step against the FP32 ALU peak (SMs x 128 lanes x 2 flop x the
     maximum SM clock), with the scope table's flop per unit; also against the FMA rate the probe
     measured on this GPU, and as FMA-pipe issue (the FMAs the kernel executes per unit)."""
@@ -347,7 +354,8 @@ def roofline(form_res, dev, probes):
         d = {"kernel": k, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
              "frac": achieved / fp32_peak, "kernel_ms": ms,
              "flop_per_unit": flop[k], "units_per_launch": units,
-             "peak_note": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % (sms, sm_max)}
+             "peak_note": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % (sms, sm_max),
+             "traffic": NCU_TRAFFIC.get((form, k)), "traffic_unit": "B per launch (ncu DRAM read + write)"}
         if probes and probes.get("fp32_tflops_at_max_clock"):
             d["peak_probe"] = probes["fp32_tflops_at_max_clock"]
             d["frac_vs_probe"] = achieved / probes["fp32_tflops_at_max_clock"]
@@ -356,7 +364,7 @@ def roofline(form_res, dev, probes):
         out[k] = d
     dom = dict(out[top]) if top in out else {"kernel": top, "bound": "hbm", "achieved": None,
                                              "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s",
-                                             "frac": None}
+                                             "frac": None, "traffic": None}
     return dom, out
 
 
@@ -379,7 +387,7 @@ def run_ours(args, rank, world, local_rank):
     value = throughput(job_units, total_ms)
     e2e_value = throughput(job_units_e2e, e2e_total)
     probes = probe_peaks(dev, local_rank) if world == 1 else None
-    dom, rl = roofline(head, dev, probes)
+    dom, rl = roofline(head, dev, probes, args.render)
     st = head["st"]
     tc_head = args.render == "tc"
     out = {
@@ -418,7 +426,7 @@ def run_ours(args, rank, world, local_rank):
         other = "fp32" if tc_head else "tc"
         res_o = time_form(args, dev, other, inp, min(args.steps, 100), flush)
         tot_o = sum(res_o["step_ms"])
-        dom_o, _ = roofline(res_o, dev, probes)
+        dom_o, _ = roofline(res_o, dev, probes, other)
         spectra[other] = res_o["spec"]
         d_head = head["spec"].double()
         d_o = res_o["spec"].double()
