@@ -46,7 +46,7 @@ static void mlp(int n, int B, const float* tx, const float* means, const float* 
         return;
     }
     const int64_t tiles = (rows + gsparc::kBwdRows - 1) / gsparc::kBwdRows;
-    emu_launch_smem(emu_dim3{(unsigned)std::min<int64_t>(tiles, 152 * 2), 1, 1}, gsparc::kBwdRows,
+    emu_launch_smem(emu_dim3{(unsigned)std::min<int64_t>(tiles, 152 * 3), 1, 1}, gsparc::kBwdThreads,
                     (size_t)gsparc::BwdSmem<HD>::kTotal * sizeof(float), gsparc::k_mlp_bwd<HD>, n, B, tx, 0.f, 0.f,
                     0.f, means, ologit, latent, w, dattr, dm, dol, dlat, g);
 }

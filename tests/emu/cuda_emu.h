@@ -254,6 +254,16 @@ inline T atomicAdd(T* p, T v) {
     return std::atomic_ref<T>(*p).fetch_add(v);
 }
 
+// the 16-byte vector atomic of sm_90+: one atomic add per element
+inline float4 atomicAdd(float4* p, float4 v) {
+    float4 old;
+    old.x = std::atomic_ref<float>(p->x).fetch_add(v.x);
+    old.y = std::atomic_ref<float>(p->y).fetch_add(v.y);
+    old.z = std::atomic_ref<float>(p->z).fetch_add(v.z);
+    old.w = std::atomic_ref<float>(p->w).fetch_add(v.w);
+    return old;
+}
+
 template <typename T>
 inline T atomicOr(T* p, T v) {
     return std::atomic_ref<T>(*p).fetch_or(v);

@@ -33,7 +33,7 @@ static void run(int N, int B, const std::vector<float>& tx, const std::vector<fl
     const int64_t tiles = (rows + gsparc::kBwdRows - 1) / gsparc::kBwdRows;
     const unsigned blocks = (unsigned)std::min<int64_t>(tiles, 2);
     gsparc_mlp_grad mg{g.W1.data(), g.b1.data(), g.W2.data(), g.b2.data(), g.W3.data(), g.b3.data()};
-    emu_launch_smem(emu_dim3{blocks, 1, 1}, gsparc::kBwdRows, (size_t)gsparc::BwdSmem<HD>::kTotal * sizeof(float),
+    emu_launch_smem(emu_dim3{blocks, 1, 1}, gsparc::kBwdThreads, (size_t)gsparc::BwdSmem<HD>::kTotal * sizeof(float),
                     gsparc::k_mlp_bwd<HD>, N, B, (const float*)tx.data(), rx[0], rx[1], rx[2],
                     (const float*)means.data(), (const float*)ologit.data(), (const float*)latent.data(), w,
                     (const float4*)dattr.data(), dm.data(), dol.data(), dlat.data(), mg);
