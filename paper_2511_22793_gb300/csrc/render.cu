@@ -23,7 +23,7 @@ int launch_fwd(const RenderArgs& a, int T, cudaStream_t s) {
 // max_items > 0: a scheduled launch (a.items), one CTA per item
 template <int S>
 int launch_bwd(const RenderArgs& a, int T, cudaStream_t s, uint32_t max_items = 0) {
-    constexpr int smem = F32Smem<S>::kTotal;
+    constexpr int smem = F32BwdSmem<S>::kTotal;
     if (!ensure_smem_attr(k_render_bwd<S>, smem)) return GSPARC_ERR_CUDA;
     if (max_items) {
         k_render_bwd<S><<<max_items, kThreads, smem, s>>>(a);
@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
 #pragma unroll
             for (int j = 0; j < kTcE; ++j) wv[j] = 0.f;
             if (__any_sync(0xffffffffu, !done)) {
-                const uint64_t mask = warp_entry_mask(geo, ext, nb, wcx, wcy, a.W);
+                const uint64_t mask = warp_entry_mask(geo, geo2, ext, nb, wcx, wcy, a.W);
                 if (!done) {
                     // phase 1: alpha and log2(1 - alpha) of every entry, independent of each other.
                     // Groups of 8 entries that miss the warp's rows are skipped (warp-uniform);
@@ -1160,6 +1160,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
         const float c_f0 = (float)(a.two_pi_over_c * (a.f0 + (double)k0 * a.df));
         const float c_df = (float)(a.two_pi_over_c * a.df);
         const int slot18 = rs18_slot(lane);
+        const uint32_t wlast = __reduce_max_sync(0xffffffffu, last);   // the warp's walk
         // The walk in either direction (a compile-time flag).  Back to front from the pixel's
         // final state, acc = the sum over later entries of w reG a (the suffix); front to back
         // from T = 1 (the forward's own recursion), acc = the same sum over the entries up to
@@ -1182,7 +1183,10 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
 #pragma unroll
                     for (int q = 0; q < 16; ++q) v[c + q] = t16[q];
                 }
-                const uint64_t mask = warp_entry_mask(mdp.geo, mdp.ext, nbp, wcx, wcy, a.W);
+                uint64_t mask = warp_entry_mask(mdp.geo, mdp.geo2, mdp.ext, nbp, wcx, wcy, a.W);
+                // positions at or past every pixel's n_contrib are live at none of the warp's pixels
+                if (lo_pos >= wlast) mask = 0ull;
+                else if (wlast - lo_pos < 64u) mask &= (1ull << (wlast - lo_pos)) - 1ull;
                 if (lane == 0) mask_at(st, warp) = mask;
                 // entries in pairs in walk order: both entries' alpha, gradient components and
                 // warp reductions sit in one block so their latencies overlap

@@ -11,8 +11,10 @@
 // thread.  Gaussian batches of the tile's sorted list are staged in shared
 // memory by bulk asynchronous copies (one batch ahead of the compositing)
 // together with their unit phasors e^{j psi_ik} for the strip, so the
-// per-(pixel, Gaussian, subcarrier) work is two FFMAs (forward) or six
-// (backward) against broadcast shared-memory reads.  Transmittance is carried
+// per-(pixel, Gaussian, subcarrier) work is one paired FMA (forward) or two paired
+// FMAs and a paired add (backward) against broadcast shared-memory reads.  A warp
+// visits only the entries that can be live at one of its pixels (an exact bound of q
+// over its 16x2 block, and in the backward the warp's own walk).  Transmittance is carried
 // as log2 T in FP32; a thread stops before T would fall below 1e-4 and the
 // CTA stops fetching once every thread has stopped.  The backward can run as
 // scheduled chunks of the walks (the items of k_bwd_schedule).
@@ -49,21 +51,18 @@ __device__ __forceinline__ float lg2(float x) {
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-// Two FP32 FMAs in one instruction (fma.rn.f32x2): d.x = fma(a.x, b.x, c.x), d.y = fma(a.y, b.y,
-// c.y), each an IEEE single-precision fused multiply-add, as fmaf.
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-        "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-    return d;
-}
+// Two FP32 FMAs in one instruction (the paired FFMA of sm_100+): d.x = fma(a.x, b.x, c.x),
+// d.y = fma(a.y, b.y, c.y), each an IEEE single-precision fused multiply-add, as fmaf.  The
+// runtime's intrinsic keeps the operands in register pairs without repacking.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// Two FP32 additions in one instruction, each an IEEE single-precision add.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 #else
 // the test suite's host shim: the library's exact counterparts of the SFU approximations
 inline float ex2(float x) { return exp2f(x); }
 inline float lg2(float x) { return log2f(x); }
 inline float2 fma2(float2 a, float2 b, float2 c) { return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y)); }
+inline float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 #endif
 
 struct RenderArgs {
@@ -261,57 +260,91 @@ __device__ __forceinline__ void stage_phasors(const RenderArgs& a, const StageRe
     }
 }
 
-// warp_entry_mask over staged records (see warp_entry_mask).
+// The backward's table: for each unit phasor t = e^{j psi} the pair (t, -j conj(t)), i.e.
+// (t.x, t.y, t.y, -t.x), so that for an upstream gradient g both Re(conj(g) t) = g.x t.x + g.y t.y
+// and Im(conj(g) t) = g.x t.y - g.y t.x are one paired FMA of (g.x, g.y) against one half.
+template <int S>
+__device__ __forceinline__ void stage_phasors_bwd(const RenderArgs& a, const StageRec* rec, int nb, int k0,
+                                                  float4 (*tab)[S]) {
+    for (int e = threadIdx.x; e < nb * S; e += kThreads) {
+        const int j = e / S, kk = e - j * S;
+        const int k = k0 + kk;
+        float2 ph = make_float2(0.f, 0.f);
+        if (k < a.K) ph = unit_phasor(a, rec[j].at.w, rec[j].at.y, k);
+        tab[j][kk] = make_float4(ph.x, ph.y, ph.y, -ph.x);
+    }
+}
+
+// Whether an entry can be live at a pixel of a warp's 16x2 block of pixel centres (centre
+// (wcx, wcy)): centre p, footprint half extents e, conic (cxx, cxy, cyy), opacity sig.  First the
+// footprint box test (the bounding box of q <= q_max, with a 0.01 px margin for rounding at its
+// edge); then the smallest q over the block (each of its two pixel rows is a quadratic in the
+// column offset, minimised over the row's continuous extent, which bounds the minimum over its
+// pixel centres from below) against the smaller of q_max and the q at which
+// alpha = sigma e^{-q/2} falls to 1/255, with a margin of 0.01 far above the rounding of either
+// side.  False therefore means eval_alpha skips the entry at every pixel of the block.  A block
+// that reaches the antipode of the entry's centre (where the azimuth wrap could split its
+// columns) keeps the box test's answer.
+__device__ __forceinline__ bool entry_reaches_block(float px, float py, float ex, float ey, float cxx, float cxy,
+                                                    float cyy, float sig, float wcx, float wcy, int W) {
+    const float hw = 0.5f * (float)W;
+    float dx = wcx - px;
+    if (dx >= hw) dx -= (float)W;
+    else if (dx < -hw) dx += (float)W;
+    const float dy = wcy - py;
+    bool hit = ex >= 0.f && fabsf(dx) <= ex + 7.51f && fabsf(dy) <= ey + 0.51f;
+    if (hit && fabsf(dx) < hw - 8.0f) {
+        // alpha >= 1/255  <=>  q <= 2 ln(255 sigma)
+        const float q_op = 2.0f * 0.6931471805599453f * lg2(255.0f * sig);
+        const float thr = fminf(kQMax, q_op) + 0.01f;
+        float qmin = 3.0e38f;
+#pragma unroll
+        for (int row = 0; row < 2; ++row) {
+            const float dr = dy + (row ? 0.5f : -0.5f);
+            const float t = fminf(fmaxf(__fdividef(-cxy * dr, cxx), dx - 7.5f), dx + 7.5f);
+            qmin = fminf(qmin, (cxx * t + 2.0f * cxy * dr) * t + cyy * dr * dr);
+        }
+        hit = qmin <= thr;
+    }
+    return hit;
+}
+
+// Bit j set when staged entry j (of nb) can be live at a pixel of the warp's block
+// (entry_reaches_block), over staged records.
 __device__ __forceinline__ uint64_t warp_entry_mask_rec(const StageRec* rec, int nb, float wcx, float wcy, int W) {
     const int lane = threadIdx.x & 31;
-    const float hw = 0.5f * (float)W;
-    bool h0 = false, h1 = false;
+    bool h[2] = {false, false};
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         const int j = lane + 32 * half;
-        bool hit = false;
         if (j < nb) {
-            const float4 p = rec[j].p0;
-            float dx = wcx - p.x;
-            if (dx >= hw) dx -= (float)W;
-            else if (dx < -hw) dx += (float)W;
-            const float dy = wcy - p.y;
-            hit = p.z >= 0.f && fabsf(dx) <= p.z + 7.51f && fabsf(dy) <= p.w + 0.51f;
+            const StageRec& r = rec[j];
+            h[half] = entry_reaches_block(r.p0.x, r.p0.y, r.p0.z, r.p0.w, r.p1.x, r.p1.y, r.p1.z, r.at.z, wcx, wcy, W);
         }
-        if (half == 0) h0 = hit;
-        else h1 = hit;
     }
-    const uint32_t lo = __ballot_sync(0xffffffffu, h0);
-    const uint32_t hi = __ballot_sync(0xffffffffu, h1);
+    const uint32_t lo = __ballot_sync(0xffffffffu, h[0]);
+    const uint32_t hi = __ballot_sync(0xffffffffu, h[1]);
     return ((uint64_t)hi << 32) | lo;
 }
 
-// Bit j set when staged entry j's footprint box reaches the warp's 16x2 block of
-// pixel centres (centre (wcx, wcy), half sizes 7.5 x 0.5).  The box is the
-// bounding box of q <= q_max, so a cleared bit means q > q_max at every pixel
-// of the warp; the 0.01 px margin covers rounding at the box edge.
-__device__ __forceinline__ uint64_t warp_entry_mask(const float4* s_geo, const float2* s_ext, int nb,
-                                                    float wcx, float wcy, int W) {
+// The same over the tensor-core kernels' staging: s_geo (p_x, p_y, c_xx, c_xy), s_geo2 (c_yy,
+// sigma), s_ext (half extents; negative for a culled or invalid entry).
+__device__ __forceinline__ uint64_t warp_entry_mask(const float4* s_geo, const float2* s_geo2, const float2* s_ext,
+                                                    int nb, float wcx, float wcy, int W) {
     const int lane = threadIdx.x & 31;
-    const float hw = 0.5f * (float)W;
-    bool h0 = false, h1 = false;
+    bool h[2] = {false, false};
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         const int j = lane + 32 * half;
-        bool hit = false;
         if (j < nb) {
+            const float4 g = s_geo[j];
+            const float2 g2 = s_geo2[j];
             const float2 e = s_ext[j];
-            float dx = wcx - s_geo[j].x;
-            if (dx >= hw) dx -= (float)W;
-            else if (dx < -hw) dx += (float)W;
-            const float dy = wcy - s_geo[j].y;
-            hit = e.x >= 0.f && fabsf(dx) <= e.x + 7.51f && fabsf(dy) <= e.y + 0.51f;
+            h[half] = entry_reaches_block(g.x, g.y, e.x, e.y, g.z, g.w, g2.x, g2.y, wcx, wcy, W);
         }
-        if (half == 0) h0 = hit;
-        else h1 = hit;
     }
-    const uint32_t lo = __ballot_sync(0xffffffffu, h0);
-    const uint32_t hi = __ballot_sync(0xffffffffu, h1);
+    const uint32_t lo = __ballot_sync(0xffffffffu, h[0]);
+    const uint32_t hi = __ballot_sync(0xffffffffu, h[1]);
     return ((uint64_t)hi << 32) | lo;
 }
 
@@ -396,19 +429,20 @@ __device__ __forceinline__ int rs18_slot(int lane) {
 }
 
 // Shared memory of the FP32 kernels (dynamic): records, phasor tables and ids of two batches,
-// the two staging mbarriers, and (backward) the per-warp gradient partial sums of a batch.
-template <int S>
+// the two staging mbarriers and a few words.  A phasor-table element is TE bytes: the unit phasor
+// (8, forward) or the phasor beside its quarter turn (16, backward: see stage_phasors_bwd).
+template <int S, int TE = 8>
 struct F32Smem {
     static constexpr int kRec = 0;                                        // StageRec[2][kBatch]
-    static constexpr int kTab = kRec + 2 * kBatch * (int)sizeof(StageRec);  // float2[2][kBatch][S]
-    static constexpr int kGid = kTab + 2 * kBatch * S * 8;                // uint32[2][kBatch]
+    static constexpr int kTab = kRec + 2 * kBatch * (int)sizeof(StageRec);  // [2][kBatch][S] elements
+    static constexpr int kGid = kTab + 2 * kBatch * S * TE;               // uint32[2][kBatch]
     static constexpr int kBar = kGid + 2 * kBatch * 4;                    // uint64[2]
-    static constexpr int kRed = kBar + 16;                                // float[8][kBatch][9]
-    static constexpr int kMask = kRed + 8 * kBatch * 9 * 4;               // uint64[8]
-    static constexpr int kMisc = kMask + 8 * 8;                           // float[8], uint32[4]
+    static constexpr int kMisc = kBar + 16;                               // float[8], uint32[4]
     static constexpr int kTotal = kMisc + 48;
-    static_assert(kTab % 16 == 0 && kBar % 8 == 0 && kMask % 8 == 0, "shared-memory alignment");
+    static_assert(kTab % 16 == 0 && kBar % 8 == 0, "shared-memory alignment");
 };
+template <int S>
+using F32BwdSmem = F32Smem<S, 16>;
 
 // Batch i of a walk over list positions [lo, end): front to back from lo, or back to front
 // from end (the last batch then the ragged one).
@@ -527,8 +561,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_fwd(RenderArgs a) {
                 if (!__any_sync(0xffffffffu, take)) return;
                 const float wa = take ? ex2(logT) * al * rec[j].at.x : 0.f;
                 const float2 w2 = make_float2(wa, wa);
+                if constexpr (S % 2 == 0) {
+                    // two subcarriers' phasors per 16-byte broadcast read
+                    const float4* t4 = reinterpret_cast<const float4*>(s_tab[buf][j]);
 #pragma unroll
-                for (int kk = 0; kk < S; ++kk) acc[kk] = fma2(w2, s_tab[buf][j][kk], acc[kk]);
+                    for (int k2 = 0; k2 < S / 2; ++k2) {
+                        const float4 t = t4[k2];
+                        acc[2 * k2] = fma2(w2, make_float2(t.x, t.y), acc[2 * k2]);
+                        acc[2 * k2 + 1] = fma2(w2, make_float2(t.z, t.w), acc[2 * k2 + 1]);
+                    }
+                } else {
+#pragma unroll
+                    for (int kk = 0; kk < S; ++kk) acc[kk] = fma2(w2, s_tab[buf][j][kk], acc[kk]);
+                }
                 logT = take ? nt : logT;
                 last = take ? bs + (uint32_t)j + 1u : last;
                 used += take ? 1u : 0u;
@@ -619,19 +664,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_fwd(RenderArgs a) {
 // walk), or a scheduled chunk of it (a.items: item r on CTA r): a back chunk [m, walk) back to
 // front, or a front chunk [0, m) front to back from T = 1 with the suffix sum taken as
 // s_tot - prefix (s_tot = Re sum_k conj(dL/dz_k) z_k over the strip, given or formed here from
-// the spectrum).  Per list entry every pixel's nine gradient components are reduced over the
-// warp in one reduce-scatter; after each batch one atomic per (Gaussian, component) adds the
-// CTA's sum.
+// the spectrum).  A warp visits only the entries whose footprint box reaches its pixels (the set
+// bits of its entry mask, in walk order); per visited entry its pixels' nine gradient components
+// are reduced over the warp in one reduce-scatter and added to the gradients by the warp (one
+// atomic per component), so a batch needs one block barrier.
 template <int S>
 __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
-    using L = F32Smem<S>;
+    using L = F32BwdSmem<S>;
     GSPARC_DYNAMIC_SMEM(sm);
     StageRec* s_rec = reinterpret_cast<StageRec*>(sm + L::kRec);
-    float2(*s_tab)[kBatch][S] = reinterpret_cast<float2(*)[kBatch][S]>(sm + L::kTab);
+    float4(*s_tab)[kBatch][S] = reinterpret_cast<float4(*)[kBatch][S]>(sm + L::kTab);
     uint32_t* s_gid = reinterpret_cast<uint32_t*>(sm + L::kGid);
     uint64_t* s_bar = reinterpret_cast<uint64_t*>(sm + L::kBar);
-    float* s_red = reinterpret_cast<float*>(sm + L::kRed);              // [warp][kBatch][9]
-    uint64_t* s_wmask = reinterpret_cast<uint64_t*>(sm + L::kMask);
     uint32_t* s_maxlast = reinterpret_cast<uint32_t*>(sm + L::kMisc + 32);
     uint32_t* s_err = s_maxlast + 1;
 
@@ -689,6 +733,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
     }
     float logT = (inside && !front) ? a.final_logT[(size_t)b * plane + pix] : 0.f;
     const uint32_t last = inside ? a.n_contrib[(size_t)b * plane + pix] : 0u;
+    const uint32_t wlast = __reduce_max_sync(0xffffffffu, last);   // the warp's walk
     if (tid == 0) {
         stage_bar_init(&s_bar[0]);
         stage_bar_init(&s_bar[1]);
@@ -721,6 +766,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
     // dpsi/dL = -(2 pi / c) (f_strip0 + kk df)
     const float c_f0 = (float)(a.two_pi_over_c * (a.f0 + (double)k0 * a.df));
     const float c_df = (float)(a.two_pi_over_c * a.df);
+    // Gradient slot of component c: attr slots 0 a, 1 phi0, 2 sigma, 3 L for c >= 5; projection
+    // slots p_x, p_y, c_xx, c_xy, c_yy for c < 5.  A one-entry reduce-scatter leaves component
+    // lane >> 1 in the even lanes below 18; a two-entry one leaves component slot18 % 9 of the
+    // first (slot18 < 9) or the second entry in the lanes where slot18 >= 0.
+    const int slot18 = rs18_slot(lane);
+    const bool holder = (lane & 1) == 0 && (lane >> 1) < 9;
+    auto add_grad = [&](int c, uint32_t gid, float v) {
+        float* dst = c >= 5 ? reinterpret_cast<float*>(&a.d_attr[(size_t)b * a.N + gid]) +
+                                  (c == 5 ? 2 : (c == 6 ? 0 : (c == 7 ? 1 : 3)))
+                            : a.d_proj + (size_t)gid * 8 + (c < 2 ? c : c + 2);
+        atomicAdd(dst, v);
+    };
     // Back to front: acc = the sum over later composited entries of w a Re(conj(g) e^{j psi})
     // (the suffix); front to back: the same sum over the entries up to this one (suffix =
     // s_tot - acc).  The two directions differ in a few selects, not in code paths.
@@ -734,8 +791,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
             *s_err = 1u;
             stage_wait(&s_bar[buf], (uint32_t)(i >> 1) & 1u, kStagePolls);   // copies still in flight
         }
-        stage_phasors<S>(a, s_rec + buf * kBatch, nb, k0, s_tab[buf]);
-        __syncthreads();   // phasors in place; the previous batch's flush is done
+        stage_phasors_bwd<S>(a, s_rec + buf * kBatch, nb, k0, s_tab[buf]);
+        // phasors of batch i in place; every warp has finished batch i - 1, whose buffers the
+        // copies of batch i + 1 now take over
+        __syncthreads();
         if (*s_err) break;
         if (i + 1 < nbatch) {
             uint32_t n_lo;
@@ -746,33 +805,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
             pf_id = load_id(i + 2);
         }
         const StageRec* rec = s_rec + buf * kBatch;
-        const uint64_t mask = warp_entry_mask_rec(rec, nb, wcx, wcy, a.W);
-        if (lane == 0) s_wmask[warp] = mask;
-        for (int jj = 0; jj < kBatch; ++jj) {
-            const int j = front ? jj : kBatch - 1 - jj;
-            if (!((mask >> j) & 1ull)) continue;   // warp-uniform: the entry misses the warp
+        const uint32_t* gids = s_gid + buf * kBatch;
+        uint64_t bits = warp_entry_mask_rec(rec, nb, wcx, wcy, a.W);
+        // positions at or past every pixel's n_contrib are live at none of the warp's pixels
+        if (b_lo >= wlast) bits = 0ull;
+        else if (wlast - b_lo < (uint32_t)kBatch) bits &= (1ull << (wlast - b_lo)) - 1ull;
+        // the gradient components of a visited entry wait in pend until a second one arrives, and
+        // the two are reduced over the warp together
+        float pend[9];
+        int pend_j = -1;
+        while (bits) {   // warp-uniform
+            const int j = front ? __ffsll((long long)bits) - 1 : 63 - __clzll((long long)bits);
+            bits &= ~(1ull << j);
             const StageRec& r = rec[j];
             const float4 gg = make_float4(r.p0.x, r.p0.y, r.p1.x, r.p1.y);
             const float2 g2 = make_float2(r.p1.z, r.at.z);
             float dx = 0.f, dy = 0.f, G = 0.f, alpha = 0.f;
             bool clamped = false;
             const bool live = b_lo + (uint32_t)j < last && eval_alpha(ux, uy, a.W, gg, g2, dx, dy, G, alpha, clamped);
-            if (!__any_sync(0xffffffffu, live)) {
-                if (lane < 9) s_red[(warp * kBatch + j) * 9 + lane] = 0.f;
-                continue;
-            }
-            // Re as two independent FMA chains (the real and the imaginary products), so that no
-            // sum is a chain of two dependent FMAs per subcarrier
-            // (the two Re chains and the Im, kk-weighted Im pair each as one paired FMA)
-            float2 re2 = make_float2(0.f, 0.f), im2 = make_float2(0.f, 0.f);   // (Re a, Re b), (Im G, Im F)
+            if (!__any_sync(0xffffffffu, live)) continue;
+            // Per subcarrier, from the last down: one 16-byte broadcast read and three paired
+            // operations.  re2 sums Re(conj(g) t) as two chains (g.x t.x and g.y t.y); suf2 sums
+            // Im(conj(g) t) (g.x t.y and -g.y t.x) over the subcarriers from kk up, and tot2 adds
+            // those suffix sums for kk >= 1, which is sum_kk kk Im_kk.
+            float2 re2 = make_float2(0.f, 0.f), suf2 = make_float2(0.f, 0.f), tot2 = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int kk = 0; kk < S; ++kk) {
-                const float2 t = s_tab[buf][j][kk];
-                re2 = fma2(g[kk], t, re2);
-                const float pi_ = fmaf(g[kk].x, t.y, -g[kk].y * t.x);
-                im2 = fma2(make_float2(pi_, pi_), make_float2(1.0f, (float)kk), im2);
+            for (int kk = S - 1; kk >= 0; --kk) {
+                const float4 t = s_tab[buf][j][kk];
+                re2 = fma2(g[kk], make_float2(t.x, t.y), re2);
+                suf2 = fma2(g[kk], make_float2(t.z, t.w), suf2);
+                if (kk > 0) tot2 = add2(tot2, suf2);
             }
-            const float reG = re2.x + re2.y, imG = im2.x, imF = im2.y;
+            const float reG = re2.x + re2.y, imG = suf2.x + suf2.y, imF = tot2.x + tot2.y;
             float gr[9];
 #pragma unroll
             for (int c = 0; c < 9; ++c) gr[c] = 0.f;
@@ -787,7 +851,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
                 const float w = T * alpha;
                 const float acc_next = fmaf(w, reGa, acc);
                 const float suffix = front ? s_tot - acc_next : acc;
-                const float dalpha = T * reGa - suffix / (1.0f - alpha);
+                // 1 - alpha >= 0.01: the approximate quotient (2 ulp) is ample for a gradient term
+                const float dalpha = T * reGa - __fdividef(suffix, 1.0f - alpha);
                 acc = acc_next;
                 logT = logT_next;
                 gr[6] = w * reG;                                  // d a
@@ -804,32 +869,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
                     gr[4] = dq * dy * dy;                             // d c_yy
                 }
             }
-            // reduce-scatter of the 9 components over the warp: lane l ends with the warp total
-            // of component l >> 1
-            const float tot = warp_reduce_scatter9(gr, lane);
-            if ((lane & 1) == 0 && (lane >> 1) < 9) s_red[(warp * kBatch + j) * 9 + (lane >> 1)] = tot;
-        }
-        __syncthreads();
-        // one atomic per (Gaussian, component) for the whole CTA
-        const uint32_t* gids = s_gid + buf * kBatch;
-        for (int e = tid; e < nb * 9; e += kThreads) {
-            const int j = e / 9, c = e - j * 9;
-            float v = 0.f;
+            if (pend_j < 0) {
 #pragma unroll
-            for (int w2 = 0; w2 < kThreads / 32; ++w2)
-                if ((s_wmask[w2] >> j) & 1ull) v += s_red[(w2 * kBatch + j) * 9 + c];
-            if (v != 0.f) {
-                const uint32_t gid = gids[j];
-                if (c >= 5) {
-                    float* dst = reinterpret_cast<float*>(&a.d_attr[(size_t)b * a.N + gid]);
-                    // attr slots: 0 a, 1 phi0, 2 sigma, 3 L
-                    const int slot = c == 5 ? 2 : (c == 6 ? 0 : (c == 7 ? 1 : 3));
-                    atomicAdd(dst + slot, v);
-                } else {
-                    const int slot = c < 2 ? c : c + 2;   // p_x, p_y, -, -, c_xx, c_xy, c_yy
-                    atomicAdd(a.d_proj + (size_t)gid * 8 + slot, v);
-                }
+                for (int c = 0; c < 9; ++c) pend[c] = gr[c];
+                pend_j = j;
+                continue;
             }
+            // reduce-scatter of both entries' 18 components over the warp; the lane holding one
+            // adds it to the gradient
+            float v[18];
+#pragma unroll
+            for (int c = 0; c < 9; ++c) {
+                v[c] = pend[c];
+                v[9 + c] = gr[c];
+            }
+            const float tot = warp_reduce_scatter18(v, lane);
+            if (slot18 >= 0 && tot != 0.f) add_grad(slot18 % 9, slot18 < 9 ? gids[pend_j] : gids[j], tot);
+            pend_j = -1;
+        }
+        if (pend_j >= 0) {
+            const float tot = warp_reduce_scatter9(pend, lane);
+            if (holder && tot != 0.f) add_grad(lane >> 1, gids[pend_j], tot);
         }
     }
     if (*s_err && tid == 0) set_status(a.status, GSPARC_ERR_TIMEOUT);

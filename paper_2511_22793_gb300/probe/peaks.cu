@@ -71,31 +71,32 @@ extern "C" int64_t gsparc_probe_launch(int kind, int blocks, int iters, float* o
     return (int64_t)blocks * 256 * iters * 4 * kChains;
 }
 
-// The paired FP32 FMA the FP32 compositing kernels use (fma.rn.f32x2) against two scalar fmaf on
-// the same operands: out_pair[i] from the paired instruction, out_scalar[i] from fmaf, for n float2
-// elements of a, b, c (device).  The two must agree bit for bit.
+// The paired FP32 operations the FP32 compositing kernels use (the runtime's __ffma2_rn and
+// __fadd2_rn) against scalar fmaf and + on the same operands: out_pair[i] = __ffma2_rn(a, b, c) and
+// out_scalar[i] = fmaf per element; with add != 0, __fadd2_rn(a, b) against a + b instead.  The two
+// must agree bit for bit.
 namespace {
-__global__ void k_fma2_check(int n, const float2* a, const float2* b, const float2* c, float2* out_pair,
+__global__ void k_fma2_check(int n, int add, const float2* a, const float2* b, const float2* c, float2* out_pair,
                              float2* out_scalar) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float2 x = a[i], y = b[i], z = c[i];
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-        "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(x.x), "f"(x.y), "f"(y.x), "f"(y.y), "f"(z.x), "f"(z.y));
-    out_pair[i] = d;
-    out_scalar[i] = make_float2(fmaf(x.x, y.x, z.x), fmaf(x.y, y.y, z.y));
+    if (add) {
+        out_pair[i] = __fadd2_rn(x, y);
+        out_scalar[i] = make_float2(__fadd_rn(x.x, y.x), __fadd_rn(x.y, y.y));
+    } else {
+        out_pair[i] = __ffma2_rn(x, y, z);
+        out_scalar[i] = make_float2(fmaf(x.x, y.x, z.x), fmaf(x.y, y.y, z.y));
+    }
 }
 }  // namespace
 
-extern "C" int gsparc_probe_fma2_check(int n, const float* a, const float* b, const float* c, float* out_pair,
-                                       float* out_scalar, void* stream) {
+extern "C" int gsparc_probe_fma2_check(int n, int add, const float* a, const float* b, const float* c,
+                                       float* out_pair, float* out_scalar, void* stream) {
     if (n < 0 || (n > 0 && (!a || !b || !c || !out_pair || !out_scalar))) return -1;
     if (n == 0) return 0;
     k_fma2_check<<<(n + 255) / 256, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        n, reinterpret_cast<const float2*>(a), reinterpret_cast<const float2*>(b), reinterpret_cast<const float2*>(c),
+        n, add, reinterpret_cast<const float2*>(a), reinterpret_cast<const float2*>(b), reinterpret_cast<const float2*>(c),
         reinterpret_cast<float2*>(out_pair), reinterpret_cast<float2*>(out_scalar));
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -33,7 +33,7 @@ static void render_fwd(const gsparc::RenderArgs& a, int T) {
 template <int S>
 static void render_bwd(const gsparc::RenderArgs& a, int T) {
     emu_launch_smem(emu_dim3{(unsigned)((a.K + S - 1) / S), (unsigned)T, (unsigned)a.B}, gsparc::kThreads,
-                    gsparc::F32Smem<S>::kTotal, gsparc::k_render_bwd<S>, a);
+                    gsparc::F32BwdSmem<S>::kTotal, gsparc::k_render_bwd<S>, a);
 }
 template <int HD>
 static void mlp(int n, int B, const float* tx, const float* means, const float* ologit, const float* latent,

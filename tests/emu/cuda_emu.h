@@ -72,6 +72,7 @@ inline float __fadd_rn(float a, float b) { return a + b; }
 inline float __fsub_rn(float a, float b) { return a - b; }
 inline float __fmul_rn(float a, float b) { return a * b; }
 inline float __fmaf_rn(float a, float b, float c) { return fmaf(a, b, c); }
+inline float __fdividef(float a, float b) { return a / b; }   // the device's is an approximation
 inline void __sincosf(float x, float* s, float* c) { sincosf(x, s, c); }
 inline float __int_as_float(int i) {
     float f;

@@ -21,7 +21,7 @@ template <int S>
 static void run(const gsparc::RenderArgs& a, int T) {
     const emu_dim3 grid{(unsigned)((a.K + S - 1) / S), (unsigned)T, (unsigned)a.B};
     emu_launch_smem(grid, gsparc::kThreads, gsparc::F32Smem<S>::kTotal, gsparc::k_render_fwd<S>, a);
-    emu_launch_smem(grid, gsparc::kThreads, gsparc::F32Smem<S>::kTotal, gsparc::k_render_bwd<S>, a);
+    emu_launch_smem(grid, gsparc::kThreads, gsparc::F32BwdSmem<S>::kTotal, gsparc::k_render_bwd<S>, a);
 }
 
 int main(int argc, char** argv) {

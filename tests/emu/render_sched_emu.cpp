@@ -28,7 +28,7 @@ static void fwd(const gsparc::RenderArgs& a, int T) {
 }
 template <int S>
 static void bwd(const gsparc::RenderArgs& a, unsigned items) {
-    emu_launch_smem(emu_dim3{items, 1, 1}, gsparc::kThreads, gsparc::F32Smem<S>::kTotal, gsparc::k_render_bwd<S>, a);
+    emu_launch_smem(emu_dim3{items, 1, 1}, gsparc::kThreads, gsparc::F32BwdSmem<S>::kTotal, gsparc::k_render_bwd<S>, a);
 }
 
 int main(int argc, char** argv) {

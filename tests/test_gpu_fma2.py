@@ -1,6 +1,7 @@
-"""The paired FP32 FMA (fma.rn.f32x2) the FP32 compositing kernels use in their subcarrier loops
-is two IEEE single-precision fused multiply-adds: on random operands (normal values, mixed
-magnitudes and signs, signed zeros, subnormals) it agrees bit for bit with two scalar fmaf."""
+"""The paired FP32 FMA and add (__ffma2_rn, __fadd2_rn) the FP32 compositing kernels use in their
+subcarrier loops are two IEEE single-precision fused multiply-adds / additions: on random operands
+(normal values, mixed magnitudes and signs, signed zeros, subnormals) they agree bit for bit with
+two scalar fmaf / additions."""
 import ctypes
 import os
 
@@ -12,10 +13,11 @@ pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_paired_fma_is_two_fmaf_bit_for_bit():
+@pytest.mark.parametrize("add", [0, 1])
+def test_paired_fma_is_two_fmaf_bit_for_bit(add):
     lib = ctypes.CDLL(os.path.join(ROOT, "paper_2511_22793_gb300", "libgsparc_probe.so"))
     lib.gsparc_probe_fma2_check.restype = ctypes.c_int
-    lib.gsparc_probe_fma2_check.argtypes = [ctypes.c_int] + [ctypes.c_void_p] * 6
+    lib.gsparc_probe_fma2_check.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 6
     rng = np.random.default_rng(8)
     n = 1 << 20
     ops = []
@@ -27,7 +29,7 @@ def test_paired_fma_is_two_fmaf_bit_for_bit():
         ops.append(torch.tensor(x.astype(np.float32), device="cuda"))
     pair = torch.empty_like(ops[0])
     scal = torch.empty_like(ops[0])
-    rc = lib.gsparc_probe_fma2_check(n, *[ctypes.c_void_p(t.data_ptr()) for t in ops], ctypes.c_void_p(pair.data_ptr()),
+    rc = lib.gsparc_probe_fma2_check(n, add, *[ctypes.c_void_p(t.data_ptr()) for t in ops], ctypes.c_void_p(pair.data_ptr()),
                                      ctypes.c_void_p(scal.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     torch.cuda.synchronize()
     assert rc == 0
