@@ -146,12 +146,14 @@ int gsparc_bin_sort_workspace(const gsparc_view* view, int32_t N, int64_t pair_c
  * (azimuth wrapping at +-pi) each get one (Gaussian, tile) pair; every tile's
  * list is ordered by (r, index).  The pairs are counted per tile, emitted into
  * per-tile buckets as the unique 64-bit keys (bits(r) << 32) | index, and
- * each bucket is sorted by its own thread block: in shared memory up to
- * 24576 pairs, by a distribution sort over 4096 depth sub-buckets (each key
- * ranked against the few keys of its sub-bucket), and by an LSD radix sort
- * (8-bit digits, only the bytes that vary in the bucket) for larger buckets,
- * in the workspace, or when the depths are too concentrated for the
- * sub-buckets.
+ * each bucket is sorted by its own thread block: up to 24576 pairs in shared
+ * memory, by a distribution sort over 8192 depth sub-buckets (each key ranked
+ * against the few keys of its sub-bucket); a larger bucket by the same sort
+ * over 16384 sub-buckets, either cut into slices of about 12288 pairs sorted
+ * in shared memory by blocks of their own (when there are fewer tiles than
+ * SMs) or whole with its keys scattered in the workspace; an LSD radix sort
+ * (8-bit digits, only the bytes that vary in the bucket, in the workspace)
+ * when the depths are too concentrated for the sub-buckets.
  *   proj [N,8]: records from gsparc_project (only p, ext and r are read).
  *   ws: device workspace of ws_bytes >= gsparc_bin_sort_workspace().
  *   sorted_ids [pair_capacity] out: Gaussian id of each sorted pair.

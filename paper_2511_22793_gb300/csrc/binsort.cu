@@ -17,7 +17,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // counts are kept in shared memory (ntiles <= kSmemTiles) and with_bcnt is set; bcnt == 0 then
 // means "not laid out".
 struct Layout {
-    size_t cnt, cursor, done, keys, alt, bcnt, total;
+    size_t cnt, cursor, done, keys, alt, extra, bcnt, total;
     int nblk;
 };
 
@@ -30,6 +30,7 @@ Layout layout(int N, int64_t cap, int ntiles, bool with_bcnt = true) {
     L.cursor = o; o += align256((size_t)ntiles * 4);
     L.keys = o;   o += align256((size_t)cap * 8);
     L.alt = o;    o += align256((size_t)cap * 8);
+    L.extra = o;  o += align256((size_t)(ntiles + 1) * 4);
     L.bcnt = 0;
     if (with_bcnt && ntiles <= kSmemTiles && N > 0) {
         L.bcnt = o;
@@ -49,6 +50,7 @@ int bin_sort_launch(const gsparc_view* view, int N, const float* proj, int64_t p
     uint32_t* cursor = reinterpret_cast<uint32_t*>(w + L.cursor);
     uint64_t* keys = reinterpret_cast<uint64_t*>(w + L.keys);
     uint64_t* alt = reinterpret_cast<uint64_t*>(w + L.alt);
+    uint32_t* extra = reinterpret_cast<uint32_t*>(w + L.extra);
     uint32_t* bcnt = L.bcnt ? reinterpret_cast<uint32_t*>(w + L.bcnt) : nullptr;
     const uint32_t cap = (uint32_t)pair_capacity;
     if (N == 0) {
@@ -63,10 +65,11 @@ int bin_sort_launch(const gsparc_view* view, int N, const float* proj, int64_t p
     const float4* p4 = reinterpret_cast<const float4*>(proj);
     uint2* ranges = reinterpret_cast<uint2*>(tile_ranges);
     k_tile_count<<<L.nblk, kBinThreads, 0, s>>>(N, view->H, view->W, TW, T, p4, cnt, bcnt, cursor, done, cap,
-                                                ranges, n_pairs, d_status);
+                                                ranges, n_pairs, extra, slice_big_buckets(T, num_sms()) ? 1 : 0,
+                                                d_status);
     k_tile_emit<<<L.nblk, kBinThreads, 0, s>>>(N, view->H, view->W, TW, T, p4, bcnt, cursor, cap, keys);
-    const int grid = std::min(T, num_sms() * 8);
-    k_tile_sort<<<grid, kSortThreads, kSortSmem, s>>>(T, ranges, keys, alt, sorted_ids, sorted_keys);
+    k_tile_sort<<<sort_grid(T, cap), kSortThreads, kSortSmem, s>>>(T, ranges, extra, keys, alt, sorted_ids,
+                                                                   sorted_keys);
     return launch_status();
 }
 
@@ -112,7 +115,7 @@ namespace {
 
 // covers layout(N, GSPARC_NOALLOC_MAX_PAIRS, T) for up to 65536 tiles
 constexpr size_t kNoAllocBytes = size_t(9) << 20;
-static_assert(size_t(GSPARC_NOALLOC_MAX_PAIRS) * 16 + 65536 * 8 + 4096 <= kNoAllocBytes,
+static_assert(size_t(GSPARC_NOALLOC_MAX_PAIRS) * 16 + 65536 * 12 + 8192 <= kNoAllocBytes,
               "no-alloc scratch below the documented limits");
 constexpr int kMaxDevices = 64;
 

@@ -17,8 +17,10 @@
 //                 the order inside a bucket is arbitrary)
 //   k_tile_sort   one CTA per tile: a distribution sort by depth (each key ranked
 //                 against the few keys of its sub-bucket), up to kSortCap keys in
-//                 shared memory over kSubBuckets sub-buckets, above that over
-//                 kSubBig sub-buckets with the keys scattered in global memory;
+//                 shared memory over kSubBuckets sub-buckets; a bucket above kSortCap keys
+//                 is cut into slices of about kSlice keys at boundaries of kSubBig depth
+//                 sub-buckets, each slice sorted in shared memory by its own CTA (the
+//                 tile's block and blocks past the tiles, from a work list of k_tile_count);
 //                 when a sub-bucket holds too many keys (many equal depths), an
 //                 LSD radix sort (8-bit digits, warp-match ranking, only the
 //                 bytes that vary in the bucket), in a global ping-pong buffer
@@ -48,6 +50,18 @@ constexpr int kSubBuckets = 8192;                   // sub-buckets of the in-til
 constexpr int kSubMax = 64;                         // largest sub-bucket ranked by comparison
 constexpr int kSubBig = 16384;                      // sub-buckets of a bucket above kSortCap keys
 constexpr int kSubMaxBig = 256;                     // largest such sub-bucket ranked by comparison
+constexpr int kSlice = 12288;                       // keys per slice of such a bucket, about
+
+// Slices of a bucket of n keys beyond its first (its tile's own block takes slice 0): none up to
+// kSortCap keys.
+__device__ __host__ __forceinline__ uint32_t extra_slices(uint32_t n) {
+    return n > (uint32_t)kSortCap ? (n + kSlice - 1) / kSlice - 1u : 0u;
+}
+// Buckets above kSortCap keys are sliced only when the tiles alone leave SMs idle; otherwise each
+// is sorted by its tile's block (keys scattered in global memory), which moves fewer bytes.
+inline bool slice_big_buckets(int T, int sms) { return T < sms; }
+// Blocks of a k_tile_sort launch: one per tile and one per extra slice of a list of cap pairs.
+inline uint32_t sort_grid(int T, uint32_t cap) { return (uint32_t)T + cap / kSlice; }
 static_assert(kSortThreads >= 256, "the digit scan gives one thread per digit");
 static_assert(kSortWarps * 256 == kSubBuckets, "histogram array shared by both in-tile sorts");
 
@@ -156,7 +170,8 @@ __device__ __forceinline__ void warp_pairs(bool valid, const Foot& f, int TW, F&
 // block to finish turns the counts into bucket offsets:
 // cursor[t] = start of tile t, tile_ranges[t] = [start, end) ([0, 0) when the bucket is
 // empty or does not fit below cap), n_pairs = total (saturated at 2^32-1), GSPARC_ERR_CAPACITY if the
-// total exceeds cap.
+// total exceeds cap, and the sort's extra slices (none unless slice_big): extra[t] = the first extra
+// slice of tile t (an exclusive scan of extra_slices over the tile ranges), extra[T] = their number.
 __global__ void __launch_bounds__(kBinThreads) k_tile_count(int N, int H, int W, int TW, int T,
                                                             const float4* __restrict__ proj,
                                                             uint32_t* __restrict__ cnt,
@@ -165,6 +180,7 @@ __global__ void __launch_bounds__(kBinThreads) k_tile_count(int N, int H, int W,
                                                             uint32_t* __restrict__ done, uint32_t cap,
                                                             uint2* __restrict__ ranges,
                                                             uint32_t* __restrict__ n_pairs,
+                                                            uint32_t* __restrict__ extra, int slice_big,
                                                             int32_t* status) {
     __shared__ uint32_t s_cnt[kSmemTiles];
     __shared__ uint32_t s_warp[kBinThreads / 32];
@@ -227,7 +243,34 @@ __global__ void __launch_bounds__(kBinThreads) k_tile_count(int N, int H, int W,
         const uint64_t tot = s_carry;
         n_pairs[0] = (uint32_t)(tot > 0xffffffffull ? 0xffffffffull : tot);
         if (tot > cap) set_status(status, GSPARC_ERR_CAPACITY);
+        s_carry = 0;
     }
+    __syncthreads();
+    // the extra slices of buckets above kSortCap keys (ranges written above by this thread)
+    for (int base = 0; base < T; base += kBinThreads) {
+        const int t = base + threadIdx.x;
+        uint32_t v = 0;
+        if (t < T) {
+            const uint2 rg = ranges[t];
+            v = slice_big ? extra_slices(rg.y - rg.x) : 0u;
+        }
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        uint64_t before = s_carry;
+        for (int w = 0; w < warp; ++w) before += s_warp[w];
+        if (t < T) extra[t] = (uint32_t)(before + x - v);
+        const uint64_t end = before + x;
+        __syncthreads();
+        if (threadIdx.x == kBinThreads - 1) s_carry = end;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) extra[T] = (uint32_t)s_carry;
 }
 
 // Every pair's key (bits(r) << 32) | index into its tile's bucket.  A block reserves one
@@ -527,14 +570,137 @@ __device__ __forceinline__ bool sort_big_bucket(const uint64_t* src, uint64_t* a
     return true;
 }
 
-// One CTA per tile (grid-stride over tiles).  A bucket of up to kSortCap keys is sorted by
-// distribution: keys are counted into kSubBuckets sub-buckets by depth, scattered to their
-// sub-bucket in shared memory (arbitrary order inside it), and each key's final place is
-// its sub-bucket's start plus the number of smaller keys in the same sub-bucket (the keys
-// are unique, so the places are distinct).  A bucket above kSortCap keys, or one whose
-// largest sub-bucket exceeds kSubMax keys (many equal depths), takes the LSD radix sort in
-// global memory with `alt` as the second buffer.
+// fn(key) over the keys src[0, n), four loads in flight per thread.
+template <class F>
+__device__ __forceinline__ void for_keys4(const uint64_t* src, int n, F&& fn) {
+    for (int j0 = threadIdx.x; j0 < n; j0 += 4 * kSortThreads) {
+        uint64_t k[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u * kSortThreads;
+            k[u] = j < n ? __ldcg(src + j) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (j0 + u * kSortThreads < n) fn(k[u]);
+    }
+}
+
+// Slice c of a bucket of n > kSortCap keys (src, its first list position base): the keys are
+// counted into kSubBig depth sub-buckets (hist, in the block's key buffer; the map over the
+// bucket's depth range, the same in every slice), the counts scanned, and the slice is the run
+// of sub-buckets whose starts fall in [c n / P, (c + 1) n / P) for P slices.  Its keys are
+// gathered into shared memory (buf) by sub-bucket and each is placed at its sub-bucket's start
+// plus the number of smaller keys there.  Returns false, having written nothing, when a
+// sub-bucket holds more than kSubMaxBig keys (then slice 0 takes the radix sort and the others
+// nothing).
+__device__ __forceinline__ bool sort_slice(const uint64_t* src, int n, uint32_t c, uint32_t base, int tile,
+                                           SortShared& sh, uint32_t* hist, uint64_t* buf, uint32_t* sorted_ids,
+                                           uint64_t* sorted_keys) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t P = extra_slices((uint32_t)n) + 1u;
+    if (threadIdx.x == 0) {
+        sh.dmin = 0xffffffffu;
+        sh.dmax = 0u;
+        sh.maxb = 0u;
+    }
+    for (int e = threadIdx.x; e < kSubBig; e += kSortThreads) hist[e] = 0;
+    __syncthreads();
+    uint32_t lo = 0xffffffffu, hi = 0u;
+    for_keys4(src, n, [&](uint64_t k) {
+        const uint32_t d = (uint32_t)(k >> 32);
+        lo = min(lo, d);
+        hi = max(hi, d);
+    });
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) {
+        atomicMin(&sh.dmin, lo);
+        atomicMax(&sh.dmax, hi);
+    }
+    __syncthreads();
+    const SubMap sm = sub_map(sh.dmin, sh.dmax, kSubBig);
+    for_keys4(src, n, [&](uint64_t k) { atomicAdd(&hist[sub_bucket(k, sm, kSubBig)], 1u); });
+    __syncthreads();
+    constexpr int kPer = kSubBig / kSortThreads;
+    {
+        uint32_t sum = 0, mx = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t v = hist[threadIdx.x * kPer + q];
+            sum += v;
+            mx = max(mx, v);
+        }
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if (lane == 0) atomicMax(&sh.maxb, mx);
+        uint32_t off = sort_block_scan(sum, sh.warp_sum);
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t v = hist[threadIdx.x * kPer + q];
+            hist[threadIdx.x * kPer + q] = off;   // the start of the sub-bucket
+            off += v;
+        }
+    }
+    if (threadIdx.x == 0) {
+        sh.dmin = (uint32_t)kSubBig;   // first sub-bucket of the slice
+        sh.dmax = (uint32_t)kSubBig;   // first sub-bucket of the next slice
+    }
+    __syncthreads();
+    if (sh.maxb > (uint32_t)kSubMaxBig) {
+        __syncthreads();
+        return false;
+    }
+    // sub-bucket b opens slice s when its start times P first reaches s n (empty sub-buckets
+    // hold no keys, so which slice they fall in does not matter)
+    {
+        const uint64_t t0 = (uint64_t)c * (uint32_t)n, t1 = (uint64_t)(c + 1) * (uint32_t)n;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int b = threadIdx.x * kPer + q;
+            const uint64_t st = (uint64_t)hist[b] * P;
+            const uint64_t pv = b > 0 ? (uint64_t)hist[b - 1] * P : 0ull;
+            if (st >= t0 && (b == 0 || pv < t0)) sh.dmin = (uint32_t)b;
+            if (st >= t1 && (b == 0 || pv < t1)) sh.dmax = (uint32_t)b;
+        }
+    }
+    __syncthreads();
+    const int b_lo = (int)sh.dmin, b_hi = (int)sh.dmax;
+    const uint32_t s_lo = b_lo < kSubBig ? hist[b_lo] : (uint32_t)n;
+    const uint32_t s_hi = b_hi < kSubBig ? hist[b_hi] : (uint32_t)n;
+    const int m = (int)(s_hi - s_lo);   // <= n / P + kSubMaxBig
+    __syncthreads();   // every thread has read the slice's starts before the gather moves them
+    for_keys4(src, n, [&](uint64_t k) {
+        const int b = sub_bucket(k, sm, kSubBig);
+        if (b >= b_lo && b < b_hi) buf[atomicAdd(&hist[b], 1u) - s_lo] = k;
+    });
+    __syncthreads();
+    // hist[b] is now the end of sub-bucket b (= the start of b + 1) inside the slice
+    for (int p = threadIdx.x; p < m; p += kSortThreads) {
+        const uint64_t k = buf[p];
+        const int b = sub_bucket(k, sm, kSubBig);
+        const int s0 = (b > b_lo ? (int)hist[b - 1] : (int)s_lo) - (int)s_lo;
+        const int e0 = (int)hist[b] - (int)s_lo;
+        int rank = 0;
+        for (int q = s0; q < e0; ++q) rank += buf[q] < k;
+        const uint32_t dst = base + s_lo + (uint32_t)(s0 + rank);
+        sorted_ids[dst] = (uint32_t)k;
+        if (sorted_keys) sorted_keys[dst] = ((uint64_t)tile << 32) | (k >> 32);
+    }
+    __syncthreads();
+    return true;
+}
+
+// Block t < T sorts tile t's bucket: up to kSortCap keys by distribution (keys counted into
+// kSubBuckets sub-buckets by depth, scattered to their sub-bucket in shared memory in arbitrary
+// order inside it, each key's final place its sub-bucket's start plus the number of smaller keys
+// in the same sub-bucket; the keys are unique, so the places are distinct); above kSortCap keys
+// slice 0 of the bucket (sort_slice) when the bucket is sliced, else the whole bucket with its keys
+// scattered in global memory (sort_big_bucket).  Block T + e takes extra slice e of the work list of
+// k_tile_count (blocks past its end return).  A bucket whose largest sub-bucket is too large (many
+// equal depths) takes the LSD radix sort in global memory with `alt` as the second buffer (its
+// first block; the other slices of such a bucket return).
 __global__ void __launch_bounds__(kSortThreads, 1) k_tile_sort(int T, const uint2* __restrict__ ranges,
+                                                               const uint32_t* __restrict__ extra,
                                                                uint64_t* __restrict__ keys,
                                                                uint64_t* __restrict__ alt,
                                                                uint32_t* __restrict__ sorted_ids,
@@ -543,13 +709,49 @@ __global__ void __launch_bounds__(kSortThreads, 1) k_tile_sort(int T, const uint
     SortShared& sh = *reinterpret_cast<SortShared*>(smem_raw);
     uint64_t* buf = reinterpret_cast<uint64_t*>(smem_raw + ((sizeof(SortShared) + 15) & ~size_t(15)));
     const int lane = threadIdx.x & 31;
-    for (int tile = blockIdx.x; tile < T; tile += gridDim.x) {
+    int tile;
+    uint32_t slice = 0;
+    if ((int)blockIdx.x < T) {
+        tile = (int)blockIdx.x;
+    } else {
+        const uint32_t e = blockIdx.x - (uint32_t)T;
+        if (e >= __ldg(&extra[T])) return;   // the whole block
+        // the tile: the last t with extra[t] <= e (tiles without extra slices repeat the next offset)
+        int lo = 0, hi = T - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&extra[mid]) <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        tile = lo;
+        slice = 1u + e - __ldg(&extra[tile]);
+    }
+    {
         const uint2 r = ranges[tile];
         const int n = (int)(r.y - r.x);
-        if (n <= 0) continue;
+        if (n <= 0) return;
         const uint64_t* src = keys + r.x;
-        bool radix = n > kSortCap;
-        if (!radix) {
+        if (n > kSortCap) {
+            // the slice's keys in the front of the buffer, the kSubBig counters behind them
+            static_assert((size_t)(kSlice + kSubMaxBig) * 8 + kSubBig * 4 <= (size_t)kSortCap * 8,
+                          "slice keys and large-bucket histogram in the key buffer");
+            uint32_t* hist = reinterpret_cast<uint32_t*>(buf + kSlice + kSubMaxBig);
+            const bool sliced = __ldg(&extra[tile + 1]) > __ldg(&extra[tile]);
+            if (sliced ? sort_slice(src, n, slice, r.x, tile, sh, hist, buf, sorted_ids, sorted_keys)
+                       : sort_big_bucket(src, alt + r.x, n, r.x, tile, sh, reinterpret_cast<uint32_t*>(buf),
+                                         sorted_ids, sorted_keys))
+                return;
+            if (slice != 0) return;   // the whole block: slice 0 takes the radix sort
+            const uint64_t* res = sort_bucket(keys + r.x, alt + r.x, n, sh);
+            for (int j = threadIdx.x; j < n; j += kSortThreads) {
+                const uint64_t k = res[j];
+                sorted_ids[r.x + j] = (uint32_t)k;
+                if (sorted_keys) sorted_keys[r.x + j] = ((uint64_t)tile << 32) | (k >> 32);
+            }
+            return;
+        }
+        bool radix = false;
+        {
             if (threadIdx.x == 0) {
                 sh.dmin = 0xffffffffu;
                 sh.dmax = 0u;
@@ -614,10 +816,6 @@ __global__ void __launch_bounds__(kSortThreads, 1) k_tile_sort(int T, const uint
             }
             __syncthreads();
         }
-        if (radix && n > kSortCap &&
-            sort_big_bucket(src, alt + r.x, n, r.x, tile, sh, reinterpret_cast<uint32_t*>(buf), sorted_ids,
-                            sorted_keys))
-            radix = false;
         if (radix) {
             const uint64_t* res = sort_bucket(keys + r.x, alt + r.x, n, sh);
             for (int j = threadIdx.x; j < n; j += kSortThreads) {
@@ -625,7 +823,6 @@ __global__ void __launch_bounds__(kSortThreads, 1) k_tile_sort(int T, const uint
                 sorted_ids[r.x + j] = (uint32_t)k;
                 if (sorted_keys) sorted_keys[r.x + j] = ((uint64_t)tile << 32) | (k >> 32);
             }
-            __syncthreads();
         }
     }
 }

@@ -1,11 +1,14 @@
 // Runs the library's binning and sorting kernels (csrc/binsort.cuh) under the host shim with the
 // launch sequence of gsparc_bin_sort: tile counters and ticket zeroed, k_tile_count and
-// k_tile_emit over blocks of kBinThreads records, k_tile_sort over min(T, 4) blocks (its
-// grid-stride loop over the tiles; the library launches min(T, 8 x SMs)) with the
-// kernel's dynamic shared memory.
-// With with_bcnt, k_tile_count also writes the per-(block, tile) counts and k_tile_emit takes
-// them instead of counting for itself (the library's path when T <= kSmemTiles).
-// Input: int32 N, H, W, capacity, with_bcnt; float proj[8N].  Output: uint32 n_pairs; int32
+// k_tile_emit over blocks of kBinThreads records, k_tile_sort over sort_grid(T, capacity) blocks
+// (one per tile, then the extra slices of buckets above kSortCap keys; blocks past the work list
+// return) with the kernel's dynamic shared memory.
+// With with_bcnt (bit 0 of the fifth header word), k_tile_count also writes the per-(block, tile)
+// counts and k_tile_emit takes them instead of counting for itself (the library's path when
+// T <= kSmemTiles).  Bit 1 turns off the slicing of buckets above kSortCap keys (the library's
+// choice when there are at least as many tiles as SMs): each is then sorted whole by its tile's
+// block.
+// Input: int32 N, H, W, capacity, flags; float proj[8N].  Output: uint32 n_pairs; int32
 // status; uint32 tile_ranges[2T]; uint32 sorted_ids[capacity]; uint64 sorted_keys[capacity];
 // int32 violations.
 #include <stdio.h>
@@ -26,7 +29,7 @@ int main(int argc, char** argv) {
     if (N && fread(proj.data(), 16, 2 * (size_t)N, f) != 2 * (size_t)N) return 2;
     fclose(f);
     const int TW = (W + 15) / 16, TH = (H + 15) / 16, T = TW * TH;
-    std::vector<uint32_t> cnt(T, 0u), cursor(T, 0u), ids(cap, 0xffffffffu), done(4, 0u);
+    std::vector<uint32_t> cnt(T, 0u), cursor(T, 0u), ids(cap, 0xffffffffu), done(4, 0u), extra(T + 1, 0xdeadbeefu);
     std::vector<uint2> ranges(T, uint2{0xffffffffu, 0xffffffffu});
     std::vector<uint64_t> keys(cap > 0 ? cap : 1), alt(cap > 0 ? cap : 1), skeys(cap, ~0ull);
     uint32_t n_pairs = 0xffffffffu;
@@ -37,16 +40,17 @@ int main(int argc, char** argv) {
     } else {
         using namespace gsparc;
         const unsigned nblk = (unsigned)((N + kBinThreads - 1) / kBinThreads);
-        const bool with_bcnt = hdr[4] != 0 && T <= kSmemTiles;
+        const bool with_bcnt = (hdr[4] & 1) != 0 && T <= kSmemTiles;
+        const int slice_big = (hdr[4] & 2) ? 0 : 1;   // bit 1: sort large buckets whole (many tiles)
         std::vector<uint32_t> bcnt(with_bcnt ? (size_t)nblk * T : 1, 0xdeadbeefu);   // written before read
         uint32_t* bc = with_bcnt ? bcnt.data() : nullptr;
         emu_launch(emu_dim3{nblk, 1, 1}, kBinThreads, k_tile_count, N, H, W, TW, T, (const float4*)proj.data(),
-                   cnt.data(), bc, cursor.data(), done.data(), cap, ranges.data(), &n_pairs, &status);
+                   cnt.data(), bc, cursor.data(), done.data(), cap, ranges.data(), &n_pairs, extra.data(), slice_big, &status);
         emu_launch(emu_dim3{nblk, 1, 1}, kBinThreads, k_tile_emit, N, H, W, TW, T, (const float4*)proj.data(),
                    (const uint32_t*)bc, cursor.data(), cap, keys.data());
-        const unsigned grid = (unsigned)std::min(T, 4);     // grid-stride over the tiles
-        emu_launch_smem(emu_dim3{grid, 1, 1}, kSortThreads, kSortSmem, k_tile_sort, T, (const uint2*)ranges.data(),
-                        keys.data(), alt.data(), ids.data(), skeys.data());
+        emu_launch_smem(emu_dim3{sort_grid(T, cap), 1, 1}, kSortThreads, kSortSmem, k_tile_sort, T,
+                        (const uint2*)ranges.data(), (const uint32_t*)extra.data(), keys.data(), alt.data(), ids.data(),
+                        skeys.data());
     }
     FILE* o = fopen(argv[2], "wb");
     if (!o) return 2;

@@ -92,7 +92,7 @@ int main(int argc, char** argv) {
     // binning and sort
     const int TW = tiles_x(view), T = TW * tiles_y(view);
     const uint32_t cap = 64u * (uint32_t)n + 64u;
-    std::vector<uint32_t> cnt(T, 0u), cursor(T, 0u), done(4, 0u), ids(cap, 0u);
+    std::vector<uint32_t> cnt(T, 0u), cursor(T, 0u), done(4, 0u), ids(cap, 0u), extra(T + 1, 0u);
     std::vector<uint2> ranges(T);
     std::vector<uint64_t> keys(cap), alt(cap);
     uint32_t n_pairs = 0;
@@ -100,11 +100,12 @@ int main(int argc, char** argv) {
     const unsigned nblk = (unsigned)((n + kBinThreads - 1) / kBinThreads);
     std::vector<uint32_t> bcnt((size_t)nblk * T);   // T <= kSmemTiles here: emit takes the blocks' counts
     emu_launch(emu_dim3{nblk, 1, 1}, kBinThreads, k_tile_count, n, H, W, TW, T, (const float4*)proj.data(), cnt.data(),
-               bcnt.data(), cursor.data(), done.data(), cap, ranges.data(), &n_pairs, &status);
+               bcnt.data(), cursor.data(), done.data(), cap, ranges.data(), &n_pairs, extra.data(), 1, &status);
     emu_launch(emu_dim3{nblk, 1, 1}, kBinThreads, k_tile_emit, n, H, W, TW, T, (const float4*)proj.data(),
                (const uint32_t*)bcnt.data(), cursor.data(), cap, keys.data());
-    emu_launch_smem(emu_dim3{(unsigned)std::min(T, 152 * 8), 1, 1}, kSortThreads, kSortSmem, k_tile_sort, T,
-                    (const uint2*)ranges.data(), keys.data(), alt.data(), ids.data(), (uint64_t*)nullptr);
+    emu_launch_smem(emu_dim3{sort_grid(T, cap), 1, 1}, kSortThreads, kSortSmem, k_tile_sort, T,
+                    (const uint2*)ranges.data(), (const uint32_t*)extra.data(), keys.data(), alt.data(), ids.data(),
+                    (uint64_t*)nullptr);
     // attribute network
     gsparc::W w{W1.data(), b1.data(), W2.data(), b2.data(), W3.data(), b3.data()};
     std::vector<float4> attr((size_t)B * n);

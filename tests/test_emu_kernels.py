@@ -199,9 +199,10 @@ def test_projection_kernels_logic(emu_bin, tmp_path, n, H, W, seed, rot):
         assert np.linalg.norm(got - want) <= 1e-3 * np.linalg.norm(want)
 
 
-def _binsort_run(exe, tmp_path, rec, H, W, cap, bcnt=True):
+def _binsort_run(exe, tmp_path, rec, H, W, cap, bcnt=True, slice_big=True):
     n = rec.shape[0]
-    raw = _run(exe, tmp_path, np.array([n, H, W, cap, int(bcnt)], np.int32).tobytes() + np.ascontiguousarray(
+    flags = int(bcnt) | (0 if slice_big else 2)
+    raw = _run(exe, tmp_path, np.array([n, H, W, cap, flags], np.int32).tobytes() + np.ascontiguousarray(
         rec, np.float32).tobytes())
     T = ((W + 15) // 16) * ((H + 15) // 16)
     n_pairs, status = int(np.frombuffer(raw[:4], np.uint32)[0]), int(np.frombuffer(raw[4:8], np.int32)[0])
@@ -220,14 +221,15 @@ def _binsort_run(exe, tmp_path, rec, H, W, cap, bcnt=True):
                                              (3000, 45, 180, 6, "plain"), (1500, 45, 180, 14, "three_depths"),
                                              (1500, 45, 180, 17, "one_depth"),
                                              (2000, 90, 360, 12, "overflow"), (400, 90, 360, 16, "culled"),
-                                             (30000, 16, 32, 18, "big")])
+                                             (30000, 16, 32, 18, "big"), (30000, 16, 32, 19, "big_whole")])
 def test_binsort_kernels_logic(emu_bin, tmp_path, n, H, W, seed, case):
     """k_tile_count, k_tile_emit and k_tile_sort (the library's source under the host shim)
     against the oracle's stable (tile, r, index) sort, bit for bit: ragged grids, 1 to 5,000
     records, the shared-memory distribution sort, three distinct depths and a single depth (tiles
     whose depth sub-buckets exceed 64 keys take the radix path; ties by index), a capacity below
     the pair count, every record culled, and buckets above the shared-memory capacity (two tiles
-    of ~30k pairs: the distribution sort with its keys scattered in global memory).  The radix
+    of ~30k pairs: cut into slices of about 12k keys sorted by blocks of their own, and sorted
+    whole with the keys scattered in global memory, the choice when tiles outnumber SMs).  The radix
     path on such large buckets is the GPU tests': every warp vote is a scheduling round in the
     shim, which makes those sizes slow on the CPU.  Each case runs with the per-block counts
     handed from k_tile_count to k_tile_emit (the library's path at these tile counts); the larger
@@ -246,7 +248,8 @@ def test_binsort_kernels_logic(emu_bin, tmp_path, n, H, W, seed, case):
     ok, ov, orng = obs.bin_sort(rec, H, W)
     cap = len(ov) // 2 if case == "overflow" else max(16, len(ov))
     for bcnt in ((True, False) if case in ("plain", "overflow") and n >= 1000 else (True,)):
-        n_pairs, status, ranges, ids, keys = _binsort_run(exe, tmp_path, rec, H, W, cap, bcnt)
+        n_pairs, status, ranges, ids, keys = _binsort_run(exe, tmp_path, rec, H, W, cap, bcnt,
+                                                          slice_big=case != "big_whole")
         assert n_pairs == len(ov)
         if case == "overflow":
             assert status == -5
