@@ -57,7 +57,9 @@ WORKLOAD = dict(name="fwd+bwd, 50k Gaussians, 64 subcarriers, 360x90, hidden 32,
 # scope table counts it: forward ~10 flop (the complex product of w = T alpha with the emission
 # a e^{j psi} and its accumulation), backward ~20 flop (the conjugate products of dL/dz with
 # the emission for the alpha, amplitude, phase and path-length derivatives).  The kernels hoist
-# the per-(Gaussian, subcarrier) phasor out of the pixel loop and execute 2 and 6 FMAs per unit.
+# the per-(Gaussian, subcarrier) phasor out of the pixel loop and execute 2 and 6 FP32 lane
+# operations per unit on the FMA pipe (forward one paired FMA; backward two paired FMAs and one
+# paired add).
 FLOP_FWD_UNIT = 10
 FLOP_BWD_UNIT = 20
 FMA_FWD_UNIT, FMA_BWD_UNIT = 2, 6
@@ -67,8 +69,8 @@ FP32_LANES_PER_SM = 128
 # kernels as they are now (one launch each, L2 flushed before the step); set an entry to None
 # when its kernel changes until it is captured again.  Algorithmic bytes for comparison: the
 # 16.6 MB upstream gradient (backward) or target (forward) read once, plus per-pixel state.
-NCU_TRAFFIC = {("fp32", "render_bwd"): 17_568_512 + 512, ("fp32", "render_fwd"): 17_780_736 + 768,
-               ("tc", "render_bwd"): 17_510_912, ("tc", "render_fwd"): 17_175_040}
+NCU_TRAFFIC = {("fp32", "render_bwd"): 17_885_696 + 512, ("fp32", "render_fwd"): 17_780_480 + 256,
+               ("tc", "render_bwd"): 17_508_864, ("tc", "render_fwd"): 17_176_064 + 256}
 
 
 def _env_int(k, d):

@@ -59,7 +59,7 @@ int bin_sort_launch(const gsparc_view* view, int N, const float* proj, int64_t p
         if (cudaMemsetAsync(n_pairs, 0, sizeof(uint32_t), s) != cudaSuccess) return GSPARC_ERR_CUDA;
         return GSPARC_OK;
     }
-    // tile counters and the block ticket are contiguous
+    // tile counters, the block ticket and the sort's work counter are contiguous
     if (cudaMemsetAsync(w + L.cnt, 0, L.cursor - L.cnt, s) != cudaSuccess) return GSPARC_ERR_CUDA;
     if (!ensure_smem_attr(k_tile_sort, (int)kSortSmem)) return GSPARC_ERR_CUDA;
     const float4* p4 = reinterpret_cast<const float4*>(proj);
@@ -68,8 +68,8 @@ int bin_sort_launch(const gsparc_view* view, int N, const float* proj, int64_t p
                                                 ranges, n_pairs, extra, slice_big_buckets(T, num_sms()) ? 1 : 0,
                                                 d_status);
     k_tile_emit<<<L.nblk, kBinThreads, 0, s>>>(N, view->H, view->W, TW, T, p4, bcnt, cursor, cap, keys);
-    k_tile_sort<<<sort_grid(T, cap), kSortThreads, kSortSmem, s>>>(T, ranges, extra, keys, alt, sorted_ids,
-                                                                   sorted_keys);
+    k_tile_sort<<<sort_grid(T, cap, num_sms()), kSortThreads, kSortSmem, s>>>(T, ranges, extra, done + 1, keys,
+                                                                              alt, sorted_ids, sorted_keys);
     return launch_status();
 }
 

@@ -60,10 +60,12 @@ __device__ __host__ __forceinline__ uint32_t extra_slices(uint32_t n) {
 // Buckets above kSortCap keys are sliced only when the tiles alone leave SMs idle; otherwise each
 // is sorted by its tile's block (keys scattered in global memory), which moves fewer bytes.
 inline bool slice_big_buckets(int T, int sms) { return T < sms; }
-// Blocks of a k_tile_sort launch: one per tile and one per extra slice of a list of cap pairs.
-inline uint32_t sort_grid(int T, uint32_t cap) { return (uint32_t)T + cap / kSlice; }
-static_assert(kSortThreads >= 256, "the digit scan gives one thread per digit");
-static_assert(kSortWarps * 256 == kSubBuckets, "histogram array shared by both in-tile sorts");
+// Blocks of a k_tile_sort launch: one per SM (each holds 200+ KB of shared memory), or fewer when
+// a list of cap pairs has fewer work items (its tiles and the extra slices of its buckets).
+inline uint32_t sort_grid(int T, uint32_t cap, int sms) {
+    const uint64_t most = (uint64_t)T + (slice_big_buckets(T, sms) ? cap / kSlice : 0u);
+    return (uint32_t)(most < (uint64_t)sms ? most : (uint64_t)sms);
+}
 
 // Column / row tile ranges touched by one projection record.  Every float
 // step is a single correctly rounded operation (explicit _rn intrinsics keep
@@ -690,42 +692,12 @@ __device__ __forceinline__ bool sort_slice(const uint64_t* src, int n, uint32_t 
     return true;
 }
 
-// Block t < T sorts tile t's bucket: up to kSortCap keys by distribution (keys counted into
-// kSubBuckets sub-buckets by depth, scattered to their sub-bucket in shared memory in arbitrary
-// order inside it, each key's final place its sub-bucket's start plus the number of smaller keys
-// in the same sub-bucket; the keys are unique, so the places are distinct); above kSortCap keys
-// slice 0 of the bucket (sort_slice) when the bucket is sliced, else the whole bucket with its keys
-// scattered in global memory (sort_big_bucket).  Block T + e takes extra slice e of the work list of
-// k_tile_count (blocks past its end return).  A bucket whose largest sub-bucket is too large (many
-// equal depths) takes the LSD radix sort in global memory with `alt` as the second buffer (its
-// first block; the other slices of such a bucket return).
-__global__ void __launch_bounds__(kSortThreads, 1) k_tile_sort(int T, const uint2* __restrict__ ranges,
-                                                               const uint32_t* __restrict__ extra,
-                                                               uint64_t* __restrict__ keys,
-                                                               uint64_t* __restrict__ alt,
-                                                               uint32_t* __restrict__ sorted_ids,
-                                                               uint64_t* __restrict__ sorted_keys) {
-    GSPARC_DYNAMIC_SMEM(smem_raw);
-    SortShared& sh = *reinterpret_cast<SortShared*>(smem_raw);
-    uint64_t* buf = reinterpret_cast<uint64_t*>(smem_raw + ((sizeof(SortShared) + 15) & ~size_t(15)));
+// Item tile < T of k_tile_sort: the tile's bucket.
+__device__ __forceinline__ void sort_tile(int tile, const uint2* __restrict__ ranges, const uint32_t* __restrict__ extra,
+                                          uint64_t* __restrict__ keys, uint64_t* __restrict__ alt,
+                                          uint32_t* __restrict__ sorted_ids, uint64_t* __restrict__ sorted_keys,
+                                          SortShared& sh, uint64_t* buf) {
     const int lane = threadIdx.x & 31;
-    int tile;
-    uint32_t slice = 0;
-    if ((int)blockIdx.x < T) {
-        tile = (int)blockIdx.x;
-    } else {
-        const uint32_t e = blockIdx.x - (uint32_t)T;
-        if (e >= __ldg(&extra[T])) return;   // the whole block
-        // the tile: the last t with extra[t] <= e (tiles without extra slices repeat the next offset)
-        int lo = 0, hi = T - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(&extra[mid]) <= e) lo = mid;
-            else hi = mid - 1;
-        }
-        tile = lo;
-        slice = 1u + e - __ldg(&extra[tile]);
-    }
     {
         const uint2 r = ranges[tile];
         const int n = (int)(r.y - r.x);
@@ -737,11 +709,10 @@ __global__ void __launch_bounds__(kSortThreads, 1) k_tile_sort(int T, const uint
                           "slice keys and large-bucket histogram in the key buffer");
             uint32_t* hist = reinterpret_cast<uint32_t*>(buf + kSlice + kSubMaxBig);
             const bool sliced = __ldg(&extra[tile + 1]) > __ldg(&extra[tile]);
-            if (sliced ? sort_slice(src, n, slice, r.x, tile, sh, hist, buf, sorted_ids, sorted_keys)
+            if (sliced ? sort_slice(src, n, 0u, r.x, tile, sh, hist, buf, sorted_ids, sorted_keys)
                        : sort_big_bucket(src, alt + r.x, n, r.x, tile, sh, reinterpret_cast<uint32_t*>(buf),
                                          sorted_ids, sorted_keys))
                 return;
-            if (slice != 0) return;   // the whole block: slice 0 takes the radix sort
             const uint64_t* res = sort_bucket(keys + r.x, alt + r.x, n, sh);
             for (int j = threadIdx.x; j < n; j += kSortThreads) {
                 const uint64_t k = res[j];
@@ -824,6 +795,54 @@ __global__ void __launch_bounds__(kSortThreads, 1) k_tile_sort(int T, const uint
                 if (sorted_keys) sorted_keys[r.x + j] = ((uint64_t)tile << 32) | (k >> 32);
             }
         }
+    }
+}
+
+// Persistent blocks that take work items from a counter (work[0], zero-initialised): item t < T
+// sorts tile t's bucket, up to kSortCap keys by distribution (keys counted into kSubBuckets
+// sub-buckets by depth, scattered to their sub-bucket in shared memory in arbitrary order inside
+// it, each key's final place its sub-bucket's start plus the number of smaller keys in the same
+// sub-bucket; the keys are unique, so the places are distinct); above kSortCap keys slice 0 of the
+// bucket (sort_slice) when the bucket is sliced, else the whole bucket with its keys scattered in
+// global memory (sort_big_bucket).  Items T + e are the extra slices e of the work list of
+// k_tile_count.  A bucket whose largest sub-bucket is too large (many equal depths) takes the LSD
+// radix sort in global memory with `alt` as the second buffer (its tile's item; its extra slices
+// are skipped).
+__global__ void __launch_bounds__(kSortThreads, 1) k_tile_sort(int T, const uint2* __restrict__ ranges,
+                                                               const uint32_t* __restrict__ extra,
+                                                               uint32_t* __restrict__ work,
+                                                               uint64_t* __restrict__ keys,
+                                                               uint64_t* __restrict__ alt,
+                                                               uint32_t* __restrict__ sorted_ids,
+                                                               uint64_t* __restrict__ sorted_keys) {
+    GSPARC_DYNAMIC_SMEM(smem_raw);
+    SortShared& sh = *reinterpret_cast<SortShared*>(smem_raw);
+    uint64_t* buf = reinterpret_cast<uint64_t*>(smem_raw + ((sizeof(SortShared) + 15) & ~size_t(15)));
+    __shared__ uint32_t s_item;
+    const uint32_t n_items = (uint32_t)T + __ldg(&extra[T]);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(work, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        __syncthreads();   // every thread has its item before thread 0 takes the next
+        if (item >= n_items) return;   // the whole block
+        if (item < (uint32_t)T) {
+            sort_tile((int)item, ranges, extra, keys, alt, sorted_ids, sorted_keys, sh, buf);
+        } else {
+            const uint32_t e = item - (uint32_t)T;
+            // the tile: the last t with extra[t] <= e (tiles without extra slices repeat the next offset)
+            int lo = 0, hi = T - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(&extra[mid]) <= e) lo = mid;
+                else hi = mid - 1;
+            }
+            const uint2 r = ranges[lo];
+            uint32_t* hist = reinterpret_cast<uint32_t*>(buf + kSlice + kSubMaxBig);
+            sort_slice(keys + r.x, (int)(r.y - r.x), 1u + e - __ldg(&extra[lo]), r.x, lo, sh, hist, buf, sorted_ids,
+                       sorted_keys);
+        }
+        __syncthreads();   // the next item reuses the shared memory
     }
 }
 

@@ -1183,7 +1183,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
 #pragma unroll
                     for (int q = 0; q < 16; ++q) v[c + q] = t16[q];
                 }
-                uint64_t mask = warp_entry_mask(mdp.geo, mdp.geo2, mdp.ext, nbp, wcx, wcy, a.W);
+                uint64_t mask = warp_entry_mask<false>(mdp.geo, mdp.geo2, mdp.ext, nbp, wcx, wcy, a.W);
                 // positions at or past every pixel's n_contrib are live at none of the warp's pixels
                 if (lo_pos >= wlast) mask = 0ull;
                 else if (wlast - lo_pos < 64u) mask &= (1ull << (wlast - lo_pos)) - 1ull;

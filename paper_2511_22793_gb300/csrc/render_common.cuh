@@ -285,6 +285,8 @@ __device__ __forceinline__ void stage_phasors_bwd(const RenderArgs& a, const Sta
 // side.  False therefore means eval_alpha skips the entry at every pixel of the block.  A block
 // that reaches the antipode of the entry's centre (where the azimuth wrap could split its
 // columns) keeps the box test's answer.
+// With kExact false only the box test is made (a superset of the entries, cheaper per entry).
+template <bool kExact = true>
 __device__ __forceinline__ bool entry_reaches_block(float px, float py, float ex, float ey, float cxx, float cxy,
                                                     float cyy, float sig, float wcx, float wcy, int W) {
     const float hw = 0.5f * (float)W;
@@ -293,7 +295,7 @@ __device__ __forceinline__ bool entry_reaches_block(float px, float py, float ex
     else if (dx < -hw) dx += (float)W;
     const float dy = wcy - py;
     bool hit = ex >= 0.f && fabsf(dx) <= ex + 7.51f && fabsf(dy) <= ey + 0.51f;
-    if (hit && fabsf(dx) < hw - 8.0f) {
+    if (kExact && hit && fabsf(dx) < hw - 8.0f) {
         // alpha >= 1/255  <=>  q <= 2 ln(255 sigma)
         const float q_op = 2.0f * 0.6931471805599453f * lg2(255.0f * sig);
         const float thr = fminf(kQMax, q_op) + 0.01f;
@@ -328,7 +330,10 @@ __device__ __forceinline__ uint64_t warp_entry_mask_rec(const StageRec* rec, int
 }
 
 // The same over the tensor-core kernels' staging: s_geo (p_x, p_y, c_xx, c_xy), s_geo2 (c_yy,
-// sigma), s_ext (half extents; negative for a culled or invalid entry).
+// sigma), s_ext (half extents; negative for a culled or invalid entry).  kExact false: the box
+// test alone (the tensor-core backward, where the mask sits on each batch's critical path and the
+// entries it would drop are skipped by the live test at little cost).
+template <bool kExact = true>
 __device__ __forceinline__ uint64_t warp_entry_mask(const float4* s_geo, const float2* s_geo2, const float2* s_ext,
                                                     int nb, float wcx, float wcy, int W) {
     const int lane = threadIdx.x & 31;
@@ -340,7 +345,7 @@ __device__ __forceinline__ uint64_t warp_entry_mask(const float4* s_geo, const f
             const float4 g = s_geo[j];
             const float2 g2 = s_geo2[j];
             const float2 e = s_ext[j];
-            h[half] = entry_reaches_block(g.x, g.y, e.x, e.y, g.z, g.w, g2.x, g2.y, wcx, wcy, W);
+            h[half] = entry_reaches_block<kExact>(g.x, g.y, e.x, e.y, g.z, g.w, g2.x, g2.y, wcx, wcy, W);
         }
     }
     const uint32_t lo = __ballot_sync(0xffffffffu, h[0]);

@@ -1,8 +1,8 @@
 // Runs the library's binning and sorting kernels (csrc/binsort.cuh) under the host shim with the
 // launch sequence of gsparc_bin_sort: tile counters and ticket zeroed, k_tile_count and
-// k_tile_emit over blocks of kBinThreads records, k_tile_sort over sort_grid(T, capacity) blocks
-// (one per tile, then the extra slices of buckets above kSortCap keys; blocks past the work list
-// return) with the kernel's dynamic shared memory.
+// k_tile_emit over blocks of kBinThreads records, k_tile_sort over sort_grid(T, capacity, 4)
+// persistent blocks (as on a GPU of 4 SMs: the tiles and the extra slices of buckets above kSortCap
+// keys taken from a work counter) with the kernel's dynamic shared memory.
 // With with_bcnt (bit 0 of the fifth header word), k_tile_count also writes the per-(block, tile)
 // counts and k_tile_emit takes them instead of counting for itself (the library's path when
 // T <= kSmemTiles).  Bit 1 turns off the slicing of buckets above kSortCap keys (the library's
@@ -41,15 +41,16 @@ int main(int argc, char** argv) {
         using namespace gsparc;
         const unsigned nblk = (unsigned)((N + kBinThreads - 1) / kBinThreads);
         const bool with_bcnt = (hdr[4] & 1) != 0 && T <= kSmemTiles;
-        const int slice_big = (hdr[4] & 2) ? 0 : 1;   // bit 1: sort large buckets whole (many tiles)
+        // bit 1: sort large buckets whole (the library's choice when the tiles outnumber the SMs)
+        const int slice_big = (hdr[4] & 2) ? 0 : 1;
         std::vector<uint32_t> bcnt(with_bcnt ? (size_t)nblk * T : 1, 0xdeadbeefu);   // written before read
         uint32_t* bc = with_bcnt ? bcnt.data() : nullptr;
         emu_launch(emu_dim3{nblk, 1, 1}, kBinThreads, k_tile_count, N, H, W, TW, T, (const float4*)proj.data(),
                    cnt.data(), bc, cursor.data(), done.data(), cap, ranges.data(), &n_pairs, extra.data(), slice_big, &status);
         emu_launch(emu_dim3{nblk, 1, 1}, kBinThreads, k_tile_emit, N, H, W, TW, T, (const float4*)proj.data(),
                    (const uint32_t*)bc, cursor.data(), cap, keys.data());
-        emu_launch_smem(emu_dim3{sort_grid(T, cap), 1, 1}, kSortThreads, kSortSmem, k_tile_sort, T,
-                        (const uint2*)ranges.data(), (const uint32_t*)extra.data(), keys.data(), alt.data(), ids.data(),
+        emu_launch_smem(emu_dim3{sort_grid(T, cap, 4), 1, 1}, kSortThreads, kSortSmem, k_tile_sort, T,
+                        (const uint2*)ranges.data(), (const uint32_t*)extra.data(), done.data() + 1, keys.data(), alt.data(), ids.data(),
                         skeys.data());
     }
     FILE* o = fopen(argv[2], "wb");

@@ -103,8 +103,8 @@ int main(int argc, char** argv) {
                bcnt.data(), cursor.data(), done.data(), cap, ranges.data(), &n_pairs, extra.data(), 1, &status);
     emu_launch(emu_dim3{nblk, 1, 1}, kBinThreads, k_tile_emit, n, H, W, TW, T, (const float4*)proj.data(),
                (const uint32_t*)bcnt.data(), cursor.data(), cap, keys.data());
-    emu_launch_smem(emu_dim3{sort_grid(T, cap), 1, 1}, kSortThreads, kSortSmem, k_tile_sort, T,
-                    (const uint2*)ranges.data(), (const uint32_t*)extra.data(), keys.data(), alt.data(), ids.data(),
+    emu_launch_smem(emu_dim3{sort_grid(T, cap, 4), 1, 1}, kSortThreads, kSortSmem, k_tile_sort, T,
+                    (const uint2*)ranges.data(), (const uint32_t*)extra.data(), done.data() + 1, keys.data(), alt.data(), ids.data(),
                     (uint64_t*)nullptr);
     // attribute network
     gsparc::W w{W1.data(), b1.data(), W2.data(), b2.data(), W3.data(), b3.data()};
