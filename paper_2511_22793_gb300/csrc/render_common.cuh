@@ -247,31 +247,72 @@ __device__ __forceinline__ void stage_issue(const RenderArgs& a, int b, int nb, 
     }
 }
 
-// Unit phasors of the strip's subcarriers for the nb entries of rec (every thread), into tab.
-template <int S>
-__device__ __forceinline__ void stage_phasors(const RenderArgs& a, const StageRec* rec, int nb, int k0,
-                                              float2 (*tab)[S]) {
-    for (int e = threadIdx.x; e < nb * S; e += kThreads) {
-        const int j = e / S, kk = e - j * S;
-        const int k = k0 + kk;
-        float2 ph = make_float2(0.f, 0.f);
-        if (k < a.K) ph = unit_phasor(a, rec[j].at.w, rec[j].at.y, k);
-        tab[j][kk] = ph;
+// Unit phasors of R consecutive subcarriers k0 .. k0 + R - 1 of one Gaussian: the first by
+// unit_phasor, each next one by a complex product with the step e^{-j 2 pi L df / c} (the
+// cycles L df / c per subcarrier, reduced, to the SFU sine/cosine), so that at most R - 1 <= 7
+// roundings of a product separate a phasor from its directly computed value (relative error
+// ~1e-6, far below the 1e-3 bound on spectra).
+template <int R>
+__device__ __forceinline__ void phasor_run(const RenderArgs& a, float L, float phi0, int k0, float2 (&u)[R]) {
+    u[0] = unit_phasor(a, L, phi0, k0);
+    if constexpr (R > 1) {
+        float c = L * a.dlam;
+        c -= rintf(c);
+        float sn, cs;
+        __sincosf(6.283185307179586f * c, &sn, &cs);
+        const float dx = cs, dy = -sn;   // e^{-j 2 pi c}
+#pragma unroll
+        for (int m = 1; m < R; ++m) {
+            const float x = u[m - 1].x, y = u[m - 1].y;
+            u[m] = make_float2(fmaf(x, dx, -y * dy), fmaf(x, dy, y * dx));
+        }
     }
 }
 
-// The backward's table: for each unit phasor t = e^{j psi} the pair (t, -j conj(t)), i.e.
-// (t.x, t.y, t.y, -t.x), so that for an upstream gradient g both Re(conj(g) t) = g.x t.x + g.y t.y
-// and Im(conj(g) t) = g.x t.y - g.y t.x are one paired FMA of (g.x, g.y) against one half.
+// Unit phasors of the strip's subcarriers for the nb entries of rec (every thread), into tab:
+// each thread forms runs of up to 8 consecutive subcarriers of one entry (phasor_run).  In a
+// float4 table every element is (t, -j conj t) = (t.x, t.y, t.y, -t.x), the backward's form: for an
+// upstream gradient g both Re(conj(g) t) = g.x t.x + g.y t.y and Im(conj(g) t) = g.x t.y - g.y t.x
+// are then one paired FMA of (g.x, g.y) against one half.  (The forward uses it.)
+template <int S, class E>
+__device__ __forceinline__ void stage_phasor_runs(const RenderArgs& a, const StageRec* rec, int nb, int k0,
+                                                  E (*tab)[S]) {
+    constexpr int R = S >= 8 ? 8 : S, NR = S / R;
+    for (int it = threadIdx.x; it < nb * NR; it += kThreads) {
+        const int j = it / NR, kk0 = (it - j * NR) * R;
+        float2 u[R];
+        if (k0 + kk0 < a.K) {
+            phasor_run<R>(a, rec[j].at.w, rec[j].at.y, k0 + kk0, u);
+        } else {
+#pragma unroll
+            for (int m = 0; m < R; ++m) u[m] = make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            const float2 t = k0 + kk0 + m < a.K ? u[m] : make_float2(0.f, 0.f);
+            if constexpr (sizeof(E) == 16) tab[j][kk0 + m] = make_float4(t.x, t.y, t.y, -t.x);
+            else tab[j][kk0 + m] = t;
+        }
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void stage_phasors(const RenderArgs& a, const StageRec* rec, int nb, int k0,
+                                              float2 (*tab)[S]) {
+    stage_phasor_runs<S>(a, rec, nb, k0, tab);
+}
+// The backward's table, each phasor formed on its own (unit_phasor): the backward waits for its
+// table at every batch, and eight independent phasors per thread finish sooner than a run of
+// eight dependent products.
 template <int S>
 __device__ __forceinline__ void stage_phasors_bwd(const RenderArgs& a, const StageRec* rec, int nb, int k0,
                                                   float4 (*tab)[S]) {
     for (int e = threadIdx.x; e < nb * S; e += kThreads) {
         const int j = e / S, kk = e - j * S;
         const int k = k0 + kk;
-        float2 ph = make_float2(0.f, 0.f);
-        if (k < a.K) ph = unit_phasor(a, rec[j].at.w, rec[j].at.y, k);
-        tab[j][kk] = make_float4(ph.x, ph.y, ph.y, -ph.x);
+        float2 t = make_float2(0.f, 0.f);
+        if (k < a.K) t = unit_phasor(a, rec[j].at.w, rec[j].at.y, k);
+        tab[j][kk] = make_float4(t.x, t.y, t.y, -t.x);
     }
 }
 
@@ -439,8 +480,9 @@ __device__ __forceinline__ int rs18_slot(int lane) {
 template <int S, int TE = 8>
 struct F32Smem {
     static constexpr int kRec = 0;                                        // StageRec[2][kBatch]
-    static constexpr int kTab = kRec + 2 * kBatch * (int)sizeof(StageRec);  // [2][kBatch][S] elements
-    static constexpr int kGid = kTab + 2 * kBatch * S * TE;               // uint32[2][kBatch]
+    static constexpr int kRow = S;                                        // table row
+    static constexpr int kTab = kRec + 2 * kBatch * (int)sizeof(StageRec);  // [2][kBatch][kRow] elements
+    static constexpr int kGid = kTab + 2 * kBatch * kRow * TE;            // uint32[2][kBatch]
     static constexpr int kBar = kGid + 2 * kBatch * 4;                    // uint64[2]
     static constexpr int kMisc = kBar + 16;                               // float[8], uint32[4]
     static constexpr int kTotal = kMisc + 48;
@@ -471,7 +513,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_fwd(RenderArgs a) {
     using L = F32Smem<S>;
     GSPARC_DYNAMIC_SMEM(sm);
     StageRec* s_rec = reinterpret_cast<StageRec*>(sm + L::kRec);
-    float2(*s_tab)[kBatch][S] = reinterpret_cast<float2(*)[kBatch][S]>(sm + L::kTab);
+    float2(*s_tab)[kBatch][L::kRow] = reinterpret_cast<float2(*)[kBatch][L::kRow]>(sm + L::kTab);
     uint32_t* s_gid = reinterpret_cast<uint32_t*>(sm + L::kGid);
     uint64_t* s_bar = reinterpret_cast<uint64_t*>(sm + L::kBar);
     float* s_part = reinterpret_cast<float*>(sm + L::kMisc);
@@ -678,7 +720,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
     using L = F32BwdSmem<S>;
     GSPARC_DYNAMIC_SMEM(sm);
     StageRec* s_rec = reinterpret_cast<StageRec*>(sm + L::kRec);
-    float4(*s_tab)[kBatch][S] = reinterpret_cast<float4(*)[kBatch][S]>(sm + L::kTab);
+    float4(*s_tab)[kBatch][L::kRow] = reinterpret_cast<float4(*)[kBatch][L::kRow]>(sm + L::kTab);
     uint32_t* s_gid = reinterpret_cast<uint32_t*>(sm + L::kGid);
     uint64_t* s_bar = reinterpret_cast<uint64_t*>(sm + L::kBar);
     uint32_t* s_maxlast = reinterpret_cast<uint32_t*>(sm + L::kMisc + 32);
