@@ -380,8 +380,16 @@ __global__ void __launch_bounds__(kRowsB, 1) k_mlp_bwd_tc(
         }
         tc_fence_before();
         if (valid) {
+            float* dl = d_latent + (size_t)i * GSPARC_LATENT;
+            if ((reinterpret_cast<uintptr_t>(d_latent) & 15) == 0) {   // four 16-byte vector atomics
 #pragma unroll
-            for (int f = 0; f < GSPARC_LATENT; ++f) atomicAdd(&d_latent[(size_t)i * GSPARC_LATENT + f], dh0[3 + f]);
+                for (int q = 0; q < GSPARC_LATENT / 4; ++q)
+                    atomicAdd(reinterpret_cast<float4*>(dl) + q,
+                              make_float4(dh0[3 + 4 * q], dh0[4 + 4 * q], dh0[5 + 4 * q], dh0[6 + 4 * q]));
+            } else {
+#pragma unroll
+                for (int f = 0; f < GSPARC_LATENT; ++f) atomicAdd(dl + f, dh0[3 + f]);
+            }
             atomicAdd(&d_ologit[i], do2);
             // a = sigmoid(o0 - ln d)/d: explicit ln d (-do0), network input ln d, L = d + r
             const float dlogd = -do0 + dh0[GSPARC_MLP_IN - 1];
@@ -414,12 +422,24 @@ __global__ void __launch_bounds__(kRowsB, 1) k_mlp_bwd_tc(
 #pragma unroll
             for (int q = 0; q < 16; ++q) v[c + q] = w16[q];
         }
+        // every CTA adds into the same entries at about the same time: with 16-byte aligned
+        // gradients four entries go as one vector atomic (a quarter of the operations queueing
+        // at the L2)
+        const bool vec = ((reinterpret_cast<uintptr_t>(g.W1) | reinterpret_cast<uintptr_t>(g.W2)) & 15) == 0;
+        auto add_row = [&](float* dst, const float* src) {
+            if (vec) {
+#pragma unroll
+                for (int n = 0; n < HD; n += 4)
+                    atomicAdd(reinterpret_cast<float4*>(dst + n), make_float4(src[n], src[n + 1], src[n + 2], src[n + 3]));
+            } else {
+#pragma unroll
+                for (int n = 0; n < HD; ++n) atomicAdd(dst + n, src[n]);
+            }
+        };
         if (t < GSPARC_MLP_IN) {
-#pragma unroll
-            for (int n = 0; n < HD; ++n) atomicAdd(&g.W1[t * HD + n], v[n]);
+            add_row(&g.W1[t * HD], v);
         } else if (t >= L::kFH1 && t < L::kFH1 + HD) {
-#pragma unroll
-            for (int n = 0; n < HD; ++n) atomicAdd(&g.W2[(t - L::kFH1) * HD + n], v[HD + n]);
+            add_row(&g.W2[(t - L::kFH1) * HD], v + HD);
         } else if (t >= L::kFH2 && t < L::kFH2 + HD) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) atomicAdd(&g.W3[(t - L::kFH2) * 3 + c], v[2 * HD + c]);

@@ -550,7 +550,12 @@ __global__ void __launch_bounds__(kBwdThreads, HD <= 32 ? 3 : 1)
             atomicAdd(&d_means[3 * i + 2], gm2);
         }
     }
-    // one atomic per entry: rows of the first factor are weight rows, its ones row the bias
+    // The weight gradients: rows of the first factor are weight rows, its ones row the bias.
+    // Every CTA adds into the same entries at about the same time, so the atomics queue at the
+    // L2; with 16-byte aligned gradients the four columns of a block row go as one vector atomic
+    // (a quarter of the operations), else one atomic per entry.
+    const bool vec = ((reinterpret_cast<uintptr_t>(g.W1) | reinterpret_cast<uintptr_t>(g.b1) |
+                       reinterpret_cast<uintptr_t>(g.W2) | reinterpret_cast<uintptr_t>(g.b2)) & 15) == 0;
 #pragma unroll
     for (int m = 0; m < S::kPer; ++m) {
         const int blk = t + kBwdThreads * m;
@@ -558,19 +563,22 @@ __global__ void __launch_bounds__(kBwdThreads, HD <= 32 ? 3 : 1)
         const GBlk gb = grad_block<HD>(blk);
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
+            const int fr = gb.p0 + p;
+            float* row = nullptr;   // the block row's four entries (columns q0 .. q0 + 3)
+            if (blk < S::kBlk1) row = fr < IN ? &g.W1[fr * HD + gb.q0] : (fr == IN ? &g.b1[gb.q0] : nullptr);
+            else if (blk < S::kBlk1 + S::kBlk2)
+                row = fr < HD ? &g.W2[fr * HD + gb.q0] : (fr == HD ? &g.b2[gb.q0] : nullptr);
+            if (row) {
+                if (vec) {
+                    atomicAdd(reinterpret_cast<float4*>(row),
+                              make_float4(acc[m][4 * p], acc[m][4 * p + 1], acc[m][4 * p + 2], acc[m][4 * p + 3]));
+                } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int fr = gb.p0 + p, c = gb.q0 + q;
-                const float v = acc[m][4 * p + q];
-                if (blk < S::kBlk1) {
-                    if (fr < IN) atomicAdd(&g.W1[fr * HD + c], v);
-                    else if (fr == IN) atomicAdd(&g.b1[c], v);
-                } else if (blk < S::kBlk1 + S::kBlk2) {
-                    if (fr < HD) atomicAdd(&g.W2[fr * HD + c], v);
-                    else if (fr == HD) atomicAdd(&g.b2[c], v);
-                } else if (c < 3) {
-                    atomicAdd(&g.W3[fr * 3 + c], v);
+                    for (int q = 0; q < 4; ++q) atomicAdd(row + q, acc[m][4 * p + q]);
                 }
+            } else if (blk >= S::kBlk1 + S::kBlk2) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) atomicAdd(&g.W3[fr * 3 + q], acc[m][4 * p + q]);
             }
         }
     }
