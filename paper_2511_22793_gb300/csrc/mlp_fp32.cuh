@@ -182,6 +182,11 @@ struct BwdSmem {
     static_assert(kW1T % 4 == 0 && kW3 % 4 == 0 && kA0 % 4 == 0 && kA1 % 4 == 0 && kG1 % 4 == 0, "16-byte rows");
 };
 static_assert(kBwdRows == 64 && kBwdThreads == 128, "tile products: 16 row groups x 8 column groups");
+#ifdef GSPARC_HOST_SHIM
+constexpr bool kHostShim = true;    // the test suite's host shim has no bulk copies: atomics
+#else
+constexpr bool kHostShim = false;
+#endif
 
 // Offset of rows r..r+3 (r a multiple of 4) of feature x in a feature-major array.
 __device__ __forceinline__ int fm4(int x, int r) { return x * kBwdRows + (((r >> 2) ^ ((x >> 2) & 7)) << 2); }
@@ -551,34 +556,83 @@ __global__ void __launch_bounds__(kBwdThreads, HD <= 32 ? 3 : 1)
         }
     }
     // The weight gradients: rows of the first factor are weight rows, its ones row the bias.
-    // Every CTA adds into the same entries at about the same time, so the atomics queue at the
-    // L2; with 16-byte aligned gradients the four columns of a block row go as one vector atomic
-    // (a quarter of the operations), else one atomic per entry.
-    const bool vec = ((reinterpret_cast<uintptr_t>(g.W1) | reinterpret_cast<uintptr_t>(g.b1) |
-                       reinterpret_cast<uintptr_t>(g.W2) | reinterpret_cast<uintptr_t>(g.b2)) & 15) == 0;
+    // Every CTA adds into the same entries at about the same time, so that the additions queue
+    // at the L2.  With 16-byte aligned gradients the CTA's sums are laid out in shared memory as
+    // the gradient arrays (W1, b1, W2, b2, W3; every entry written by one thread) and added to
+    // global memory by bulk reductions (cp.reduce.async.bulk .add.f32, a few per CTA);
+    // otherwise each entry by an atomic.
+    const bool aligned = ((reinterpret_cast<uintptr_t>(g.W1) | reinterpret_cast<uintptr_t>(g.b1) |
+                           reinterpret_cast<uintptr_t>(g.W2) | reinterpret_cast<uintptr_t>(g.b2) |
+                           reinterpret_cast<uintptr_t>(g.W3)) & 15) == 0;
+#ifndef GSPARC_HOST_SHIM
+    if (aligned) {
+        constexpr int oW1 = 0, ob1 = oW1 + IN * HD, oW2 = ob1 + HD, ob2 = oW2 + HD * HD, oW3 = ob2 + HD;
+        static_assert(ob1 % 4 == 0 && oW2 % 4 == 0 && ob2 % 4 == 0 && oW3 % 4 == 0 && (3 * HD) % 4 == 0,
+                      "16-byte segments");
+        static_assert(oW3 + 3 * HD <= S::kTotal - S::kA0, "staging within the tile buffers");
+        float* st = sm + S::kA0;   // the tile buffers are free after the last tile
+        __syncthreads();           // every thread is past its last tile
 #pragma unroll
-    for (int m = 0; m < S::kPer; ++m) {
-        const int blk = t + kBwdThreads * m;
-        if (blk >= S::kBlocks) continue;
-        const GBlk gb = grad_block<HD>(blk);
+        for (int m = 0; m < S::kPer; ++m) {
+            const int blk = t + kBwdThreads * m;
+            if (blk >= S::kBlocks) continue;
+            const GBlk gb = grad_block<HD>(blk);
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int fr = gb.p0 + p;
-            float* row = nullptr;   // the block row's four entries (columns q0 .. q0 + 3)
-            if (blk < S::kBlk1) row = fr < IN ? &g.W1[fr * HD + gb.q0] : (fr == IN ? &g.b1[gb.q0] : nullptr);
-            else if (blk < S::kBlk1 + S::kBlk2)
-                row = fr < HD ? &g.W2[fr * HD + gb.q0] : (fr == HD ? &g.b2[gb.q0] : nullptr);
-            if (row) {
-                if (vec) {
-                    atomicAdd(reinterpret_cast<float4*>(row),
-                              make_float4(acc[m][4 * p], acc[m][4 * p + 1], acc[m][4 * p + 2], acc[m][4 * p + 3]));
-                } else {
+            for (int p = 0; p < 4; ++p) {
+                const int fr = gb.p0 + p;
+                float* row = nullptr;
+                if (blk < S::kBlk1) row = fr < IN ? st + oW1 + fr * HD + gb.q0 : (fr == IN ? st + ob1 + gb.q0 : nullptr);
+                else if (blk < S::kBlk1 + S::kBlk2)
+                    row = fr < HD ? st + oW2 + fr * HD + gb.q0 : (fr == HD ? st + ob2 + gb.q0 : nullptr);
+                if (row) {
+                    st4(row, acc[m][4 * p], acc[m][4 * p + 1], acc[m][4 * p + 2], acc[m][4 * p + 3]);
+                } else if (blk >= S::kBlk1 + S::kBlk2) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) atomicAdd(row + q, acc[m][4 * p + q]);
+                    for (int q = 0; q < 3; ++q) st[oW3 + fr * 3 + q] = acc[m][4 * p + q];
                 }
-            } else if (blk >= S::kBlk1 + S::kBlk2) {
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the stores, to the bulk copies
+        __syncthreads();
+        if (t == 0) {
+            auto bulk_add = [&](float* dst, const float* src, int n) {
+                asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst),
+                             "r"(static_cast<uint32_t>(__cvta_generic_to_shared(src))), "r"(4 * n)
+                             : "memory");
+            };
+            bulk_add(g.W1, st + oW1, IN * HD);
+            bulk_add(g.b1, st + ob1, HD);
+            bulk_add(g.W2, st + oW2, HD * HD);
+            bulk_add(g.b2, st + ob2, HD);
+            bulk_add(g.W3, st + oW3, 3 * HD);
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // shared memory read before exit
+        }
+    }
+#endif
+    if (!aligned || kHostShim) {
 #pragma unroll
-                for (int q = 0; q < 3; ++q) atomicAdd(&g.W3[fr * 3 + q], acc[m][4 * p + q]);
+        for (int m = 0; m < S::kPer; ++m) {
+            const int blk = t + kBwdThreads * m;
+            if (blk >= S::kBlocks) continue;
+            const GBlk gb = grad_block<HD>(blk);
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int fr = gb.p0 + p;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int c = gb.q0 + q;
+                    const float v = acc[m][4 * p + q];
+                    if (blk < S::kBlk1) {
+                        if (fr < IN) atomicAdd(&g.W1[fr * HD + c], v);
+                        else if (fr == IN) atomicAdd(&g.b1[c], v);
+                    } else if (blk < S::kBlk1 + S::kBlk2) {
+                        if (fr < HD) atomicAdd(&g.W2[fr * HD + c], v);
+                        else if (fr == HD) atomicAdd(&g.b2[c], v);
+                    } else if (c < 3) {
+                        atomicAdd(&g.W3[fr * 3 + c], v);
+                    }
+                }
             }
         }
     }
