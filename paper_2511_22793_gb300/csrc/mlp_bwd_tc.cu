@@ -422,35 +422,71 @@ __global__ void __launch_bounds__(kRowsB, 1) k_mlp_bwd_tc(
 #pragma unroll
             for (int q = 0; q < 16; ++q) v[c + q] = w16[q];
         }
-        // every CTA adds into the same entries at about the same time: with 16-byte aligned
-        // gradients four entries go as one vector atomic (a quarter of the operations queueing
-        // at the L2)
-        const bool vec = ((reinterpret_cast<uintptr_t>(g.W1) | reinterpret_cast<uintptr_t>(g.W2)) & 15) == 0;
-        auto add_row = [&](float* dst, const float* src) {
-            if (vec) {
+        // every CTA adds into the same entries at about the same time, so the additions queue at
+        // the L2: with 16-byte aligned gradients the CTA's rows are laid out in shared memory as
+        // the gradient arrays (the per-row operand buffer is free after the last tile) and added
+        // by bulk reductions (cp.reduce.async.bulk .add.f32), else one atomic per entry
+        const bool aligned = ((reinterpret_cast<uintptr_t>(g.W1) | reinterpret_cast<uintptr_t>(g.b1) |
+                               reinterpret_cast<uintptr_t>(g.W2) | reinterpret_cast<uintptr_t>(g.b2) |
+                               reinterpret_cast<uintptr_t>(g.W3)) & 15) == 0;
+        constexpr int IN = GSPARC_MLP_IN;
+        constexpr int oW1 = 0, ob1 = oW1 + IN * HD, oW2 = ob1 + HD, ob2 = oW2 + HD * HD, oW3 = ob2 + HD;
+        static_assert(ob1 % 4 == 0 && oW2 % 4 == 0 && ob2 % 4 == 0 && oW3 % 4 == 0 && (3 * HD) % 4 == 0,
+                      "16-byte segments");
+        static_assert((oW3 + 3 * HD) * 4 <= L::kARow, "staging within the per-row operand buffer");
+        if (aligned) {
+            float* st = reinterpret_cast<float*>(sm + L::kA0);
+            auto put = [&](float* dst, const float* src, int n) {
+                for (int q = 0; q < n; q += 4) *reinterpret_cast<float4*>(dst + q) = make_float4(src[q], src[q + 1], src[q + 2], src[q + 3]);
+            };
+            if (t < IN) {
+                put(st + oW1 + t * HD, v, HD);
+            } else if (t >= L::kFH1 && t < L::kFH1 + HD) {
+                put(st + oW2 + (t - L::kFH1) * HD, v + HD, HD);
+            } else if (t >= L::kFH2 && t < L::kFH2 + HD) {
 #pragma unroll
-                for (int n = 0; n < HD; n += 4)
-                    atomicAdd(reinterpret_cast<float4*>(dst + n), make_float4(src[n], src[n + 1], src[n + 2], src[n + 3]));
-            } else {
+                for (int c = 0; c < 3; ++c) st[oW3 + (t - L::kFH2) * 3 + c] = v[2 * HD + c];
+            } else if (t == L::kFOne) {
+                put(st + ob1, v, HD);
+                put(st + ob2, v + HD, HD);
 #pragma unroll
-                for (int n = 0; n < HD; ++n) atomicAdd(dst + n, src[n]);
+                for (int c = 0; c < 3; ++c) atomicAdd(&g.b3[c], v[2 * HD + c]);
             }
-        };
-        if (t < GSPARC_MLP_IN) {
-            add_row(&g.W1[t * HD], v);
-        } else if (t >= L::kFH1 && t < L::kFH1 + HD) {
-            add_row(&g.W2[(t - L::kFH1) * HD], v + HD);
-        } else if (t >= L::kFH2 && t < L::kFH2 + HD) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) atomicAdd(&g.W3[(t - L::kFH2) * 3 + c], v[2 * HD + c]);
-        } else if (t == L::kFOne) {
-#pragma unroll
-            for (int n = 0; n < HD; ++n) {
-                atomicAdd(&g.b1[n], v[n]);
-                atomicAdd(&g.b2[n], v[HD + n]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the stores, to the bulk copies
+            __syncthreads();
+            if (t == 0) {
+                auto bulk_add = [&](float* dst, const float* src, int n) {
+                    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst),
+                                 "r"(static_cast<uint32_t>(__cvta_generic_to_shared(src))), "r"(4 * n)
+                                 : "memory");
+                };
+                bulk_add(g.W1, st + oW1, IN * HD);
+                bulk_add(g.b1, st + ob1, HD);
+                bulk_add(g.W2, st + oW2, HD * HD);
+                bulk_add(g.b2, st + ob2, HD);
+                bulk_add(g.W3, st + oW3, 3 * HD);
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // shared memory read before exit
             }
+        } else {
+            if (t < IN) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) atomicAdd(&g.b3[c], v[2 * HD + c]);
+                for (int n = 0; n < HD; ++n) atomicAdd(&g.W1[t * HD + n], v[n]);
+            } else if (t >= L::kFH1 && t < L::kFH1 + HD) {
+#pragma unroll
+                for (int n = 0; n < HD; ++n) atomicAdd(&g.W2[(t - L::kFH1) * HD + n], v[HD + n]);
+            } else if (t >= L::kFH2 && t < L::kFH2 + HD) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) atomicAdd(&g.W3[(t - L::kFH2) * 3 + c], v[2 * HD + c]);
+            } else if (t == L::kFOne) {
+#pragma unroll
+                for (int n = 0; n < HD; ++n) {
+                    atomicAdd(&g.b1[n], v[n]);
+                    atomicAdd(&g.b2[n], v[HD + n]);
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) atomicAdd(&g.b3[c], v[2 * HD + c]);
+            }
         }
     }
     if (!ok && t == 0) atomicAdd(&g.b3[0], __int_as_float(0x7fc00000));   // an expired wait poisons the result
