@@ -249,8 +249,8 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
     float2* s_geo2 = reinterpret_cast<float2*>(sm + L::kGeo2);
     float2* s_ext = reinterpret_cast<float2*>(sm + L::kExt);
     float* s_amp = reinterpret_cast<float*>(sm + L::kAmp);
-    float* s_phi = reinterpret_cast<float*>(sm + L::kPhi);
-    float* s_len = reinterpret_cast<float*>(sm + L::kLen);
+    float* s_phi = reinterpret_cast<float*>(sm + L::kPhi);   // per entry: phase_base at the strip's k0
+    float* s_len = reinterpret_cast<float*>(sm + L::kLen);   // per entry: phase step L df / c
     float* s_csi = reinterpret_cast<float*>(sm + L::kCsi);   // [warp][2S], every slot written once
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + F::kBars);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + F::kMisc);
@@ -364,8 +364,9 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
                     s_geo2[e] = make_float2(pf_p1.z, pf_at.z);
                     s_ext[e] = make_float2(pf_p0.z, pf_p0.w);
                     s_amp[e] = pf_at.x;
-                    s_phi[e] = pf_at.y;
-                    s_len[e] = pf_at.w;
+                    // the phasor operand's per-entry phase at the strip's first subcarrier and step
+                    s_phi[e] = phase_base(a, pf_at.w, pf_at.y, k0);
+                    s_len[e] = pf_at.w * a.dlam;
                 } else {
                     s_geo[e] = make_float4(0.f, 0.f, __int_as_float(0x7fc00000), 0.f);
                     s_geo2[e] = make_float2(0.f, 0.f);
@@ -393,7 +394,7 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
                     re[q] = 0.f;
                     im[q] = 0.f;
                     if (j < nb && k < a.K) {
-                        const float2 ph = unit_phasor(a, len[j], phi[j], k);
+                        const float2 ph = phasor_at(phi[j], len[j], kk);
                         re[q] = amp[j] * ph.x;
                         im[q] = amp[j] * ph.y;
                     }
@@ -789,8 +790,8 @@ struct TbMeta {
     float2* geo2;
     float2* ext;
     float* amp;
-    float* phi;
-    float* len;
+    float* phi;    // phase_base at the strip's first subcarrier
+    float* len;    // phase step L df / c
     uint32_t* gid;
 };
 
@@ -1062,8 +1063,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
                     md.geo2[e] = make_float2(pf_p1.z, pf_at.z);
                     md.ext[e] = make_float2(pf_p0.z, pf_p0.w);
                     md.amp[e] = pf_at.x;
-                    md.phi[e] = pf_at.y;
-                    md.len[e] = pf_at.w;
+                    // the phasor operand's per-entry phase at the strip's first subcarrier and step
+                    md.phi[e] = phase_base(a, pf_at.w, pf_at.y, k0);
+                    md.len[e] = pf_at.w * a.dlam;
                     md.gid[e] = pf_gid;
                 } else {
                     md.geo[e] = make_float4(0.f, 0.f, __int_as_float(0x7fc00000), 0.f);
@@ -1088,7 +1090,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
                 for (int q = 0; q < 8; q += 2) {
                     const int kk = (c0 + q) / 2, k = k0 + kk;
                     float2 u = make_float2(0.f, 0.f);
-                    if (j < nb && k < a.K) u = unit_phasor(a, md.len[j], md.phi[j], k);
+                    if (j < nb && k < a.K) u = phasor_at(md.phi[j], md.len[j], kk);
                     r0[q] = u.x;
                     r0[q + 1] = u.y;
                     r1[q] = u.y;
