@@ -158,21 +158,24 @@ def test_bin_sort_few_distinct_depths():
     assert np.array_equal(ranges, orng)
 
 
-def test_bin_sort_serving_scale_sampled_tiles():
-    """The 500k-Gaussian serving scene at 720x180 (about 11M pairs; the densest tiles
-    above the shared-memory capacity): the GPU's own projection records binned and
-    sorted, every tile's pair count against the oracle's footprint rule, and the full
-    (r, id) lists of the 8 largest tiles and 8 random ones bit for bit."""
+@pytest.mark.parametrize("H,W", [(180, 720), (90, 360), (45, 180)])
+def test_bin_sort_serving_scale_sampled_tiles(H, W):
+    """The 500k-Gaussian serving scene at its three resolutions (1.7M to 11M pairs; the densest
+    tiles above the shared-memory capacity): at 720x180 the tiles outnumber the SMs and such
+    buckets are sorted whole, at 360x90 and 180x45 they are cut into slices sorted by blocks of
+    their own.  The GPU's own projection records binned and sorted, every tile's pair count
+    against the oracle's footprint rule, and the full (r, id) lists of the 8 largest tiles and 8
+    random ones bit for bit."""
     sc = synth.make_scene(500_000, seed=0, bf16_latent=True)
     ds = DeviceScene.from_host(sc, DEV)
-    r = Renderer(180, 720, 1, sc.n, device=DEV)
+    r = Renderer(H, W, 1, sc.n, device=DEV)
     r.geometry(ds)
     assert r.check() == 0
     npairs = int(r.n_pairs.item())
     rec = r.proj.cpu().numpy()
     ids = r.sorted_ids[:npairs].cpu().numpy().view(np.uint32)
     rng = r.tile_ranges.cpu().numpy().view(np.uint32).astype(np.int64)
-    tiles = obs.footprint_tiles(rec, 180, 720)
+    tiles = obs.footprint_tiles(rec, H, W)
     lens = np.fromiter((len(t) for t in tiles), dtype=np.int64, count=len(tiles))
     flat = np.fromiter((t for ts in tiles for t in ts), dtype=np.int64, count=int(lens.sum()))
     owner = np.repeat(np.arange(len(tiles), dtype=np.int64), lens)
