@@ -411,9 +411,11 @@ def run_ours(args, rank, world, local_rank):
         "kernels_ms": head["kernels_ms"],
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": head["h2d"],
                 "d2h_bytes_per_step": head["d2h"], "ms_per_step": e2e_total / args.steps,
-                "copies": "inside the step's graph: scene, network and transmitters first, the target spectrum "
-                          "on a third stream beside projection, binning and the forward (spectrum written, "
-                          "loss by gsparc_l2_loss once the target is in)",
+                "copies": "inside the step's graph: means, log-scales and quaternions first (projection's "
+                          "inputs), the rest of the scene, the network and the transmitters on the second "
+                          "stream ahead of the network forward, the target spectrum on a third stream after "
+                          "them, beside projection, binning and the forward (spectrum written, loss by "
+                          "gsparc_l2_loss once the target is in)",
                 "agrees_with_step_graph": head["agree"]},
         "gpu_launches": st.launches * args.steps,
         "launch": "whole step captured once as a CUDA graph (gradient zeroing and network forward beside "

@@ -176,26 +176,31 @@ class TrainStep:
 
     def enqueue_from_host(self, inp):
         """The step with its inputs in pinned host memory (`inp`: a PackedInputs whose views are
-        this step's scene, network, transmitters and, last, the target): the scene, network and
-        transmitters are copied first, the target on a third stream beside projection, binning and
-        the forward, which therefore writes the spectrum (the tensor-core form's fused loss would
-        wait for the whole target); the loss and dL/dz follow once the target is in, and the
-        tensor-core backward forms s_tot from the spectrum.  Same loss and gradients as enqueue()."""
+        this step's scene (means, log-scales, quaternions first), network, transmitters and, last,
+        the target): the projection's inputs are copied first, then the rest of the scene, the
+        network and the transmitters on the second stream ahead of the network forward, and the
+        target on a third stream after them, beside projection, binning and the forward, which
+        therefore writes the spectrum (the fused loss would wait for the whole target); the loss
+        and dL/dz follow once the target is in, and the backward forms s_tot from the spectrum.
+        Same loss and gradients as enqueue()."""
         r, s = self.r, self.scene
         cur = torch.cuda.current_stream(r.device)
         if not hasattr(self, "copy_s"):
             self.copy_s = torch.cuda.Stream(r.device)
-        inp.upload(0, len(inp.views) - 1)
-        scene_in = torch.cuda.Event()
-        scene_in.record(cur)
-        self.copy_s.wait_event(scene_in)
+        inp.upload(0, 3)
+        geo_in = torch.cuda.Event()
+        geo_in.record(cur)
+        self.side.wait_event(geo_in)
+        with torch.cuda.stream(self.side):
+            inp.upload(3, len(inp.views) - 1)
+            rest_in = torch.cuda.Event()
+            rest_in.record(self.side)
+            self.gbuf.zero_()
+        self.copy_s.wait_event(rest_in)
         with torch.cuda.stream(self.copy_s):
             inp.upload(len(inp.views) - 1)
         tgt_in = torch.cuda.Event()
         tgt_in.record(self.copy_s)
-        self.side.wait_event(scene_in)
-        with torch.cuda.stream(self.side):
-            self.gbuf.zero_()
         self._mlp_fwd(self.side)
         joined = torch.cuda.Event()
         joined.record(self.side)
