@@ -286,3 +286,42 @@ def test_attr_mlp_bwd_tensor_cores(n, B, hidden, seed):
         e_fp, e_or = rel_l2(tc[c], fp[c]), rel_l2(tc[c], ref[c])
         assert e_fp <= (1e-4 if c < 3 else 1e-3), "%s: relative L2 vs FP32 kernel %.3e" % (k, e_fp)
         assert e_or <= 1e-3, "%s: relative L2 vs oracle %.3e" % (k, e_or)
+
+
+@pytest.mark.parametrize("tc", [False, True])
+def test_attr_mlp_bwd_weight_gradients_unaligned(tc):
+    """The network backward adds each thread block's weight and bias gradients by bulk reductions
+    when the gradient arrays are 16-byte aligned and by one atomic per entry otherwise: the same
+    weight, bias and per-Gaussian gradients either way (views of a buffer at a 4-byte offset
+    against separate tensors; relative L2 <= 1e-5, the additions only reordered)."""
+    n, B, hidden, seed = 3000, 2, 32, 61
+    sc = synth.make_scene(n, seed=seed)
+    mlp = synth.make_mlp(hidden, seed=seed + 1)
+    tx = synth.make_tx(B, seed=seed + 2)
+    r = Renderer(90, 360, 1, n, device=DEV)
+    ds = DeviceScene.from_host(sc, DEV)
+    dm = DeviceMLP.from_host(mlp, DEV)
+    txd = torch.tensor(tx, device=DEV)
+    d_attr = torch.tensor(np.random.default_rng(seed + 3).normal(size=(B, n, 4)).astype(np.float32), device=DEV)
+
+    def grads(unaligned):
+        shapes = [t.shape for t in dm.tensors()]
+        sizes = [int(np.prod(sh)) for sh in shapes]
+        if unaligned:
+            flat = torch.zeros(sum(sizes) + 1, device=DEV)
+            offs = np.cumsum([1] + sizes)
+            gw = [flat[int(o):int(o) + z].view(sh) for o, z, sh in zip(offs[:-1], sizes, shapes)]
+            assert all(t.data_ptr() % 16 != 0 for t in gw[:4])
+        else:
+            gw = [torch.zeros(sh, device=DEV) for sh in shapes]
+        gm = torch.zeros((n, 3), device=DEV)
+        go = torch.zeros(n, device=DEV)
+        gl = torch.zeros((n, 16), device=DEV)
+        r.attributes_backward(ds, dm, txd, d_attr, gm, go, gl, gw, tensor_cores=tc)
+        torch.cuda.synchronize()
+        return [t.cpu().numpy().astype(np.float64) for t in [gm, go, gl] + gw]
+
+    a, u = grads(False), grads(True)
+    for c, k in enumerate(["means", "opacity_logit", "latent", "W1", "b1", "W2", "b2", "W3", "b3"]):
+        assert np.all(np.isfinite(u[c])), k
+        assert rel_l2(u[c], a[c]) <= 1e-5, "%s: %.3e" % (k, rel_l2(u[c], a[c]))
