@@ -582,8 +582,10 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
                     const int k = k0 + c / 2 + q;
                     if (k < a.K) {
                         const float nan = __int_as_float(0x7fc00000);
-                        a.spectrum[((size_t)b * a.K + k) * plane + pix] =
-                            ok ? make_float2(v[2 * q], v[2 * q + 1]) : make_float2(nan, nan);
+                        const float2 z = ok ? make_float2(v[2 * q], v[2 * q + 1]) : make_float2(nan, nan);
+                        float2* dst = &a.spectrum[((size_t)b * a.K + k) * plane + pix];
+                        if (a.stream_out) __stcs(dst, z);
+                        else *dst = z;
                     }
                 }
             }

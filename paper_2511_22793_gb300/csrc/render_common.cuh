@@ -101,6 +101,9 @@ struct RenderArgs {
     int32_t* status;
     // polls before a pipeline wait of the tensor-core kernels gives up
     uint32_t spin;
+    // the spectrum is written with evict-first stores (a large output would otherwise push the
+    // Gaussians' records out of L2 while the kernel still gathers them)
+    bool stream_out;
     // cycles of subcarrier k = L * (lam0_hi + lam0_lo + k * dlam), lam = f / c
     float lam0_hi, lam0_lo, dlam;
     // d(psi)/dL = -2 pi f_k / c, split as c_f0 + kk * c_df inside a strip
@@ -687,7 +690,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_fwd(RenderArgs a) {
                 if (k >= a.K) continue;
                 const size_t e = ((size_t)b * a.K + k) * plane + pix;
                 const float2 z = acc[k8 + q];
-                if (a.spectrum) a.spectrum[e] = z;
+                if (a.spectrum) {
+                    if (a.stream_out) __stcs(&a.spectrum[e], z);
+                    else a.spectrum[e] = z;
+                }
                 if (a.l2_grad) {
                     const float dr = z.x - t[q].x, di = z.y - t[q].y;
                     l2acc = fmaf(dr, dr, fmaf(di, di, l2acc));
@@ -993,6 +999,8 @@ bool fill_args(const gsparc_view* view, const gsparc_band* band, int32_t B, int3
     a.two_pi_over_c = 2.0 * 3.14159265358979323846 / kCLight;
     a.f0 = f0;
     a.df = band->df;
+    // an output above a quarter of the 129 MB L2 streams past it
+    a.stream_out = (double)B * band->K * view->H * view->W * 8.0 > 32.0 * 1024 * 1024;
     return true;
 }
 
