@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_fwd(RenderArgs a) {
         if (__any_sync(0xffffffffu, !done)) {
             // groups of 8 entries.  alpha and log2(1 - alpha): eval_alpha's operations in its order
             // (the backward re-takes the same decisions; a skipped entry gets al = -1), branch-free
-            // over the whole group when three or more of its entries reach the warp's rows (the
+            // over the whole group when five or more of its entries can be live at the warp's pixels (the
             // eight evaluations overlap), entry by entry otherwise.  Then the transmittance
             // recursion and the accumulation in list order.  A group that misses the warp is skipped.
             auto alpha_of = [&](int j, float& al, float& nlv) {
@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_fwd(RenderArgs a) {
             for (int g0 = 0; g0 < kBatch; g0 += 8) {
                 const uint32_t gbits = (uint32_t)(mask >> g0) & 0xffu;
                 if (gbits == 0u) continue;   // warp-uniform
-                if (__popc(gbits) <= 2) {
+                if (__popc(gbits) <= 4) {
                     for (uint32_t bits = gbits; bits; bits &= bits - 1u) {
                         const int j = g0 + __ffs((int)bits) - 1;
                         float al, nlv;
