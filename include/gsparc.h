@@ -698,6 +698,9 @@ int gsparc_scale_rows(int32_t rows, int64_t per, const float* w, float* x, void*
  * well above any wait of a healthy launch).  Process-wide; read when a call
  * enqueues its kernel.  Returns the previous setting.  Meant for tests of the
  * timeout path: a small bound makes a wait expire without a fault or a hang.
+ * Bounds below 1024 are counted in non-blocking polls (mbarrier.test_wait), so
+ * that a bound of 1 ends every wait whose phase is not already complete; larger
+ * bounds poll with the suspending mbarrier.try_wait.
  */
 uint32_t gsparc_set_wait_limit(uint32_t polls);
 

@@ -61,8 +61,27 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
+// Limits below this many polls are counted with the non-blocking mbarrier.test_wait: a
+// try_wait may suspend the thread until the phase completes (up to a hardware-chosen window), so
+// a limit of a few try_wait polls can still see every phase complete.  With test_wait a limit of
+// one poll ends each wait whose phase is not already complete when the thread first looks.
+constexpr uint32_t kCountedPolls = 1024;
+
 // Bounded wait for the given phase parity; false when `polls` polls found it incomplete.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t polls = kSpin) {
+    if (polls < kCountedPolls) {
+        for (uint32_t it = 0; it < polls; ++it) {
+            uint32_t done;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}\n"
+                : "=r"(done)
+                : "r"(mbar), "r"(parity)
+                : "memory");
+            if (done) return true;
+        }
+        return false;
+    }
     for (uint32_t it = 0; it < polls; ++it) {
         uint32_t done;
         asm volatile(
