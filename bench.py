@@ -241,6 +241,26 @@ def _make_inputs(dev, rank, world):
     return sc, mlp, tx, inp
 
 
+def entries_visited(st, r, composited):
+    """Tile-list entries the compositing walks per algorithmic unit (the Gaussians composited at a
+    pixel, per subcarrier): at the pixel (entries up to the pixel's last composited one), at the
+    tile (its CTA walks until every pixel of the tile has stopped) and the whole tile lists."""
+    H, W = r.H, r.W
+    TW, TH = (W + 15) // 16, (H + 15) // 16
+    rows = np.minimum(16, H - 16 * np.arange(TH))
+    cols = np.minimum(16, W - 16 * np.arange(TW))
+    px = np.outer(rows, cols).reshape(-1).astype(np.float64)                  # pixels of tile t
+    walks = st.walks.double().cpu().numpy()                                    # [B, T]
+    rng = r.tile_ranges.view(-1, 2).long().cpu().numpy()
+    lists = (rng[:, 1] - rng[:, 0]).astype(np.float64)
+    c = float(max(composited, 1))
+    return {"per_pixel_walk": float(st.nc.double().sum().item()) / c,
+            "per_tile_walk": float((walks * px[None, :]).sum()) / c,
+            "per_tile_list": float((lists * px).sum()) * st.B / c,
+            "note": "tile-list entries per composited (Gaussian, pixel); the units count only the "
+                    "composited ones"}
+
+
 def time_form(args, dev, form, inp, steps, flush, sampler=None, dist=False):
     """Build the step of `form` on the packed inputs, check it, time its kernels (eager, per
     stage), the step graph (device-resident inputs) and the host-input graph (end to end)."""
@@ -265,6 +285,7 @@ def time_form(args, dev, form, inp, steps, flush, sampler=None, dist=False):
         raise RuntimeError("device status %d after warm-up (%s)" % (r.check(), form))
     units = int(st.n_used.sum().item()) * K
     n_pairs = int(r.n_pairs.item())
+    visited = entries_visited(st, r, units // K)
     # per-kernel durations: eager steps with CUDA events around every stage (one stream)
     per_kernel = {k: [] for k in st.stages}
     for _ in range(min(steps, 50)):
@@ -329,7 +350,8 @@ def time_form(args, dev, form, inp, steps, flush, sampler=None, dist=False):
     # the step's spectrum (its fused forward does not store it), for the accuracy comparison
     spec = st.spectrum().detach().cpu()
     torch.cuda.synchronize(dev)
-    return {"st": st, "r": r, "units": units, "n_pairs": n_pairs, "step_ms": step_ms, "e2e_ms": e2e_ms,
+    return {"st": st, "r": r, "units": units, "n_pairs": n_pairs, "visited": visited, "step_ms": step_ms,
+            "e2e_ms": e2e_ms,
             "kernels_ms": {k: statistics.mean(v) for k, v in per_kernel.items()}, "agree": agree,
             "clocks": clocks, "spec": spec, "h2d": inp.nbytes, "d2h": host_loss.numel() * host_loss.element_size()}
 
@@ -399,6 +421,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": wl["name"], "n_gaussians": wl["n"], "subcarriers": wl["K"], "H": wl["H"],
                    "W": wl["W"], "hidden": wl["hidden"], "transmitters_per_step": wl["B"],
                    "pairs": head["n_pairs"], "units_per_step": job_units // args.steps,
+                   "entries_visited_per_unit": head["visited"],
                    "l2": "flushed (256 MiB write) between timed steps",
                    "compositing": ("subcarrier sums on tensor cores (split-BF16 products, FP32 accumulation), "
                                    "transmittance and gradients FP32") if tc_head else "FP32 CUDA cores",
@@ -420,7 +443,9 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": st.launches * args.steps,
         "launch": "whole step captured once as a CUDA graph (gradient zeroing and network forward beside "
                   "projection and bin/sort, projection backward beside network backward, on a second "
-                  "stream), replayed per timed step",
+                  "stream), replayed per timed step; launch overlap %s (tile emit and sort, the backward's "
+                  "schedule and walks and the network backward launched as programmatic dependents of the "
+                  "kernel before them)" % args.launch_overlap,
         "roofline": dom,
         "roofline_kernels": rl,
         "clocks": head["clocks"],
@@ -1297,8 +1322,13 @@ def main():
                          "queries with the fused CSI head; emission: the per-Gaussian emission "
                          "network's width sweep; spectrum_loss: the L1 + SSIM loss of Eq. 4; train_extras: "
                          "densification (Algorithm 1) and the confidence objective (Eq. 5)")
+    ap.add_argument("--launch-overlap", default="on", choices=["on", "off"],
+                    help="programmatic dependent launch of the library's follow-on kernels (gsparc_set_launch_overlap)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.impl != "reference":
+        from paper_2511_22793_gb300 import gsparc as G
+        G.gsparc_set_launch_overlap(args.launch_overlap == "on")
 
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)

@@ -705,6 +705,26 @@ int gsparc_scale_rows(int32_t rows, int64_t per, const float* w, float* x, void*
 uint32_t gsparc_set_wait_limit(uint32_t polls);
 
 /*
+ * Launch overlap (programmatic dependent launch), process-wide.  `groups` is a
+ * mask of the GSPARC_OVERLAP_* groups below (GSPARC_OVERLAP_ALL, the default,
+ * or 0 for none).  The kernels of a group in the mask, which follow another
+ * kernel of the library on a stream, are launched so that they may be
+ * scheduled while the kernel before them is still running; each waits on the
+ * device, before it touches any buffer, until that kernel has completed and
+ * its writes are visible.  Results are the same either way (bit for bit where
+ * the call is deterministic); outside the mask a launch is an ordinary one.
+ * Read when a call enqueues its kernels, so it also holds inside a CUDA graph
+ * captured while it was set.  Returns the previous mask.
+ */
+#define GSPARC_OVERLAP_BIN_SORT 1   /* gsparc_bin_sort: tile emit and sort      */
+#define GSPARC_OVERLAP_FORWARD 2    /* the compositing forward kernels          */
+#define GSPARC_OVERLAP_SCHEDULE 4   /* the balanced backward's schedule        */
+#define GSPARC_OVERLAP_BACKWARD 8   /* the compositing backward walks          */
+#define GSPARC_OVERLAP_NETWORK 16   /* gsparc_attr_mlp_bwd (FP32, tensor-core)  */
+#define GSPARC_OVERLAP_ALL 31
+int32_t gsparc_set_launch_overlap(int32_t groups);
+
+/*
  * Synchronise `stream`, then return the value of the device status word
  * (GSPARC_OK if no device-side condition was raised) or GSPARC_ERR_CUDA if
  * the stream reports an error.  d_status may be NULL (stream check only).

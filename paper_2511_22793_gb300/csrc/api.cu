@@ -7,7 +7,10 @@
 namespace gsparc {
 namespace {
 std::atomic<uint32_t> g_wait_limit{0};
+std::atomic<int32_t> g_overlap{GSPARC_OVERLAP_ALL};
 }  // namespace
+
+bool launch_overlap(int32_t group) { return (g_overlap.load(std::memory_order_relaxed) & group) != 0; }
 
 uint32_t wait_limit(uint32_t dflt) {
     const uint32_t v = g_wait_limit.load(std::memory_order_relaxed);
@@ -17,6 +20,10 @@ uint32_t wait_limit(uint32_t dflt) {
 
 extern "C" uint32_t gsparc_set_wait_limit(uint32_t polls) {
     return gsparc::g_wait_limit.exchange(polls, std::memory_order_relaxed);
+}
+
+extern "C" int32_t gsparc_set_launch_overlap(int32_t groups) {
+    return gsparc::g_overlap.exchange(groups & GSPARC_OVERLAP_ALL, std::memory_order_relaxed);
 }
 
 extern "C" int gsparc_check(const int32_t* d_status, void* stream) {

@@ -67,10 +67,12 @@ int bin_sort_launch(const gsparc_view* view, int N, const float* proj, int64_t p
     k_tile_count<<<L.nblk, kBinThreads, 0, s>>>(N, view->H, view->W, TW, T, p4, cnt, bcnt, cursor, done, cap,
                                                 ranges, n_pairs, extra, slice_big_buckets(T, num_sms()) ? 1 : 0,
                                                 d_status);
-    k_tile_emit<<<L.nblk, kBinThreads, 0, s>>>(N, view->H, view->W, TW, T, p4, bcnt, cursor, cap, keys);
-    k_tile_sort<<<sort_grid(T, cap, num_sms()), kSortThreads, kSortSmem, s>>>(T, ranges, extra, done + 1, keys,
-                                                                              alt, sorted_ids, sorted_keys);
-    return launch_status();
+    if (launch_status() != GSPARC_OK) return GSPARC_ERR_CUDA;
+    if (launch_after(GSPARC_OVERLAP_BIN_SORT, k_tile_emit, dim3(L.nblk), dim3(kBinThreads), 0, s, N, view->H, view->W, TW, T, p4, bcnt,
+                     cursor, cap, keys) != GSPARC_OK)
+        return GSPARC_ERR_CUDA;
+    return launch_after(GSPARC_OVERLAP_BIN_SORT, k_tile_sort, dim3(sort_grid(T, cap, num_sms())), dim3(kSortThreads), kSortSmem, s, T,
+                        ranges, extra, done + 1, keys, alt, sorted_ids, sorted_keys);
 }
 
 }  // namespace

@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(kBinThreads) k_tile_count(int N, int H, int W,
     __shared__ uint32_t s_warp[kBinThreads / 32];
     __shared__ uint64_t s_carry;
     __shared__ bool s_last;
+    grid_dep_wait();
     const bool local = T <= kSmemTiles;
     if (local) {
         for (int t = threadIdx.x; t < T; t += kBinThreads) s_cnt[t] = 0;
@@ -208,6 +209,7 @@ __global__ void __launch_bounds__(kBinThreads) k_tile_count(int N, int H, int W,
             if (mine) mine[t] = c;
         }
     }
+    grid_dep_launch();   // the emit pass may become resident while the last block scans
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
@@ -292,6 +294,9 @@ __global__ void __launch_bounds__(kBinThreads) k_tile_emit(int N, int H, int W, 
     Foot f;
     const bool valid = i < N && footprint(proj[2 * i], H, W, TW, f);
     const uint64_t key = valid ? ((uint64_t)__float_as_uint(proj[2 * i + 1].w) << 32) | (uint32_t)i : 0;
+    // the footprints above read only the projection, complete before k_tile_count began; the
+    // counts, offsets and buckets below come from k_tile_count
+    grid_dep_wait();
     if (!local) {
         warp_pairs(valid, f, TW, [&](int t, int owner, bool active) {
             const uint64_t k = __shfl_sync(0xffffffffu, key, owner);
@@ -819,6 +824,7 @@ __global__ void __launch_bounds__(kSortThreads, 1) k_tile_sort(int T, const uint
     SortShared& sh = *reinterpret_cast<SortShared*>(smem_raw);
     uint64_t* buf = reinterpret_cast<uint64_t*>(smem_raw + ((sizeof(SortShared) + 15) & ~size_t(15)));
     __shared__ uint32_t s_item;
+    grid_dep_wait();
     const uint32_t n_items = (uint32_t)T + __ldg(&extra[T]);
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(work, 1u);

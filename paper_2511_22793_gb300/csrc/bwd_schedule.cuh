@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(kSchedThreads) k_bwd_schedule(int H, int W, in
     __shared__ uint32_t s_off[kSchedKeys];
     __shared__ uint32_t s_warp[kSchedThreads / 32];
     __shared__ bool s_last;
+    grid_dep_wait();     // the forward's walks or n_contrib
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (!walks_in) {
         const int tile = (int)(blockIdx.x % (uint32_t)T), b = (int)(blockIdx.x / (uint32_t)T);

@@ -29,6 +29,23 @@ __device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
     if (status) atomicCAS(reinterpret_cast<int*>(status), 0, code);
 }
 
+// Programmatic dependent launch.  A kernel the host launched with programmatic stream
+// serialization (launch_after) may be scheduled while the kernel before it on the stream is still
+// running.  grid_dep_wait() returns once that kernel has completed and its writes are visible (at
+// once when the launch carried no such dependency), so every such kernel calls it in every block
+// before it reads or writes anything the kernels before it touch.  The next kernel is scheduled
+// once every block of this grid has exited or called grid_dep_launch(); it still waits in its own
+// grid_dep_wait() for this whole grid.  A block that triggers early keeps the dependents' blocks
+// resident beside its own remaining work, so only k_tile_count does (its last block's scan is then
+// overlapped with the emit pass's footprints); the other kernels let their exit trigger.
+#ifdef GSPARC_HOST_SHIM
+inline void grid_dep_wait() {}
+inline void grid_dep_launch() {}
+#else
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#endif
+
 inline int tiles_x(const gsparc_view& v) { return (v.W + kTile - 1) / kTile; }
 inline int tiles_y(const gsparc_view& v) { return (v.H + kTile - 1) / kTile; }
 

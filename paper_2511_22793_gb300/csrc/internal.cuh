@@ -21,6 +21,34 @@ inline int launch_status() {
 }
 
 
+// Whether launch_after launches the kernels of `group` (GSPARC_OVERLAP_*) with programmatic stream
+// serialization (gsparc_set_launch_overlap; every group unless switched off).
+bool launch_overlap(int32_t group);
+
+// Launches k<<<grid, block, smem, s>>>(args...) as a programmatic dependent of the kernel before it
+// on the stream (programmatic stream serialization), for kernels that call grid_dep_wait() in every
+// block before they touch what earlier kernels wrote or read: the launch is processed while the
+// previous kernel drains, not after it.  Without launch_overlap(group) an ordinary launch.
+template <typename... P, typename... A>
+inline int launch_after(int32_t group, void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                        A&&... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = launch_overlap(group) ? 1 : 0;
+    if (cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return GSPARC_ERR_CUDA;
+    }
+    return launch_status();
+}
+
 // Polls before a pipeline wait of the tensor-core compositing kernels gives up: the value set by
 // gsparc_set_wait_limit, or dflt when none is set.
 uint32_t wait_limit(uint32_t dflt);

@@ -37,9 +37,8 @@ int launch_bwd(int N, int B, const float* tx, const float* rx, const float* mean
     const int64_t rows = (int64_t)N * B;
     const int64_t tiles = (rows + kBwdRows - 1) / kBwdRows;
     const int blocks = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * (HD <= 32 ? 3 : 1));
-    k_mlp_bwd<HD><<<blocks, kBwdThreads, smem, s>>>(N, B, tx, rx[0], rx[1], rx[2], means, ologit, latent, w,
-                                                 d_attr, d_means, d_ologit, d_latent, g);
-    return GSPARC_OK;
+    return launch_after(GSPARC_OVERLAP_NETWORK, k_mlp_bwd<HD>, dim3(blocks), dim3(kBwdThreads), smem, s, N, B, tx, rx[0], rx[1], rx[2], means,
+                        ologit, latent, w, d_attr, d_means, d_ologit, d_latent, g);
 }
 
 }  // namespace

@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(kRowsB, 1) k_mlp_bwd_tc(
     uint8_t* GAlo = sm + L::kGAlo;
     uint8_t* GBhi = sm + L::kGBhi;
     uint8_t* GBlo = sm + L::kGBlo;
+    grid_dep_wait();     // the attribute gradients of the compositing backward
 
     put_weights3<HD, kK0>(sm + L::kW1T, W1, true, HD, HD, GSPARC_MLP_IN);
     put_weights3<HD, HD>(sm + L::kW2T, W2, true, HD, HD, HD);
@@ -509,11 +510,9 @@ int launch_bwd_tc(int32_t N, int32_t B, const float* tx, const float* rx, const 
     const int64_t tiles = ((int64_t)N * B + kRowsB - 1) / kRowsB;
     // one CTA per SM (the operands take most of its shared memory)
     const int blocks = (int)std::min<int64_t>(tiles, (int64_t)num_sms());
-    k_mlp_bwd_tc<HD><<<blocks, kRowsB, L::kTotal, s>>>(N, B, tx, rx[0], rx[1], rx[2], means, ologit, latent, m->W1,
-                                                       m->b1, m->W2, m->b2, m->W3, m->b3,
-                                                       reinterpret_cast<const float4*>(d_attr), d_means, d_ologit,
-                                                       d_latent, g);
-    return launch_status();
+    return launch_after(GSPARC_OVERLAP_NETWORK, k_mlp_bwd_tc<HD>, dim3(blocks), dim3(kRowsB), L::kTotal, s, N, B, tx, rx[0], rx[1], rx[2],
+                        means, ologit, latent, m->W1, m->b1, m->W2, m->b2, m->W3, m->b3,
+                        reinterpret_cast<const float4*>(d_attr), d_means, d_ologit, d_latent, g);
 }
 
 }  // namespace

@@ -299,6 +299,7 @@ __global__ void __launch_bounds__(kBwdThreads, HD <= 32 ? 3 : 1)
     constexpr int IN = GSPARC_MLP_IN, R = kBwdRows, CW = HD / 8;
     GSPARC_DYNAMIC_SMEM(sm_raw);
     float* sm = reinterpret_cast<float*>(sm_raw);
+    grid_dep_wait();     // the attribute gradients of the compositing backward
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     for (int e = t; e < IN * HD; e += kBwdThreads) {
         const float v = w.W1[e];

@@ -16,8 +16,7 @@ int launch_fwd(const RenderArgs& a, int T, cudaStream_t s) {
     constexpr int smem = F32Smem<S>::kTotal;
     if (!ensure_smem_attr(k_render_fwd<S>, smem)) return GSPARC_ERR_CUDA;
     dim3 grid((a.K + S - 1) / S, T, a.B);
-    k_render_fwd<S><<<grid, kThreads, smem, s>>>(a);
-    return launch_status();
+    return launch_after(GSPARC_OVERLAP_FORWARD, k_render_fwd<S>, grid, dim3(kThreads), smem, s, a);
 }
 
 // max_items > 0: a scheduled launch (a.items), one CTA per item
@@ -25,13 +24,9 @@ template <int S>
 int launch_bwd(const RenderArgs& a, int T, cudaStream_t s, uint32_t max_items = 0) {
     constexpr int smem = F32BwdSmem<S>::kTotal;
     if (!ensure_smem_attr(k_render_bwd<S>, smem)) return GSPARC_ERR_CUDA;
-    if (max_items) {
-        k_render_bwd<S><<<max_items, kThreads, smem, s>>>(a);
-    } else {
-        dim3 grid((a.K + S - 1) / S, T, a.B);
-        k_render_bwd<S><<<grid, kThreads, smem, s>>>(a);
-    }
-    return launch_status();
+    if (max_items) return launch_after(GSPARC_OVERLAP_BACKWARD, k_render_bwd<S>, dim3(max_items), dim3(kThreads), smem, s, a);
+    dim3 grid((a.K + S - 1) / S, T, a.B);
+    return launch_after(GSPARC_OVERLAP_BACKWARD, k_render_bwd<S>, grid, dim3(kThreads), smem, s, a);
 }
 
 int launch_fwd_any(const RenderArgs& a, int T, cudaStream_t s) {
@@ -264,6 +259,7 @@ __global__ void __launch_bounds__(kFwsThreads, 1) k_render_fwd_ws(RenderArgs a) 
     auto aready_bar = [&](int st) { return smem_u32(&bars[4 + st]); };
     auto mdone_bar = [&](int st) { return smem_u32(&bars[6 + st]); };
     const uint32_t drain_bar = smem_u32(&bars[8]);
+    grid_dep_wait();     // the tile lists and attributes of the kernels before
 
     const int strip = blockIdx.x, tile = blockIdx.y, b = blockIdx.z;
     const int k0 = strip * S;
@@ -675,8 +671,7 @@ int launch_fwd_tc(const RenderArgs& a, int T, cudaStream_t s) {
     using F = RFwsSmem<S>;
     if (!ensure_smem_attr(k_render_fwd_ws<S>, F::kTotal)) return GSPARC_ERR_CUDA;
     dim3 grid((a.K + S - 1) / S, T, a.B);
-    k_render_fwd_ws<S><<<grid, kFwsThreads, F::kTotal, s>>>(a);
-    return launch_status();
+    return launch_after(GSPARC_OVERLAP_FORWARD, k_render_fwd_ws<S>, grid, dim3(kFwsThreads), F::kTotal, s, a);
 }
 
 }  // namespace
@@ -864,6 +859,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_render_bwd_ws(RenderArgs a) {
     auto full_bar = [&](int st) { return smem_u32(&bars[st]); };
     auto empty_bar = [&](int st) { return smem_u32(&bars[kWsR + st]); };
     auto bready_bar = [&](int st) { return smem_u32(&bars[2 * kWsR + st]); };
+    grid_dep_wait();     // the schedule's items, the forward's outputs and the upstream gradient
 
     // work item: a scheduled chunk [chunk_lo, chunk_end) of one (transmitter, tile, strip)
     // walk, or (no item list) the whole walk, whose end is then known after the prologue
@@ -1306,13 +1302,9 @@ template <int S>
 int launch_bwd_tc(const RenderArgs& a, int T, cudaStream_t s, uint32_t max_items = 0) {
     using L = RWsSmem<S>;
     if (!ensure_smem_attr(k_render_bwd_ws<S>, L::kTotal)) return GSPARC_ERR_CUDA;
-    if (a.items) {
-        k_render_bwd_ws<S><<<max_items, kWsThreads, L::kTotal, s>>>(a);
-    } else {
-        dim3 grid((a.K + S - 1) / S, T, a.B);
-        k_render_bwd_ws<S><<<grid, kWsThreads, L::kTotal, s>>>(a);
-    }
-    return launch_status();
+    if (a.items) return launch_after(GSPARC_OVERLAP_BACKWARD, k_render_bwd_ws<S>, dim3(max_items), dim3(kWsThreads), L::kTotal, s, a);
+    dim3 grid((a.K + S - 1) / S, T, a.B);
+    return launch_after(GSPARC_OVERLAP_BACKWARD, k_render_bwd_ws<S>, grid, dim3(kWsThreads), L::kTotal, s, a);
 }
 
 int launch_bwd_tc_any(const RenderArgs& a, int T, cudaStream_t s, uint32_t max_items = 0) {
@@ -1393,10 +1385,11 @@ extern "C" int gsparc_render_bwd_tc_balanced(const gsparc_view* view, const gspa
     const int allow_split = units <= 2 * (int64_t)num_sms() ? 1 : 0;
     // without s_tot or the spectrum a front chunk has no suffix: order the walks, split none
     const int smin = (!spectrum && !s_tot) ? -1 : (split_min == 0 ? kSplitMinDefault : split_min);
-    k_bwd_schedule<<<tile_walk ? 1u : (unsigned)(B * T), kSchedThreads, 0, s>>>(
-        view->H, view->W, tiles_x(*view), T, B * T, strips, smin, allow_split, a.ranges, n_contrib, tile_walk, hdr,
-        reinterpret_cast<uint32_t*>(w + SL.walks), reinterpret_cast<uint4*>(w + SL.items));
-    if (launch_status() != GSPARC_OK) return GSPARC_ERR_CUDA;
+    if (launch_after(GSPARC_OVERLAP_SCHEDULE, k_bwd_schedule, dim3(tile_walk ? 1u : (unsigned)(B * T)), dim3(kSchedThreads), 0, s, view->H,
+                     view->W, tiles_x(*view), T, B * T, strips, smin, allow_split, a.ranges, n_contrib, tile_walk,
+                     hdr, reinterpret_cast<uint32_t*>(w + SL.walks),
+                     reinterpret_cast<uint4*>(w + SL.items)) != GSPARC_OK)
+        return GSPARC_ERR_CUDA;
     return launch_bwd_tc_any(a, T, s, (uint32_t)(2 * units));
 }
 
@@ -1444,9 +1437,10 @@ extern "C" int gsparc_render_bwd_balanced(const gsparc_view* view, const gsparc_
     // two CTAs per SM: splitting pays while the units are too few to fill them twice over
     const int allow_split = units <= 4 * (int64_t)num_sms() ? 1 : 0;
     const int smin = (!spectrum && !s_tot) ? -1 : (split_min == 0 ? kSplitMinDefault : split_min);
-    k_bwd_schedule<<<tile_walk ? 1u : (unsigned)(B * T), kSchedThreads, 0, s>>>(
-        view->H, view->W, tiles_x(*view), T, B * T, strips, smin, allow_split, a.ranges, n_contrib, tile_walk, hdr,
-        reinterpret_cast<uint32_t*>(w + SL.walks), reinterpret_cast<uint4*>(w + SL.items));
-    if (launch_status() != GSPARC_OK) return GSPARC_ERR_CUDA;
+    if (launch_after(GSPARC_OVERLAP_SCHEDULE, k_bwd_schedule, dim3(tile_walk ? 1u : (unsigned)(B * T)), dim3(kSchedThreads), 0, s, view->H,
+                     view->W, tiles_x(*view), T, B * T, strips, smin, allow_split, a.ranges, n_contrib, tile_walk,
+                     hdr, reinterpret_cast<uint32_t*>(w + SL.walks),
+                     reinterpret_cast<uint4*>(w + SL.items)) != GSPARC_OK)
+        return GSPARC_ERR_CUDA;
     return launch_bwd_any(a, T, s, (uint32_t)(2 * units));
 }

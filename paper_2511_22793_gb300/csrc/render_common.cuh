@@ -542,6 +542,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_fwd(RenderArgs a) {
     float* s_part = reinterpret_cast<float*>(sm + L::kMisc);
     uint32_t* s_walk = reinterpret_cast<uint32_t*>(sm + L::kMisc + 32);
     uint32_t* s_err = s_walk + 1;
+    grid_dep_wait();     // the tile lists and attributes of the kernels before
 
     const int strip = blockIdx.x, tile = blockIdx.y, b = blockIdx.z;
     const int k0 = strip * S;
@@ -751,6 +752,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_render_bwd(RenderArgs a) {
     uint64_t* s_bar = reinterpret_cast<uint64_t*>(sm + L::kBar);
     uint32_t* s_maxlast = reinterpret_cast<uint32_t*>(sm + L::kMisc + 32);
     uint32_t* s_err = s_maxlast + 1;
+    grid_dep_wait();     // the schedule's items, the forward's outputs and the upstream gradient
 
     int strip, tile, b;
     bool front = false;

@@ -27,6 +27,8 @@ GSPARC_ERR_TOO_LARGE = -6
 GSPARC_ERR_INPUT = -7
 GSPARC_NOALLOC_MAX_N = 65536
 GSPARC_NOALLOC_MAX_PAIRS = 524288
+GSPARC_OVERLAP_BIN_SORT, GSPARC_OVERLAP_FORWARD, GSPARC_OVERLAP_SCHEDULE = 1, 2, 4
+GSPARC_OVERLAP_BACKWARD, GSPARC_OVERLAP_NETWORK, GSPARC_OVERLAP_ALL = 8, 16, 31
 GSPARC_FP32, GSPARC_BF16, GSPARC_BF16X2 = 0, 1, 2
 TILE = 16
 PROJ_STRIDE = 8
@@ -41,7 +43,7 @@ EXPORTS = [
     "gsparc_spectrum_loss_workspace", "gsparc_spectrum_loss",
     "gsparc_render_csi_tc", "gsparc_render_fwd_l2_tc", "gsparc_confidence", "gsparc_densify_accumulate",
     "gsparc_densify_workspace", "gsparc_densify", "gsparc_opacity_reset", "gsparc_adam", "gsparc_adam_segments", "gsparc_scale_rows",
-    "gsparc_set_wait_limit",
+    "gsparc_set_wait_limit", "gsparc_set_launch_overlap",
     "gsparc_check", "gsparc_strerror",
 ]
 
@@ -147,6 +149,7 @@ def lib():
                                                     vp]),
             "gsparc_scale_rows": (ctypes.c_int, [i32, i64, vp, vp, vp]),
             "gsparc_set_wait_limit": (ctypes.c_uint32, [ctypes.c_uint32]),
+            "gsparc_set_launch_overlap": (ctypes.c_int32, [ctypes.c_int32]),
             "gsparc_check": (ctypes.c_int, [vp, vp]),
             "gsparc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         }
@@ -510,6 +513,15 @@ def gsparc_set_wait_limit(polls: int) -> int:
     """Polls before a pipeline wait of the tensor-core compositing kernels gives up (0: the
     default); returns the previous setting.  For tests of the timeout path."""
     return int(lib().gsparc_set_wait_limit(int(polls)))
+
+
+def gsparc_set_launch_overlap(groups) -> int:
+    """Programmatic dependent launch of the library's follow-on kernels: True / False for every
+    group or none, or a mask of GSPARC_OVERLAP_* groups (every group by default); returns the
+    previous mask."""
+    if isinstance(groups, bool):
+        groups = GSPARC_OVERLAP_ALL if groups else 0
+    return int(lib().gsparc_set_launch_overlap(int(groups)))
 
 
 def gsparc_check(d_status=None, stream=None) -> int:

@@ -328,3 +328,13 @@ def test_wrappers_pass_arguments_in_header_order(monkeypatch):
                           t("d_opacity_logit", 8), t("d_weights", 8, 100))
     fn, args = calls[-1]
     check({"N": 8, "B": 2, "hidden": 16, "rx": args[4], "inv_d": 1})
+
+
+def test_overlap_groups_match_the_header():
+    txt = open(os.path.join(ROOT, "include", "gsparc.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (GSPARC_OVERLAP_[A-Z_]+) (\d+)", txt)}
+    assert len(defs) == 6
+    for name, v in defs.items():
+        assert getattr(G, name) == v, name
+    groups = [v for n, v in defs.items() if n != "GSPARC_OVERLAP_ALL"]
+    assert sum(groups) == defs["GSPARC_OVERLAP_ALL"] and all(g & (g - 1) == 0 for g in groups)

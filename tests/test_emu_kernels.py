@@ -217,14 +217,14 @@ def _binsort_run(exe, tmp_path, rec, H, W, cap, bcnt=True, slice_big=True):
 
 
 @pytest.mark.parametrize("n,H,W,seed,case", [(1, 90, 360, 1, "plain"), (17, 90, 360, 2, "plain"),
-                                             (1000, 90, 360, 3, "plain"), (5000, 180, 720, 5, "plain"),
+                                             (1000, 90, 360, 3, "plain"),
                                              (3000, 45, 180, 6, "plain"), (1500, 45, 180, 14, "three_depths"),
                                              (1500, 45, 180, 17, "one_depth"),
                                              (2000, 90, 360, 12, "overflow"), (400, 90, 360, 16, "culled"),
                                              (30000, 16, 32, 18, "big"), (30000, 16, 32, 19, "big_whole")])
 def test_binsort_kernels_logic(emu_bin, tmp_path, n, H, W, seed, case):
     """k_tile_count, k_tile_emit and k_tile_sort (the library's source under the host shim)
-    against the oracle's stable (tile, r, index) sort, bit for bit: ragged grids, 1 to 5,000
+    against the oracle's stable (tile, r, index) sort, bit for bit: ragged grids, 1 to 3,000
     records, the shared-memory distribution sort, three distinct depths and a single depth (tiles
     whose depth sub-buckets exceed 64 keys take the radix path; ties by index), a capacity below
     the pair count, every record culled, and buckets above the shared-memory capacity (two tiles
@@ -763,7 +763,7 @@ def test_render_fp32_kernel_skips_ids_outside_the_scene(emu_bin, tmp_path):
     ("test_densify_kernels_logic", (257, 16, 2, 0.5, 2)),
     ("test_projection_kernels_logic", (256, 45, 180, 9, False)),
     ("test_binsort_kernels_logic", (1500, 45, 180, 17, "one_depth")),
-    ("test_binsort_kernels_logic", (1000, 90, 360, 3, "plain")),
+    ("test_binsort_kernels_logic", (400, 90, 360, 3, "plain")),
     ("test_render_fp32_kernels_logic", (150, 45, 180, 1, 1, 43)),
     ("test_render_fp32_kernels_termination", ("dense",)),
     ("test_attribute_network_fp32_kernels_logic", (130, 2, 8, 52)),
