@@ -65,6 +65,10 @@ class TrainStep:
             G.gsparc_render_bwd_workspace(r.view, r.band, B)
         self.bwd_ws = torch.zeros(ws, dtype=torch.uint8, device=dev)
         self.side = torch.cuda.Stream(dev)
+        # the host-input step's third stream and the pinned word its loss is copied to (made here:
+        # neither can be created while a graph is being captured)
+        self.copy_s = torch.cuda.Stream(dev)
+        self.host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
         self.stages = STAGES
         # kernels of the library launched by one step: project 1, bin/sort 3, network 1, forward
         # with the loss fused 1, backward 2 (its schedule and the scheduled walks), network
@@ -182,11 +186,10 @@ class TrainStep:
         target on a third stream after them, beside projection, binning and the forward, which
         therefore writes the spectrum (the fused loss would wait for the whole target); the loss
         and dL/dz follow once the target is in, and the backward forms s_tot from the spectrum.
-        Same loss and gradients as enqueue()."""
+        The loss is copied to pinned host memory (`host_loss`) on the third stream while the
+        backward runs.  Same loss and gradients as enqueue()."""
         r, s = self.r, self.scene
         cur = torch.cuda.current_stream(r.device)
-        if not hasattr(self, "copy_s"):
-            self.copy_s = torch.cuda.Stream(r.device)
         inp.upload(0, 3)
         geo_in = torch.cuda.Event()
         geo_in.record(cur)
@@ -217,6 +220,13 @@ class TrainStep:
                                 self.logT, self.nc, self.n_used, d_status=r.status)
         cur.wait_event(tgt_in)
         G.gsparc_l2_loss(self.spec, self.target, self.loss, self.d_spec)
+        loss_done = torch.cuda.Event()
+        loss_done.record(cur)
+        self.copy_s.wait_event(loss_done)
+        with torch.cuda.stream(self.copy_s):
+            self.host_loss.copy_(self.loss, non_blocking=True)
+        loss_out = torch.cuda.Event()
+        loss_out.record(self.copy_s)
         fn = G.gsparc_render_bwd_tc_balanced if self.form == "tc" else G.gsparc_render_bwd_balanced
         fn(r.view, r.band, B, r.n, r.proj, r.tile_ranges, r.sorted_ids, self.attr, self.spec, None, self.logT,
            self.nc, self.d_spec, self.bwd_ws, self.d_attr, self.d_proj, d_status=r.status)
@@ -228,6 +238,7 @@ class TrainStep:
         joined2.record(self.side)
         self._mlp_bwd()
         cur.wait_event(joined2)
+        cur.wait_event(loss_out)
 
     def capture(self, inp=None):
         """The concurrent step (with inp: its host-input form) captured as one CUDA graph (the
