@@ -211,21 +211,29 @@ int gsparc_bin_sort_noalloc(const gsparc_view* view, int32_t N, const float* pro
  *   L = d_i + |mu_i - rx| (path length, metres).
  *   tx [B,3] device; rx [3] HOST; means [N,3]; opacity_logit [N]; latent [N,16];
  *   attr [B,N,4] out.  precision: GSPARC_FP32, GSPARC_BF16 or GSPARC_BF16X2.
+ *   hidden (may be NULL; GSPARC_FP32 only, else GSPARC_ERR_INVALID) out: the
+ *   post-ReLU activations for gsparc_attr_mlp_bwd, feature-major
+ *   [2 * mlp->hidden][ld], ld = B*N rounded up to a multiple of 4, row
+ *   b*N + i: h1 in the first mlp->hidden feature rows, h2 in the next;
+ *   16-byte aligned.  The ld - B*N padding columns are not written.
  */
 int gsparc_attr_mlp(int32_t N, int32_t B, const float* tx, const float* rx, const float* means,
                     const float* opacity_logit, const float* latent, const gsparc_mlp* mlp,
-                    int32_t precision, float* attr, void* stream);
+                    int32_t precision, float* attr, float* hidden, void* stream);
 
 /*
  * Gradient of gsparc_attr_mlp in FP32 (Algorithm 1 Backprop through the
- * network), recomputing the forward activations.  d_attr [B,N,4] holds
- * dL/d(a, phi0, sigma, L).  Accumulates into d_means [N,3], d_opacity_logit
- * [N], d_latent [N,16] and every buffer of *grads.
+ * network).  d_attr [B,N,4] holds dL/d(a, phi0, sigma, L).  Accumulates into
+ * d_means [N,3], d_opacity_logit [N], d_latent [N,16] and every buffer of
+ * *grads.  hidden: the activations an FP32 gsparc_attr_mlp call of the same
+ * inputs stored (layout there; 16-byte aligned), read in place of
+ * recomputing them; NULL recomputes them.
  */
 int gsparc_attr_mlp_bwd(int32_t N, int32_t B, const float* tx, const float* rx, const float* means,
                         const float* opacity_logit, const float* latent, const gsparc_mlp* mlp,
                         const float* d_attr, float* d_means, float* d_opacity_logit,
-                        float* d_latent, const gsparc_mlp_grad* grads, void* stream);
+                        float* d_latent, const gsparc_mlp_grad* grads, const float* hidden,
+                        void* stream);
 
 /*
  * gsparc_attr_mlp_bwd with the network's matrix products on the tensor cores

@@ -101,12 +101,16 @@ __device__ __forceinline__ void load_h0(const RowIn& in, const float* __restrict
     h0[19] = in.logd;
 }
 
+// One thread per (transmitter, Gaussian) row.  hidden (may be null): the row's post-ReLU
+// activations h1 and h2 stored feature-major, hidden[j * ld + row] = h1_j and
+// hidden[(HD + j) * ld + row] = h2_j, for the backward to read instead of recomputing them.
 template <int HD>
 __global__ void __launch_bounds__(128) k_mlp_fwd(int N, int B, const float* __restrict__ tx, float rx0,
                                                  float rx1, float rx2, const float* __restrict__ means,
                                                  const float* __restrict__ ologit,
                                                  const float* __restrict__ latent, W w,
-                                                 float4* __restrict__ attr) {
+                                                 float4* __restrict__ attr, float* __restrict__ hidden,
+                                                 int64_t ld) {
     using L = WSmem<HD>;
     __shared__ float sw[L::kTotal];
     load_weights<HD>(w, sw);
@@ -124,6 +128,7 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(int N, int B, const float* __re
 #pragma unroll
         for (int f = 0; f < GSPARC_MLP_IN; ++f) acc = fmaf(h0[f], sw[L::kW1 + f * HD + j], acc);
         h1[j] = fmaxf(acc, 0.f);
+        if (hidden) hidden[(size_t)j * ld + row] = h1[j];
     }
     float o0 = sw[L::kB3 + 0], o1 = sw[L::kB3 + 1], o2 = sw[L::kB3 + 2];
 #pragma unroll 4
@@ -132,6 +137,7 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(int N, int B, const float* __re
 #pragma unroll
         for (int j = 0; j < HD; ++j) acc = fmaf(h1[j], sw[L::kW2 + j * HD + j2], acc);
         const float h2 = fmaxf(acc, 0.f);
+        if (hidden) hidden[(size_t)(HD + j2) * ld + row] = h2;
         o0 = fmaf(h2, sw[L::kW3 + j2 * 3 + 0], o0);
         o1 = fmaf(h2, sw[L::kW3 + j2 * 3 + 1], o1);
         o2 = fmaf(h2, sw[L::kW3 + j2 * 3 + 2], o2);
@@ -191,6 +197,45 @@ constexpr bool kHostShim = false;
 // Offset of rows r..r+3 (r a multiple of 4) of feature x in a feature-major array.
 __device__ __forceinline__ int fm4(int x, int r) { return x * kBwdRows + (((r >> 2) ^ ((x >> 2) & 7)) << 2); }
 __device__ __forceinline__ int fm(int x, int r) { return fm4(x, r & ~3) + (r & 3); }
+
+// A tile's stored activations (features 0..HD-1 of A1 and A2, from k_mlp_fwd's `hidden`) into
+// shared memory: a 16-byte asynchronous copy (cp.async: no registers held while it is in flight)
+// per 4-row group inside the rows, zeros past them (the padding rows' dL/do is zero, and these
+// values multiply it in the weight-gradient sums, so they must be finite).  Sixteen consecutive
+// threads read 256 contiguous bytes of one feature.  hidden and ld: 16-byte aligned, ld % 4 == 0.
+template <int HD>
+__device__ __forceinline__ void fetch_hidden(float* sm, const float* __restrict__ hidden, int64_t ld,
+                                             int64_t row0, int64_t rows, int t) {
+    using S = BwdSmem<HD>;
+    constexpr int G4 = kBwdRows / 4;
+    for (int e = t; e < 2 * HD * G4; e += kBwdThreads) {
+        const int f = e / G4, gi = e - f * G4;
+        const int64_t r = row0 + 4 * gi;
+        float* dst = sm + (f < HD ? S::kA1 + fm4(f, 4 * gi) : S::kA2 + fm4(f - HD, 4 * gi));
+        const float* src = hidden + (size_t)f * ld + r;
+#ifndef GSPARC_HOST_SHIM
+        if (r + 4 <= rows) {
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                             static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                         "l"(src)
+                         : "memory");
+            continue;
+        }
+#endif
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = r + q < rows ? src[q] : 0.f;
+    }
+#ifndef GSPARC_HOST_SHIM
+    asm volatile("cp.async.commit_group;" ::: "memory");
+#endif
+}
+
+// Completion of this thread's fetch_hidden copies (a block barrier then shows them to all).
+__device__ __forceinline__ void fetch_hidden_wait() {
+#ifndef GSPARC_HOST_SHIM
+    asm volatile("cp.async.wait_all;" ::: "memory");
+#endif
+}
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
@@ -284,7 +329,9 @@ __device__ __forceinline__ void load_raw(const float* __restrict__ tx, const flo
 }
 
 // Persistent CTAs of 128 threads over tiles of 64 rows.  Per tile: the rows' inputs (one thread
-// per row), the forward recomputed as tile products (h1 = relu(h0 W1 + b1), h2 = relu(h1 W2 + b2)),
+// per row), the forward's activations, recomputed as tile products (h1 = relu(h0 W1 + b1),
+// h2 = relu(h1 W2 + b2)) or, with `hidden` (k_mlp_fwd's stored h1 and h2, leading dimension ld),
+// copied in asynchronously while the previous tile finishes,
 // the outputs and dL/do per row, du2 per row, du1 = (du2 W2^T) . [h1 > 0] and dL/dh0 = du1 W1^T as
 // tile products, the weight gradients added into the 4x4 blocks each thread keeps in registers
 // across tiles (one atomic per weight entry per CTA at the end), and the per-row input gradients
@@ -294,7 +341,7 @@ __global__ void __launch_bounds__(kBwdThreads, HD <= 32 ? 3 : 1)
     k_mlp_bwd(int N, int B, const float* __restrict__ tx, float rx0, float rx1, float rx2,
               const float* __restrict__ means, const float* __restrict__ ologit, const float* __restrict__ latent,
               W w, const float4* __restrict__ d_attr, float* __restrict__ d_means, float* __restrict__ d_ologit,
-              float* __restrict__ d_latent, gsparc_mlp_grad g) {
+              float* __restrict__ d_latent, gsparc_mlp_grad g, const float* __restrict__ hidden, int64_t ld) {
     using S = BwdSmem<HD>;
     constexpr int IN = GSPARC_MLP_IN, R = kBwdRows, CW = HD / 8;
     GSPARC_DYNAMIC_SMEM(sm_raw);
@@ -341,6 +388,7 @@ __global__ void __launch_bounds__(kBwdThreads, HD <= 32 ? 3 : 1)
     RowRaw nxt{};
     if (rowt && (int64_t)blockIdx.x * R + t < rows)
         load_raw(tx, means, ologit, latent, d_attr, (int64_t)blockIdx.x * R + t, N, nxt);
+    if (hidden && (int64_t)blockIdx.x < tiles) fetch_hidden<HD>(sm, hidden, ld, (int64_t)blockIdx.x * R, rows, t);
     __syncthreads();
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         // rows' inputs (threads 0..63, one row each), then the next tile's raw inputs requested
@@ -378,7 +426,9 @@ __global__ void __launch_bounds__(kBwdThreads, HD <= 32 ? 3 : 1)
 #pragma unroll
             for (int f = 0; f < IN; ++f) sm[S::kA0 + fm(f, t)] = 0.f;
         }
+        if (hidden) fetch_hidden_wait();   // this tile's h1, h2, requested a phase ahead
         __syncthreads();
+        if (!hidden) {
         {   // h1 = relu(h0 W1 + b1)
             float c[4][CW];
 #pragma unroll
@@ -411,6 +461,7 @@ __global__ void __launch_bounds__(kBwdThreads, HD <= 32 ? 3 : 1)
             tile_store<CW>(sm + S::kA2, rg, cg, c);
         }
         __syncthreads();
+        }
         // outputs, dL/do and du2 = (W3 do) . [h2 > 0], per row
         float do0 = 0.f, do1 = 0.f, do2 = 0.f, s0 = 0.f;
         if (rowt) {
@@ -522,6 +573,8 @@ __global__ void __launch_bounds__(kBwdThreads, HD <= 32 ? 3 : 1)
             }
         }
         __syncthreads();
+        // A1 and A2 are free until the next tile's products: its stored activations on their way
+        if (hidden && tile + gridDim.x < tiles) fetch_hidden<HD>(sm, hidden, ld, (tile + gridDim.x) * R, rows, t);
         // the rows' input gradients: latents, ln d (network input and explicit term), means
         if (valid) {
             float* dl = d_latent + (size_t)i * GSPARC_LATENT;

@@ -100,9 +100,9 @@ def lib():
             "gsparc_bin_sort": (ctypes.c_int, [P(View), i32, vp, i64, vp, ctypes.c_size_t, vp, vp, vp,
                                                vp, vp, vp]),
             "gsparc_bin_sort_noalloc": (ctypes.c_int, [P(View), i32, vp, i64, vp, vp, vp, vp, vp, vp]),
-            "gsparc_attr_mlp": (ctypes.c_int, [i32, i32, vp, P(f32), vp, vp, vp, P(MLP), i32, vp, vp]),
+            "gsparc_attr_mlp": (ctypes.c_int, [i32, i32, vp, P(f32), vp, vp, vp, P(MLP), i32, vp, vp, vp]),
             "gsparc_attr_mlp_bwd": (ctypes.c_int, [i32, i32, vp, P(f32), vp, vp, vp, P(MLP), vp, vp,
-                                                   vp, vp, P(MLPGrad), vp]),
+                                                   vp, vp, P(MLPGrad), vp, vp]),
             "gsparc_attr_mlp_bwd_tc": (ctypes.c_int, [i32, i32, vp, P(f32), vp, vp, vp, P(MLP), i32, vp,
                                                       vp, vp, vp, P(MLPGrad), vp]),
             "gsparc_emission_stride": (i32, [i32]),
@@ -258,18 +258,25 @@ def gsparc_bin_sort_noalloc(view, n, proj, pair_capacity, sorted_ids, sorted_key
           _stream(stream))
 
 
-def gsparc_attr_mlp(tx, rx, means, opacity_logit, latent, mlp: MLP, precision, attr, stream=None):
+def hidden_ld(rows: int) -> int:
+    """Leading dimension of the network's stored activations (gsparc_attr_mlp's `hidden`)."""
+    return (int(rows) + 3) // 4 * 4
+
+
+def gsparc_attr_mlp(tx, rx, means, opacity_logit, latent, mlp: MLP, precision, attr, stream=None, hidden=None):
+    """hidden (FP32 only): [2 * mlp.hidden * hidden_ld(B * N)] floats that receive the activations
+    gsparc_attr_mlp_bwd can take instead of recomputing them."""
     rxa = (ctypes.c_float * 3)(*[float(v) for v in rx])
     _call("gsparc_attr_mlp", means.shape[0], tx.shape[0], _p(tx), rxa, _p(means), _p(opacity_logit),
-          _p(latent), ctypes.byref(mlp), int(precision), _p(attr), _stream(stream))
+          _p(latent), ctypes.byref(mlp), int(precision), _p(attr), _p(hidden), _stream(stream))
 
 
 def gsparc_attr_mlp_bwd(tx, rx, means, opacity_logit, latent, mlp: MLP, d_attr, d_means,
-                        d_opacity_logit, d_latent, grads: MLPGrad, stream=None):
+                        d_opacity_logit, d_latent, grads: MLPGrad, stream=None, hidden=None):
     rxa = (ctypes.c_float * 3)(*[float(v) for v in rx])
     _call("gsparc_attr_mlp_bwd", means.shape[0], tx.shape[0], _p(tx), rxa, _p(means),
           _p(opacity_logit), _p(latent), ctypes.byref(mlp), _p(d_attr), _p(d_means),
-          _p(d_opacity_logit), _p(d_latent), ctypes.byref(grads), _stream(stream))
+          _p(d_opacity_logit), _p(d_latent), ctypes.byref(grads), _p(hidden), _stream(stream))
 
 
 def gsparc_attr_mlp_bwd_tc(tx, rx, means, opacity_logit, latent, mlp: MLP, precision, d_attr, d_means,

@@ -151,12 +151,14 @@ class Renderer:
 
     # -- per-query attributes and compositing ---------------------------------------
     def attributes(self, scene: DeviceScene, mlp: DeviceMLP, tx: torch.Tensor, precision=G.GSPARC_FP32,
-                   out=None, stream=None):
+                   out=None, stream=None, hidden=None):
+        """hidden (FP32): a buffer of 2 * mlp.hidden * hidden_ld(B * n) floats that receives the
+        network's activations for attributes_backward."""
         B = int(tx.shape[0])
         attr = out if out is not None else torch.empty((B, self.n, 4), dtype=torch.float32,
                                                        device=self.device)
         G.gsparc_attr_mlp(tx, self.rx, scene.means, scene.opacity_logit, scene.latent, mlp.struct(),
-                          precision, attr, stream)
+                          precision, attr, stream, hidden=hidden)
         return attr
 
     def alloc_outputs(self, B):
@@ -220,8 +222,9 @@ class Renderer:
            d_status=self.status)
 
     def attributes_backward(self, scene, mlp, tx, d_attr, d_means, d_ologit, d_latent, d_weights,
-                            stream=None, tensor_cores=False):
-        """tensor_cores: the tcgen05 form (split-BF16 products, hidden 16 or 32)."""
+                            stream=None, tensor_cores=False, hidden=None):
+        """tensor_cores: the tcgen05 form (split-BF16 products, hidden 16 or 32); hidden: the FP32
+        form reads the activations attributes(hidden=...) stored instead of recomputing them."""
         if tensor_cores:
             G.gsparc_attr_mlp_bwd_tc(tx, self.rx, scene.means, scene.opacity_logit, scene.latent,
                                      mlp.struct(), G.GSPARC_BF16X2, d_attr, d_means, d_ologit, d_latent,
@@ -229,7 +232,7 @@ class Renderer:
         else:
             G.gsparc_attr_mlp_bwd(tx, self.rx, scene.means, scene.opacity_logit, scene.latent,
                                   mlp.struct(), d_attr, d_means, d_ologit, d_latent,
-                                  G.make_mlp_grad(*d_weights), stream)
+                                  G.make_mlp_grad(*d_weights), stream, hidden=hidden)
 
     def project_backward(self, scene, d_proj, d_means, d_log_scales, d_quats, stream=None):
         G.gsparc_project_bwd(self.view, scene.means, scene.log_scales, scene.quats, d_proj, d_means,

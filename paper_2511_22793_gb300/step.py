@@ -58,6 +58,10 @@ class TrainStep:
         tc = form == "tc"
         self.mlp_tc = tc and mlp.hidden in (16, 32)
         self.mlp_prec = G.GSPARC_BF16X2 if tc else G.GSPARC_FP32
+        # The FP32 network backward recomputes the forward's activations: storing them in the forward
+        # (gsparc_attr_mlp's `hidden`) makes the backward 33 -> 29 us, but the forward's 12.8 MB of
+        # extra stores, on the second stream beside projection and bin/sort, cost the step more.
+        self.hidden = None
         strips = G.s_tot_strips(r.K) if tc else G.fp32_strips(r.K)
         self.s_tot = torch.empty((B, strips, r.H, r.W), dtype=torch.float32, device=dev)
         self.walks = r.walk_buffer(B)
@@ -92,7 +96,7 @@ class TrainStep:
     def _mlp_fwd(self, stream=None):
         s = self.scene
         G.gsparc_attr_mlp(self.tx, self.r.rx, s.means, s.opacity_logit, s.latent, self.mlp_s, self.mlp_prec,
-                          self.attr, stream)
+                          self.attr, stream, hidden=self.hidden)
 
     def _mlp_bwd(self, stream=None):
         s, g = self.scene, self.grads
@@ -101,7 +105,7 @@ class TrainStep:
                                      G.GSPARC_BF16X2, self.d_attr, g[0], g[3], g[4], self.grad_s, stream)
         else:
             G.gsparc_attr_mlp_bwd(self.tx, self.r.rx, s.means, s.opacity_logit, s.latent, self.mlp_s,
-                                  self.d_attr, g[0], g[3], g[4], self.grad_s, stream)
+                                  self.d_attr, g[0], g[3], g[4], self.grad_s, stream, hidden=self.hidden)
 
     def _proj_bwd(self, stream=None):
         s, g = self.scene, self.grads

@@ -42,13 +42,13 @@ static void mlp(int n, int B, const float* tx, const float* means, const float* 
     const int64_t rows = (int64_t)n * B;
     if (!backward) {
         emu_launch(emu_dim3{(unsigned)((rows + 127) / 128), 1, 1}, 128, gsparc::k_mlp_fwd<HD>, n, B, tx, 0.f, 0.f,
-                   0.f, means, ologit, latent, w, attr);
+                   0.f, means, ologit, latent, w, attr, static_cast<float*>(nullptr), (int64_t)0);
         return;
     }
     const int64_t tiles = (rows + gsparc::kBwdRows - 1) / gsparc::kBwdRows;
     emu_launch_smem(emu_dim3{(unsigned)std::min<int64_t>(tiles, 152 * 3), 1, 1}, gsparc::kBwdThreads,
                     (size_t)gsparc::BwdSmem<HD>::kTotal * sizeof(float), gsparc::k_mlp_bwd<HD>, n, B, tx, 0.f, 0.f,
-                    0.f, means, ologit, latent, w, dattr, dm, dol, dlat, g);
+                    0.f, means, ologit, latent, w, dattr, dm, dol, dlat, g, static_cast<const float*>(nullptr), (int64_t)0);
 }
 
 int main(int argc, char** argv) {

@@ -108,7 +108,15 @@ def test_invalid_arguments_rejected_on_host(L):
     m.hidden = 12
     rx = (ctypes.c_float * 3)(0, 0, 0)
     assert L.gsparc_attr_mlp(10, 1, vp(256), rx, vp(256), vp(256), vp(256), ctypes.byref(m), 0,
-                             vp(256), None) == G.GSPARC_ERR_INVALID
+                             vp(256), None, None) == G.GSPARC_ERR_INVALID
+    m.hidden = 32
+    for w in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        setattr(m, w, vp(256))
+    # stored activations: FP32 only, 16-byte aligned
+    assert L.gsparc_attr_mlp(10, 1, vp(256), rx, vp(256), vp(256), vp(256), ctypes.byref(m), G.GSPARC_BF16X2,
+                             vp(256), vp(256), None) == G.GSPARC_ERR_INVALID
+    assert L.gsparc_attr_mlp(10, 1, vp(256), rx, vp(256), vp(256), vp(256), ctypes.byref(m), G.GSPARC_FP32,
+                             vp(256), vp(260), None) == G.GSPARC_ERR_INVALID
     assert L.gsparc_adam(10, vp(256), vp(256), vp(256), vp(256), ctypes.c_float(1e-3),
                          ctypes.c_float(0.9), ctypes.c_float(0.999), ctypes.c_float(1e-15), 0, None) == \
         G.GSPARC_ERR_INVALID

@@ -319,11 +319,13 @@ def test_render_fp32_kernels_logic(emu_bin, tmp_path, n, H, W, K, B, seed):
             assert np.linalg.norm(dattr[b, :, col] - refs[b][:, c]) <= 1e-3 * np.linalg.norm(refs[b][:, c]), (b, c)
 
 
-@pytest.mark.parametrize("n,B,hidden,seed", [(300, 1, 32, 51), (130, 2, 8, 52), (200, 1, 64, 53),
-                                             (70, 3, 16, 54)])
-def test_attribute_network_fp32_kernels_logic(emu_bin, tmp_path, n, B, hidden, seed):
+@pytest.mark.parametrize("n,B,hidden,seed,keep", [(300, 1, 32, 51, 0), (130, 2, 8, 52, 0), (200, 1, 64, 53, 0),
+                                                  (70, 3, 16, 54, 0), (300, 1, 32, 51, 1), (70, 3, 16, 54, 1)])
+def test_attribute_network_fp32_kernels_logic(emu_bin, tmp_path, n, B, hidden, seed, keep):
     """k_mlp_fwd and k_mlp_bwd (the library's FP32 attribute network, under the host shim; the
-    backward as two persistent CTAs taking several 128-row passes each) against the oracle's
+    backward as two persistent CTAs taking several 128-row passes each; with keep, the forward
+    stores its activations and the backward reads them, padding rows of the buffer holding NaN
+    that the backward must not take in) against the oracle's
     attributes (2e-5 relative per component) and its vector-Jacobian product (1e-4 relative L2
     for the means, logits, latents and every weight block); the seeds keep every hidden
     pre-activation more than 1e-5 from the ReLU kink, so both sides take the same decisions."""
@@ -336,7 +338,7 @@ def test_attribute_network_fp32_kernels_logic(emu_bin, tmp_path, n, B, hidden, s
     tx = synth.make_tx(B, seed=seed + 2)
     rx = np.zeros(3, np.float32)
     d_attr = np.random.default_rng(seed + 3).normal(size=(B, n, 4)).astype(np.float32)
-    payload = np.array([n, B, hidden], np.int32).tobytes() + tx.tobytes() + rx.tobytes() + sc.means.tobytes() + \
+    payload = np.array([n, B, hidden, keep], np.int32).tobytes() + tx.tobytes() + rx.tobytes() + sc.means.tobytes() + \
         sc.opacity_logit.tobytes() + sc.latent.tobytes() + b"".join(a.tobytes() for a in mlp.arrays()) + \
         d_attr.tobytes()
     raw = _run(exe, tmp_path, payload)
@@ -766,7 +768,7 @@ def test_render_fp32_kernel_skips_ids_outside_the_scene(emu_bin, tmp_path):
     ("test_binsort_kernels_logic", (400, 90, 360, 3, "plain")),
     ("test_render_fp32_kernels_logic", (150, 45, 180, 1, 1, 43)),
     ("test_render_fp32_kernels_termination", ("dense",)),
-    ("test_attribute_network_fp32_kernels_logic", (130, 2, 8, 52)),
+    ("test_attribute_network_fp32_kernels_logic", (130, 2, 8, 52, 1)),
     ("test_emission_kernels_logic", (40, 8, 9, False)),
     ("test_spectrum_loss_kernels_logic", (1, 2, 16, 16)),
     ("test_heads_loss_and_adam_kernels_logic", (2, 3, 17, 23, 3001, 700, 1)),

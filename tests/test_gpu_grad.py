@@ -220,13 +220,14 @@ def _row_err(got, want):
     return np.linalg.norm(g - w, axis=1) / np.maximum(np.linalg.norm(w, axis=1), 1e-30)
 
 
-def _mlp_grads_gpu(r, ds, dm, txd, d_attr_np, tc):
+def _mlp_grads_gpu(r, ds, dm, txd, d_attr_np, tc, hidden=None):
     n = ds.n
     gm = torch.zeros((n, 3), device=DEV)
     go = torch.zeros(n, device=DEV)
     gl = torch.zeros((n, 16), device=DEV)
     gw = [torch.zeros_like(t) for t in dm.tensors()]
-    r.attributes_backward(ds, dm, txd, torch.tensor(d_attr_np, device=DEV), gm, go, gl, gw, tensor_cores=tc)
+    r.attributes_backward(ds, dm, txd, torch.tensor(d_attr_np, device=DEV), gm, go, gl, gw, tensor_cores=tc,
+                          hidden=hidden)
     torch.cuda.synchronize()
     return [t.cpu().numpy().astype(np.float64) for t in [gm, go, gl] + gw]
 
@@ -286,6 +287,79 @@ def test_attr_mlp_bwd_tensor_cores(n, B, hidden, seed):
         e_fp, e_or = rel_l2(tc[c], fp[c]), rel_l2(tc[c], ref[c])
         assert e_fp <= (1e-4 if c < 3 else 1e-3), "%s: relative L2 vs FP32 kernel %.3e" % (k, e_fp)
         assert e_or <= 1e-3, "%s: relative L2 vs oracle %.3e" % (k, e_or)
+
+
+def _fp32_kink_margin(sc, mlp, tx):
+    """Per Gaussian, min over transmitters and hidden units of |u| - bound(u), u the FP64
+    pre-activation and bound(u) = 1e-5 (1 + sum |terms|), layer 2 also carrying layer 1's bound
+    through |W2| (FP32 rounding of a sum of at most 65 terms is below 65 * 2^-24 ~ 4e-6 of its
+    sum of magnitudes): FP32 sums of the same terms in any order (the forward's per-row dot
+    products, the backward's tile products) and the exact sum take the same ReLU decision where
+    it is > 0."""
+    f64 = lambda a: torch.tensor(np.asarray(a), dtype=torch.float64)
+    means, latent = f64(sc.means), f64(sc.latent)
+    W1, b1, W2, b2 = (f64(a) for a in mlp.arrays()[:4])
+    out = torch.full((sc.n,), float("inf"), dtype=torch.float64)
+    for t in np.asarray(tx, dtype=np.float64):
+        d = torch.clamp(torch.linalg.norm(means - f64(t), dim=1), min=0.01)
+        h0 = torch.cat([f64(t).reshape(1, 3).expand(sc.n, 3), latent, torch.log(d).reshape(-1, 1)], 1)
+        u1 = h0 @ W1 + b1
+        h1 = torch.relu(u1)
+        u2 = h1 @ W2 + b2
+        bnd1 = 1e-5 * (1 + h0.abs() @ W1.abs() + b1.abs())
+        bnd2 = 1e-5 * (1 + h1.abs() @ W2.abs() + b2.abs()) + bnd1 @ W2.abs()
+        m1 = (u1.abs() - bnd1).min(1).values
+        m2 = (u2.abs() - bnd2).min(1).values
+        out = torch.minimum(out, torch.minimum(m1, m2))
+    return out.numpy()
+
+
+@pytest.mark.parametrize("n,B,hidden,seed", [(3000, 1, 32, 41), (777, 2, 32, 44), (1001, 3, 16, 42),
+                                            (513, 1, 64, 45), (999, 1, 8, 46)])
+def test_attr_mlp_bwd_stored_activations(n, B, hidden, seed):
+    """gsparc_attr_mlp_bwd reading the activations the FP32 forward stored (the buffer NaN
+    beforehand, so its unwritten padding columns must stay out of every sum) against the same call
+    recomputing them and against the FP64 oracle.  The forward's attributes are unchanged by
+    storing, bit for bit; every stored entry is finite.  The stored activations are the forward's
+    own sums, the recomputed ones the backward's tile products (and FP64's sums are exact), so a
+    ReLU decision can differ only at a pre-activation within FP32 rounding of zero: rows differing
+    by more than 1e-4 from the recomputing call or 1e-3 from the oracle must have such a kink and
+    are left out (their upstream gradient zeroed); the rest agree to 1e-5 relative L2
+    (per-Gaussian gradients) and 1e-4 (weight gradients), and everything is within 1e-3 of the
+    oracle."""
+    sc = synth.make_scene(n, seed=seed)
+    mlp = synth.make_mlp(hidden, seed=seed + 1)
+    tx = synth.make_tx(B, seed=seed + 2)
+    r = Renderer(90, 360, 1, n, device=DEV)
+    ds = DeviceScene.from_host(sc, DEV)
+    dm = DeviceMLP.from_host(mlp, DEV)
+    txd = torch.tensor(tx, device=DEV)
+    ld = G.hidden_ld(B * n)
+    hid = torch.full((2 * hidden * ld,), float("nan"), device=DEV)
+    a0 = r.attributes(ds, dm, txd)
+    a1 = r.attributes(ds, dm, txd, hidden=hid)
+    torch.cuda.synchronize()
+    assert torch.equal(a0, a1)
+    h = hid.view(2 * hidden, ld)
+    assert torch.isfinite(h[:, :B * n]).all() and (h[:, :B * n] >= 0).all()
+    d_attr_np = np.random.default_rng(seed + 3).normal(size=(B, n, 4)).astype(np.float32)
+    rec = _mlp_grads_gpu(r, ds, dm, txd, d_attr_np, False)
+    kept = _mlp_grads_gpu(r, ds, dm, txd, d_attr_np, False, hidden=hid)
+    ref = _mlp_grads_oracle(sc, mlp, tx, d_attr_np)
+    differ = np.zeros(n, bool)
+    for c in range(3):
+        differ |= (_row_err(kept[c], rec[c]) > 1e-4) | (_row_err(kept[c], ref[c]) > 1e-3)
+    margin = _fp32_kink_margin(sc, mlp, tx)
+    assert np.all(margin[differ] <= 0.0), np.flatnonzero(differ & (margin > 0))
+    if differ.any():
+        d_attr_np[:, differ] = 0.0
+        rec = _mlp_grads_gpu(r, ds, dm, txd, d_attr_np, False)
+        kept = _mlp_grads_gpu(r, ds, dm, txd, d_attr_np, False, hidden=hid)
+        ref = _mlp_grads_oracle(sc, mlp, tx, d_attr_np)
+    for k, (a, b, c) in enumerate(zip(kept, rec, ref)):
+        bound = 1e-5 if k < 3 else 1e-4
+        assert np.linalg.norm(a - b) <= bound * np.linalg.norm(b), k
+        assert np.linalg.norm(a - c) <= 1e-3 * np.linalg.norm(c), k
 
 
 @pytest.mark.parametrize("tc", [False, True])
