@@ -28,8 +28,12 @@ void launch_fwd(int N, int B, const float* tx, const float* rx, const float* mea
                 const float* latent, const W& w, float4* attr, float* hidden, cudaStream_t s) {
     const int64_t rows = (int64_t)N * B;
     const int blocks = (int)((rows + 127) / 128);
-    k_mlp_fwd<HD><<<blocks, 128, 0, s>>>(N, B, tx, rx[0], rx[1], rx[2], means, ologit, latent, w, attr, hidden,
-                                         hidden_ld(rows));
+    if (hidden)
+        k_mlp_fwd<HD, true><<<blocks, 128, 0, s>>>(N, B, tx, rx[0], rx[1], rx[2], means, ologit, latent, w, attr,
+                                                   hidden, hidden_ld(rows));
+    else
+        k_mlp_fwd<HD, false><<<blocks, 128, 0, s>>>(N, B, tx, rx[0], rx[1], rx[2], means, ologit, latent, w,
+                                                    attr, nullptr, 0);
 }
 
 template <int HD>

@@ -101,10 +101,11 @@ __device__ __forceinline__ void load_h0(const RowIn& in, const float* __restrict
     h0[19] = in.logd;
 }
 
-// One thread per (transmitter, Gaussian) row.  hidden (may be null): the row's post-ReLU
-// activations h1 and h2 stored feature-major, hidden[j * ld + row] = h1_j and
-// hidden[(HD + j) * ld + row] = h2_j, for the backward to read instead of recomputing them.
-template <int HD>
+// One thread per (transmitter, Gaussian) row.  KEEP: the row's post-ReLU activations h1 and h2
+// stored feature-major, hidden[j * ld + row] = h1_j and hidden[(HD + j) * ld + row] = h2_j, for
+// the backward to read instead of recomputing them (a separate instantiation, so that the form
+// without them compiles to the plain loops).
+template <int HD, bool KEEP = false>
 __global__ void __launch_bounds__(128) k_mlp_fwd(int N, int B, const float* __restrict__ tx, float rx0,
                                                  float rx1, float rx2, const float* __restrict__ means,
                                                  const float* __restrict__ ologit,
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(int N, int B, const float* __re
 #pragma unroll
         for (int f = 0; f < GSPARC_MLP_IN; ++f) acc = fmaf(h0[f], sw[L::kW1 + f * HD + j], acc);
         h1[j] = fmaxf(acc, 0.f);
-        if (hidden) hidden[(size_t)j * ld + row] = h1[j];
+        if constexpr (KEEP) hidden[(size_t)j * ld + row] = h1[j];
     }
     float o0 = sw[L::kB3 + 0], o1 = sw[L::kB3 + 1], o2 = sw[L::kB3 + 2];
 #pragma unroll 4
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(int N, int B, const float* __re
 #pragma unroll
         for (int j = 0; j < HD; ++j) acc = fmaf(h1[j], sw[L::kW2 + j * HD + j2], acc);
         const float h2 = fmaxf(acc, 0.f);
-        if (hidden) hidden[(size_t)(HD + j2) * ld + row] = h2;
+        if constexpr (KEEP) hidden[(size_t)(HD + j2) * ld + row] = h2;
         o0 = fmaf(h2, sw[L::kW3 + j2 * 3 + 0], o0);
         o1 = fmaf(h2, sw[L::kW3 + j2 * 3 + 1], o1);
         o2 = fmaf(h2, sw[L::kW3 + j2 * 3 + 2], o2);

@@ -32,9 +32,14 @@ static void run(int N, int B, const std::vector<float>& tx, const std::vector<fl
     const int64_t ld = (rows + 3) / 4 * 4;
     std::vector<float> hid(keep ? (size_t)(2 * HD) * ld : 0, nanf(""));
     float* hp = keep ? hid.data() : nullptr;
-    emu_launch(emu_dim3{(unsigned)((rows + 127) / 128), 1, 1}, 128, gsparc::k_mlp_fwd<HD>, N, B,
-               (const float*)tx.data(), rx[0], rx[1], rx[2], (const float*)means.data(), (const float*)ologit.data(),
-               (const float*)latent.data(), w, attr.data(), hp, ld);
+    if (keep)
+        emu_launch(emu_dim3{(unsigned)((rows + 127) / 128), 1, 1}, 128, gsparc::k_mlp_fwd<HD, true>, N, B,
+                   (const float*)tx.data(), rx[0], rx[1], rx[2], (const float*)means.data(),
+                   (const float*)ologit.data(), (const float*)latent.data(), w, attr.data(), hp, ld);
+    else
+        emu_launch(emu_dim3{(unsigned)((rows + 127) / 128), 1, 1}, 128, gsparc::k_mlp_fwd<HD, false>, N, B,
+                   (const float*)tx.data(), rx[0], rx[1], rx[2], (const float*)means.data(),
+                   (const float*)ologit.data(), (const float*)latent.data(), w, attr.data(), hp, ld);
     const int64_t tiles = (rows + gsparc::kBwdRows - 1) / gsparc::kBwdRows;
     const unsigned blocks = (unsigned)std::min<int64_t>(tiles, 2);
     gsparc_mlp_grad mg{g.W1.data(), g.b1.data(), g.W2.data(), g.b2.data(), g.W3.data(), g.b3.data()};
